@@ -1,0 +1,299 @@
+"""Classical and recursive fast matrix multiplication, and the error bounds.
+
+Oracle module (test infrastructure only; see the package docstring).
+
+A *plan* is a recursion tree.  ``Node(rule, children)`` applies ``rule`` at
+this node; ``children[r]`` is the node that computes product M_r one level
+down (``None`` = classical product at the base case).  Stationary and uniform
+non-stationary plans (Sec. 3.2, 3.3) are trees with one rule per level
+(:func:`uniform`); non-uniform plans (Sec. 3.4) give every node its own rule.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Callable, Optional, Sequence
+
+import numpy as np
+
+from . import precision
+from .rules import Rule, canonical, principal
+
+
+@dataclass
+class Node:
+    rule: Rule
+    children: list  # length R, entries Node or None
+
+
+def uniform(rules: Sequence[Rule]) -> Optional[Node]:
+    """Tree of a uniform non-stationary plan: ``rules[l]`` at every node of
+    level l+1 (Sec. 3.3).  Stationary = the same rule repeated (Sec. 3.2)."""
+    if not rules:
+        return None
+    child = uniform(rules[1:])
+    return Node(rules[0], [child] * rules[0].R)
+
+
+def dims(node: Optional[Node]):
+    """(prod m0, prod k0, prod n0) along one root-to-leaf path (all paths of a
+    plan partition alike, Sec. 3.4)."""
+    if node is None:
+        return 1, 1, 1
+    m, k, n = dims(node.children[0])
+    return node.rule.m0 * m, node.rule.k0 * k, node.rule.n0 * n
+
+
+def depth(node: Optional[Node]) -> int:
+    return 0 if node is None else 1 + depth(node.children[0])
+
+
+# ---------------------------------------------------------------------------
+# Products
+# ---------------------------------------------------------------------------
+
+def classical(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """C = AB by the classical algorithm in float64 (the base case of
+    Eq. 3.2); the inner products are evaluated by the BLAS matmul."""
+    return np.asarray(A, dtype=np.float64) @ np.asarray(B, dtype=np.float64)
+
+
+def classical_exact(A, B):
+    """C = AB with Python integers / Fractions, for brute force on tiny
+    inputs."""
+    M, K = len(A), len(A[0])
+    N = len(B[0])
+    return [[sum(A[i][k] * B[k][j] for k in range(K)) for j in range(N)] for i in range(M)]
+
+
+def classical_exact_fixed(A: np.ndarray, B: np.ndarray, frac_bits: int = 48):
+    """Exact C = AB for inputs that are multiples of 2^-frac_bits with
+    |entries| < 2 (fixed point), returned as an object array of Python
+    integers holding C * 2^(2 frac_bits).  Each input is split into four
+    16-bit integer limbs; the limb products are exact in int64 (K up to
+    2^20), and Python integers add them with their shifts."""
+    sa = np.round(np.asarray(A, np.float64) * 2.0**frac_bits)
+    sb = np.round(np.asarray(B, np.float64) * 2.0**frac_bits)
+    assert np.array_equal(sa / 2.0**frac_bits, A) and np.array_equal(sb / 2.0**frac_bits, B)
+    ia, ib = sa.astype(np.int64), sb.astype(np.int64)
+
+    def limbs(X):
+        sgn = np.sign(X)
+        X = np.abs(X)
+        return [sgn * ((X >> (16 * t)) & 0xFFFF) for t in range(4)]
+
+    la, lb = limbs(ia), limbs(ib)
+    out = np.zeros((A.shape[0], B.shape[1]), dtype=object)
+    for s, a in enumerate(la):
+        for t, b in enumerate(lb):
+            if not a.any() or not b.any():
+                continue
+            p = (a @ b).astype(object)
+            out = out + p * (1 << (16 * (s + t)))
+    return out
+
+
+def exact_to_float(Cint, frac_bits: int = 48) -> np.ndarray:
+    """Round the exact fixed-point result of classical_exact_fixed to float64."""
+    from fractions import Fraction
+    den = 1 << (2 * frac_bits)
+    return np.vectorize(lambda v: float(Fraction(int(v), den)))(Cint).astype(np.float64)
+
+
+def _seq_sum(terms, dtype):
+    """Sequential sum c_1 X_1 + c_2 X_2 + ... in the order given, each step
+    rounded to ``dtype`` (the summation model of Eq. 4.3)."""
+    acc = None
+    for c, X in terms:
+        t = (dtype(c) * X).astype(dtype)
+        acc = t if acc is None else (acc + t).astype(dtype)
+    return acc
+
+
+def _pad(X: np.ndarray, rows: int, cols: int) -> np.ndarray:
+    if X.shape == (rows, cols):
+        return X
+    out = np.zeros((rows, cols), dtype=X.dtype)
+    out[: X.shape[0], : X.shape[1]] = X
+    return out
+
+
+def _recurse(A, B, node, leaf, dtype):
+    if node is None:
+        return leaf(A, B)
+    r = canonical(node.rule)
+    m0, k0, n0 = r.m0, r.k0, r.n0
+    mb, kb, nb = A.shape[0] // m0, A.shape[1] // k0, B.shape[1] // n0
+    Ab = [A[p * mb:(p + 1) * mb, q * kb:(q + 1) * kb] for p in range(m0) for q in range(k0)]
+    Bb = [B[p * kb:(p + 1) * kb, q * nb:(q + 1) * nb] for p in range(k0) for q in range(n0)]
+    Ms = []
+    for j in range(r.R):
+        # S_r, T_r: sequential sums in index order (Eq. 3.2)
+        S = _seq_sum([(r.U[i, j], Ab[i]) for i in range(m0 * k0) if r.U[i, j] != 0], dtype)
+        T = _seq_sum([(r.V[i, j], Bb[i]) for i in range(k0 * n0) if r.V[i, j] != 0], dtype)
+        if S is None:
+            S = np.zeros((mb, kb), dtype)
+        if T is None:
+            T = np.zeros((kb, nb), dtype)
+        Ms.append(_recurse(S, T, node.children[j], leaf, dtype))
+    C = np.zeros((m0 * mb, n0 * nb), dtype=dtype)
+    for k in range(m0 * n0):
+        p, q = divmod(k, n0)
+        # C_k = sum_r W[k, r] M_r, r in order (Eq. 3.2)
+        blk = _seq_sum([(r.W[k, j], Ms[j]) for j in range(r.R) if r.W[k, j] != 0], dtype)
+        if blk is not None:
+            C[p * mb:(p + 1) * mb, q * nb:(q + 1) * nb] = blk
+    return C
+
+
+def fmm(A: np.ndarray, B: np.ndarray, plan: Optional[Node],
+        leaf: Optional[Callable] = None, dtype=np.float64) -> np.ndarray:
+    """C = AB by the recursive fast algorithm of Eq. 3.2 with the given plan.
+
+    A and B are zero-padded once, up front, so that every level partitions
+    evenly (Sec. 3.2 pads with zeros; reading: pad M, K, N to the next
+    multiple of the product of the base-case dimensions along the tree).
+    S_r, T_r and C_k are sequential sums in index order computed in
+    ``dtype``; the leaves call ``leaf(S, T)`` (default: classical float64).
+    """
+    leaf = leaf or classical
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    pm, pk, pn = dims(plan)
+    Mp, Kp, Np = -(-M // pm) * pm, -(-K // pk) * pk, -(-N // pn) * pn
+    Ap = _pad(np.asarray(A, dtype=dtype), Mp, Kp)
+    Bp = _pad(np.asarray(B, dtype=dtype), Kp, Np)
+    if M == 0 or N == 0:
+        return np.zeros((M, N), dtype=dtype)
+    return _recurse(Ap, Bp, plan, leaf, dtype)[:M, :N]
+
+
+def abs_plan(node: Optional[Node]) -> Optional[Node]:
+    """Same tree with |U|, |V|, |W|."""
+    if node is None:
+        return None
+    r = node.rule
+    ar = Rule(r.name + "|abs|", r.m0, r.k0, r.n0, np.abs(r.U), np.abs(r.V), np.abs(r.W),
+              r.order_a, r.order_b, r.order_c)
+    return Node(ar, [abs_plan(c) for c in node.children])
+
+
+def growth(A: np.ndarray, B: np.ndarray, plan: Optional[Node]) -> np.ndarray:
+    """Componentwise growth quantity of the proof of Theorem 4.1:
+        G_ij = sum_r |W-product| (sum_i |U-product| |A_i|) (sum_j |V-product| |B_j|)
+    evaluated entrywise (before the max-norms are taken).  The proof bounds
+    |C_k - fl(C_k)| by delta_k * eps * G to first order, and G <= (K/K0^L)
+    E^L ||A|| ||B||.  Computed as the fast algorithm run on |A|, |B| with
+    |U|, |V|, |W| in float64."""
+    return fmm(np.abs(A), np.abs(B), abs_plan(plan))
+
+
+# ---------------------------------------------------------------------------
+# Leaf products in reduced precision (emulation of the leaf formats)
+# ---------------------------------------------------------------------------
+
+def leaf_rounded(fmt: str) -> Callable:
+    """Leaf product with S and T rounded to ``fmt`` ('bf16', 'fp16') and the
+    product formed exactly (float64)."""
+    def leaf(S, T):
+        return classical(precision.round_to(S, fmt), precision.round_to(T, fmt))
+    return leaf
+
+
+def leaf_bf16x3(S, T):
+    """Leaf product with S = hi + lo, T = hi' + lo' split into bf16 parts and
+    the three products hi hi' + hi lo' + lo hi' formed exactly (float64)."""
+    sh, sl = precision.split_bf16(S)
+    th, tl = precision.split_bf16(T)
+    return classical(sh, th) + classical(sh, tl) + classical(sl, th)
+
+
+# ---------------------------------------------------------------------------
+# Bounds (Theorems 4.1, 4.2; Sec. 4.5)
+# ---------------------------------------------------------------------------
+
+def bound_uniform(rules: Sequence[Rule], K: int, normA: float, normB: float,
+                  eps: float) -> float:
+    """Theorem 4.2 (Theorem 4.1 when all rules are equal), first order:
+        (K/prod K0 + sum_l Q_l) (K/prod K0) (prod_l E_l) ||A|| ||B|| eps
+    with ||.|| the max-norm.  K is the (padded) inner dimension."""
+    pk = int(np.prod([r.k0 for r in rules])) if rules else 1
+    kl = K / pk
+    Qs = sum(principal(r).Q for r in rules)
+    Es = float(np.prod([principal(r).E for r in rules])) if rules else 1.0
+    return (kl + Qs) * kl * Es * normA * normB * eps
+
+
+def delta_vector(node: Optional[Node], chi: float = 0.0) -> np.ndarray:
+    """Accumulation counts delta_k of Sec. 4.5 without the K/prod K0 term,
+    over the flattened output blocks k = (k_1, ..., k_L) (k_1 slowest):
+    delta^{[l]}_k = gamma_{k_l} + max_{r: W[k_l, r] != 0} delta^{[l+1, r]}_k
+    with chi (the alpha + beta counts along the path) at the leaves."""
+    if node is None:
+        return np.array([chi])
+    r = canonical(node.rule)
+    p = principal(r)
+    subs = [delta_vector(node.children[j], chi + p.alpha[j] + p.beta[j]) for j in range(r.R)]
+    out = []
+    for k in range(r.m0 * r.n0):
+        cands = [subs[j] for j in range(r.R) if r.W[k, j] != 0]
+        out.append(p.gamma[k] + np.max(np.stack(cands), axis=0))
+    return np.concatenate(out)
+
+
+def xi_vector(node: Optional[Node]) -> np.ndarray:
+    """Growth factors xi_k of Sec. 4.5 (simplified form), flattened over
+    k = (k_1, ..., k_L): xi = sum_r |W[k_1, r]| a_r b_r xi^{child r}."""
+    if node is None:
+        return np.array([1.0])
+    r = canonical(node.rule)
+    p = principal(r)
+    subs = [xi_vector(node.children[j]) for j in range(r.R)]
+    out = []
+    for k in range(r.m0 * r.n0):
+        acc = np.zeros_like(subs[0])
+        for j in range(r.R):
+            if r.W[k, j] != 0:
+                acc = acc + abs(r.W[k, j]) * p.a[j] * p.b[j] * subs[j]
+        out.append(acc)
+    return np.concatenate(out)
+
+
+def bound_tree(plan: Optional[Node], K: int, normA: float, normB: float, eps: float) -> float:
+    """Sec. 4.5 bound for any plan: (K/prod K0 + max_k delta_k)(K/prod K0)
+    max_k xi_k ||A|| ||B|| eps (first order)."""
+    _, pk, _ = dims(plan)
+    kl = K / pk
+    return (kl + float(delta_vector(plan).max())) * kl * float(xi_vector(plan).max()) \
+        * normA * normB * eps
+
+
+def flop_count(plan: Optional[Node], M: int, K: int, N: int) -> dict:
+    """Leaf flops 2 * R^L * (M/pm)(K/pk)(N/pn) of the padded problem and the
+    classical 2MKN."""
+    pm, pk, pn = dims(plan)
+    leaves = 1
+    node = plan
+    while node is not None:
+        leaves *= node.rule.R
+        node = node.children[0]
+    Mp, Kp, Np = -(-M // pm) * pm, -(-K // pk) * pk, -(-N // pn) * pn
+    return {"leaf": 2.0 * leaves * (Mp // pm) * (Kp // pk) * (Np // pn),
+            "classical": 2.0 * M * K * N, "leaves": leaves}
+
+
+# ---------------------------------------------------------------------------
+# Errors (Sec. 6.5)
+# ---------------------------------------------------------------------------
+
+def err_max(C_hat: np.ndarray, C: np.ndarray) -> float:
+    return float(np.max(np.abs(np.asarray(C_hat, np.float64) - C))) if C.size else 0.0
+
+
+def err_componentwise(C_hat: np.ndarray, C: np.ndarray) -> float:
+    """max_ij |c_hat - c| / |c| over entries with c != 0 (Sec. 6.5)."""
+    C_hat = np.asarray(C_hat, np.float64)
+    nz = C != 0
+    if not nz.any():
+        return 0.0
+    return float(np.max(np.abs(C_hat[nz] - C[nz]) / np.abs(C[nz])))

@@ -1,0 +1,167 @@
+"""Pins for the oracle's recursive fast multiplication and its bounds.
+
+Pinned against: exact integer arithmetic (brute force and classical), exact
+rational brute force on tiny inputs, Theorem 4.1 / 4.2 and the componentwise
+first-order bound from the proof of Theorem 4.1, and Example 6.1.
+"""
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import fmm as F
+from oracle import precision as P
+from oracle import rules as R
+from paper_1507_00687_gb300 import inputs
+
+S, Wg, C121 = R.strassen(), R.winograd(), R.classical(1, 2, 1)
+
+
+@pytest.mark.parametrize("rules", [[S, S], [Wg], [Wg, Wg, Wg], [S, C121, S],
+                                   [R.fast323()], [S, R.fast323()]],
+                         ids=["S2", "W1", "W3", "S-C121-S", "f323", "S-f323"])
+def test_integer_inputs_exact(rules):
+    # n=16, entries in [-4, 4]: every intermediate is a small integer, so the
+    # fast algorithm must equal the classical product exactly.
+    A = inputs.integers((16, 16), -4, 4, seed=1)
+    B = inputs.integers((16, 16), -4, 4, seed=2)
+    assert np.array_equal(F.fmm(A, B, F.uniform(rules)), A @ B)
+
+
+@pytest.mark.parametrize("shape", [(13, 7, 9), (1, 1, 1), (5, 3, 2), (17, 33, 8), (0, 4, 3)])
+def test_ragged_shapes_padding_exact(shape):
+    M, K, N = shape
+    A = inputs.integers((M, K), -3, 3, seed=3)
+    B = inputs.integers((K, N), -3, 3, seed=4)
+    for rules in ([S], [S, S], [Wg, C121]):
+        out = F.fmm(A, B, F.uniform(rules))
+        assert out.shape == (M, N)
+        assert np.array_equal(out, A @ B)
+
+
+def test_brute_force_all_sign_patterns_2x2():
+    # Every A, B in {-1, 1}^{2x2}: compare with the exact rational product.
+    tree = F.uniform([S])
+    for bits in itertools.product((-1, 1), repeat=8):
+        A = np.array(bits[:4], float).reshape(2, 2)
+        B = np.array(bits[4:], float).reshape(2, 2)
+        exact = F.classical_exact([[Fraction(int(x)) for x in r] for r in A],
+                                  [[Fraction(int(x)) for x in r] for r in B])
+        assert np.array_equal(F.fmm(A, B, tree), np.array(exact, dtype=float))
+
+
+def test_brute_force_rationals_4x4():
+    g = np.random.default_rng(5)
+    for trial in range(20):
+        A = [[Fraction(int(g.integers(-9, 10)), int(g.integers(1, 5))) for _ in range(4)] for _ in range(4)]
+        B = [[Fraction(int(g.integers(-9, 10)), int(g.integers(1, 5))) for _ in range(4)] for _ in range(4)]
+        exact = np.array(F.classical_exact(A, B), dtype=float)
+        got = F.fmm(np.array(A, float), np.array(B, float), F.uniform([Wg, S]))
+        assert np.max(np.abs(got - exact)) <= 64 * 2.0**-53 * np.max(np.abs(exact)) + 1e-300
+
+
+def _fixed(shape, seed, bits=48):
+    # U[-1,1] rounded to 48 fractional bits, so classical_exact_fixed gives
+    # the exact product.
+    X = inputs.uniform(shape, -1.0, 1.0, seed)
+    return np.round(X * 2**bits) / 2**bits
+
+
+def test_exact_fixed_product_against_fractions():
+    A = _fixed((5, 7), 1)
+    B = _fixed((7, 3), 2)
+    want = F.classical_exact([[Fraction(x) for x in r] for r in A], [[Fraction(x) for x in r] for r in B])
+    got = F.classical_exact_fixed(A, B)
+    den = 1 << 96
+    assert all(Fraction(int(got[i, j]), den) == want[i][j] for i in range(5) for j in range(3))
+
+
+def test_theorem_4_1_config_small():
+    # Strassen, L = 2, n = 256, FP64, A, B ~ U[-1, 1]; bound of Theorem 4.1:
+    # (K/K0^L + Q L)(K/K0^L) E^L ||A|| ||B|| eps = (64 + 16) 64 144 eps.
+    A = _fixed((256, 256), 11)
+    B = _fixed((256, 256), 12)
+    C = F.exact_to_float(F.classical_exact_fixed(A, B))
+    got = F.fmm(A, B, F.uniform([S, S]))
+    eps = 2.0**-53
+    bound = F.bound_uniform([S, S], 256, np.abs(A).max(), np.abs(B).max(), eps)
+    assert bound == pytest.approx((64 + 16) * 64 * 144 * eps * np.abs(A).max() * np.abs(B).max())
+    assert bound <= 8.2e-11
+    err = F.err_max(got, C)
+    assert 0 < err <= bound
+    # componentwise form from the proof: |E_k| <= delta eps G (first order)
+    G = F.growth(A, B, F.uniform([S, S]))
+    delta = 256 / 4 + 2 * R.principal(S).Q
+    assert np.all(np.abs(got - C) <= delta * eps * G * (1 + 1e-6))
+
+
+@pytest.mark.parametrize("rules", [[Wg, C121, Wg], [S, Wg], [R.fast323(), S]],
+                         ids=["W-C-W", "S-W", "323-S"])
+def test_theorem_4_2_uniform_nonstationary(rules):
+    tree = F.uniform(rules)
+    pm, pk, pn = F.dims(tree)
+    A = _fixed((pm * 8, pk * 8), 21)
+    B = _fixed((pk * 8, pn * 8), 22)
+    C = F.exact_to_float(F.classical_exact_fixed(A, B))
+    got = F.fmm(A, B, tree)
+    bound = F.bound_uniform(rules, A.shape[1], np.abs(A).max(), np.abs(B).max(), 2.0**-53)
+    assert F.err_max(got, C) <= bound
+    assert F.bound_tree(tree, A.shape[1], np.abs(A).max(), np.abs(B).max(), 2.0**-53) == pytest.approx(bound)
+
+
+def test_theorem_special_cases():
+    # L = 0: K^2 ||A|| ||B|| eps (Sec. 4.3 remark)
+    assert F.bound_uniform([], 100, 1.0, 1.0, 1.0) == 100**2
+    # full recursion, square: (1 + Q L) E^L ||A|| ||B|| eps
+    L = 5
+    assert F.bound_uniform([S] * L, 2**L, 1.0, 1.0, 1.0) == (1 + 8 * L) * 12.0**L
+
+
+def test_growth_bound_relation():
+    # G <= (K/K0^L) E^L ||A|| ||B|| entrywise (last step of the proof)
+    A = inputs.uniform((32, 32), -1, 1, 31)
+    B = inputs.uniform((32, 32), -1, 1, 32)
+    for rules in ([S], [S, S], [Wg, Wg]):
+        G = F.growth(A, B, F.uniform(rules))
+        E = np.prod([R.principal(r).E for r in rules])
+        assert G.max() <= (32 / 2**len(rules)) * E * np.abs(A).max() * np.abs(B).max() * (1 + 1e-12)
+        assert np.all(G >= np.abs(A) @ np.abs(B) * (1 - 1e-12))
+
+
+def test_example_6_1_relative_error():
+    # Example 6.1: Strassen's c11 has relative error O(eps/z) without scaling,
+    # O(eps) with outside scaling.  Small perturbations make the roundings
+    # real (the example's own remark).
+    z = 1.2345e-9
+    A = np.array([[1.0, 1.0 + 2**-30], [1.0 - 2**-31, 1.0]])
+    B = np.array([[z, 1.0 + 2**-29], [z * (1 + 2**-28), 1.0]])
+    C = np.array(F.classical_exact([[Fraction(x) for x in r] for r in A],
+                                   [[Fraction(x) for x in r] for r in B]), dtype=float)
+    plain = F.fmm(A, B, F.uniform([S]))
+    rel_plain = abs(plain[0, 0] - C[0, 0]) / abs(C[0, 0])
+    from oracle import scaling as Sc
+    st = Sc.repeated(A, B, "O")
+    scaled = Sc.unscale(F.fmm(st.A, st.B, F.uniform([S])), st)
+    rel_scaled = abs(scaled[0, 0] - C[0, 0]) / abs(C[0, 0])
+    assert rel_plain > 1e3 * 2.0**-53
+    assert rel_scaled < 8 * 2.0**-53
+
+
+def test_emulated_leaf_formats_bracket():
+    # bf16x3 emulation is far closer to the exact product than bf16.
+    A = inputs.uniform((64, 64), -1, 1, 41)
+    B = inputs.uniform((64, 64), -1, 1, 42)
+    C = A @ B
+    tree = F.uniform([S])
+    e16 = F.err_max(F.fmm(A, B, tree, leaf=F.leaf_rounded("bf16"), dtype=np.float32), C)
+    ex3 = F.err_max(F.fmm(A, B, tree, leaf=F.leaf_bf16x3, dtype=np.float32), C)
+    assert ex3 < e16 / 64
+    G = F.growth(A, B, tree)
+    assert ex3 <= (3 * 2.0**-16 + 8 * 2.0**-24) * G.max()
+
+
+def test_flop_count():
+    f = F.flop_count(F.uniform([S, S]), 4096, 4096, 4096)
+    assert f["leaves"] == 49
+    assert f["leaf"] == 2.0 * 49 * 1024**3

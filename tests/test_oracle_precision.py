@@ -1,0 +1,47 @@
+"""Pins for the oracle's rounding emulation against IEEE / OCP definitions
+(hand-computed ties) and independent library conversions."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import precision as P
+
+
+def test_bf16_ties_to_even():
+    x = np.array([1 + 2**-8, 1 + 3 * 2**-8, -(1 + 2**-8), 1 + 2**-8 + 2**-20, 0.0])
+    assert list(P.round_to(x, "bf16")) == [1.0, 1 + 2**-6, -1.0, 1 + 2**-7, 0.0]
+
+
+def test_fp16_range_and_subnormals():
+    x = np.array([65504.0, 65520.0, 2.0**-24, 2.0**-25, 3 * 2.0**-25])
+    r = P.round_to(x, "fp16")
+    assert r[0] == 65504.0 and np.isinf(r[1])
+    assert r[2] == 2.0**-24 and r[3] == 0.0 and r[4] == 2.0**-23
+
+
+@pytest.mark.parametrize("fmt,tdtype", [("bf16", torch.bfloat16), ("fp16", torch.float16)])
+def test_matches_library_conversion(fmt, tdtype):
+    g = np.random.default_rng(7)
+    x = np.concatenate([g.normal(size=4000) * 10.0 ** g.integers(-6, 6, size=4000),
+                        g.uniform(-1, 1, size=1000)]).astype(np.float32).astype(np.float64)
+    if fmt == "fp16":
+        x = x[np.abs(x) < 60000]
+    want = torch.from_numpy(x).to(torch.float32).to(tdtype).to(torch.float64).numpy()
+    assert np.array_equal(P.round_to(x, fmt), want)
+
+
+def test_e4m3_matches_library_in_range():
+    g = np.random.default_rng(8)
+    x = g.uniform(-440, 440, size=3000) * 2.0 ** g.integers(-10, 0, size=3000)
+    want = torch.from_numpy(x).to(torch.float32).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(P.round_to(x, "e4m3"), want)
+    assert P.round_to(np.array([1000.0]), "e4m3")[0] == 448.0
+
+
+def test_split_bf16():
+    g = np.random.default_rng(9)
+    x = g.uniform(-1, 1, size=10000).astype(np.float32).astype(np.float64)
+    hi, lo = P.split_bf16(x)
+    assert np.array_equal(hi, P.round_to(hi, "bf16")) and np.array_equal(lo, P.round_to(lo, "bf16"))
+    assert np.all(np.abs(x - hi - lo) <= 2.0**-16 * np.abs(x))
+    assert np.all(np.abs(lo) <= 2.0**-8 * np.abs(x))

@@ -1,0 +1,180 @@
+"""Pins for the oracle's rules, principal quantities and rule transforms.
+
+Every expected value is printed in the paper (golden files cite where) or
+follows from the Brent equations (exact rational check).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fmm as F
+from oracle import rules as R
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+RULES = {
+    "classical222": lambda: R.classical(2, 2, 2),
+    "strassen": R.strassen,
+    "strassen*classical211": lambda: R.compose(R.strassen(), R.classical(2, 1, 1)),
+    "strassen*classical121": lambda: R.compose(R.strassen(), R.classical(1, 2, 1)),
+    "fast323": R.fast323,
+    "fast323^rot": lambda: R.rotate(R.fast323()),
+}
+
+
+@pytest.mark.parametrize("row", _golden("table1.txt"), ids=lambda r: r[0])
+def test_table1_principal_quantities(row):
+    name, m0, k0, n0, Rk, nnz, Q, E = row
+    rule = RULES[name]()
+    p = R.principal(rule)
+    assert (rule.m0, rule.k0, rule.n0, rule.R) == (int(m0), int(k0), int(n0), int(Rk))
+    assert p.nnz == int(nnz)
+    assert p.Q == float(Q)
+    assert p.E == float(E)
+    assert R.brent_violations(rule) == 0
+
+
+def test_stability_vectors_printed():
+    g = {r[0]: [float(x) for x in r[1:]] for r in _golden("stability_vectors.txt")}
+    assert list(R.principal(R.strassen()).e) == g["strassen"]
+    # <3,2,3>: W rows are row-major C; the printed vector lists column-major C
+    e = R.principal(R.fast323()).e.reshape(3, 3)
+    assert list(e.T.reshape(-1)) == g["fast323_colmajor"]
+
+
+@pytest.mark.parametrize("make", [R.strassen, R.winograd, R.fast323,
+                                  lambda: R.classical(2, 2, 2),
+                                  lambda: R.classical(1, 2, 1),
+                                  lambda: R.classical(2, 1, 1),
+                                  lambda: R.classical(2, 3, 4)])
+def test_brent_holds(make):
+    assert R.brent_violations(make()) == 0
+
+
+def test_strassen_stated_ordering_is_not_matmul():
+    # The App. A numbers under the ordering App. A states violate Brent; this
+    # pins the index-order reading used everywhere else.
+    assert R.brent_violations(R.strassen_printed_convention()) == 12
+
+
+def test_brent_catches_planted_mistakes():
+    s = R.strassen()
+    for which in ("U", "V", "W"):
+        M = getattr(s, which).copy()
+        M[0, 0] = -M[0, 0]
+        bad = R.Rule("bad", 2, 2, 2, *(M if w == which else getattr(s, w) for w in "UVW"),
+                     s.order_a, s.order_b, s.order_c)
+        assert R.brent_violations(bad) > 0
+    # swapped columns of W only (a transposed output assignment)
+    W = s.W[:, [1, 0, 2, 3, 4, 5, 6]]
+    assert R.brent_violations(R.Rule("bad", 2, 2, 2, s.U, s.V, W, "row", "row", "col")) > 0
+
+
+def test_winograd_quantities():
+    # Not printed in the paper; Sec. 5.2 only says its stability factor is
+    # slightly larger than Strassen's 12.  Q, E, nnz of the flattened form.
+    p = R.principal(R.winograd())
+    assert (p.Q, p.E, p.nnz) == (10.0, 18.0, 42)
+    assert p.E > R.principal(R.strassen()).E
+    assert list(p.alpha) == [1, 1, 4, 1, 2, 3, 2]
+
+
+@pytest.mark.parametrize("make", [R.strassen, R.winograd, R.fast323])
+def test_gradient_rules_brent(make):
+    r = make()
+    dA, dB = R.rule_for_dA(r), R.rule_for_dB(r)
+    assert (dA.m0, dA.k0, dA.n0) == (r.m0, r.n0, r.k0)
+    assert (dB.m0, dB.k0, dB.n0) == (r.k0, r.m0, r.n0)
+    assert R.brent_violations(dA) == 0
+    assert R.brent_violations(dB) == 0
+
+
+def test_rotations_are_rules():
+    f = R.fast323()
+    r1 = R.rotate(f)
+    r2 = R.rotate(r1)
+    assert (r1.m0, r1.k0, r1.n0) == (3, 3, 2)
+    assert (r2.m0, r2.k0, r2.n0) == (2, 3, 3)
+    assert R.brent_violations(r1) == 0 and R.brent_violations(r2) == 0
+    # cyclic invariance of Strassen's Q and E (App. A)
+    s = R.principal(R.strassen())
+    for rr in (R.rotate(R.strassen()), R.rotate(R.rotate(R.strassen()))):
+        p = R.principal(rr)
+        assert (p.Q, p.E) == (s.Q, s.E)
+
+
+def _variant(rule, XU, XV, XW, name):
+    return R.Rule(name, rule.m0, rule.k0, rule.n0, XU @ rule.U, XV @ rule.V, XW @ rule.W,
+                  rule.order_a, rule.order_b, rule.order_c)
+
+
+def test_dalberto_two_level_factor():
+    g = {r[0]: float(r[1]) for r in _golden("stability_vectors.txt") if len(r) == 2}
+    s = R.strassen()
+    P, I = np.array([[0, 1], [1, 0]]), np.eye(2)
+    # Reading: permute the columns of B and the columns of C together; in the
+    # effective ordering of App. A that is (I x P) V and (P x I) W.  The
+    # printed (P x I) V, (I x P) W fails Brent but has the same factor.
+    valid = _variant(s, np.eye(4), np.kron(I, P), np.kron(P, I), "dalberto")
+    printed = _variant(s, np.eye(4), np.kron(P, I), np.kron(I, P), "printed")
+    assert R.brent_violations(valid) == 0
+    assert R.brent_violations(printed) > 0
+    for v in (valid, printed):
+        tree = F.Node(s, [F.Node(v if r in (0, 2, 3) else s, [None] * 7) for r in range(7)])
+        assert F.xi_vector(tree).max() == g["strassen_L2_dalberto"]
+    assert F.xi_vector(F.uniform([s, s])).max() == g["strassen_L2_stationary"]
+
+
+def test_fast323_nonuniform_two_level_factor():
+    g = {r[0]: float(r[1]) for r in _golden("stability_vectors.txt") if len(r) == 2}
+    f = R.fast323()
+    I2 = np.eye(2)
+    P = np.array([[1, 0, 0], [0, 0, 1], [0, 1, 0]])
+    Pp = np.array([[0, 1, 0], [0, 0, 1], [1, 0, 0]])
+    v1 = _variant(f, np.kron(I2, P), np.kron(P, I2), np.kron(P, P), "v1")
+    v2 = _variant(f, np.kron(I2, Pp), np.kron(Pp, I2), np.kron(Pp, Pp), "v2")
+    assert R.brent_violations(v1) == 0 and R.brent_violations(v2) == 0
+    node_rule = {n: f for n in (2, 6, 8, 14, 15)}
+    node_rule.update({n: v1 for n in (1, 3, 10, 11)})
+    node_rule.update({n: v2 for n in (4, 5, 7, 9, 12, 13)})
+    tree = F.Node(f, [F.Node(node_rule[r + 1], [None] * 15) for r in range(15)])
+    assert F.xi_vector(tree).max() == g["fast323_L2_nonuniform"]
+    assert F.xi_vector(F.uniform([f, f])).max() == g["fast323_L2_stationary"]
+
+
+def test_uniform_tree_quantities_reduce_to_theorem_4_2():
+    # For uniform plans the Sec. 4.5 recursions reduce to sum Q and prod E.
+    s, w, c = R.strassen(), R.winograd(), R.classical(1, 2, 1)
+    for rules in ([s], [s, s], [w, c, w], [s, w], [w, w, w]):
+        tree = F.uniform(rules)
+        Qs = sum(R.principal(r).Q for r in rules)
+        Es = np.prod([R.principal(r).E for r in rules])
+        assert F.delta_vector(tree).max() == Qs
+        assert F.xi_vector(tree).max() == Es
+
+
+def test_composition_matches_two_levels():
+    # A composed rule equals two levels of recursion (flattening, Eq. 4.4).
+    s, c = R.strassen(), R.classical(1, 2, 1)
+    comp = R.compose(s, c)
+    assert R.brent_violations(comp) == 0
+    g = np.random.default_rng(0)
+    A = g.integers(-3, 4, size=(8, 16)).astype(float)
+    B = g.integers(-3, 4, size=(16, 8)).astype(float)
+    one = F.fmm(A, B, F.uniform([comp]))
+    two = F.fmm(A, B, F.uniform([s, c]))
+    assert np.array_equal(one, A @ B) and np.array_equal(two, A @ B)
+    pc = R.principal(comp)
+    assert pc.E == R.principal(s).E * R.principal(c).E
