@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark: effective TFLOP/s (2MNK/t) of the scaled fast multiplication.
+
+Workload (one "step" = the whole hot path on one product): square n = 4096,
+FP32 inputs A = D1 X D2, B = D3 Y D4 (X, Y ~ U[0,1), diagonal entries
+2^U(-12,12)), outside-then-inside power-of-two scaling (two steps of Alg. 3:
+four reduction kernels) followed by one fused launch of the Winograd
+variant, one recursion level, bf16 hi+lo three-product leaves with FP32
+accumulation.  Inputs stay resident in HBM; L2 is flushed (256 MiB write,
+untimed) before every timed step.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU float64 oracle on a bounded sample of the
+same workload (the reference arm of this method).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_DEFAULT = 4096
+SEED = 1507 + 1000
+METRIC = "effective TFLOP/s (2MNK/t) at stated max error vs FP64; fast vs classical"
+UNIT = "TFLOP/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--rule", default="winograd")
+    ap.add_argument("--levels", type=int, default=1)
+    ap.add_argument("--leaf", default="bf16x3")
+    ap.add_argument("--scaling", default="OI")
+    ap.add_argument("--no-extras", action="store_true", help="skip comparator / variant timings")
+    return ap.parse_args()
+
+
+def workload_config(args):
+    return {"workload": f"{args.rule} L={args.levels}, n={args.n} square, FP32 data, {args.leaf} leaves, "
+                        f"scaling {args.scaling or 'none'}",
+            "rule": args.rule, "levels": args.levels, "M": args.n, "K": args.n, "N": args.n,
+            "leaf": args.leaf, "scaling_steps": args.scaling,
+            "inputs": "A=D1 X D2, B=D3 Y D4, X,Y~U[0,1), D=2^U(-12,12), seeded",
+            "l2": "flushed before each timed step (256 MiB memset, untimed)"}
+
+
+def launches_per_scale(steps: str) -> int:
+    """Kernels fmm_scale launches: 3 initial fills, 4 per O step (row
+    reduction, fill, column reduction, zero fix-up), 3 per I step (fill,
+    column reduction, row reduction)."""
+    return 0 if not steps else 3 + 4 * steps.count("O") + 3 * steps.count("I")
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fmm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- oracle legs
+
+def oracle_inputs(n: int, seed: int):
+    from paper_1507_00687_gb300 import inputs
+    A, B = inputs.diag_scaled_pair(n, n, n, seed=seed)
+    return A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64)
+
+
+def oracle_step(A, B, args):
+    """One oracle pass (pow2 scaling + recursive fast product, float64) on a
+    sample of the workload; returns seconds."""
+    from oracle import fmm as OF
+    from oracle import rules as OR
+    from oracle import scaling as OS
+    rule = {"winograd": OR.winograd, "strassen": OR.strassen}[args.rule]()
+    tree = OF.uniform([rule] * args.levels)
+    t0 = time.perf_counter()
+    if args.scaling:
+        st = OS.pow2_repeated(A, B, args.scaling)
+        Ap, Bp = OS.pow2_apply(A, B, st.eA, st.d, st.eB)
+        OS.pow2_unscale(OF.fmm(Ap, Bp, tree), st.eA, st.eB)
+    else:
+        OF.fmm(A, B, tree)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args) -> dict:
+    n_s = min(args.n, 2048)
+    oracle_step(*oracle_inputs(256, SEED), args)  # warm numpy / BLAS
+    A, B = oracle_inputs(n_s, SEED)
+    ts = [oracle_step(A, B, args) for _ in range(3)]
+    t = statistics.median(ts)
+    return {"value": 2.0 * n_s**3 / t / 1e12, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one n={n_s} product of the same distribution ({(n_s / args.n) ** 3:.3g} of the "
+                      f"workload's flops), float64 numpy oracle with BLAS leaf products, median of 3 "
+                      f"({t:.2f} s each)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # size the per-step sample so that warm-up + timed steps take ~2 minutes
+    A, B = oracle_inputs(512, SEED)
+    oracle_step(A, B, args)
+    t512 = min(oracle_step(A, B, args) for _ in range(2))
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    n_s = int(512 * (per_step / t512) ** (1.0 / 3.0)) // 64 * 64
+    n_s = max(128, min(args.n, 2048, n_s))
+    A, B = oracle_inputs(n_s, SEED)
+    for _ in range(args.warmup):
+        oracle_step(A, B, args)
+    tot = 0.0
+    for i in range(args.steps):
+        tot += oracle_step(A, B, args)
+    t = tot / max(args.steps, 1)
+    v = 2.0 * n_s**3 / t / 1e12
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": dict(workload_config(args), sample_n=n_s),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"each step one n={n_s} product of the workload's distribution "
+                                      f"(float64 numpy oracle, BLAS leaf products)"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_1507_00687_gb300 import build
+    build.build()
+    from paper_1507_00687_gb300 import api, inputs
+
+    n = args.n
+    A64, B64 = inputs.diag_scaled_pair(n, n, n, seed=SEED + rank)
+    hA = torch.from_numpy(A64).float().pin_memory()
+    hB = torch.from_numpy(B64).float().pin_memory()
+    hC = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    A = hA.cuda()
+    B = hB.cuda()
+    C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    eA = torch.empty(n, dtype=torch.int32, device="cuda")
+    d = torch.empty(n, dtype=torch.int32, device="cuda")
+    eB = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    rules = [args.rule] * args.levels
+    plan = api.Plan(rules, args.leaf)
+    info = plan.info()
+
+    def step(pl=plan, scaling=args.scaling, kev=None):
+        if scaling:
+            from paper_1507_00687_gb300 import _native as Nn
+            import ctypes
+            Nn.check(Nn.lib().fmm_scale(scaling.encode(), ctypes.c_void_p(A.data_ptr()),
+                                        ctypes.c_void_p(B.data_ptr()), Nn.DT_F32, n, n, n, n, n,
+                                        ctypes.c_void_p(eA.data_ptr()), ctypes.c_void_p(d.data_ptr()),
+                                        ctypes.c_void_p(eB.data_ptr()), ctypes.c_void_p(stream.cuda_stream)),
+                     "fmm_scale")
+        if kev is not None:
+            kev[0].record(stream)
+        if scaling:
+            api.multiply(pl, A, B, eA, d, eB, out=C)
+        else:
+            api.multiply(pl, A, B, out=C)
+        if kev is not None:
+            kev[1].record(stream)
+
+    def timed(steps, pl=plan, scaling=args.scaling, clocks=None):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        kevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        if clocks:
+            clocks.start()
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            step(pl, scaling, kevs[i])
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ck = clocks.stop() if clocks else None
+        api.sync_status()
+        st = [a.elapsed_time(b) for a, b in evs]
+        kt = [a.elapsed_time(b) for a, b in kevs]
+        return statistics.mean(st), statistics.mean(kt), ck
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    api.sync_status()
+    clocks = Clocks(local)
+    ms, kms, ck = timed(args.steps, clocks=clocks)
+    if world > 1:
+        t = torch.tensor([ms, kms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, kms = float(t[0]), float(t[1])
+    flops = 2.0 * n**3
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # ---------------- end to end through the public API with host buffers
+    def e2e_step():
+        A.copy_(hA, non_blocking=True)
+        B.copy_(hB, non_blocking=True)
+        step()
+        hC.copy_(C, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_steps = max(3, min(args.steps, 30))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = e0.elapsed_time(e1) / e_steps
+    if world > 1:
+        t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t[0])
+    api.sync_status()
+
+    # ---------------- accuracy (max-norm vs an FP64 product of the same inputs)
+    step()
+    torch.cuda.synchronize()
+    C_fast = C.double()
+    ref = A.double() @ B.double()   # FP64 reference product (measurement only)
+    err_fast = float((C_fast - ref).abs().max())
+    normA, normB = float(A.abs().max()), float(B.abs().max())
+    eps_leaf = {"bf16x3": 3 * 2.0**-16, "bf16": 2.0**-8, "fp16": 2.0**-11}[args.leaf]
+    bound_unscaled = plan.bound(n, normA, normB, eps_leaf)
+    extras = {}
+    if not args.no_extras:
+        plan0 = api.Plan([], args.leaf)
+        c_ms, c_kms, _ = timed(max(10, args.steps // 4), plan0, args.scaling)
+        step(plan0, args.scaling)
+        torch.cuda.synchronize()
+        err_cls = float((C.double() - ref).abs().max())
+        extras["classical_same_kernel"] = {"tflops": flops / (c_ms * 1e-3) / 1e12, "ms_per_step": c_ms,
+                                           "kernel_ms": c_kms, "max_abs_err": err_cls,
+                                           "note": "L=0 plan through the same fused kernel, same scaling"}
+        ns_ms, ns_kms, _ = timed(max(10, args.steps // 4), plan, "")
+        step(plan, "")
+        torch.cuda.synchronize()
+        extras["fast_no_scaling"] = {"tflops": flops / (ns_ms * 1e-3) / 1e12, "ms_per_step": ns_ms,
+                                     "max_abs_err": float((C.double() - ref).abs().max())}
+        rel = lambda X: float(((X - ref).abs() / ref.abs().clamp_min(1e-300)).max())  # noqa: E731
+        step(plan, args.scaling)
+        torch.cuda.synchronize()
+        extras["componentwise_rel_err"] = {"fast_scaled": rel(C.double())}
+        step(plan, "")
+        torch.cuda.synchronize()
+        extras["componentwise_rel_err"]["fast_unscaled"] = rel(C.double())
+        if args.levels == 1:
+            try:
+                plan2 = api.Plan([args.rule] * 2, args.leaf)
+                l2_ms, l2_kms, _ = timed(max(10, args.steps // 4), plan2, args.scaling)
+                step(plan2, args.scaling)
+                torch.cuda.synchronize()
+                extras["fast_L2"] = {"tflops": flops / (l2_ms * 1e-3) / 1e12, "ms_per_step": l2_ms,
+                                     "kernel_ms": l2_kms, "max_abs_err": float((C.double() - ref).abs().max())}
+            except Exception as e:  # plan outside the supported range
+                extras["fast_L2"] = {"unavailable": str(e)}
+        del plan0
+    del ref, C_fast
+
+    # ---------------- roofline of the dominant kernel (the fused multiply)
+    import json as _json
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = _json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    peak_src = "of measured (bf16_tflops_sustained)" if peaks else "of fallback"
+    leaf_flops = 2.0 * info["leaves"] * (-(-n // info["pm"])) * (-(-n // info["pk"])) * (-(-n // info["pn"]))
+    mma_flops = leaf_flops * (3 if args.leaf == "bf16x3" else 1)
+    achieved = mma_flops / (kms * 1e-3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        tj = _json.load(open(prof))
+        key = f"{args.rule}_L{args.levels}_{args.leaf}_n{n}"
+        traffic = tj.get(key)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32-in/bf16x3-leaf/f32-acc" if args.leaf == "bf16x3" else args.leaf,
+           "data": "synthetic", "config": workload_config(args),
+           "paper_effective_tflops": world * (2.0 * n**3 - n**2) / (ms * 1e-3) / 1e12,
+           "kernel_ms": kms,
+           "executed_flop_fraction": mma_flops / (kms * 1e-3) / 1e12 / peak,
+           "error": {"max_abs_err_vs_fp64": err_fast, "theorem_4_1_bound_unscaled": bound_unscaled,
+                     "eps_leaf": eps_leaf, "normA": normA, "normB": normB},
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                        "kernel": "fused_fmm_kernel", "algorithmic_flops_per_launch": mma_flops},
+           "e2e": {"value": world * flops / (e_ms * 1e-3) / 1e12, "unit": UNIT,
+                   "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
+                   "ms_per_step": e_ms},
+           "gpu_launches": args.steps * (launches_per_scale(args.scaling) + 1),
+           "clocks": ck, "plan": info}
+    out.update(extras)
+    if rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * fmm.h -- C ABI of the GB300 (sm_103a) recursive fast matrix multiplication
+ * library with power-of-two diagonal scaling.
+ *
+ * Method: Ballard, Benson, Druinsky, Lipshitz, Schwartz, "Improving the
+ * numerical stability of fast matrix multiplication" (SIAM J. Matrix Anal.
+ * Appl. 37(4), 2016).  C = A B with A (M x K) and B (K x N) computed by L
+ * levels of bilinear rules [[U, V, W]] (Sec. 3, Eq. 3.1 / 3.2) and a
+ * classical base case, optionally on the scaled operands of Sec. 6
+ * (Algs. 1-3).
+ *
+ * Conventions (every entry point):
+ *  - Matrices are row-major with a leading dimension (elements) >= the row
+ *    length.  Device pointers are caller-owned CUDA device memory; the
+ *    library never frees them.  Element data must be 16-byte aligned and
+ *    leading dimensions multiples of 16 bytes for the vectorised paths;
+ *    other layouts are accepted and take a slower element-wise path.
+ *  - Calls that take a cudaStream_t (passed as void*, NULL = legacy default
+ *    stream) are asynchronous: host-detectable errors return at once and
+ *    launch nothing; errors the device detects (a bounded wait that ran out,
+ *    a non-finite input to a scaling step) are recorded in a device status
+ *    word that fmm_sync_status() reads and clears.
+ *  - Exponent vectors are int32 device arrays: D_A = diag(2^eA) (length M),
+ *    D = diag(2^d) (length K), D_B = diag(2^eB) (length N); any may be NULL
+ *    (= all zeros).  Scaled operands A' = 2^-eA A 2^d and
+ *    B' = 2^-d B 2^-eB are never materialised: the multiply kernel applies
+ *    the exponents while it loads, and multiplies its output by 2^(eA+eB).
+ *  - Thread safety: plans are immutable after creation and may be used from
+ *    several host threads; calls on one stream execute in order.
+ */
+#ifndef FMM_H_
+#define FMM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FMM_OK = 0,
+  FMM_ERR_ARG = 1,            /* NULL pointer, negative size, bad enum      */
+  FMM_ERR_NOT_MATMUL = 2,     /* a rule violates the Brent equations        */
+  FMM_ERR_SHAPE = 3,          /* leading dimension too small, size limits   */
+  FMM_ERR_ALIGN = 4,          /* reserved                                   */
+  FMM_ERR_DTYPE = 5,          /* unsupported dtype / leaf-format pairing    */
+  FMM_ERR_WORKSPACE = 6,      /* workspace missing or too small             */
+  FMM_ERR_CUDA = 7,           /* a CUDA runtime call failed                 */
+  FMM_ERR_DEVICE_TIMEOUT = 8, /* a kernel's bounded wait ran out            */
+  FMM_ERR_NONFINITE = 9,      /* Inf/NaN met by a scaling step              */
+  FMM_ERR_UNSUPPORTED = 10    /* plan shape outside what the kernels handle */
+} fmm_status;
+
+/* Single-index order of the entries of a base-case operand (Sec. 3.1). */
+enum { FMM_ORDER_ROW = 0, FMM_ORDER_COL = 1 };
+
+/* Element types of A and B in device memory. */
+enum { FMM_DT_F32 = 0, FMM_DT_BF16 = 1, FMM_DT_F16 = 2 };
+
+/* Leaf-product formats.  S_r and T_r are always formed in FP32; the leaf
+ * rounds them to this format and multiplies on the tensor cores with FP32
+ * accumulation.  BF16X3 splits x = hi + lo (hi = rn_bf16(x),
+ * lo = rn_bf16(x - hi)) and sums hi*hi' + hi*lo' + lo*hi'. */
+enum { FMM_LEAF_BF16 = 0, FMM_LEAF_F16 = 1, FMM_LEAF_BF16X3 = 2 };
+
+/*
+ * One base-case rule <m0, k0, n0; r> = [[U, V, W]] (Sec. 3.1, Eq. 3.1):
+ *   C_k = sum_r W[k,r] M_r,  M_r = S_r T_r,
+ *   S_r = sum_i U[i,r] A_i,  T_r = sum_j V[j,r] B_j.
+ * U is (m0*k0) x r, V is (k0*n0) x r, W is (m0*n0) x r, each a host array
+ * stored row-major (entry (i, r) at [i*r_count + r]).  order_a/b/c give how
+ * the single index i (j, k) enumerates the entries of the m0 x k0 block of A
+ * (of B, of C): FMM_ORDER_ROW or FMM_ORDER_COL.  The paper states A, B
+ * column-major and C row-major (Sec. 3.1); its Strassen table (App. A)
+ * needs A, B row-major and C column-major.  The arrays are copied by
+ * fmm_plan; the caller keeps ownership.
+ */
+typedef struct {
+  int m0, k0, n0, r;
+  const double* U;
+  const double* V;
+  const double* W;
+  int order_a, order_b, order_c;
+} fmm_rule;
+
+typedef struct fmm_plan_s* fmm_plan_t;
+
+/*
+ * Build a uniform non-stationary plan (Sec. 3.3; stationary when all levels
+ * repeat one rule, Sec. 3.2): rules[l] is used at recursion level l+1,
+ * l = 0..levels-1, and the classical algorithm at the leaves.  levels = 0 is
+ * the classical product.  Every rule is checked against the Brent equations
+ * (FMM_ERR_NOT_MATMUL on failure) and the levels are flattened into R^L
+ * leaf descriptors (Eq. 4.4): leaf (r_1..r_L) multiplies
+ *   S = sum prod_l U[i_l, r_l] A_(i_1..i_L),  T likewise with V,
+ * and adds prod_l W[k_l, r_l] times its product into C block (k_1..k_L).
+ * leaf_format is FMM_LEAF_*.  *out owns host and device memory; release it
+ * with fmm_plan_destroy.  Uses the current CUDA device.
+ */
+fmm_status fmm_plan(fmm_plan_t* out, int levels, const fmm_rule* rules, int leaf_format);
+
+fmm_status fmm_plan_destroy(fmm_plan_t plan);
+
+/*
+ * Principal quantities of the plan (Sec. 4.1, Theorem 4.2): sum over levels
+ * of Q (Def. 4.1), product of E (Def. 4.2), number of leaves R^L,
+ * nnz of the flattened [[U, V, W]], and the products of m0, k0, n0 over the
+ * levels (the padding granules).  Any output pointer may be NULL.
+ */
+fmm_status fmm_plan_info(fmm_plan_t plan, double* q_sum, double* e_prod, int64_t* leaves,
+                         int64_t* nnz, int64_t* pm, int64_t* pk, int64_t* pn);
+
+/*
+ * First-order bound of Theorem 4.2 for this plan and a K-dimension:
+ *   (Kl + sum Q)(Kl) (prod E) normA normB eps,  Kl = ceil(K / prod k0).
+ */
+fmm_status fmm_plan_bound(fmm_plan_t plan, int64_t K, double normA, double normB, double eps,
+                          double* bound);
+
+/*
+ * O step of Alg. 3 (Alg. 1 when d_in is NULL) in power-of-two form:
+ *   eA[i] = e(max_k |A_ik| 2^d_k),   eB[j] = e(max_k 2^-d_k |B_kj|),
+ * e(x) the frexp exponent (x = f 2^e, 1/2 <= f < 1), 0 for an all-zero
+ * row / column.  The scaled operands 2^-eA A 2^d and 2^-d B 2^-eB then have
+ * row (column) maxima in [1/2, 1) (Prop. 6.1).  A is M x K (lda), B is
+ * K x N (ldb), both of element type dtype (FMM_DT_*).  d_in: length K or
+ * NULL.  eA (length M) and eB (length N) are overwritten.  Inf/NaN in A or
+ * B sets FMM_ERR_NONFINITE in the device status word.
+ */
+fmm_status fmm_scale_outside(const void* A, const void* B, int dtype, int64_t M, int64_t K,
+                             int64_t N, int64_t lda, int64_t ldb, const int32_t* d_in,
+                             int32_t* eA, int32_t* eB, void* stream);
+
+/*
+ * I step of Alg. 3 (Alg. 2 when eA, eB are NULL), Eq. 6.6 in power-of-two
+ * form, on the operands currently scaled by eA and eB:
+ *   d[k] = floor((e(max_j |B_kj| 2^-eB_j) - e(max_i 2^-eA_i |A_ik|)) / 2),
+ * 0 when either maximum is zero.  The result replaces any previous d (the
+ * cumulative inside scale of Alg. 3 equals this value, because previous
+ * inside exponents cancel out of the ratio).  d has length K.
+ */
+fmm_status fmm_scale_inside(const void* A, const void* B, int dtype, int64_t M, int64_t K,
+                            int64_t N, int64_t lda, int64_t ldb, const int32_t* eA,
+                            const int32_t* eB, int32_t* d, void* stream);
+
+/*
+ * Alg. 3 with a fixed step sequence: steps is a string over {'O','I'}
+ * ("O" = Alg. 1, "I" = Alg. 2, "OI" = outside then inside, "OIOI" = twice
+ * repeated).  eA, d, eB are zeroed first and then updated by each step.
+ */
+fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype, int64_t M,
+                     int64_t K, int64_t N, int64_t lda, int64_t ldb, int32_t* eA, int32_t* d,
+                     int32_t* eB, void* stream);
+
+/*
+ * Workspace bytes fmm_multiply needs for this plan and shape (0 for every
+ * plan the fused kernel runs without intermediates).
+ */
+fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t M, int64_t K, int64_t N, size_t* bytes);
+
+/*
+ * C = A B by the plan's fast algorithm (Eq. 3.2), on the scaled operands
+ * when exponents are given (Algs. 1-3: C = D_A (A' B') D_B).  A: M x K
+ * (lda), B: K x N (ldb), element type in_dtype; C: M x N float32 (ldc),
+ * overwritten.  M, K, N are zero-padded internally up to multiples of the
+ * plan's granules (Sec. 3.2).  One kernel launch forms S_r and T_r in its
+ * load stage, multiplies on the tensor cores and adds W-weighted products
+ * into C in its epilogue; each output tile is owned by one CTA, so the
+ * result is deterministic.  ws/ws_bytes: see fmm_workspace_size (may be
+ * NULL/0 when that is 0).
+ */
+fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void* B, int64_t ldb,
+                        float* C, int64_t ldc, int64_t M, int64_t K, int64_t N, int in_dtype,
+                        const int32_t* eA, const int32_t* d, const int32_t* eB, void* ws,
+                        size_t ws_bytes, void* stream);
+
+/*
+ * Gradients of C = A B for a given dC (M x N, float32, lddc):
+ *   dA = dC B^T (M x K, float32, ldda),  dB = A^T dC (K x N, float32, lddb),
+ * each by a fast algorithm derived from the plan's rules through the cyclic
+ * symmetry of the matrix-multiplication tensor (the rule transforms of
+ * Sec. 5.3 and App. A-C): dA uses [[W, V^T, U]] (an <m0,n0,k0> rule), dB
+ * uses [[U^T, W, V]] (a <k0,m0,n0> rule), where ^T re-indexes the operand's
+ * entries by transposition.  dA or dB may be NULL to skip it.  A and B have
+ * element type in_dtype.
+ */
+fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc, const void* A,
+                                 int64_t lda, const void* B, int64_t ldb, float* dA,
+                                 int64_t ldda, float* dB, int64_t lddb, int64_t M, int64_t K,
+                                 int64_t N, int in_dtype, void* stream);
+
+/*
+ * Synchronise the stream, then read and clear the device status word.
+ * Returns FMM_OK, FMM_ERR_DEVICE_TIMEOUT, FMM_ERR_NONFINITE or FMM_ERR_CUDA.
+ */
+fmm_status fmm_sync_status(void* stream);
+
+/* Static English description of a status code. */
+const char* fmm_status_string(fmm_status s);
+
+/* Library version string. */
+const char* fmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_H_ */

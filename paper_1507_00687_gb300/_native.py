@@ -1,0 +1,83 @@
+"""ctypes binding of libfmm.so (include/fmm.h): argument marshalling only.
+
+Loading fails loudly (ImportError / OSError) when the library has not been
+built; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfmm.so")
+
+FMM_OK = 0
+STATUS_NAMES = {
+    0: "FMM_OK", 1: "FMM_ERR_ARG", 2: "FMM_ERR_NOT_MATMUL", 3: "FMM_ERR_SHAPE", 4: "FMM_ERR_ALIGN",
+    5: "FMM_ERR_DTYPE", 6: "FMM_ERR_WORKSPACE", 7: "FMM_ERR_CUDA", 8: "FMM_ERR_DEVICE_TIMEOUT",
+    9: "FMM_ERR_NONFINITE", 10: "FMM_ERR_UNSUPPORTED",
+}
+ORDER_ROW, ORDER_COL = 0, 1
+DT_F32, DT_BF16, DT_F16 = 0, 1, 2
+LEAF_BF16, LEAF_F16, LEAF_BF16X3 = 0, 1, 2
+
+# Every symbol include/fmm.h declares.
+EXPORTS = [
+    "fmm_plan", "fmm_plan_destroy", "fmm_plan_info", "fmm_plan_bound", "fmm_scale_outside",
+    "fmm_scale_inside", "fmm_scale", "fmm_workspace_size", "fmm_multiply", "fmm_multiply_backward",
+    "fmm_sync_status", "fmm_status_string", "fmm_version",
+]
+
+
+class FmmRule(C.Structure):
+    _fields_ = [("m0", C.c_int), ("k0", C.c_int), ("n0", C.c_int), ("r", C.c_int),
+                ("U", C.POINTER(C.c_double)), ("V", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
+                ("order_a", C.c_int), ("order_b", C.c_int), ("order_c", C.c_int)]
+
+
+class FmmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)} ({lib().fmm_status_string(code).decode()})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfmm.so is not built ({LIB_PATH}); run paper_1507_00687_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    i64, i32p, vp, st = C.c_int64, C.POINTER(C.c_int32), C.c_void_p, C.c_int
+    L.fmm_plan.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(FmmRule), C.c_int]
+    L.fmm_plan_destroy.argtypes = [vp]
+    L.fmm_plan_info.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i64),
+                                C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    L.fmm_plan_bound.argtypes = [vp, i64, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
+    L.fmm_scale_outside.argtypes = [vp, vp, C.c_int, i64, i64, i64, i64, i64, vp, vp, vp, vp]
+    L.fmm_scale_inside.argtypes = [vp, vp, C.c_int, i64, i64, i64, i64, i64, vp, vp, vp, vp]
+    L.fmm_scale.argtypes = [C.c_char_p, vp, vp, C.c_int, i64, i64, i64, i64, i64, vp, vp, vp, vp]
+    L.fmm_workspace_size.argtypes = [vp, i64, i64, i64, C.POINTER(C.c_size_t)]
+    L.fmm_multiply.argtypes = [vp, vp, i64, vp, i64, vp, i64, i64, i64, i64, C.c_int, vp, vp, vp, vp,
+                               C.c_size_t, vp]
+    L.fmm_multiply_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, i64, i64, i64,
+                                        C.c_int, vp]
+    L.fmm_sync_status.argtypes = [vp]
+    L.fmm_status_string.argtypes = [C.c_int]
+    L.fmm_status_string.restype = C.c_char_p
+    L.fmm_version.argtypes = []
+    L.fmm_version.restype = C.c_char_p
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if name not in ("fmm_status_string", "fmm_version"):
+            f.restype = st
+    _lib = L
+    return L
+
+
+def check(code: int, what: str) -> None:
+    if code != FMM_OK:
+        raise FmmError(code, what)

@@ -1,0 +1,184 @@
+"""PyTorch-facing wrappers over the C ABI (device memory and streams only;
+every step of the computation runs in the library's CUDA kernels)."""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence, Union
+
+import numpy as np
+import torch
+
+from . import _native as N
+from .rules import BaseRule, get as get_rule
+
+LEAF = {"bf16": N.LEAF_BF16, "fp16": N.LEAF_F16, "bf16x3": N.LEAF_BF16X3}
+DTYPE = {torch.float32: N.DT_F32, torch.bfloat16: N.DT_BF16, torch.float16: N.DT_F16}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _rowmajor(t: torch.Tensor, name: str) -> int:
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if t.shape[0] > 0 and t.shape[1] > 1 and t.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (unit column stride)")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return max(t.stride(0), t.shape[1], 1)
+
+
+class Plan:
+    """A flattened uniform non-stationary plan (fmm_plan): ``rules[l]`` at
+    level l+1, classical leaves, leaf products in ``leaf`` format."""
+
+    def __init__(self, rules: Sequence[Union[str, BaseRule]], leaf: str = "bf16x3"):
+        self.rules = [get_rule(r) if isinstance(r, str) else r for r in rules]
+        self.leaf = leaf
+        self._keep = []
+        arr = (N.FmmRule * max(1, len(self.rules)))()
+        for i, r in enumerate(self.rules):
+            U = np.ascontiguousarray(r.U, np.float64)
+            V = np.ascontiguousarray(r.V, np.float64)
+            W = np.ascontiguousarray(r.W, np.float64)
+            self._keep += [U, V, W]
+            dp = C.POINTER(C.c_double)
+            arr[i] = N.FmmRule(r.m0, r.k0, r.n0, r.r, U.ctypes.data_as(dp), V.ctypes.data_as(dp),
+                               W.ctypes.data_as(dp), r.order_a, r.order_b, r.order_c)
+        h = C.c_void_p()
+        N.check(N.lib().fmm_plan(C.byref(h), len(self.rules), arr, LEAF[leaf]), "fmm_plan")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        q, e = C.c_double(), C.c_double()
+        leaves, nnz, pm, pk, pn = (C.c_int64() for _ in range(5))
+        N.check(N.lib().fmm_plan_info(self._h, C.byref(q), C.byref(e), C.byref(leaves), C.byref(nnz),
+                                      C.byref(pm), C.byref(pk), C.byref(pn)), "fmm_plan_info")
+        return {"q_sum": q.value, "e_prod": e.value, "leaves": leaves.value, "nnz": nnz.value,
+                "pm": pm.value, "pk": pk.value, "pn": pn.value}
+
+    def bound(self, K: int, normA: float, normB: float, eps: float) -> float:
+        b = C.c_double()
+        N.check(N.lib().fmm_plan_bound(self._h, K, normA, normB, eps, C.byref(b)), "fmm_plan_bound")
+        return b.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                N.lib().fmm_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
+def scale(A: torch.Tensor, B: torch.Tensor, steps: str, stream=None):
+    """Alg. 3 with power-of-two scales and a fixed step sequence ("O", "I",
+    "OI", "IO", "OIOI", ...); returns int32 device tensors (eA, d, eB)."""
+    M, K = A.shape
+    K2, Nn = B.shape
+    assert K == K2 and A.dtype == B.dtype
+    lda, ldb = _rowmajor(A, "A"), _rowmajor(B, "B")
+    dev = A.device
+    eA = torch.empty(M, dtype=torch.int32, device=dev)
+    d = torch.empty(K, dtype=torch.int32, device=dev)
+    eB = torch.empty(Nn, dtype=torch.int32, device=dev)
+    N.check(N.lib().fmm_scale(steps.encode(), _ptr(A), _ptr(B), DTYPE[A.dtype], M, K, Nn, lda, ldb,
+                              _ptr(eA), _ptr(d), _ptr(eB), _stream(stream)), "fmm_scale")
+    return eA, d, eB
+
+
+def scale_outside(A, B, d=None, eA=None, eB=None, stream=None):
+    """One O step (Alg. 1 when d is None); returns (eA, eB)."""
+    M, K = A.shape
+    Nn = B.shape[1]
+    eA = eA if eA is not None else torch.empty(M, dtype=torch.int32, device=A.device)
+    eB = eB if eB is not None else torch.empty(Nn, dtype=torch.int32, device=A.device)
+    N.check(N.lib().fmm_scale_outside(_ptr(A), _ptr(B), DTYPE[A.dtype], M, K, Nn, _rowmajor(A, "A"),
+                                      _rowmajor(B, "B"), _ptr(d), _ptr(eA), _ptr(eB), _stream(stream)),
+            "fmm_scale_outside")
+    return eA, eB
+
+
+def scale_inside(A, B, eA=None, eB=None, d=None, stream=None):
+    """One I step (Alg. 2 when eA, eB are None); returns d."""
+    M, K = A.shape
+    Nn = B.shape[1]
+    d = d if d is not None else torch.empty(K, dtype=torch.int32, device=A.device)
+    N.check(N.lib().fmm_scale_inside(_ptr(A), _ptr(B), DTYPE[A.dtype], M, K, Nn, _rowmajor(A, "A"),
+                                     _rowmajor(B, "B"), _ptr(eA), _ptr(eB), _ptr(d), _stream(stream)),
+            "fmm_scale_inside")
+    return d
+
+
+def multiply(plan: Plan, A: torch.Tensor, B: torch.Tensor, eA=None, d=None, eB=None,
+             out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """C = A B (float32) by the plan's fast algorithm on the scaled operands
+    (C = D_A (A' B') D_B when exponents are given)."""
+    M, K = A.shape
+    K2, Nn = B.shape
+    if K != K2 or A.dtype != B.dtype:
+        raise ValueError("shape / dtype mismatch")
+    if out is None:
+        out = torch.empty((M, Nn), dtype=torch.float32, device=A.device)
+    N.check(N.lib().fmm_multiply(plan.handle, _ptr(A), _rowmajor(A, "A"), _ptr(B), _rowmajor(B, "B"),
+                                 _ptr(out), _rowmajor(out, "C"), M, K, Nn, DTYPE[A.dtype], _ptr(eA), _ptr(d),
+                                 _ptr(eB), None, 0, _stream(stream)), "fmm_multiply")
+    return out
+
+
+def multiply_backward(plan: Plan, dC: torch.Tensor, A: torch.Tensor, B: torch.Tensor, need_a: bool = True,
+                      need_b: bool = True, stream=None):
+    """(dA, dB) = (dC B^T, A^T dC) by the permuted fast rules."""
+    M, K = A.shape
+    Nn = B.shape[1]
+    dC = dC.contiguous().float()
+    dA = torch.empty((M, K), dtype=torch.float32, device=A.device) if need_a else None
+    dB = torch.empty((K, Nn), dtype=torch.float32, device=A.device) if need_b else None
+    N.check(N.lib().fmm_multiply_backward(plan.handle, _ptr(dC), _rowmajor(dC, "dC"), _ptr(A),
+                                          _rowmajor(A, "A"), _ptr(B), _rowmajor(B, "B"), _ptr(dA),
+                                          K if dA is not None else 0, _ptr(dB),
+                                          Nn if dB is not None else 0, M, K, Nn, DTYPE[A.dtype],
+                                          _stream(stream)), "fmm_multiply_backward")
+    return dA, dB
+
+
+def sync_status(stream=None) -> None:
+    """Synchronise and raise FmmError if a kernel recorded a device error."""
+    N.check(N.lib().fmm_sync_status(_stream(stream)), "device status")
+
+
+class FastMatmul(torch.autograd.Function):
+    """C = A B with the plan's fast algorithm forward and the permuted fast
+    rules backward (dA = dC B^T, dB = A^T dC)."""
+
+    @staticmethod
+    def forward(ctx, A, B, plan):
+        ctx.save_for_backward(A, B)
+        ctx.plan = plan
+        return multiply(plan, A.contiguous(), B.contiguous())
+
+    @staticmethod
+    def backward(ctx, dC):
+        A, B = ctx.saved_tensors
+        dA, dB = multiply_backward(ctx.plan, dC, A.contiguous(), B.contiguous(),
+                                   ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        if dA is not None:
+            dA = dA.to(A.dtype)
+        if dB is not None:
+            dB = dB.to(B.dtype)
+        return dA, dB, None
+
+
+def fast_matmul(A, B, plan):
+    return FastMatmul.apply(A, B, plan)

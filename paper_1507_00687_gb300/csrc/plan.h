@@ -1,0 +1,67 @@
+// Internal plan representation shared by the host plan compiler, the C ABI
+// and the kernels.  Not part of the public ABI (see include/fmm.h).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/fmm.h"
+
+namespace fmm {
+
+// Upper bound on the flattened terms of one leaf (Eq. 4.4): the number of
+// A blocks summed into S_r, of B blocks summed into T_r, and of C blocks the
+// product M_r is added into.
+constexpr int kMaxTerms = 16;
+
+// One leaf of the flattened plan: S = sum a_coef[t] A(a_blk[t]),
+// T = sum b_coef[t] B(b_blk[t]), C(c_blk[t]) += c_coef[t] * S T.
+// Blocks are packed (row_block << 16) | col_block in the block grid of the
+// operand (A: pm x pk blocks, B: pk x pn, C: pm x pn).  c_first[t] is 1 when
+// this leaf is the first (in leaf order) to touch C block c_blk[t], so the
+// epilogue stores instead of accumulating.
+struct LeafDesc {
+  int32_t na, nb, nc, pad;
+  int32_t a_blk[kMaxTerms];
+  float a_coef[kMaxTerms];
+  int32_t b_blk[kMaxTerms];
+  float b_coef[kMaxTerms];
+  int32_t c_blk[kMaxTerms];
+  float c_coef[kMaxTerms];
+  int32_t c_first[kMaxTerms];
+};
+
+// A rule re-indexed so that A, B and C blocks are all enumerated row-major.
+struct CanonRule {
+  int m0, k0, n0, r;
+  std::vector<double> U, V, W;  // (m0 k0) x r, (k0 n0) x r, (m0 n0) x r, row-major
+  double Q = 0, E = 0;
+  int64_t nnz = 0;
+};
+
+struct Plan {
+  int levels = 0;
+  int leaf_format = FMM_LEAF_BF16;
+  std::vector<CanonRule> rules;
+  int64_t pm = 1, pk = 1, pn = 1;  // products of m0, k0, n0 over the levels
+  int64_t leaves = 1;
+  double q_sum = 0, e_prod = 1;
+  int64_t nnz = 0;
+  int max_terms = 0;  // max over leaves of na, nb, nc
+  std::vector<LeafDesc> host;
+  LeafDesc* dev = nullptr;  // device copy (on `device`)
+  int device = -1;
+  Plan* grad_a = nullptr;  // plan for dA = dC B^T  (lazily built)
+  Plan* grad_b = nullptr;  // plan for dB = A^T dC
+};
+
+// Host plan compiler (plan.cpp).
+fmm_status canonicalize(const fmm_rule& in, CanonRule* out);
+int brent_violations(const CanonRule& r);
+void principal_quantities(CanonRule* r);
+fmm_status build_plan(const std::vector<CanonRule>& rules, int leaf_format, Plan** out);
+void destroy_plan(Plan* p);
+CanonRule rule_for_grad_a(const CanonRule& r);  // <m0, n0, k0>: [[W, V^T, U]]
+CanonRule rule_for_grad_b(const CanonRule& r);  // <k0, m0, n0>: [[U^T, W, V]]
+
+}  // namespace fmm

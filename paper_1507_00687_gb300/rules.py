@@ -1,0 +1,112 @@
+"""Built-in base-case rules [[U, V, W]] (Sec. 3.1) in the form fmm_plan takes.
+
+Each rule carries the single-index order of its A, B and C entries; the
+library re-indexes and checks the Brent equations itself.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+ROW, COL = 0, 1
+
+
+@dataclass(frozen=True)
+class BaseRule:
+    name: str
+    m0: int
+    k0: int
+    n0: int
+    U: np.ndarray
+    V: np.ndarray
+    W: np.ndarray
+    order_a: int = ROW
+    order_b: int = ROW
+    order_c: int = ROW
+
+    @property
+    def r(self) -> int:
+        return int(self.U.shape[1])
+
+
+def strassen() -> BaseRule:
+    """Strassen <2,2,2;7> with the numbers of App. A.  The table is a
+    matrix-multiplication rule when A and B entries are enumerated row-major
+    and C entries column-major."""
+    U = np.array([[1, 0, 1, 0, 1, -1, 0], [0, 0, 0, 0, 1, 0, 1],
+                  [0, 1, 0, 0, 0, 1, 0], [1, 1, 0, 1, 0, 0, -1]], np.float64)
+    V = np.array([[1, 1, 0, -1, 0, 1, 0], [0, 0, 1, 0, 0, 1, 0],
+                  [0, 0, 0, 1, 0, 0, 1], [1, 0, -1, 0, 1, 0, 1]], np.float64)
+    W = np.array([[1, 0, 0, 1, -1, 0, 1], [0, 1, 0, 1, 0, 0, 0],
+                  [0, 0, 1, 0, 1, 0, 0], [1, -1, 1, 0, 0, 1, 0]], np.float64)
+    return BaseRule("strassen", 2, 2, 2, U, V, W, ROW, ROW, COL)
+
+
+def winograd() -> BaseRule:
+    """Strassen-Winograd <2,2,2;7>: products a11 b11, a12 b21,
+    (a11 + a12 - a21 - a22) b22, a22 (b11 - b12 - b21 + b22),
+    (a21 + a22)(b12 - b11), (a21 + a22 - a11)(b11 - b12 + b22),
+    (a11 - a21)(b22 - b12); c11 = m1 + m2, c12 = m1 + m3 + m5 + m6,
+    c21 = m1 - m4 + m6 + m7, c22 = m1 + m5 + m6 + m7 (every shared partial
+    sum of the textbook schedule expanded, as the [[U, V, W]] form needs).
+    Row-major A, B, C."""
+    U = np.array([[1, 0, 1, 0, 0, -1, 1], [0, 1, 1, 0, 0, 0, 0],
+                  [0, 0, -1, 0, 1, 1, -1], [0, 0, -1, 1, 1, 1, 0]], np.float64)
+    V = np.array([[1, 0, 0, 1, -1, 1, 0], [0, 0, 0, -1, 1, -1, -1],
+                  [0, 1, 0, -1, 0, 0, 0], [0, 0, 1, 1, 0, 1, 1]], np.float64)
+    W = np.array([[1, 1, 0, 0, 0, 0, 0], [1, 0, 1, 0, 1, 1, 0],
+                  [1, 0, 0, -1, 0, 1, 1], [1, 0, 0, 0, 1, 1, 1]], np.float64)
+    return BaseRule("winograd", 2, 2, 2, U, V, W)
+
+
+def classical(m0: int, k0: int, n0: int) -> BaseRule:
+    """The classical <m0,k0,n0; m0 k0 n0> rule, one product per (i, k, j)."""
+    R = m0 * k0 * n0
+    U = np.zeros((m0 * k0, R))
+    V = np.zeros((k0 * n0, R))
+    W = np.zeros((m0 * n0, R))
+    for r, (i, k, j) in enumerate((i, k, j) for i in range(m0) for k in range(k0) for j in range(n0)):
+        U[i * k0 + k, r] = V[k * n0 + j, r] = W[i * n0 + j, r] = 1
+    return BaseRule(f"classical{m0}{k0}{n0}", m0, k0, n0, U, V, W)
+
+
+def fast323() -> BaseRule:
+    """The rank-15 <3,2,3> rule of App. B (A, B column-major, C row-major)."""
+    U = np.array([
+        [0, 1, 0, 0, -1, 1, 1, 0, 0, 0, -1, 0, 0, 0, -1],
+        [0, 1, 0, 0, 0, 0, 0, -1, 0, -1, 0, 0, 1, -1, 0],
+        [0, 0, 0, 1, 0, 0, 0, -1, 0, -1, 1, 0, 0, -1, 0],
+        [-1, 0, 1, 0, 1, 0, 0, 0, 0, 0, 1, 0, 0, 0, 1],
+        [-1, 0, 0, 0, 0, 1, 0, 1, 0, 1, 0, 1, -1, 0, 0],
+        [0, 0, -1, 0, 0, 0, 0, 1, 1, 0, -1, 0, 0, 0, -1]], np.float64)
+    V = np.array([
+        [0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 1, 1],
+        [0, 0, 1, 0, 0, 0, 0, -1, 1, -1, 0, 0, 0, 1, 0],
+        [0, -1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 1, 1, -1, 0],
+        [-1, 0, 0, 0, 0, 0, 0, 1, 0, 1, 0, 1, 0, -1, 0],
+        [0, 1, 1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1],
+        [1, 0, 1, 0, 1, 1, 1, 0, 0, 0, 0, 0, 0, 0, 1]], np.float64)
+    W = np.array([
+        [0, 0, 1, 0, 0, 0, -1, 0, 1, 0, 0, 0, 0, 0, -1],
+        [1, 0, 0, 0, 1, 1, 0, 0, 0, 0, 0, -1, 0, 0, 0],
+        [0, 0, 0, 0, 1, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0],
+        [0, 0, 0, -1, 0, 0, 0, 0, 0, -1, 0, 1, 0, -1, 0],
+        [0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 0, 0],
+        [0, 1, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0, 1, 0, 0],
+        [0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0],
+        [0, 0, 0, 0, 0, 0, 0, 1, 1, -1, 0, 0, -1, 0, 0],
+        [0, 0, 0, -1, 1, 0, 0, 0, 0, 0, 1, 0, 0, 0, -1]], np.float64)
+    return BaseRule("fast323", 3, 2, 3, U, V, W, COL, COL, ROW)
+
+
+BUILTIN = {"strassen": strassen, "winograd": winograd, "fast323": fast323,
+           "classical121": lambda: classical(1, 2, 1), "classical211": lambda: classical(2, 1, 1),
+           "classical112": lambda: classical(1, 1, 2), "classical222": lambda: classical(2, 2, 2)}
+
+
+def get(name: str) -> BaseRule:
+    try:
+        return BUILTIN[name]()
+    except KeyError:
+        raise ValueError(f"unknown rule {name!r}; known: {sorted(BUILTIN)}") from None
