@@ -60,10 +60,11 @@ def workload_config(args):
 
 
 def launches_per_scale(steps: str) -> int:
-    """Kernels fmm_scale launches: 3 initial fills, 4 per O step (row
-    reduction, fill, column reduction, zero fix-up), 3 per I step (fill,
-    column reduction, row reduction)."""
-    return 0 if not steps else 3 + 4 * steps.count("O") + 3 * steps.count("I")
+    """Kernels one scaled step launches besides the multiply: fmm_scale's 3
+    initial fills, 4 per O step (row reduction, fill, column reduction, zero
+    fix-up), 3 per I step (fill, column reduction, row reduction), and the 2
+    apply passes that write the scaled operands."""
+    return 0 if not steps else 3 + 4 * steps.count("O") + 3 * steps.count("I") + 2
 
 
 # ---------------------------------------------------------------- clocks
@@ -221,6 +222,7 @@ def main():
     rules = [args.rule] * args.levels
     plan = api.Plan(rules, args.leaf)
     info = plan.info()
+    ws = torch.empty(api.workspace_bytes(plan, n, n, n), dtype=torch.uint8, device="cuda")
 
     def step(pl=plan, scaling=args.scaling, kev=None):
         if scaling:
@@ -234,7 +236,7 @@ def main():
         if kev is not None:
             kev[0].record(stream)
         if scaling:
-            api.multiply(pl, A, B, eA, d, eB, out=C)
+            api.multiply(pl, A, B, eA, d, eB, out=C, ws=ws)
         else:
             api.multiply(pl, A, B, out=C)
         if kev is not None:

@@ -22,9 +22,10 @@
  *    word that fmm_sync_status() reads and clears.
  *  - Exponent vectors are int32 device arrays: D_A = diag(2^eA) (length M),
  *    D = diag(2^d) (length K), D_B = diag(2^eB) (length N); any may be NULL
- *    (= all zeros).  Scaled operands A' = 2^-eA A 2^d and
- *    B' = 2^-d B 2^-eB are never materialised: the multiply kernel applies
- *    the exponents while it loads, and multiplies its output by 2^(eA+eB).
+ *    (= all zeros).  The scaled operands A' = 2^-eA A 2^d and
+ *    B' = 2^-d B 2^-eB are exact; fmm_multiply writes them into the
+ *    caller's workspace in one bandwidth-bound pass and multiplies its
+ *    output by 2^(eA+eB) in the epilogue of the fused kernel.
  *  - Thread safety: plans are immutable after creation and may be used from
  *    several host threads; calls on one stream execute in order.
  */
@@ -154,8 +155,10 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
                      int32_t* eB, void* stream);
 
 /*
- * Workspace bytes fmm_multiply needs for this plan and shape (0 for every
- * plan the fused kernel runs without intermediates).
+ * Workspace bytes fmm_multiply needs for this plan and shape when exponent
+ * vectors are passed (an upper bound over input types): room for the scaled
+ * copies A' and B' (fp32; bf16 for bf16 inputs), which one HBM-bound pass
+ * each writes before the multiply.  Unscaled calls need no workspace.
  */
 fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t M, int64_t K, int64_t N, size_t* bytes);
 
@@ -167,8 +170,10 @@ fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t M, int64_t K, int64_t N, 
  * plan's granules (Sec. 3.2).  One kernel launch forms S_r and T_r in its
  * load stage, multiplies on the tensor cores and adds W-weighted products
  * into C in its epilogue; each output tile is owned by one CTA, so the
- * result is deterministic.  ws/ws_bytes: see fmm_workspace_size (may be
- * NULL/0 when that is 0).
+ * result is deterministic.  ws/ws_bytes: device workspace, 256-byte
+ * aligned, of at least fmm_workspace_size bytes when any exponent vector is
+ * given or the inputs are fp16 (which are widened to fp32 there);
+ * FMM_ERR_WORKSPACE otherwise.  May be NULL/0 for unscaled fp32 / bf16.
  */
 fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void* B, int64_t ldb,
                         float* C, int64_t ldc, int64_t M, int64_t K, int64_t N, int in_dtype,
@@ -183,7 +188,7 @@ fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void*
  * Sec. 5.3 and App. A-C): dA uses [[W, V^T, U]] (an <m0,n0,k0> rule), dB
  * uses [[U^T, W, V]] (a <k0,m0,n0> rule), where ^T re-indexes the operand's
  * entries by transposition.  dA or dB may be NULL to skip it.  A and B have
- * element type in_dtype.
+ * element type in_dtype (FMM_DT_F32 or FMM_DT_BF16; FMM_ERR_DTYPE for fp16).
  */
 fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc, const void* A,
                                  int64_t lda, const void* B, int64_t ldb, float* dA,
@@ -195,6 +200,13 @@ fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc,
  * Returns FMM_OK, FMM_ERR_DEVICE_TIMEOUT, FMM_ERR_NONFINITE or FMM_ERR_CUDA.
  */
 fmm_status fmm_sync_status(void* stream);
+
+/*
+ * Text of the last CUDA runtime error a library call on this host thread
+ * met (empty when none); the pointer stays valid until the next library
+ * call on the thread.
+ */
+const char* fmm_last_error(void);
 
 /* Static English description of a status code. */
 const char* fmm_status_string(fmm_status s);

@@ -25,7 +25,7 @@ LEAF_BF16, LEAF_F16, LEAF_BF16X3 = 0, 1, 2
 EXPORTS = [
     "fmm_plan", "fmm_plan_destroy", "fmm_plan_info", "fmm_plan_bound", "fmm_scale_outside",
     "fmm_scale_inside", "fmm_scale", "fmm_workspace_size", "fmm_multiply", "fmm_multiply_backward",
-    "fmm_sync_status", "fmm_status_string", "fmm_version",
+    "fmm_sync_status", "fmm_status_string", "fmm_version", "fmm_last_error",
 ]
 
 
@@ -37,7 +37,9 @@ class FmmRule(C.Structure):
 
 class FmmError(RuntimeError):
     def __init__(self, code: int, what: str):
-        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)} ({lib().fmm_status_string(code).decode()})")
+        detail = lib().fmm_last_error().decode() if code == 7 else ""
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)} ({lib().fmm_status_string(code).decode()})"
+                         + (f" [{detail}]" if detail else ""))
         self.code = code
 
 
@@ -70,9 +72,11 @@ def lib():
     L.fmm_status_string.restype = C.c_char_p
     L.fmm_version.argtypes = []
     L.fmm_version.restype = C.c_char_p
+    L.fmm_last_error.argtypes = []
+    L.fmm_last_error.restype = C.c_char_p
     for name in EXPORTS:
         f = getattr(L, name)
-        if name not in ("fmm_status_string", "fmm_version"):
+        if name not in ("fmm_status_string", "fmm_version", "fmm_last_error"):
             f.restype = st
     _lib = L
     return L

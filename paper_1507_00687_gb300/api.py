@@ -121,19 +121,32 @@ def scale_inside(A, B, eA=None, eB=None, d=None, stream=None):
     return d
 
 
+def workspace_bytes(plan: Plan, M: int, K: int, Ncols: int) -> int:
+    """Bytes of device workspace a scaled multiply of this shape needs."""
+    b = C.c_size_t()
+    N.check(N.lib().fmm_workspace_size(plan.handle, M, K, Ncols, C.byref(b)), "fmm_workspace_size")
+    return b.value
+
+
 def multiply(plan: Plan, A: torch.Tensor, B: torch.Tensor, eA=None, d=None, eB=None,
-             out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+             out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """C = A B (float32) by the plan's fast algorithm on the scaled operands
-    (C = D_A (A' B') D_B when exponents are given)."""
+    (C = D_A (A' B') D_B when exponents are given; the scaled copies go to
+    ``ws``, a uint8 device tensor of workspace_bytes(), allocated here when
+    not given)."""
     M, K = A.shape
     K2, Nn = B.shape
     if K != K2 or A.dtype != B.dtype:
         raise ValueError("shape / dtype mismatch")
     if out is None:
         out = torch.empty((M, Nn), dtype=torch.float32, device=A.device)
+    scaled = eA is not None or d is not None or eB is not None or A.dtype == torch.float16
+    if scaled and ws is None:
+        ws = torch.empty(workspace_bytes(plan, M, K, Nn), dtype=torch.uint8, device=A.device)
     N.check(N.lib().fmm_multiply(plan.handle, _ptr(A), _rowmajor(A, "A"), _ptr(B), _rowmajor(B, "B"),
                                  _ptr(out), _rowmajor(out, "C"), M, K, Nn, DTYPE[A.dtype], _ptr(eA), _ptr(d),
-                                 _ptr(eB), None, 0, _stream(stream)), "fmm_multiply")
+                                 _ptr(eB), _ptr(ws) if scaled else None, ws.numel() if scaled else 0,
+                                 _stream(stream)), "fmm_multiply")
     return out
 
 

@@ -16,6 +16,15 @@
 
 namespace fmm {
 
+static thread_local std::string t_last_error;
+
+// Record a failed CUDA call's error text for fmm_last_error().
+static bool cuda_ok(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  t_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return false;
+}
+
 // Device status word: bits kStatusTimeout / kStatusNonfinite, OR-ed by the
 // kernels, read and cleared by fmm_sync_status.
 __device__ int g_status;
@@ -97,12 +106,13 @@ static fmm_status run_plan(const Plan* p, TileOperand a, TileOperand b, float* C
   const int64_t bm = (M + p->pm - 1) / p->pm, bk = (K + p->pk - 1) / p->pk, bn = (N + p->pn - 1) / p->pn;
   a.T = M; a.K = K; a.bt = bm; a.bk = bk;
   b.T = N; b.K = K; b.bt = bn; b.bk = bk;
-  // 16-byte vector loads along the contiguous index need every term's start
-  // (block offset + 8-element chunk) to stay 16-byte aligned.
+  // Vector loads of 8 consecutive elements (32 bytes for fp32, 16 for 16-bit
+  // types) need every chunk start -- block offset + multiple of 8 elements
+  // along the contiguous index, any row -- to be aligned to that size.
   auto vec = [&](const TileOperand& o) {
-    const int es = esize(o.dtype);
     const int64_t blk = o.kcontig ? o.bk : o.bt;
-    return ((uintptr_t)o.ptr % 16 == 0) && ((o.ld * es) % 16 == 0) && ((blk * es) % 16 == 0) ? 1 : 0;
+    const uintptr_t align = o.dtype == kF32 ? 32 : 16;
+    return ((uintptr_t)o.ptr % align == 0) && (o.ld % 8 == 0) && (blk % 8 == 0) ? 1 : 0;
   };
   a.vec_ok = vec(a);
   b.vec_ok = vec(b);
@@ -121,9 +131,12 @@ static fmm_status run_plan(const Plan* p, TileOperand a, TileOperand b, float* C
   g.leaves = p->dev;
   g.num_leaves = p->leaves;
   g.kl = bk;
+  g.pm = p->pm;
+  g.pk = p->pk;
+  g.pn = p->pn;
   g.status = status;
   g.timeout_ns = timeout_ns();
-  return launch_fused_gemm(g, p->leaf_format, st) == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
+  return cuda_ok(launch_fused_gemm(g, p->leaf_format, st), "fused multiply launch") ? FMM_OK : FMM_ERR_CUDA;
 }
 
 }  // namespace fmm
@@ -190,9 +203,11 @@ fmm_status fmm_scale_outside(const void* A, const void* B, int dtype, int64_t M,
     if (launch_fill(eB, N, 0, st) != cudaSuccess) return FMM_ERR_CUDA;
     return FMM_OK;
   }
-  if (launch_row_exp(A, dtype, M, K, lda, d_in, +1, eA, kRowOStep, status, st) != cudaSuccess) return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_row_exp(A, dtype, M, K, lda, d_in, +1, eA, kRowOStep, status, st), "row reduction"))
+    return FMM_ERR_CUDA;
   // eB_j = e(max_k 2^-d_k |B_kj|): column reduction of B with row shifts -d.
-  if (launch_col_exp(B, dtype, K, N, ldb, d_in, -1, eB, status, st) != cudaSuccess) return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_col_exp(B, dtype, K, N, ldb, d_in, -1, eB, status, st), "column reduction"))
+    return FMM_ERR_CUDA;
   if (launch_zero_sentinel(eB, N, st) != cudaSuccess) return FMM_ERR_CUDA;
   return FMM_OK;
 }
@@ -234,17 +249,23 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
   return FMM_OK;
 }
 
+// Workspace of a scaled multiply: the scaled copies A' (M x ldA') and
+// B' (K x ldB') in fp32 (bf16 for bf16 inputs), leading dimensions rounded
+// up to 8 elements, each 256-byte aligned.
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+static size_t scaled_ws_bytes(int64_t M, int64_t K, int64_t N, int es) {
+  return (size_t)round_up(M * round_up(K, 8) * es, 256) + (size_t)round_up(K * round_up(N, 8) * es, 256);
+}
+
 fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t M, int64_t K, int64_t N, size_t* bytes) {
   if (!plan || !bytes || M < 0 || K < 0 || N < 0) return FMM_ERR_ARG;
-  *bytes = 0;
+  *bytes = scaled_ws_bytes(M, K, N, 4);
   return FMM_OK;
 }
 
 fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
                         int64_t ldc, int64_t M, int64_t K, int64_t N, int in_dtype, const int32_t* eA,
                         const int32_t* d, const int32_t* eB, void* ws, size_t ws_bytes, void* stream) {
-  (void)ws;
-  (void)ws_bytes;
   const Plan* p = reinterpret_cast<const Plan*>(plan);
   if (!p || !valid_dtype(in_dtype) || M < 0 || K < 0 || N < 0) return FMM_ERR_ARG;
   if (M > 0 && N > 0 && !C) return FMM_ERR_ARG;
@@ -253,15 +274,37 @@ fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void*
     return FMM_ERR_SHAPE;
   if (in_dtype == FMM_DT_F16 && p->leaf_format == FMM_LEAF_BF16X3) return FMM_ERR_DTYPE;
   if ((M + p->pm - 1) / p->pm >= (1ll << 31) || (N + p->pn - 1) / p->pn >= (1ll << 31)) return FMM_ERR_SHAPE;
+  cudaStream_t st = as_stream(stream);
+  const void* Aop = A;
+  const void* Bop = B;
+  int64_t ldA = lda, ldB = ldb;
+  int dt = in_dtype;
+  if ((eA || d || eB || in_dtype == FMM_DT_F16) && M > 0 && N > 0 && K > 0) {
+    // Algs. 1-3: multiply A' = 2^-eA A 2^d and B' = 2^-d B 2^-eB (exact
+    // copies written by one HBM-bound pass each), unscale in the epilogue.
+    // fp16 inputs always take this path (as an exact widening to fp32).
+    const int wdt = in_dtype == FMM_DT_BF16 ? kBF16 : kF32;
+    const int es = wdt == kF32 ? 4 : 2;
+    if (!ws || ws_bytes < scaled_ws_bytes(M, K, N, es) || (uintptr_t)ws % 256 != 0) return FMM_ERR_WORKSPACE;
+    ldA = round_up(K, 8);
+    ldB = round_up(N, 8);
+    void* Ap = ws;
+    void* Bp = static_cast<char*>(ws) + round_up(M * ldA * es, 256);
+    if (!cuda_ok(launch_apply_exp(A, in_dtype, M, K, lda, eA, -1, d, +1, Ap, ldA, st), "apply scaling to A"))
+      return FMM_ERR_CUDA;
+    if (!cuda_ok(launch_apply_exp(B, in_dtype, K, N, ldb, d, -1, eB, -1, Bp, ldB, st), "apply scaling to B"))
+      return FMM_ERR_CUDA;
+    Aop = Ap;
+    Bop = Bp;
+    dt = wdt;
+  }
   TileOperand a{};
-  a.ptr = A; a.ld = lda; a.dtype = in_dtype; a.kcontig = 1;
-  a.t_exp = eA; a.t_sign = -1; a.k_exp = d; a.k_sign = +1;
+  a.ptr = Aop; a.ld = ldA; a.dtype = dt; a.kcontig = 1;
   a.blk_t_shift = 16; a.blk_k_shift = 0;
   TileOperand b{};
-  b.ptr = B; b.ld = ldb; b.dtype = in_dtype; b.kcontig = 0;
-  b.t_exp = eB; b.t_sign = -1; b.k_exp = d; b.k_sign = -1;
+  b.ptr = Bop; b.ld = ldB; b.dtype = dt; b.kcontig = 0;
   b.blk_t_shift = 0; b.blk_k_shift = 16;
-  return run_plan(p, a, b, C, ldc, M, K, N, eA, eB, as_stream(stream));
+  return run_plan(p, a, b, C, ldc, M, K, N, eA, eB, st);
 }
 
 fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc, const void* A, int64_t lda,
@@ -270,6 +313,7 @@ fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc,
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p || !valid_dtype(in_dtype) || M < 0 || K < 0 || N < 0) return FMM_ERR_ARG;
   if (M > 0 && N > 0 && (!dC || lddc < N)) return FMM_ERR_ARG;
+  if (in_dtype == FMM_DT_F16) return FMM_ERR_DTYPE;
   if (in_dtype == FMM_DT_F16 && p->leaf_format == FMM_LEAF_BF16X3) return FMM_ERR_DTYPE;
   static std::mutex mu;
   {
@@ -341,5 +385,7 @@ const char* fmm_status_string(fmm_status s) {
 }
 
 const char* fmm_version(void) { return "fmm-gb300 0.1 (sm_103a)"; }
+
+const char* fmm_last_error(void) { return t_last_error.c_str(); }
 
 }  // extern "C"

@@ -149,10 +149,28 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor for an MN-major operand tile in the
+// 128-byte-swizzle canonical layout: for each k a 128-byte row of 64
+// consecutive M (or N) elements, 8-k groups 1024 bytes apart (stride byte
+// offset), 64-element M/N chunks 8192 bytes apart (leading byte offset),
+// 16-byte units XOR-permuted by (k mod 8).
+__device__ __forceinline__ uint64_t smem_desc_mn_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)(8192 >> 4) << 16;          // leading byte offset: next 64-wide M/N chunk
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-k group
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
 // Instruction descriptor, kind::f16: fp32 accumulator, A/B of type
-// `ab_fmt` (0 = fp16, 1 = bf16), both K-major, M x N tile.
-__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_fmt, int M, int N) {
-  return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// `ab_fmt` (0 = fp16, 1 = bf16), M x N tile; a_mn / b_mn select the
+// MN-major (transposed) operand layout instead of K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_fmt, int M, int N, bool a_mn = false,
+                                                 bool b_mn = false) {
+  return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // 32 lanes x 32 consecutive fp32 columns of TMEM into registers (one lane

@@ -17,11 +17,14 @@ cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
                            int* out, int* status, cudaStream_t st);
 cudaError_t launch_zero_sentinel(int* p, int64_t n, cudaStream_t st);
 cudaError_t launch_fill(int* p, int64_t n, int v, cudaStream_t st);
+// Y = 2^(rs re_i + cs ce_k) X (exact), Y in fp32 (bf16 when X is bf16).
+cudaError_t launch_apply_exp(const void* X, int dt, int64_t R, int64_t C, int64_t ld, const int* re, int rs,
+                             const int* ce, int cs, void* Y, int64_t ldy, cudaStream_t st);
 
 // One operand of the fused multiply as the kernel sees it: a tile has
 // "t" rows (the M side for A, the N side for B) and "k" columns.  Element
 // (t, k) of the logical operand is at ptr[t*ld + k] when kcontig, else at
-// ptr[k*ld + t].  The scale applied on load is 2^(t_sign*t_exp[t] + k_sign*k_exp[k]).
+// ptr[k*ld + t].
 struct TileOperand {
   const void* ptr;
   int64_t ld;
@@ -30,10 +33,6 @@ struct TileOperand {
   int vec_ok;    // 16-byte vector loads allowed along the contiguous index
   int64_t T, K;  // logical extents
   int64_t bt, bk;  // leaf block extents along t and k
-  const int* t_exp;
-  int t_sign;
-  const int* k_exp;
-  int k_sign;
   int blk_t_shift;  // term block packing: t block = (blk >> blk_t_shift) & 0xFFFF
   int blk_k_shift;  //                      k block = (blk >> blk_k_shift) & 0xFFFF
 };
@@ -53,7 +52,8 @@ struct GemmArgs {
   EpilogueArgs c;
   const LeafDesc* leaves;
   int64_t num_leaves;
-  int64_t kl;  // leaf K extent
+  int64_t kl;          // leaf K extent
+  int64_t pm, pk, pn;  // leaf block grid (products of m0, k0, n0)
   int* status;
   uint64_t timeout_ns;
 };

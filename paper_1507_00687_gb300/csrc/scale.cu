@@ -7,6 +7,7 @@
 // monotone in |x|.  So no mantissa is ever multiplied and the scale factors
 // are exact by construction.  Both kernels are single passes over the
 // matrix, HBM-bound: 4 (fp32) or 2 (bf16/fp16) bytes read per element.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -134,6 +135,86 @@ __global__ void __launch_bounds__(256) col_exp_kernel(const void* X, int64_t R, 
   if (nf) atomicOr(status, kStatusNonfinite);
 }
 
+// x 2^e, exact whenever the result is a normal number (two multiplies when
+// 2^e alone is outside the binary32 range).
+__device__ __forceinline__ float scale_pow2(float x, int e) {
+  if (e >= -126 && e <= 127) return x * exp2i(e);
+  const int h = e / 2;
+  return (x * exp2i(h)) * exp2i(e - h);
+}
+
+// Apply pass of Algs. 1-3: Y[i, k] = 2^(rs re_i + cs ce_k) X[i, k] for an
+// R x C matrix, written in the output type (fp32, or bf16 for bf16 input,
+// where a power-of-two scaling of a bf16 value is again a bf16 value).  One
+// HBM-bound pass: each thread moves 4 consecutive elements of one row.
+template <int DT, bool OUT_BF16>
+__global__ void __launch_bounds__(256) apply_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
+                                                        const int* re, int rs, const int* ce, int cs, void* Y,
+                                                        int64_t ldy, int vec_ok) {
+  const int64_t C4 = (C + 3) / 4;
+  const int64_t total = R * C4;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / C4, c0 = (idx % C4) * 4;
+    const int er = re ? rs * __ldg(re + i) : 0;
+    float x[4];
+    int ec[4] = {0, 0, 0, 0};
+    const bool full = vec_ok && c0 + 4 <= C;
+    if (full) {
+      if constexpr (DT == kF32) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + i * ld + c0));
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+      } else {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const unsigned short*>(X) + i * ld + c0));
+        const uint32_t h[4] = {v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          x[t] = DT == kBF16 ? __uint_as_float(h[t] << 16) : __half2float(__ushort_as_half((unsigned short)h[t]));
+      }
+      if (ce) {
+        const int4 e = __ldg(reinterpret_cast<const int4*>(ce + c0));
+        ec[0] = e.x; ec[1] = e.y; ec[2] = e.z; ec[3] = e.w;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int64_t c = c0 + t;
+        if (c < C) {
+          if constexpr (DT == kF32) x[t] = __ldg(reinterpret_cast<const float*>(X) + i * ld + c);
+          else if constexpr (DT == kBF16)
+            x[t] = __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(X) + i * ld + c) << 16);
+          else x[t] = __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(X) + i * ld + c)));
+          if (ce) ec[t] = __ldg(ce + c);
+        } else {
+          x[t] = 0.f;
+        }
+      }
+    }
+    float y[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) y[t] = scale_pow2(x[t], er + cs * ec[t]);
+    if constexpr (OUT_BF16) {
+      unsigned short* out = reinterpret_cast<unsigned short*>(Y) + i * ldy + c0;
+      // exact: a power-of-two multiple of a bf16 value in range is a bf16 value
+      const uint32_t b0 = __float_as_uint(y[0]) >> 16, b1 = __float_as_uint(y[1]) >> 16;
+      const uint32_t b2 = __float_as_uint(y[2]) >> 16, b3 = __float_as_uint(y[3]) >> 16;
+      if (full) {
+        *reinterpret_cast<uint2*>(out) = make_uint2(b0 | (b1 << 16), b2 | (b3 << 16));
+      } else {
+        const uint32_t b[4] = {b0, b1, b2, b3};
+        for (int t = 0; t < 4 && c0 + t < C; ++t) out[t] = (unsigned short)b[t];
+      }
+    } else {
+      float* out = reinterpret_cast<float*>(Y) + i * ldy + c0;
+      if (full) {
+        *reinterpret_cast<float4*>(out) = make_float4(y[0], y[1], y[2], y[3]);
+      } else {
+        for (int t = 0; t < 4 && c0 + t < C; ++t) out[t] = y[t];
+      }
+    }
+  }
+}
+
 __global__ void fill_kernel(int* p, int64_t n, int v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
@@ -201,6 +282,30 @@ cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
 cudaError_t launch_zero_sentinel(int* p, int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   zero_sentinel_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(p, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_exp(const void* X, int dt, int64_t R, int64_t C, int64_t ld, const int* re, int rs,
+                             const int* ce, int cs, void* Y, int64_t ldy, cudaStream_t st) {
+  if (R == 0 || C == 0) return cudaSuccess;
+  const bool out_bf16 = dt == kBF16;
+  const int vec = vec_aligned(X, ld, dt) && ((uintptr_t)Y % 16 == 0) && (ldy % 4 == 0) &&
+                          ((uintptr_t)ce % 16 == 0)
+                      ? 1
+                      : 0;
+  const int64_t total = R * ((C + 3) / 4);
+  const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
+  switch (dt) {
+    case kF32:
+      apply_exp_kernel<kF32, false><<<grid, 256, 0, st>>>(X, R, C, ld, re, rs, ce, cs, Y, ldy, vec);
+      break;
+    case kBF16:
+      apply_exp_kernel<kBF16, true><<<grid, 256, 0, st>>>(X, R, C, ld, re, rs, ce, cs, Y, ldy, vec);
+      break;
+    default:
+      apply_exp_kernel<kF16, false><<<grid, 256, 0, st>>>(X, R, C, ld, re, rs, ce, cs, Y, ldy, vec);
+      break;
+  }
   return cudaGetLastError();
 }
 

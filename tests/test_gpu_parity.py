@@ -100,7 +100,7 @@ def test_multiply_integer_inputs_bit_exact(api, names, M, K, N):
     A = inputs.integers((M, K), -4, 4, seed=M)
     B = inputs.integers((K, N), -4, 4, seed=N + 1)
     want = A @ B
-    for dt, leaf in (("f32", "bf16x3"), ("bf16", "bf16"), ("f32", "fp16"), ("f16", "fp16")):
+    for dt, leaf in (("f32", "bf16x3"), ("bf16", "bf16"), ("f32", "fp16"), ("f16", "fp16"), ("bf16", "bf16x3")):
         plan = api.Plan(names, leaf)
         got = api.multiply(plan, to_dev(A, dt), to_dev(B, dt))
         api.sync_status()
