@@ -26,6 +26,7 @@
  *    B' = 2^-d B 2^-eB are exact; fmm_multiply writes them into the
  *    caller's workspace in one bandwidth-bound pass and multiplies its
  *    output by 2^(eA+eB) in the epilogue of the fused kernel.
+ *  - Device code needs sm_103a and the CUDA driver's tensor-map encoder.
  *  - Thread safety: plans are immutable after creation and may be used from
  *    several host threads; calls on one stream execute in order.
  */
@@ -155,10 +156,13 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
                      int32_t* eB, void* stream);
 
 /*
- * Workspace bytes fmm_multiply needs for this plan and shape when exponent
- * vectors are passed (an upper bound over input types): room for the scaled
- * copies A' and B' (fp32; bf16 for bf16 inputs), which one HBM-bound pass
- * each writes before the multiply.  Unscaled calls need no workspace.
+ * Workspace bytes fmm_multiply / fmm_multiply_backward need for this plan
+ * and shape (an upper bound over input types).  The fused kernel reads its
+ * operands through tensor-memory-access copies of whole 128 x 64 tiles; an
+ * operand whose leaf blocks are not whole tiles, whose rows are not 16-byte
+ * aligned, that is scaled (exponent vectors given) or fp16 is first written,
+ * by one bandwidth-bound pass, as a blocked, zero-padded, scaled copy into
+ * the workspace.  Calls whose operands need no copy may pass NULL / 0.
  */
 fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t M, int64_t K, int64_t N, size_t* bytes);
 
@@ -171,9 +175,9 @@ fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t M, int64_t K, int64_t N, 
  * load stage, multiplies on the tensor cores and adds W-weighted products
  * into C in its epilogue; each output tile is owned by one CTA, so the
  * result is deterministic.  ws/ws_bytes: device workspace, 256-byte
- * aligned, of at least fmm_workspace_size bytes when any exponent vector is
- * given or the inputs are fp16 (which are widened to fp32 there);
- * FMM_ERR_WORKSPACE otherwise.  May be NULL/0 for unscaled fp32 / bf16.
+ * aligned, of fmm_workspace_size bytes, used when an operand needs a
+ * prepared copy (see fmm_workspace_size); FMM_ERR_WORKSPACE if one is needed
+ * and the workspace is missing or too small.
  */
 fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void* B, int64_t ldb,
                         float* C, int64_t ldc, int64_t M, int64_t K, int64_t N, int in_dtype,
@@ -188,12 +192,14 @@ fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void*
  * Sec. 5.3 and App. A-C): dA uses [[W, V^T, U]] (an <m0,n0,k0> rule), dB
  * uses [[U^T, W, V]] (a <k0,m0,n0> rule), where ^T re-indexes the operand's
  * entries by transposition.  dA or dB may be NULL to skip it.  A and B have
- * element type in_dtype (FMM_DT_F32 or FMM_DT_BF16; FMM_ERR_DTYPE for fp16).
+ * element type in_dtype.  ws/ws_bytes: device workspace as for fmm_multiply
+ * (fmm_workspace_size covers both passes; the two products run one after
+ * the other and reuse it).
  */
 fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc, const void* A,
                                  int64_t lda, const void* B, int64_t ldb, float* dA,
                                  int64_t ldda, float* dB, int64_t lddb, int64_t M, int64_t K,
-                                 int64_t N, int in_dtype, void* stream);
+                                 int64_t N, int in_dtype, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Synchronise the stream, then read and clear the device status word.

@@ -66,7 +66,7 @@ def lib():
     L.fmm_multiply.argtypes = [vp, vp, i64, vp, i64, vp, i64, i64, i64, i64, C.c_int, vp, vp, vp, vp,
                                C.c_size_t, vp]
     L.fmm_multiply_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, i64, i64, i64,
-                                        C.c_int, vp]
+                                        C.c_int, vp, C.c_size_t, vp]
     L.fmm_sync_status.argtypes = [vp]
     L.fmm_status_string.argtypes = [C.c_int]
     L.fmm_status_string.restype = C.c_char_p

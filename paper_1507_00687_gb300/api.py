@@ -128,41 +128,55 @@ def workspace_bytes(plan: Plan, M: int, K: int, Ncols: int) -> int:
     return b.value
 
 
+_WS = {}
+
+
+def _workspace(plan: Plan, M: int, K: int, Ncols: int, device) -> torch.Tensor:
+    """A cached device workspace of at least workspace_bytes() bytes."""
+    need = workspace_bytes(plan, M, K, Ncols)
+    key = torch.device(device).index
+    ws = _WS.get(key)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=device)
+        _WS[key] = ws
+    return ws
+
+
 def multiply(plan: Plan, A: torch.Tensor, B: torch.Tensor, eA=None, d=None, eB=None,
              out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """C = A B (float32) by the plan's fast algorithm on the scaled operands
-    (C = D_A (A' B') D_B when exponents are given; the scaled copies go to
-    ``ws``, a uint8 device tensor of workspace_bytes(), allocated here when
-    not given)."""
+    (C = D_A (A' B') D_B when exponents are given).  ``ws`` is a uint8 device
+    tensor of workspace_bytes() used for operand copies (scaled, padded or
+    realigned); a cached one is used when not given."""
     M, K = A.shape
     K2, Nn = B.shape
     if K != K2 or A.dtype != B.dtype:
         raise ValueError("shape / dtype mismatch")
     if out is None:
         out = torch.empty((M, Nn), dtype=torch.float32, device=A.device)
-    scaled = eA is not None or d is not None or eB is not None or A.dtype == torch.float16
-    if scaled and ws is None:
-        ws = torch.empty(workspace_bytes(plan, M, K, Nn), dtype=torch.uint8, device=A.device)
+    if ws is None:
+        ws = _workspace(plan, M, K, Nn, A.device)
     N.check(N.lib().fmm_multiply(plan.handle, _ptr(A), _rowmajor(A, "A"), _ptr(B), _rowmajor(B, "B"),
                                  _ptr(out), _rowmajor(out, "C"), M, K, Nn, DTYPE[A.dtype], _ptr(eA), _ptr(d),
-                                 _ptr(eB), _ptr(ws) if scaled else None, ws.numel() if scaled else 0,
-                                 _stream(stream)), "fmm_multiply")
+                                 _ptr(eB), _ptr(ws), ws.numel(), _stream(stream)), "fmm_multiply")
     return out
 
 
 def multiply_backward(plan: Plan, dC: torch.Tensor, A: torch.Tensor, B: torch.Tensor, need_a: bool = True,
-                      need_b: bool = True, stream=None):
+                      need_b: bool = True, ws: Optional[torch.Tensor] = None, stream=None):
     """(dA, dB) = (dC B^T, A^T dC) by the permuted fast rules."""
     M, K = A.shape
     Nn = B.shape[1]
     dC = dC.contiguous().float()
+    if ws is None:
+        ws = _workspace(plan, M, K, Nn, A.device)
     dA = torch.empty((M, K), dtype=torch.float32, device=A.device) if need_a else None
     dB = torch.empty((K, Nn), dtype=torch.float32, device=A.device) if need_b else None
     N.check(N.lib().fmm_multiply_backward(plan.handle, _ptr(dC), _rowmajor(dC, "dC"), _ptr(A),
                                           _rowmajor(A, "A"), _ptr(B), _rowmajor(B, "B"), _ptr(dA),
                                           K if dA is not None else 0, _ptr(dB),
-                                          Nn if dB is not None else 0, M, K, Nn, DTYPE[A.dtype],
-                                          _stream(stream)), "fmm_multiply_backward")
+                                          Nn if dB is not None else 0, M, K, Nn, DTYPE[A.dtype], _ptr(ws),
+                                          ws.numel(), _stream(stream)), "fmm_multiply_backward")
     return dA, dB
 
 

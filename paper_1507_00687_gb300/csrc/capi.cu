@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/fmm.h"
@@ -52,7 +53,6 @@ static uint64_t timeout_ns() {
   return v;
 }
 
-static int esize(int dt) { return dt == kF32 ? 4 : 2; }
 
 static bool valid_dtype(int dt) { return dt == FMM_DT_F32 || dt == FMM_DT_BF16 || dt == FMM_DT_F16; }
 
@@ -91,52 +91,167 @@ static fmm_status make_plan(const std::vector<CanonRule>& rules, int leaf, Plan*
   return FMM_OK;
 }
 
-// Run the flattened plan p on operands described by (a, b) into C.
-// Block extents follow from the plan's granules: leaf block = ceil(dim / granule).
-static fmm_status run_plan(const Plan* p, TileOperand a, TileOperand b, float* C, int64_t ldc, int64_t M,
-                           int64_t K, int64_t N, const int* eA, const int* eB, cudaStream_t st) {
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+static int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+// ---------------------------------------------------------------- tensor maps
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// A 2-D tensor map over a row-major (rows x cols, ld) matrix with a box of
+// box_cols x box_rows elements, no swizzle, zero fill outside.
+static bool make_map(CUtensorMap* m, const void* ptr, int dt, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                     int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    t_last_error = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * (dt == kF32 ? 4 : 2))};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, dt == kF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    t_last_error = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- operands
+
+// One operand of a fast product as stored by the caller: a row-major memory
+// matrix (rows x cols, ld).  kcontig: the product's k index runs along the
+// memory columns (t along rows); else t runs along the columns.  T, Kd: the
+// logical extents; pt, pk: the plan's block counts along t and k; re / ce:
+// optional exponents scaling memory rows / columns (signs rs, cs).
+struct Source {
+  const void* ptr;
+  int64_t ld;
+  int dtype;
+  bool kcontig;
+  int64_t T, Kd, pt, pk;
+  const int* re;
+  int rs;
+  const int* ce;
+  int cs;
+};
+
+// Bytes of the prepared copy of a source (fp32 upper bound).
+static int64_t prepared_bytes(int64_t T, int64_t Kd, int64_t pt, int64_t pk) {
+  return round_up(pt * round_up(ceil_div(T, pt), 128) * pk * round_up(ceil_div(Kd, pk), 64) * 4, 256);
+}
+
+// Build the kernel's view of a source: use the caller's matrix when every
+// block is already whole tiles, aligned and unscaled; else write the
+// blocked, padded (and scaled) copy into *ws and use that.
+static fmm_status prepare(const Source& s, int blk_t_shift, int blk_k_shift, char** ws, char* ws_end, TileOperand* op,
+                          CUtensorMap* map, cudaStream_t st) {
+  const int64_t bt = ceil_div(s.T, s.pt), bk = ceil_div(s.Kd, s.pk);
+  const int64_t btp = round_up(bt, 128), bkp = round_up(bk, 64);
+  const int es = s.dtype == kF32 ? 4 : 2;
+  const bool direct = !s.re && !s.ce && s.dtype != kF16 && (uintptr_t)s.ptr % 16 == 0 && (s.ld * es) % 16 == 0 &&
+                      bt == btp && bk == bkp && bt * s.pt == s.T && bk * s.pk == s.Kd;
+  op->kcontig = s.kcontig ? 1 : 0;
+  op->bt = btp;
+  op->bk = bkp;
+  op->blk_t_shift = blk_t_shift;
+  op->blk_k_shift = blk_k_shift;
+  if (direct) {
+    op->ptr = s.ptr;
+    op->ld = s.ld;
+    op->dtype = s.dtype;
+  } else {
+    const int odt = s.dtype == kBF16 ? kBF16 : kF32;
+    const int oes = odt == kF32 ? 4 : 2;
+    // memory rows follow t (kcontig) or k; columns the other index
+    const int64_t rblk = s.kcontig ? bt : bk, rpad = s.kcontig ? btp : bkp;
+    const int64_t cblk = s.kcontig ? bk : bt, cpad = s.kcontig ? bkp : btp;
+    const int64_t R = s.kcontig ? s.T : s.Kd, Cc = s.kcontig ? s.Kd : s.T;
+    const int64_t Rp = (s.kcontig ? s.pt : s.pk) * rpad, Cp = (s.kcontig ? s.pk : s.pt) * cpad;
+    const int64_t bytes = round_up(Rp * Cp * oes, 256);
+    if (*ws + bytes > ws_end) return FMM_ERR_WORKSPACE;
+    if (!cuda_ok(launch_prepare(s.ptr, s.dtype, R, Cc, s.ld, rblk, rpad, cblk, cpad, s.re, s.rs, s.ce, s.cs, *ws, Rp,
+                                Cp, Cp, st),
+                 "operand preparation"))
+      return FMM_ERR_CUDA;
+    op->ptr = *ws;
+    op->ld = Cp;
+    op->dtype = odt;
+    *ws += bytes;
+  }
+  // memory rows x cols of the prepared operand
+  const int64_t rows = s.kcontig ? s.pt * btp : s.pk * bkp, cols = s.kcontig ? s.pk * bkp : s.pt * btp;
+  if (!make_map(map, op->ptr, op->dtype, rows, cols, op->ld, s.kcontig ? 64 : 128, s.kcontig ? 128 : 64))
+    return FMM_ERR_CUDA;
+  return FMM_OK;
+}
+
+// Run the flattened plan p: C (M x N) = X (M x K) Y (K x N) with X, Y given
+// as sources (X: t = M, k = K; Y: t = N, k = K).
+static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, float* C, int64_t ldc, int64_t M,
+                           int64_t K, int64_t N, const int* eA, const int* eB, void* ws, size_t ws_bytes,
+                           cudaStream_t st) {
   if (M == 0 || N == 0) return FMM_OK;
   if (K == 0) {
-    return cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)N * 4, (size_t)M, st) == cudaSuccess ? FMM_OK
-                                                                                                   : FMM_ERR_CUDA;
+    return cuda_ok(cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)N * 4, (size_t)M, st), "memset")
+               ? FMM_OK
+               : FMM_ERR_CUDA;
   }
   int* status = status_ptr();
   if (!status) return FMM_ERR_CUDA;
   if (ensure_uploaded(p) != FMM_OK) return FMM_ERR_CUDA;
-  const int64_t bm = (M + p->pm - 1) / p->pm, bk = (K + p->pk - 1) / p->pk, bn = (N + p->pn - 1) / p->pn;
-  a.T = M; a.K = K; a.bt = bm; a.bk = bk;
-  b.T = N; b.K = K; b.bt = bn; b.bk = bk;
-  // Vector loads of 8 consecutive elements (32 bytes for fp32, 16 for 16-bit
-  // types) need every chunk start -- block offset + multiple of 8 elements
-  // along the contiguous index, any row -- to be aligned to that size.
-  auto vec = [&](const TileOperand& o) {
-    const int64_t blk = o.kcontig ? o.bk : o.bt;
-    const uintptr_t align = o.dtype == kF32 ? 32 : 16;
-    return ((uintptr_t)o.ptr % align == 0) && (o.ld % 8 == 0) && (blk % 8 == 0) ? 1 : 0;
-  };
-  a.vec_ok = vec(a);
-  b.vec_ok = vec(b);
-  GemmArgs g{};
-  g.a = a;
-  g.b = b;
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  char* w = static_cast<char*>(ws);
+  char* w_end = w ? w + ws_bytes : nullptr;
+  if (w && (uintptr_t)w % 256 != 0) return FMM_ERR_WORKSPACE;
+  fmm_status s = prepare(x, 16, 0, &w, w_end, &g.a, &g.map_a, st);
+  if (s != FMM_OK) return s;
+  s = prepare(y, 0, 16, &w, w_end, &g.b, &g.map_b, st);
+  if (s != FMM_OK) return s;
   g.c.C = C;
   g.c.ldc = ldc;
   g.c.M = M;
   g.c.N = N;
-  g.c.bm = bm;
-  g.c.bn = bn;
+  g.c.bm = ceil_div(M, p->pm);
+  g.c.bn = ceil_div(N, p->pn);
   g.c.eA = eA;
   g.c.eB = eB;
-  g.c.vec_ok = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0) && (bn % 4 == 0) ? 1 : 0;
+  g.c.vec_ok = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0) && (g.c.bn % 4 == 0) ? 1 : 0;
   g.leaves = p->dev;
   g.num_leaves = p->leaves;
-  g.kl = bk;
-  g.pm = p->pm;
-  g.pk = p->pk;
-  g.pn = p->pn;
   g.status = status;
   g.timeout_ns = timeout_ns();
   return cuda_ok(launch_fused_gemm(g, p->leaf_format, st), "fused multiply launch") ? FMM_OK : FMM_ERR_CUDA;
+}
+
+// Workspace of fmm_multiply and fmm_multiply_backward (fp32 upper bound):
+// the prepared copies of the two operands of the largest of the forward,
+// dA and dB products.
+static size_t ws_bytes_for(const Plan* p, int64_t M, int64_t K, int64_t N) {
+  const int64_t fwd = prepared_bytes(M, K, p->pm, p->pk) + prepared_bytes(N, K, p->pn, p->pk);
+  const int64_t da = prepared_bytes(M, N, p->pm, p->pn) + prepared_bytes(K, N, p->pk, p->pn);
+  const int64_t db = prepared_bytes(K, M, p->pk, p->pm) + prepared_bytes(N, M, p->pn, p->pm);
+  return (size_t)std::max(fwd, std::max(da, db));
 }
 
 }  // namespace fmm
@@ -249,17 +364,9 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
   return FMM_OK;
 }
 
-// Workspace of a scaled multiply: the scaled copies A' (M x ldA') and
-// B' (K x ldB') in fp32 (bf16 for bf16 inputs), leading dimensions rounded
-// up to 8 elements, each 256-byte aligned.
-static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
-static size_t scaled_ws_bytes(int64_t M, int64_t K, int64_t N, int es) {
-  return (size_t)round_up(M * round_up(K, 8) * es, 256) + (size_t)round_up(K * round_up(N, 8) * es, 256);
-}
-
 fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t M, int64_t K, int64_t N, size_t* bytes) {
   if (!plan || !bytes || M < 0 || K < 0 || N < 0) return FMM_ERR_ARG;
-  *bytes = scaled_ws_bytes(M, K, N, 4);
+  *bytes = ws_bytes_for(reinterpret_cast<const Plan*>(plan), M, K, N);
   return FMM_OK;
 }
 
@@ -273,47 +380,23 @@ fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void*
   if ((M > 0 && K > 0 && lda < K) || (K > 0 && N > 0 && ldb < N) || (M > 0 && N > 0 && ldc < N))
     return FMM_ERR_SHAPE;
   if (in_dtype == FMM_DT_F16 && p->leaf_format == FMM_LEAF_BF16X3) return FMM_ERR_DTYPE;
-  if ((M + p->pm - 1) / p->pm >= (1ll << 31) || (N + p->pn - 1) / p->pn >= (1ll << 31)) return FMM_ERR_SHAPE;
-  cudaStream_t st = as_stream(stream);
-  const void* Aop = A;
-  const void* Bop = B;
-  int64_t ldA = lda, ldB = ldb;
-  int dt = in_dtype;
-  if ((eA || d || eB || in_dtype == FMM_DT_F16) && M > 0 && N > 0 && K > 0) {
-    // Algs. 1-3: multiply A' = 2^-eA A 2^d and B' = 2^-d B 2^-eB (exact
-    // copies written by one HBM-bound pass each), unscale in the epilogue.
-    // fp16 inputs always take this path (as an exact widening to fp32).
-    const int wdt = in_dtype == FMM_DT_BF16 ? kBF16 : kF32;
-    const int es = wdt == kF32 ? 4 : 2;
-    if (!ws || ws_bytes < scaled_ws_bytes(M, K, N, es) || (uintptr_t)ws % 256 != 0) return FMM_ERR_WORKSPACE;
-    ldA = round_up(K, 8);
-    ldB = round_up(N, 8);
-    void* Ap = ws;
-    void* Bp = static_cast<char*>(ws) + round_up(M * ldA * es, 256);
-    if (!cuda_ok(launch_apply_exp(A, in_dtype, M, K, lda, eA, -1, d, +1, Ap, ldA, st), "apply scaling to A"))
-      return FMM_ERR_CUDA;
-    if (!cuda_ok(launch_apply_exp(B, in_dtype, K, N, ldb, d, -1, eB, -1, Bp, ldB, st), "apply scaling to B"))
-      return FMM_ERR_CUDA;
-    Aop = Ap;
-    Bop = Bp;
-    dt = wdt;
-  }
-  TileOperand a{};
-  a.ptr = Aop; a.ld = ldA; a.dtype = dt; a.kcontig = 1;
-  a.blk_t_shift = 16; a.blk_k_shift = 0;
-  TileOperand b{};
-  b.ptr = Bop; b.ld = ldB; b.dtype = dt; b.kcontig = 0;
-  b.blk_t_shift = 0; b.blk_k_shift = 16;
-  return run_plan(p, a, b, C, ldc, M, K, N, eA, eB, st);
+  if (ceil_div(M, p->pm) >= (1ll << 30) || ceil_div(N, p->pn) >= (1ll << 30) || ceil_div(K, p->pk) >= (1ll << 30))
+    return FMM_ERR_SHAPE;
+  // A: t = M (rows of A), k = K (columns): k-contiguous; rows scaled by
+  // 2^-eA, columns by 2^d.  B: t = N (columns of B), k = K (rows):
+  // t-contiguous; rows scaled by 2^-d, columns by 2^-eB (Algs. 1-3).
+  const Source a{A, lda, in_dtype, true, M, K, p->pm, p->pk, eA, -1, d, +1};
+  const Source b{B, ldb, in_dtype, false, N, K, p->pn, p->pk, d, -1, eB, -1};
+  return run_plan(p, a, b, C, ldc, M, K, N, eA, eB, ws, ws_bytes, as_stream(stream));
 }
 
 fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc, const void* A, int64_t lda,
                                  const void* B, int64_t ldb, float* dA, int64_t ldda, float* dB, int64_t lddb,
-                                 int64_t M, int64_t K, int64_t N, int in_dtype, void* stream) {
+                                 int64_t M, int64_t K, int64_t N, int in_dtype, void* ws, size_t ws_bytes,
+                                 void* stream) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p || !valid_dtype(in_dtype) || M < 0 || K < 0 || N < 0) return FMM_ERR_ARG;
   if (M > 0 && N > 0 && (!dC || lddc < N)) return FMM_ERR_ARG;
-  if (in_dtype == FMM_DT_F16) return FMM_ERR_DTYPE;
   if (in_dtype == FMM_DT_F16 && p->leaf_format == FMM_LEAF_BF16X3) return FMM_ERR_DTYPE;
   static std::mutex mu;
   {
@@ -332,25 +415,25 @@ fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc,
   }
   cudaStream_t st = as_stream(stream);
   if (dA) {
-    // dA (M x K) = dC (M x N) B^T (N x K): operand 1 is dC (k = n contiguous),
-    // operand 2 is B^T, whose element (t = k, k' = n) is B[k][n] (contiguous in n).
+    // dA (M x K) = dC (M x N) B^T (N x K), an <m0, n0, k0> product.  dC:
+    // t = M, k = N, k-contiguous.  B^T: t = K (rows of B), k = N (columns of
+    // B): k-contiguous in B's memory.
     if (M > 0 && K > 0 && (ldda < K || (N > 0 && (!B || ldb < N)))) return FMM_ERR_SHAPE;
-    TileOperand a{};
-    a.ptr = dC; a.ld = lddc; a.dtype = kF32; a.kcontig = 1; a.blk_t_shift = 16; a.blk_k_shift = 0;
-    TileOperand b{};
-    b.ptr = B; b.ld = ldb; b.dtype = in_dtype; b.kcontig = 1; b.blk_t_shift = 0; b.blk_k_shift = 16;
-    fmm_status s = run_plan(p->grad_a, a, b, dA, ldda, M, N, K, nullptr, nullptr, st);
+    const Plan* g = p->grad_a;
+    const Source x{dC, lddc, kF32, true, M, N, g->pm, g->pk, nullptr, 0, nullptr, 0};
+    const Source y{B, ldb, in_dtype, true, K, N, g->pn, g->pk, nullptr, 0, nullptr, 0};
+    fmm_status s = run_plan(g, x, y, dA, ldda, M, N, K, nullptr, nullptr, ws, ws_bytes, st);
     if (s != FMM_OK) return s;
   }
   if (dB) {
-    // dB (K x N) = A^T (K x M) dC (M x N): A^T's element (t = k, k' = m) is
-    // A[m][k] (contiguous in t); dC's element (t = n, k' = m) is dC[m][n].
+    // dB (K x N) = A^T (K x M) dC (M x N), a <k0, m0, n0> product.  A^T:
+    // t = K (columns of A), k = M (rows of A): t-contiguous.  dC: t = N,
+    // k = M: t-contiguous.
     if (K > 0 && N > 0 && (lddb < N || (M > 0 && (!A || lda < K)))) return FMM_ERR_SHAPE;
-    TileOperand a{};
-    a.ptr = A; a.ld = lda; a.dtype = in_dtype; a.kcontig = 0; a.blk_t_shift = 16; a.blk_k_shift = 0;
-    TileOperand b{};
-    b.ptr = dC; b.ld = lddc; b.dtype = kF32; b.kcontig = 0; b.blk_t_shift = 0; b.blk_k_shift = 16;
-    fmm_status s = run_plan(p->grad_b, a, b, dB, lddb, K, M, N, nullptr, nullptr, st);
+    const Plan* g = p->grad_b;
+    const Source x{A, lda, in_dtype, false, K, M, g->pm, g->pk, nullptr, 0, nullptr, 0};
+    const Source y{dC, lddc, kF32, false, N, M, g->pn, g->pk, nullptr, 0, nullptr, 0};
+    fmm_status s = run_plan(g, x, y, dB, lddb, K, M, N, nullptr, nullptr, ws, ws_bytes, st);
     if (s != FMM_OK) return s;
   }
   return FMM_OK;

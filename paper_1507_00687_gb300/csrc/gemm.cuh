@@ -1,30 +1,33 @@
 #pragma once
-// Fused recursive fast matrix multiplication kernel (sm_103a, tcgen05).
+// Fused recursive fast matrix multiplication kernel (sm_103a, tcgen05 + TMA).
 //
 // One launch runs every leaf of a flattened plan (Eq. 4.4):
-//   S_r = sum_t a_coef[t] A'(a_blk[t]),  T_r = sum_t b_coef[t] B'(b_blk[t]),
-//   M_r = S_r T_r,                       C(c_blk[t]) += c_coef[t] M_r,
-// on operands A', B' (when scaling, the power-of-two scaled copies that the
-// apply pass of scale.cu wrote) and the unscale C = 2^eA C' 2^eB of
-// Algs. 1-3 folded into the last step.
+//   S_r = sum_t a_coef[t] A(a_blk[t]),  T_r = sum_t b_coef[t] B(b_blk[t]),
+//   M_r = S_r T_r,                      C(c_blk[t]) += c_coef[t] M_r,
+// and folds the unscale C = 2^eA C' 2^eB of Algs. 1-3 into the last step.
+// The operands it reads are "prepared": every leaf block is a whole number of
+// 128 x 64 tiles (the host either uses the caller's matrices directly or lets
+// the apply pass write scaled, zero-padded copies), so no tile ever crosses a
+// block or matrix edge.
 //
-// CTA roles (384 threads, one CTA per SM, persistent over output tiles):
+// CTA roles (384 threads, one CTA per SM, persistent over 128 x 128 output
+// tiles of the leaf block grid; a CTA visits every leaf for its tile, in leaf
+// order, so each C element is updated by one thread in a fixed order):
 //   warps 0-3   epilogue: TMEM -> registers, C(blk) = / += coef 2^(eA+eB) M_r
-//   warp  4     TMEM allocator and single-thread tcgen05.mma issuer
-//   warps 5-11  producers: load the terms of S_r / T_r from global memory,
-//               sum them in FP32 in index order,
-//               round to the leaf format (bf16 / fp16 / bf16 hi+lo) and
-//               store the tile in the 128-byte-swizzled K-major layout the
-//               tensor core reads.
-// A CTA owns one BM x BN tile coordinate of the leaf block grid and visits
-// every leaf for it in leaf order, so each C element is updated by one
-// thread in a fixed order: the result is deterministic.
+//   warp 4      lane 0: TMEM allocator and single-thread tcgen05.mma issuer;
+//               lane 1: TMA issuer -- one bulk tensor copy per term tile into a
+//               ring of shared-memory staging slots
+//   warps 5-11  producers: add the staged term tiles in FP32 in index order,
+//               round to the leaf format (bf16 / fp16 / bf16 hi+lo) and store
+//               the tensor-core operand tiles (A K-major or MN-major, B
+//               likewise, 128-byte swizzle).
 //
 // Every mbarrier wait is bounded (globaltimer); on expiry the kernel sets the
-// timeout bit of the status word, stops all roles, drains its MMAs and frees
-// its TMEM before returning.
+// timeout bit of the status word, stops all roles, waits for its own copies
+// and MMAs, frees its TMEM and returns.
 #include <cmath>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -32,117 +35,46 @@
 #include "device.cuh"
 #include "kernels.h"
 
-// Kernel templates of the fused multiply; instantiated per leaf format by
-// gemm_bf16.cu, gemm_f16.cu and gemm_bf16x3.cu.
-
 namespace fmm {
 namespace gemm {
 
-constexpr int BM = 128;
-constexpr int BK = 64;
+constexpr int BM = 128;  // tile rows (M side) = TMEM lanes
+constexpr int BN = 128;  // tile columns (N side)
+constexpr int BK = 64;   // K per stage
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;
 constexpr int kProdWarp0 = 5;
 constexpr int kProdWarps = 7;  // 12 warps in all: registers are granted per 4 warps
 constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kThreads = (kEpiWarps + 1 + kProdWarps) * 32;
+constexpr int kChunks = BM * BK / 8;  // 16-byte output units per operand tile (both sides)
+constexpr int kChunksPerThread = (kChunks + kProdThreads - 1) / kProdThreads;
+constexpr int kSlotBytes = 128 * 64 * 4;  // one staged fp32 term tile
 
 constexpr int kModeBF16 = 0, kModeF16 = 1, kModeBF16x3 = 2;
 
-
-// Per-iteration facts about one term of one operand side, computed once per
-// term so that a load unit costs one shared-memory lookup and one add:
-//   base      element offset of the term's tile origin (t0, k0) in its operand
-//   interior  the whole ROWS x 64 tile lies inside the term's block and the
-//             operand, and vector loads are allowed
-struct TermInfo {
-  int64_t base;
-  float coef;
-  int32_t interior;
-  int32_t tb, kb;
-};
-
-// What the producers of one pipeline iteration read from shared memory.
-// Two copies alternate; the copy for iteration i+1 is written during
-// iteration i, and the producers' named barrier at the top of each
-// iteration orders the writes before the reads.
-struct StageCtx {
-  TermInfo a[kMaxTerms];
-  TermInfo b[kMaxTerms];
-  int32_t na, nb;
-  int32_t a_interior, b_interior;  // every term of the side is interior
-};
-
-template <int BN, int MODE>
+template <int MODE>
 struct Cfg {
   static constexpr int kSplit = MODE == kModeBF16x3 ? 2 : 1;
   static constexpr int kATile = BM * BK * 2;
   static constexpr int kBTile = BN * BK * 2;
   static constexpr int kStage = kSplit * (kATile + kBTile);
-  static constexpr int kCtx = 2 * (int)sizeof(StageCtx);  // two iteration contexts
-  static constexpr int kStages =
-      (220 * 1024 - kCtx) / kStage > 8 ? 8 : (220 * 1024 - kCtx) / kStage;
+  static constexpr int kSlots = MODE == kModeBF16x3 ? 2 : 3;
+  static constexpr int kStaging = kSlots * kSlotBytes;
+  static constexpr int kStages = (220 * 1024 - kStaging) / kStage > 4 ? 4 : (220 * 1024 - kStaging) / kStage;
   static constexpr int kTmemCols = 2 * BN;  // double-buffered fp32 accumulator
-  static constexpr int kBarBytes = 256;
-  static constexpr int kSmem = kStages * kStage + kCtx + kBarBytes + 1024;  // + alignment slack
+  static constexpr int kBarBytes = 512;
+  static constexpr int kSmem = kStages * kStage + kStaging + kBarBytes + 1024;  // + alignment slack
 };
 
-// ------------------------------------------------------------ producer side
+// What the TMA issuer tells the producers about each staged tile.
+struct SlotInfo {
+  float coef;
+  int32_t flags;  // kLastA: last A term of its iteration; kLastB: last B term
+};
+constexpr int kLastA = 1, kLastB = 2;
 
-template <int DT>
-__device__ __forceinline__ float load1(const void* p, int64_t idx) {
-  if constexpr (DT == kF32) {
-    return __ldg(reinterpret_cast<const float*>(p) + idx);
-  } else if constexpr (DT == kBF16) {
-    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(p) + idx));
-  } else {
-    return __half2float(__ldg(reinterpret_cast<const __half*>(p) + idx));
-  }
-}
-
-// 16-byte read-only load that does not allocate in L1 (operand data is
-// streamed once per CTA; L1 is left to the small, reused lookups).
-__device__ __forceinline__ uint4 ldg_stream(const void* p) {
-  uint4 r;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-               : "l"(p));
-  return r;
-}
-
-template <int DT>
-__device__ __forceinline__ void load8(const void* p, int64_t idx, float (&v)[8]) {
-  if constexpr (DT == kF32) {
-    const uint4* q = reinterpret_cast<const uint4*>(reinterpret_cast<const float*>(p) + idx);
-    const uint4 x = ldg_stream(q), y = ldg_stream(q + 1);
-    v[0] = __uint_as_float(x.x); v[1] = __uint_as_float(x.y); v[2] = __uint_as_float(x.z); v[3] = __uint_as_float(x.w);
-    v[4] = __uint_as_float(y.x); v[5] = __uint_as_float(y.y); v[6] = __uint_as_float(y.z); v[7] = __uint_as_float(y.w);
-  } else {
-    uint4 x = ldg_stream(reinterpret_cast<const unsigned short*>(p) + idx);
-    uint32_t w[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if constexpr (DT == kBF16) {
-        v[2 * t] = __uint_as_float(w[t] << 16);
-        v[2 * t + 1] = __uint_as_float(w[t] & 0xFFFF0000u);
-      } else {
-        __half2 h = *reinterpret_cast<__half2*>(&w[t]);
-        float2 f = __half22float2(h);
-        v[2 * t] = f.x;
-        v[2 * t + 1] = f.y;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ uint32_t pack2(float a, float b, int mode) {
-  if (mode == kModeF16) {
-    __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-  }
-  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<uint32_t*>(&h);
-}
+// ------------------------------------------------------------ smem layouts
 
 // Byte offset of the 16-byte unit holding elements (t, 8kc .. 8kc+7) of a
 // K-major tile: one 128-byte row of 64 k per t, 8-row groups 1024 bytes
@@ -156,6 +88,15 @@ __device__ __forceinline__ uint32_t kmajor_off(int t, int kc) {
 // apart, 64-wide t chunks 8192 bytes apart, units XOR-swizzled by (k mod 8).
 __device__ __forceinline__ uint32_t mnmajor_off(int k, int tu) {
   return (uint32_t)((tu >> 3) * 8192 + (k >> 3) * 1024 + (k & 7) * 128 + (((tu & 7) ^ (k & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b, int mode) {
+  if (mode == kModeF16) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
 }
 
 // Round 8 FP32 sums to the leaf format and store them (hi, and lo for the
@@ -185,232 +126,53 @@ __device__ __forceinline__ void store_unit(uint8_t* hi, uint8_t* lo, uint32_t of
   }
 }
 
-// One load unit in flight: 8 operand values of one term (its coefficient is
-// looked up when it is consumed).
-struct Slot {
-  float v[8];
-};
-
-// 32-byte / 16-byte read-only loads that do not allocate in L1 (operand data
-// is streamed; L1 is left to small reused lookups).
-__device__ __forceinline__ void ldg_v8f(const void* p, float (&v)[8]) {
-  asm volatile("ld.global.nc.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
-               : "l"(p));
-}
-
+// Chunk c of a staged term tile: its 8 values.  The staged tile is the TMA
+// box in row-major order: KC sides [128 t][64 k], MN sides [64 k][128 t].
+// Chunk c covers (t = c / 8, k = 8 (c % 8) ..) for KC and (k = c / 16,
+// t = 8 (c % 16) ..) for MN; either way its 8 values are contiguous at
+// element offset 8 c.
 template <int DT>
-__device__ __forceinline__ void load8_vec(const void* p, int64_t idx, float (&v)[8]) {
+__device__ __forceinline__ void read_chunk(const uint8_t* slot, int c, float (&v)[8]) {
   if constexpr (DT == kF32) {
-    ldg_v8f(reinterpret_cast<const float*>(p) + idx, v);
+    const float4 a = *reinterpret_cast<const float4*>(slot + c * 32);
+    const float4 b = *reinterpret_cast<const float4*>(slot + c * 32 + 16);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
   } else {
-    const uint4 x = ldg_stream(reinterpret_cast<const unsigned short*>(p) + idx);
+    const uint4 x = *reinterpret_cast<const uint4*>(slot + c * 16);
     const uint32_t w[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      if constexpr (DT == kBF16) {
-        v[2 * t] = __uint_as_float(w[t] << 16);
-        v[2 * t + 1] = __uint_as_float(w[t] & 0xFFFF0000u);
-      } else {
-        const __half2 h = *reinterpret_cast<const __half2*>(&w[t]);
-        const float2 f = __half22float2(h);
-        v[2 * t] = f.x;
-        v[2 * t + 1] = f.y;
-      }
+      v[2 * t] = __uint_as_float(w[t] << 16);
+      v[2 * t + 1] = __uint_as_float(w[t] & 0xFFFF0000u);
     }
   }
 }
 
-// Position of chunk c of this thread inside the ROWS x 64 tile.
-// KC (k contiguous): (t = c / 8, k = 8 (c % 8) .. +7), K-major smem layout.
-// MN (t contiguous): (k = c / (ROWS/8), t = 8 (c % (ROWS/8)) .. +7),
-//                    MN-major smem layout.
-template <int ROWS, bool KC>
-__device__ __forceinline__ int64_t chunk_off(int64_t ld, int c) {
-  if constexpr (KC) {
-    return (int64_t)(c >> 3) * ld + (c & 7) * 8;
-  } else {
-    constexpr int TU = ROWS / 8;
-    return (int64_t)(c / TU) * ld + (c % TU) * 8;
-  }
-}
-template <int ROWS, bool KC>
+template <bool KC>
 __device__ __forceinline__ uint32_t chunk_smem(int c) {
   if constexpr (KC) {
     return kmajor_off(c >> 3, c & 7);
   } else {
-    constexpr int TU = ROWS / 8;
-    return mnmajor_off(c / TU, c % TU);
+    return mnmajor_off(c >> 4, c & 15);
   }
 }
 
-// Interior tiles: every term's ROWS x 64 tile lies inside its block and the
-// operand, so every unit is one unconditional vector load.  Loads run
-// kDepth units ahead of the arithmetic in a register ring, so each thread
-// keeps kDepth x 32 bytes in flight; the loop body has no data-dependent
-// branches between a load and its use.
-constexpr int kDepth = 8;
+// ------------------------------------------------------------ TMA / bulk copies
 
-template <int ROWS, int MODE, int DT, bool KC>
-__device__ __forceinline__ void fill_interior(const TileOperand& op, const TermInfo* terms, int nterms, uint8_t* hi,
-                                              uint8_t* lo, int ptid) {
-  const int nch = (ROWS * 8 - ptid + kProdThreads - 1) / kProdThreads;  // chunks of this thread
-  Slot ring[kDepth];
-  int ic = 0, it = 0;  // next unit to issue: chunk (of this thread), term
-  int cc = 0, ct = 0;  // next unit to consume
-  int64_t ioff = chunk_off<ROWS, KC>(op.ld, ptid);
-#pragma unroll
-  for (int s = 0; s < kDepth; ++s) {
-    if (ic < nch) {
-      load8_vec<DT>(op.ptr, terms[it].base + ioff, ring[s].v);
-      if (++it == nterms) {
-        it = 0;
-        if (++ic < nch) ioff = chunk_off<ROWS, KC>(op.ld, ptid + kProdThreads * ic);
-      }
-    }
-  }
-  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int units = nch * nterms;
-#pragma unroll 1
-  for (int base = 0; base < units; base += kDepth) {
-#pragma unroll
-    for (int s = 0; s < kDepth; ++s) {
-      if (cc < nch) {
-        const float coef = terms[ct].coef;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] = fmaf(coef, ring[s].v[j], acc[j]);
-        if (++ct == nterms) {
-          store_unit<MODE>(hi, lo, chunk_smem<ROWS, KC>(ptid + kProdThreads * cc), acc);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc[j] = 0.f;
-          ct = 0;
-          ++cc;
-        }
-      }
-      if (ic < nch) {
-        load8_vec<DT>(op.ptr, terms[it].base + ioff, ring[s].v);
-        if (++it == nterms) {
-          it = 0;
-          if (++ic < nch) ioff = chunk_off<ROWS, KC>(op.ld, ptid + kProdThreads * ic);
-        }
-      }
-    }
-  }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
 }
 
-// Tiles touching a block or operand edge: element-wise loads with the
-// block and operand limits (zero outside), one chunk at a time.
-template <int ROWS, int MODE>
-__device__ __noinline__ void fill_boundary(const TileOperand& op, const TermInfo* terms, int nterms, int64_t t0,
-                                           int64_t k0, uint8_t* hi, uint8_t* lo, int ptid) {
-  for (int c = ptid; c < ROWS * 8; c += kProdThreads) {
-    int tl, kl;
-    uint32_t soff;
-    if (op.kcontig) {
-      tl = c >> 3; kl = (c & 7) * 8; soff = kmajor_off(c >> 3, c & 7);
-    } else {
-      constexpr int TU = ROWS / 8;
-      kl = c / TU; tl = (c % TU) * 8; soff = mnmajor_off(c / TU, c % TU);
-    }
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int t = 0; t < nterms; ++t) {
-      const TermInfo& ti = terms[t];
-      const int64_t tg = t0 + tl, kg = k0 + kl;
-      const int64_t gt = (int64_t)ti.tb * op.bt + tg, gk = (int64_t)ti.kb * op.bk + kg;
-      const int64_t off = op.kcontig ? (int64_t)tl * op.ld + kl : (int64_t)kl * op.ld + tl;
-      for (int j = 0; j < 8; ++j) {
-        const bool ok = op.kcontig ? (tg < op.bt && gt < op.T && kg + j < op.bk && gk + j < op.K)
-                                   : (kg < op.bk && gk < op.K && tg + j < op.bt && gt + j < op.T);
-        if (ok) {
-          const int64_t idx = ti.base + off + j;
-          const float v = op.dtype == kF32 ? load1<kF32>(op.ptr, idx)
-                                           : (op.dtype == kBF16 ? load1<kBF16>(op.ptr, idx) : load1<kF16>(op.ptr, idx));
-          acc[j] = fmaf(ti.coef, v, acc[j]);
-        }
-      }
-    }
-    store_unit<MODE>(hi, lo, soff, acc);
-  }
-}
-
-// Produce one ROWS x 64 operand tile: for each chunk, the sum over the
-// leaf's terms in term (index) order, rounded to the leaf format.
-template <int ROWS, int MODE, int DT, bool KC>
-__device__ __forceinline__ void fill_tile(const TileOperand& op, const TermInfo* terms, int nterms, bool interior,
-                                          int64_t t0, int64_t k0, uint8_t* hi, uint8_t* lo, int ptid) {
-  if (nterms <= 0) return;
-  if (interior) {
-    fill_interior<ROWS, MODE, DT, KC>(op, terms, nterms, hi, lo, ptid);
-  } else {
-    fill_boundary<ROWS, MODE>(op, terms, nterms, t0, k0, hi, lo, ptid);
-  }
-}
-
-// ------------------------------------------------------------ iteration context
-
-struct IterPos {
-  int64_t tm, tn, leaf, kt;
-};
-
-// Phase 1 (global loads into registers) and phase 2 (compute and store) of
-// writing the context of one iteration.  Threads 0-15 own A's terms, 16-31
-// B's terms, 32-33 the term counts.
-struct CtxLoad {
-  int32_t blk, n;
-  float coef;
-};
-
-__device__ __forceinline__ void ctx_load(const GemmArgs& a, const IterPos& p, int ptid, CtxLoad& cl) {
-  const LeafDesc* L = a.leaves + p.leaf;
-  if (ptid < 2 * kMaxTerms) {
-    const int q = ptid % kMaxTerms;
-    const bool side_a = ptid < kMaxTerms;
-    cl.n = __ldg(side_a ? &L->na : &L->nb);
-    cl.blk = __ldg(side_a ? &L->a_blk[q] : &L->b_blk[q]);
-    cl.coef = __ldg(side_a ? &L->a_coef[q] : &L->b_coef[q]);
-  } else if (ptid < 2 * kMaxTerms + 2) {
-    cl.n = __ldg(ptid == 2 * kMaxTerms ? &L->na : &L->nb);
-  }
-}
-
-template <int ROWS>
-__device__ __forceinline__ TermInfo term_info(const TileOperand& op, int32_t blk, float coef, int64_t t0,
-                                              int64_t k0) {
-  TermInfo ti;
-  const int64_t tb = (blk >> op.blk_t_shift) & 0xFFFF, kb = (blk >> op.blk_k_shift) & 0xFFFF;
-  const int64_t gt0 = tb * op.bt + t0, gk0 = kb * op.bk + k0;
-  ti.base = op.kcontig ? gt0 * op.ld + gk0 : gk0 * op.ld + gt0;
-  ti.coef = coef;
-  ti.tb = (int32_t)tb;
-  ti.kb = (int32_t)kb;
-  ti.interior = (op.vec_ok && t0 + ROWS <= op.bt && k0 + BK <= op.bk && gt0 + ROWS <= op.T && gk0 + BK <= op.K) ? 1 : 0;
-  return ti;
-}
-
-template <int BN>
-__device__ __forceinline__ void ctx_store(const GemmArgs& a, const IterPos& p, int ptid, const CtxLoad& cl,
-                                          StageCtx* c) {
-  if (ptid < 2 * kMaxTerms) {
-    // threads 0-31 are warp 0 of the producers: lanes 0-15 A's terms, 16-31 B's
-    const int q = ptid % kMaxTerms;
-    bool interior = true;
-    if (q < cl.n) {
-      const TermInfo ti = ptid < kMaxTerms ? term_info<BM>(a.a, cl.blk, cl.coef, p.tm * BM, p.kt * BK)
-                                           : term_info<BN>(a.b, cl.blk, cl.coef, p.tn * BN, p.kt * BK);
-      interior = ti.interior != 0;
-      if (ptid < kMaxTerms) c->a[q] = ti;
-      else c->b[q] = ti;
-    }
-    const unsigned all = __ballot_sync(0xffffffffu, interior);
-    if (ptid == 0) {
-      c->a_interior = (all & 0x0000FFFFu) == 0x0000FFFFu;
-      c->b_interior = (all & 0xFFFF0000u) == 0xFFFF0000u;
-    }
-  } else if (ptid == 2 * kMaxTerms) {
-    c->na = cl.n;
-  } else if (ptid == 2 * kMaxTerms + 1) {
-    c->nb = cl.n;
-  }
+// 2-D tiled bulk tensor copy global -> shared, completion counted on *bar.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int32_t x, int32_t y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
 // ------------------------------------------------------------ epilogue side
@@ -463,21 +225,23 @@ __device__ __forceinline__ void epi_chunk(const EpilogueArgs& c, const LeafDesc*
 
 // ------------------------------------------------------------ the kernel
 
-template <int BN, int MODE, int DTA, bool KCA, int DTB, bool KCB>
+template <int MODE, int DTA, bool KCA, int DTB, bool KCB>
 __global__ void __launch_bounds__(kThreads, 1) fused_fmm_kernel(const __grid_constant__ GemmArgs args) {
-  using C = Cfg<BN, MODE>;
+  using C = Cfg<MODE>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  StageCtx* ctx = reinterpret_cast<StageCtx*>(smem + C::kStages * C::kStage);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStage + C::kCtx);
+  uint8_t* staging = smem + C::kStages * C::kStage;
+  uint64_t* full = reinterpret_cast<uint64_t*>(staging + C::kStaging);
   uint64_t* empty = full + C::kStages;
-  uint64_t* tfull = empty + C::kStages;
+  uint64_t* sfull = empty + C::kStages;
+  uint64_t* sempty = sfull + C::kSlots;
+  uint64_t* tfull = sempty + C::kSlots;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  SlotInfo* sinfo = reinterpret_cast<SlotInfo*>(drain + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sinfo + C::kSlots);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  volatile int* prod_abort = abort_flag + 1;  // written by producers only
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -485,13 +249,16 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fmm_kernel(const __grid_con
       mbar_init(&full[s], kProdThreads);
       mbar_init(&empty[s], 1);
     }
+    for (int s = 0; s < C::kSlots; ++s) {
+      mbar_init(&sfull[s], 1);
+      mbar_init(&sempty[s], kProdThreads);
+    }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kEpiWarps * 32);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
-    *prod_abort = 0;
     mbar_fence_init();
   }
   if (warp == kMmaWarp) tmem_alloc(tmem_slot, C::kTmemCols);
@@ -500,67 +267,74 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fmm_kernel(const __grid_con
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int64_t ntm = (args.c.bm + BM - 1) / BM;
-  const int64_t ntn = (args.c.bn + BN - 1) / BN;
+  const int64_t ntm = args.a.bt / BM;  // prepared block extents are tile multiples
+  const int64_t ntn = args.b.bt / BN;
   const int64_t ntiles = ntm * ntn;
-  const int64_t KT = (args.kl + BK - 1) / BK;
+  const int64_t KT = args.a.bk / BK;
   const int64_t NL = args.num_leaves;
+  const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  const int64_t iters = my_tiles * NL * KT;
 
   if (warp >= kProdWarp0) {
     // ---------------------------------------------------------- producers
     const int ptid = threadIdx.x - kProdWarp0 * 32;
-    // The terms of each iteration are staged in shared memory one iteration
-    // ahead; all producers pass a named barrier per iteration, so they also
-    // share the decision to stop (prod_abort is read after it).
-    const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
-    const int64_t per_tile = NL * KT;
-    const int64_t iters = my_tiles * per_tile;
-    auto pos = [&](int64_t i) {
-      const int64_t tile = blockIdx.x + (i / per_tile) * gridDim.x, r = i % per_tile;
-      return IterPos{tile / ntn, tile % ntn, r / KT, r % KT};
-    };
-    if (iters > 0) {
-      CtxLoad cl;
-      const IterPos p0 = pos(0);
-      ctx_load(args, p0, ptid, cl);
-      ctx_store<BN>(args, p0, ptid, cl, ctx);
-    }
-    int stage = 0;
-    uint32_t phase = 0;
+    int stage = 0, slot = 0;
+    uint32_t phase = 0, sphase = 0;
     bool ok = true;
-    for (int64_t i = 0; i < iters; ++i) {
-      ok = mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns);
-      if (!ok) *prod_abort = 1;
-      asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory");
-      ok = *prod_abort == 0;
-      if (!ok) break;
-      const IterPos p = pos(i);
-      const StageCtx* cur = ctx + (i & 1);
-      CtxLoad cl;
-      const bool more = i + 1 < iters;
-      IterPos pn{};
-      if (more) {
-        pn = pos(i + 1);
-        ctx_load(args, pn, ptid, cl);
+    for (int64_t i = 0; i < iters && ok; ++i) {
+#pragma unroll 1
+      for (int side = 0; side < 2 && ok; ++side) {
+        float acc[kChunksPerThread][8];
+#pragma unroll
+        for (int q = 0; q < kChunksPerThread; ++q)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[q][j] = 0.f;
+        // add the side's staged term tiles, in term order
+        for (;;) {
+          if (!mbar_wait_bounded(&sfull[slot], sphase, abort_flag, args.timeout_ns)) { ok = false; break; }
+          const SlotInfo info = sinfo[slot];
+          const uint8_t* st = staging + slot * kSlotBytes;
+#pragma unroll
+          for (int q = 0; q < kChunksPerThread; ++q) {
+            const int c = ptid + kProdThreads * q;
+            if (c < kChunks) {
+              float v[8];
+              if (side == 0) read_chunk<DTA>(st, c, v);
+              else read_chunk<DTB>(st, c, v);
+#pragma unroll
+              for (int j = 0; j < 8; ++j) acc[q][j] = fmaf(info.coef, v[j], acc[q][j]);
+            }
+          }
+          mbar_arrive(&sempty[slot]);
+          if (++slot == C::kSlots) { slot = 0; sphase ^= 1u; }
+          if (info.flags & (side == 0 ? kLastA : kLastB)) break;
+        }
+        if (!ok) break;
+        if (side == 0 && !mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + stage * C::kStage;
+        uint8_t* hi = side == 0 ? st : st + C::kSplit * C::kATile;
+        uint8_t* lo = hi + (side == 0 ? C::kATile : C::kBTile);
+#pragma unroll
+        for (int q = 0; q < kChunksPerThread; ++q) {
+          const int c = ptid + kProdThreads * q;
+          if (c < kChunks) {
+            const uint32_t off = side == 0 ? chunk_smem<KCA>(c) : chunk_smem<KCB>(c);
+            store_unit<MODE>(hi, lo, off, acc[q]);
+          }
+        }
       }
-      uint8_t* st = smem + stage * C::kStage;
-      uint8_t* a_hi = st;
-      uint8_t* a_lo = st + C::kATile;
-      uint8_t* b_hi = st + C::kSplit * C::kATile;
-      uint8_t* b_lo = b_hi + C::kBTile;
-      fill_tile<BM, MODE, DTA, KCA>(args.a, cur->a, cur->na, cur->a_interior, p.tm * BM, p.kt * BK, a_hi, a_lo,
-                                    ptid);
-      if (more) ctx_store<BN>(args, pn, ptid, cl, ctx + ((i + 1) & 1));
-      fill_tile<BN, MODE, DTB, KCB>(args.b, cur->b, cur->nb, cur->b_interior, p.tn * BN, p.kt * BK, b_hi, b_lo,
-                                    ptid);
+      if (!ok) break;
       fence_proxy_async_smem();
       mbar_arrive(&full[stage]);
       if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
     }
     if (!ok) *abort_flag = 1;
   } else if (warp == kMmaWarp) {
-    // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
+      // -------------------------------------------------------- MMA issuer
       // K-major operands advance 32 bytes per 16-wide K step inside the
       // swizzled row; MN-major operands advance two 8-k groups (2048 bytes).
       constexpr bool a_mn = !KCA, b_mn = !KCB;
@@ -575,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fmm_kernel(const __grid_con
       uint32_t phase = 0, acc_iter = 0;
       bool ok = true;
       const uint32_t sbase = smem_u32(smem);
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int64_t tile = 0; tile < my_tiles && ok; ++tile) {
         for (int64_t leaf = 0; leaf < NL && ok; ++leaf) {
           const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
           if (!mbar_wait_bounded(&tempty[buf], aph ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
@@ -607,12 +381,58 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fmm_kernel(const __grid_con
         }
       }
       if (!ok) *abort_flag = 1;
-      // All issued MMAs complete before TMEM is released.  MMAs never wait on
-      // anything, so this wait ends within microseconds; it has its own 1 s
-      // cap, independent of the configured wait limit and of the abort flag.
+      // All issued MMAs complete before TMEM is released (own 1 s cap: MMAs
+      // never wait on anything).
       mma_commit(drain);
       const uint64_t t0 = globaltimer_ns();
       while (!mbar_try_wait(drain, 0) && globaltimer_ns() - t0 < 1000000000ull) {
+      }
+    } else if (lane == 1) {
+      // -------------------------------------------------------- TMA issuer
+      int slot = 0;
+      uint32_t sphase = 0;
+      bool ok = true;
+      uint32_t armed = 0, armed_parity = 0;  // per slot: copy issued, parity it completes
+      const int64_t tb_a = args.a.bt, tb_b = args.b.bt, kbx = args.a.bk;
+      for (int64_t i = 0; i < iters && ok; ++i) {
+        const int64_t tile = blockIdx.x + (i / (NL * KT)) * gridDim.x, r = i % (NL * KT);
+        const int64_t leaf = r / KT, kt = r % KT;
+        const int64_t tm = tile / ntn, tn = tile % ntn;
+        const LeafDesc* L = args.leaves + leaf;
+        for (int side = 0; side < 2 && ok; ++side) {
+          const int n = side == 0 ? __ldg(&L->na) : __ldg(&L->nb);
+          const TileOperand& op = side == 0 ? args.a : args.b;
+          const CUtensorMap* map = side == 0 ? &args.map_a : &args.map_b;
+          const uint32_t bytes = (uint32_t)(128 * 64 * (op.dtype == kF32 ? 4 : 2));
+          for (int t = 0; t < n && ok; ++t) {
+            if (!mbar_wait_bounded(&sempty[slot], sphase ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
+            const int32_t blk = side == 0 ? __ldg(&L->a_blk[t]) : __ldg(&L->b_blk[t]);
+            const int64_t tb = (blk >> op.blk_t_shift) & 0xFFFF, kb = (blk >> op.blk_k_shift) & 0xFFFF;
+            const int64_t tpos = tb * (side == 0 ? tb_a : tb_b) + (side == 0 ? tm : tn) * 128;
+            const int64_t kpos = kb * kbx + kt * BK;
+            SlotInfo info;
+            info.coef = side == 0 ? __ldg(&L->a_coef[t]) : __ldg(&L->b_coef[t]);
+            info.flags = (t == n - 1) ? (side == 0 ? kLastA : kLastB) : 0;
+            sinfo[slot] = info;
+            mbar_arrive_expect_tx(&sfull[slot], bytes);
+            // KC operands: x = k, y = t;  MN operands: x = t, y = k
+            if (op.kcontig) tma_load_2d(staging + slot * kSlotBytes, map, (int32_t)kpos, (int32_t)tpos, &sfull[slot]);
+            else tma_load_2d(staging + slot * kSlotBytes, map, (int32_t)tpos, (int32_t)kpos, &sfull[slot]);
+            armed |= 1u << slot;
+            armed_parity = (armed_parity & ~(1u << slot)) | (sphase << slot);
+            if (++slot == C::kSlots) { slot = 0; sphase ^= 1u; }
+          }
+        }
+      }
+      if (!ok) *abort_flag = 1;
+      // No copy may still be writing shared memory when the CTA exits: wait
+      // (1 s cap each) for every issued copy whose slot was not seen free.
+      for (int s = 0; s < C::kSlots; ++s) {
+        if (armed & (1u << s)) {
+          const uint64_t t0 = globaltimer_ns();
+          while (!mbar_try_wait(&sfull[s], (armed_parity >> s) & 1u) && globaltimer_ns() - t0 < 1000000000ull) {
+          }
+        }
       }
     }
     __syncwarp();
@@ -655,10 +475,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fmm_kernel(const __grid_con
 }
 
 // Launch one instantiation: grid = min(tiles, SMs), one CTA per SM.
-template <int BN, int MODE, int DTA, bool KCA, int DTB, bool KCB>
+template <int MODE, int DTA, bool KCA, int DTB, bool KCB>
 cudaError_t launch_cfg(const GemmArgs& a, cudaStream_t st) {
-  using C = Cfg<BN, MODE>;
-  auto kern = fused_fmm_kernel<BN, MODE, DTA, KCA, DTB, KCB>;
+  using C = Cfg<MODE>;
+  auto kern = fused_fmm_kernel<MODE, DTA, KCA, DTB, KCB>;
   static bool attr_set[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -668,27 +488,31 @@ cudaError_t launch_cfg(const GemmArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  const int64_t ntiles = ((a.c.bm + BM - 1) / BM) * ((a.c.bn + BN - 1) / BN);
+  const int64_t ntiles = (a.a.bt / BM) * (a.b.bt / BN);
   const int64_t grid = std::min<int64_t>(ntiles, device_sm_count());
   kern<<<(unsigned)grid, kThreads, C::kSmem, st>>>(a);
   return cudaGetLastError();
 }
 
 // The operand (dtype, layout) pairs the forward and backward passes use:
-// forward A (in, k-contiguous) x B (in, n-contiguous); dA = dC B^T with
-// dC (fp32, k-contiguous) x B^T (in, k-contiguous); dB = A^T dC with
-// A^T (in, m-contiguous) x dC (fp32, n-contiguous); in = fp32 or bf16.
+// forward A (k-contiguous) x B (n-contiguous); dA = dC B^T with both
+// operands k-contiguous; dB = A^T dC with both operands t-contiguous.
+// Element types fp32 or bf16 (each side independently).
 template <int MODE>
 cudaError_t launch_mode(const GemmArgs& a, cudaStream_t st) {
-  constexpr int BN = 256;
   const int da = a.a.dtype, db = a.b.dtype;
   const bool ka = a.a.kcontig != 0, kb = a.b.kcontig != 0;
-  if (ka && !kb && da == kF32 && db == kF32) return launch_cfg<BN, MODE, kF32, true, kF32, false>(a, st);
-  if (ka && !kb && da == kBF16 && db == kBF16) return launch_cfg<BN, MODE, kBF16, true, kBF16, false>(a, st);
-  if (ka && kb && da == kF32 && db == kF32) return launch_cfg<BN, MODE, kF32, true, kF32, true>(a, st);
-  if (ka && kb && da == kF32 && db == kBF16) return launch_cfg<BN, MODE, kF32, true, kBF16, true>(a, st);
-  if (!ka && !kb && da == kF32 && db == kF32) return launch_cfg<BN, MODE, kF32, false, kF32, false>(a, st);
-  if (!ka && !kb && da == kBF16 && db == kF32) return launch_cfg<BN, MODE, kBF16, false, kF32, false>(a, st);
+#define FMM_LAUNCH(KA, KB)                                                                            \
+  if (ka == KA && kb == KB) {                                                                         \
+    if (da == kF32 && db == kF32) return launch_cfg<MODE, kF32, KA, kF32, KB>(a, st);                 \
+    if (da == kBF16 && db == kBF16) return launch_cfg<MODE, kBF16, KA, kBF16, KB>(a, st);             \
+    if (da == kF32 && db == kBF16) return launch_cfg<MODE, kF32, KA, kBF16, KB>(a, st);               \
+    if (da == kBF16 && db == kF32) return launch_cfg<MODE, kBF16, KA, kF32, KB>(a, st);               \
+  }
+  FMM_LAUNCH(true, false)
+  FMM_LAUNCH(true, true)
+  FMM_LAUNCH(false, false)
+#undef FMM_LAUNCH
   return cudaErrorNotSupported;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "plan.h"
@@ -17,46 +18,54 @@ cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
                            int* out, int* status, cudaStream_t st);
 cudaError_t launch_zero_sentinel(int* p, int64_t n, cudaStream_t st);
 cudaError_t launch_fill(int* p, int64_t n, int v, cudaStream_t st);
-// Y = 2^(rs re_i + cs ce_k) X (exact), Y in fp32 (bf16 when X is bf16).
-cudaError_t launch_apply_exp(const void* X, int dt, int64_t R, int64_t C, int64_t ld, const int* re, int rs,
-                             const int* ce, int cs, void* Y, int64_t ldy, cudaStream_t st);
+
 
 // One operand of the fused multiply as the kernel sees it: a tile has
-// "t" rows (the M side for A, the N side for B) and "k" columns.  Element
-// (t, k) of the logical operand is at ptr[t*ld + k] when kcontig, else at
-// ptr[k*ld + t].
+// "t" rows (the M side for A, the N side for B) and "k" columns.  The
+// operand is "prepared": every leaf block (bt x bk, tile multiples) starts at
+// element (tb*bt, kb*bk) of the tensor map's (t, k) grid, and everything
+// outside the logical matrix inside a block is zero.  kcontig: k is the
+// contiguous index of the tensor (TMA x = k, y = t); else t is (x = t, y = k).
 struct TileOperand {
   const void* ptr;
   int64_t ld;
-  int dtype;     // kF32 / kBF16 / kF16
-  int kcontig;   // 1: k is the contiguous index
-  int vec_ok;    // 16-byte vector loads allowed along the contiguous index
-  int64_t T, K;  // logical extents
-  int64_t bt, bk;  // leaf block extents along t and k
-  int blk_t_shift;  // term block packing: t block = (blk >> blk_t_shift) & 0xFFFF
-  int blk_k_shift;  //                      k block = (blk >> blk_k_shift) & 0xFFFF
+  int dtype;       // kF32 / kBF16
+  int kcontig;
+  int64_t bt, bk;  // prepared block extents (multiples of 128 and 64)
+  int blk_t_shift; // term block packing: t block = (blk >> blk_t_shift) & 0xFFFF
+  int blk_k_shift; //                      k block = (blk >> blk_k_shift) & 0xFFFF
 };
 
 struct EpilogueArgs {
   float* C;
   int64_t ldc;
   int64_t M, N;
-  int64_t bm, bn;  // leaf block extents
+  int64_t bm, bn;  // logical leaf block extents
   const int* eA;   // C scale 2^(eA_i + eB_j), nullable
   const int* eB;
   int vec_ok;
 };
 
 struct GemmArgs {
+  alignas(64) CUtensorMap map_a;
+  alignas(64) CUtensorMap map_b;
   TileOperand a, b;
   EpilogueArgs c;
   const LeafDesc* leaves;
   int64_t num_leaves;
-  int64_t kl;          // leaf K extent
-  int64_t pm, pk, pn;  // leaf block grid (products of m0, k0, n0)
   int* status;
   uint64_t timeout_ns;
 };
+
+// Prepare one operand: Y (R' x C', leading dimension ldy) = the blocked,
+// zero-padded, power-of-two-scaled copy of X (R x C, ld): output row r'
+// = rb * row_pad + r takes source row rb * row_blk + r when r < row_blk,
+// columns likewise; entries outside the source are 0; each value is
+// multiplied by 2^(rs re[row] + cs ce[col]) (exact).  Y is fp32, or bf16
+// when X is bf16.
+cudaError_t launch_prepare(const void* X, int dt, int64_t R, int64_t C, int64_t ld, int64_t row_blk,
+                           int64_t row_pad, int64_t col_blk, int64_t col_pad, const int* re, int rs, const int* ce,
+                           int cs, void* Y, int64_t Rp, int64_t Cp, int64_t ldy, cudaStream_t st);
 
 // Launch the fused recursive-fast-multiply kernel for a flattened plan.
 cudaError_t launch_fused_gemm(const GemmArgs& args, int leaf_format, cudaStream_t st);

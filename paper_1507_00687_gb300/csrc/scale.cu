@@ -143,74 +143,49 @@ __device__ __forceinline__ float scale_pow2(float x, int e) {
   return (x * exp2i(h)) * exp2i(e - h);
 }
 
-// Apply pass of Algs. 1-3: Y[i, k] = 2^(rs re_i + cs ce_k) X[i, k] for an
-// R x C matrix, written in the output type (fp32, or bf16 for bf16 input,
-// where a power-of-two scaling of a bf16 value is again a bf16 value).  One
-// HBM-bound pass: each thread moves 4 consecutive elements of one row.
+// Operand preparation (the apply pass of Algs. 1-3, plus blocking): each
+// thread writes 4 consecutive output columns of one output row (row_pad and
+// col_pad are multiples of 4, so a group never straddles two blocks), reading
+// the matching source elements (zero outside the source) and scaling them by
+// 2^(rs re[row] + cs ce[col]).  One HBM-bound pass.
 template <int DT, bool OUT_BF16>
-__global__ void __launch_bounds__(256) apply_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
-                                                        const int* re, int rs, const int* ce, int cs, void* Y,
-                                                        int64_t ldy, int vec_ok) {
-  const int64_t C4 = (C + 3) / 4;
-  const int64_t total = R * C4;
+__global__ void __launch_bounds__(256) prepare_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
+                                                      int64_t row_blk, int64_t row_pad, int64_t col_blk,
+                                                      int64_t col_pad, const int* re, int rs, const int* ce, int cs,
+                                                      void* Y, int64_t Rp, int64_t Cp, int64_t ldy) {
+  const int64_t C4 = Cp / 4;
+  const int64_t total = Rp * C4;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / C4, c0 = (idx % C4) * 4;
-    const int er = re ? rs * __ldg(re + i) : 0;
-    float x[4];
-    int ec[4] = {0, 0, 0, 0};
-    const bool full = vec_ok && c0 + 4 <= C;
-    if (full) {
-      if constexpr (DT == kF32) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + i * ld + c0));
-        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-      } else {
-        const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const unsigned short*>(X) + i * ld + c0));
-        const uint32_t h[4] = {v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16};
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          x[t] = DT == kBF16 ? __uint_as_float(h[t] << 16) : __half2float(__ushort_as_half((unsigned short)h[t]));
-      }
-      if (ce) {
-        const int4 e = __ldg(reinterpret_cast<const int4*>(ce + c0));
-        ec[0] = e.x; ec[1] = e.y; ec[2] = e.z; ec[3] = e.w;
-      }
-    } else {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int64_t c = c0 + t;
-        if (c < C) {
-          if constexpr (DT == kF32) x[t] = __ldg(reinterpret_cast<const float*>(X) + i * ld + c);
-          else if constexpr (DT == kBF16)
-            x[t] = __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(X) + i * ld + c) << 16);
-          else x[t] = __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(X) + i * ld + c)));
-          if (ce) ec[t] = __ldg(ce + c);
-        } else {
-          x[t] = 0.f;
-        }
-      }
-    }
+    const int64_t rp = idx / C4, cp0 = (idx % C4) * 4;
+    const int64_t rb = rp / row_pad, rr = rp % row_pad;
+    const int64_t src_r = rb * row_blk + rr;
+    const bool row_ok = rr < row_blk && src_r < R;
+    const int er = (row_ok && re) ? rs * __ldg(re + src_r) : 0;
     float y[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) y[t] = scale_pow2(x[t], er + cs * ec[t]);
+    for (int t = 0; t < 4; ++t) {
+      const int64_t cp = cp0 + t, cb = cp / col_pad, cc = cp % col_pad;
+      const int64_t src_c = cb * col_blk + cc;
+      float x = 0.f;
+      if (row_ok && cc < col_blk && src_c < C) {
+        const int64_t i = src_r * ld + src_c;
+        if constexpr (DT == kF32) x = __ldg(reinterpret_cast<const float*>(X) + i);
+        else if constexpr (DT == kBF16)
+          x = __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(X) + i) << 16);
+        else x = __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(X) + i)));
+        x = scale_pow2(x, er + (ce ? cs * __ldg(ce + src_c) : 0));
+      }
+      y[t] = x;
+    }
     if constexpr (OUT_BF16) {
-      unsigned short* out = reinterpret_cast<unsigned short*>(Y) + i * ldy + c0;
       // exact: a power-of-two multiple of a bf16 value in range is a bf16 value
       const uint32_t b0 = __float_as_uint(y[0]) >> 16, b1 = __float_as_uint(y[1]) >> 16;
       const uint32_t b2 = __float_as_uint(y[2]) >> 16, b3 = __float_as_uint(y[3]) >> 16;
-      if (full) {
-        *reinterpret_cast<uint2*>(out) = make_uint2(b0 | (b1 << 16), b2 | (b3 << 16));
-      } else {
-        const uint32_t b[4] = {b0, b1, b2, b3};
-        for (int t = 0; t < 4 && c0 + t < C; ++t) out[t] = (unsigned short)b[t];
-      }
+      *reinterpret_cast<uint2*>(reinterpret_cast<unsigned short*>(Y) + rp * ldy + cp0) =
+          make_uint2(b0 | (b1 << 16), b2 | (b3 << 16));
     } else {
-      float* out = reinterpret_cast<float*>(Y) + i * ldy + c0;
-      if (full) {
-        *reinterpret_cast<float4*>(out) = make_float4(y[0], y[1], y[2], y[3]);
-      } else {
-        for (int t = 0; t < 4 && c0 + t < C; ++t) out[t] = y[t];
-      }
+      *reinterpret_cast<float4*>(reinterpret_cast<float*>(Y) + rp * ldy + cp0) = make_float4(y[0], y[1], y[2], y[3]);
     }
   }
 }
@@ -285,25 +260,24 @@ cudaError_t launch_zero_sentinel(int* p, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply_exp(const void* X, int dt, int64_t R, int64_t C, int64_t ld, const int* re, int rs,
-                             const int* ce, int cs, void* Y, int64_t ldy, cudaStream_t st) {
-  if (R == 0 || C == 0) return cudaSuccess;
-  const bool out_bf16 = dt == kBF16;
-  const int vec = vec_aligned(X, ld, dt) && ((uintptr_t)Y % 16 == 0) && (ldy % 4 == 0) &&
-                          ((uintptr_t)ce % 16 == 0)
-                      ? 1
-                      : 0;
-  const int64_t total = R * ((C + 3) / 4);
+cudaError_t launch_prepare(const void* X, int dt, int64_t R, int64_t C, int64_t ld, int64_t row_blk,
+                           int64_t row_pad, int64_t col_blk, int64_t col_pad, const int* re, int rs, const int* ce,
+                           int cs, void* Y, int64_t Rp, int64_t Cp, int64_t ldy, cudaStream_t st) {
+  if (Rp == 0 || Cp == 0) return cudaSuccess;
+  const int64_t total = Rp * (Cp / 4);
   const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
   switch (dt) {
     case kF32:
-      apply_exp_kernel<kF32, false><<<grid, 256, 0, st>>>(X, R, C, ld, re, rs, ce, cs, Y, ldy, vec);
+      prepare_kernel<kF32, false><<<grid, 256, 0, st>>>(X, R, C, ld, row_blk, row_pad, col_blk, col_pad, re, rs, ce,
+                                                         cs, Y, Rp, Cp, ldy);
       break;
     case kBF16:
-      apply_exp_kernel<kBF16, true><<<grid, 256, 0, st>>>(X, R, C, ld, re, rs, ce, cs, Y, ldy, vec);
+      prepare_kernel<kBF16, true><<<grid, 256, 0, st>>>(X, R, C, ld, row_blk, row_pad, col_blk, col_pad, re, rs, ce,
+                                                         cs, Y, Rp, Cp, ldy);
       break;
     default:
-      apply_exp_kernel<kF16, false><<<grid, 256, 0, st>>>(X, R, C, ld, re, rs, ce, cs, Y, ldy, vec);
+      prepare_kernel<kF16, false><<<grid, 256, 0, st>>>(X, R, C, ld, row_blk, row_pad, col_blk, col_pad, re, rs, ce,
+                                                         cs, Y, Rp, Cp, ldy);
       break;
   }
   return cudaGetLastError();

@@ -107,6 +107,29 @@ def test_multiply_integer_inputs_bit_exact(api, names, M, K, N):
         assert np.array_equal(dev_values(got), want), (dt, leaf)
 
 
+# Shapes whose tiling is exact take the streaming producers (every tile
+# interior); the last one has more tiles than SMs, so CTAs loop over tiles.
+STREAM_CASES = [(["strassen"], 512, 256, 1024), (["winograd", "winograd"], 512, 256, 1024),
+                (["strassen", "classical121"], 256, 256, 512), ([], 4096, 128, 4096),
+                (["winograd"], 2048, 384, 1024)]
+
+
+@pytest.mark.parametrize("names,M,K,N", STREAM_CASES, ids=lambda x: "-".join(x) if isinstance(x, list) else str(x))
+def test_streaming_path_integer_exact_and_uniform(api, names, M, K, N):
+    A = inputs.integers((M, K), -4, 4, seed=M + 3)
+    B = inputs.integers((K, N), -4, 4, seed=N + 4)
+    for dt, leaf in (("f32", "bf16x3"), ("bf16", "bf16"), ("f32", "fp16")):
+        got = api.multiply(api.Plan(names, leaf), to_dev(A, dt), to_dev(B, dt))
+        api.sync_status()
+        assert np.array_equal(dev_values(got), A @ B), (dt, leaf)
+    Ar = inputs.uniform((M, K), -1, 1, seed=7)
+    Br = inputs.uniform((K, N), -1, 1, seed=8)
+    Ad, Bd = to_dev(Ar, "f32"), to_dev(Br, "f32")
+    got = dev_values(api.multiply(api.Plan(names, "bf16x3"), Ad, Bd))
+    C, G = oracle_reference(dev_values(Ad), dev_values(Bd), names)
+    assert_within(got, C, G, names, K, "bf16x3", "streaming")
+
+
 def test_multiply_leading_dims_and_k_zero(api):
     A = inputs.integers((70, 90), -3, 3, seed=1)
     B = inputs.integers((90, 50), -3, 3, seed=2)
