@@ -184,6 +184,43 @@ fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void*
                         const int32_t* eA, const int32_t* d, const int32_t* eB, void* ws,
                         size_t ws_bytes, void* stream);
 
+/* Size of the static scratch array fmm_multiply_noalloc works in. */
+#define FMM_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/*
+ * fmm_multiply without a caller-supplied workspace and without allocating
+ * anything.  The paper has no counterpart: this is a library convenience.
+ *
+ * Who needs it: code that must not call cudaMalloc (or any allocator) on
+ * the device -- for instance a caller running under a memory pool or arena
+ * that owns all device memory, a plugin inside a host framework that does
+ * not hand out scratch buffers, or code on a latency-critical path where an
+ * allocation could synchronise the device.  Such a caller passes only its
+ * inputs and output; the scratch (the plan's leaf table and the prepared
+ * operand copies described under fmm_workspace_size) lives in one array of
+ * FMM_NOALLOC_SCRATCH_BYTES bytes that the library declares in device
+ * memory.  Every GPU that loads the library holds that array until the
+ * process exits.
+ *
+ * Arguments, layouts and results are those of fmm_multiply.  Returns
+ * FMM_ERR_WORKSPACE, before touching the device, when the leaf table plus
+ * the prepared operands (fp32 upper bound, as fmm_workspace_size counts
+ * them for the forward product) would exceed FMM_NOALLOC_SCRATCH_BYTES;
+ * fmm_last_error() then says how many bytes the problem needs.
+ *
+ * The first call on a device looks up the array's device address (once
+ * per device); make that first call before any stream capture begins.
+ * Nothing in the array needs to start at zero: each call copies the leaf
+ * table in and rewrites every prepared element (padding included) before
+ * the multiply kernel reads it.  All calls share the one array, so calls
+ * whose work overlaps on the GPU (different streams, or threads without
+ * ordering) race on it and give wrong results; order them on one stream.
+ */
+fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, const void* B,
+                                int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t K,
+                                int64_t N, int in_dtype, const int32_t* eA, const int32_t* d,
+                                const int32_t* eB, void* stream);
+
 /*
  * Gradients of C = A B for a given dC (M x N, float32, lddc):
  *   dA = dC B^T (M x K, float32, ldda),  dB = A^T dC (K x N, float32, lddb),
@@ -209,8 +246,9 @@ fmm_status fmm_sync_status(void* stream);
 
 /*
  * Text of the last CUDA runtime error a library call on this host thread
- * met (empty when none); the pointer stays valid until the next library
- * call on the thread.
+ * met, or of the last size rejection by fmm_multiply_noalloc (empty when
+ * none); the pointer stays valid until the next library call on the
+ * thread.
  */
 const char* fmm_last_error(void);
 

@@ -25,8 +25,11 @@ LEAF_BF16, LEAF_F16, LEAF_BF16X3 = 0, 1, 2
 EXPORTS = [
     "fmm_plan", "fmm_plan_destroy", "fmm_plan_info", "fmm_plan_bound", "fmm_scale_outside",
     "fmm_scale_inside", "fmm_scale", "fmm_workspace_size", "fmm_multiply", "fmm_multiply_backward",
-    "fmm_sync_status", "fmm_status_string", "fmm_version", "fmm_last_error",
+    "fmm_sync_status", "fmm_status_string", "fmm_version", "fmm_last_error", "fmm_multiply_noalloc",
 ]
+
+# Bytes of the library's static scratch array (FMM_NOALLOC_SCRATCH_BYTES).
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class FmmRule(C.Structure):
@@ -65,6 +68,7 @@ def lib():
     L.fmm_workspace_size.argtypes = [vp, i64, i64, i64, C.POINTER(C.c_size_t)]
     L.fmm_multiply.argtypes = [vp, vp, i64, vp, i64, vp, i64, i64, i64, i64, C.c_int, vp, vp, vp, vp,
                                C.c_size_t, vp]
+    L.fmm_multiply_noalloc.argtypes = [vp, vp, i64, vp, i64, vp, i64, i64, i64, i64, C.c_int, vp, vp, vp, vp]
     L.fmm_multiply_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, i64, i64, i64,
                                         C.c_int, vp, C.c_size_t, vp]
     L.fmm_sync_status.argtypes = [vp]

@@ -206,10 +206,12 @@ static fmm_status prepare(const Source& s, int blk_t_shift, int blk_k_shift, cha
 }
 
 // Run the flattened plan p: C (M x N) = X (M x K) Y (K x N) with X, Y given
-// as sources (X: t = M, k = K; Y: t = N, k = K).
+// as sources (X: t = M, k = K; Y: t = N, k = K).  leaves: a device copy of
+// the plan's leaf table to use instead of the plan's own upload (NULL: the
+// plan's own, uploaded on first use).
 static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, float* C, int64_t ldc, int64_t M,
                            int64_t K, int64_t N, const int* eA, const int* eB, void* ws, size_t ws_bytes,
-                           cudaStream_t st) {
+                           cudaStream_t st, const LeafDesc* leaves = nullptr) {
   if (M == 0 || N == 0) return FMM_OK;
   if (K == 0) {
     return cuda_ok(cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)N * 4, (size_t)M, st), "memset")
@@ -218,7 +220,10 @@ static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, floa
   }
   int* status = status_ptr();
   if (!status) return FMM_ERR_CUDA;
-  if (ensure_uploaded(p) != FMM_OK) return FMM_ERR_CUDA;
+  if (!leaves) {
+    if (ensure_uploaded(p) != FMM_OK) return FMM_ERR_CUDA;
+    leaves = p->dev;
+  }
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
   char* w = static_cast<char*>(ws);
@@ -237,7 +242,7 @@ static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, floa
   g.c.eA = eA;
   g.c.eB = eB;
   g.c.vec_ok = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0) && (g.c.bn % 4 == 0) ? 1 : 0;
-  g.leaves = p->dev;
+  g.leaves = leaves;
   g.num_leaves = p->leaves;
   g.status = status;
   g.timeout_ns = timeout_ns();
@@ -252,6 +257,32 @@ static size_t ws_bytes_for(const Plan* p, int64_t M, int64_t K, int64_t N) {
   const int64_t da = prepared_bytes(M, N, p->pm, p->pn) + prepared_bytes(K, N, p->pk, p->pn);
   const int64_t db = prepared_bytes(K, M, p->pk, p->pm) + prepared_bytes(N, M, p->pn, p->pm);
   return (size_t)std::max(fwd, std::max(da, db));
+}
+
+// ---------------------------------------------------------------- no-alloc scratch
+
+// Scratch of fmm_multiply_noalloc: the leaf table, then the prepared operand
+// copies.  A file-scope device array, so that callers that may not allocate
+// device memory still get a workspace; every device that loads the library
+// holds it until exit.  In host code this name is only a stand-in for the
+// array; its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FMM_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the first fmm_multiply_noalloc call there).
+static char* noalloc_scratch() {
+  static char* cache[64] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice") || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev]) {
+    void* ptr = nullptr;
+    if (!cuda_ok(cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "cudaGetSymbolAddress(no-alloc scratch)"))
+      return nullptr;
+    cache[dev] = static_cast<char*>(ptr);
+  }
+  return cache[dev];
 }
 
 }  // namespace fmm
@@ -388,6 +419,41 @@ fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void*
   const Source a{A, lda, in_dtype, true, M, K, p->pm, p->pk, eA, -1, d, +1};
   const Source b{B, ldb, in_dtype, false, N, K, p->pn, p->pk, d, -1, eB, -1};
   return run_plan(p, a, b, C, ldc, M, K, N, eA, eB, ws, ws_bytes, as_stream(stream));
+}
+
+fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, const void* B, int64_t ldb,
+                                float* C, int64_t ldc, int64_t M, int64_t K, int64_t N, int in_dtype,
+                                const int32_t* eA, const int32_t* d, const int32_t* eB, void* stream) {
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  if (!p || !valid_dtype(in_dtype) || M < 0 || K < 0 || N < 0) return FMM_ERR_ARG;
+  if (M > 0 && N > 0 && !C) return FMM_ERR_ARG;
+  if ((M > 0 && K > 0 && !A) || (K > 0 && N > 0 && !B)) return FMM_ERR_ARG;
+  if ((M > 0 && K > 0 && lda < K) || (K > 0 && N > 0 && ldb < N) || (M > 0 && N > 0 && ldc < N))
+    return FMM_ERR_SHAPE;
+  if (in_dtype == FMM_DT_F16 && p->leaf_format == FMM_LEAF_BF16X3) return FMM_ERR_DTYPE;
+  if (ceil_div(M, p->pm) >= (1ll << 30) || ceil_div(N, p->pn) >= (1ll << 30) || ceil_div(K, p->pk) >= (1ll << 30))
+    return FMM_ERR_SHAPE;
+  if (M == 0 || N == 0) return FMM_OK;
+  // The size check comes before any device call.
+  const size_t table_bytes = p->host.size() * sizeof(LeafDesc);
+  const size_t table = (size_t)round_up((int64_t)table_bytes, 256);
+  const size_t need = table + (size_t)prepared_bytes(M, K, p->pm, p->pk) + (size_t)prepared_bytes(N, K, p->pn, p->pk);
+  if (need > FMM_NOALLOC_SCRATCH_BYTES) {
+    t_last_error = "fmm_multiply_noalloc: this problem needs " + std::to_string(need) +
+                   " bytes of scratch; the static scratch holds " + std::to_string(FMM_NOALLOC_SCRATCH_BYTES);
+    return FMM_ERR_WORKSPACE;
+  }
+  char* scratch = noalloc_scratch();
+  if (!scratch) return FMM_ERR_CUDA;
+  cudaStream_t st = as_stream(stream);
+  if (!cuda_ok(cudaMemcpyAsync(scratch, p->host.data(), table_bytes, cudaMemcpyHostToDevice, st),
+               "leaf table copy into the no-alloc scratch"))
+    return FMM_ERR_CUDA;
+  // Operands as in fmm_multiply.
+  const Source a{A, lda, in_dtype, true, M, K, p->pm, p->pk, eA, -1, d, +1};
+  const Source b{B, ldb, in_dtype, false, N, K, p->pn, p->pk, d, -1, eB, -1};
+  return run_plan(p, a, b, C, ldc, M, K, N, eA, eB, scratch + table, FMM_NOALLOC_SCRATCH_BYTES - table, st,
+                  reinterpret_cast<const LeafDesc*>(scratch));
 }
 
 fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc, const void* A, int64_t lda,
