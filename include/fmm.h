@@ -156,6 +156,30 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
                      int32_t* eB, void* stream);
 
 /*
+ * Where a multiply forms the operand combinations S_r = sum u A_i and
+ * T_r = sum v B_j of Eq. 4.4 (the products and the output combination are
+ * the same in both; so are the sums, in FP32 in index order, and their
+ * rounding to the leaf format, hence the results):
+ *   FMM_SCHEDULE_LOAD_STAGE  in the load stage of the multiply kernel: the
+ *     term tiles are staged in shared memory and summed by producer warps
+ *     into the tensor-core operand tiles; workspace only for prepared
+ *     operand copies;
+ *   FMM_SCHEDULE_PASS        by a bandwidth-bound combination pass that
+ *     writes every S_r and T_r once, in the leaf format, into the workspace
+ *     (R^L leaf blocks per operand, two planes for the hi+lo split); the
+ *     multiply kernel then streams them with bulk tensor copies;
+ *   FMM_SCHEDULE_AUTO        (default) the pass schedule when the given
+ *     workspace holds it, else the load-stage schedule.
+ */
+#define FMM_SCHEDULE_AUTO 0
+#define FMM_SCHEDULE_LOAD_STAGE 1
+#define FMM_SCHEDULE_PASS 2
+
+/* Set the plan's schedule (FMM_SCHEDULE_*); FMM_ERR_ARG for other values.
+ * The gradient products of fmm_multiply_backward follow it. */
+fmm_status fmm_plan_set_schedule(fmm_plan_t plan, int schedule);
+
+/*
  * Workspace bytes fmm_multiply / fmm_multiply_backward need for this plan
  * and shape (an upper bound over input types).  The fused kernel reads its
  * operands through tensor-memory-access copies of whole 128 x 64 tiles; an
@@ -163,6 +187,8 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
  * aligned, that is scaled (exponent vectors given) or fp16 is first written,
  * by one bandwidth-bound pass, as a blocked, zero-padded, scaled copy into
  * the workspace.  Calls whose operands need no copy may pass NULL / 0.
+ * Under the AUTO and PASS schedules the size also covers the combined
+ * operands of the pass schedule (see fmm_plan_set_schedule).
  */
 fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t M, int64_t K, int64_t N, size_t* bytes);
 

@@ -20,12 +20,14 @@ STATUS_NAMES = {
 ORDER_ROW, ORDER_COL = 0, 1
 DT_F32, DT_BF16, DT_F16 = 0, 1, 2
 LEAF_BF16, LEAF_F16, LEAF_BF16X3 = 0, 1, 2
+SCHEDULE_AUTO, SCHEDULE_LOAD_STAGE, SCHEDULE_PASS = 0, 1, 2
 
 # Every symbol include/fmm.h declares.
 EXPORTS = [
     "fmm_plan", "fmm_plan_destroy", "fmm_plan_info", "fmm_plan_bound", "fmm_scale_outside",
     "fmm_scale_inside", "fmm_scale", "fmm_workspace_size", "fmm_multiply", "fmm_multiply_backward",
     "fmm_sync_status", "fmm_status_string", "fmm_version", "fmm_last_error", "fmm_multiply_noalloc",
+    "fmm_plan_set_schedule",
 ]
 
 # Bytes of the library's static scratch array (FMM_NOALLOC_SCRATCH_BYTES).
@@ -59,6 +61,7 @@ def lib():
     i64, i32p, vp, st = C.c_int64, C.POINTER(C.c_int32), C.c_void_p, C.c_int
     L.fmm_plan.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(FmmRule), C.c_int]
     L.fmm_plan_destroy.argtypes = [vp]
+    L.fmm_plan_set_schedule.argtypes = [vp, C.c_int]
     L.fmm_plan_info.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i64),
                                 C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     L.fmm_plan_bound.argtypes = [vp, i64, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]

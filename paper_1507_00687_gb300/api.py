@@ -12,6 +12,7 @@ from . import _native as N
 from .rules import BaseRule, get as get_rule
 
 LEAF = {"bf16": N.LEAF_BF16, "fp16": N.LEAF_F16, "bf16x3": N.LEAF_BF16X3}
+SCHEDULE = {"auto": N.SCHEDULE_AUTO, "load_stage": N.SCHEDULE_LOAD_STAGE, "pass": N.SCHEDULE_PASS}
 DTYPE = {torch.float32: N.DT_F32, torch.bfloat16: N.DT_BF16, torch.float16: N.DT_F16}
 
 
@@ -36,9 +37,12 @@ def _rowmajor(t: torch.Tensor, name: str) -> int:
 
 class Plan:
     """A flattened uniform non-stationary plan (fmm_plan): ``rules[l]`` at
-    level l+1, classical leaves, leaf products in ``leaf`` format."""
+    level l+1, classical leaves, leaf products in ``leaf`` format.
+    ``schedule`` (fmm_plan_set_schedule): "auto", "load_stage" (S_r, T_r
+    formed in the multiply kernel's load stage) or "pass" (formed by a
+    combination pass into the workspace)."""
 
-    def __init__(self, rules: Sequence[Union[str, BaseRule]], leaf: str = "bf16x3"):
+    def __init__(self, rules: Sequence[Union[str, BaseRule]], leaf: str = "bf16x3", schedule: str = "auto"):
         self.rules = [get_rule(r) if isinstance(r, str) else r for r in rules]
         self.leaf = leaf
         self._keep = []
@@ -54,6 +58,8 @@ class Plan:
         h = C.c_void_p()
         N.check(N.lib().fmm_plan(C.byref(h), len(self.rules), arr, LEAF[leaf]), "fmm_plan")
         self._h = h
+        self.schedule = schedule
+        N.check(N.lib().fmm_plan_set_schedule(h, SCHEDULE[schedule]), "fmm_plan_set_schedule")
 
     @property
     def handle(self):

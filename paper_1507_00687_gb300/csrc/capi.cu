@@ -136,6 +136,30 @@ static bool make_map(CUtensorMap* m, const void* ptr, int dt, int64_t rows, int6
   return true;
 }
 
+// A 2-D tensor map over a row-major 16-bit matrix (rows x cols, ld) with a
+// box of 64 columns (128 bytes) x box_rows rows, landing in shared memory in
+// the 128-byte-swizzle layout the K-major MMA descriptors read.
+static bool make_map_sw128(CUtensorMap* m, const void* ptr, bool f16, int64_t rows, int64_t cols, int64_t ld,
+                           int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    t_last_error = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    t_last_error = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------- operands
 
 // One operand of a fast product as stored by the caller: a row-major memory
@@ -205,6 +229,103 @@ static fmm_status prepare(const Source& s, int blk_t_shift, int blk_k_shift, cha
   return FMM_OK;
 }
 
+// ---------------------------------------------------------------- pass schedule
+
+// Tile width along N of the pass-schedule multiply for a leaf block of bt_b
+// columns: 256 (fewer operand bytes per flop) unless the block is narrower.
+// FMM_TILE_N=128 or 256 overrides it (tuning).
+static int pass_tile_n(int64_t bt_b) {
+  static int forced = [] {
+    const char* s = std::getenv("FMM_TILE_N");
+    const int v = s ? std::atoi(s) : 0;
+    return (v == 128 || v == 256) ? v : 0;
+  }();
+  if (forced) return forced;
+  return bt_b >= 256 ? 256 : 128;
+}
+
+// Bytes of one side's combined operands: planes x R leaf blocks of
+// round_up(bt, tile) x round_up(bk, 64) 16-bit elements.
+static int64_t combined_bytes(int64_t T, int64_t Kd, int64_t pt, int64_t pk, int64_t leaves, int planes,
+                              int64_t tile) {
+  return round_up(planes * leaves * round_up(ceil_div(T, pt), tile) * round_up(ceil_div(Kd, pk), 64) * 2, 256);
+}
+
+// Workspace of the pass schedule for the product X (T_x x Kd) Y (Kd x T_y)
+// (upper bound over the tile width).
+static int64_t pass_bytes(const Plan* p, int64_t Tx, int64_t Kd, int64_t Ty, int64_t ptx, int64_t pk,
+                          int64_t pty) {
+  const int planes = p->leaf_format == FMM_LEAF_BF16X3 ? 2 : 1;
+  return combined_bytes(Tx, Kd, ptx, pk, p->leaves, planes, 128) +
+         combined_bytes(Ty, Kd, pty, pk, p->leaves, planes, 256);
+}
+
+// The pass schedule: the combination pass writes S_r (from x) and T_r (from
+// y) for every leaf into the workspace; the multiply kernel then streams
+// them.  Returns FMM_ERR_WORKSPACE when the workspace is too small.
+static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, const EpilogueArgs& c,
+                           const LeafDesc* leaves, int* status, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const int planes = p->leaf_format == FMM_LEAF_BF16X3 ? 2 : 1;
+  const int64_t R = p->leaves;
+  const int64_t bt_a = ceil_div(x.T, x.pt), bt_b = ceil_div(y.T, y.pt), bk = ceil_div(x.Kd, x.pk);
+  const int bn = pass_tile_n(bt_b);
+  const int64_t tp_a = round_up(bt_a, 128), tp_b = round_up(bt_b, bn), kp = round_up(bk, 64);
+  const int64_t bytes_a = round_up(planes * R * tp_a * kp * 2, 256);
+  const int64_t bytes_b = round_up(planes * R * tp_b * kp * 2, 256);
+  if (!ws || (uintptr_t)ws % 256 != 0 || (int64_t)ws_bytes < bytes_a + bytes_b) return FMM_ERR_WORKSPACE;
+  char* wa = static_cast<char*>(ws);
+  char* wb = wa + bytes_a;
+  // One side: the source's memory rows follow t (k-contiguous) or k.
+  auto combine = [&](const Source& s, int64_t bt, int64_t tp, int side, char* out) {
+    CombineArgs ca;
+    ca.src = s.ptr;
+    ca.ld = s.ld;
+    ca.dtype = s.dtype;
+    ca.rows = s.kcontig ? s.T : s.Kd;
+    ca.cols = s.kcontig ? s.Kd : s.T;
+    ca.b_rows = s.kcontig ? bt : bk;
+    ca.b_cols = s.kcontig ? bk : bt;
+    ca.p_rows = s.kcontig ? tp : kp;
+    ca.p_cols = s.kcontig ? kp : tp;
+    ca.t_rows = s.kcontig ? 1 : 0;
+    ca.re = s.re;
+    ca.rs = s.rs;
+    ca.ce = s.ce;
+    ca.cs = s.cs;
+    ca.leaves = leaves;
+    ca.num_leaves = R;
+    ca.side = side;
+    ca.blk_t_shift = side == 0 ? 16 : 0;
+    ca.blk_k_shift = side == 0 ? 0 : 16;
+    ca.out = out;
+    ca.fmt = p->leaf_format;
+    return launch_combine(ca, st);
+  };
+  if (!cuda_ok(combine(x, bt_a, tp_a, 0, wa), "combination pass (A)")) return FMM_ERR_CUDA;
+  if (!cuda_ok(combine(y, bt_b, tp_b, 1, wb), "combination pass (B)")) return FMM_ERR_CUDA;
+  DirectArgs d;
+  std::memset(&d, 0, sizeof(d));
+  const bool f16 = p->leaf_format == FMM_LEAF_F16;
+  // K-major planes: rows (plane, leaf, t), k contiguous, box 64 k x tile t;
+  // MN-major planes: rows (plane, leaf, k), t contiguous, box 64 t x 64 k.
+  auto map = [&](CUtensorMap* m, const Source& s, char* buf, int64_t tp, int tile) {
+    return s.kcontig ? make_map_sw128(m, buf, f16, planes * R * tp, kp, kp, tile)
+                     : make_map_sw128(m, buf, f16, planes * R * kp, tp, tp, 64);
+  };
+  if (!map(&d.map_a, x, wa, tp_a, 128) || !map(&d.map_b, y, wb, tp_b, bn)) return FMM_ERR_CUDA;
+  d.a_mn = x.kcontig ? 0 : 1;
+  d.b_mn = y.kcontig ? 0 : 1;
+  d.c = c;
+  d.leaves = leaves;
+  d.num_leaves = R;
+  d.tp_a = tp_a;
+  d.tp_b = tp_b;
+  d.kp = kp;
+  d.status = status;
+  d.timeout_ns = timeout_ns();
+  return cuda_ok(launch_direct_gemm(d, p->leaf_format, bn, st), "multiply launch") ? FMM_OK : FMM_ERR_CUDA;
+}
+
 // Run the flattened plan p: C (M x N) = X (M x K) Y (K x N) with X, Y given
 // as sources (X: t = M, k = K; Y: t = N, k = K).  leaves: a device copy of
 // the plan's leaf table to use instead of the plan's own upload (NULL: the
@@ -224,6 +345,20 @@ static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, floa
     if (ensure_uploaded(p) != FMM_OK) return FMM_ERR_CUDA;
     leaves = p->dev;
   }
+  EpilogueArgs c;
+  c.C = C;
+  c.ldc = ldc;
+  c.M = M;
+  c.N = N;
+  c.bm = ceil_div(M, p->pm);
+  c.bn = ceil_div(N, p->pn);
+  c.eA = eA;
+  c.eB = eB;
+  c.vec_ok = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0) && (c.bn % 4 == 0) ? 1 : 0;
+  const bool pass = p->schedule == FMM_SCHEDULE_PASS ||
+                    (p->schedule == FMM_SCHEDULE_AUTO && ws && (uintptr_t)ws % 256 == 0 &&
+                     (int64_t)ws_bytes >= pass_bytes(p, M, K, N, p->pm, p->pk, p->pn));
+  if (pass) return run_pass(p, x, y, c, leaves, status, ws, ws_bytes, st);
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
   char* w = static_cast<char*>(ws);
@@ -233,15 +368,7 @@ static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, floa
   if (s != FMM_OK) return s;
   s = prepare(y, 0, 16, &w, w_end, &g.b, &g.map_b, st);
   if (s != FMM_OK) return s;
-  g.c.C = C;
-  g.c.ldc = ldc;
-  g.c.M = M;
-  g.c.N = N;
-  g.c.bm = ceil_div(M, p->pm);
-  g.c.bn = ceil_div(N, p->pn);
-  g.c.eA = eA;
-  g.c.eB = eB;
-  g.c.vec_ok = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0) && (g.c.bn % 4 == 0) ? 1 : 0;
+  g.c = c;
   g.leaves = leaves;
   g.num_leaves = p->leaves;
   g.status = status;
@@ -253,9 +380,15 @@ static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, floa
 // the prepared copies of the two operands of the largest of the forward,
 // dA and dB products.
 static size_t ws_bytes_for(const Plan* p, int64_t M, int64_t K, int64_t N) {
-  const int64_t fwd = prepared_bytes(M, K, p->pm, p->pk) + prepared_bytes(N, K, p->pn, p->pk);
-  const int64_t da = prepared_bytes(M, N, p->pm, p->pn) + prepared_bytes(K, N, p->pk, p->pn);
-  const int64_t db = prepared_bytes(K, M, p->pk, p->pm) + prepared_bytes(N, M, p->pn, p->pm);
+  int64_t fwd = prepared_bytes(M, K, p->pm, p->pk) + prepared_bytes(N, K, p->pn, p->pk);
+  int64_t da = prepared_bytes(M, N, p->pm, p->pn) + prepared_bytes(K, N, p->pk, p->pn);
+  int64_t db = prepared_bytes(K, M, p->pk, p->pm) + prepared_bytes(N, M, p->pn, p->pm);
+  if (p->schedule != FMM_SCHEDULE_LOAD_STAGE) {
+    // dA = dC B^T is an <m0, n0, k0> product, dB = A^T dC a <k0, m0, n0> one.
+    fwd = std::max(fwd, pass_bytes(p, M, K, N, p->pm, p->pk, p->pn));
+    da = std::max(da, pass_bytes(p, M, N, K, p->pm, p->pn, p->pk));
+    db = std::max(db, pass_bytes(p, K, M, N, p->pk, p->pm, p->pn));
+  }
   return (size_t)std::max(fwd, std::max(da, db));
 }
 
@@ -308,6 +441,16 @@ fmm_status fmm_plan(fmm_plan_t* out, int levels, const fmm_rule* rules, int leaf
 
 fmm_status fmm_plan_destroy(fmm_plan_t plan) {
   destroy_plan(reinterpret_cast<Plan*>(plan));
+  return FMM_OK;
+}
+
+fmm_status fmm_plan_set_schedule(fmm_plan_t plan, int schedule) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p || (schedule != FMM_SCHEDULE_AUTO && schedule != FMM_SCHEDULE_LOAD_STAGE && schedule != FMM_SCHEDULE_PASS))
+    return FMM_ERR_ARG;
+  p->schedule = schedule;
+  if (p->grad_a) p->grad_a->schedule = schedule;
+  if (p->grad_b) p->grad_b->schedule = schedule;
   return FMM_OK;
 }
 
@@ -477,6 +620,7 @@ fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc,
       if (s != FMM_OK) return s;
       s = make_plan(gb, p->leaf_format, &p->grad_b);
       if (s != FMM_OK) return s;
+      p->grad_a->schedule = p->grad_b->schedule = p->schedule;
     }
   }
   cudaStream_t st = as_stream(stream);

@@ -48,6 +48,14 @@ __device__ __forceinline__ float exp2i(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
+// x 2^e, exact whenever the result is a normal number (two multiplies when
+// 2^e alone is outside the binary32 range).
+__device__ __forceinline__ float scale_pow2(float x, int e) {
+  if (e >= -126 && e <= 127) return x * exp2i(e);
+  const int h = e / 2;
+  return (x * exp2i(h)) * exp2i(e - h);
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include "device.cuh"
+#include "gemm_common.cuh"
 #include "kernels.h"
 
 namespace fmm {
@@ -155,71 +156,6 @@ __device__ __forceinline__ uint32_t chunk_smem(int c) {
     return kmajor_off(c >> 3, c & 7);
   } else {
     return mnmajor_off(c >> 4, c & 15);
-  }
-}
-
-// ------------------------------------------------------------ TMA / bulk copies
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// 2-D tiled bulk tensor copy global -> shared, completion counted on *bar.
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int32_t x, int32_t y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// ------------------------------------------------------------ epilogue side
-
-__device__ __forceinline__ void epi_chunk(const EpilogueArgs& c, const LeafDesc* L, int64_t ml, int64_t nl0,
-                                          const uint32_t (&r)[32]) {
-  const int nc = __ldg(&L->nc);
-  for (int t = 0; t < nc; ++t) {
-    const int32_t blk = __ldg(&L->c_blk[t]);
-    const int64_t bi = (blk >> 16) & 0xFFFF, bj = blk & 0xFFFF;
-    const int64_t gi = bi * c.bm + ml;
-    if (gi >= c.M) continue;
-    const float coef = __ldg(&L->c_coef[t]);
-    const bool first = __ldg(&L->c_first[t]) != 0;
-    const float s = c.eA ? coef * exp2i(__ldg(c.eA + gi)) : coef;
-    const int64_t gj0 = bj * c.bn + nl0;
-    float* crow = c.C + gi * c.ldc;
-    if (c.vec_ok && nl0 + 32 <= c.bn && gj0 + 32 <= c.N) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        float4 v;
-        float* vp = reinterpret_cast<float*>(&v);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = 4 * q + u;
-          float x = s * __uint_as_float(r[j]);
-          if (c.eB) x *= exp2i(__ldg(c.eB + gj0 + j));
-          vp[u] = x;
-        }
-        float4* dst = reinterpret_cast<float4*>(crow + gj0 + 4 * q);
-        if (!first) {
-          const float4 o = *dst;
-          v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
-        }
-        *dst = v;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int64_t nl = nl0 + j, gj = gj0 + j;
-        if (nl < c.bn && gj < c.N) {
-          float x = s * __uint_as_float(r[j]);
-          if (c.eB) x *= exp2i(__ldg(c.eB + gj));
-          crow[gj] = first ? x : crow[gj] + x;
-        }
-      }
-    }
   }
 }
 

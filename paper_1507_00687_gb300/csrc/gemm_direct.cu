@@ -1,0 +1,290 @@
+// Leaf products over combined operands (Eq. 4.4, second and third lines):
+// M_r = S_r T_r on the tensor cores, C(c_blk) += w 2^(eA+eB) M_r in the
+// epilogue, for operands the combination pass already formed in the leaf
+// format.  There is no arithmetic between memory and the tensor cores, so
+// the kernel is the plain warp-specialised tcgen05 pipeline:
+//
+//   warps 0-3  epilogue: TMEM -> registers, C(blk) = / += coef 2^(eA+eB) M_r
+//   warp 4     lane 0: TMEM allocator and single-thread tcgen05.mma issuer
+//   warp 5     lane 0: TMA issuer: bulk tensor copies of each operand plane
+//              and stage straight into the 128-byte-swizzled layout the MMA
+//              descriptors read (K-major: one 64 k x rows box; MN-major: one
+//              64 t x 64 k box per 64 rows)
+//
+// One CTA per SM, persistent over BM x BN output tiles of the leaf-block
+// grid; a CTA visits every leaf for its tile in leaf order, so each C
+// element is updated by one thread in a fixed order (deterministic).  The
+// fp32 accumulator is double-buffered in TMEM so the epilogue of leaf r
+// overlaps the products of leaf r + 1.  Every mbarrier wait is bounded
+// (globaltimer); on expiry the kernel sets the timeout bit of the status
+// word, stops all roles, waits for its own copies and MMAs, frees its TMEM
+// and returns.
+#include <algorithm>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/fmm.h"
+#include "device.cuh"
+#include "gemm_common.cuh"
+#include "kernels.h"
+
+namespace fmm {
+namespace direct {
+
+using gemm::epi_chunk;
+using gemm::mbar_arrive_expect_tx;
+using gemm::tma_load_2d;
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int kEpiWarps = 4;
+constexpr int kMmaWarp = 4;
+constexpr int kTmaWarp = 5;
+constexpr int kThreads = 6 * 32;
+
+template <int FMT, int BN>
+struct Cfg {
+  static constexpr int kSplit = FMT == FMM_LEAF_BF16X3 ? 2 : 1;
+  static constexpr int kATile = BM * BK * 2;
+  static constexpr int kBTile = BN * BK * 2;
+  static constexpr int kStage = kSplit * (kATile + kBTile);
+  static constexpr int kStages = (220 * 1024) / kStage > 8 ? 8 : (220 * 1024) / kStage;
+  static constexpr int kTmemCols = 2 * BN;
+  static constexpr int kBarBytes = 256;
+  static constexpr int kSmem = kStages * kStage + kBarBytes + 1024;  // + alignment slack
+};
+
+// Operand tile of `rows` t x 64 k from plane row block `blk` (= plane R +
+// leaf) at t offset t0, k offset k0, into dst.
+template <bool MN>
+__device__ __forceinline__ void load_tile(uint8_t* dst, const CUtensorMap* map, int rows, int64_t blk, int64_t tp,
+                                          int64_t kp, int64_t t0, int64_t k0, uint64_t* bar) {
+  if constexpr (MN) {
+    for (int c = 0; c < rows / 64; ++c)
+      tma_load_2d(dst + c * 8192, map, (int32_t)(t0 + 64 * c), (int32_t)(blk * kp + k0), bar);
+  } else {
+    tma_load_2d(dst, map, (int32_t)k0, (int32_t)(blk * tp + t0), bar);
+  }
+}
+
+// Descriptor of the 16-wide k step k16 of an operand tile at saddr.
+template <bool MN>
+__device__ __forceinline__ uint64_t tile_desc(uint32_t saddr, int k16) {
+  return MN ? smem_desc_mn_sw128(saddr + k16 * 2048) : smem_desc_sw128(saddr + k16 * 32);
+}
+
+template <int FMT, int BN, bool A_MN, bool B_MN>
+__global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_constant__ DirectArgs args) {
+  using C = Cfg<FMT, BN>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStage);
+  uint64_t* empty = full + C::kStages;
+  uint64_t* tfull = empty + C::kStages;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kEpiWarps * 32);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == kMmaWarp) tmem_alloc(tmem_slot, C::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int64_t ntm = args.tp_a / BM;
+  const int64_t ntn = args.tp_b / BN;
+  const int64_t ntiles = ntm * ntn;
+  const int64_t KT = args.kp / BK;
+  const int64_t NL = args.num_leaves;
+  const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+
+  if (warp == kTmaWarp) {
+    if (lane == 0) {
+      // ------------------------------------------------------ TMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      uint32_t armed = 0, armed_parity = 0;  // per stage: copy issued, parity it completes
+      const int64_t iters = my_tiles * NL * KT;
+      for (int64_t i = 0; i < iters && ok; ++i) {
+        const int64_t tile = blockIdx.x + (i / (NL * KT)) * gridDim.x, rem = i % (NL * KT);
+        const int64_t leaf = rem / KT, kt = rem % KT;
+        const int64_t tm = tile / ntn, tn = tile % ntn;
+        if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
+        uint8_t* st = smem + stage * C::kStage;
+        mbar_arrive_expect_tx(&full[stage], (uint32_t)C::kStage);
+        const int64_t k0 = kt * BK, ta = tm * BM, tb = tn * BN;
+        load_tile<A_MN>(st, &args.map_a, BM, leaf, args.tp_a, args.kp, ta, k0, &full[stage]);
+        load_tile<B_MN>(st + C::kSplit * C::kATile, &args.map_b, BN, leaf, args.tp_b, args.kp, tb, k0, &full[stage]);
+        if constexpr (C::kSplit == 2) {
+          load_tile<A_MN>(st + C::kATile, &args.map_a, BM, NL + leaf, args.tp_a, args.kp, ta, k0, &full[stage]);
+          load_tile<B_MN>(st + 2 * C::kATile + C::kBTile, &args.map_b, BN, NL + leaf, args.tp_b, args.kp, tb, k0,
+                          &full[stage]);
+        }
+        armed |= 1u << stage;
+        armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
+        if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
+      }
+      if (!ok) *abort_flag = 1;
+      // No copy may still be writing shared memory when the CTA exits: wait
+      // (1 s cap each) for every issued copy.
+      for (int s = 0; s < C::kStages; ++s) {
+        if (armed & (1u << s)) {
+          const uint64_t t0 = globaltimer_ns();
+          while (!mbar_try_wait(&full[s], (armed_parity >> s) & 1u) && globaltimer_ns() - t0 < 1000000000ull) {
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ------------------------------------------------------ MMA issuer
+      constexpr uint32_t idesc = idesc_f16(FMT == FMM_LEAF_F16 ? 0u : 1u, BM, BN, A_MN, B_MN);
+      int stage = 0;
+      uint32_t phase = 0, acc_iter = 0;
+      bool ok = true;
+      const uint32_t sbase = smem_u32(smem);
+      for (int64_t tile = 0; tile < my_tiles && ok; ++tile) {
+        for (int64_t leaf = 0; leaf < NL && ok; ++leaf) {
+          const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
+          if (!mbar_wait_bounded(&tempty[buf], aph ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + buf * BN;
+          for (int64_t kt = 0; kt < KT; ++kt) {
+            if (!mbar_wait_bounded(&full[stage], phase, abort_flag, args.timeout_ns)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a_hi = sbase + stage * C::kStage;
+            const uint32_t a_lo = a_hi + C::kATile;
+            const uint32_t b_hi = a_hi + C::kSplit * C::kATile;
+            const uint32_t b_lo = b_hi + C::kBTile;
+#pragma unroll
+            for (int k16 = 0; k16 < BK / 16; ++k16) {
+              const uint32_t acc = (kt > 0 || k16 > 0) ? 1u : 0u;
+              const uint64_t ah = tile_desc<A_MN>(a_hi, k16), bh = tile_desc<B_MN>(b_hi, k16);
+              mma_f16(d_tmem, ah, bh, idesc, acc);
+              if constexpr (C::kSplit == 2) {
+                mma_f16(d_tmem, ah, tile_desc<B_MN>(b_lo, k16), idesc, 1u);
+                mma_f16(d_tmem, tile_desc<A_MN>(a_lo, k16), bh, idesc, 1u);
+              }
+            }
+            mma_commit(&empty[stage]);
+            if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
+          }
+          if (!ok) break;
+          mma_commit(&tfull[buf]);
+          ++acc_iter;
+        }
+      }
+      if (!ok) *abort_flag = 1;
+      // All issued MMAs complete before TMEM is released (own 1 s cap: MMAs
+      // never wait on anything).
+      mma_commit(drain);
+      const uint64_t t0 = globaltimer_ns();
+      while (!mbar_try_wait(drain, 0) && globaltimer_ns() - t0 < 1000000000ull) {
+      }
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------------- epilogue
+    uint32_t acc_iter = 0;
+    bool ok = true;
+    const int row = warp * 32 + lane;  // TMEM lane = tile row
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const int64_t tm = tile / ntn, tn = tile % ntn;
+      const int64_t ml = tm * BM + row;
+      for (int64_t leaf = 0; leaf < NL; ++leaf) {
+        const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
+        // warp-uniform outcome: the TMEM loads below are .sync.aligned
+        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&tfull[buf], aph, abort_flag, args.timeout_ns));
+        if (!ok) break;
+        tc_fence_after();
+        const LeafDesc* L = args.leaves + leaf;
+#pragma unroll 1
+        for (int cc = 0; cc < BN / 32; ++cc) {
+          uint32_t r[32];
+          tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(warp * 32) << 16) + buf * BN + cc * 32, r);
+          if (ml < args.c.bm) epi_chunk(args.c, L, ml, tn * BN + cc * 32, r);
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[buf]);
+        ++acc_iter;
+      }
+    }
+    if (!ok) *abort_flag = 1;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(args.status, kStatusTimeout);
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, C::kTmemCols);
+  }
+}
+
+// Launch one instantiation: grid = min(tiles, SMs), one CTA per SM.
+template <int FMT, int BN, bool A_MN, bool B_MN>
+cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
+  using C = Cfg<FMT, BN>;
+  auto kern = direct_fmm_kernel<FMT, BN, A_MN, B_MN>;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  if (a.tp_a % BM != 0 || a.tp_b % BN != 0 || a.kp % BK != 0) return cudaErrorInvalidValue;
+  const int64_t ntiles = (a.tp_a / BM) * (a.tp_b / BN);
+  if (ntiles == 0) return cudaSuccess;
+  const int64_t grid = std::min<int64_t>(ntiles, device_sm_count());
+  kern<<<(unsigned)grid, kThreads, C::kSmem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Operand layouts used: forward (A K-major, B MN-major), dA = dC B^T (both
+// K-major), dB = A^T dC (both MN-major).
+template <int FMT, int BN>
+cudaError_t launch_layout(const DirectArgs& a, cudaStream_t st) {
+  if (!a.a_mn && a.b_mn) return launch_cfg<FMT, BN, false, true>(a, st);
+  if (!a.a_mn && !a.b_mn) return launch_cfg<FMT, BN, false, false>(a, st);
+  if (a.a_mn && a.b_mn) return launch_cfg<FMT, BN, true, true>(a, st);
+  return cudaErrorNotSupported;
+}
+
+template <int BN>
+cudaError_t launch_bn(const DirectArgs& a, int fmt, cudaStream_t st) {
+  switch (fmt) {
+    case FMM_LEAF_BF16: return launch_layout<FMM_LEAF_BF16, BN>(a, st);
+    case FMM_LEAF_F16: return launch_layout<FMM_LEAF_F16, BN>(a, st);
+    default: return launch_layout<FMM_LEAF_BF16X3, BN>(a, st);
+  }
+}
+
+}  // namespace direct
+
+cudaError_t launch_direct_gemm(const DirectArgs& a, int leaf_format, int bn, cudaStream_t st) {
+  return bn == 256 ? direct::launch_bn<256>(a, leaf_format, st) : direct::launch_bn<128>(a, leaf_format, st);
+}
+
+}  // namespace fmm

@@ -67,6 +67,57 @@ cudaError_t launch_prepare(const void* X, int dt, int64_t R, int64_t C, int64_t 
                            int64_t row_pad, int64_t col_blk, int64_t col_pad, const int* re, int rs, const int* ce,
                            int cs, void* Y, int64_t Rp, int64_t Cp, int64_t ldy, cudaStream_t st);
 
+// One side of the operand combination pass: for every leaf r of a plan,
+// S_r = sum over the leaf's terms of coef * X(block), in FP32 in term
+// order, each element of X scaled by 2^(rs re[row] + cs ce[col]) of its
+// memory row / column, rounded to the leaf format.  X is a row-major memory
+// matrix (rows x cols, ld) cut into blocks of b_rows x b_cols; each combined
+// block keeps that orientation and is padded to p_rows x p_cols: plane p
+// (0 = the rounded value, 1 = the bf16 remainder of the hi+lo split), leaf
+// r, row i, column j at out[((p R + r) p_rows + i) p_cols + j].
+struct CombineArgs {
+  const void* src;
+  int64_t ld;
+  int dtype;            // kF32 / kBF16 / kF16
+  int64_t rows, cols;   // memory extents of X
+  int64_t b_rows, b_cols;
+  int64_t p_rows, p_cols;  // multiples of 32 and 64
+  int t_rows;           // memory rows follow the operand's t index (else its k index)
+  const int* re;        // memory-row exponents (nullable), sign rs
+  int rs;
+  const int* ce;        // memory-column exponents (nullable), sign cs
+  int cs;
+  const LeafDesc* leaves;
+  int64_t num_leaves;
+  int side;             // 0: the leaves' A terms, 1: their B terms
+  int blk_t_shift, blk_k_shift;
+  void* out;            // 16-bit elements
+  int fmt;              // FMM_LEAF_BF16 / FMM_LEAF_F16 / FMM_LEAF_BF16X3
+};
+
+cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st);
+
+// Multiply kernel over combined operands (the pass schedule): each operand
+// is the 16-bit output of the combination pass, K-major ([plane][R][tp][kp],
+// k contiguous) or MN-major ([plane][R][kp][tp], t contiguous), read whole
+// tiles at a time through the tensor maps (box 64 k x 128 / BN t for
+// K-major, 64 t x 64 k for MN-major).
+struct DirectArgs {
+  alignas(64) CUtensorMap map_a;
+  alignas(64) CUtensorMap map_b;
+  EpilogueArgs c;
+  const LeafDesc* leaves;
+  int64_t num_leaves;
+  int64_t tp_a, tp_b;  // padded t extent per leaf block (multiples of the tile)
+  int64_t kp;          // padded k extent (multiple of 64)
+  int a_mn, b_mn;      // operand layouts
+  int* status;
+  uint64_t timeout_ns;
+};
+
+// bn: tile width along N (128 or 256).
+cudaError_t launch_direct_gemm(const DirectArgs& args, int leaf_format, int bn, cudaStream_t st);
+
 // Launch the fused recursive-fast-multiply kernel for a flattened plan.
 cudaError_t launch_fused_gemm(const GemmArgs& args, int leaf_format, cudaStream_t st);
 

@@ -42,6 +42,7 @@ struct CanonRule {
 struct Plan {
   int levels = 0;
   int leaf_format = FMM_LEAF_BF16;
+  int schedule = FMM_SCHEDULE_AUTO;  // where S_r / T_r are formed (fmm_plan_set_schedule)
   std::vector<CanonRule> rules;
   int64_t pm = 1, pk = 1, pn = 1;  // products of m0, k0, n0 over the levels
   int64_t leaves = 1;

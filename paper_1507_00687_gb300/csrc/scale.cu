@@ -135,13 +135,6 @@ __global__ void __launch_bounds__(256) col_exp_kernel(const void* X, int64_t R, 
   if (nf) atomicOr(status, kStatusNonfinite);
 }
 
-// x 2^e, exact whenever the result is a normal number (two multiplies when
-// 2^e alone is outside the binary32 range).
-__device__ __forceinline__ float scale_pow2(float x, int e) {
-  if (e >= -126 && e <= 127) return x * exp2i(e);
-  const int h = e / 2;
-  return (x * exp2i(h)) * exp2i(e - h);
-}
 
 // Operand preparation (the apply pass of Algs. 1-3, plus blocking): each
 // thread writes 4 consecutive output columns of one output row (row_pad and

@@ -90,10 +90,16 @@ PLANS = [[], ["strassen"], ["winograd"], ["strassen", "strassen"], ["winograd", 
          ["strassen", "fast323"]]
 SHAPES = [(256, 256, 256), (300, 200, 250), (16, 16, 16), (1000, 520, 776), (1, 3, 2), (129, 65, 257)]
 
+# Where S_r and T_r are formed: in the multiply kernel's load stage, or by
+# the combination pass into the workspace.  Both are checked everywhere the
+# multiply is.
+SCHEDULES = ["load_stage", "pass"]
 
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("names", PLANS, ids=lambda n: "-".join(n) or "classical")
 @pytest.mark.parametrize("M,K,N", SHAPES)
-def test_multiply_integer_inputs_bit_exact(api, names, M, K, N):
+def test_multiply_integer_inputs_bit_exact(api, schedule, names, M, K, N):
     # Entries in [-4, 4]: every S, T entry is an integer small enough to be
     # exact in bf16 and fp16 and every sum stays below 2^24, so the fast
     # algorithm must return exactly the classical product.
@@ -101,7 +107,7 @@ def test_multiply_integer_inputs_bit_exact(api, names, M, K, N):
     B = inputs.integers((K, N), -4, 4, seed=N + 1)
     want = A @ B
     for dt, leaf in (("f32", "bf16x3"), ("bf16", "bf16"), ("f32", "fp16"), ("f16", "fp16"), ("bf16", "bf16x3")):
-        plan = api.Plan(names, leaf)
+        plan = api.Plan(names, leaf, schedule)
         got = api.multiply(plan, to_dev(A, dt), to_dev(B, dt))
         api.sync_status()
         assert np.array_equal(dev_values(got), want), (dt, leaf)
@@ -114,18 +120,19 @@ STREAM_CASES = [(["strassen"], 512, 256, 1024), (["winograd", "winograd"], 512, 
                 (["winograd"], 2048, 384, 1024)]
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("names,M,K,N", STREAM_CASES, ids=lambda x: "-".join(x) if isinstance(x, list) else str(x))
-def test_streaming_path_integer_exact_and_uniform(api, names, M, K, N):
+def test_streaming_path_integer_exact_and_uniform(api, schedule, names, M, K, N):
     A = inputs.integers((M, K), -4, 4, seed=M + 3)
     B = inputs.integers((K, N), -4, 4, seed=N + 4)
     for dt, leaf in (("f32", "bf16x3"), ("bf16", "bf16"), ("f32", "fp16")):
-        got = api.multiply(api.Plan(names, leaf), to_dev(A, dt), to_dev(B, dt))
+        got = api.multiply(api.Plan(names, leaf, schedule), to_dev(A, dt), to_dev(B, dt))
         api.sync_status()
         assert np.array_equal(dev_values(got), A @ B), (dt, leaf)
     Ar = inputs.uniform((M, K), -1, 1, seed=7)
     Br = inputs.uniform((K, N), -1, 1, seed=8)
     Ad, Bd = to_dev(Ar, "f32"), to_dev(Br, "f32")
-    got = dev_values(api.multiply(api.Plan(names, "bf16x3"), Ad, Bd))
+    got = dev_values(api.multiply(api.Plan(names, "bf16x3", schedule), Ad, Bd))
     C, G = oracle_reference(dev_values(Ad), dev_values(Bd), names)
     assert_within(got, C, G, names, K, "bf16x3", "streaming")
 
@@ -149,25 +156,27 @@ def test_multiply_leading_dims_and_k_zero(api):
 
 # ---------------------------------------------------------------- multiply, real inputs
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("names", [[], ["strassen"], ["winograd"], ["strassen", "strassen"],
                                    ["winograd", "winograd"], ["fast323"]], ids=lambda n: "-".join(n) or "classical")
 @pytest.mark.parametrize("leaf", ["bf16x3", "bf16", "fp16"])
-def test_multiply_uniform_within_tolerance(api, names, leaf):
+def test_multiply_uniform_within_tolerance(api, schedule, names, leaf):
     M, K, N = 700, 520, 650
     A = inputs.uniform((M, K), -1, 1, seed=5)
     B = inputs.uniform((K, N), -1, 1, seed=6)
     Ad, Bd = to_dev(A, "f32"), to_dev(B, "f32")
     A64, B64 = dev_values(Ad), dev_values(Bd)
-    plan = api.Plan(names, leaf)
+    plan = api.Plan(names, leaf, schedule)
     got = dev_values(api.multiply(plan, Ad, Bd))
     api.sync_status()
     C, G = oracle_reference(A64, B64, names)
     assert_within(got, C, G, names, K, leaf, f"{names} {leaf}")
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("names", [["strassen"], ["winograd"], []], ids=lambda n: "-".join(n) or "classical")
 @pytest.mark.parametrize("leaf", ["bf16", "fp16", "bf16x3"])
-def test_multiply_matches_rounding_emulation(api, names, leaf):
+def test_multiply_matches_rounding_emulation(api, schedule, names, leaf):
     # One level: S_r, T_r are formed in FP32 in index order on both sides, so
     # the rounded leaf operands agree exactly; only the FP32 accumulation of
     # the tensor core and of the output sums differ.
@@ -176,7 +185,7 @@ def test_multiply_matches_rounding_emulation(api, names, leaf):
     B = inputs.uniform((K, N), -1, 1, seed=16)
     Ad, Bd = to_dev(A, "f32"), to_dev(B, "f32")
     A64, B64 = dev_values(Ad), dev_values(Bd)
-    plan = api.Plan(names, leaf)
+    plan = api.Plan(names, leaf, schedule)
     got = dev_values(api.multiply(plan, Ad, Bd))
     from gpu_common import oracle_tree
     tree = oracle_tree(names)
@@ -202,9 +211,10 @@ def test_bf16x3_detects_dropped_correction(api):
         assert_within(got, C, G, ["strassen"], K, "bf16x3")
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("steps", ["", "O", "OI", "IO", "OIOI"])
 @pytest.mark.parametrize("names", [["winograd"], ["strassen", "strassen"]], ids=lambda n: "-".join(n))
-def test_multiply_scaled_within_tolerance(api, steps, names):
+def test_multiply_scaled_within_tolerance(api, schedule, steps, names):
     M, K, N = 512, 384, 448
     A, B = inputs.diag_scaled_pair(M, K, N, seed=9)
     Ad, Bd = to_dev(A, "f32"), to_dev(B, "f32")
@@ -218,7 +228,7 @@ def test_multiply_scaled_within_tolerance(api, steps, names):
     else:
         eA = d = eB = None
         tA = td = tB = None
-    plan = api.Plan(names, "bf16x3")
+    plan = api.Plan(names, "bf16x3", schedule)
     got = dev_values(api.multiply(plan, Ad, Bd, tA, td, tB))
     api.sync_status()
     C, G = oracle_reference(A64, B64, names, eA, d, eB)
@@ -246,9 +256,10 @@ def test_scaling_improves_componentwise_error(api):
 
 # ---------------------------------------------------------------- backward
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("names", [["strassen"], ["winograd"], ["strassen", "strassen"], ["fast323"], []],
                          ids=lambda n: "-".join(n) or "classical")
-def test_backward_against_oracle(api, names):
+def test_backward_against_oracle(api, schedule, names):
     from oracle import rules as OR
     from gpu_common import ORACLE_RULES
     M, K, N = 320, 256, 384
@@ -257,7 +268,7 @@ def test_backward_against_oracle(api, names):
     G0 = inputs.uniform((M, N), -1, 1, seed=53)
     Ad, Bd, dC = to_dev(A, "bf16"), to_dev(B, "bf16"), to_dev(G0, "f32")
     A64, B64, dC64 = dev_values(Ad), dev_values(Bd), dev_values(dC)
-    plan = api.Plan(names, "bf16x3")
+    plan = api.Plan(names, "bf16x3", schedule)
     dA, dB = api.multiply_backward(plan, dC, Ad, Bd)
     api.sync_status()
     ra = OF.uniform([OR.rule_for_dA(ORACLE_RULES[n]()) for n in names])
@@ -352,3 +363,29 @@ print('ALIVE', x)
                        timeout=300)
     assert "ALIVE 8.0" in r.stdout, r.stdout + r.stderr
     assert ("CODE 8" in r.stdout) or ("NO-TIMEOUT" in r.stdout)
+
+
+# ---------------------------------------------------------------- schedules
+
+def test_schedule_workspace_rules(api):
+    # The pass schedule needs the combined operands in the workspace; given
+    # only the load-stage workspace, a forced pass schedule reports
+    # FMM_ERR_WORKSPACE while the automatic one runs the load-stage schedule.
+    from paper_1507_00687_gb300 import _native as N
+    M, K, N_ = 384, 320, 448
+    A = inputs.uniform((M, K), -1, 1, seed=61)
+    B = inputs.uniform((K, N_), -1, 1, seed=62)
+    Ad, Bd = to_dev(A, "f32"), to_dev(B, "f32")
+    small = api.workspace_bytes(api.Plan(["winograd"], "bf16x3", "load_stage"), M, K, N_)
+    big = api.workspace_bytes(api.Plan(["winograd"], "bf16x3", "pass"), M, K, N_)
+    assert big > small
+    ws = torch.empty(small, dtype=torch.uint8, device="cuda")
+    with pytest.raises(N.FmmError) as e:
+        api.multiply(api.Plan(["winograd"], "bf16x3", "pass"), Ad, Bd, ws=ws)
+    assert e.value.code == 6
+    got = {s: dev_values(api.multiply(api.Plan(["winograd"], "bf16x3", s), Ad, Bd,
+                                      ws=ws if s == "auto" else None)) for s in ("auto", "load_stage", "pass")}
+    api.sync_status()
+    C, G = oracle_reference(dev_values(Ad), dev_values(Bd), ["winograd"])
+    for s, v in got.items():
+        assert_within(v, C, G, ["winograd"], K, "bf16x3", s)
