@@ -4,10 +4,13 @@
 Workload (one "step" = the whole hot path on one product): square n = 4096,
 FP32 inputs A = D1 X D2, B = D3 Y D4 (X, Y ~ U[0,1), diagonal entries
 2^U(-12,12)), outside-then-inside power-of-two scaling (two steps of Alg. 3:
-four reduction kernels) followed by one fused launch of the Winograd
-variant, one recursion level, bf16 hi+lo three-product leaves with FP32
-accumulation.  Inputs stay resident in HBM; L2 is flushed (256 MiB write,
-untimed) before every timed step.  Prints one JSON line.
+four reduction kernels) followed by the multiply of the Winograd variant,
+one recursion level, bf16 hi+lo three-product leaves with FP32
+accumulation: under the default (pass) schedule, one combination pass per
+operand forms S_r / T_r with the scaling applied, then one tensor-core
+launch forms the leaf products and adds them into C.  Inputs stay resident
+in HBM; L2 is flushed (256 MiB write, untimed) before every timed step.
+Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -46,6 +49,7 @@ def parse():
     ap.add_argument("--levels", type=int, default=1)
     ap.add_argument("--leaf", default="bf16x3")
     ap.add_argument("--scaling", default="OI")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "pass", "load_stage"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator / variant timings")
     return ap.parse_args()
 
@@ -54,17 +58,9 @@ def workload_config(args):
     return {"workload": f"{args.rule} L={args.levels}, n={args.n} square, FP32 data, {args.leaf} leaves, "
                         f"scaling {args.scaling or 'none'}",
             "rule": args.rule, "levels": args.levels, "M": args.n, "K": args.n, "N": args.n,
-            "leaf": args.leaf, "scaling_steps": args.scaling,
+            "leaf": args.leaf, "scaling_steps": args.scaling, "schedule": args.schedule,
             "inputs": "A=D1 X D2, B=D3 Y D4, X,Y~U[0,1), D=2^U(-12,12), seeded",
             "l2": "flushed before each timed step (256 MiB memset, untimed)"}
-
-
-def launches_per_scale(steps: str) -> int:
-    """Kernels one scaled step launches besides the multiply: fmm_scale's 3
-    initial fills, 4 per O step (row reduction, fill, column reduction, zero
-    fix-up), 3 per I step (fill, column reduction, row reduction), and the 2
-    apply passes that write the scaled operands."""
-    return 0 if not steps else 3 + 4 * steps.count("O") + 3 * steps.count("I") + 2
 
 
 # ---------------------------------------------------------------- clocks
@@ -220,9 +216,8 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     rules = [args.rule] * args.levels
-    plan = api.Plan(rules, args.leaf)
+    plan = api.Plan(rules, args.leaf, args.schedule)
     info = plan.info()
-    ws = torch.empty(api.workspace_bytes(plan, n, n, n), dtype=torch.uint8, device="cuda")
 
     def step(pl=plan, scaling=args.scaling, kev=None):
         if scaling:
@@ -236,18 +231,21 @@ def main():
         if kev is not None:
             kev[0].record(stream)
         if scaling:
-            api.multiply(pl, A, B, eA, d, eB, out=C, ws=ws)
+            api.multiply(pl, A, B, eA, d, eB, out=C)
         else:
             api.multiply(pl, A, B, out=C)
         if kev is not None:
             kev[1].record(stream)
 
-    def timed(steps, pl=plan, scaling=args.scaling, clocks=None):
+    def timed(steps, pl=plan, scaling=args.scaling, clocks=None, kernels=None):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         kevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        step(pl, scaling)  # untimed: sizes this plan's cached workspace
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        if kernels is not None:
+            api.kernel_timing(True)
         if clocks:
             clocks.start()
         for i in range(steps):
@@ -259,6 +257,10 @@ def main():
         if world > 1:
             dist.barrier()
         ck = clocks.stop() if clocks else None
+        if kernels is not None:
+            api.kernel_timing(False)
+            for kind in ("scale", "prepare", "combine", "multiply", ""):
+                kernels[kind] = api.kernel_timing_read(kind)
         api.sync_status()
         st = [a.elapsed_time(b) for a, b in evs]
         kt = [a.elapsed_time(b) for a, b in kevs]
@@ -269,7 +271,8 @@ def main():
     torch.cuda.synchronize()
     api.sync_status()
     clocks = Clocks(local)
-    ms, kms, ck = timed(args.steps, clocks=clocks)
+    kern = {}
+    ms, kms, ck = timed(args.steps, clocks=clocks, kernels=kern)
     if world > 1:
         t = torch.tensor([ms, kms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -312,14 +315,14 @@ def main():
     bound_unscaled = plan.bound(n, normA, normB, eps_leaf)
     extras = {}
     if not args.no_extras:
-        plan0 = api.Plan([], args.leaf)
+        plan0 = api.Plan([], args.leaf, args.schedule)
         c_ms, c_kms, _ = timed(max(10, args.steps // 4), plan0, args.scaling)
         step(plan0, args.scaling)
         torch.cuda.synchronize()
         err_cls = float((C.double() - ref).abs().max())
         extras["classical_same_kernel"] = {"tflops": flops / (c_ms * 1e-3) / 1e12, "ms_per_step": c_ms,
                                            "kernel_ms": c_kms, "max_abs_err": err_cls,
-                                           "note": "L=0 plan through the same fused kernel, same scaling"}
+                                           "note": "L=0 plan through the same kernels, same scaling"}
         ns_ms, ns_kms, _ = timed(max(10, args.steps // 4), plan, "")
         step(plan, "")
         torch.cuda.synchronize()
@@ -334,7 +337,7 @@ def main():
         extras["componentwise_rel_err"]["fast_unscaled"] = rel(C.double())
         if args.levels == 1:
             try:
-                plan2 = api.Plan([args.rule] * 2, args.leaf)
+                plan2 = api.Plan([args.rule] * 2, args.leaf, args.schedule)
                 l2_ms, l2_kms, _ = timed(max(10, args.steps // 4), plan2, args.scaling)
                 step(plan2, args.scaling)
                 torch.cuda.synchronize()
@@ -345,7 +348,7 @@ def main():
         del plan0
     del ref, C_fast
 
-    # ---------------- roofline of the dominant kernel (the fused multiply)
+    # ---------------- roofline of the dominant kernel (the tensor-core multiply)
     import json as _json
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = _json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
@@ -353,12 +356,25 @@ def main():
     peak_src = "of measured (bf16_tflops_sustained)" if peaks else "of fallback"
     leaf_flops = 2.0 * info["leaves"] * (-(-n // info["pm"])) * (-(-n // info["pk"])) * (-(-n // info["pn"]))
     mma_flops = leaf_flops * (3 if args.leaf == "bf16x3" else 1)
-    achieved = mma_flops / (kms * 1e-3) / 1e12
+    mult_ms, mult_n = kern["multiply"]
+    mult_ms_per = mult_ms / max(1, mult_n)
+    achieved = mma_flops / (mult_ms_per * 1e-3) / 1e12
+    sched_used = "pass" if kern["combine"][1] > 0 else "load_stage"
+    kname = "direct_fmm_kernel" if sched_used == "pass" else "fused_fmm_kernel"
+    # the combination pass: reads each operand once, writes R^L combined
+    # leaf blocks (two bf16 planes for bf16x3, else one 16-bit plane)
+    planes = 2 if args.leaf == "bf16x3" else 1
+    bt = -(-n // info["pm"])
+    tp, kp = -(-bt // 128) * 128, -(-(-(-n // info["pk"])) // 64) * 64
+    comb_bytes = n * n * 4 + planes * info["leaves"] * tp * kp * 2
+    comb_ms, comb_n = kern["combine"]
+    kernel_times = {k or "all": {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / max(1, v[1])}
+                    for k, v in kern.items()}
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         tj = _json.load(open(prof))
-        key = f"{args.rule}_L{args.levels}_{args.leaf}_n{n}"
+        key = f"{kname}:{args.rule}_L{args.levels}_{args.leaf}_n{n}"
         traffic = tj.get(key)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -366,17 +382,25 @@ def main():
            "vs_baseline": None, "dtype": "f32-in/bf16x3-leaf/f32-acc" if args.leaf == "bf16x3" else args.leaf,
            "data": "synthetic", "config": workload_config(args),
            "paper_effective_tflops": world * (2.0 * n**3 - n**2) / (ms * 1e-3) / 1e12,
-           "kernel_ms": kms,
-           "executed_flop_fraction": mma_flops / (kms * 1e-3) / 1e12 / peak,
+           "multiply_call_ms": kms,
+           "schedule": sched_used,
+           "kernel_times": kernel_times,
+           "combine_pass": ({"ms_per_launch": comb_ms / comb_n, "algorithmic_bytes_per_launch": comb_bytes,
+                             "achieved_GBps": comb_bytes / (comb_ms / comb_n * 1e-3) / 1e9,
+                             "peak_GBps": peaks.get("hbm_gbs"),
+                             "frac": (comb_bytes / (comb_ms / comb_n * 1e-3) / 1e9 / peaks["hbm_gbs"])
+                             if peaks.get("hbm_gbs") else None} if comb_n else None),
+           "executed_flop_fraction": achieved / peak,
            "error": {"max_abs_err_vs_fp64": err_fast, "theorem_4_1_bound_unscaled": bound_unscaled,
                      "eps_leaf": eps_leaf, "normA": normA, "normB": normB},
            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                        "kernel": "fused_fmm_kernel", "algorithmic_flops_per_launch": mma_flops},
+                        "kernel": kname, "algorithmic_flops_per_launch": mma_flops,
+                        "ms_per_launch": mult_ms_per},
            "e2e": {"value": world * flops / (e_ms * 1e-3) / 1e12, "unit": UNIT,
                    "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
                    "ms_per_step": e_ms},
-           "gpu_launches": args.steps * (launches_per_scale(args.scaling) + 1),
+           "gpu_launches": kern[""][1],
            "clocks": ck, "plan": info}
     out.update(extras)
     if rank == 0 and world == 1:

@@ -265,6 +265,21 @@ fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc,
                                  int64_t N, int in_dtype, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * Per-kernel timing, for measurement.  fmm_kernel_timing(1) starts
+ * recording (discarding earlier records): every kernel the library launches
+ * from then on is bracketed by two CUDA events recorded on its launching
+ * stream; fmm_kernel_timing(0) stops recording.  fmm_kernel_timing_read
+ * waits for the recorded events and returns the summed device time (ms)
+ * and the number of launches of one kind -- "scale" (scaling reductions and
+ * fills), "prepare" (operand copies of the load-stage schedule), "combine"
+ * (the combination pass), "multiply" (the tensor-core kernels) -- or of all
+ * kinds when kind is NULL or "".  The library's own work is unchanged; the
+ * events add a few microseconds of host time per launch.
+ */
+fmm_status fmm_kernel_timing(int enable);
+fmm_status fmm_kernel_timing_read(const char* kind, double* total_ms, int64_t* launches);
+
+/*
  * Synchronise the stream, then read and clear the device status word.
  * Returns FMM_OK, FMM_ERR_DEVICE_TIMEOUT, FMM_ERR_NONFINITE or FMM_ERR_CUDA.
  */

@@ -27,7 +27,7 @@ EXPORTS = [
     "fmm_plan", "fmm_plan_destroy", "fmm_plan_info", "fmm_plan_bound", "fmm_scale_outside",
     "fmm_scale_inside", "fmm_scale", "fmm_workspace_size", "fmm_multiply", "fmm_multiply_backward",
     "fmm_sync_status", "fmm_status_string", "fmm_version", "fmm_last_error", "fmm_multiply_noalloc",
-    "fmm_plan_set_schedule",
+    "fmm_plan_set_schedule", "fmm_kernel_timing", "fmm_kernel_timing_read",
 ]
 
 # Bytes of the library's static scratch array (FMM_NOALLOC_SCRATCH_BYTES).
@@ -62,6 +62,8 @@ def lib():
     L.fmm_plan.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(FmmRule), C.c_int]
     L.fmm_plan_destroy.argtypes = [vp]
     L.fmm_plan_set_schedule.argtypes = [vp, C.c_int]
+    L.fmm_kernel_timing.argtypes = [C.c_int]
+    L.fmm_kernel_timing_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64)]
     L.fmm_plan_info.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i64),
                                 C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     L.fmm_plan_bound.argtypes = [vp, i64, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]

@@ -186,6 +186,19 @@ def multiply_backward(plan: Plan, dC: torch.Tensor, A: torch.Tensor, B: torch.Te
     return dA, dB
 
 
+def kernel_timing(enable: bool) -> None:
+    """Start (discarding earlier records) or stop per-kernel event timing."""
+    N.check(N.lib().fmm_kernel_timing(1 if enable else 0), "fmm_kernel_timing")
+
+
+def kernel_timing_read(kind: str = "") -> tuple:
+    """(total ms, launches) of the recorded kernels of one kind ("scale",
+    "prepare", "combine", "multiply") or of all kinds."""
+    ms, n = C.c_double(), C.c_int64()
+    N.check(N.lib().fmm_kernel_timing_read(kind.encode(), C.byref(ms), C.byref(n)), "fmm_kernel_timing_read")
+    return ms.value, n.value
+
+
 def sync_status(stream=None) -> None:
     """Synchronise and raise FmmError if a kernel recorded a device error."""
     N.check(N.lib().fmm_sync_status(_stream(stream)), "device status")

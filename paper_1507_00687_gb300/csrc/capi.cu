@@ -285,6 +285,8 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
     ca.cols = s.kcontig ? s.Kd : s.T;
     ca.b_rows = s.kcontig ? bt : bk;
     ca.b_cols = s.kcontig ? bk : bt;
+    ca.n_rb = s.kcontig ? s.pt : s.pk;
+    ca.n_cb = s.kcontig ? s.pk : s.pt;
     ca.p_rows = s.kcontig ? tp : kp;
     ca.p_cols = s.kcontig ? kp : tp;
     ca.t_rows = s.kcontig ? 1 : 0;
@@ -301,8 +303,9 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
     ca.fmt = p->leaf_format;
     return launch_combine(ca, st);
   };
-  if (!cuda_ok(combine(x, bt_a, tp_a, 0, wa), "combination pass (A)")) return FMM_ERR_CUDA;
+  // B first: a scaling sequence that ends with a pass over B leaves it in L2
   if (!cuda_ok(combine(y, bt_b, tp_b, 1, wb), "combination pass (B)")) return FMM_ERR_CUDA;
+  if (!cuda_ok(combine(x, bt_a, tp_a, 0, wa), "combination pass (A)")) return FMM_ERR_CUDA;
   DirectArgs d;
   std::memset(&d, 0, sizeof(d));
   const bool f16 = p->leaf_format == FMM_LEAF_F16;
@@ -520,20 +523,67 @@ fmm_status fmm_scale_inside(const void* A, const void* B, int dtype, int64_t M, 
   return FMM_OK;
 }
 
+// The step pair O, I of Alg. 3 starting from d = 0 (M, K, N > 0), in the
+// order rows(A) -> eA, columns(A 2^-eA) -> d, columns(B) -> eB,
+// rows(2^-eB B) with d -> d: the same four reductions as fmm_scale_outside
+// then fmm_scale_inside with the same results.
+static fmm_status scale_oi_from_zero(const void* A, const void* B, int dtype, int64_t M, int64_t K, int64_t N,
+                                     int64_t lda, int64_t ldb, int32_t* eA, int32_t* d, int32_t* eB,
+                                     cudaStream_t st) {
+  if (!valid_dtype(dtype) || !A || !B || !eA || !d || !eB) return FMM_ERR_ARG;
+  if (lda < K || ldb < N) return FMM_ERR_SHAPE;
+  int* status = status_ptr();
+  if (!status) return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_row_exp(A, dtype, M, K, lda, nullptr, +1, eA, kRowOStep, status, st), "row reduction"))
+    return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_col_exp(A, dtype, M, K, lda, eA, -1, d, status, st), "column reduction"))
+    return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_col_exp(B, dtype, K, N, ldb, nullptr, -1, eB, status, st), "column reduction"))
+    return FMM_ERR_CUDA;
+  if (launch_zero_sentinel(eB, N, st) != cudaSuccess) return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_row_exp(B, dtype, K, N, ldb, eB, -1, d, kRowIStep, status, st), "row reduction"))
+    return FMM_ERR_CUDA;
+  return FMM_OK;
+}
+
 fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype, int64_t M, int64_t K, int64_t N,
                      int64_t lda, int64_t ldb, int32_t* eA, int32_t* d, int32_t* eB, void* stream) {
   if (!steps) return FMM_ERR_ARG;
-  for (const char* c = steps; *c; ++c)
+  bool has_o = false, has_i = false;
+  for (const char* c = steps; *c; ++c) {
     if (*c != 'O' && *c != 'I') return FMM_ERR_ARG;
+    has_o |= *c == 'O';
+    has_i |= *c == 'I';
+  }
   if ((M > 0 && !eA) || (K > 0 && !d) || (N > 0 && !eB)) return FMM_ERR_ARG;
   cudaStream_t st = as_stream(stream);
-  if (launch_fill(eA, M, 0, st) != cudaSuccess || launch_fill(d, K, 0, st) != cudaSuccess ||
-      launch_fill(eB, N, 0, st) != cudaSuccess)
+  // Every vector starts at zero (no scaling).  A vector that some step
+  // overwrites completely needs no fill; and while a vector is still all
+  // zeros the steps that read it are told so (no shift), which selects the
+  // unshifted reductions.
+  if (!has_o && (launch_fill(eA, M, 0, st) != cudaSuccess || launch_fill(eB, N, 0, st) != cudaSuccess))
     return FMM_ERR_CUDA;
+  if (!has_i && launch_fill(d, K, 0, st) != cudaSuccess) return FMM_ERR_CUDA;
+  bool d_zero = true, e_zero = true;
   for (const char* c = steps; *c; ++c) {
-    fmm_status s = *c == 'O' ? fmm_scale_outside(A, B, dtype, M, K, N, lda, ldb, d, eA, eB, stream)
-                             : fmm_scale_inside(A, B, dtype, M, K, N, lda, ldb, eA, eB, d, stream);
+    if (c[0] == 'O' && c[1] == 'I' && d_zero && M > 0 && K > 0 && N > 0) {
+      // An O step on unshifted operands followed by an I step: the I step's
+      // column pass over A needs only eA, so each operand's two passes run
+      // back to back (the second one mostly from L2): rows of A, columns of
+      // A, columns of B, rows of B.
+      fmm_status s = scale_oi_from_zero(A, B, dtype, M, K, N, lda, ldb, eA, d, eB, st);
+      if (s != FMM_OK) return s;
+      e_zero = d_zero = false;
+      ++c;
+      continue;
+    }
+    fmm_status s = *c == 'O'
+                       ? fmm_scale_outside(A, B, dtype, M, K, N, lda, ldb, d_zero ? nullptr : d, eA, eB, stream)
+                       : fmm_scale_inside(A, B, dtype, M, K, N, lda, ldb, e_zero ? nullptr : eA,
+                                          e_zero ? nullptr : eB, d, stream);
     if (s != FMM_OK) return s;
+    if (*c == 'O') e_zero = false;
+    else d_zero = false;
   }
   return FMM_OK;
 }

@@ -164,12 +164,109 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs a) 
   }
 }
 
+// Staged form for plans with few input blocks (at most kMaxStaged): every
+// input block's TR x 64 tile is loaded and scaled once into shared memory
+// (in block order), then each leaf's terms are summed from there in term
+// order -- the same arithmetic as above with each element scaled once
+// instead of once per use.  TR * 16 threads, one row of 4 columns each.
+constexpr int kMaxStaged = 16;
+
+template <int DT, int FMT, int TR>
+__global__ void __launch_bounds__(TR * 16) combine_staged_kernel(const CombineArgs a) {
+  extern __shared__ float4 tile4[];  // [block][TR][16]
+  const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * kTC;
+  const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15, tc = tq * 4;
+  const int es = DT == kF32 ? 4 : 2;
+  const bool vec_ok = ((uintptr_t)a.src % (4 * es) == 0) && (a.ld % 4 == 0) && (a.b_cols % 4 == 0) &&
+                      (!a.ce || (uintptr_t)a.ce % 16 == 0);
+  const int n_rb = (int)a.n_rb, n_cb = (int)a.n_cb;
+  const int64_t lr = r0 + tr, lc = c0 + tc;
+  for (int rb = 0; rb < n_rb; ++rb) {
+    const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows);
+    const int64_t gr = rb * a.b_rows + lr;
+    const bool row_in = r0 + TR <= nr;
+    const int er = (a.re && lr < nr) ? a.rs * __ldg(a.re + gr) : 0;
+    const char* src_row = static_cast<const char*>(a.src) + gr * a.ld * es;
+    for (int cb = 0; cb < n_cb; ++cb) {
+      const int64_t nc = min(a.b_cols, a.cols - cb * a.b_cols);
+      const int64_t gc = cb * a.b_cols + lc;
+      float x[4];
+      if (vec_ok && row_in && c0 + kTC <= nc) {
+        load4<DT>(src_row, gc, x);
+        if (a.re || a.ce) {
+          int4 ec = make_int4(0, 0, 0, 0);
+          if (a.ce) ec = __ldg(reinterpret_cast<const int4*>(a.ce + gc));
+          x[0] = scale_pow2(x[0], er + a.cs * ec.x);
+          x[1] = scale_pow2(x[1], er + a.cs * ec.y);
+          x[2] = scale_pow2(x[2], er + a.cs * ec.z);
+          x[3] = scale_pow2(x[3], er + a.cs * ec.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          x[j] = 0.f;
+          if (lr < nr && lc + j < nc) {
+            const float v = load_elem<DT>(src_row, gc + j);
+            x[j] = scale_pow2(v, er + (a.ce ? a.cs * __ldg(a.ce + gc + j) : 0));
+          }
+        }
+      }
+      tile4[((rb * n_cb + cb) * TR + tr) * 16 + tq] = make_float4(x[0], x[1], x[2], x[3]);
+    }
+  }
+  __syncthreads();
+  const int64_t R = a.num_leaves;
+  unsigned short* out = static_cast<unsigned short*>(a.out);
+  const int64_t plane = R * a.p_rows * a.p_cols;
+  for (int64_t r = 0; r < R; ++r) {
+    const LeafDesc* L = a.leaves + r;
+    const int n = a.side == 0 ? __ldg(&L->na) : __ldg(&L->nb);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int t = 0; t < n; ++t) {
+      const int32_t blk = a.side == 0 ? __ldg(&L->a_blk[t]) : __ldg(&L->b_blk[t]);
+      const float coef = a.side == 0 ? __ldg(&L->a_coef[t]) : __ldg(&L->b_coef[t]);
+      const int bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
+      const int b = a.t_rows ? bt * n_cb + bk : bk * n_cb + bt;
+      const float4 v = tile4[(b * TR + tr) * 16 + tq];
+      acc[0] = fmaf(coef, v.x, acc[0]);
+      acc[1] = fmaf(coef, v.y, acc[1]);
+      acc[2] = fmaf(coef, v.z, acc[2]);
+      acc[3] = fmaf(coef, v.w, acc[3]);
+    }
+    const int64_t off = (r * a.p_rows + lr) * a.p_cols + lc;
+    store4<FMT>(out + off, out + off + plane, acc);
+  }
+}
+
+template <int DT, int FMT>
+void launch_staged(const CombineArgs& a, int nb, cudaStream_t st) {
+  // TR rows per CTA so that the staged tiles take at most 48 KB
+  if (nb <= 6) {
+    combine_staged_kernel<DT, FMT, 32><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / 32)), 512,
+                                         nb * 32 * 256, st>>>(a);
+  } else if (nb <= 12) {
+    combine_staged_kernel<DT, FMT, 16><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / 16)), 256,
+                                         nb * 16 * 256, st>>>(a);
+  } else {
+    combine_staged_kernel<DT, FMT, 8><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / 8)), 128,
+                                        nb * 8 * 256, st>>>(a);
+  }
+}
+
+template <int DT, int FMT>
+void launch_fmt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
+  const int64_t nb = a.n_rb * a.n_cb;
+  if (nb <= kMaxStaged) launch_staged<DT, FMT>(a, (int)nb, st);
+  else combine_kernel<DT, FMT><<<grid, kThreads, 0, st>>>(a);
+}
+
 template <int DT>
 cudaError_t launch_dt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
+  KernelTimer timer("combine", st);
   switch (a.fmt) {
-    case FMM_LEAF_BF16: combine_kernel<DT, FMM_LEAF_BF16><<<grid, kThreads, 0, st>>>(a); break;
-    case FMM_LEAF_F16: combine_kernel<DT, FMM_LEAF_F16><<<grid, kThreads, 0, st>>>(a); break;
-    default: combine_kernel<DT, FMM_LEAF_BF16X3><<<grid, kThreads, 0, st>>>(a); break;
+    case FMM_LEAF_BF16: launch_fmt<DT, FMM_LEAF_BF16>(a, grid, st); break;
+    case FMM_LEAF_F16: launch_fmt<DT, FMM_LEAF_F16>(a, grid, st); break;
+    default: launch_fmt<DT, FMM_LEAF_BF16X3>(a, grid, st); break;
   }
   return cudaGetLastError();
 }

@@ -426,6 +426,7 @@ cudaError_t launch_cfg(const GemmArgs& a, cudaStream_t st) {
   }
   const int64_t ntiles = (a.a.bt / BM) * (a.b.bt / BN);
   const int64_t grid = std::min<int64_t>(ntiles, device_sm_count());
+  KernelTimer timer("multiply", st);
   kern<<<(unsigned)grid, kThreads, C::kSmem, st>>>(a);
   return cudaGetLastError();
 }

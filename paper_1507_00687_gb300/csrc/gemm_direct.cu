@@ -258,6 +258,7 @@ cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
   const int64_t ntiles = (a.tp_a / BM) * (a.tp_b / BN);
   if (ntiles == 0) return cudaSuccess;
   const int64_t grid = std::min<int64_t>(ntiles, device_sm_count());
+  KernelTimer timer("multiply", st);
   kern<<<(unsigned)grid, kThreads, C::kSmem, st>>>(a);
   return cudaGetLastError();
 }

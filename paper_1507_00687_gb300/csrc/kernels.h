@@ -81,6 +81,7 @@ struct CombineArgs {
   int dtype;            // kF32 / kBF16 / kF16
   int64_t rows, cols;   // memory extents of X
   int64_t b_rows, b_cols;
+  int64_t n_rb, n_cb;   // number of row / column blocks
   int64_t p_rows, p_cols;  // multiples of 32 and 64
   int t_rows;           // memory rows follow the operand's t index (else its k index)
   const int* re;        // memory-row exponents (nullable), sign rs
@@ -120,6 +121,23 @@ cudaError_t launch_direct_gemm(const DirectArgs& args, int leaf_format, int bn, 
 
 // Launch the fused recursive-fast-multiply kernel for a flattened plan.
 cudaError_t launch_fused_gemm(const GemmArgs& args, int leaf_format, cudaStream_t st);
+
+// While kernel timing is enabled (fmm_kernel_timing), an object of this
+// type brackets one kernel launch with CUDA events on its stream; kinds:
+// "scale", "prepare", "combine", "multiply".
+class KernelTimer {
+ public:
+  KernelTimer(const char* kind, cudaStream_t st);
+  ~KernelTimer();
+  KernelTimer(const KernelTimer&) = delete;
+  KernelTimer& operator=(const KernelTimer&) = delete;
+
+ private:
+  const char* kind_;
+  cudaStream_t st_;
+  void* start_ = nullptr;
+  void* stop_ = nullptr;
+};
 
 // Number of SMs of the current device (cached).
 int device_sm_count();

@@ -15,126 +15,257 @@
 
 namespace fmm {
 
+// ---------------------------------------------------------------- decoding
+
+// Four consecutive raw encodings (16 bytes for fp32, 8 for 16-bit types),
+// loaded without using them so that several loads can be in flight.
 template <int DT>
-__device__ __forceinline__ int elem_fexp(const void* base, int64_t idx, bool* nf) {
+__device__ __forceinline__ uint4 raw4(const void* base, int64_t idx) {
   if constexpr (DT == kF32) {
-    return fexp_f32(__ldg(reinterpret_cast<const uint32_t*>(base) + idx), nf);
+    return __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const uint32_t*>(base) + idx));
   } else {
-    uint32_t b = __ldg(reinterpret_cast<const unsigned short*>(base) + idx);
-    return DT == kBF16 ? fexp_bf16(b, nf) : fexp_f16(b, nf);
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const unsigned short*>(base) + idx));
+    return make_uint4(v.x, v.y, 0u, 0u);
   }
 }
 
 template <int DT>
-__device__ __forceinline__ void elem_fexp4(const void* base, int64_t idx, bool* nf, int (&e)[4]) {
-  if constexpr (DT == kF32) {
-    uint4 v = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const uint32_t*>(base) + idx));
-    e[0] = fexp_f32(v.x, nf); e[1] = fexp_f32(v.y, nf); e[2] = fexp_f32(v.z, nf); e[3] = fexp_f32(v.w, nf);
-  } else {
-    uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const unsigned short*>(base) + idx));
-    uint32_t h[4] = {v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16};
+__device__ __forceinline__ uint32_t raw1(const void* base, int64_t idx) {
+  if constexpr (DT == kF32) return __ldg(reinterpret_cast<const uint32_t*>(base) + idx);
+  else return __ldg(reinterpret_cast<const unsigned short*>(base) + idx);
+}
+
+// raw4 for columns c .. c + 3 of row offset `row` when some may lie at or
+// beyond C: those read as the encoding 0 (a zero, which never raises a
+// maximum).  Vector load when all four exist and alignment allows.
+template <int DT>
+__device__ __forceinline__ uint4 raw4_guarded(const void* base, int64_t row, int64_t c, int64_t C, bool vec) {
+  if (vec && c + 4 <= C) return raw4<DT>(base, row + c);
+  uint32_t b[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) e[t] = DT == kBF16 ? fexp_bf16(h[t], nf) : fexp_f16(h[t], nf);
+  for (int t = 0; t < 4; ++t) b[t] = (c + t < C) ? raw1<DT>(base, row + c + t) : 0u;
+  if constexpr (DT == kF32) return make_uint4(b[0], b[1], b[2], b[3]);
+  else return make_uint4(b[0] | (b[1] << 16), b[2] | (b[3] << 16), 0u, 0u);
+}
+
+// The four encodings held in a raw4 result.
+template <int DT>
+__device__ __forceinline__ void unpack4(uint4 v, uint32_t (&b)[4]) {
+  if constexpr (DT == kF32) {
+    b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+  } else {
+    b[0] = v.x & 0xFFFFu; b[1] = v.x >> 16; b[2] = v.y & 0xFFFFu; b[3] = v.y >> 16;
   }
 }
 
-__device__ __forceinline__ int block_max(int v, int* red) {
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    v = lane < (int)(blockDim.x >> 5) ? red[lane] : kZeroExp;
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) red[0] = v;
+// frexp exponent of one encoding, with the common case (a normal number:
+// biased exponent field minus the bias, minus one) inline and zero,
+// subnormals and Inf/NaN through the exact decoders.
+template <int DT>
+__device__ __forceinline__ int fexp_fast(uint32_t bits, bool* nf) {
+  if constexpr (DT == kF32) {
+    const uint32_t be = (bits >> 23) & 0xFFu;
+    if (be - 1u < 254u) return (int)be - 126;
+    return fexp_f32(bits, nf);
+  } else if constexpr (DT == kBF16) {
+    const uint32_t be = (bits >> 7) & 0xFFu;
+    if (be - 1u < 254u) return (int)be - 126;
+    return fexp_bf16(bits, nf);
+  } else {
+    const uint32_t be = (bits >> 10) & 0x1Fu;
+    if (be - 1u < 30u) return (int)be - 14;
+    return fexp_f16(bits, nf);
   }
-  __syncthreads();
-  v = red[0];
-  __syncthreads();
-  return v;
 }
+
+// |x| as an integer: for finite values its order is the order of |x|, so
+// the exponent of a max-abs is the exponent of the max of these keys.
+template <int DT>
+__device__ __forceinline__ uint32_t abs_bits(uint32_t bits) {
+  return DT == kF32 ? (bits & 0x7FFFFFFFu) : (bits & 0x7FFFu);
+}
+template <int DT>
+__device__ __forceinline__ int fexp_of_abs_max(uint32_t m, bool* nf) {
+  if constexpr (DT == kF32) return fexp_f32(m, nf);
+  else if constexpr (DT == kBF16) return fexp_bf16(m, nf);
+  else return fexp_f16(m, nf);
+}
+
+// Any value at or below this is "no nonzero entry": shifted exponents of
+// zeros (kZeroExp + a small shift) stay far below it.
+constexpr int kZeroThreshold = kZeroExp / 2;
+
+// ---------------------------------------------------------------- row reduction
 
 // Row reduction.  For each row i of the R x C matrix X:
-//   m_i = max_j ( e(X_ij) + cs * ce_j )          (kZeroExp if the row is 0)
+//   m_i = max_j ( e(X_ij) + cs * ce_j )          (no nonzero entry: zero row)
 // mode kRowOStep:  out[i] = m_i, or 0 for a zero row          (O step)
 // mode kRowIStep:  out[i] holds e_x (a column max of the other operand, from
 //   col_exp_kernel); out[i] = floor((m_i - e_x) / 2), 0 if either is zero
 //   (the I-step exponent of Eq. 6.6).
-template <int DT>
-__global__ void __launch_bounds__(256) row_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
-                                                      const int* ce, int cs, int* out, int mode,
-                                                      int vec_ok, int* status) {
-  __shared__ int red[32];
+// One warp per row, kRowBatch 16-byte loads in flight per lane, and the row
+// maximum a warp shuffle reduction.  Without column shifts (SHIFT false) the
+// row max is taken over |x| as integers and decoded once.
+constexpr int kRowWarps = 8;
+constexpr int kRowBatch = 8;
+
+template <int DT, bool SHIFT>
+__global__ void __launch_bounds__(kRowWarps * 32) row_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
+                                                                 const int* ce, int cs, int* out, int mode,
+                                                                 int vec_ok, int* status) {
   bool nf = false;
-  for (int64_t i = blockIdx.x; i < R; i += gridDim.x) {
-    int m = kZeroExp;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * kRowWarps + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.x * kRowWarps;
+  // the vector path also needs the column exponents 16-byte aligned
+  const bool vec = vec_ok && (!SHIFT || ((uintptr_t)ce % 16 == 0));
+  for (int64_t i = w0; i < R; i += nw) {
+    int m = kZeroExp;       // SHIFT: max shifted exponent
+    uint32_t mb = 0;        // !SHIFT: max |x| key
     const int64_t rowoff = i * ld;
-    if (vec_ok) {
+    auto take = [&](uint32_t bits, int c) {
+      if constexpr (SHIFT) m = max(m, fexp_fast<DT>(bits, &nf) + cs * c);
+      else mb = max(mb, abs_bits<DT>(bits));
+    };
+    int64_t jdone = 0;
+    if (vec) {
       const int64_t C4 = C >> 2;
-      for (int64_t j4 = threadIdx.x; j4 < C4; j4 += blockDim.x) {
-        int e[4];
-        elem_fexp4<DT>(X, rowoff + 4 * j4, &nf, e);
+      int64_t j4 = lane;
+      for (; j4 + 32 * (kRowBatch - 1) < C4; j4 += 32 * kRowBatch) {
+        uint4 v[kRowBatch];
+        int4 c[kRowBatch];
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (e[t] != kZeroExp) m = max(m, e[t] + (ce ? cs * __ldg(ce + 4 * j4 + t) : 0));
+        for (int u = 0; u < kRowBatch; ++u) v[u] = raw4<DT>(X, rowoff + 4 * (j4 + 32 * u));
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u)
+          c[u] = SHIFT ? __ldg(reinterpret_cast<const int4*>(ce + 4 * (j4 + 32 * u))) : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) {
+          uint32_t b[4];
+          unpack4<DT>(v[u], b);
+          take(b[0], c[u].x); take(b[1], c[u].y); take(b[2], c[u].z); take(b[3], c[u].w);
+        }
       }
-      for (int64_t j = 4 * C4 + threadIdx.x; j < C; j += blockDim.x) {
-        int e = elem_fexp<DT>(X, rowoff + j, &nf);
-        if (e != kZeroExp) m = max(m, e + (ce ? cs * __ldg(ce + j) : 0));
+      for (; j4 < C4; j4 += 32) {
+        const uint4 v = raw4<DT>(X, rowoff + 4 * j4);
+        const int4 c = SHIFT ? __ldg(reinterpret_cast<const int4*>(ce + 4 * j4)) : make_int4(0, 0, 0, 0);
+        uint32_t b[4];
+        unpack4<DT>(v, b);
+        take(b[0], c.x); take(b[1], c.y); take(b[2], c.z); take(b[3], c.w);
       }
-    } else {
-      for (int64_t j = threadIdx.x; j < C; j += blockDim.x) {
-        int e = elem_fexp<DT>(X, rowoff + j, &nf);
-        if (e != kZeroExp) m = max(m, e + (ce ? cs * __ldg(ce + j) : 0));
-      }
+      jdone = 4 * C4;
     }
-    m = block_max(m, red);
-    if (threadIdx.x == 0) {
+    for (int64_t j = jdone + lane; j < C; j += 32) take(raw1<DT>(X, rowoff + j), SHIFT ? __ldg(ce + j) : 0);
+    if constexpr (!SHIFT) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+      m = fexp_of_abs_max<DT>(mb, &nf);
+    } else {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) {
+      const bool zero = m <= kZeroThreshold;
       if (mode == kRowOStep) {
-        out[i] = (m == kZeroExp) ? 0 : m;
+        out[i] = zero ? 0 : m;
       } else {
         const int ex = out[i];
-        out[i] = (m == kZeroExp || ex == kZeroExp) ? 0 : ((m - ex) >> 1);  // arithmetic shift = floor
+        out[i] = (zero || ex <= kZeroThreshold) ? 0 : ((m - ex) >> 1);  // arithmetic shift = floor
       }
     }
   }
   if (nf) atomicOr(status, kStatusNonfinite);
 }
+
+// ---------------------------------------------------------------- column reduction
 
 // Column reduction: out[j] = max(out[j], max_i (e(X_ij) + rs * re_i)) over
-// a chunk of rows per CTA (out pre-filled with kZeroExp).  Each thread owns
-// 4 adjacent columns; a warp reads 512 contiguous bytes (fp32) per row.
-template <int DT>
-__global__ void __launch_bounds__(256) col_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
-                                                      const int* re, int rs, int* out, int rows_per_cta,
-                                                      int vec_ok, int* status) {
+// a chunk of rows per CTA (out pre-filled with kZeroExp; nothing is written
+// for a column with no nonzero entry in the chunk).  A CTA covers a span of
+// kColSpan columns with kColGroups groups of 256 threads, each group
+// streaming whole rows of its share of the chunk (16 bytes x kColVec per
+// thread per row, so DRAM sees long contiguous runs) with kColRows rows'
+// loads in flight; the groups' maxima meet in shared memory, so one
+// atomicMax per column covers the CTA's rows.  Without row shifts (SHIFT
+// false) the maximum is taken over |x| as integers and decoded once.
+constexpr int kColVec = 2;
+constexpr int kColSpan = 256 * 4 * kColVec;  // 2048 columns
+constexpr int kColRows = 2;
+constexpr int kColGroups = 4;
+constexpr int kColThreads = 256 * kColGroups;
+constexpr int kColSmem = kColGroups * kColSpan * 4;
+
+template <int DT, bool SHIFT>
+__global__ void __launch_bounds__(kColThreads) col_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
+                                                              const int* re, int rs, int* out, int rows_per_cta,
+                                                              int vec_ok, int* status) {
+  extern __shared__ int red[];  // [kColGroups][kColSpan]
   bool nf = false;
-  const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
-  const int64_t r1 = min(R, r0 + rows_per_cta);
-  if (c0 < C) {
-    int m[4] = {kZeroExp, kZeroExp, kZeroExp, kZeroExp};
-    const bool full = vec_ok && (c0 + 4 <= C);
-    for (int64_t i = r0; i < r1; ++i) {
-      const int sh = re ? rs * __ldg(re + i) : 0;
-      int e[4];
-      if (full) {
-        elem_fexp4<DT>(X, i * ld + c0, &nf, e);
-      } else {
+  const int group = threadIdx.x >> 8, lt = threadIdx.x & 255;
+  const int64_t span0 = (int64_t)blockIdx.x * kColSpan;
+  const int rows_g = rows_per_cta / kColGroups;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta + (int64_t)group * rows_g;
+  const int64_t r1 = min(R, r0 + rows_g);
+  int m[kColVec][4];
+  uint32_t mb[kColVec][4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) e[t] = (c0 + t < C) ? elem_fexp<DT>(X, i * ld + c0 + t, &nf) : kZeroExp;
-      }
+  for (int q = 0; q < kColVec; ++q)
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (e[t] != kZeroExp) m[t] = max(m[t], e[t] + sh);
+    for (int t = 0; t < 4; ++t) {
+      m[q][t] = kZeroExp;
+      mb[q][t] = 0u;
     }
+  auto take = [&](int q, int t, uint32_t bits, int sh) {
+    if constexpr (SHIFT) m[q][t] = max(m[q][t], fexp_fast<DT>(bits, &nf) + sh);
+    else mb[q][t] = max(mb[q][t], abs_bits<DT>(bits));
+  };
+  // column of (q, t): span0 + 1024 q + 4 lt + t
+  const int64_t cbase = span0 + 4 * (int64_t)lt;
+  const bool vec = vec_ok != 0;
+  int64_t i = r0;
+  for (; i + kColRows <= r1; i += kColRows) {
+    uint4 v[kColRows][kColVec];
+    int sh[kColRows];
+#pragma unroll
+    for (int u = 0; u < kColRows; ++u)
+#pragma unroll
+      for (int q = 0; q < kColVec; ++q) v[u][q] = raw4_guarded<DT>(X, (i + u) * ld, cbase + 1024 * q, C, vec);
+#pragma unroll
+    for (int u = 0; u < kColRows; ++u) sh[u] = SHIFT ? rs * __ldg(re + i + u) : 0;
+#pragma unroll
+    for (int u = 0; u < kColRows; ++u)
+#pragma unroll
+      for (int q = 0; q < kColVec; ++q) {
+        uint32_t b[4];
+        unpack4<DT>(v[u][q], b);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) take(q, t, b[t], sh[u]);
+      }
+  }
+  for (; i < r1; ++i) {
+    const int sh = SHIFT ? rs * __ldg(re + i) : 0;
+#pragma unroll
+    for (int q = 0; q < kColVec; ++q) {
+      uint32_t b[4];
+      unpack4<DT>(raw4_guarded<DT>(X, i * ld, cbase + 1024 * q, C, vec), b);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) take(q, t, b[t], sh);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kColVec; ++q)
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      if (c0 + t < C && m[t] != kZeroExp) atomicMax(out + c0 + t, m[t]);
+      red[group * kColSpan + 1024 * q + 4 * lt + t] = SHIFT ? m[q][t] : fexp_of_abs_max<DT>(mb[q][t], &nf);
+  __syncthreads();
+  for (int c = threadIdx.x; c < kColSpan; c += kColThreads) {
+    int e = red[c];
+#pragma unroll
+    for (int g = 1; g < kColGroups; ++g) e = max(e, red[g * kColSpan + c]);
+    if (span0 + c < C && e > kZeroThreshold) atomicMax(out + span0 + c, e);
   }
   if (nf) atomicOr(status, kStatusNonfinite);
 }
-
 
 // Operand preparation (the apply pass of Algs. 1-3, plus blocking): each
 // thread writes 4 consecutive output columns of one output row (row_pad and
@@ -215,12 +346,18 @@ cudaError_t launch_row_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
                            int* out, int mode, int* status, cudaStream_t st) {
   if (R == 0) return cudaSuccess;
   const int vec = vec_aligned(X, ld, dt) ? 1 : 0;
-  const int64_t grid = std::min<int64_t>(R, (int64_t)sm_count() * 16);
+  const int64_t grid = std::min<int64_t>((R + kRowWarps - 1) / kRowWarps, (int64_t)sm_count() * 8);
   dim3 g((unsigned)grid);
+  const int nt = kRowWarps * 32;
+  KernelTimer timer("scale", st);
   switch (dt) {
-    case kF32: row_exp_kernel<kF32><<<g, 256, 0, st>>>(X, R, C, ld, ce, cs, out, mode, vec, status); break;
-    case kBF16: row_exp_kernel<kBF16><<<g, 256, 0, st>>>(X, R, C, ld, ce, cs, out, mode, vec, status); break;
-    default: row_exp_kernel<kF16><<<g, 256, 0, st>>>(X, R, C, ld, ce, cs, out, mode, vec, status); break;
+#define FMM_ROW(DT)                                                                              \
+  (ce ? row_exp_kernel<DT, true><<<g, nt, 0, st>>>(X, R, C, ld, ce, cs, out, mode, vec, status)   \
+      : row_exp_kernel<DT, false><<<g, nt, 0, st>>>(X, R, C, ld, ce, cs, out, mode, vec, status))
+    case kF32: FMM_ROW(kF32); break;
+    case kBF16: FMM_ROW(kBF16); break;
+    default: FMM_ROW(kF16); break;
+#undef FMM_ROW
   }
   return cudaGetLastError();
 }
@@ -228,27 +365,46 @@ cudaError_t launch_row_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
 cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t ld, const int* re, int rs,
                            int* out, int* status, cudaStream_t st) {
   if (C == 0) return cudaSuccess;
-  fill_kernel<<<(unsigned)std::min<int64_t>((C + 255) / 256, 4096), 256, 0, st>>>(out, C, kZeroExp);
+  {
+    KernelTimer fill_timer("scale", st);
+    fill_kernel<<<(unsigned)std::min<int64_t>((C + 255) / 256, 4096), 256, 0, st>>>(out, C, kZeroExp);
+  }
   if (R == 0) return cudaGetLastError();
   const int vec = vec_aligned(X, ld, dt) ? 1 : 0;
-  const int64_t gx = (C + 1023) / 1024;
-  // enough CTAs to cover ~8 per SM; at least 16 rows per CTA
-  int64_t target = (int64_t)sm_count() * 8;
-  int64_t gy = std::max<int64_t>(1, std::min<int64_t>((target + gx - 1) / gx, (R + 15) / 16));
+  const int64_t gx = (C + kColSpan - 1) / kColSpan;
+  // about one CTA per SM in all; each group's rows a multiple of the batch
+  const int64_t target = (int64_t)sm_count();
+  const int64_t unit = (int64_t)kColRows * kColGroups;
+  int64_t gy = std::max<int64_t>(1, std::min<int64_t>((target + gx - 1) / gx, (R + unit - 1) / unit));
   gy = std::min<int64_t>(gy, 65535);
-  const int rows = (int)((R + gy - 1) / gy);
+  const int rows = (int)(((R + gy - 1) / gy + unit - 1) / unit * unit);
   gy = (R + rows - 1) / rows;
   dim3 g((unsigned)gx, (unsigned)gy);
+  static bool attr_done[64][6] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  KernelTimer timer("scale", st);
   switch (dt) {
-    case kF32: col_exp_kernel<kF32><<<g, 256, 0, st>>>(X, R, C, ld, re, rs, out, rows, vec, status); break;
-    case kBF16: col_exp_kernel<kBF16><<<g, 256, 0, st>>>(X, R, C, ld, re, rs, out, rows, vec, status); break;
-    default: col_exp_kernel<kF16><<<g, 256, 0, st>>>(X, R, C, ld, re, rs, out, rows, vec, status); break;
+#define FMM_COL(DT, I)                                                                                       \
+  if (!attr_done[dev][2 * I]) {                                                                             \
+    cudaFuncSetAttribute(col_exp_kernel<DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kColSmem);   \
+    cudaFuncSetAttribute(col_exp_kernel<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kColSmem);  \
+    attr_done[dev][2 * I] = true;                                                                           \
+  }                                                                                                          \
+  if (re) col_exp_kernel<DT, true><<<g, kColThreads, kColSmem, st>>>(X, R, C, ld, re, rs, out, rows, vec, status); \
+  else col_exp_kernel<DT, false><<<g, kColThreads, kColSmem, st>>>(X, R, C, ld, re, rs, out, rows, vec, status);
+    case kF32: { FMM_COL(kF32, 0) break; }
+    case kBF16: { FMM_COL(kBF16, 1) break; }
+    default: { FMM_COL(kF16, 2) break; }
+#undef FMM_COL
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_zero_sentinel(int* p, int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  KernelTimer timer("scale", st);
   zero_sentinel_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(p, n);
   return cudaGetLastError();
 }
@@ -259,6 +415,7 @@ cudaError_t launch_prepare(const void* X, int dt, int64_t R, int64_t C, int64_t 
   if (Rp == 0 || Cp == 0) return cudaSuccess;
   const int64_t total = Rp * (Cp / 4);
   const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
+  KernelTimer timer("prepare", st);
   switch (dt) {
     case kF32:
       prepare_kernel<kF32, false><<<grid, 256, 0, st>>>(X, R, C, ld, row_blk, row_pad, col_blk, col_pad, re, rs, ce,
@@ -278,6 +435,7 @@ cudaError_t launch_prepare(const void* X, int dt, int64_t R, int64_t C, int64_t 
 
 cudaError_t launch_fill(int* p, int64_t n, int v, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  KernelTimer timer("scale", st);
   fill_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(p, n, v);
   return cudaGetLastError();
 }
