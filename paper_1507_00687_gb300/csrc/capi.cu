@@ -137,10 +137,10 @@ static bool make_map(CUtensorMap* m, const void* ptr, int dt, int64_t rows, int6
 }
 
 // A 2-D tensor map over a row-major 16-bit matrix (rows x cols, ld) with a
-// box of 64 columns (128 bytes) x box_rows rows, landing in shared memory in
-// the 128-byte-swizzle layout the K-major MMA descriptors read.
-static bool make_map_sw128(CUtensorMap* m, const void* ptr, bool f16, int64_t rows, int64_t cols, int64_t ld,
-                           int box_rows) {
+// box of box_cols (32 or 64: 64 or 128 bytes) x box_rows, landing in shared
+// memory in the 64- or 128-byte-swizzle layout the MMA descriptors read.
+static bool make_map_sw(CUtensorMap* m, const void* ptr, bool f16, int64_t rows, int64_t cols, int64_t ld,
+                        int box_cols, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) {
     t_last_error = "cuTensorMapEncodeTiled unavailable";
@@ -148,11 +148,12 @@ static bool make_map_sw128(CUtensorMap* m, const void* ptr, bool f16, int64_t ro
   }
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                   const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     t_last_error = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
     return false;
@@ -309,11 +310,12 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
   DirectArgs d;
   std::memset(&d, 0, sizeof(d));
   const bool f16 = p->leaf_format == FMM_LEAF_F16;
-  // K-major planes: rows (plane, leaf, t), k contiguous, box 64 k x tile t;
-  // MN-major planes: rows (plane, leaf, k), t contiguous, box 64 t x 64 k.
+  // K-major planes: rows (plane, leaf, t), k contiguous, box BK k x tile t;
+  // MN-major planes: rows (plane, leaf, k), t contiguous, box 64 t x BK k.
+  const int bk_step = direct_gemm_bk(p->leaf_format);
   auto map = [&](CUtensorMap* m, const Source& s, char* buf, int64_t tp, int tile) {
-    return s.kcontig ? make_map_sw128(m, buf, f16, planes * R * tp, kp, kp, tile)
-                     : make_map_sw128(m, buf, f16, planes * R * kp, tp, tp, 64);
+    return s.kcontig ? make_map_sw(m, buf, f16, planes * R * tp, kp, kp, bk_step, tile)
+                     : make_map_sw(m, buf, f16, planes * R * kp, tp, tp, 64, bk_step);
   };
   if (!map(&d.map_a, x, wa, tp_a, 128) || !map(&d.map_b, y, wb, tp_b, bn)) return FMM_ERR_CUDA;
   d.a_mn = x.kcontig ? 0 : 1;

@@ -157,18 +157,30 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Same for 64-byte rows (32 x 16-bit along K): 8-row groups 512 bytes
+// apart, the 64-byte swizzle pattern.  Tile bases are 512-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
+  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)4 << 61;                    // 64-byte swizzle
+  return d;
+}
+
 // Shared-memory matrix descriptor for an MN-major operand tile in the
 // 128-byte-swizzle canonical layout: for each k a 128-byte row of 64
 // consecutive M (or N) elements, 8-k groups 1024 bytes apart (stride byte
-// offset), 64-element M/N chunks 8192 bytes apart (leading byte offset),
-// 16-byte units XOR-permuted by (k mod 8).
-__device__ __forceinline__ uint64_t smem_desc_mn_sw128(uint32_t saddr) {
+// offset), 64-element M/N chunks `chunk_bytes` apart (leading byte offset;
+// 128 bytes x the tile's k extent), 16-byte units XOR-permuted by (k mod 8).
+__device__ __forceinline__ uint64_t smem_desc_mn_sw128(uint32_t saddr, uint32_t chunk_bytes = 8192) {
   uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)(8192 >> 4) << 16;          // leading byte offset: next 64-wide M/N chunk
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-k group
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);    // start address
+  d |= (uint64_t)((chunk_bytes >> 4) & 0x3FFFu) << 16;  // leading byte offset: next 64-wide M/N chunk
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: next 8-k group
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
   return d;
 }
 

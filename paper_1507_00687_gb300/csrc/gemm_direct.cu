@@ -37,14 +37,16 @@ using gemm::mbar_arrive_expect_tx;
 using gemm::tma_load_2d;
 
 constexpr int BM = 128;
-constexpr int BK = 64;
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;
 constexpr int kTmaWarp = 5;
 constexpr int kThreads = 6 * 32;
 
+// K per stage: 64 (128-byte rows); the kernel also supports 32 (64-byte
+// rows, a deeper ring of smaller stages), which measured slower.
 template <int FMT, int BN>
 struct Cfg {
+  static constexpr int BK = 64;
   static constexpr int kSplit = FMT == FMM_LEAF_BF16X3 ? 2 : 1;
   static constexpr int kATile = BM * BK * 2;
   static constexpr int kBTile = BN * BK * 2;
@@ -55,28 +57,34 @@ struct Cfg {
   static constexpr int kSmem = kStages * kStage + kBarBytes + 1024;  // + alignment slack
 };
 
-// Operand tile of `rows` t x 64 k from plane row block `blk` (= plane R +
-// leaf) at t offset t0, k offset k0, into dst.
-template <bool MN>
+// Operand tile of `rows` t x BK k from plane row block `blk` (= plane R +
+// leaf) at t offset t0, k offset k0, into dst.  MN-major: one 64 t x BK k
+// box (BK rows of 128 bytes) per 64 t.
+template <bool MN, int BK>
 __device__ __forceinline__ void load_tile(uint8_t* dst, const CUtensorMap* map, int rows, int64_t blk, int64_t tp,
                                           int64_t kp, int64_t t0, int64_t k0, uint64_t* bar) {
   if constexpr (MN) {
     for (int c = 0; c < rows / 64; ++c)
-      tma_load_2d(dst + c * 8192, map, (int32_t)(t0 + 64 * c), (int32_t)(blk * kp + k0), bar);
+      tma_load_2d(dst + c * (BK * 128), map, (int32_t)(t0 + 64 * c), (int32_t)(blk * kp + k0), bar);
   } else {
     tma_load_2d(dst, map, (int32_t)k0, (int32_t)(blk * tp + t0), bar);
   }
 }
 
-// Descriptor of the 16-wide k step k16 of an operand tile at saddr.
-template <bool MN>
+// Descriptor of the 16-wide k step k16 of an operand tile at saddr:
+// MN-major advances two 8-k groups (2048 bytes); K-major advances 32 bytes
+// inside the swizzled row (128-byte rows for BK 64, 64-byte rows for 32).
+template <bool MN, int BK>
 __device__ __forceinline__ uint64_t tile_desc(uint32_t saddr, int k16) {
-  return MN ? smem_desc_mn_sw128(saddr + k16 * 2048) : smem_desc_sw128(saddr + k16 * 32);
+  if constexpr (MN) return smem_desc_mn_sw128(saddr + k16 * 2048, BK * 128);
+  else if constexpr (BK == 64) return smem_desc_sw128(saddr + k16 * 32);
+  else return smem_desc_sw64(saddr + k16 * 32);
 }
 
 template <int FMT, int BN, bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_constant__ DirectArgs args) {
   using C = Cfg<FMT, BN>;
+  constexpr int BK = C::BK;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -131,12 +139,13 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
         uint8_t* st = smem + stage * C::kStage;
         mbar_arrive_expect_tx(&full[stage], (uint32_t)C::kStage);
         const int64_t k0 = kt * BK, ta = tm * BM, tb = tn * BN;
-        load_tile<A_MN>(st, &args.map_a, BM, leaf, args.tp_a, args.kp, ta, k0, &full[stage]);
-        load_tile<B_MN>(st + C::kSplit * C::kATile, &args.map_b, BN, leaf, args.tp_b, args.kp, tb, k0, &full[stage]);
+        load_tile<A_MN, BK>(st, &args.map_a, BM, leaf, args.tp_a, args.kp, ta, k0, &full[stage]);
+        load_tile<B_MN, BK>(st + C::kSplit * C::kATile, &args.map_b, BN, leaf, args.tp_b, args.kp, tb, k0,
+                            &full[stage]);
         if constexpr (C::kSplit == 2) {
-          load_tile<A_MN>(st + C::kATile, &args.map_a, BM, NL + leaf, args.tp_a, args.kp, ta, k0, &full[stage]);
-          load_tile<B_MN>(st + 2 * C::kATile + C::kBTile, &args.map_b, BN, NL + leaf, args.tp_b, args.kp, tb, k0,
-                          &full[stage]);
+          load_tile<A_MN, BK>(st + C::kATile, &args.map_a, BM, NL + leaf, args.tp_a, args.kp, ta, k0, &full[stage]);
+          load_tile<B_MN, BK>(st + 2 * C::kATile + C::kBTile, &args.map_b, BN, NL + leaf, args.tp_b, args.kp, tb, k0,
+                              &full[stage]);
         }
         armed |= 1u << stage;
         armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
@@ -178,11 +187,11 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
 #pragma unroll
             for (int k16 = 0; k16 < BK / 16; ++k16) {
               const uint32_t acc = (kt > 0 || k16 > 0) ? 1u : 0u;
-              const uint64_t ah = tile_desc<A_MN>(a_hi, k16), bh = tile_desc<B_MN>(b_hi, k16);
+              const uint64_t ah = tile_desc<A_MN, BK>(a_hi, k16), bh = tile_desc<B_MN, BK>(b_hi, k16);
               mma_f16(d_tmem, ah, bh, idesc, acc);
               if constexpr (C::kSplit == 2) {
-                mma_f16(d_tmem, ah, tile_desc<B_MN>(b_lo, k16), idesc, 1u);
-                mma_f16(d_tmem, tile_desc<A_MN>(a_lo, k16), bh, idesc, 1u);
+                mma_f16(d_tmem, ah, tile_desc<B_MN, BK>(b_lo, k16), idesc, 1u);
+                mma_f16(d_tmem, tile_desc<A_MN, BK>(a_lo, k16), bh, idesc, 1u);
               }
             }
             mma_commit(&empty[stage]);
@@ -254,7 +263,7 @@ cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  if (a.tp_a % BM != 0 || a.tp_b % BN != 0 || a.kp % BK != 0) return cudaErrorInvalidValue;
+  if (a.tp_a % BM != 0 || a.tp_b % BN != 0 || a.kp % C::BK != 0) return cudaErrorInvalidValue;
   const int64_t ntiles = (a.tp_a / BM) * (a.tp_b / BN);
   if (ntiles == 0) return cudaSuccess;
   const int64_t grid = std::min<int64_t>(ntiles, device_sm_count());
@@ -283,6 +292,10 @@ cudaError_t launch_bn(const DirectArgs& a, int fmt, cudaStream_t st) {
 }
 
 }  // namespace direct
+
+int direct_gemm_bk(int leaf_format) {
+  return leaf_format == FMM_LEAF_BF16X3 ? direct::Cfg<FMM_LEAF_BF16X3, 256>::BK : direct::Cfg<FMM_LEAF_BF16, 256>::BK;
+}
 
 cudaError_t launch_direct_gemm(const DirectArgs& a, int leaf_format, int bn, cudaStream_t st) {
   return bn == 256 ? direct::launch_bn<256>(a, leaf_format, st) : direct::launch_bn<128>(a, leaf_format, st);

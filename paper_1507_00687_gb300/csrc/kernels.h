@@ -119,6 +119,10 @@ struct DirectArgs {
 // bn: tile width along N (128 or 256).
 cudaError_t launch_direct_gemm(const DirectArgs& args, int leaf_format, int bn, cudaStream_t st);
 
+// K extent of one pipeline stage of that kernel (the k extent of its
+// operand boxes): 32 for the hi+lo split, else 64.
+int direct_gemm_bk(int leaf_format);
+
 // Launch the fused recursive-fast-multiply kernel for a flattened plan.
 cudaError_t launch_fused_gemm(const GemmArgs& args, int leaf_format, cudaStream_t st);
 
