@@ -170,10 +170,24 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
  *     multiply kernel then streams them with bulk tensor copies;
  *   FMM_SCHEDULE_AUTO        (default) the pass schedule when the given
  *     workspace holds it, else the load-stage schedule.
+ * Under the pass schedule the output combination C_k += sum w M_r (Eq. 4.4,
+ * third line) runs either in the multiply kernel's epilogue (one CTA per
+ * output tile position visits every leaf) or, when one leaf's tiles are too
+ * few to occupy the GPU (deep recursion, small products), over stored leaf
+ * products: every (leaf, tile) pair is a unit of work, the epilogue stores
+ * M_r in the workspace and a bandwidth-bound pass forms C.  Both give the
+ * same result (the same operations per element, in leaf order).
+ * FMM_SCHEDULE_PASS (and AUTO) use stored products when the workspace
+ * holds them (measured faster on GB300 at every size tried);
+ * FMM_SCHEDULE_PASS_EPILOGUE and FMM_SCHEDULE_PASS_PRODUCTS force one form.
+ * Stored products need a plan of more than one leaf and at most 96 C
+ * blocks; otherwise the epilogue form runs.
  */
 #define FMM_SCHEDULE_AUTO 0
 #define FMM_SCHEDULE_LOAD_STAGE 1
 #define FMM_SCHEDULE_PASS 2
+#define FMM_SCHEDULE_PASS_EPILOGUE 3
+#define FMM_SCHEDULE_PASS_PRODUCTS 4
 
 /* Set the plan's schedule (FMM_SCHEDULE_*); FMM_ERR_ARG for other values.
  * The gradient products of fmm_multiply_backward follow it. */

@@ -12,7 +12,8 @@ from . import _native as N
 from .rules import BaseRule, get as get_rule
 
 LEAF = {"bf16": N.LEAF_BF16, "fp16": N.LEAF_F16, "bf16x3": N.LEAF_BF16X3}
-SCHEDULE = {"auto": N.SCHEDULE_AUTO, "load_stage": N.SCHEDULE_LOAD_STAGE, "pass": N.SCHEDULE_PASS}
+SCHEDULE = {"auto": N.SCHEDULE_AUTO, "load_stage": N.SCHEDULE_LOAD_STAGE, "pass": N.SCHEDULE_PASS,
+            "pass_epilogue": N.SCHEDULE_PASS_EPILOGUE, "pass_products": N.SCHEDULE_PASS_PRODUCTS}
 DTYPE = {torch.float32: N.DT_F32, torch.bfloat16: N.DT_BF16, torch.float16: N.DT_F16}
 
 
@@ -40,7 +41,8 @@ class Plan:
     level l+1, classical leaves, leaf products in ``leaf`` format.
     ``schedule`` (fmm_plan_set_schedule): "auto", "load_stage" (S_r, T_r
     formed in the multiply kernel's load stage) or "pass" (formed by a
-    combination pass into the workspace)."""
+    combination pass into the workspace; "pass_epilogue" / "pass_products"
+    force where the output combination runs)."""
 
     def __init__(self, rules: Sequence[Union[str, BaseRule]], leaf: str = "bf16x3", schedule: str = "auto"):
         self.rules = [get_rule(r) if isinstance(r, str) else r for r in rules]

@@ -69,8 +69,10 @@ static fmm_status ensure_uploaded(const Plan* cp) {
   if (p->dev) return dev == p->device ? FMM_OK : FMM_ERR_CUDA;
   const size_t bytes = p->host.size() * sizeof(LeafDesc);
   LeafDesc* d = nullptr;
-  if (cudaMalloc(&d, bytes) != cudaSuccess) return FMM_ERR_CUDA;
-  if (cudaMemcpy(d, p->host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMalloc(&d, bytes + p->lists.size() * 4) != cudaSuccess) return FMM_ERR_CUDA;
+  if (cudaMemcpy(d, p->host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(reinterpret_cast<char*>(d) + bytes, p->lists.data(), p->lists.size() * 4, cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
     cudaFree(d);
     return FMM_ERR_CUDA;
   }
@@ -252,13 +254,20 @@ static int64_t combined_bytes(int64_t T, int64_t Kd, int64_t pt, int64_t pk, int
   return round_up(planes * leaves * round_up(ceil_div(T, pt), tile) * round_up(ceil_div(Kd, pk), 64) * 2, 256);
 }
 
+// Bytes of the stored leaf products (fp32, R padded leaf blocks).
+static int64_t products_bytes(int64_t Tx, int64_t Ty, int64_t ptx, int64_t pty, int64_t leaves, int64_t tile_n) {
+  return round_up(leaves * round_up(ceil_div(Tx, ptx), 128) * round_up(ceil_div(Ty, pty), tile_n) * 4, 256);
+}
+
 // Workspace of the pass schedule for the product X (T_x x Kd) Y (Kd x T_y)
-// (upper bound over the tile width).
+// (upper bound over the tile width; with room for stored leaf products
+// when the plan has more than one leaf).
 static int64_t pass_bytes(const Plan* p, int64_t Tx, int64_t Kd, int64_t Ty, int64_t ptx, int64_t pk,
                           int64_t pty) {
   const int planes = p->leaf_format == FMM_LEAF_BF16X3 ? 2 : 1;
   return combined_bytes(Tx, Kd, ptx, pk, p->leaves, planes, 128) +
-         combined_bytes(Ty, Kd, pty, pk, p->leaves, planes, 256);
+         combined_bytes(Ty, Kd, pty, pk, p->leaves, planes, 256) +
+         (p->leaves > 1 ? products_bytes(Tx, Ty, ptx, pty, p->leaves, 256) : 0);
 }
 
 // The pass schedule: the combination pass writes S_r (from x) and T_r (from
@@ -276,6 +285,15 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
   if (!ws || (uintptr_t)ws % 256 != 0 || (int64_t)ws_bytes < bytes_a + bytes_b) return FMM_ERR_WORKSPACE;
   char* wa = static_cast<char*>(ws);
   char* wb = wa + bytes_a;
+  // Stored leaf products unless the epilogue form is asked for: measured
+  // faster at every size (every SM gets (leaf, tile) units; the fused
+  // epilogue leaves SMs idle when tiles per leaf are few, and its C
+  // read-modify-writes cost more than one more bandwidth pass).
+  const int64_t bytes_m = round_up(R * tp_a * tp_b * 4, 256);
+  const bool want_m = p->schedule != FMM_SCHEDULE_PASS_EPILOGUE;
+  const bool store_m = want_m && R > 1 && p->pm * p->pn <= kMaxOutBlocks &&
+                       (int64_t)ws_bytes >= bytes_a + bytes_b + bytes_m;
+  float* mbuf = store_m ? reinterpret_cast<float*>(wb + bytes_b) : nullptr;
   // One side: the source's memory rows follow t (k-contiguous) or k.
   auto combine = [&](const Source& s, int64_t bt, int64_t tp, int side, char* out) {
     CombineArgs ca;
@@ -298,6 +316,11 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
     ca.leaves = leaves;
     ca.num_leaves = R;
     ca.side = side;
+    const int32_t* lists = reinterpret_cast<const int32_t*>(leaves + R);
+    ca.t_start = lists + p->list_off[side];
+    ca.t_blk = ca.t_start + R + 1;
+    ca.t_coef = reinterpret_cast<const float*>(ca.t_blk + p->list_nnz[side]);
+    ca.t_nnz = p->list_nnz[side];
     ca.blk_t_shift = side == 0 ? 16 : 0;
     ca.blk_k_shift = side == 0 ? 0 : 16;
     ca.out = out;
@@ -326,15 +349,35 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
   d.tp_a = tp_a;
   d.tp_b = tp_b;
   d.kp = kp;
+  d.mbuf = mbuf;
   d.status = status;
   d.timeout_ns = timeout_ns();
-  return cuda_ok(launch_direct_gemm(d, p->leaf_format, bn, st), "multiply launch") ? FMM_OK : FMM_ERR_CUDA;
+  if (!cuda_ok(launch_direct_gemm(d, p->leaf_format, bn, st), "multiply launch")) return FMM_ERR_CUDA;
+  if (!store_m) return FMM_OK;
+  OutArgs o;
+  o.mbuf = mbuf;
+  o.tp_a = tp_a;
+  o.tp_b = tp_b;
+  o.c = c;
+  o.leaves = leaves;
+  o.num_leaves = R;
+  o.c_blocks = p->pm * p->pn;
+  o.pn = p->pn;
+  {
+    const int32_t* lists = reinterpret_cast<const int32_t*>(leaves + R);
+    o.c_start = lists + p->list_off[2];
+    o.c_blk = o.c_start + R + 1;
+    o.c_coef = reinterpret_cast<const float*>(o.c_blk + p->list_nnz[2]);
+    o.c_nnz = p->list_nnz[2];
+  }
+  return cuda_ok(launch_out_combine(o, st), "output combination pass") ? FMM_OK : FMM_ERR_CUDA;
 }
 
 // Run the flattened plan p: C (M x N) = X (M x K) Y (K x N) with X, Y given
 // as sources (X: t = M, k = K; Y: t = N, k = K).  leaves: a device copy of
-// the plan's leaf table to use instead of the plan's own upload (NULL: the
-// plan's own, uploaded on first use).
+// the plan's tables (the LeafDesc array followed by the term lists) to use
+// instead of the plan's own upload (NULL: the plan's own, uploaded on first
+// use).
 static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, float* C, int64_t ldc, int64_t M,
                            int64_t K, int64_t N, const int* eA, const int* eB, void* ws, size_t ws_bytes,
                            cudaStream_t st, const LeafDesc* leaves = nullptr) {
@@ -360,7 +403,8 @@ static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, floa
   c.eA = eA;
   c.eB = eB;
   c.vec_ok = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0) && (c.bn % 4 == 0) ? 1 : 0;
-  const bool pass = p->schedule == FMM_SCHEDULE_PASS ||
+  const bool pass = p->schedule == FMM_SCHEDULE_PASS || p->schedule == FMM_SCHEDULE_PASS_EPILOGUE ||
+                    p->schedule == FMM_SCHEDULE_PASS_PRODUCTS ||
                     (p->schedule == FMM_SCHEDULE_AUTO && ws && (uintptr_t)ws % 256 == 0 &&
                      (int64_t)ws_bytes >= pass_bytes(p, M, K, N, p->pm, p->pk, p->pn));
   if (pass) return run_pass(p, x, y, c, leaves, status, ws, ws_bytes, st);
@@ -451,8 +495,7 @@ fmm_status fmm_plan_destroy(fmm_plan_t plan) {
 
 fmm_status fmm_plan_set_schedule(fmm_plan_t plan, int schedule) {
   Plan* p = reinterpret_cast<Plan*>(plan);
-  if (!p || (schedule != FMM_SCHEDULE_AUTO && schedule != FMM_SCHEDULE_LOAD_STAGE && schedule != FMM_SCHEDULE_PASS))
-    return FMM_ERR_ARG;
+  if (!p || schedule < FMM_SCHEDULE_AUTO || schedule > FMM_SCHEDULE_PASS_PRODUCTS) return FMM_ERR_ARG;
   p->schedule = schedule;
   if (p->grad_a) p->grad_a->schedule = schedule;
   if (p->grad_b) p->grad_b->schedule = schedule;
@@ -630,7 +673,8 @@ fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, con
     return FMM_ERR_SHAPE;
   if (M == 0 || N == 0) return FMM_OK;
   // The size check comes before any device call.
-  const size_t table_bytes = p->host.size() * sizeof(LeafDesc);
+  const size_t leaf_bytes = p->host.size() * sizeof(LeafDesc);
+  const size_t table_bytes = leaf_bytes + p->lists.size() * 4;
   const size_t table = (size_t)round_up((int64_t)table_bytes, 256);
   const size_t need = table + (size_t)prepared_bytes(M, K, p->pm, p->pk) + (size_t)prepared_bytes(N, K, p->pn, p->pk);
   if (need > FMM_NOALLOC_SCRATCH_BYTES) {
@@ -641,8 +685,11 @@ fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, con
   char* scratch = noalloc_scratch();
   if (!scratch) return FMM_ERR_CUDA;
   cudaStream_t st = as_stream(stream);
-  if (!cuda_ok(cudaMemcpyAsync(scratch, p->host.data(), table_bytes, cudaMemcpyHostToDevice, st),
-               "leaf table copy into the no-alloc scratch"))
+  if (!cuda_ok(cudaMemcpyAsync(scratch, p->host.data(), leaf_bytes, cudaMemcpyHostToDevice, st),
+               "leaf table copy into the no-alloc scratch") ||
+      !cuda_ok(cudaMemcpyAsync(scratch + leaf_bytes, p->lists.data(), p->lists.size() * 4, cudaMemcpyHostToDevice,
+                               st),
+               "term list copy into the no-alloc scratch"))
     return FMM_ERR_CUDA;
   // Operands as in fmm_multiply.
   const Source a{A, lda, in_dtype, true, M, K, p->pm, p->pk, eA, -1, d, +1};

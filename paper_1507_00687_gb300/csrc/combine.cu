@@ -19,6 +19,8 @@
 // them; every output element (padding included) is written.  HBM-bound:
 // each input element is read once from DRAM, each output element written
 // once.
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -164,22 +166,37 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs a) 
   }
 }
 
-// Staged form for plans with few input blocks (at most kMaxStaged): every
-// input block's TR x 64 tile is loaded and scaled once into shared memory
-// (in block order), then each leaf's terms are summed from there in term
-// order -- the same arithmetic as above with each element scaled once
-// instead of once per use.  TR * 16 threads, one row of 4 columns each.
-constexpr int kMaxStaged = 16;
+// Staged form for plans with at most kMaxStaged input blocks: every input
+// block's TR x 64 tile is loaded and scaled once into shared memory (in
+// block order), the side's compact term list is copied there too, and each
+// leaf's terms are summed from shared memory in term order -- the same
+// arithmetic as above with each element scaled once instead of once per
+// use.  TR * 16 threads, one row of 4 columns each.
+constexpr int kMaxStaged = 64;
 
 template <int DT, int FMT, int TR>
 __global__ void __launch_bounds__(TR * 16) combine_staged_kernel(const CombineArgs a) {
-  extern __shared__ float4 tile4[];  // [block][TR][16]
+  extern __shared__ float4 tile4[];  // [block][TR][16], then the term list
   const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * kTC;
   const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15, tc = tq * 4;
   const int es = DT == kF32 ? 4 : 2;
   const bool vec_ok = ((uintptr_t)a.src % (4 * es) == 0) && (a.ld % 4 == 0) && (a.b_cols % 4 == 0) &&
                       (!a.ce || (uintptr_t)a.ce % 16 == 0);
   const int n_rb = (int)a.n_rb, n_cb = (int)a.n_cb;
+  const int nb = n_rb * n_cb;
+  const int64_t R = a.num_leaves;
+  const int nnz = (int)a.t_nnz;
+  // term list in shared memory: float4 offset of the term's block tile, coef
+  int* toff = reinterpret_cast<int*>(tile4 + nb * TR * 16);
+  float* tcoef = reinterpret_cast<float*>(toff + nnz);
+  int* tstart = reinterpret_cast<int*>(tcoef + nnz);
+  for (int i = threadIdx.x; i < nnz; i += TR * 16) {
+    const int32_t blk = __ldg(a.t_blk + i);
+    const int bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
+    toff[i] = (a.t_rows ? bt * n_cb + bk : bk * n_cb + bt) * TR * 16;
+    tcoef[i] = __ldg(a.t_coef + i);
+  }
+  for (int64_t i = threadIdx.x; i <= R; i += TR * 16) tstart[i] = __ldg(a.t_start + i);
   const int64_t lr = r0 + tr, lc = c0 + tc;
   for (int rb = 0; rb < n_rb; ++rb) {
     const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows);
@@ -215,48 +232,64 @@ __global__ void __launch_bounds__(TR * 16) combine_staged_kernel(const CombineAr
     }
   }
   __syncthreads();
-  const int64_t R = a.num_leaves;
   unsigned short* out = static_cast<unsigned short*>(a.out);
   const int64_t plane = R * a.p_rows * a.p_cols;
-  for (int64_t r = 0; r < R; ++r) {
-    const LeafDesc* L = a.leaves + r;
-    const int n = a.side == 0 ? __ldg(&L->na) : __ldg(&L->nb);
+  const int me = tr * 16 + tq;
+  unsigned short* orow = out + lr * a.p_cols + lc;
+  const int64_t leaf_stride = a.p_rows * a.p_cols;
+  int t = tstart[0];
+  for (int64_t r = 0; r < R; ++r, orow += leaf_stride) {
+    const int t1 = tstart[r + 1];
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int t = 0; t < n; ++t) {
-      const int32_t blk = a.side == 0 ? __ldg(&L->a_blk[t]) : __ldg(&L->b_blk[t]);
-      const float coef = a.side == 0 ? __ldg(&L->a_coef[t]) : __ldg(&L->b_coef[t]);
-      const int bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
-      const int b = a.t_rows ? bt * n_cb + bk : bk * n_cb + bt;
-      const float4 v = tile4[(b * TR + tr) * 16 + tq];
+    for (; t < t1; ++t) {
+      const float coef = tcoef[t];
+      const float4 v = tile4[toff[t] + me];
       acc[0] = fmaf(coef, v.x, acc[0]);
       acc[1] = fmaf(coef, v.y, acc[1]);
       acc[2] = fmaf(coef, v.z, acc[2]);
       acc[3] = fmaf(coef, v.w, acc[3]);
     }
-    const int64_t off = (r * a.p_rows + lr) * a.p_cols + lc;
-    store4<FMT>(out + off, out + off + plane, acc);
+    store4<FMT>(orow, orow + plane, acc);
   }
+}
+
+// Shared memory of the staged form: block tiles plus the term list.
+inline size_t staged_smem(int nb, int tr, int64_t nnz, int64_t leaves) {
+  return (size_t)nb * tr * 256 + (size_t)nnz * 8 + (size_t)(leaves + 1) * 4;
+}
+constexpr size_t kStagedSmemMax = 200 * 1024;
+
+template <int DT, int FMT, int TR>
+void launch_staged_tr(const CombineArgs& a, int nb, cudaStream_t st) {
+  static bool attr_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_done[dev]) {
+    cudaFuncSetAttribute(combine_staged_kernel<DT, FMT, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kStagedSmemMax);
+    attr_done[dev] = true;
+  }
+  combine_staged_kernel<DT, FMT, TR><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / TR)), TR * 16,
+                                       staged_smem(nb, TR, a.t_nnz, a.num_leaves), st>>>(a);
 }
 
 template <int DT, int FMT>
 void launch_staged(const CombineArgs& a, int nb, cudaStream_t st) {
-  // TR rows per CTA so that the staged tiles take at most 48 KB
-  if (nb <= 6) {
-    combine_staged_kernel<DT, FMT, 32><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / 32)), 512,
-                                         nb * 32 * 256, st>>>(a);
-  } else if (nb <= 12) {
-    combine_staged_kernel<DT, FMT, 16><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / 16)), 256,
-                                         nb * 16 * 256, st>>>(a);
-  } else {
-    combine_staged_kernel<DT, FMT, 8><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / 8)), 128,
-                                        nb * 8 * 256, st>>>(a);
-  }
+  // TR rows per CTA so that the staged tiles take at most 32 KB
+  if (nb <= 4) launch_staged_tr<DT, FMT, 32>(a, nb, st);
+  else if (nb <= 8) launch_staged_tr<DT, FMT, 16>(a, nb, st);
+  else if (nb <= 16) launch_staged_tr<DT, FMT, 8>(a, nb, st);
+  else if (nb <= 32) launch_staged_tr<DT, FMT, 4>(a, nb, st);
+  else launch_staged_tr<DT, FMT, 2>(a, nb, st);
 }
 
 template <int DT, int FMT>
 void launch_fmt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
   const int64_t nb = a.n_rb * a.n_cb;
-  if (nb <= kMaxStaged) launch_staged<DT, FMT>(a, (int)nb, st);
+  const int tr = nb <= 4 ? 32 : nb <= 8 ? 16 : nb <= 16 ? 8 : nb <= 32 ? 4 : 2;
+  if (nb <= kMaxStaged && staged_smem((int)nb, tr, a.t_nnz, a.num_leaves) <= kStagedSmemMax)
+    launch_staged<DT, FMT>(a, (int)nb, st);
   else combine_kernel<DT, FMT><<<grid, kThreads, 0, st>>>(a);
 }
 
@@ -271,7 +304,118 @@ cudaError_t launch_dt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Output combination pass over stored leaf products M_r: one CTA covers a
+// TR x 64 position tile of every C block and walks the leaves in order,
+// keeping one fp32 accumulator per (C block, position) in shared memory
+// (each thread only ever touches its own positions); then writes C.  The
+// per-element arithmetic is the fused epilogue's: s = w 2^eA_i,
+// x = s M 2^eB_j, C = x for the first leaf touching the block, else C + x.
+// The C-side term list sits in shared memory; the M_r loads of kOutBatch
+// leaves are issued together.
+constexpr int kOutBatch = 4;
+
+template <int TR>
+__global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
+  extern __shared__ float4 acc4[];  // [c_blocks][TR][16], then the term list
+  const EpilogueArgs& c = a.c;
+  const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15;
+  const int64_t lr = (int64_t)blockIdx.y * TR + tr, lc = (int64_t)blockIdx.x * kTC + tq * 4;
+  const int pn = (int)a.pn;
+  const int64_t R = a.num_leaves;
+  const int nnz = (int)a.c_nnz;
+  int* cblk = reinterpret_cast<int*>(acc4 + a.c_blocks * TR * 16);
+  float* ccoef = reinterpret_cast<float*>(cblk + nnz);
+  int* cstart = reinterpret_cast<int*>(ccoef + nnz);
+  for (int i = threadIdx.x; i < nnz; i += TR * 16) {
+    cblk[i] = __ldg(a.c_blk + i);
+    ccoef[i] = __ldg(a.c_coef + i);
+  }
+  for (int64_t i = threadIdx.x; i <= R; i += TR * 16) cstart[i] = __ldg(a.c_start + i);
+  __syncthreads();
+  const int me = tr * 16 + tq;
+  const float* mcol = a.mbuf + lr * a.tp_b + lc;
+  const int64_t leaf_stride = a.tp_a * a.tp_b;
+  for (int64_t r0 = 0; r0 < R; r0 += kOutBatch) {
+    float4 m[kOutBatch];
+#pragma unroll
+    for (int u = 0; u < kOutBatch; ++u)
+      if (r0 + u < R) m[u] = __ldg(reinterpret_cast<const float4*>(mcol + (r0 + u) * leaf_stride));
+#pragma unroll
+    for (int u = 0; u < kOutBatch; ++u) {
+      if (r0 + u >= R) break;
+      const int t1 = cstart[r0 + u + 1];
+      for (int t = cstart[r0 + u]; t < t1; ++t) {
+        const int32_t word = cblk[t];
+        const bool first = (word & kFirstBit) != 0;
+        const int bi = (word >> 16) & 0x7FFF, bj = word & 0xFFFF;
+        const float coef = ccoef[t];
+        const int64_t gi = bi * c.bm + lr, gj = bj * c.bn + lc;
+        const float sc = (c.eA && gi < c.M) ? coef * exp2i(__ldg(c.eA + gi)) : coef;
+        float x[4] = {sc * m[u].x, sc * m[u].y, sc * m[u].z, sc * m[u].w};
+        if (c.eB) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (gj + j < c.N) x[j] *= exp2i(__ldg(c.eB + gj + j));
+        }
+        float4& acc = acc4[(bi * pn + bj) * TR * 16 + me];
+        if (first) {
+          acc = make_float4(x[0], x[1], x[2], x[3]);
+        } else {
+          acc.x += x[0]; acc.y += x[1]; acc.z += x[2]; acc.w += x[3];
+        }
+      }
+    }
+  }
+  if (lr >= c.bm) return;
+  for (int64_t k = 0; k < a.c_blocks; ++k) {
+    const int64_t bi = k / pn, bj = k % pn;
+    const int64_t gi = bi * c.bm + lr, gj = bj * c.bn + lc;
+    if (gi >= c.M) continue;
+    const float4 v = acc4[k * TR * 16 + me];
+    float* dst = c.C + gi * c.ldc + gj;
+    if (c.vec_ok && lc + 4 <= c.bn && gj + 4 <= c.N) {
+      *reinterpret_cast<float4*>(dst) = v;
+    } else {
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (lc + j < c.bn && gj + j < c.N) dst[j] = vv[j];
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st) {
+  if (a.c_blocks > kMaxOutBlocks || a.c.bm > a.tp_a || a.c.bn > a.tp_b || a.tp_b % kTC != 0)
+    return cudaErrorInvalidValue;
+  if (a.c.bm == 0 || a.c.bn == 0) return cudaSuccess;
+  const size_t list_bytes = (size_t)a.c_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
+  if (list_bytes > 150 * 1024) return cudaErrorInvalidValue;
+  KernelTimer timer("combine", st);
+  const unsigned gx = (unsigned)((a.c.bn + kTC - 1) / kTC);
+  const int nb = (int)a.c_blocks;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  // TR rows per CTA so that the accumulators take at most 48 KB
+  auto go = [&](auto tr_tag) {
+    constexpr int TR = decltype(tr_tag)::value;
+    static bool attr_done[64] = {};
+    if (!attr_done[dev]) {
+      cudaFuncSetAttribute(out_combine_kernel<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_done[dev] = true;
+    }
+    const unsigned gy = (unsigned)((a.c.bm + TR - 1) / TR);
+    out_combine_kernel<TR><<<dim3(gx, gy), TR * 16, (size_t)nb * TR * 256 + list_bytes, st>>>(a);
+  };
+  if (nb <= 6) go(std::integral_constant<int, 32>());
+  else if (nb <= 12) go(std::integral_constant<int, 16>());
+  else if (nb <= 24) go(std::integral_constant<int, 8>());
+  else if (nb <= 48) go(std::integral_constant<int, 4>());
+  else go(std::integral_constant<int, 2>());
+  return cudaGetLastError();
+}
 
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st) {
   if (a.p_rows % kTR != 0 || a.p_cols % kTC != 0 || a.p_rows / kTR > 65535) return cudaErrorInvalidValue;

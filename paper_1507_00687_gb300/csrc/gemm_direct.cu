@@ -11,11 +11,18 @@
 //              descriptors read (K-major: one 64 k x rows box; MN-major: one
 //              64 t x 64 k box per 64 rows)
 //
-// One CTA per SM, persistent over BM x BN output tiles of the leaf-block
-// grid; a CTA visits every leaf for its tile in leaf order, so each C
-// element is updated by one thread in a fixed order (deterministic).  The
-// fp32 accumulator is double-buffered in TMEM so the epilogue of leaf r
-// overlaps the products of leaf r + 1.  Every mbarrier wait is bounded
+// One CTA per SM, persistent over work units, each one BM x BN tile of one
+// leaf product.  Two orders:
+//   fused epilogue (args.mbuf null): a CTA owns a tile position and visits
+//     every leaf for it in leaf order, adding w 2^(eA+eB) M_r into C in its
+//     epilogue, so each C element is updated by one thread in a fixed order
+//     (deterministic);
+//   stored products (args.mbuf set): units (leaf, tile) are spread over all
+//     CTAs and the epilogue stores the fp32 tile of M_r; the output
+//     combination pass then forms C.  For plans with few tiles per leaf
+//     (deep recursion, small products) this keeps every SM busy.
+// The fp32 accumulator is double-buffered in TMEM so the epilogue of one
+// unit overlaps the products of the next.  Every mbarrier wait is bounded
 // (globaltimer); on expiry the kernel sets the timeout bit of the status
 // word, stops all roles, waits for its own copies and MMAs, frees its TMEM
 // and returns.
@@ -121,7 +128,23 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
   const int64_t ntiles = ntm * ntn;
   const int64_t KT = args.kp / BK;
   const int64_t NL = args.num_leaves;
-  const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  const bool store_m = args.mbuf != nullptr;
+  const int64_t nunits = store_m ? NL * ntiles : ntiles;  // leaves of a tile count as one unit when fused
+  const int64_t my_units = ((nunits - blockIdx.x + gridDim.x - 1) / gridDim.x) * (store_m ? 1 : NL);
+  // The j-th unit of this CTA: its leaf and tile position.
+  auto unit = [&](int64_t j, int64_t* leaf, int64_t* tm, int64_t* tn) {
+    int64_t tile;
+    if (store_m) {
+      const int64_t u = blockIdx.x + j * gridDim.x;
+      *leaf = u / ntiles;
+      tile = u % ntiles;
+    } else {
+      tile = blockIdx.x + (j / NL) * gridDim.x;
+      *leaf = j % NL;
+    }
+    *tm = tile / ntn;
+    *tn = tile % ntn;
+  };
 
   if (warp == kTmaWarp) {
     if (lane == 0) {
@@ -130,11 +153,11 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
       uint32_t phase = 0;
       bool ok = true;
       uint32_t armed = 0, armed_parity = 0;  // per stage: copy issued, parity it completes
-      const int64_t iters = my_tiles * NL * KT;
+      const int64_t iters = my_units * KT;
       for (int64_t i = 0; i < iters && ok; ++i) {
-        const int64_t tile = blockIdx.x + (i / (NL * KT)) * gridDim.x, rem = i % (NL * KT);
-        const int64_t leaf = rem / KT, kt = rem % KT;
-        const int64_t tm = tile / ntn, tn = tile % ntn;
+        const int64_t kt = i % KT;
+        int64_t leaf, tm, tn;
+        unit(i / KT, &leaf, &tm, &tn);
         if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
         uint8_t* st = smem + stage * C::kStage;
         mbar_arrive_expect_tx(&full[stage], (uint32_t)C::kStage);
@@ -171,8 +194,8 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
       uint32_t phase = 0, acc_iter = 0;
       bool ok = true;
       const uint32_t sbase = smem_u32(smem);
-      for (int64_t tile = 0; tile < my_tiles && ok; ++tile) {
-        for (int64_t leaf = 0; leaf < NL && ok; ++leaf) {
+      for (int64_t j = 0; j < my_units && ok; ++j) {
+        {
           const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
           if (!mbar_wait_bounded(&tempty[buf], aph ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
           tc_fence_after();
@@ -216,26 +239,34 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
     uint32_t acc_iter = 0;
     bool ok = true;
     const int row = warp * 32 + lane;  // TMEM lane = tile row
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const int64_t tm = tile / ntn, tn = tile % ntn;
+    for (int64_t j = 0; j < my_units && ok; ++j) {
+      int64_t leaf, tm, tn;
+      unit(j, &leaf, &tm, &tn);
       const int64_t ml = tm * BM + row;
-      for (int64_t leaf = 0; leaf < NL; ++leaf) {
-        const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
-        // warp-uniform outcome: the TMEM loads below are .sync.aligned
-        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&tfull[buf], aph, abort_flag, args.timeout_ns));
-        if (!ok) break;
-        tc_fence_after();
-        const LeafDesc* L = args.leaves + leaf;
+      const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
+      // warp-uniform outcome: the TMEM loads below are .sync.aligned
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&tfull[buf], aph, abort_flag, args.timeout_ns));
+      if (!ok) break;
+      tc_fence_after();
+      const LeafDesc* L = args.leaves + leaf;
+      // stored products: M_r (padded tp_a x tp_b, fp32) row ml, from column tn BN
+      float* mrow = store_m ? args.mbuf + (leaf * args.tp_a + ml) * args.tp_b + tn * BN : nullptr;
 #pragma unroll 1
-        for (int cc = 0; cc < BN / 32; ++cc) {
-          uint32_t r[32];
-          tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(warp * 32) << 16) + buf * BN + cc * 32, r);
-          if (ml < args.c.bm) epi_chunk(args.c, L, ml, tn * BN + cc * 32, r);
+      for (int cc = 0; cc < BN / 32; ++cc) {
+        uint32_t r[32];
+        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(warp * 32) << 16) + buf * BN + cc * 32, r);
+        if (store_m) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<uint4*>(mrow + cc * 32 + 4 * q) =
+                make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+        } else if (ml < args.c.bm) {
+          epi_chunk(args.c, L, ml, tn * BN + cc * 32, r);
         }
-        tc_fence_before();
-        mbar_arrive(&tempty[buf]);
-        ++acc_iter;
       }
+      tc_fence_before();
+      mbar_arrive(&tempty[buf]);
+      ++acc_iter;
     }
     if (!ok) *abort_flag = 1;
   }
@@ -265,8 +296,9 @@ cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
   }
   if (a.tp_a % BM != 0 || a.tp_b % BN != 0 || a.kp % C::BK != 0) return cudaErrorInvalidValue;
   const int64_t ntiles = (a.tp_a / BM) * (a.tp_b / BN);
-  if (ntiles == 0) return cudaSuccess;
-  const int64_t grid = std::min<int64_t>(ntiles, device_sm_count());
+  if (ntiles == 0 || a.num_leaves == 0) return cudaSuccess;
+  const int64_t units = a.mbuf ? ntiles * a.num_leaves : ntiles;
+  const int64_t grid = std::min<int64_t>(units, device_sm_count());
   KernelTimer timer("multiply", st);
   kern<<<(unsigned)grid, kThreads, C::kSmem, st>>>(a);
   return cudaGetLastError();

@@ -91,6 +91,10 @@ struct CombineArgs {
   const LeafDesc* leaves;
   int64_t num_leaves;
   int side;             // 0: the leaves' A terms, 1: their B terms
+  const int32_t* t_start;  // the side's compact term list (Plan::lists)
+  const int32_t* t_blk;
+  const float* t_coef;
+  int64_t t_nnz;
   int blk_t_shift, blk_k_shift;
   void* out;            // 16-bit elements
   int fmt;              // FMM_LEAF_BF16 / FMM_LEAF_F16 / FMM_LEAF_BF16X3
@@ -112,9 +116,30 @@ struct DirectArgs {
   int64_t tp_a, tp_b;  // padded t extent per leaf block (multiples of the tile)
   int64_t kp;          // padded k extent (multiple of 64)
   int a_mn, b_mn;      // operand layouts
+  float* mbuf;         // null: fused epilogue into C; else store M_r, [leaf][tp_a][tp_b] fp32
   int* status;
   uint64_t timeout_ns;
 };
+
+// Output combination pass (third line of Eq. 4.4) over stored leaf products:
+// for every C block k and element, C = sum over the leaves r in leaf order of
+// w_kr 2^(eA_i + eB_j) M_r (the first term stored, the rest added), exactly
+// as the fused epilogue would.  mbuf as DirectArgs::mbuf.
+struct OutArgs {
+  const float* mbuf;
+  int64_t tp_a, tp_b;
+  EpilogueArgs c;
+  const LeafDesc* leaves;
+  int64_t num_leaves;
+  int64_t c_blocks;  // pm x pn C blocks (at most kMaxOutBlocks)
+  int64_t pn;        // C blocks per block row
+  const int32_t* c_start;  // the C-side compact term list (Plan::lists)
+  const int32_t* c_blk;
+  const float* c_coef;
+  int64_t c_nnz;
+};
+constexpr int kMaxOutBlocks = 96;
+cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st);
 
 // bn: tile width along N (128 or 256).
 cudaError_t launch_direct_gemm(const DirectArgs& args, int leaf_format, int bn, cudaStream_t st);

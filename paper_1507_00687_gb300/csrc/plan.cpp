@@ -205,6 +205,30 @@ fmm_status build_plan(const std::vector<CanonRule>& rules_in, int leaf_format, P
       d.c_first[t] = touched.insert(blk).second ? 1 : 0;
     }
   }
+  // compact per-side term lists
+  for (int side = 0; side < 3; ++side) {
+    int64_t nnz = 0;
+    for (const LeafDesc& d : p->host) nnz += side == 0 ? d.na : side == 1 ? d.nb : d.nc;
+    p->list_off[side] = (int64_t)p->lists.size();
+    p->list_nnz[side] = nnz;
+    const size_t base = p->lists.size();
+    p->lists.resize(base + (size_t)(p->leaves + 1 + 2 * nnz));
+    int32_t* start = p->lists.data() + base;
+    int32_t* blk = start + p->leaves + 1;
+    int32_t* coef = blk + nnz;
+    int64_t at = 0;
+    for (int64_t r = 0; r < p->leaves; ++r) {
+      const LeafDesc& d = p->host[(size_t)r];
+      start[r] = (int32_t)at;
+      const int n = side == 0 ? d.na : side == 1 ? d.nb : d.nc;
+      for (int t = 0; t < n; ++t, ++at) {
+        const float c = side == 0 ? d.a_coef[t] : side == 1 ? d.b_coef[t] : d.c_coef[t];
+        blk[at] = side == 0 ? d.a_blk[t] : side == 1 ? d.b_blk[t] : (d.c_blk[t] | (d.c_first[t] ? kFirstBit : 0));
+        std::memcpy(&coef[at], &c, 4);
+      }
+    }
+    start[p->leaves] = (int32_t)at;
+  }
   *out = p;
   return FMM_OK;
 }

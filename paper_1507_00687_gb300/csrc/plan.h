@@ -12,7 +12,7 @@ namespace fmm {
 // Upper bound on the flattened terms of one leaf (Eq. 4.4): the number of
 // A blocks summed into S_r, of B blocks summed into T_r, and of C blocks the
 // product M_r is added into.
-constexpr int kMaxTerms = 16;
+constexpr int kMaxTerms = 64;
 
 // One leaf of the flattened plan: S = sum a_coef[t] A(a_blk[t]),
 // T = sum b_coef[t] B(b_blk[t]), C(c_blk[t]) += c_coef[t] * S T.
@@ -20,6 +20,8 @@ constexpr int kMaxTerms = 16;
 // operand (A: pm x pk blocks, B: pk x pn, C: pm x pn).  c_first[t] is 1 when
 // this leaf is the first (in leaf order) to touch C block c_blk[t], so the
 // epilogue stores instead of accumulating.
+constexpr int32_t kFirstBit = (int32_t)0x80000000u;
+
 struct LeafDesc {
   int32_t na, nb, nc, pad;
   int32_t a_blk[kMaxTerms];
@@ -50,7 +52,16 @@ struct Plan {
   int64_t nnz = 0;
   int max_terms = 0;  // max over leaves of na, nb, nc
   std::vector<LeafDesc> host;
-  LeafDesc* dev = nullptr;  // device copy (on `device`)
+  // The same terms as compact per-side lists (what the bandwidth passes
+  // read): for side s (0 = A, 1 = B, 2 = C), int32 words at list_off[s]:
+  // start[leaves + 1], then blk[list_nnz[s]], then coef[list_nnz[s]] (float
+  // bits); leaf r's terms are [start[r], start[r + 1]).  C blocks carry
+  // kFirstBit when the leaf is the first to touch the block.
+  std::vector<int32_t> lists;
+  int64_t list_off[3] = {0, 0, 0};
+  int64_t list_nnz[3] = {0, 0, 0};
+  // Device copy (on `device`): the LeafDesc array followed by `lists`.
+  LeafDesc* dev = nullptr;
   int device = -1;
   Plan* grad_a = nullptr;  // plan for dA = dC B^T  (lazily built)
   Plan* grad_b = nullptr;  // plan for dB = A^T dC

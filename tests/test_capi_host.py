@@ -94,10 +94,12 @@ def test_plan_rejects_bad_args(native):
     assert L.fmm_plan(C.byref(h), -1, None, 0) == 1
     assert L.fmm_plan(C.byref(h), 0, None, 7) == 1
     assert L.fmm_plan_info(None, None, None, None, None, None, None, None) == 1
-    # unsupported flattening: Winograd^3 needs 64 terms per operand
+    # unsupported flattening: Winograd^4 needs 256 terms per operand (the
+    # limit is 64, which Winograd^3 reaches)
     from paper_1507_00687_gb300 import api
+    assert api.Plan(["winograd"] * 3).info()["leaves"] == 343
     with pytest.raises(native.FmmError) as e:
-        api.Plan(["winograd"] * 3)
+        api.Plan(["winograd"] * 4)
     assert e.value.code == 10
 
 

@@ -91,9 +91,10 @@ PLANS = [[], ["strassen"], ["winograd"], ["strassen", "strassen"], ["winograd", 
 SHAPES = [(256, 256, 256), (300, 200, 250), (16, 16, 16), (1000, 520, 776), (1, 3, 2), (129, 65, 257)]
 
 # Where S_r and T_r are formed: in the multiply kernel's load stage, or by
-# the combination pass into the workspace.  Both are checked everywhere the
-# multiply is.
-SCHEDULES = ["load_stage", "pass"]
+# the combination pass into the workspace -- with the output combination in
+# the multiply epilogue or over stored leaf products.  All three are checked
+# everywhere the multiply is.
+SCHEDULES = ["load_stage", "pass_epilogue", "pass_products"]
 
 
 @pytest.mark.parametrize("schedule", SCHEDULES)
