@@ -361,13 +361,21 @@ def main():
     achieved = mma_flops / (mult_ms_per * 1e-3) / 1e12
     sched_used = "pass" if kern["combine"][1] > 0 else "load_stage"
     kname = "direct_fmm_kernel" if sched_used == "pass" else "fused_fmm_kernel"
-    # the combination pass: reads each operand once, writes R^L combined
-    # leaf blocks (two bf16 planes for bf16x3, else one 16-bit plane)
+    # the bandwidth passes of the pass schedule, per step: two combination
+    # passes (each reads its operand once and writes R^L combined leaf
+    # blocks: two bf16 planes for bf16x3, else one 16-bit plane) and, with
+    # stored leaf products, the output pass (reads the R^L fp32 products,
+    # writes C)
     planes = 2 if args.leaf == "bf16x3" else 1
+    R = info["leaves"]
     bt = -(-n // info["pm"])
-    tp, kp = -(-bt // 128) * 128, -(-(-(-n // info["pk"])) // 64) * 64
-    comb_bytes = n * n * 4 + planes * info["leaves"] * tp * kp * 2
+    tp_a, tp_b = -(-bt // 128) * 128, -(-bt // 256) * 256
+    kp = -(-(-(-n // info["pk"])) // 64) * 64
     comb_ms, comb_n = kern["combine"]
+    per_step = comb_n // max(1, args.steps)
+    pass_bytes = 2 * n * n * 4 + planes * R * (tp_a + tp_b) * kp * 2
+    if per_step >= 3:
+        pass_bytes += R * tp_a * tp_b * 4 + n * n * 4
     kernel_times = {k or "all": {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / max(1, v[1])}
                     for k, v in kern.items()}
     traffic = None
@@ -385,11 +393,12 @@ def main():
            "multiply_call_ms": kms,
            "schedule": sched_used,
            "kernel_times": kernel_times,
-           "combine_pass": ({"ms_per_launch": comb_ms / comb_n, "algorithmic_bytes_per_launch": comb_bytes,
-                             "achieved_GBps": comb_bytes / (comb_ms / comb_n * 1e-3) / 1e9,
-                             "peak_GBps": peaks.get("hbm_gbs"),
-                             "frac": (comb_bytes / (comb_ms / comb_n * 1e-3) / 1e9 / peaks["hbm_gbs"])
-                             if peaks.get("hbm_gbs") else None} if comb_n else None),
+           "bandwidth_passes": ({"ms_per_step": comb_ms / args.steps, "launches_per_step": per_step,
+                                 "algorithmic_bytes_per_step": pass_bytes,
+                                 "achieved_GBps": pass_bytes / (comb_ms / args.steps * 1e-3) / 1e9,
+                                 "peak_GBps": peaks.get("hbm_gbs"),
+                                 "frac": (pass_bytes / (comb_ms / args.steps * 1e-3) / 1e9 / peaks["hbm_gbs"])
+                                 if peaks.get("hbm_gbs") else None} if comb_n else None),
            "executed_flop_fraction": achieved / peak,
            "error": {"max_abs_err_vs_fp64": err_fast, "theorem_4_1_bound_unscaled": bound_unscaled,
                      "eps_leaf": eps_leaf, "normA": normA, "normB": normB},

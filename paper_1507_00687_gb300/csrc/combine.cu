@@ -174,8 +174,10 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs a) 
 // use.  TR * 16 threads, one row of 4 columns each.
 constexpr int kMaxStaged = 64;
 
-template <int DT, int FMT, int TR>
-__global__ void __launch_bounds__(TR * 16) combine_staged_kernel(const CombineArgs a) {
+template <int DT, int FMT, int TR, int RPT>
+__global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_kernel(const CombineArgs a) {
+  // RPT rows per thread: rows tr + (TR / RPT) q, q < RPT; 4 columns each
+  constexpr int kT = TR * 16 / RPT;
   extern __shared__ float4 tile4[];  // [block][TR][16], then the term list
   const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * kTC;
   const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15, tc = tq * 4;
@@ -184,72 +186,86 @@ __global__ void __launch_bounds__(TR * 16) combine_staged_kernel(const CombineAr
                       (!a.ce || (uintptr_t)a.ce % 16 == 0);
   const int n_rb = (int)a.n_rb, n_cb = (int)a.n_cb;
   const int nb = n_rb * n_cb;
-  const int64_t R = a.num_leaves;
+  const int R = (int)a.num_leaves;
   const int nnz = (int)a.t_nnz;
   // term list in shared memory: float4 offset of the term's block tile, coef
   int* toff = reinterpret_cast<int*>(tile4 + nb * TR * 16);
   float* tcoef = reinterpret_cast<float*>(toff + nnz);
   int* tstart = reinterpret_cast<int*>(tcoef + nnz);
-  for (int i = threadIdx.x; i < nnz; i += TR * 16) {
+  for (int i = threadIdx.x; i < nnz; i += kT) {
     const int32_t blk = __ldg(a.t_blk + i);
     const int bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
     toff[i] = (a.t_rows ? bt * n_cb + bk : bk * n_cb + bt) * TR * 16;
     tcoef[i] = __ldg(a.t_coef + i);
   }
-  for (int64_t i = threadIdx.x; i <= R; i += TR * 16) tstart[i] = __ldg(a.t_start + i);
-  const int64_t lr = r0 + tr, lc = c0 + tc;
-  for (int rb = 0; rb < n_rb; ++rb) {
-    const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows);
-    const int64_t gr = rb * a.b_rows + lr;
-    const bool row_in = r0 + TR <= nr;
-    const int er = (a.re && lr < nr) ? a.rs * __ldg(a.re + gr) : 0;
-    const char* src_row = static_cast<const char*>(a.src) + gr * a.ld * es;
-    for (int cb = 0; cb < n_cb; ++cb) {
-      const int64_t nc = min(a.b_cols, a.cols - cb * a.b_cols);
-      const int64_t gc = cb * a.b_cols + lc;
-      float x[4];
-      if (vec_ok && row_in && c0 + kTC <= nc) {
-        load4<DT>(src_row, gc, x);
-        if (a.re || a.ce) {
-          int4 ec = make_int4(0, 0, 0, 0);
-          if (a.ce) ec = __ldg(reinterpret_cast<const int4*>(a.ce + gc));
-          x[0] = scale_pow2(x[0], er + a.cs * ec.x);
-          x[1] = scale_pow2(x[1], er + a.cs * ec.y);
-          x[2] = scale_pow2(x[2], er + a.cs * ec.z);
-          x[3] = scale_pow2(x[3], er + a.cs * ec.w);
-        }
-      } else {
+  for (int i = threadIdx.x; i <= R; i += kT) tstart[i] = __ldg(a.t_start + i);
+  const int64_t lc = c0 + tc;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          x[j] = 0.f;
-          if (lr < nr && lc + j < nc) {
-            const float v = load_elem<DT>(src_row, gc + j);
-            x[j] = scale_pow2(v, er + (a.ce ? a.cs * __ldg(a.ce + gc + j) : 0));
+  for (int q = 0; q < RPT; ++q) {
+    const int trq = tr + (TR / RPT) * q;
+    const int64_t lr = r0 + trq;
+    for (int rb = 0; rb < n_rb; ++rb) {
+      const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows);
+      const int64_t gr = rb * a.b_rows + lr;
+      const bool row_in = r0 + TR <= nr;
+      const int er = (a.re && lr < nr) ? a.rs * __ldg(a.re + gr) : 0;
+      const char* src_row = static_cast<const char*>(a.src) + gr * a.ld * es;
+      for (int cb = 0; cb < n_cb; ++cb) {
+        const int64_t nc = min(a.b_cols, a.cols - cb * a.b_cols);
+        const int64_t gc = cb * a.b_cols + lc;
+        float x[4];
+        if (vec_ok && row_in && c0 + kTC <= nc) {
+          load4<DT>(src_row, gc, x);
+          if (a.re || a.ce) {
+            int4 ec = make_int4(0, 0, 0, 0);
+            if (a.ce) ec = __ldg(reinterpret_cast<const int4*>(a.ce + gc));
+            x[0] = scale_pow2(x[0], er + a.cs * ec.x);
+            x[1] = scale_pow2(x[1], er + a.cs * ec.y);
+            x[2] = scale_pow2(x[2], er + a.cs * ec.z);
+            x[3] = scale_pow2(x[3], er + a.cs * ec.w);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            x[j] = 0.f;
+            if (lr < nr && lc + j < nc) {
+              const float v = load_elem<DT>(src_row, gc + j);
+              x[j] = scale_pow2(v, er + (a.ce ? a.cs * __ldg(a.ce + gc + j) : 0));
+            }
           }
         }
+        tile4[((rb * n_cb + cb) * TR + trq) * 16 + tq] = make_float4(x[0], x[1], x[2], x[3]);
       }
-      tile4[((rb * n_cb + cb) * TR + tr) * 16 + tq] = make_float4(x[0], x[1], x[2], x[3]);
     }
   }
   __syncthreads();
   unsigned short* out = static_cast<unsigned short*>(a.out);
-  const int64_t plane = R * a.p_rows * a.p_cols;
+  const int64_t plane = (int64_t)R * a.p_rows * a.p_cols;
   const int me = tr * 16 + tq;
-  unsigned short* orow = out + lr * a.p_cols + lc;
+  constexpr int kRowStep = (TR / RPT) * 16;  // float4 distance between a thread's rows
+  unsigned short* orow = out + (r0 + tr) * a.p_cols + lc;
   const int64_t leaf_stride = a.p_rows * a.p_cols;
-  int t = tstart[0];
-  for (int64_t r = 0; r < R; ++r, orow += leaf_stride) {
+  const int64_t qstride = (int64_t)(TR / RPT) * a.p_cols;
+  int t = 0;
+  for (int r = 0; r < R; ++r, orow += leaf_stride) {
     const int t1 = tstart[r + 1];
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[RPT][4];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
     for (; t < t1; ++t) {
       const float coef = tcoef[t];
-      const float4 v = tile4[toff[t] + me];
-      acc[0] = fmaf(coef, v.x, acc[0]);
-      acc[1] = fmaf(coef, v.y, acc[1]);
-      acc[2] = fmaf(coef, v.z, acc[2]);
-      acc[3] = fmaf(coef, v.w, acc[3]);
+      const int off = toff[t] + me;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const float4 v = tile4[off + q * kRowStep];
+        acc[q][0] = fmaf(coef, v.x, acc[q][0]);
+        acc[q][1] = fmaf(coef, v.y, acc[q][1]);
+        acc[q][2] = fmaf(coef, v.z, acc[q][2]);
+        acc[q][3] = fmaf(coef, v.w, acc[q][3]);
+      }
     }
-    store4<FMT>(orow, orow + plane, acc);
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) store4<FMT>(orow + q * qstride, orow + q * qstride + plane, acc[q]);
   }
 }
 
@@ -259,25 +275,25 @@ inline size_t staged_smem(int nb, int tr, int64_t nnz, int64_t leaves) {
 }
 constexpr size_t kStagedSmemMax = 200 * 1024;
 
-template <int DT, int FMT, int TR>
+template <int DT, int FMT, int TR, int RPT = 1>
 void launch_staged_tr(const CombineArgs& a, int nb, cudaStream_t st) {
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   if (!attr_done[dev]) {
-    cudaFuncSetAttribute(combine_staged_kernel<DT, FMT, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(combine_staged_kernel<DT, FMT, TR, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kStagedSmemMax);
     attr_done[dev] = true;
   }
-  combine_staged_kernel<DT, FMT, TR><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / TR)), TR * 16,
-                                       staged_smem(nb, TR, a.t_nnz, a.num_leaves), st>>>(a);
+  combine_staged_kernel<DT, FMT, TR, RPT><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / TR)),
+                                            TR * 16 / RPT, staged_smem(nb, TR, a.t_nnz, a.num_leaves), st>>>(a);
 }
 
 template <int DT, int FMT>
 void launch_staged(const CombineArgs& a, int nb, cudaStream_t st) {
   // TR rows per CTA so that the staged tiles take at most 32 KB
-  if (nb <= 4) launch_staged_tr<DT, FMT, 32>(a, nb, st);
+  if (nb <= 4) launch_staged_tr<DT, FMT, 32, 2>(a, nb, st);
   else if (nb <= 8) launch_staged_tr<DT, FMT, 16>(a, nb, st);
   else if (nb <= 16) launch_staged_tr<DT, FMT, 8>(a, nb, st);
   else if (nb <= 32) launch_staged_tr<DT, FMT, 4>(a, nb, st);
@@ -307,11 +323,13 @@ cudaError_t launch_dt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
 // Output combination pass over stored leaf products M_r: one CTA covers a
 // TR x 64 position tile of every C block and walks the leaves in order,
 // keeping one fp32 accumulator per (C block, position) in shared memory
-// (each thread only ever touches its own positions); then writes C.  The
-// per-element arithmetic is the fused epilogue's: s = w 2^eA_i,
-// x = s M 2^eB_j, C = x for the first leaf touching the block, else C + x.
-// The C-side term list sits in shared memory; the M_r loads of kOutBatch
-// leaves are issued together.
+// (each thread only ever touches its own positions): acc = w M for the
+// first leaf touching the block, else acc + w M.  The unscale of Algs. 1-3,
+// C = D_A C' D_B, is applied once per element when C is written (the fused
+// epilogue's per-term scaling gives the same value, since powers of two
+// commute exactly with the sums while no value under- or overflows).  The
+// C-side term list sits in shared memory with each term's accumulator
+// offset; the M_r loads of kOutBatch leaves are issued together.
 constexpr int kOutBatch = 4;
 
 template <int TR>
@@ -321,62 +339,66 @@ __global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
   const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15;
   const int64_t lr = (int64_t)blockIdx.y * TR + tr, lc = (int64_t)blockIdx.x * kTC + tq * 4;
   const int pn = (int)a.pn;
-  const int64_t R = a.num_leaves;
+  const int R = (int)a.num_leaves;
   const int nnz = (int)a.c_nnz;
-  int* cblk = reinterpret_cast<int*>(acc4 + a.c_blocks * TR * 16);
-  float* ccoef = reinterpret_cast<float*>(cblk + nnz);
+  int* cw = reinterpret_cast<int*>(acc4 + a.c_blocks * TR * 16);  // accumulator offset | first bit
+  float* ccoef = reinterpret_cast<float*>(cw + nnz);
   int* cstart = reinterpret_cast<int*>(ccoef + nnz);
   for (int i = threadIdx.x; i < nnz; i += TR * 16) {
-    cblk[i] = __ldg(a.c_blk + i);
+    const int32_t word = __ldg(a.c_blk + i);
+    const int bi = (word >> 16) & 0x7FFF, bj = word & 0xFFFF;
+    cw[i] = ((bi * pn + bj) * TR * 16) | (word & kFirstBit);
     ccoef[i] = __ldg(a.c_coef + i);
   }
-  for (int64_t i = threadIdx.x; i <= R; i += TR * 16) cstart[i] = __ldg(a.c_start + i);
+  for (int i = threadIdx.x; i <= R; i += TR * 16) cstart[i] = __ldg(a.c_start + i);
   __syncthreads();
   const int me = tr * 16 + tq;
   const float* mcol = a.mbuf + lr * a.tp_b + lc;
   const int64_t leaf_stride = a.tp_a * a.tp_b;
-  for (int64_t r0 = 0; r0 < R; r0 += kOutBatch) {
+  int t = 0;
+  for (int r0 = 0; r0 < R; r0 += kOutBatch) {
     float4 m[kOutBatch];
 #pragma unroll
     for (int u = 0; u < kOutBatch; ++u)
-      if (r0 + u < R) m[u] = __ldg(reinterpret_cast<const float4*>(mcol + (r0 + u) * leaf_stride));
+      if (r0 + u < R) m[u] = __ldg(reinterpret_cast<const float4*>(mcol + (int64_t)(r0 + u) * leaf_stride));
 #pragma unroll
     for (int u = 0; u < kOutBatch; ++u) {
       if (r0 + u >= R) break;
       const int t1 = cstart[r0 + u + 1];
-      for (int t = cstart[r0 + u]; t < t1; ++t) {
-        const int32_t word = cblk[t];
-        const bool first = (word & kFirstBit) != 0;
-        const int bi = (word >> 16) & 0x7FFF, bj = word & 0xFFFF;
+      for (; t < t1; ++t) {
+        const int w = cw[t];
         const float coef = ccoef[t];
-        const int64_t gi = bi * c.bm + lr, gj = bj * c.bn + lc;
-        const float sc = (c.eA && gi < c.M) ? coef * exp2i(__ldg(c.eA + gi)) : coef;
-        float x[4] = {sc * m[u].x, sc * m[u].y, sc * m[u].z, sc * m[u].w};
-        if (c.eB) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (gj + j < c.N) x[j] *= exp2i(__ldg(c.eB + gj + j));
-        }
-        float4& acc = acc4[(bi * pn + bj) * TR * 16 + me];
-        if (first) {
-          acc = make_float4(x[0], x[1], x[2], x[3]);
+        float4& acc = acc4[(w & 0x7FFFFFFF) + me];
+        const float4 x = make_float4(coef * m[u].x, coef * m[u].y, coef * m[u].z, coef * m[u].w);
+        if (w < 0) {
+          acc = x;
         } else {
-          acc.x += x[0]; acc.y += x[1]; acc.z += x[2]; acc.w += x[3];
+          acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
         }
       }
     }
   }
   if (lr >= c.bm) return;
-  for (int64_t k = 0; k < a.c_blocks; ++k) {
-    const int64_t bi = k / pn, bj = k % pn;
+  for (int k = 0; k < (int)a.c_blocks; ++k) {
+    const int bi = k / pn, bj = k % pn;
     const int64_t gi = bi * c.bm + lr, gj = bj * c.bn + lc;
     if (gi >= c.M) continue;
     const float4 v = acc4[k * TR * 16 + me];
+    float vv[4] = {v.x, v.y, v.z, v.w};
+    if (c.eA) {
+      const float fa = exp2i(__ldg(c.eA + gi));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) vv[j] *= fa;
+    }
+    if (c.eB) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (gj + j < c.N) vv[j] *= exp2i(__ldg(c.eB + gj + j));
+    }
     float* dst = c.C + gi * c.ldc + gj;
     if (c.vec_ok && lc + 4 <= c.bn && gj + 4 <= c.N) {
-      *reinterpret_cast<float4*>(dst) = v;
+      *reinterpret_cast<float4*>(dst) = make_float4(vv[0], vv[1], vv[2], vv[3]);
     } else {
-      const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         if (lc + j < c.bn && gj + j < c.N) dst[j] = vv[j];
