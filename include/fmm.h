@@ -262,6 +262,48 @@ fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, con
                                 const int32_t* eB, void* stream);
 
 /*
+ * Batches: many independent products of uneven shapes, each with its own
+ * plan (rule, recursion depth), run as one fixed sequence of launches over
+ * all of them -- the batched scaling reductions, one combination pass, ONE
+ * persistent tensor-core launch over every product's (leaf, tile) work
+ * units, one output pass -- so a whole batch costs about nine launches.
+ * fmm_batch_create does all host work and every allocation-free layout
+ * decision once: it checks the problems, lays out the per-product exponent
+ * vectors, combined operands and stored leaf products, and the launch
+ * tables, in the caller's workspace (ws, 256-byte aligned, of
+ * fmm_batch_workspace_size bytes), and copies the tables there
+ * (synchronously).  fmm_batch_run then only launches kernels on the stream,
+ * with no host synchronisation or allocation, so it can be captured in a
+ * CUDA graph and replayed; each replay recomputes every C from the current
+ * contents of the A and B buffers.
+ *
+ * All plans of a batch must share their leaf format, and each must have at
+ * most 96 C blocks (pm x pn); every M, K, N must be positive.  A and B have
+ * element type in_dtype; steps is "" (no scaling), "O", "I" or "OI" (Alg. 3
+ * steps starting from no scaling, as fmm_scale; the exponents live in the
+ * workspace).  The plans, the batch and the workspace must outlive every run.
+ */
+typedef struct {
+  fmm_plan_t plan;
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  float* C;
+  int64_t ldc;
+  int64_t M, K, N;
+} fmm_problem;
+
+typedef struct fmm_batch_s* fmm_batch_t;
+
+fmm_status fmm_batch_workspace_size(const fmm_problem* problems, int count, int in_dtype,
+                                    const char* steps, size_t* bytes);
+fmm_status fmm_batch_create(fmm_batch_t* out, const fmm_problem* problems, int count, int in_dtype,
+                            const char* steps, void* ws, size_t ws_bytes);
+fmm_status fmm_batch_run(fmm_batch_t batch, void* stream);
+fmm_status fmm_batch_destroy(fmm_batch_t batch);
+
+/*
  * Gradients of C = A B for a given dC (M x N, float32, lddc):
  *   dA = dC B^T (M x K, float32, ldda),  dB = A^T dC (K x N, float32, lddb),
  * each by a fast algorithm derived from the plan's rules through the cyclic

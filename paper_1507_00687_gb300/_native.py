@@ -28,6 +28,7 @@ EXPORTS = [
     "fmm_scale_inside", "fmm_scale", "fmm_workspace_size", "fmm_multiply", "fmm_multiply_backward",
     "fmm_sync_status", "fmm_status_string", "fmm_version", "fmm_last_error", "fmm_multiply_noalloc",
     "fmm_plan_set_schedule", "fmm_kernel_timing", "fmm_kernel_timing_read",
+    "fmm_batch_workspace_size", "fmm_batch_create", "fmm_batch_run", "fmm_batch_destroy",
 ]
 
 # Bytes of the library's static scratch array (FMM_NOALLOC_SCRATCH_BYTES).
@@ -38,6 +39,12 @@ class FmmRule(C.Structure):
     _fields_ = [("m0", C.c_int), ("k0", C.c_int), ("n0", C.c_int), ("r", C.c_int),
                 ("U", C.POINTER(C.c_double)), ("V", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
                 ("order_a", C.c_int), ("order_b", C.c_int), ("order_c", C.c_int)]
+
+
+class FmmProblem(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("A", C.c_void_p), ("lda", C.c_int64), ("B", C.c_void_p),
+                ("ldb", C.c_int64), ("C", C.c_void_p), ("ldc", C.c_int64), ("M", C.c_int64), ("K", C.c_int64),
+                ("N", C.c_int64)]
 
 
 class FmmError(RuntimeError):
@@ -63,6 +70,12 @@ def lib():
     L.fmm_plan_destroy.argtypes = [vp]
     L.fmm_plan_set_schedule.argtypes = [vp, C.c_int]
     L.fmm_kernel_timing.argtypes = [C.c_int]
+    L.fmm_batch_workspace_size.argtypes = [C.POINTER(FmmProblem), C.c_int, C.c_int, C.c_char_p,
+                                           C.POINTER(C.c_size_t)]
+    L.fmm_batch_create.argtypes = [C.POINTER(vp), C.POINTER(FmmProblem), C.c_int, C.c_int, C.c_char_p, vp,
+                                   C.c_size_t]
+    L.fmm_batch_run.argtypes = [vp, vp]
+    L.fmm_batch_destroy.argtypes = [vp]
     L.fmm_kernel_timing_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64)]
     L.fmm_plan_info.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(i64),
                                 C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]

@@ -188,6 +188,52 @@ def multiply_backward(plan: Plan, dC: torch.Tensor, A: torch.Tensor, B: torch.Te
     return dA, dB
 
 
+class Batch:
+    """Many independent products C_i = A_i B_i, each with its own plan, run
+    as one fixed launch sequence (fmm_batch_create / fmm_batch_run): batched
+    scaling reductions, one combination pass, one persistent tensor-core
+    launch over every product's work units, one output pass.  ``problems``
+    is a sequence of (plan, A, B, C) with row-major device tensors of one
+    element type and float32 C; ``steps`` is "", "O", "I" or "OI".  The
+    workspace is allocated here; ``run`` launches only (capturable in a CUDA
+    graph) and recomputes every C from the current A and B."""
+
+    def __init__(self, problems, steps: str = "OI", ws: Optional[torch.Tensor] = None):
+        self._keep = list(problems)
+        dt = problems[0][1].dtype
+        arr = (N.FmmProblem * len(problems))()
+        for i, (plan, A, B, Cm) in enumerate(problems):
+            M, K = A.shape
+            K2, Nn = B.shape
+            if K != K2 or A.dtype != dt or B.dtype != dt or tuple(Cm.shape) != (M, Nn) or Cm.dtype != torch.float32:
+                raise ValueError(f"problem {i}: shape / dtype mismatch")
+            arr[i] = N.FmmProblem(plan.handle.value, A.data_ptr(), _rowmajor(A, "A"), B.data_ptr(),
+                                  _rowmajor(B, "B"), Cm.data_ptr(), _rowmajor(Cm, "C"), M, K, Nn)
+        self._arr = arr
+        self.steps = steps
+        need = C.c_size_t()
+        N.check(N.lib().fmm_batch_workspace_size(arr, len(problems), DTYPE[dt], steps.encode(), C.byref(need)),
+                "fmm_batch_workspace_size")
+        self.ws = ws if ws is not None else torch.empty(max(need.value, 256), dtype=torch.uint8,
+                                                        device=problems[0][1].device)
+        h = C.c_void_p()
+        N.check(N.lib().fmm_batch_create(C.byref(h), arr, len(problems), DTYPE[dt], steps.encode(), _ptr(self.ws),
+                                         self.ws.numel()), "fmm_batch_create")
+        self._h = h
+
+    def run(self, stream=None) -> None:
+        N.check(N.lib().fmm_batch_run(self._h, _stream(stream)), "fmm_batch_run")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                N.lib().fmm_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
 def kernel_timing(enable: bool) -> None:
     """Start (discarding earlier records) or stop per-kernel event timing."""
     N.check(N.lib().fmm_kernel_timing(1 if enable else 0), "fmm_kernel_timing")

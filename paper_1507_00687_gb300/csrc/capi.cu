@@ -1,6 +1,7 @@
 // C ABI (include/fmm.h): argument validation, plan lifetime, and the
 // launch sequences of the scaling steps, the forward and the backward
 // multiply.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -163,6 +164,12 @@ static bool make_map_sw(CUtensorMap* m, const void* ptr, bool f16, int64_t rows,
   return true;
 }
 
+// Rows of X start on 16-byte boundaries (the reductions' vector path).
+static int vec_aligned_host(const void* X, int64_t ld, int dt) {
+  const int es = dt == FMM_DT_F32 ? 4 : 2;
+  return ((uintptr_t)X % 16 == 0) && ((ld * es) % 16 == 0) ? 1 : 0;
+}
+
 // ---------------------------------------------------------------- operands
 
 // One operand of a fast product as stored by the caller: a row-major memory
@@ -270,107 +277,145 @@ static int64_t pass_bytes(const Plan* p, int64_t Tx, int64_t Kd, int64_t Ty, int
          (p->leaves > 1 ? products_bytes(Tx, Ty, ptx, pty, p->leaves, 256) : 0);
 }
 
-// The pass schedule: the combination pass writes S_r (from x) and T_r (from
-// y) for every leaf into the workspace; the multiply kernel then streams
-// them.  Returns FMM_ERR_WORKSPACE when the workspace is too small.
-static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, const EpilogueArgs& c,
-                           const LeafDesc* leaves, int* status, void* ws, size_t ws_bytes, cudaStream_t st) {
-  const int planes = p->leaf_format == FMM_LEAF_BF16X3 ? 2 : 1;
-  const int64_t R = p->leaves;
-  const int64_t bt_a = ceil_div(x.T, x.pt), bt_b = ceil_div(y.T, y.pt), bk = ceil_div(x.Kd, x.pk);
-  const int bn = pass_tile_n(bt_b);
-  const int64_t tp_a = round_up(bt_a, 128), tp_b = round_up(bt_b, bn), kp = round_up(bk, 64);
-  const int64_t bytes_a = round_up(planes * R * tp_a * kp * 2, 256);
-  const int64_t bytes_b = round_up(planes * R * tp_b * kp * 2, 256);
-  if (!ws || (uintptr_t)ws % 256 != 0 || (int64_t)ws_bytes < bytes_a + bytes_b) return FMM_ERR_WORKSPACE;
-  char* wa = static_cast<char*>(ws);
-  char* wb = wa + bytes_a;
-  // Stored leaf products unless the epilogue form is asked for: measured
-  // faster at every size (every SM gets (leaf, tile) units; the fused
-  // epilogue leaves SMs idle when tiles per leaf are few, and its C
-  // read-modify-writes cost more than one more bandwidth pass).
-  const int64_t bytes_m = round_up(R * tp_a * tp_b * 4, 256);
-  const bool want_m = p->schedule != FMM_SCHEDULE_PASS_EPILOGUE;
-  const bool store_m = want_m && R > 1 && p->pm * p->pn <= kMaxOutBlocks &&
-                       (int64_t)ws_bytes >= bytes_a + bytes_b + bytes_m;
-  float* mbuf = store_m ? reinterpret_cast<float*>(wb + bytes_b) : nullptr;
-  // One side: the source's memory rows follow t (k-contiguous) or k.
-  auto combine = [&](const Source& s, int64_t bt, int64_t tp, int side, char* out) {
-    CombineArgs ca;
-    ca.src = s.ptr;
-    ca.ld = s.ld;
-    ca.dtype = s.dtype;
-    ca.rows = s.kcontig ? s.T : s.Kd;
-    ca.cols = s.kcontig ? s.Kd : s.T;
-    ca.b_rows = s.kcontig ? bt : bk;
-    ca.b_cols = s.kcontig ? bk : bt;
-    ca.n_rb = s.kcontig ? s.pt : s.pk;
-    ca.n_cb = s.kcontig ? s.pk : s.pt;
-    ca.p_rows = s.kcontig ? tp : kp;
-    ca.p_cols = s.kcontig ? kp : tp;
-    ca.t_rows = s.kcontig ? 1 : 0;
-    ca.re = s.re;
-    ca.rs = s.rs;
-    ca.ce = s.ce;
-    ca.cs = s.cs;
-    ca.leaves = leaves;
-    ca.num_leaves = R;
-    ca.side = side;
-    const int32_t* lists = reinterpret_cast<const int32_t*>(leaves + R);
-    ca.t_start = lists + p->list_off[side];
-    ca.t_blk = ca.t_start + R + 1;
-    ca.t_coef = reinterpret_cast<const float*>(ca.t_blk + p->list_nnz[side]);
-    ca.t_nnz = p->list_nnz[side];
-    ca.blk_t_shift = side == 0 ? 16 : 0;
-    ca.blk_k_shift = side == 0 ? 0 : 16;
-    ca.out = out;
-    ca.fmt = p->leaf_format;
-    return launch_combine(ca, st);
-  };
-  // B first: a scaling sequence that ends with a pass over B leaves it in L2
-  if (!cuda_ok(combine(y, bt_b, tp_b, 1, wb), "combination pass (B)")) return FMM_ERR_CUDA;
-  if (!cuda_ok(combine(x, bt_a, tp_a, 0, wa), "combination pass (A)")) return FMM_ERR_CUDA;
-  DirectArgs d;
-  std::memset(&d, 0, sizeof(d));
+// Geometry of the pass schedule for one product: leaf block extents, their
+// padded extents in the combined operands (t: 128 for A, bn for B; k: 64)
+// and the workspace bytes of the combined A, B and the stored products.
+struct PassGeom {
+  int planes, bn;
+  int64_t R, bt_a, bt_b, bk, tp_a, tp_b, kp, bytes_a, bytes_b, bytes_m;
+};
+
+static PassGeom pass_geom(const Plan* p, const Source& x, const Source& y, int bn) {
+  PassGeom g;
+  g.planes = p->leaf_format == FMM_LEAF_BF16X3 ? 2 : 1;
+  g.R = p->leaves;
+  g.bt_a = ceil_div(x.T, x.pt);
+  g.bt_b = ceil_div(y.T, y.pt);
+  g.bk = ceil_div(x.Kd, x.pk);
+  g.bn = bn > 0 ? bn : pass_tile_n(g.bt_b);
+  g.tp_a = round_up(g.bt_a, 128);
+  g.tp_b = round_up(g.bt_b, g.bn);
+  g.kp = round_up(g.bk, 64);
+  g.bytes_a = round_up(g.planes * g.R * g.tp_a * g.kp * 2, 256);
+  g.bytes_b = round_up(g.planes * g.R * g.tp_b * g.kp * 2, 256);
+  g.bytes_m = round_up(g.R * g.tp_a * g.tp_b * 4, 256);
+  return g;
+}
+
+// Combination-pass arguments for one side (0: A terms from x, 1: B terms
+// from y); the source's memory rows follow t (k-contiguous) or k.
+static CombineArgs combine_args(const Plan* p, const PassGeom& g, const Source& s, int side, const LeafDesc* leaves,
+                                char* out) {
+  const int64_t bt = side == 0 ? g.bt_a : g.bt_b, tp = side == 0 ? g.tp_a : g.tp_b;
+  CombineArgs ca;
+  std::memset(&ca, 0, sizeof(ca));
+  ca.src = s.ptr;
+  ca.ld = s.ld;
+  ca.dtype = s.dtype;
+  ca.rows = s.kcontig ? s.T : s.Kd;
+  ca.cols = s.kcontig ? s.Kd : s.T;
+  ca.b_rows = s.kcontig ? bt : g.bk;
+  ca.b_cols = s.kcontig ? g.bk : bt;
+  ca.n_rb = s.kcontig ? s.pt : s.pk;
+  ca.n_cb = s.kcontig ? s.pk : s.pt;
+  ca.p_rows = s.kcontig ? tp : g.kp;
+  ca.p_cols = s.kcontig ? g.kp : tp;
+  ca.t_rows = s.kcontig ? 1 : 0;
+  ca.re = s.re;
+  ca.rs = s.rs;
+  ca.ce = s.ce;
+  ca.cs = s.cs;
+  ca.leaves = leaves;
+  ca.num_leaves = g.R;
+  ca.side = side;
+  const int32_t* lists = reinterpret_cast<const int32_t*>(leaves + g.R);
+  ca.t_start = lists + p->list_off[side];
+  ca.t_blk = ca.t_start + g.R + 1;
+  ca.t_coef = reinterpret_cast<const float*>(ca.t_blk + p->list_nnz[side]);
+  ca.t_nnz = p->list_nnz[side];
+  ca.blk_t_shift = side == 0 ? 16 : 0;
+  ca.blk_k_shift = side == 0 ? 0 : 16;
+  ca.out = out;
+  ca.fmt = p->leaf_format;
+  return ca;
+}
+
+// Multiply-kernel arguments (tensor maps over the combined operands wa, wb).
+static bool direct_args(const Plan* p, const PassGeom& g, const Source& x, const Source& y, const EpilogueArgs& c,
+                        const LeafDesc* leaves, char* wa, char* wb, float* mbuf, int* status, DirectArgs* d) {
+  std::memset(d, 0, sizeof(*d));
   const bool f16 = p->leaf_format == FMM_LEAF_F16;
   // K-major planes: rows (plane, leaf, t), k contiguous, box BK k x tile t;
   // MN-major planes: rows (plane, leaf, k), t contiguous, box 64 t x BK k.
   const int bk_step = direct_gemm_bk(p->leaf_format);
   auto map = [&](CUtensorMap* m, const Source& s, char* buf, int64_t tp, int tile) {
-    return s.kcontig ? make_map_sw(m, buf, f16, planes * R * tp, kp, kp, bk_step, tile)
-                     : make_map_sw(m, buf, f16, planes * R * kp, tp, tp, 64, bk_step);
+    return s.kcontig ? make_map_sw(m, buf, f16, g.planes * g.R * tp, g.kp, g.kp, bk_step, tile)
+                     : make_map_sw(m, buf, f16, g.planes * g.R * g.kp, tp, tp, 64, bk_step);
   };
-  if (!map(&d.map_a, x, wa, tp_a, 128) || !map(&d.map_b, y, wb, tp_b, bn)) return FMM_ERR_CUDA;
-  d.a_mn = x.kcontig ? 0 : 1;
-  d.b_mn = y.kcontig ? 0 : 1;
-  d.c = c;
-  d.leaves = leaves;
-  d.num_leaves = R;
-  d.tp_a = tp_a;
-  d.tp_b = tp_b;
-  d.kp = kp;
-  d.mbuf = mbuf;
-  d.status = status;
-  d.timeout_ns = timeout_ns();
-  if (!cuda_ok(launch_direct_gemm(d, p->leaf_format, bn, st), "multiply launch")) return FMM_ERR_CUDA;
-  if (!store_m) return FMM_OK;
+  if (!map(&d->map_a, x, wa, g.tp_a, 128) || !map(&d->map_b, y, wb, g.tp_b, g.bn)) return false;
+  d->a_mn = x.kcontig ? 0 : 1;
+  d->b_mn = y.kcontig ? 0 : 1;
+  d->c = c;
+  d->leaves = leaves;
+  d->num_leaves = g.R;
+  d->tp_a = g.tp_a;
+  d->tp_b = g.tp_b;
+  d->kp = g.kp;
+  d->mbuf = mbuf;
+  d->status = status;
+  d->timeout_ns = timeout_ns();
+  return true;
+}
+
+// Output-pass arguments over the stored products mbuf.
+static OutArgs out_args(const Plan* p, const PassGeom& g, const EpilogueArgs& c, const LeafDesc* leaves,
+                        float* mbuf) {
   OutArgs o;
+  std::memset(&o, 0, sizeof(o));
   o.mbuf = mbuf;
-  o.tp_a = tp_a;
-  o.tp_b = tp_b;
+  o.tp_a = g.tp_a;
+  o.tp_b = g.tp_b;
   o.c = c;
   o.leaves = leaves;
-  o.num_leaves = R;
+  o.num_leaves = g.R;
   o.c_blocks = p->pm * p->pn;
   o.pn = p->pn;
-  {
-    const int32_t* lists = reinterpret_cast<const int32_t*>(leaves + R);
-    o.c_start = lists + p->list_off[2];
-    o.c_blk = o.c_start + R + 1;
-    o.c_coef = reinterpret_cast<const float*>(o.c_blk + p->list_nnz[2]);
-    o.c_nnz = p->list_nnz[2];
-  }
-  return cuda_ok(launch_out_combine(o, st), "output combination pass") ? FMM_OK : FMM_ERR_CUDA;
+  const int32_t* lists = reinterpret_cast<const int32_t*>(leaves + g.R);
+  o.c_start = lists + p->list_off[2];
+  o.c_blk = o.c_start + g.R + 1;
+  o.c_coef = reinterpret_cast<const float*>(o.c_blk + p->list_nnz[2]);
+  o.c_nnz = p->list_nnz[2];
+  return o;
+}
+
+// The pass schedule: the combination pass writes S_r (from x) and T_r (from
+// y) for every leaf into the workspace; the multiply kernel then streams
+// them and either adds W-weighted products into C in its epilogue or stores
+// them for the output pass.  FMM_ERR_WORKSPACE when the workspace is too
+// small.
+static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, const EpilogueArgs& c,
+                           const LeafDesc* leaves, int* status, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const PassGeom g = pass_geom(p, x, y, 0);
+  if (!ws || (uintptr_t)ws % 256 != 0 || (int64_t)ws_bytes < g.bytes_a + g.bytes_b) return FMM_ERR_WORKSPACE;
+  char* wa = static_cast<char*>(ws);
+  char* wb = wa + g.bytes_a;
+  // Stored leaf products unless the epilogue form is asked for: measured
+  // faster at every size (every SM gets (leaf, tile) units; the fused
+  // epilogue leaves SMs idle when tiles per leaf are few, and its C
+  // read-modify-writes cost more than one more bandwidth pass).
+  const bool want_m = p->schedule != FMM_SCHEDULE_PASS_EPILOGUE;
+  const bool store_m = want_m && g.R > 1 && p->pm * p->pn <= kMaxOutBlocks &&
+                       (int64_t)ws_bytes >= g.bytes_a + g.bytes_b + g.bytes_m;
+  float* mbuf = store_m ? reinterpret_cast<float*>(wb + g.bytes_b) : nullptr;
+  // B first: a scaling sequence that ends with a pass over B leaves it in L2
+  if (!cuda_ok(launch_combine(combine_args(p, g, y, 1, leaves, wb), st), "combination pass (B)")) return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_combine(combine_args(p, g, x, 0, leaves, wa), st), "combination pass (A)")) return FMM_ERR_CUDA;
+  DirectArgs d;
+  if (!direct_args(p, g, x, y, c, leaves, wa, wb, mbuf, status, &d)) return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_direct_gemm(d, p->leaf_format, g.bn, st), "multiply launch")) return FMM_ERR_CUDA;
+  if (!store_m) return FMM_OK;
+  return cuda_ok(launch_out_combine(out_args(p, g, c, leaves, mbuf), st), "output combination pass") ? FMM_OK
+                                                                                                     : FMM_ERR_CUDA;
 }
 
 // Run the flattened plan p: C (M x N) = X (M x K) Y (K x N) with X, Y given
@@ -465,6 +510,286 @@ static char* noalloc_scratch() {
     cache[dev] = static_cast<char*>(ptr);
   }
   return cache[dev];
+}
+
+// ---------------------------------------------------------------- batches
+
+constexpr int kBatchTileN = 128;
+
+// Steps a batch supports (Alg. 3 from no scaling).
+static int batch_steps(const char* steps) {
+  if (!steps || !*steps) return 0;
+  if (!std::strcmp(steps, "O")) return 1;
+  if (!std::strcmp(steps, "I")) return 2;
+  if (!std::strcmp(steps, "OI")) return 3;
+  return -1;
+}
+
+// Where each part of a batch lives in the workspace, computed identically
+// by fmm_batch_workspace_size and fmm_batch_create.
+struct BatchLayout {
+  size_t off_red[4], off_red_start[4];
+  size_t off_comb, off_comb_start, off_direct, off_unit_start, off_out, off_out_start;
+  size_t off_exp;                  // eA (sum M) | d (sum K) | eB (sum N), int32
+  int64_t sum_m, sum_k, sum_n;
+  std::vector<size_t> off_a, off_b, off_m;  // per problem, combined A / B and stored products
+  std::vector<PassGeom> geom;
+  size_t total;
+};
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static Source batch_source_a(const fmm_problem& q, const Plan* p, int dt, const int* eA, const int* d) {
+  return Source{q.A, q.lda, dt, true, q.M, q.K, p->pm, p->pk, eA, -1, d, +1};
+}
+static Source batch_source_b(const fmm_problem& q, const Plan* p, int dt, const int* d, const int* eB) {
+  return Source{q.B, q.ldb, dt, false, q.N, q.K, p->pn, p->pk, d, -1, eB, -1};
+}
+
+static fmm_status batch_layout(const fmm_problem* probs, int count, int dt, BatchLayout* L) {
+  size_t at = 0;
+  const size_t cnt = (size_t)count;
+  for (int k = 0; k < 4; ++k) {
+    L->off_red[k] = at;
+    at = align_up(at + cnt * sizeof(ReduceArgs), 256);
+    L->off_red_start[k] = at;
+    at = align_up(at + (cnt + 1) * 8, 256);
+  }
+  L->off_comb = at;
+  at = align_up(at + 2 * cnt * sizeof(CombineArgs), 256);
+  L->off_comb_start = at;
+  at = align_up(at + (2 * cnt + 1) * 8, 256);
+  L->off_direct = at;
+  at = align_up(at + cnt * sizeof(DirectArgs), 256);
+  L->off_unit_start = at;
+  at = align_up(at + (cnt + 1) * 8, 256);
+  L->off_out = at;
+  at = align_up(at + cnt * sizeof(OutArgs), 256);
+  L->off_out_start = at;
+  at = align_up(at + (cnt + 1) * 8, 256);
+  L->sum_m = L->sum_k = L->sum_n = 0;
+  for (int i = 0; i < count; ++i) {
+    L->sum_m += probs[i].M;
+    L->sum_k += probs[i].K;
+    L->sum_n += probs[i].N;
+  }
+  L->off_exp = at;
+  at = align_up(at + (size_t)(L->sum_m + L->sum_k + L->sum_n) * 4, 256);
+  L->off_a.resize(cnt);
+  L->off_b.resize(cnt);
+  L->off_m.resize(cnt);
+  L->geom.resize(cnt);
+  for (int i = 0; i < count; ++i) {
+    const Plan* p = reinterpret_cast<const Plan*>(probs[i].plan);
+    const Source x = batch_source_a(probs[i], p, dt, nullptr, nullptr);
+    const Source y = batch_source_b(probs[i], p, dt, nullptr, nullptr);
+    const PassGeom g = pass_geom(p, x, y, kBatchTileN);
+    L->geom[(size_t)i] = g;
+    L->off_a[(size_t)i] = at;
+    at += (size_t)g.bytes_a;
+    L->off_b[(size_t)i] = at;
+    at += (size_t)g.bytes_b;
+    L->off_m[(size_t)i] = at;
+    at += (size_t)g.bytes_m;
+  }
+  L->total = at;
+  return FMM_OK;
+}
+
+static fmm_status batch_check(const fmm_problem* probs, int count, int dt, const char* steps) {
+  if (!probs || count <= 0 || count > 30000 || !valid_dtype(dt) || batch_steps(steps) < 0) return FMM_ERR_ARG;
+  int fmt = -1;
+  for (int i = 0; i < count; ++i) {
+    const fmm_problem& q = probs[i];
+    const Plan* p = reinterpret_cast<const Plan*>(q.plan);
+    if (!p || !q.A || !q.B || !q.C) return FMM_ERR_ARG;
+    if (q.M <= 0 || q.K <= 0 || q.N <= 0 || q.lda < q.K || q.ldb < q.N || q.ldc < q.N) return FMM_ERR_SHAPE;
+    if (fmt >= 0 && p->leaf_format != fmt) return FMM_ERR_ARG;
+    fmt = p->leaf_format;
+    if (dt == FMM_DT_F16 && fmt == FMM_LEAF_BF16X3) return FMM_ERR_DTYPE;
+    if (p->pm * p->pn > kMaxOutBlocks || p->pm * p->pk > 64 || p->pk * p->pn > 64) return FMM_ERR_UNSUPPORTED;
+    if (ceil_div(q.M, p->pm) >= (1ll << 30) || ceil_div(q.N, p->pn) >= (1ll << 30) ||
+        ceil_div(q.K, p->pk) >= (1ll << 30))
+      return FMM_ERR_SHAPE;
+  }
+  return FMM_OK;
+}
+
+struct Batch {
+  int count = 0, dt = 0, fmt = 0, steps = 0;
+  char* ws = nullptr;
+  int* status = nullptr;
+  BatchLayout L;
+  int64_t red_total[4] = {0, 0, 0, 0};
+  int64_t comb_total = 0, unit_total = 0, out_total = 0;
+  int comb_tr = 32, out_tr = 32;
+  size_t comb_smem = 0, out_smem = 0;
+  DirectArgs layout;  // status, wait limit, operand layouts
+};
+
+static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
+  const int count = b->count, dt = b->dt;
+  BatchLayout& L = b->L;
+  char* ws = b->ws;
+  int* eA_all = reinterpret_cast<int*>(ws + L.off_exp);
+  int* d_all = eA_all + L.sum_m;
+  int* eB_all = d_all + L.sum_k;
+  const bool o_step = b->steps & 1, i_step = b->steps & 2;
+  std::vector<ReduceArgs> red[4];
+  std::vector<int64_t> red_start[4];
+  for (int k = 0; k < 4; ++k) {
+    red[k].resize((size_t)count);
+    red_start[k].assign((size_t)count + 1, 0);
+  }
+  std::vector<CombineArgs> comb(2 * (size_t)count);
+  std::vector<int64_t> comb_start(2 * (size_t)count + 1, 0);
+  std::vector<DirectArgs> dir((size_t)count);
+  std::vector<int64_t> unit_start((size_t)count + 1, 0);
+  std::vector<OutArgs> out((size_t)count);
+  std::vector<int64_t> out_start((size_t)count + 1, 0);
+  int64_t max_nb = 1, max_cb = 1;
+  for (int i = 0; i < count; ++i) {
+    const Plan* p = reinterpret_cast<const Plan*>(probs[i].plan);
+    max_nb = std::max(max_nb, std::max(p->pm * p->pk, p->pk * p->pn));
+    max_cb = std::max(max_cb, p->pm * p->pn);
+  }
+  b->comb_tr = combine_batched_rows(max_nb);
+  b->out_tr = out_batched_rows(max_cb);
+  int64_t om = 0, ok_ = 0, on = 0;
+  for (int i = 0; i < count; ++i) {
+    const fmm_problem& q = probs[i];
+    const Plan* p = reinterpret_cast<const Plan*>(q.plan);
+    if (ensure_uploaded(p) != FMM_OK) return FMM_ERR_CUDA;
+    const LeafDesc* leaves = p->dev;
+    int* eA = eA_all + om;
+    int* d = d_all + ok_;
+    int* eB = eB_all + on;
+    om += q.M;
+    ok_ += q.K;
+    on += q.N;
+    const size_t u = (size_t)i;
+    // scaling reductions: rows(A) -> eA, columns(A) -> d, columns(B) -> eB, rows(B) -> d
+    const int vec_a = vec_aligned_host(q.A, q.lda, dt), vec_b = vec_aligned_host(q.B, q.ldb, dt);
+    red[0][u] = ReduceArgs{q.A, q.M, q.K, q.lda, nullptr, +1, eA, vec_a, 0, 0};
+    red[1][u] = ReduceArgs{q.A, q.M, q.K, q.lda, o_step ? eA : nullptr, -1, d, vec_a, kBatchColRows,
+                           ceil_div(q.K, kBatchColSpan)};
+    red[2][u] = ReduceArgs{q.B, q.K, q.N, q.ldb, nullptr, -1, eB, vec_b, kBatchColRows, ceil_div(q.N, kBatchColSpan)};
+    red[3][u] = ReduceArgs{q.B, q.K, q.N, q.ldb, o_step ? eB : nullptr, -1, d, vec_b, 0, 0};
+    red_start[0][u + 1] = red_start[0][u] + q.M;
+    red_start[1][u + 1] = red_start[1][u] + red[1][u].gx * ceil_div(q.M, kBatchColRows);
+    red_start[2][u + 1] = red_start[2][u] + red[2][u].gx * ceil_div(q.K, kBatchColRows);
+    red_start[3][u + 1] = red_start[3][u] + q.K;
+    // passes and multiply
+    const Source x = batch_source_a(q, p, dt, o_step ? eA : nullptr, i_step ? d : nullptr);
+    const Source y = batch_source_b(q, p, dt, i_step ? d : nullptr, o_step ? eB : nullptr);
+    const PassGeom& g = L.geom[u];
+    char* wa = ws + L.off_a[u];
+    char* wb = ws + L.off_b[u];
+    float* mbuf = reinterpret_cast<float*>(ws + L.off_m[u]);
+    comb[2 * u] = combine_args(p, g, x, 0, leaves, wa);
+    comb[2 * u + 1] = combine_args(p, g, y, 1, leaves, wb);
+    for (int sd = 0; sd < 2; ++sd) {
+      const CombineArgs& ca = comb[2 * u + (size_t)sd];
+      comb_start[2 * u + (size_t)sd + 1] = comb_start[2 * u + (size_t)sd] + (ca.p_rows / b->comb_tr) * (ca.p_cols / 64);
+      b->comb_smem = std::max(b->comb_smem, combine_staged_smem(ca.n_rb * ca.n_cb, b->comb_tr, ca.t_nnz, g.R));
+    }
+    EpilogueArgs c;
+    c.C = q.C;
+    c.ldc = q.ldc;
+    c.M = q.M;
+    c.N = q.N;
+    c.bm = ceil_div(q.M, p->pm);
+    c.bn = ceil_div(q.N, p->pn);
+    c.eA = o_step ? eA : nullptr;
+    c.eB = o_step ? eB : nullptr;
+    c.vec_ok = ((uintptr_t)q.C % 16 == 0) && (q.ldc % 4 == 0) && (c.bn % 4 == 0) ? 1 : 0;
+    if (!direct_args(p, g, x, y, c, leaves, wa, wb, mbuf, b->status, &dir[u])) return FMM_ERR_CUDA;
+    unit_start[u + 1] = unit_start[u] + g.R * (g.tp_a / 128) * (g.tp_b / kBatchTileN);
+    out[u] = out_args(p, g, c, leaves, mbuf);
+    out_start[u + 1] = out_start[u] + ceil_div(c.bm, b->out_tr) * ceil_div(c.bn, 64);
+    b->out_smem = std::max(b->out_smem, (size_t)(p->pm * p->pn * b->out_tr * 256 + out[u].c_nnz * 8 +
+                                                 (out[u].num_leaves + 1) * 4));
+  }
+  if (b->comb_smem > 200 * 1024 || b->out_smem > 200 * 1024) {
+    t_last_error = "batch: a plan's term lists do not fit the passes' shared memory";
+    return FMM_ERR_UNSUPPORTED;
+  }
+  for (int k = 0; k < 4; ++k) b->red_total[k] = red_start[k][(size_t)count];
+  b->comb_total = comb_start[2 * (size_t)count];
+  b->unit_total = unit_start[(size_t)count];
+  b->out_total = out_start[(size_t)count];
+  b->layout = dir[0];
+  // copy the tables into the workspace
+  auto put = [&](size_t off, const void* src, size_t bytes) {
+    return cuda_ok(cudaMemcpy(ws + off, src, bytes, cudaMemcpyHostToDevice), "batch table copy");
+  };
+  for (int k = 0; k < 4; ++k)
+    if (!put(L.off_red[k], red[k].data(), red[k].size() * sizeof(ReduceArgs)) ||
+        !put(L.off_red_start[k], red_start[k].data(), red_start[k].size() * 8))
+      return FMM_ERR_CUDA;
+  if (!put(L.off_comb, comb.data(), comb.size() * sizeof(CombineArgs)) ||
+      !put(L.off_comb_start, comb_start.data(), comb_start.size() * 8) ||
+      !put(L.off_direct, dir.data(), dir.size() * sizeof(DirectArgs)) ||
+      !put(L.off_unit_start, unit_start.data(), unit_start.size() * 8) ||
+      !put(L.off_out, out.data(), out.size() * sizeof(OutArgs)) ||
+      !put(L.off_out_start, out_start.data(), out_start.size() * 8))
+    return FMM_ERR_CUDA;
+  return FMM_OK;
+}
+
+static fmm_status batch_run(const Batch* b, cudaStream_t st) {
+  const BatchLayout& L = b->L;
+  char* ws = b->ws;
+  int* eA_all = reinterpret_cast<int*>(ws + L.off_exp);
+  int* d_all = eA_all + L.sum_m;
+  int* eB_all = d_all + L.sum_k;
+  auto red = [&](int k) { return reinterpret_cast<const ReduceArgs*>(ws + L.off_red[k]); };
+  auto red_start = [&](int k) { return reinterpret_cast<const int64_t*>(ws + L.off_red_start[k]); };
+  const bool o_step = b->steps & 1, i_step = b->steps & 2;
+  const int n = b->count;
+  if (o_step && i_step) {
+    // rows(A) -> eA; columns(2^-eA A) -> d; columns(B) -> eB; rows(2^-eB B) with d -> d
+    if (!cuda_ok(launch_fill(d_all, L.sum_k + L.sum_n, kZeroExp, st), "batch fill") ||
+        !cuda_ok(launch_row_exp_batched(red(0), red_start(0), n, b->red_total[0], b->dt, false, kRowOStep, b->status, st),
+                 "batch row reduction") ||
+        !cuda_ok(launch_col_exp_batched(red(1), red_start(1), n, b->red_total[1], b->dt, true, b->status, st),
+                 "batch column reduction") ||
+        !cuda_ok(launch_col_exp_batched(red(2), red_start(2), n, b->red_total[2], b->dt, false, b->status, st),
+                 "batch column reduction") ||
+        !cuda_ok(launch_zero_sentinel(eB_all, L.sum_n, st), "batch fix-up") ||
+        !cuda_ok(launch_row_exp_batched(red(3), red_start(3), n, b->red_total[3], b->dt, true, kRowIStep, b->status, st),
+                 "batch row reduction"))
+      return FMM_ERR_CUDA;
+  } else if (o_step) {
+    if (!cuda_ok(launch_fill(eB_all, L.sum_n, kZeroExp, st), "batch fill") ||
+        !cuda_ok(launch_row_exp_batched(red(0), red_start(0), n, b->red_total[0], b->dt, false, kRowOStep, b->status, st),
+                 "batch row reduction") ||
+        !cuda_ok(launch_col_exp_batched(red(2), red_start(2), n, b->red_total[2], b->dt, false, b->status, st),
+                 "batch column reduction") ||
+        !cuda_ok(launch_zero_sentinel(eB_all, L.sum_n, st), "batch fix-up"))
+      return FMM_ERR_CUDA;
+  } else if (i_step) {
+    if (!cuda_ok(launch_fill(d_all, L.sum_k, kZeroExp, st), "batch fill") ||
+        !cuda_ok(launch_col_exp_batched(red(1), red_start(1), n, b->red_total[1], b->dt, false, b->status, st),
+                 "batch column reduction") ||
+        !cuda_ok(launch_row_exp_batched(red(3), red_start(3), n, b->red_total[3], b->dt, false, kRowIStep, b->status, st),
+                 "batch row reduction"))
+      return FMM_ERR_CUDA;
+  }
+  if (!cuda_ok(launch_combine_batched(reinterpret_cast<const CombineArgs*>(ws + L.off_comb),
+                                      reinterpret_cast<const int64_t*>(ws + L.off_comb_start), 2 * n, b->comb_total,
+                                      b->dt, b->fmt, b->comb_tr, b->comb_smem, st),
+               "batch combination pass") ||
+      !cuda_ok(launch_direct_gemm_batched(b->layout, reinterpret_cast<const DirectArgs*>(ws + L.off_direct),
+                                          reinterpret_cast<const int64_t*>(ws + L.off_unit_start), n, b->unit_total,
+                                          b->fmt, kBatchTileN, st),
+               "batch multiply") ||
+      !cuda_ok(launch_out_combine_batched(reinterpret_cast<const OutArgs*>(ws + L.off_out),
+                                          reinterpret_cast<const int64_t*>(ws + L.off_out_start), n, b->out_total,
+                                          b->out_tr, b->out_smem, st),
+               "batch output pass"))
+    return FMM_ERR_CUDA;
+  return FMM_OK;
 }
 
 }  // namespace fmm
@@ -774,6 +1099,59 @@ const char* fmm_status_string(fmm_status s) {
     case FMM_ERR_UNSUPPORTED: return "plan outside the supported range";
   }
   return "unknown status";
+}
+
+fmm_status fmm_batch_workspace_size(const fmm_problem* problems, int count, int in_dtype, const char* steps,
+                                    size_t* bytes) {
+  if (!bytes) return FMM_ERR_ARG;
+  fmm_status s = batch_check(problems, count, in_dtype, steps);
+  if (s != FMM_OK) return s;
+  BatchLayout L;
+  batch_layout(problems, count, in_dtype, &L);
+  *bytes = L.total;
+  return FMM_OK;
+}
+
+fmm_status fmm_batch_create(fmm_batch_t* out, const fmm_problem* problems, int count, int in_dtype,
+                            const char* steps, void* ws, size_t ws_bytes) {
+  if (!out) return FMM_ERR_ARG;
+  *out = nullptr;
+  fmm_status s = batch_check(problems, count, in_dtype, steps);
+  if (s != FMM_OK) return s;
+  Batch* b = new Batch();
+  b->count = count;
+  b->dt = in_dtype;
+  b->fmt = reinterpret_cast<const Plan*>(problems[0].plan)->leaf_format;
+  b->steps = batch_steps(steps);
+  batch_layout(problems, count, in_dtype, &b->L);
+  if (!ws || (uintptr_t)ws % 256 != 0 || ws_bytes < b->L.total) {
+    delete b;
+    return FMM_ERR_WORKSPACE;
+  }
+  b->ws = static_cast<char*>(ws);
+  b->status = status_ptr();
+  if (!b->status) {
+    delete b;
+    return FMM_ERR_CUDA;
+  }
+  s = batch_build(b, problems);
+  if (s != FMM_OK) {
+    delete b;
+    return s;
+  }
+  *out = reinterpret_cast<fmm_batch_t>(b);
+  return FMM_OK;
+}
+
+fmm_status fmm_batch_run(fmm_batch_t batch, void* stream) {
+  const Batch* b = reinterpret_cast<const Batch*>(batch);
+  if (!b) return FMM_ERR_ARG;
+  return batch_run(b, as_stream(stream));
+}
+
+fmm_status fmm_batch_destroy(fmm_batch_t batch) {
+  delete reinterpret_cast<Batch*>(batch);
+  return FMM_OK;
 }
 
 const char* fmm_version(void) { return "fmm-gb300 0.1 (sm_103a)"; }

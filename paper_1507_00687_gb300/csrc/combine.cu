@@ -175,11 +175,10 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs a) 
 constexpr int kMaxStaged = 64;
 
 template <int DT, int FMT, int TR, int RPT>
-__global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_kernel(const CombineArgs a) {
+__device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_t bx, int64_t by, float4* tile4) {
   // RPT rows per thread: rows tr + (TR / RPT) q, q < RPT; 4 columns each
   constexpr int kT = TR * 16 / RPT;
-  extern __shared__ float4 tile4[];  // [block][TR][16], then the term list
-  const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * kTC;
+  const int64_t r0 = by * TR, c0 = bx * kTC;
   const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15, tc = tq * 4;
   const int es = DT == kF32 ? 4 : 2;
   const bool vec_ok = ((uintptr_t)a.src % (4 * es) == 0) && (a.ld % 4 == 0) && (a.b_cols % 4 == 0) &&
@@ -269,6 +268,35 @@ __global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_kernel(const Com
   }
 }
 
+template <int DT, int FMT, int TR, int RPT>
+__global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_kernel(const CombineArgs a) {
+  extern __shared__ float4 tile4[];  // [block][TR][16], then the term list
+  combine_staged_body<DT, FMT, TR, RPT>(a, blockIdx.x, blockIdx.y, tile4);
+}
+
+// Index of the problem whose [start[p], start[p + 1]) range holds idx.
+__device__ __forceinline__ int find_problem(const int64_t* start, int count, int64_t idx) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= idx) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Batched form: CTA b belongs to entry p with start[p] <= b < start[p + 1]
+// and covers tile (local mod gx, local / gx), gx = p_cols / 64.
+template <int DT, int FMT, int TR, int RPT>
+__global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_batched_kernel(const CombineArgs* args,
+                                                                              const int64_t* start, int count) {
+  extern __shared__ float4 tile4[];
+  const int p = find_problem(start, count, blockIdx.x);
+  const CombineArgs& a = args[p];
+  const int64_t local = blockIdx.x - __ldg(start + p), gx = a.p_cols / kTC;
+  combine_staged_body<DT, FMT, TR, RPT>(a, local % gx, local / gx, tile4);
+}
+
 // Shared memory of the staged form: block tiles plus the term list.
 inline size_t staged_smem(int nb, int tr, int64_t nnz, int64_t leaves) {
   return (size_t)nb * tr * 256 + (size_t)nnz * 8 + (size_t)(leaves + 1) * 4;
@@ -333,11 +361,10 @@ cudaError_t launch_dt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
 constexpr int kOutBatch = 4;
 
 template <int TR>
-__global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
-  extern __shared__ float4 acc4[];  // [c_blocks][TR][16], then the term list
+__device__ __forceinline__ void out_combine_body(const OutArgs& a, int64_t bx, int64_t by, float4* acc4) {
   const EpilogueArgs& c = a.c;
   const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15;
-  const int64_t lr = (int64_t)blockIdx.y * TR + tr, lc = (int64_t)blockIdx.x * kTC + tq * 4;
+  const int64_t lr = by * TR + tr, lc = bx * kTC + tq * 4;
   const int pn = (int)a.pn;
   const int R = (int)a.num_leaves;
   const int nnz = (int)a.c_nnz;
@@ -406,6 +433,24 @@ __global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
   }
 }
 
+template <int TR>
+__global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
+  extern __shared__ float4 acc4[];  // [c_blocks][TR][16], then the term list
+  out_combine_body<TR>(a, blockIdx.x, blockIdx.y, acc4);
+}
+
+// Batched form: CTA b belongs to problem p with start[p] <= b < start[p + 1]
+// and covers position tile (local mod gx, local / gx), gx = ceil(bn / 64).
+template <int TR>
+__global__ void __launch_bounds__(TR * 16) out_combine_batched_kernel(const OutArgs* args, const int64_t* start,
+                                                                      int count) {
+  extern __shared__ float4 acc4[];
+  const int p = find_problem(start, count, blockIdx.x);
+  const OutArgs& a = args[p];
+  const int64_t local = blockIdx.x - __ldg(start + p), gx = (a.c.bn + kTC - 1) / kTC;
+  out_combine_body<TR>(a, local % gx, local / gx, acc4);
+}
+
 }  // namespace
 
 cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st) {
@@ -438,6 +483,91 @@ cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st) {
   else go(std::integral_constant<int, 2>());
   return cudaGetLastError();
 }
+
+// Rows per CTA of the staged combination for a block count (tiles <= 32 KB).
+static int staged_tr(int64_t nb) { return nb <= 4 ? 32 : nb <= 8 ? 16 : nb <= 16 ? 8 : nb <= 32 ? 4 : 2; }
+// Rows per CTA of the output pass for a C block count (accumulators <= 48 KB).
+static int out_tr(int64_t nb) { return nb <= 6 ? 32 : nb <= 12 ? 16 : nb <= 24 ? 8 : nb <= 48 ? 4 : 2; }
+
+int combine_batched_rows(int64_t max_blocks) { return staged_tr(max_blocks); }
+int out_batched_rows(int64_t max_c_blocks) { return out_tr(max_c_blocks); }
+
+template <int DT, int FMT, int TR>
+static void launch_combine_batched_tr(const CombineArgs* args, const int64_t* start, int count, int64_t total,
+                                      size_t smem, cudaStream_t st) {
+  constexpr int RPT = TR == 32 ? 2 : 1;
+  static bool attr_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_done[dev]) {
+    cudaFuncSetAttribute(combine_staged_batched_kernel<DT, FMT, TR, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kStagedSmemMax);
+    attr_done[dev] = true;
+  }
+  combine_staged_batched_kernel<DT, FMT, TR, RPT><<<(unsigned)total, TR * 16 / RPT, smem, st>>>(args, start, count);
+}
+
+template <int DT, int FMT>
+static void launch_combine_batched_fmt(const CombineArgs* args, const int64_t* start, int count, int64_t total,
+                                       int tr, size_t smem, cudaStream_t st) {
+  switch (tr) {
+    case 32: launch_combine_batched_tr<DT, FMT, 32>(args, start, count, total, smem, st); break;
+    case 16: launch_combine_batched_tr<DT, FMT, 16>(args, start, count, total, smem, st); break;
+    case 8: launch_combine_batched_tr<DT, FMT, 8>(args, start, count, total, smem, st); break;
+    case 4: launch_combine_batched_tr<DT, FMT, 4>(args, start, count, total, smem, st); break;
+    default: launch_combine_batched_tr<DT, FMT, 2>(args, start, count, total, smem, st); break;
+  }
+}
+
+cudaError_t launch_combine_batched(const CombineArgs* args, const int64_t* start, int count, int64_t total, int dt,
+                                   int fmt, int tr, size_t smem, cudaStream_t st) {
+  if (total == 0 || count == 0) return cudaSuccess;
+  if (smem > kStagedSmemMax) return cudaErrorInvalidValue;
+  KernelTimer timer("combine", st);
+#define FMM_CB(DT)                                                                                   \
+  switch (fmt) {                                                                                     \
+    case FMM_LEAF_BF16: launch_combine_batched_fmt<DT, FMM_LEAF_BF16>(args, start, count, total, tr, smem, st); break; \
+    case FMM_LEAF_F16: launch_combine_batched_fmt<DT, FMM_LEAF_F16>(args, start, count, total, tr, smem, st); break;   \
+    default: launch_combine_batched_fmt<DT, FMM_LEAF_BF16X3>(args, start, count, total, tr, smem, st); break;         \
+  }
+  switch (dt) {
+    case kF32: FMM_CB(kF32) break;
+    case kBF16: FMM_CB(kBF16) break;
+    default: FMM_CB(kF16) break;
+  }
+#undef FMM_CB
+  return cudaGetLastError();
+}
+
+cudaError_t launch_out_combine_batched(const OutArgs* args, const int64_t* start, int count, int64_t total, int tr,
+                                       size_t smem, cudaStream_t st) {
+  if (total == 0 || count == 0) return cudaSuccess;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  KernelTimer timer("combine", st);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  auto go = [&](auto tr_tag) {
+    constexpr int TR = decltype(tr_tag)::value;
+    static bool attr_done[64] = {};
+    if (!attr_done[dev]) {
+      cudaFuncSetAttribute(out_combine_batched_kernel<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_done[dev] = true;
+    }
+    out_combine_batched_kernel<TR><<<(unsigned)total, TR * 16, smem, st>>>(args, start, count);
+  };
+  switch (tr) {
+    case 32: go(std::integral_constant<int, 32>()); break;
+    case 16: go(std::integral_constant<int, 16>()); break;
+    case 8: go(std::integral_constant<int, 8>()); break;
+    case 4: go(std::integral_constant<int, 4>()); break;
+    default: go(std::integral_constant<int, 2>()); break;
+  }
+  return cudaGetLastError();
+}
+
+size_t combine_staged_smem(int64_t nb, int tr, int64_t nnz, int64_t leaves) { return staged_smem((int)nb, tr, nnz, leaves); }
 
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st) {
   if (a.p_rows % kTR != 0 || a.p_cols % kTC != 0 || a.p_rows / kTR > 65535) return cudaErrorInvalidValue;

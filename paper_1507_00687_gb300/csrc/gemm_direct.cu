@@ -27,6 +27,7 @@
 // word, stops all roles, waits for its own copies and MMAs, frees its TMEM
 // and returns.
 #include <algorithm>
+#include <cstring>
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -88,8 +89,31 @@ __device__ __forceinline__ uint64_t tile_desc(uint32_t saddr, int k16) {
   else return smem_desc_sw64(saddr + k16 * 32);
 }
 
+// What one launch covers: one problem (`one`), or, when `tab` is set, the
+// `count` problems of a batch whose (leaf, tile) units are numbered
+// consecutively: units of problem p are [unit_start[p], unit_start[p + 1]).
+// Batched problems always store their leaf products.
+struct DirectLaunch {
+  DirectArgs one;
+  const DirectArgs* tab;
+  const int64_t* unit_start;
+  int count;
+  int64_t total_units;
+};
+
+__device__ __forceinline__ int find_unit_problem(const int64_t* start, int count, int64_t u) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <int FMT, int BN, bool A_MN, bool B_MN>
-__global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_constant__ DirectArgs args) {
+__global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_constant__ DirectLaunch launch) {
+  const DirectArgs& args = launch.one;  // the single problem (status, timeout for both forms)
   using C = Cfg<FMT, BN>;
   constexpr int BK = C::BK;
   extern __shared__ uint8_t smem_raw[];
@@ -123,27 +147,46 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int64_t ntm = args.tp_a / BM;
-  const int64_t ntn = args.tp_b / BN;
-  const int64_t ntiles = ntm * ntn;
-  const int64_t KT = args.kp / BK;
-  const int64_t NL = args.num_leaves;
-  const bool store_m = args.mbuf != nullptr;
-  const int64_t nunits = store_m ? NL * ntiles : ntiles;  // leaves of a tile count as one unit when fused
-  const int64_t my_units = ((nunits - blockIdx.x + gridDim.x - 1) / gridDim.x) * (store_m ? 1 : NL);
-  // The j-th unit of this CTA: its leaf and tile position.
-  auto unit = [&](int64_t j, int64_t* leaf, int64_t* tm, int64_t* tn) {
+  const bool batched = launch.tab != nullptr;
+  const bool store_m = batched || args.mbuf != nullptr;
+  int64_t my_units;
+  if (batched) {
+    my_units = (launch.total_units - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  } else {
+    const int64_t ntiles = (args.tp_a / BM) * (args.tp_b / BN);
+    const int64_t nunits = store_m ? args.num_leaves * ntiles : ntiles;  // a tile's leaves: one unit when fused
+    my_units = ((nunits - blockIdx.x + gridDim.x - 1) / gridDim.x) * (store_m ? 1 : args.num_leaves);
+  }
+  // The j-th unit of this CTA: its problem, leaf, tile position and k steps.
+  struct Unit {
+    const DirectArgs* a;
+    int64_t leaf, tm, tn, kt;
+  };
+  auto unit = [&](int64_t j) {
+    Unit w;
+    int64_t local;
+    if (batched) {
+      const int64_t u = blockIdx.x + j * gridDim.x;
+      const int p = find_unit_problem(launch.unit_start, launch.count, u);
+      w.a = launch.tab + p;
+      local = u - __ldg(launch.unit_start + p);
+    } else {
+      w.a = &args;
+      local = blockIdx.x + j * gridDim.x;
+    }
+    const int64_t ntn = w.a->tp_b / BN, ntiles = (w.a->tp_a / BM) * ntn;
     int64_t tile;
     if (store_m) {
-      const int64_t u = blockIdx.x + j * gridDim.x;
-      *leaf = u / ntiles;
-      tile = u % ntiles;
+      w.leaf = local / ntiles;
+      tile = local % ntiles;
     } else {
-      tile = blockIdx.x + (j / NL) * gridDim.x;
-      *leaf = j % NL;
+      tile = blockIdx.x + (j / w.a->num_leaves) * gridDim.x;
+      w.leaf = j % w.a->num_leaves;
     }
-    *tm = tile / ntn;
-    *tn = tile % ntn;
+    w.tm = tile / ntn;
+    w.tn = tile % ntn;
+    w.kt = w.a->kp / BK;
+    return w;
   };
 
   if (warp == kTmaWarp) {
@@ -153,26 +196,26 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
       uint32_t phase = 0;
       bool ok = true;
       uint32_t armed = 0, armed_parity = 0;  // per stage: copy issued, parity it completes
-      const int64_t iters = my_units * KT;
-      for (int64_t i = 0; i < iters && ok; ++i) {
-        const int64_t kt = i % KT;
-        int64_t leaf, tm, tn;
-        unit(i / KT, &leaf, &tm, &tn);
-        if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
-        uint8_t* st = smem + stage * C::kStage;
-        mbar_arrive_expect_tx(&full[stage], (uint32_t)C::kStage);
-        const int64_t k0 = kt * BK, ta = tm * BM, tb = tn * BN;
-        load_tile<A_MN, BK>(st, &args.map_a, BM, leaf, args.tp_a, args.kp, ta, k0, &full[stage]);
-        load_tile<B_MN, BK>(st + C::kSplit * C::kATile, &args.map_b, BN, leaf, args.tp_b, args.kp, tb, k0,
-                            &full[stage]);
-        if constexpr (C::kSplit == 2) {
-          load_tile<A_MN, BK>(st + C::kATile, &args.map_a, BM, NL + leaf, args.tp_a, args.kp, ta, k0, &full[stage]);
-          load_tile<B_MN, BK>(st + 2 * C::kATile + C::kBTile, &args.map_b, BN, NL + leaf, args.tp_b, args.kp, tb, k0,
-                              &full[stage]);
+      for (int64_t j = 0; j < my_units && ok; ++j) {
+        const Unit w = unit(j);
+        const DirectArgs& a = *w.a;
+        const int64_t NL = a.num_leaves;
+        for (int64_t kt = 0; kt < w.kt && ok; ++kt) {
+          if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
+          uint8_t* st = smem + stage * C::kStage;
+          mbar_arrive_expect_tx(&full[stage], (uint32_t)C::kStage);
+          const int64_t k0 = kt * BK, ta = w.tm * BM, tb = w.tn * BN;
+          load_tile<A_MN, BK>(st, &a.map_a, BM, w.leaf, a.tp_a, a.kp, ta, k0, &full[stage]);
+          load_tile<B_MN, BK>(st + C::kSplit * C::kATile, &a.map_b, BN, w.leaf, a.tp_b, a.kp, tb, k0, &full[stage]);
+          if constexpr (C::kSplit == 2) {
+            load_tile<A_MN, BK>(st + C::kATile, &a.map_a, BM, NL + w.leaf, a.tp_a, a.kp, ta, k0, &full[stage]);
+            load_tile<B_MN, BK>(st + 2 * C::kATile + C::kBTile, &a.map_b, BN, NL + w.leaf, a.tp_b, a.kp, tb, k0,
+                                &full[stage]);
+          }
+          armed |= 1u << stage;
+          armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
+          if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
         }
-        armed |= 1u << stage;
-        armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
-        if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
       }
       if (!ok) *abort_flag = 1;
       // No copy may still be writing shared memory when the CTA exits: wait
@@ -196,6 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
       const uint32_t sbase = smem_u32(smem);
       for (int64_t j = 0; j < my_units && ok; ++j) {
         {
+          const int64_t KT = unit(j).kt;
           const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
           if (!mbar_wait_bounded(&tempty[buf], aph ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
           tc_fence_after();
@@ -240,17 +284,18 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
     bool ok = true;
     const int row = warp * 32 + lane;  // TMEM lane = tile row
     for (int64_t j = 0; j < my_units && ok; ++j) {
-      int64_t leaf, tm, tn;
-      unit(j, &leaf, &tm, &tn);
-      const int64_t ml = tm * BM + row;
+      const Unit w = unit(j);
+      const DirectArgs& a = *w.a;
+      const int64_t leaf = w.leaf, tn = w.tn;
+      const int64_t ml = w.tm * BM + row;
       const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
       // warp-uniform outcome: the TMEM loads below are .sync.aligned
       ok = __all_sync(0xffffffffu, mbar_wait_bounded(&tfull[buf], aph, abort_flag, args.timeout_ns));
       if (!ok) break;
       tc_fence_after();
-      const LeafDesc* L = args.leaves + leaf;
+      const LeafDesc* L = a.leaves + leaf;
       // stored products: M_r (padded tp_a x tp_b, fp32) row ml, from column tn BN
-      float* mrow = store_m ? args.mbuf + (leaf * args.tp_a + ml) * args.tp_b + tn * BN : nullptr;
+      float* mrow = store_m ? a.mbuf + (leaf * a.tp_a + ml) * a.tp_b + tn * BN : nullptr;
 #pragma unroll 1
       for (int cc = 0; cc < BN / 32; ++cc) {
         uint32_t r[32];
@@ -260,8 +305,8 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
           for (int q = 0; q < 8; ++q)
             *reinterpret_cast<uint4*>(mrow + cc * 32 + 4 * q) =
                 make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-        } else if (ml < args.c.bm) {
-          epi_chunk(args.c, L, ml, tn * BN + cc * 32, r);
+        } else if (ml < a.c.bm) {
+          epi_chunk(a.c, L, ml, tn * BN + cc * 32, r);
         }
       }
       tc_fence_before();
@@ -282,7 +327,8 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
 
 // Launch one instantiation: grid = min(tiles, SMs), one CTA per SM.
 template <int FMT, int BN, bool A_MN, bool B_MN>
-cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
+cudaError_t launch_cfg(const DirectArgs& a, const DirectArgs* tab, const int64_t* unit_start, int count,
+                       int64_t total_units, cudaStream_t st) {
   using C = Cfg<FMT, BN>;
   auto kern = direct_fmm_kernel<FMT, BN, A_MN, B_MN>;
   static bool attr_set[64] = {false};
@@ -294,32 +340,48 @@ cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  if (a.tp_a % BM != 0 || a.tp_b % BN != 0 || a.kp % C::BK != 0) return cudaErrorInvalidValue;
-  const int64_t ntiles = (a.tp_a / BM) * (a.tp_b / BN);
-  if (ntiles == 0 || a.num_leaves == 0) return cudaSuccess;
-  const int64_t units = a.mbuf ? ntiles * a.num_leaves : ntiles;
+  DirectLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  int64_t units;
+  if (tab) {
+    L.one = a;  // status and timeout
+    L.tab = tab;
+    L.unit_start = unit_start;
+    L.count = count;
+    L.total_units = total_units;
+    units = total_units;
+  } else {
+    if (a.tp_a % BM != 0 || a.tp_b % BN != 0 || a.kp % C::BK != 0) return cudaErrorInvalidValue;
+    const int64_t ntiles = (a.tp_a / BM) * (a.tp_b / BN);
+    if (ntiles == 0 || a.num_leaves == 0) return cudaSuccess;
+    L.one = a;
+    units = a.mbuf ? ntiles * a.num_leaves : ntiles;
+  }
+  if (units == 0) return cudaSuccess;
   const int64_t grid = std::min<int64_t>(units, device_sm_count());
   KernelTimer timer("multiply", st);
-  kern<<<(unsigned)grid, kThreads, C::kSmem, st>>>(a);
+  kern<<<(unsigned)grid, kThreads, C::kSmem, st>>>(L);
   return cudaGetLastError();
 }
 
 // Operand layouts used: forward (A K-major, B MN-major), dA = dC B^T (both
 // K-major), dB = A^T dC (both MN-major).
 template <int FMT, int BN>
-cudaError_t launch_layout(const DirectArgs& a, cudaStream_t st) {
-  if (!a.a_mn && a.b_mn) return launch_cfg<FMT, BN, false, true>(a, st);
-  if (!a.a_mn && !a.b_mn) return launch_cfg<FMT, BN, false, false>(a, st);
-  if (a.a_mn && a.b_mn) return launch_cfg<FMT, BN, true, true>(a, st);
+cudaError_t launch_layout(const DirectArgs& a, const DirectArgs* tab, const int64_t* us, int count, int64_t total,
+                          cudaStream_t st) {
+  if (!a.a_mn && a.b_mn) return launch_cfg<FMT, BN, false, true>(a, tab, us, count, total, st);
+  if (!a.a_mn && !a.b_mn) return launch_cfg<FMT, BN, false, false>(a, tab, us, count, total, st);
+  if (a.a_mn && a.b_mn) return launch_cfg<FMT, BN, true, true>(a, tab, us, count, total, st);
   return cudaErrorNotSupported;
 }
 
 template <int BN>
-cudaError_t launch_bn(const DirectArgs& a, int fmt, cudaStream_t st) {
+cudaError_t launch_bn(const DirectArgs& a, int fmt, const DirectArgs* tab, const int64_t* us, int count,
+                      int64_t total, cudaStream_t st) {
   switch (fmt) {
-    case FMM_LEAF_BF16: return launch_layout<FMM_LEAF_BF16, BN>(a, st);
-    case FMM_LEAF_F16: return launch_layout<FMM_LEAF_F16, BN>(a, st);
-    default: return launch_layout<FMM_LEAF_BF16X3, BN>(a, st);
+    case FMM_LEAF_BF16: return launch_layout<FMM_LEAF_BF16, BN>(a, tab, us, count, total, st);
+    case FMM_LEAF_F16: return launch_layout<FMM_LEAF_F16, BN>(a, tab, us, count, total, st);
+    default: return launch_layout<FMM_LEAF_BF16X3, BN>(a, tab, us, count, total, st);
   }
 }
 
@@ -330,7 +392,15 @@ int direct_gemm_bk(int leaf_format) {
 }
 
 cudaError_t launch_direct_gemm(const DirectArgs& a, int leaf_format, int bn, cudaStream_t st) {
-  return bn == 256 ? direct::launch_bn<256>(a, leaf_format, st) : direct::launch_bn<128>(a, leaf_format, st);
+  return bn == 256 ? direct::launch_bn<256>(a, leaf_format, nullptr, nullptr, 0, 0, st)
+                   : direct::launch_bn<128>(a, leaf_format, nullptr, nullptr, 0, 0, st);
+}
+
+cudaError_t launch_direct_gemm_batched(const DirectArgs& layout, const DirectArgs* tab, const int64_t* unit_start,
+                                       int count, int64_t total_units, int leaf_format, int bn, cudaStream_t st) {
+  if (count == 0 || total_units == 0) return cudaSuccess;
+  return bn == 256 ? direct::launch_bn<256>(layout, leaf_format, tab, unit_start, count, total_units, st)
+                   : direct::launch_bn<128>(layout, leaf_format, tab, unit_start, count, total_units, st);
 }
 
 }  // namespace fmm

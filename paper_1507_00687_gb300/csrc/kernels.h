@@ -17,6 +17,32 @@ cudaError_t launch_row_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
 cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t ld, const int* re, int rs,
                            int* out, int* status, cudaStream_t st);
 cudaError_t launch_zero_sentinel(int* p, int64_t n, cudaStream_t st);
+
+// One problem of a batched reduction (rows: R x C, ld; shift: column
+// exponents for row reductions, row exponents for column reductions, sign
+// `sign`, nullable; out: per-row or per-column result).  gx, rows_per_cta:
+// the column-reduction CTA grid of this problem.
+struct ReduceArgs {
+  const void* X;
+  int64_t R, C, ld;
+  const int* shift;
+  int sign;
+  int* out;
+  int vec;
+  int rows_per_cta;
+  int64_t gx;
+};
+constexpr int kBatchColRows = 64;  // rows per CTA of a batched column reduction
+constexpr int kBatchColSpan = 2048;  // columns per CTA of a column reduction
+
+// Batched reductions over `count` problems of one element type.  args and
+// start live in device memory: start[p] = first warp (row reductions: one
+// row per warp) or first CTA (column reductions: args[p].gx spans x
+// ceil(R / rows_per_cta) chunks) of problem p, start[count] the total.
+cudaError_t launch_row_exp_batched(const ReduceArgs* args, const int64_t* start, int count, int64_t total, int dt,
+                                   bool shift, int mode, int* status, cudaStream_t st);
+cudaError_t launch_col_exp_batched(const ReduceArgs* args, const int64_t* start, int count, int64_t total, int dt,
+                                   bool shift, int* status, cudaStream_t st);
 cudaError_t launch_fill(int* p, int64_t n, int v, cudaStream_t st);
 
 
@@ -141,8 +167,30 @@ struct OutArgs {
 constexpr int kMaxOutBlocks = 96;
 cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st);
 
+// Batched combination / output passes over `count` entries whose arguments
+// live in device memory; start[p] is the first CTA of entry p (combination:
+// (p_rows / tr) x (p_cols / 64) CTAs; output: ceil(bm / tr) x ceil(bn / 64)),
+// start[count] = total.  One element type and leaf format per launch; tr
+// (rows per CTA) from combine_batched_rows / out_batched_rows for the largest
+// block count of the batch; smem the largest entry's shared memory.
+int combine_batched_rows(int64_t max_blocks);
+int out_batched_rows(int64_t max_c_blocks);
+size_t combine_staged_smem(int64_t nb, int tr, int64_t nnz, int64_t leaves);
+cudaError_t launch_combine_batched(const CombineArgs* args, const int64_t* start, int count, int64_t total, int dt,
+                                   int fmt, int tr, size_t smem, cudaStream_t st);
+cudaError_t launch_out_combine_batched(const OutArgs* args, const int64_t* start, int count, int64_t total, int tr,
+                                       size_t smem, cudaStream_t st);
+
 // bn: tile width along N (128 or 256).
 cudaError_t launch_direct_gemm(const DirectArgs& args, int leaf_format, int bn, cudaStream_t st);
+
+// The same kernel over a batch: tab (device memory) holds `count` problems,
+// each with its tensor maps, leaves and stored-product buffer (mbuf set);
+// unit_start (device) numbers their (leaf, tile) units consecutively.
+// `layout` gives the status word, the wait limit and the operand layouts
+// (a_mn, b_mn), which all problems share, as they share leaf format and bn.
+cudaError_t launch_direct_gemm_batched(const DirectArgs& layout, const DirectArgs* tab, const int64_t* unit_start,
+                                       int count, int64_t total_units, int leaf_format, int bn, cudaStream_t st);
 
 // K extent of one pipeline stage of that kernel (the k extent of its
 // operand boxes): 32 for the hi+lo split, else 64.

@@ -109,6 +109,67 @@ constexpr int kZeroThreshold = kZeroExp / 2;
 constexpr int kRowWarps = 8;
 constexpr int kRowBatch = 8;
 
+// Row i, one warp (lane = its lane index).
+template <int DT, bool SHIFT>
+__device__ __forceinline__ void row_exp_one(const void* X, int64_t C, int64_t ld, const int* ce, int cs, int* out,
+                                            int mode, bool vec_ok, int64_t i, int lane, bool* nf) {
+  // the vector path also needs the column exponents 16-byte aligned
+  const bool vec = vec_ok && (!SHIFT || ((uintptr_t)ce % 16 == 0));
+  int m = kZeroExp;       // SHIFT: max shifted exponent
+  uint32_t mb = 0;        // !SHIFT: max |x| key
+  const int64_t rowoff = i * ld;
+  auto take = [&](uint32_t bits, int c) {
+    if constexpr (SHIFT) m = max(m, fexp_fast<DT>(bits, nf) + cs * c);
+    else mb = max(mb, abs_bits<DT>(bits));
+  };
+  int64_t jdone = 0;
+  if (vec) {
+    const int64_t C4 = C >> 2;
+    int64_t j4 = lane;
+    for (; j4 + 32 * (kRowBatch - 1) < C4; j4 += 32 * kRowBatch) {
+      uint4 v[kRowBatch];
+      int4 c[kRowBatch];
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) v[u] = raw4<DT>(X, rowoff + 4 * (j4 + 32 * u));
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u)
+        c[u] = SHIFT ? __ldg(reinterpret_cast<const int4*>(ce + 4 * (j4 + 32 * u))) : make_int4(0, 0, 0, 0);
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) {
+        uint32_t b[4];
+        unpack4<DT>(v[u], b);
+        take(b[0], c[u].x); take(b[1], c[u].y); take(b[2], c[u].z); take(b[3], c[u].w);
+      }
+    }
+    for (; j4 < C4; j4 += 32) {
+      const uint4 v = raw4<DT>(X, rowoff + 4 * j4);
+      const int4 c = SHIFT ? __ldg(reinterpret_cast<const int4*>(ce + 4 * j4)) : make_int4(0, 0, 0, 0);
+      uint32_t b[4];
+      unpack4<DT>(v, b);
+      take(b[0], c.x); take(b[1], c.y); take(b[2], c.z); take(b[3], c.w);
+    }
+    jdone = 4 * C4;
+  }
+  for (int64_t j = jdone + lane; j < C; j += 32) take(raw1<DT>(X, rowoff + j), SHIFT ? __ldg(ce + j) : 0);
+  if constexpr (!SHIFT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    m = fexp_of_abs_max<DT>(mb, nf);
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  if (lane == 0) {
+    const bool zero = m <= kZeroThreshold;
+    if (mode == kRowOStep) {
+      out[i] = zero ? 0 : m;
+    } else {
+      const int ex = out[i];
+      out[i] = (zero || ex <= kZeroThreshold) ? 0 : ((m - ex) >> 1);  // arithmetic shift = floor
+    }
+  }
+}
+
 template <int DT, bool SHIFT>
 __global__ void __launch_bounds__(kRowWarps * 32) row_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
                                                                  const int* ce, int cs, int* out, int mode,
@@ -117,63 +178,35 @@ __global__ void __launch_bounds__(kRowWarps * 32) row_exp_kernel(const void* X, 
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (int64_t)blockIdx.x * kRowWarps + (threadIdx.x >> 5);
   const int64_t nw = (int64_t)gridDim.x * kRowWarps;
-  // the vector path also needs the column exponents 16-byte aligned
-  const bool vec = vec_ok && (!SHIFT || ((uintptr_t)ce % 16 == 0));
-  for (int64_t i = w0; i < R; i += nw) {
-    int m = kZeroExp;       // SHIFT: max shifted exponent
-    uint32_t mb = 0;        // !SHIFT: max |x| key
-    const int64_t rowoff = i * ld;
-    auto take = [&](uint32_t bits, int c) {
-      if constexpr (SHIFT) m = max(m, fexp_fast<DT>(bits, &nf) + cs * c);
-      else mb = max(mb, abs_bits<DT>(bits));
-    };
-    int64_t jdone = 0;
-    if (vec) {
-      const int64_t C4 = C >> 2;
-      int64_t j4 = lane;
-      for (; j4 + 32 * (kRowBatch - 1) < C4; j4 += 32 * kRowBatch) {
-        uint4 v[kRowBatch];
-        int4 c[kRowBatch];
-#pragma unroll
-        for (int u = 0; u < kRowBatch; ++u) v[u] = raw4<DT>(X, rowoff + 4 * (j4 + 32 * u));
-#pragma unroll
-        for (int u = 0; u < kRowBatch; ++u)
-          c[u] = SHIFT ? __ldg(reinterpret_cast<const int4*>(ce + 4 * (j4 + 32 * u))) : make_int4(0, 0, 0, 0);
-#pragma unroll
-        for (int u = 0; u < kRowBatch; ++u) {
-          uint32_t b[4];
-          unpack4<DT>(v[u], b);
-          take(b[0], c[u].x); take(b[1], c[u].y); take(b[2], c[u].z); take(b[3], c[u].w);
-        }
-      }
-      for (; j4 < C4; j4 += 32) {
-        const uint4 v = raw4<DT>(X, rowoff + 4 * j4);
-        const int4 c = SHIFT ? __ldg(reinterpret_cast<const int4*>(ce + 4 * j4)) : make_int4(0, 0, 0, 0);
-        uint32_t b[4];
-        unpack4<DT>(v, b);
-        take(b[0], c.x); take(b[1], c.y); take(b[2], c.z); take(b[3], c.w);
-      }
-      jdone = 4 * C4;
-    }
-    for (int64_t j = jdone + lane; j < C; j += 32) take(raw1<DT>(X, rowoff + j), SHIFT ? __ldg(ce + j) : 0);
-    if constexpr (!SHIFT) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-      m = fexp_of_abs_max<DT>(mb, &nf);
-    } else {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    }
-    if (lane == 0) {
-      const bool zero = m <= kZeroThreshold;
-      if (mode == kRowOStep) {
-        out[i] = zero ? 0 : m;
-      } else {
-        const int ex = out[i];
-        out[i] = (zero || ex <= kZeroThreshold) ? 0 : ((m - ex) >> 1);  // arithmetic shift = floor
-      }
-    }
+  for (int64_t i = w0; i < R; i += nw) row_exp_one<DT, SHIFT>(X, C, ld, ce, cs, out, mode, vec_ok != 0, i, lane, &nf);
+  if (nf) atomicOr(status, kStatusNonfinite);
+}
+
+// Index of the problem whose [start[p], start[p + 1]) range holds idx
+// (start ascending, start[0] = 0, count problems).
+__device__ __forceinline__ int batch_find(const int64_t* start, int count, int64_t idx) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= idx) lo = mid;
+    else hi = mid - 1;
   }
+  return lo;
+}
+
+// Batched row reduction: warp w of the launch takes global row w; rows of
+// problem p are [start[p], start[p + 1]).
+template <int DT, bool SHIFT>
+__global__ void __launch_bounds__(kRowWarps * 32) row_exp_batched_kernel(const ReduceArgs* args,
+                                                                         const int64_t* start, int count, int mode,
+                                                                         int* status) {
+  bool nf = false;
+  const int64_t g = (int64_t)blockIdx.x * kRowWarps + (threadIdx.x >> 5);
+  if (g >= __ldg(start + count)) return;
+  const int p = batch_find(start, count, g);
+  const ReduceArgs a = args[p];
+  row_exp_one<DT, SHIFT>(a.X, a.C, a.ld, a.shift, a.sign, a.out, mode, a.vec != 0, g - __ldg(start + p),
+                         threadIdx.x & 31, &nf);
   if (nf) atomicOr(status, kStatusNonfinite);
 }
 
@@ -195,16 +228,15 @@ constexpr int kColGroups = 4;
 constexpr int kColThreads = 256 * kColGroups;
 constexpr int kColSmem = kColGroups * kColSpan * 4;
 
+// One CTA of the column reduction: column span bx, row chunk by.
 template <int DT, bool SHIFT>
-__global__ void __launch_bounds__(kColThreads) col_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
-                                                              const int* re, int rs, int* out, int rows_per_cta,
-                                                              int vec_ok, int* status) {
-  extern __shared__ int red[];  // [kColGroups][kColSpan]
-  bool nf = false;
+__device__ __forceinline__ void col_exp_cta(const void* X, int64_t R, int64_t C, int64_t ld, const int* re, int rs,
+                                            int* out, int rows_per_cta, bool vec, int64_t bx, int64_t by, int* red,
+                                            bool* nf) {
   const int group = threadIdx.x >> 8, lt = threadIdx.x & 255;
-  const int64_t span0 = (int64_t)blockIdx.x * kColSpan;
+  const int64_t span0 = bx * kColSpan;
   const int rows_g = rows_per_cta / kColGroups;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta + (int64_t)group * rows_g;
+  const int64_t r0 = by * rows_per_cta + (int64_t)group * rows_g;
   const int64_t r1 = min(R, r0 + rows_g);
   int m[kColVec][4];
   uint32_t mb[kColVec][4];
@@ -216,12 +248,11 @@ __global__ void __launch_bounds__(kColThreads) col_exp_kernel(const void* X, int
       mb[q][t] = 0u;
     }
   auto take = [&](int q, int t, uint32_t bits, int sh) {
-    if constexpr (SHIFT) m[q][t] = max(m[q][t], fexp_fast<DT>(bits, &nf) + sh);
+    if constexpr (SHIFT) m[q][t] = max(m[q][t], fexp_fast<DT>(bits, nf) + sh);
     else mb[q][t] = max(mb[q][t], abs_bits<DT>(bits));
   };
   // column of (q, t): span0 + 1024 q + 4 lt + t
   const int64_t cbase = span0 + 4 * (int64_t)lt;
-  const bool vec = vec_ok != 0;
   int64_t i = r0;
   for (; i + kColRows <= r1; i += kColRows) {
     uint4 v[kColRows][kColVec];
@@ -256,7 +287,7 @@ __global__ void __launch_bounds__(kColThreads) col_exp_kernel(const void* X, int
   for (int q = 0; q < kColVec; ++q)
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      red[group * kColSpan + 1024 * q + 4 * lt + t] = SHIFT ? m[q][t] : fexp_of_abs_max<DT>(mb[q][t], &nf);
+      red[group * kColSpan + 1024 * q + 4 * lt + t] = SHIFT ? m[q][t] : fexp_of_abs_max<DT>(mb[q][t], nf);
   __syncthreads();
   for (int c = threadIdx.x; c < kColSpan; c += kColThreads) {
     int e = red[c];
@@ -264,6 +295,31 @@ __global__ void __launch_bounds__(kColThreads) col_exp_kernel(const void* X, int
     for (int g = 1; g < kColGroups; ++g) e = max(e, red[g * kColSpan + c]);
     if (span0 + c < C && e > kZeroThreshold) atomicMax(out + span0 + c, e);
   }
+}
+
+template <int DT, bool SHIFT>
+__global__ void __launch_bounds__(kColThreads) col_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
+                                                              const int* re, int rs, int* out, int rows_per_cta,
+                                                              int vec_ok, int* status) {
+  extern __shared__ int red[];  // [kColGroups][kColSpan]
+  bool nf = false;
+  col_exp_cta<DT, SHIFT>(X, R, C, ld, re, rs, out, rows_per_cta, vec_ok != 0, blockIdx.x, blockIdx.y, red, &nf);
+  if (nf) atomicOr(status, kStatusNonfinite);
+}
+
+// Batched column reduction: CTA b of the launch belongs to the problem whose
+// [start[p], start[p + 1]) holds b; within it, CTAs run over
+// (column span, row chunk) with args[p].gx spans.
+template <int DT, bool SHIFT>
+__global__ void __launch_bounds__(kColThreads) col_exp_batched_kernel(const ReduceArgs* args, const int64_t* start,
+                                                                      int count, int* status) {
+  extern __shared__ int red[];
+  bool nf = false;
+  const int p = batch_find(start, count, blockIdx.x);
+  const ReduceArgs a = args[p];
+  const int64_t local = blockIdx.x - __ldg(start + p);
+  col_exp_cta<DT, SHIFT>(a.X, a.R, a.C, a.ld, a.shift, a.sign, a.out, a.rows_per_cta, a.vec != 0, local % a.gx,
+                         local / a.gx, red, &nf);
   if (nf) atomicOr(status, kStatusNonfinite);
 }
 
@@ -399,6 +455,53 @@ cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
     default: { FMM_COL(kF16, 2) break; }
 #undef FMM_COL
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_exp_batched(const ReduceArgs* args, const int64_t* start, int count, int64_t total, int dt,
+                                   bool shift, int mode, int* status, cudaStream_t st) {
+  if (total == 0 || count == 0) return cudaSuccess;
+  const unsigned g = (unsigned)((total + kRowWarps - 1) / kRowWarps);
+  const int nt = kRowWarps * 32;
+  KernelTimer timer("scale", st);
+#define FMM_ROWB(DT)                                                                                   \
+  (shift ? row_exp_batched_kernel<DT, true><<<g, nt, 0, st>>>(args, start, count, mode, status)        \
+         : row_exp_batched_kernel<DT, false><<<g, nt, 0, st>>>(args, start, count, mode, status))
+  switch (dt) {
+    case kF32: FMM_ROWB(kF32); break;
+    case kBF16: FMM_ROWB(kBF16); break;
+    default: FMM_ROWB(kF16); break;
+  }
+#undef FMM_ROWB
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_exp_batched(const ReduceArgs* args, const int64_t* start, int count, int64_t total, int dt,
+                                   bool shift, int* status, cudaStream_t st) {
+  static_assert(kBatchColRows % (kColRows * kColGroups) == 0, "row chunk must be whole batches");
+  static_assert(kBatchColSpan == kColSpan, "column span");
+  if (total == 0 || count == 0) return cudaSuccess;
+  static bool attr_done[64][6] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  KernelTimer timer("scale", st);
+  const unsigned g = (unsigned)total;
+#define FMM_COLB(DT, I)                                                                                          \
+  if (!attr_done[dev][I]) {                                                                                      \
+    cudaFuncSetAttribute(col_exp_batched_kernel<DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kColSmem); \
+    cudaFuncSetAttribute(col_exp_batched_kernel<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                         kColSmem);                                                                              \
+    attr_done[dev][I] = true;                                                                                    \
+  }                                                                                                              \
+  if (shift) col_exp_batched_kernel<DT, true><<<g, kColThreads, kColSmem, st>>>(args, start, count, status);   \
+  else col_exp_batched_kernel<DT, false><<<g, kColThreads, kColSmem, st>>>(args, start, count, status);
+  switch (dt) {
+    case kF32: { FMM_COLB(kF32, 0) break; }
+    case kBF16: { FMM_COLB(kBF16, 1) break; }
+    default: { FMM_COLB(kF16, 2) break; }
+  }
+#undef FMM_COLB
   return cudaGetLastError();
 }
 

@@ -1,0 +1,112 @@
+"""Batched products (fmm_batch_create / fmm_batch_run): mixed shapes and
+plans in one launch sequence, each product checked against the oracle within
+the parity tolerance; CUDA-graph capture and replay on new inputs; the batch
+against the single-product path."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import assert_within, dev_values, oracle_reference, require_gpu, to_dev
+from oracle import scaling as OS
+from paper_1507_00687_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+MIX = [(["strassen"], 384, 256, 512), ([], 128, 640, 256), (["winograd"], 1000, 520, 776),
+       (["winograd", "winograd"], 512, 384, 640), (["strassen", "classical121"], 300, 200, 250),
+       (["fast323"], 450, 320, 390), (["winograd"], 129, 65, 257), (["strassen", "strassen"], 1024, 512, 768)]
+
+
+@pytest.fixture(scope="module")
+def api():
+    return require_gpu()
+
+
+def _problems(api, leaf, dt, seed):
+    probs, host = [], []
+    for i, (names, M, K, N) in enumerate(MIX):
+        A, B = inputs.diag_scaled_pair(M, K, N, seed=seed + i)
+        Ad, Bd = to_dev(A, dt), to_dev(B, dt)
+        C = torch.full((M, N), float("nan"), device="cuda")
+        probs.append((api.Plan(names, leaf), Ad, Bd, C))
+        host.append(names)
+    return probs, host
+
+
+@pytest.mark.parametrize("steps", ["", "OI", "O", "I"])
+def test_batch_matches_oracle(api, steps):
+    probs, names = _problems(api, "bf16x3", "f32", 300)
+    batch = api.Batch(probs, steps)
+    batch.run()
+    api.sync_status()
+    for (plan, Ad, Bd, C), nm in zip(probs, names):
+        A64, B64 = dev_values(Ad), dev_values(Bd)
+        if steps:
+            st = OS.pow2_repeated(A64, B64, steps)
+            Cref, G = oracle_reference(A64, B64, nm, st.eA, st.d, st.eB)
+        else:
+            Cref, G = oracle_reference(A64, B64, nm)
+        assert_within(dev_values(C), Cref, G, nm, Ad.shape[1], "bf16x3", f"batch {nm} {steps}")
+
+
+def test_batch_bf16_leaves_and_integers_exact(api):
+    # Integer entries in [-4, 4]: every leaf product is exact, so each batched
+    # product equals the classical product bit for bit.
+    probs = []
+    for i, (names, M, K, N) in enumerate(MIX):
+        A = inputs.integers((M, K), -4, 4, seed=40 + i)
+        B = inputs.integers((K, N), -4, 4, seed=80 + i)
+        probs.append((api.Plan(names, "bf16"), to_dev(A, "bf16"), to_dev(B, "bf16"),
+                      torch.empty((M, N), device="cuda"), A @ B))
+    batch = api.Batch([p[:4] for p in probs], "")
+    batch.run()
+    api.sync_status()
+    for plan, Ad, Bd, C, want in probs:
+        assert np.array_equal(dev_values(C), want)
+
+
+def test_batch_cuda_graph_replay_on_new_inputs(api):
+    probs, names = _problems(api, "bf16x3", "f32", 500)
+    batch = api.Batch(probs, "OI")
+    batch.run()  # first run outside the capture (library set-up happens here)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.run()
+    # new inputs into the same buffers, then replay
+    for i, (plan, Ad, Bd, C) in enumerate(probs):
+        A, B = inputs.diag_scaled_pair(Ad.shape[0], Ad.shape[1], Bd.shape[1], seed=900 + i)
+        Ad.copy_(torch.from_numpy(A).float())
+        Bd.copy_(torch.from_numpy(B).float())
+        C.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    api.sync_status()
+    for (plan, Ad, Bd, C), nm in zip(probs, names):
+        A64, B64 = dev_values(Ad), dev_values(Bd)
+        st = OS.pow2_repeated(A64, B64, "OI")
+        Cref, G = oracle_reference(A64, B64, nm, st.eA, st.d, st.eB)
+        assert_within(dev_values(C), Cref, G, nm, Ad.shape[1], "bf16x3", f"graph replay {nm}")
+
+
+def test_batch_agrees_with_single_products(api):
+    probs, names = _problems(api, "bf16x3", "f32", 700)
+    batch = api.Batch(probs, "OI")
+    batch.run()
+    api.sync_status()
+    for (plan, Ad, Bd, C), nm in zip(probs, names):
+        eA, d, eB = api.scale(Ad, Bd, "OI")
+        single = api.multiply(plan, Ad, Bd, eA, d, eB)
+        _, G = oracle_reference(dev_values(Ad), dev_values(Bd), nm)
+        A64, B64 = dev_values(Ad), dev_values(Bd)
+        st = OS.pow2_repeated(A64, B64, "OI")
+        _, G = oracle_reference(A64, B64, nm, st.eA, st.d, st.eB)
+        assert_within(dev_values(C), dev_values(single), G, nm, Ad.shape[1], "bf16x3", f"batch vs single {nm}")
+
+
+def test_batch_rejects_mixed_leaf_formats(api):
+    from paper_1507_00687_gb300 import _native as N
+    A = torch.ones((64, 64), device="cuda")
+    with pytest.raises(N.FmmError):
+        api.Batch([(api.Plan(["strassen"], "bf16"), A, A, torch.empty_like(A)),
+                   (api.Plan(["strassen"], "bf16x3"), A, A, torch.empty_like(A))], "")
