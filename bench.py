@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--scaling", default="OI")
     ap.add_argument("--schedule", default="auto", choices=["auto", "pass", "load_stage"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator / variant timings")
+    ap.add_argument("--batch", type=int, default=512, help="products in the batched workload extra (0: skip)")
     return ap.parse_args()
 
 
@@ -61,6 +62,64 @@ def workload_config(args):
             "leaf": args.leaf, "scaling_steps": args.scaling, "schedule": args.schedule,
             "inputs": "A=D1 X D2, B=D3 Y D4, X,Y~U[0,1), D=2^U(-12,12), seeded",
             "l2": "flushed before each timed step (256 MiB memset, untimed)"}
+
+
+# ---------------------------------------------------------------- batched workload
+
+def batched_workload(api, inputs, torch, count: int) -> dict:
+    """``count`` independent products, each dimension log-uniform over the
+    multiples of 128 in [512, 4096]; BF16 inputs U[-1, 1] (seeded, made on
+    the device), BF16 leaves with FP32 accumulation, outside-inside scaling;
+    plans chosen per product by the autotuner; the whole batch one launch
+    sequence (one persistent tensor-core launch) replayed from a CUDA graph.
+    Inputs total several GB, far beyond L2, so no flush is needed."""
+    dims = inputs.log_uniform_dims(count, 512, 4096, 128, seed=1507 + 4000)
+    t0 = time.time()
+    tuner = api.Autotuner(leaf="bf16", dtype=torch.bfloat16)
+    tune_s = time.time() - t0
+    gen = torch.Generator(device="cuda").manual_seed(1507 + 4001)
+    probs, choice = [], {}
+    for M, K, N in dims.tolist():
+        A = (torch.rand((M, K), generator=gen, device="cuda") * 2 - 1).to(torch.bfloat16)
+        B = (torch.rand((K, N), generator=gen, device="cuda") * 2 - 1).to(torch.bfloat16)
+        plan = tuner.plan(M, K, N)
+        key = "-".join(tuner.choose(M, K, N)) or "classical"
+        choice[key] = choice.get(key, 0) + 1
+        probs.append((plan, A, B, torch.empty((M, N), device="cuda")))
+    batch = api.Batch(probs, "OI")
+    for _ in range(3):
+        batch.run()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.run()
+    g.replay()
+    torch.cuda.synchronize()
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    api.sync_status()
+    ms = e0.elapsed_time(e1) / reps
+    flops = float(sum(2 * M * K * N for M, K, N in dims.tolist()))
+    # error of a sample of products against an FP64 product of the same inputs
+    errs = []
+    for i in range(0, count, max(1, count // 16)):
+        _, A, B, C = probs[i]
+        ref = A.double() @ B.double()
+        errs.append(float((C.double() - ref).abs().max() / (A.double().abs().max() * B.double().abs().max() *
+                                                             A.shape[1])))
+    ws_gb = batch.ws.numel() / 1e9
+    del batch, probs, g
+    torch.cuda.empty_cache()
+    return {"products": count, "tflops": flops / (ms * 1e-3) / 1e12, "ms_per_batch": ms, "total_gflop": flops / 1e9,
+            "plans": choice, "launch": "one CUDA graph replay: 6 scaling + 1 combination + 1 multiply + 1 output launch",
+            "workspace_gb": ws_gb, "autotune_s": tune_s,
+            "max_err_over_K_normA_normB_sampled": max(errs), "leaf": "bf16", "inputs": "bf16 U[-1,1]",
+            "scaling": "OI"}
 
 
 # ---------------------------------------------------------------- clocks
@@ -347,6 +406,8 @@ def main():
                 extras["fast_L2"] = {"unavailable": str(e)}
         del plan0
     del ref, C_fast
+    if not args.no_extras and args.batch > 0:
+        extras["batched"] = batched_workload(api, inputs, torch, args.batch)
 
     # ---------------- roofline of the dominant kernel (the tensor-core multiply)
     import json as _json

@@ -234,6 +234,70 @@ class Batch:
             self._h = None
 
 
+# Candidate plans the autotuner chooses from: rules per level (depth = the
+# list's length; the recursion cutoff is the smallest leaf block allowed).
+AUTOTUNE_CANDIDATES = ((), ("strassen",), ("winograd",), ("winograd", "winograd"), ("strassen", "strassen"))
+
+
+class Autotuner:
+    """Chooses, per product shape, the rule sequence (algorithm and
+    recursion depth) with the shortest measured time.  It times every
+    candidate on a ladder of square sizes on the current GPU (once; results
+    kept in ``self.table``), then, for a shape (M, K, N), predicts each
+    candidate's time from the ladder point nearest to the shape's geometric
+    mean size scaled by the candidate's flop count, and skips candidates
+    whose leaf blocks would be smaller than ``cutoff``."""
+
+    def __init__(self, leaf: str = "bf16", dtype=torch.bfloat16, sizes=(512, 1024, 2048, 4096),
+                 candidates=AUTOTUNE_CANDIDATES, cutoff: int = 256, reps: int = 5, scaling: str = "OI"):
+        self.leaf, self.dtype, self.sizes, self.cutoff = leaf, dtype, tuple(sizes), cutoff
+        self.candidates = tuple(tuple(c) for c in candidates)
+        self.table = {}
+        self._plans = {c: Plan(list(c), leaf) for c in self.candidates}
+        gen = torch.Generator(device="cuda").manual_seed(1507)
+        for n in self.sizes:
+            A = (torch.rand((n, n), generator=gen, device="cuda") * 2 - 1).to(dtype)
+            B = (torch.rand((n, n), generator=gen, device="cuda") * 2 - 1).to(dtype)
+            out = torch.empty((n, n), device="cuda")
+            for c in self.candidates:
+                if not self._fits(c, n, n, n):
+                    continue
+                plan = self._plans[c]
+                eA, d, eB = scale(A, B, scaling) if scaling else (None, None, None)
+                multiply(plan, A, B, eA, d, eB, out=out)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    multiply(plan, A, B, eA, d, eB, out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                self.table[(c, n)] = e0.elapsed_time(e1) / reps
+            del A, B, out
+        sync_status()
+
+    def _fits(self, c, M, K, N) -> bool:
+        p = self._plans[c].info()
+        return min(M // p["pm"], K // p["pk"], N // p["pn"]) >= self.cutoff or not c
+
+    def predict(self, c, M, K, N) -> float:
+        """Predicted ms of candidate c on (M, K, N): the nearest ladder time
+        scaled by the ratio of the products' classical flop counts."""
+        g = (M * K * N) ** (1.0 / 3.0)
+        pts = [n for n in self.sizes if (c, n) in self.table]
+        if not pts:
+            return float("inf")
+        n = min(pts, key=lambda s: abs(np.log(s / g)))
+        return self.table[(c, n)] * (M * K * N) / float(n ** 3)
+
+    def choose(self, M, K, N):
+        best = min((c for c in self.candidates if self._fits(c, M, K, N)), key=lambda c: self.predict(c, M, K, N))
+        return list(best)
+
+    def plan(self, M, K, N) -> "Plan":
+        return self._plans[tuple(self.choose(M, K, N))]
+
+
 def kernel_timing(enable: bool) -> None:
     """Start (discarding earlier records) or stop per-kernel event timing."""
     N.check(N.lib().fmm_kernel_timing(1 if enable else 0), "fmm_kernel_timing")

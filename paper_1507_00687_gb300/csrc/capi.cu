@@ -622,6 +622,7 @@ struct Batch {
   BatchLayout L;
   int64_t red_total[4] = {0, 0, 0, 0};
   int64_t comb_total = 0, unit_total = 0, out_total = 0;
+  int out_count = 0;
   int comb_tr = 32, out_tr = 32;
   size_t comb_smem = 0, out_smem = 0;
   DirectArgs layout;  // status, wait limit, operand layouts
@@ -645,14 +646,21 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
   std::vector<int64_t> comb_start(2 * (size_t)count + 1, 0);
   std::vector<DirectArgs> dir((size_t)count);
   std::vector<int64_t> unit_start((size_t)count + 1, 0);
-  std::vector<OutArgs> out((size_t)count);
-  std::vector<int64_t> out_start((size_t)count + 1, 0);
-  int64_t max_nb = 1, max_cb = 1;
+  std::vector<OutArgs> out;
+  std::vector<int64_t> out_start(1, 0);
+  std::vector<int64_t> unit_cost((size_t)count), units((size_t)count);
+  int64_t max_nb = 1, max_cb = 1, tiles_all = 0;
   for (int i = 0; i < count; ++i) {
     const Plan* p = reinterpret_cast<const Plan*>(probs[i].plan);
     max_nb = std::max(max_nb, std::max(p->pm * p->pk, p->pk * p->pn));
     max_cb = std::max(max_cb, p->pm * p->pn);
+    const PassGeom& g = L.geom[(size_t)i];
+    tiles_all += (g.tp_a / 128) * (g.tp_b / kBatchTileN);
   }
+  // Output combination in the multiply epilogue (each tile of each product
+  // a unit covering all its leaves) when the batch has tiles enough to
+  // occupy the GPU; else stored leaf products for the many-leaf plans.
+  const bool fused = tiles_all >= 2 * (int64_t)device_sm_count();
   b->comb_tr = combine_batched_rows(max_nb);
   b->out_tr = out_batched_rows(max_cb);
   int64_t om = 0, ok_ = 0, on = 0;
@@ -685,7 +693,7 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
     const PassGeom& g = L.geom[u];
     char* wa = ws + L.off_a[u];
     char* wb = ws + L.off_b[u];
-    float* mbuf = reinterpret_cast<float*>(ws + L.off_m[u]);
+    float* mbuf = (fused || g.R == 1) ? nullptr : reinterpret_cast<float*>(ws + L.off_m[u]);
     comb[2 * u] = combine_args(p, g, x, 0, leaves, wa);
     comb[2 * u + 1] = combine_args(p, g, y, 1, leaves, wb);
     for (int sd = 0; sd < 2; ++sd) {
@@ -704,12 +712,32 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
     c.eB = o_step ? eB : nullptr;
     c.vec_ok = ((uintptr_t)q.C % 16 == 0) && (q.ldc % 4 == 0) && (c.bn % 4 == 0) ? 1 : 0;
     if (!direct_args(p, g, x, y, c, leaves, wa, wb, mbuf, b->status, &dir[u])) return FMM_ERR_CUDA;
-    unit_start[u + 1] = unit_start[u] + g.R * (g.tp_a / 128) * (g.tp_b / kBatchTileN);
-    out[u] = out_args(p, g, c, leaves, mbuf);
-    out_start[u + 1] = out_start[u] + ceil_div(c.bm, b->out_tr) * ceil_div(c.bn, 64);
-    b->out_smem = std::max(b->out_smem, (size_t)(p->pm * p->pn * b->out_tr * 256 + out[u].c_nnz * 8 +
-                                                 (out[u].num_leaves + 1) * 4));
+    const int64_t tiles = (g.tp_a / 128) * (g.tp_b / kBatchTileN);
+    units[u] = mbuf ? g.R * tiles : tiles;
+    unit_cost[u] = (mbuf ? 1 : g.R) * (g.kp / 64);
+    if (mbuf) {
+      out.push_back(out_args(p, g, c, leaves, mbuf));
+      const OutArgs& o = out.back();
+      out_start.push_back(out_start.back() + ceil_div(c.bm, b->out_tr) * ceil_div(c.bn, 64));
+      b->out_smem = std::max(b->out_smem, (size_t)(p->pm * p->pn * b->out_tr * 256 + o.c_nnz * 8 +
+                                                   (o.num_leaves + 1) * 4));
+    }
   }
+  // Multiply table ordered by decreasing work per unit, so the round-robin
+  // assignment of units to CTAs hands out the long units first.
+  std::vector<int> order((size_t)count);
+  for (int i = 0; i < count; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return unit_cost[(size_t)x] > unit_cost[(size_t)y]; });
+  {
+    std::vector<DirectArgs> sorted((size_t)count);
+    for (int i = 0; i < count; ++i) {
+      sorted[(size_t)i] = dir[(size_t)order[(size_t)i]];
+      unit_start[(size_t)i + 1] = unit_start[(size_t)i] + units[(size_t)order[(size_t)i]];
+    }
+    dir.swap(sorted);
+  }
+  b->out_count = (int)out.size();
   if (b->comb_smem > 200 * 1024 || b->out_smem > 200 * 1024) {
     t_last_error = "batch: a plan's term lists do not fit the passes' shared memory";
     return FMM_ERR_UNSUPPORTED;
@@ -717,7 +745,7 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
   for (int k = 0; k < 4; ++k) b->red_total[k] = red_start[k][(size_t)count];
   b->comb_total = comb_start[2 * (size_t)count];
   b->unit_total = unit_start[(size_t)count];
-  b->out_total = out_start[(size_t)count];
+  b->out_total = out_start.back();
   b->layout = dir[0];
   // copy the tables into the workspace
   auto put = [&](size_t off, const void* src, size_t bytes) {
@@ -731,7 +759,7 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
       !put(L.off_comb_start, comb_start.data(), comb_start.size() * 8) ||
       !put(L.off_direct, dir.data(), dir.size() * sizeof(DirectArgs)) ||
       !put(L.off_unit_start, unit_start.data(), unit_start.size() * 8) ||
-      !put(L.off_out, out.data(), out.size() * sizeof(OutArgs)) ||
+      (!out.empty() && !put(L.off_out, out.data(), out.size() * sizeof(OutArgs))) ||
       !put(L.off_out_start, out_start.data(), out_start.size() * 8))
     return FMM_ERR_CUDA;
   return FMM_OK;
@@ -785,8 +813,8 @@ static fmm_status batch_run(const Batch* b, cudaStream_t st) {
                                           b->fmt, kBatchTileN, st),
                "batch multiply") ||
       !cuda_ok(launch_out_combine_batched(reinterpret_cast<const OutArgs*>(ws + L.off_out),
-                                          reinterpret_cast<const int64_t*>(ws + L.off_out_start), n, b->out_total,
-                                          b->out_tr, b->out_smem, st),
+                                          reinterpret_cast<const int64_t*>(ws + L.off_out_start), b->out_count,
+                                          b->out_total, b->out_tr, b->out_smem, st),
                "batch output pass"))
     return FMM_ERR_CUDA;
   return FMM_OK;

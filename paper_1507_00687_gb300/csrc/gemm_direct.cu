@@ -147,46 +147,53 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
+  // Work units of this CTA: global units u = blockIdx.x, + gridDim.x, ...;
+  // a unit is one tile of one leaf product (problems with stored products)
+  // or one tile with all its leaves in leaf order (fused epilogue).
   const bool batched = launch.tab != nullptr;
-  const bool store_m = batched || args.mbuf != nullptr;
-  int64_t my_units;
-  if (batched) {
-    my_units = (launch.total_units - blockIdx.x + gridDim.x - 1) / gridDim.x;
-  } else {
-    const int64_t ntiles = (args.tp_a / BM) * (args.tp_b / BN);
-    const int64_t nunits = store_m ? args.num_leaves * ntiles : ntiles;  // a tile's leaves: one unit when fused
-    my_units = ((nunits - blockIdx.x + gridDim.x - 1) / gridDim.x) * (store_m ? 1 : args.num_leaves);
-  }
-  // The j-th unit of this CTA: its problem, leaf, tile position and k steps.
-  struct Unit {
+  const int64_t total_units = batched ? launch.total_units
+                                      : (args.tp_a / BM) * (args.tp_b / BN) * (args.mbuf ? args.num_leaves : 1);
+  struct Cursor {
+    int64_t u, leaf, leaf_end, tm, tn, kt;
     const DirectArgs* a;
-    int64_t leaf, tm, tn, kt;
   };
-  auto unit = [&](int64_t j) {
-    Unit w;
+  auto decode = [&](Cursor& c) {
+    if (c.u >= total_units) return;
     int64_t local;
     if (batched) {
-      const int64_t u = blockIdx.x + j * gridDim.x;
-      const int p = find_unit_problem(launch.unit_start, launch.count, u);
-      w.a = launch.tab + p;
-      local = u - __ldg(launch.unit_start + p);
+      const int p = find_unit_problem(launch.unit_start, launch.count, c.u);
+      c.a = launch.tab + p;
+      local = c.u - __ldg(launch.unit_start + p);
     } else {
-      w.a = &args;
-      local = blockIdx.x + j * gridDim.x;
+      c.a = &args;
+      local = c.u;
     }
-    const int64_t ntn = w.a->tp_b / BN, ntiles = (w.a->tp_a / BM) * ntn;
+    const int64_t ntn = c.a->tp_b / BN, ntiles = (c.a->tp_a / BM) * ntn;
     int64_t tile;
-    if (store_m) {
-      w.leaf = local / ntiles;
+    if (c.a->mbuf) {
+      c.leaf = local / ntiles;
+      c.leaf_end = c.leaf + 1;
       tile = local % ntiles;
     } else {
-      tile = blockIdx.x + (j / w.a->num_leaves) * gridDim.x;
-      w.leaf = j % w.a->num_leaves;
+      c.leaf = 0;
+      c.leaf_end = c.a->num_leaves;
+      tile = local;
     }
-    w.tm = tile / ntn;
-    w.tn = tile % ntn;
-    w.kt = w.a->kp / BK;
-    return w;
+    c.tm = tile / ntn;
+    c.tn = tile % ntn;
+    c.kt = c.a->kp / BK;
+  };
+  auto first = [&]() {
+    Cursor c;
+    c.u = blockIdx.x;
+    decode(c);
+    return c;
+  };
+  auto advance = [&](Cursor& c) {
+    if (++c.leaf >= c.leaf_end) {
+      c.u += gridDim.x;
+      decode(c);
+    }
   };
 
   if (warp == kTmaWarp) {
@@ -196,8 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
       uint32_t phase = 0;
       bool ok = true;
       uint32_t armed = 0, armed_parity = 0;  // per stage: copy issued, parity it completes
-      for (int64_t j = 0; j < my_units && ok; ++j) {
-        const Unit w = unit(j);
+      for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
         const DirectArgs& a = *w.a;
         const int64_t NL = a.num_leaves;
         for (int64_t kt = 0; kt < w.kt && ok; ++kt) {
@@ -237,9 +243,9 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
       uint32_t phase = 0, acc_iter = 0;
       bool ok = true;
       const uint32_t sbase = smem_u32(smem);
-      for (int64_t j = 0; j < my_units && ok; ++j) {
+      for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
         {
-          const int64_t KT = unit(j).kt;
+          const int64_t KT = w.kt;
           const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
           if (!mbar_wait_bounded(&tempty[buf], aph ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
           tc_fence_after();
@@ -283,9 +289,9 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
     uint32_t acc_iter = 0;
     bool ok = true;
     const int row = warp * 32 + lane;  // TMEM lane = tile row
-    for (int64_t j = 0; j < my_units && ok; ++j) {
-      const Unit w = unit(j);
+    for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
       const DirectArgs& a = *w.a;
+      const bool store_m = a.mbuf != nullptr;
       const int64_t leaf = w.leaf, tn = w.tn;
       const int64_t ml = w.tm * BM + row;
       const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;

@@ -110,3 +110,42 @@ def test_batch_rejects_mixed_leaf_formats(api):
     with pytest.raises(N.FmmError):
         api.Batch([(api.Plan(["strassen"], "bf16"), A, A, torch.empty_like(A)),
                    (api.Plan(["strassen"], "bf16x3"), A, A, torch.empty_like(A))], "")
+
+
+def test_autotuner_choices_run_and_respect_cutoff(api):
+    tuner = api.Autotuner(leaf="bf16", sizes=(512, 1024), reps=2)
+    assert tuner.table, "no candidate timed"
+    for shape in ((512, 512, 512), (1024, 768, 1536), (384, 4096, 384)):
+        names = tuner.choose(*shape)
+        plan = tuner.plan(*shape)
+        info = plan.info()
+        if names:
+            assert min(shape[0] // info["pm"], shape[1] // info["pk"], shape[2] // info["pn"]) >= tuner.cutoff
+        A = (torch.rand(shape[:2], device="cuda") * 2 - 1).to(torch.bfloat16)
+        B = (torch.rand(shape[1:], device="cuda") * 2 - 1).to(torch.bfloat16)
+        got = dev_values(api.multiply(plan, A, B))
+        C, G = oracle_reference(dev_values(A), dev_values(B), names)
+        assert_within(got, C, G, names, shape[1], "bf16", f"autotuned {names}")
+
+
+def test_batch_many_products_fused_epilogue(api):
+    # Enough tiles to fill the GPU: the batch forms C in the multiply
+    # epilogue (every tile of every product one unit, all leaves in order).
+    # Eight copies of each product: identical results, within tolerance.
+    base, names = _problems(api, "bf16x3", "f32", 1100)
+    probs = []
+    for copy in range(8):
+        for plan, Ad, Bd, C in base:
+            probs.append((plan, Ad, Bd, torch.full_like(C, float("nan"))))
+    batch = api.Batch(probs, "OI")
+    batch.run()
+    api.sync_status()
+    n = len(base)
+    for i, ((plan, Ad, Bd, _), nm) in enumerate(zip(base, names)):
+        A64, B64 = dev_values(Ad), dev_values(Bd)
+        st = OS.pow2_repeated(A64, B64, "OI")
+        Cref, G = oracle_reference(A64, B64, nm, st.eA, st.d, st.eB)
+        first = dev_values(probs[i][3])
+        assert_within(first, Cref, G, nm, Ad.shape[1], "bf16x3", f"fused batch {nm}")
+        for copy in range(1, 8):
+            assert np.array_equal(dev_values(probs[copy * n + i][3]), first)
