@@ -117,7 +117,10 @@ def _pad(X: np.ndarray, rows: int, cols: int) -> np.ndarray:
     return out
 
 
-def _recurse(A, B, node, leaf, dtype):
+def _recurse(A, B, node, leaf, dtype, dvecs=None):
+    """One node of Eq. 3.2.  ``dvecs`` (root node only): per product r an
+    integer vector d, applied as S_r <- S_r 2^d (columns), T_r <- 2^-d T_r
+    (rows) before recursing -- the between-steps scaling."""
     if node is None:
         return leaf(A, B)
     r = canonical(node.rule)
@@ -134,6 +137,9 @@ def _recurse(A, B, node, leaf, dtype):
             S = np.zeros((mb, kb), dtype)
         if T is None:
             T = np.zeros((kb, nb), dtype)
+        if dvecs is not None:
+            S = (S * np.exp2(dvecs[j].astype(np.float64))[None, :]).astype(dtype)
+            T = (T * np.exp2(-dvecs[j].astype(np.float64))[:, None]).astype(dtype)
         Ms.append(_recurse(S, T, node.children[j], leaf, dtype))
     C = np.zeros((m0 * mb, n0 * nb), dtype=dtype)
     for k in range(m0 * n0):
@@ -145,8 +151,43 @@ def _recurse(A, B, node, leaf, dtype):
     return C
 
 
+def _frexp_exp(x: np.ndarray) -> np.ndarray:
+    """frexp exponent e (x = f 2^e, 1/2 <= |f| < 1) of each entry; None-like
+    sentinel -2^30 for zeros."""
+    f, e = np.frexp(x)
+    return np.where(x == 0, -(1 << 30), e).astype(np.int64)
+
+
+def between_exponents(A: np.ndarray, B: np.ndarray, node: Node) -> list:
+    """Scaling between recursive steps (the reading used here: after the
+    root node's sums, before the next level's).  For each root product r,
+    the pair (S_r, T_r) is inside-scaled as its own product A B (Alg. 2 in
+    power-of-two form): d_k = floor((e(max_j |T_r[k, j]|) - e(max_i
+    |S_r[i, k]|)) / 2), 0 where either side is zero.  S_r, T_r are the
+    root node's sequential sums in index order in FP32 (the precision the
+    operand sums are formed in); A, B already padded."""
+    r = canonical(node.rule)
+    m0, k0, n0 = r.m0, r.k0, r.n0
+    A32, B32 = np.asarray(A, np.float32), np.asarray(B, np.float32)
+    mb, kb, nb = A32.shape[0] // m0, A32.shape[1] // k0, B32.shape[1] // n0
+    Ab = [A32[p * mb:(p + 1) * mb, q * kb:(q + 1) * kb] for p in range(m0) for q in range(k0)]
+    Bb = [B32[p * kb:(p + 1) * kb, q * nb:(q + 1) * nb] for p in range(k0) for q in range(n0)]
+    out = []
+    for j in range(r.R):
+        S = _seq_sum([(r.U[i, j], Ab[i]) for i in range(m0 * k0) if r.U[i, j] != 0], np.float32)
+        T = _seq_sum([(r.V[i, j], Bb[i]) for i in range(k0 * n0) if r.V[i, j] != 0], np.float32)
+        if S is None or T is None or S.shape[0] == 0 or T.shape[1] == 0:
+            out.append(np.zeros(kb, np.int64))
+            continue
+        eS = _frexp_exp(np.abs(S).max(axis=0).astype(np.float64))
+        eT = _frexp_exp(np.abs(T).max(axis=1).astype(np.float64))
+        zero = (eS <= -(1 << 29)) | (eT <= -(1 << 29))
+        out.append(np.where(zero, 0, np.floor_divide(eT - eS, 2)).astype(np.int64))
+    return out
+
+
 def fmm(A: np.ndarray, B: np.ndarray, plan: Optional[Node],
-        leaf: Optional[Callable] = None, dtype=np.float64) -> np.ndarray:
+        leaf: Optional[Callable] = None, dtype=np.float64, between: bool = False) -> np.ndarray:
     """C = AB by the recursive fast algorithm of Eq. 3.2 with the given plan.
 
     A and B are zero-padded once, up front, so that every level partitions
@@ -165,7 +206,8 @@ def fmm(A: np.ndarray, B: np.ndarray, plan: Optional[Node],
     Bp = _pad(np.asarray(B, dtype=dtype), Kp, Np)
     if M == 0 or N == 0:
         return np.zeros((M, N), dtype=dtype)
-    return _recurse(Ap, Bp, plan, leaf, dtype)[:M, :N]
+    dvecs = between_exponents(Ap, Bp, plan) if between and depth(plan) >= 2 else None
+    return _recurse(Ap, Bp, plan, leaf, dtype, dvecs)[:M, :N]
 
 
 def abs_plan(node: Optional[Node]) -> Optional[Node]:
@@ -178,14 +220,27 @@ def abs_plan(node: Optional[Node]) -> Optional[Node]:
     return Node(ar, [abs_plan(c) for c in node.children])
 
 
-def growth(A: np.ndarray, B: np.ndarray, plan: Optional[Node]) -> np.ndarray:
+def growth(A: np.ndarray, B: np.ndarray, plan: Optional[Node], between: bool = False) -> np.ndarray:
     """Componentwise growth quantity of the proof of Theorem 4.1:
         G_ij = sum_r |W-product| (sum_i |U-product| |A_i|) (sum_j |V-product| |B_j|)
     evaluated entrywise (before the max-norms are taken).  The proof bounds
     |C_k - fl(C_k)| by delta_k * eps * G to first order, and G <= (K/K0^L)
     E^L ||A|| ||B||.  Computed as the fast algorithm run on |A|, |B| with
-    |U|, |V|, |W| in float64."""
-    return fmm(np.abs(A), np.abs(B), abs_plan(plan))
+    |U|, |V|, |W| in float64.  With ``between``, the root products' scaling
+    exponents (from the signed operands) scale the absolute sums the same
+    way."""
+    if not (between and depth(plan) >= 2):
+        return fmm(np.abs(A), np.abs(B), abs_plan(plan))
+    M, K = A.shape
+    N = B.shape[1]
+    pm, pk, pn = dims(plan)
+    Mp, Kp, Np = -(-M // pm) * pm, -(-K // pk) * pk, -(-N // pn) * pn
+    Ap = _pad(np.asarray(A, dtype=np.float64), Mp, Kp)
+    Bp = _pad(np.asarray(B, dtype=np.float64), Kp, Np)
+    if M == 0 or N == 0:
+        return np.zeros((M, N))
+    dvecs = between_exponents(Ap, Bp, plan)
+    return _recurse(np.abs(Ap), np.abs(Bp), abs_plan(plan), classical, np.float64, dvecs)[:M, :N]
 
 
 # ---------------------------------------------------------------------------

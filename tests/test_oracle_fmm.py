@@ -165,3 +165,53 @@ def test_flop_count():
     f = F.flop_count(F.uniform([S, S]), 4096, 4096, 4096)
     assert f["leaves"] == 49
     assert f["leaf"] == 2.0 * 49 * 1024**3
+
+
+# ---------------------------------------------------------------- scaling between recursive steps
+
+def test_between_scaling_is_exact_on_integers():
+    # Power-of-two scaling of each root product's pair cancels exactly: with
+    # exact arithmetic the result is still the classical product.
+    from oracle import rules as OR
+    rng = np.random.default_rng(5)
+    for rules in ([OR.strassen(), OR.strassen()], [OR.winograd(), OR.winograd()], [OR.strassen(), OR.fast323()]):
+        tree = F.uniform(rules)
+        A = rng.integers(-4, 5, size=(24, 20)).astype(np.float64)
+        B = rng.integers(-4, 5, size=(20, 18)).astype(np.float64)
+        # spread the magnitudes so that nonzero exponents occur
+        A *= np.exp2(rng.integers(-6, 7, size=(1, 20)))
+        B *= np.exp2(rng.integers(-6, 7, size=(20, 1)))
+        assert np.array_equal(F.fmm(A, B, tree, between=True), A @ B)
+
+
+def test_between_exponents_balance_each_pair():
+    # After the scaling, e(max |T_r[k, :]|) - e(max |S_r[:, k]|) is 0 or 1
+    # for every root product r and column k with both sides nonzero (the
+    # I-step property, Sec. 6.2), and d is 0 where a side is zero.
+    from oracle import rules as OR
+    from oracle.rules import canonical
+    rng = np.random.default_rng(9)
+    rules = [OR.winograd(), OR.strassen()]
+    tree = F.uniform(rules)
+    A = rng.uniform(-1, 1, size=(16, 16)) * np.exp2(rng.integers(-20, 21, size=(1, 16)))
+    B = rng.uniform(-1, 1, size=(16, 16)) * np.exp2(rng.integers(-20, 21, size=(16, 1)))
+    A[:, 3] = 0.0  # a zero column of A: its S columns vanish for some r
+    d = F.between_exponents(A, B, tree)
+    r = canonical(rules[0])
+    kb = 8
+    Ab = [A[p * 8:(p + 1) * 8, q * 8:(q + 1) * 8].astype(np.float32) for p in range(2) for q in range(2)]
+    Bb = [B[p * 8:(p + 1) * 8, q * 8:(q + 1) * 8].astype(np.float32) for p in range(2) for q in range(2)]
+    checked = 0
+    for j in range(r.R):
+        S = sum(np.float32(r.U[i, j]) * Ab[i] for i in range(4) if r.U[i, j] != 0)
+        T = sum(np.float32(r.V[i, j]) * Bb[i] for i in range(4) if r.V[i, j] != 0)
+        for k in range(kb):
+            cs, rt = np.abs(S[:, k]).max(), np.abs(T[k, :]).max()
+            if cs == 0 or rt == 0:
+                assert d[j][k] == 0
+                continue
+            es = np.frexp(cs * 2.0 ** d[j][k])[1]
+            et = np.frexp(rt * 2.0 ** -d[j][k])[1]
+            assert et - es in (0, 1), (j, k, et - es)
+            checked += 1
+    assert checked > 20
