@@ -194,6 +194,23 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
 fmm_status fmm_plan_set_schedule(fmm_plan_t plan, int schedule);
 
 /*
+ * Scaling between recursive steps (opt-in; plans of two or more levels;
+ * the paper applies Algs. 1-3 to the whole product only, so this is an
+ * extension: each sub-product of a recursive step is itself a matrix
+ * product, and it is scaled as one).  After the first level's operand sums
+ * S_r, T_r are formed (in FP32, in index order), each pair is inside-scaled
+ * as its own product A B -- Alg. 2 in power-of-two form,
+ *   d^(r)_k = floor((e(max_j |T_r[k, j]|) - e(max_i |S_r[i, k]|)) / 2),
+ * 0 where either side is zero -- S_r <- S_r 2^d, T_r <- 2^-d T_r, before the
+ * lower levels combine them.  The scale cancels exactly in every product,
+ * so only rounding changes.  Forward products under the pass schedule only:
+ * fmm_multiply returns FMM_ERR_UNSUPPORTED under the load-stage schedule,
+ * fmm_multiply_backward and fmm_multiply_noalloc ignore it, batches reject
+ * it.  enable = 0 turns it off.  A no-op for plans of fewer than two levels.
+ */
+fmm_status fmm_plan_set_between_scaling(fmm_plan_t plan, int enable);
+
+/*
  * Workspace bytes fmm_multiply / fmm_multiply_backward need for this plan
  * and shape (an upper bound over input types).  The fused kernel reads its
  * operands through tensor-memory-access copies of whole 128 x 64 tiles; an

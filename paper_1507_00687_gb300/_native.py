@@ -29,6 +29,7 @@ EXPORTS = [
     "fmm_sync_status", "fmm_status_string", "fmm_version", "fmm_last_error", "fmm_multiply_noalloc",
     "fmm_plan_set_schedule", "fmm_kernel_timing", "fmm_kernel_timing_read",
     "fmm_batch_workspace_size", "fmm_batch_create", "fmm_batch_run", "fmm_batch_destroy",
+    "fmm_plan_set_between_scaling",
 ]
 
 # Bytes of the library's static scratch array (FMM_NOALLOC_SCRATCH_BYTES).
@@ -69,6 +70,7 @@ def lib():
     L.fmm_plan.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(FmmRule), C.c_int]
     L.fmm_plan_destroy.argtypes = [vp]
     L.fmm_plan_set_schedule.argtypes = [vp, C.c_int]
+    L.fmm_plan_set_between_scaling.argtypes = [vp, C.c_int]
     L.fmm_kernel_timing.argtypes = [C.c_int]
     L.fmm_batch_workspace_size.argtypes = [C.POINTER(FmmProblem), C.c_int, C.c_int, C.c_char_p,
                                            C.POINTER(C.c_size_t)]

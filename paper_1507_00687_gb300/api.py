@@ -42,9 +42,11 @@ class Plan:
     ``schedule`` (fmm_plan_set_schedule): "auto", "load_stage" (S_r, T_r
     formed in the multiply kernel's load stage) or "pass" (formed by a
     combination pass into the workspace; "pass_epilogue" / "pass_products"
-    force where the output combination runs)."""
+    force where the output combination runs).  ``between``: scaling between
+    recursive steps (fmm_plan_set_between_scaling)."""
 
-    def __init__(self, rules: Sequence[Union[str, BaseRule]], leaf: str = "bf16x3", schedule: str = "auto"):
+    def __init__(self, rules: Sequence[Union[str, BaseRule]], leaf: str = "bf16x3", schedule: str = "auto",
+                 between: bool = False):
         self.rules = [get_rule(r) if isinstance(r, str) else r for r in rules]
         self.leaf = leaf
         self._keep = []
@@ -62,6 +64,9 @@ class Plan:
         self._h = h
         self.schedule = schedule
         N.check(N.lib().fmm_plan_set_schedule(h, SCHEDULE[schedule]), "fmm_plan_set_schedule")
+        self.between = between
+        if between:
+            N.check(N.lib().fmm_plan_set_between_scaling(h, 1), "fmm_plan_set_between_scaling")
 
     @property
     def handle(self):

@@ -272,9 +272,14 @@ static int64_t products_bytes(int64_t Tx, int64_t Ty, int64_t ptx, int64_t pty, 
 static int64_t pass_bytes(const Plan* p, int64_t Tx, int64_t Kd, int64_t Ty, int64_t ptx, int64_t pk,
                           int64_t pty) {
   const int planes = p->leaf_format == FMM_LEAF_BF16X3 ? 2 : 1;
+  int64_t between = 0;
+  if (p->between && p->levels >= 2) {
+    const int64_t k1 = ceil_div(Kd, pk) * (pk / p->rules[0].k0);
+    between = 3 * round_up(p->rules[0].r * k1 * 4, 256);
+  }
   return combined_bytes(Tx, Kd, ptx, pk, p->leaves, planes, 128) +
          combined_bytes(Ty, Kd, pty, pk, p->leaves, planes, 256) +
-         (p->leaves > 1 ? products_bytes(Tx, Ty, ptx, pty, p->leaves, 256) : 0);
+         (p->leaves > 1 ? products_bytes(Tx, Ty, ptx, pty, p->leaves, 256) : 0) + between;
 }
 
 // Geometry of the pass schedule for one product: leaf block extents, their
@@ -337,6 +342,7 @@ static CombineArgs combine_args(const Plan* p, const PassGeom& g, const Source& 
   ca.blk_k_shift = side == 0 ? 0 : 16;
   ca.out = out;
   ca.fmt = p->leaf_format;
+  ca.bk = g.bk;
   return ca;
 }
 
@@ -394,8 +400,10 @@ static OutArgs out_args(const Plan* p, const PassGeom& g, const EpilogueArgs& c,
 // them for the output pass.  FMM_ERR_WORKSPACE when the workspace is too
 // small.
 static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, const EpilogueArgs& c,
-                           const LeafDesc* leaves, int* status, void* ws, size_t ws_bytes, cudaStream_t st) {
+                           const LeafDesc* leaves, int* status, void* ws, size_t ws_bytes, cudaStream_t st,
+                           bool between) {
   const PassGeom g = pass_geom(p, x, y, 0);
+  const int64_t R = g.R;
   if (!ws || (uintptr_t)ws % 256 != 0 || (int64_t)ws_bytes < g.bytes_a + g.bytes_b) return FMM_ERR_WORKSPACE;
   char* wa = static_cast<char*>(ws);
   char* wb = wa + g.bytes_a;
@@ -407,9 +415,52 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
   const bool store_m = want_m && g.R > 1 && p->pm * p->pn <= kMaxOutBlocks &&
                        (int64_t)ws_bytes >= g.bytes_a + g.bytes_b + g.bytes_m;
   float* mbuf = store_m ? reinterpret_cast<float*>(wb + g.bytes_b) : nullptr;
+  CombineArgs ca = combine_args(p, g, x, 0, leaves, wa), cb = combine_args(p, g, y, 1, leaves, wb);
+  if (between) {
+    // Scaling between recursive steps: the first level's pairs (S_r, T_r)
+    // get inside-scaling exponents d^(r) from their FP32 sums; the
+    // combination pass then scales each term element by 2^(+-d).
+    const Plan* p1 = p->level1;
+    if (ensure_uploaded(p1) != FMM_OK) return FMM_ERR_CUDA;
+    const int64_t R1 = p1->leaves;
+    const int64_t k1 = g.bk * (p->pk / p1->pk);
+    const int64_t dbytes = round_up(R1 * k1 * 4, 256);
+    char* wz = wb + g.bytes_b + (store_m ? g.bytes_m : 0);
+    if ((int64_t)ws_bytes < (wz - wa) + 3 * dbytes) return FMM_ERR_WORKSPACE;
+    int* cexp = reinterpret_cast<int*>(wz);
+    int* rexp = reinterpret_cast<int*>(wz + dbytes);
+    int* d1 = reinterpret_cast<int*>(wz + 2 * dbytes);
+    Source x1 = x, y1 = y;
+    x1.pt = p1->pm;
+    x1.pk = p1->pk;
+    y1.pt = p1->pn;
+    y1.pk = p1->pk;
+    const PassGeom g1 = pass_geom(p1, x1, y1, 128);
+    CombineArgs na = combine_args(p1, g1, x1, 0, p1->dev, nullptr);
+    CombineArgs nb = combine_args(p1, g1, y1, 1, p1->dev, nullptr);
+    // level-1 blocks as the full plan partitions them (leaf blocks grouped)
+    const int64_t bt1a = g.bt_a * (p->pm / p1->pm), bt1b = g.bt_b * (p->pn / p1->pn);
+    na.b_rows = x.kcontig ? bt1a : k1;
+    na.b_cols = x.kcontig ? k1 : bt1a;
+    nb.b_rows = y.kcontig ? bt1b : k1;
+    nb.b_cols = y.kcontig ? k1 : bt1b;
+    if (!cuda_ok(launch_fill(cexp, 2 * dbytes / 4, kZeroExp, st), "between-steps fill") ||
+        !cuda_ok(launch_node_exp(na, cexp, k1, st), "between-steps exponents (A)") ||
+        !cuda_ok(launch_node_exp(nb, rexp, k1, st), "between-steps exponents (B)") ||
+        !cuda_ok(launch_between_finalize(cexp, rexp, d1, R1 * k1, st), "between-steps exponents"))
+      return FMM_ERR_CUDA;
+    for (CombineArgs* c2 : {&ca, &cb}) {
+      c2->between_d = d1;
+      c2->between_k1 = k1;
+      c2->leaves_per_node = R / R1;
+      c2->kb_inner = p->pk / p1->pk;
+    }
+    ca.between_sign = +1;
+    cb.between_sign = -1;
+  }
   // B first: a scaling sequence that ends with a pass over B leaves it in L2
-  if (!cuda_ok(launch_combine(combine_args(p, g, y, 1, leaves, wb), st), "combination pass (B)")) return FMM_ERR_CUDA;
-  if (!cuda_ok(launch_combine(combine_args(p, g, x, 0, leaves, wa), st), "combination pass (A)")) return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_combine(cb, st), "combination pass (B)")) return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_combine(ca, st), "combination pass (A)")) return FMM_ERR_CUDA;
   DirectArgs d;
   if (!direct_args(p, g, x, y, c, leaves, wa, wb, mbuf, status, &d)) return FMM_ERR_CUDA;
   if (!cuda_ok(launch_direct_gemm(d, p->leaf_format, g.bn, st), "multiply launch")) return FMM_ERR_CUDA;
@@ -425,7 +476,7 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
 // use).
 static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, float* C, int64_t ldc, int64_t M,
                            int64_t K, int64_t N, const int* eA, const int* eB, void* ws, size_t ws_bytes,
-                           cudaStream_t st, const LeafDesc* leaves = nullptr) {
+                           cudaStream_t st, const LeafDesc* leaves = nullptr, bool allow_between = true) {
   if (M == 0 || N == 0) return FMM_OK;
   if (K == 0) {
     return cuda_ok(cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)N * 4, (size_t)M, st), "memset")
@@ -452,7 +503,9 @@ static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, floa
                     p->schedule == FMM_SCHEDULE_PASS_PRODUCTS ||
                     (p->schedule == FMM_SCHEDULE_AUTO && ws && (uintptr_t)ws % 256 == 0 &&
                      (int64_t)ws_bytes >= pass_bytes(p, M, K, N, p->pm, p->pk, p->pn));
-  if (pass) return run_pass(p, x, y, c, leaves, status, ws, ws_bytes, st);
+  const bool between = allow_between && p->between && p->levels >= 2 && p->level1;
+  if (between && !pass) return p->schedule == FMM_SCHEDULE_LOAD_STAGE ? FMM_ERR_UNSUPPORTED : FMM_ERR_WORKSPACE;
+  if (pass) return run_pass(p, x, y, c, leaves, status, ws, ws_bytes, st, between);
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
   char* w = static_cast<char*>(ws);
@@ -607,6 +660,7 @@ static fmm_status batch_check(const fmm_problem* probs, int count, int dt, const
     if (fmt >= 0 && p->leaf_format != fmt) return FMM_ERR_ARG;
     fmt = p->leaf_format;
     if (dt == FMM_DT_F16 && fmt == FMM_LEAF_BF16X3) return FMM_ERR_DTYPE;
+    if (p->between && p->levels >= 2) return FMM_ERR_UNSUPPORTED;
     if (p->pm * p->pn > kMaxOutBlocks || p->pm * p->pk > 64 || p->pk * p->pn > 64) return FMM_ERR_UNSUPPORTED;
     if (ceil_div(q.M, p->pm) >= (1ll << 30) || ceil_div(q.N, p->pn) >= (1ll << 30) ||
         ceil_div(q.K, p->pk) >= (1ll << 30))
@@ -855,6 +909,17 @@ fmm_status fmm_plan_set_schedule(fmm_plan_t plan, int schedule) {
   return FMM_OK;
 }
 
+fmm_status fmm_plan_set_between_scaling(fmm_plan_t plan, int enable) {
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (!p) return FMM_ERR_ARG;
+  if (enable && p->levels >= 2 && !p->level1) {
+    fmm_status s = make_plan({p->rules[0]}, p->leaf_format, &p->level1);
+    if (s != FMM_OK) return s;
+  }
+  p->between = enable ? 1 : 0;
+  return FMM_OK;
+}
+
 fmm_status fmm_plan_info(fmm_plan_t plan, double* q_sum, double* e_prod, int64_t* leaves, int64_t* nnz,
                          int64_t* pm, int64_t* pk, int64_t* pn) {
   const Plan* p = reinterpret_cast<const Plan*>(plan);
@@ -1048,7 +1113,7 @@ fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, con
   const Source a{A, lda, in_dtype, true, M, K, p->pm, p->pk, eA, -1, d, +1};
   const Source b{B, ldb, in_dtype, false, N, K, p->pn, p->pk, d, -1, eB, -1};
   return run_plan(p, a, b, C, ldc, M, K, N, eA, eB, scratch + table, FMM_NOALLOC_SCRATCH_BYTES - table, st,
-                  reinterpret_cast<const LeafDesc*>(scratch));
+                  reinterpret_cast<const LeafDesc*>(scratch), /*allow_between=*/false);
 }
 
 fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc, const void* A, int64_t lda,

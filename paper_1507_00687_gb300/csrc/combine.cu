@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs a) 
 // use.  TR * 16 threads, one row of 4 columns each.
 constexpr int kMaxStaged = 64;
 
-template <int DT, int FMT, int TR, int RPT>
+template <int DT, int FMT, int TR, int RPT, bool BETWEEN = false>
 __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_t bx, int64_t by, float4* tile4) {
   // RPT rows per thread: rows tr + (TR / RPT) q, q < RPT; 4 columns each
   constexpr int kT = TR * 16 / RPT;
@@ -191,11 +191,13 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
   int* toff = reinterpret_cast<int*>(tile4 + nb * TR * 16);
   float* tcoef = reinterpret_cast<float*>(toff + nnz);
   int* tstart = reinterpret_cast<int*>(tcoef + nnz);
+  int* tkb = tstart + R + 1;  // k block of each term (between-steps scaling only)
   for (int i = threadIdx.x; i < nnz; i += kT) {
     const int32_t blk = __ldg(a.t_blk + i);
     const int bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
     toff[i] = (a.t_rows ? bt * n_cb + bk : bk * n_cb + bt) * TR * 16;
     tcoef[i] = __ldg(a.t_coef + i);
+    if (BETWEEN) tkb[i] = bk;
   }
   for (int i = threadIdx.x; i <= R; i += kT) tstart[i] = __ldg(a.t_start + i);
   const int64_t lc = c0 + tc;
@@ -251,12 +253,35 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
     float acc[RPT][4];
 #pragma unroll
     for (int q = 0; q < RPT; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+    const int* dnode = BETWEEN ? a.between_d + (r / a.leaves_per_node) * a.between_k1 : nullptr;
     for (; t < t1; ++t) {
       const float coef = tcoef[t];
       const int off = toff[t] + me;
+      // between-steps scale of this term's elements (exact powers of two)
+      float f[RPT][4];
+      if constexpr (BETWEEN) {
+        const int64_t kbase = (tkb[t] % a.kb_inner) * a.bk;
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          if (a.t_rows) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int64_t k = kbase + lc + j;
+              f[q][j] = k < a.between_k1 ? exp2i(a.between_sign * __ldg(dnode + k)) : 1.f;
+            }
+          } else {
+            const int64_t k = kbase + r0 + tr + (TR / RPT) * q;
+            const float g = k < a.between_k1 ? exp2i(a.between_sign * __ldg(dnode + k)) : 1.f;
+            f[q][0] = f[q][1] = f[q][2] = f[q][3] = g;
+          }
+        }
+      }
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
-        const float4 v = tile4[off + q * kRowStep];
+        float4 v = tile4[off + q * kRowStep];
+        if constexpr (BETWEEN) {
+          v.x *= f[q][0]; v.y *= f[q][1]; v.z *= f[q][2]; v.w *= f[q][3];
+        }
         acc[q][0] = fmaf(coef, v.x, acc[q][0]);
         acc[q][1] = fmaf(coef, v.y, acc[q][1]);
         acc[q][2] = fmaf(coef, v.z, acc[q][2]);
@@ -268,10 +293,10 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
   }
 }
 
-template <int DT, int FMT, int TR, int RPT>
+template <int DT, int FMT, int TR, int RPT, bool BETWEEN>
 __global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_kernel(const CombineArgs a) {
   extern __shared__ float4 tile4[];  // [block][TR][16], then the term list
-  combine_staged_body<DT, FMT, TR, RPT>(a, blockIdx.x, blockIdx.y, tile4);
+  combine_staged_body<DT, FMT, TR, RPT, BETWEEN>(a, blockIdx.x, blockIdx.y, tile4);
 }
 
 // Index of the problem whose [start[p], start[p + 1]) range holds idx.
@@ -297,25 +322,32 @@ __global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_batched_kernel(c
   combine_staged_body<DT, FMT, TR, RPT>(a, local % gx, local / gx, tile4);
 }
 
-// Shared memory of the staged form: block tiles plus the term list.
+// Shared memory of the staged form: block tiles plus the term list (and
+// the terms' k blocks, for the between-steps scaling).
 inline size_t staged_smem(int nb, int tr, int64_t nnz, int64_t leaves) {
-  return (size_t)nb * tr * 256 + (size_t)nnz * 8 + (size_t)(leaves + 1) * 4;
+  return (size_t)nb * tr * 256 + (size_t)nnz * 12 + (size_t)(leaves + 1) * 4;
 }
 constexpr size_t kStagedSmemMax = 200 * 1024;
 
-template <int DT, int FMT, int TR, int RPT = 1>
-void launch_staged_tr(const CombineArgs& a, int nb, cudaStream_t st) {
+template <int DT, int FMT, int TR, int RPT, bool BETWEEN>
+void launch_staged_tr_b(const CombineArgs& a, int nb, cudaStream_t st) {
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   if (!attr_done[dev]) {
-    cudaFuncSetAttribute(combine_staged_kernel<DT, FMT, TR, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(combine_staged_kernel<DT, FMT, TR, RPT, BETWEEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kStagedSmemMax);
     attr_done[dev] = true;
   }
-  combine_staged_kernel<DT, FMT, TR, RPT><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / TR)),
-                                            TR * 16 / RPT, staged_smem(nb, TR, a.t_nnz, a.num_leaves), st>>>(a);
+  combine_staged_kernel<DT, FMT, TR, RPT, BETWEEN><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / TR)),
+                                                     TR * 16 / RPT, staged_smem(nb, TR, a.t_nnz, a.num_leaves), st>>>(a);
+}
+
+template <int DT, int FMT, int TR, int RPT = 1>
+void launch_staged_tr(const CombineArgs& a, int nb, cudaStream_t st) {
+  if (a.between_d) launch_staged_tr_b<DT, FMT, TR, RPT, true>(a, nb, st);
+  else launch_staged_tr_b<DT, FMT, TR, RPT, false>(a, nb, st);
 }
 
 template <int DT, int FMT>
@@ -334,7 +366,7 @@ void launch_fmt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
   const int tr = nb <= 4 ? 32 : nb <= 8 ? 16 : nb <= 16 ? 8 : nb <= 32 ? 4 : 2;
   if (nb <= kMaxStaged && staged_smem((int)nb, tr, a.t_nnz, a.num_leaves) <= kStagedSmemMax)
     launch_staged<DT, FMT>(a, (int)nb, st);
-  else combine_kernel<DT, FMT><<<grid, kThreads, 0, st>>>(a);
+  else if (!a.between_d) combine_kernel<DT, FMT><<<grid, kThreads, 0, st>>>(a);
 }
 
 template <int DT>
@@ -451,7 +483,144 @@ __global__ void __launch_bounds__(TR * 16) out_combine_batched_kernel(const OutA
   out_combine_body<TR>(a, local % gx, local / gx, acc4);
 }
 
+// Node-exponent pass (scaling between recursive steps): one CTA covers a
+// 16 x 64 position tile of the level-1 blocks, stages the (scaled) input
+// block tiles as the combination pass does, forms each level-1 product's
+// FP32 sum in term order and reduces the frexp exponents of the sums over t
+// (over the tile's rows when t runs along memory rows, else over its
+// columns) into out[r * k1 + k] with atomicMax.
+constexpr int kNodeTR = 16;
+
+template <int DT>
+__global__ void __launch_bounds__(kNodeTR * 16) node_exp_kernel(const CombineArgs a, int* out, int64_t k1) {
+  extern __shared__ float4 tile4[];  // [block][kNodeTR][16], then colmax [R][64] ints
+  const int64_t r0 = (int64_t)blockIdx.y * kNodeTR, c0 = (int64_t)blockIdx.x * kTC;
+  const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15, tc = tq * 4;
+  const int es = DT == kF32 ? 4 : 2;
+  const bool vec_ok = ((uintptr_t)a.src % (4 * es) == 0) && (a.ld % 4 == 0) && (a.b_cols % 4 == 0) &&
+                      (!a.ce || (uintptr_t)a.ce % 16 == 0);
+  const int n_rb = (int)a.n_rb, n_cb = (int)a.n_cb, nb = n_rb * n_cb;
+  const int R = (int)a.num_leaves;
+  int* colmax = reinterpret_cast<int*>(tile4 + nb * kNodeTR * 16);
+  for (int i = threadIdx.x; i < R * kTC; i += kNodeTR * 16) colmax[i] = kZeroExp;
+  const int64_t lr = r0 + tr, lc = c0 + tc;
+  for (int rb = 0; rb < n_rb; ++rb) {
+    const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows);
+    const int64_t gr = rb * a.b_rows + lr;
+    const bool row_in = r0 + kNodeTR <= nr;
+    const int er = (a.re && lr < nr) ? a.rs * __ldg(a.re + gr) : 0;
+    const char* src_row = static_cast<const char*>(a.src) + gr * a.ld * es;
+    for (int cb = 0; cb < n_cb; ++cb) {
+      const int64_t nc = min(a.b_cols, a.cols - cb * a.b_cols);
+      const int64_t gc = cb * a.b_cols + lc;
+      float x[4];
+      if (vec_ok && row_in && c0 + kTC <= nc) {
+        load4<DT>(src_row, gc, x);
+        if (a.re || a.ce) {
+          int4 ec = make_int4(0, 0, 0, 0);
+          if (a.ce) ec = __ldg(reinterpret_cast<const int4*>(a.ce + gc));
+          x[0] = scale_pow2(x[0], er + a.cs * ec.x);
+          x[1] = scale_pow2(x[1], er + a.cs * ec.y);
+          x[2] = scale_pow2(x[2], er + a.cs * ec.z);
+          x[3] = scale_pow2(x[3], er + a.cs * ec.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          x[j] = 0.f;
+          if (lr < nr && lc + j < nc) {
+            const float v = load_elem<DT>(src_row, gc + j);
+            x[j] = scale_pow2(v, er + (a.ce ? a.cs * __ldg(a.ce + gc + j) : 0));
+          }
+        }
+      }
+      tile4[((rb * n_cb + cb) * kNodeTR + tr) * 16 + tq] = make_float4(x[0], x[1], x[2], x[3]);
+    }
+  }
+  __syncthreads();
+  const int me = tr * 16 + tq;
+  bool nf = false;
+  for (int r = 0; r < R; ++r) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int t1 = __ldg(a.t_start + r + 1);
+    for (int t = __ldg(a.t_start + r); t < t1; ++t) {
+      const int32_t blk = __ldg(a.t_blk + t);
+      const int bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
+      const int b = a.t_rows ? bt * n_cb + bk : bk * n_cb + bt;
+      const float coef = __ldg(a.t_coef + t);
+      const float4 v = tile4[b * kNodeTR * 16 + me];
+      acc[0] = fmaf(coef, v.x, acc[0]);
+      acc[1] = fmaf(coef, v.y, acc[1]);
+      acc[2] = fmaf(coef, v.z, acc[2]);
+      acc[3] = fmaf(coef, v.w, acc[3]);
+    }
+    int e[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) e[j] = fexp_f32(__float_as_uint(fabsf(acc[j])), &nf);
+    if (a.t_rows) {
+      // k along memory columns: maximum over the tile's rows
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (e[j] > kZeroExp) atomicMax(&colmax[r * kTC + tc + j], e[j]);
+    } else {
+      // k along memory rows: maximum over the tile's columns (16 threads)
+      int m = max(max(e[0], e[1]), max(e[2], e[3]));
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (tq == 0 && m > kZeroExp && lr < k1) atomicMax(out + (int64_t)r * k1 + lr, m);
+    }
+  }
+  if (a.t_rows) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < R * kTC; i += kNodeTR * 16) {
+      const int r = i / kTC, c = i % kTC;
+      if (colmax[i] > kZeroExp && c0 + c < k1) atomicMax(out + (int64_t)r * k1 + c0 + c, colmax[i]);
+    }
+  }
+}
+
+__global__ void between_finalize_kernel(const int* cexp, const int* rexp, int* d, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = cexp[i], r = rexp[i];
+  d[i] = (c <= kZeroExp / 2 || r <= kZeroExp / 2) ? 0 : ((r - c) >> 1);  // arithmetic shift = floor
+}
+
 }  // namespace
+
+cudaError_t launch_node_exp(const CombineArgs& a, int* out, int64_t k1, cudaStream_t st) {
+  const int64_t nb = a.n_rb * a.n_cb;
+  const size_t smem = (size_t)nb * kNodeTR * 256 + (size_t)a.num_leaves * kTC * 4;
+  if (smem > kStagedSmemMax) return cudaErrorInvalidValue;
+  const int64_t rows = a.b_rows, cols = a.b_cols;
+  if (rows == 0 || cols == 0 || a.num_leaves == 0) return cudaSuccess;
+  static bool attr_done[64][3] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  const dim3 grid((unsigned)((cols + kTC - 1) / kTC), (unsigned)((rows + kNodeTR - 1) / kNodeTR));
+  KernelTimer timer("combine", st);
+  auto go = [&](auto kern, int idx) {
+    if (!attr_done[dev][idx]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedSmemMax);
+      attr_done[dev][idx] = true;
+    }
+    kern<<<grid, kNodeTR * 16, smem, st>>>(a, out, k1);
+  };
+  switch (a.dtype) {
+    case kF32: go(node_exp_kernel<kF32>, 0); break;
+    case kBF16: go(node_exp_kernel<kBF16>, 1); break;
+    default: go(node_exp_kernel<kF16>, 2); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_between_finalize(const int* cexp, const int* rexp, int* d, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  KernelTimer timer("scale", st);
+  between_finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cexp, rexp, d, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st) {
   if (a.c_blocks > kMaxOutBlocks || a.c.bm > a.tp_a || a.c.bn > a.tp_b || a.tp_b % kTC != 0)
@@ -571,6 +740,12 @@ size_t combine_staged_smem(int64_t nb, int tr, int64_t nnz, int64_t leaves) { re
 
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st) {
   if (a.p_rows % kTR != 0 || a.p_cols % kTC != 0 || a.p_rows / kTR > 65535) return cudaErrorInvalidValue;
+  if (a.between_d) {
+    const int64_t nb = a.n_rb * a.n_cb;
+    const int tr = nb <= 4 ? 32 : nb <= 8 ? 16 : nb <= 16 ? 8 : nb <= 32 ? 4 : 2;
+    if (nb > kMaxStaged || staged_smem((int)nb, tr, a.t_nnz, a.num_leaves) > kStagedSmemMax)
+      return cudaErrorNotSupported;  // the between-steps scale needs the staged form
+  }
   if (a.b_rows > a.p_rows || a.b_cols > a.p_cols) return cudaErrorInvalidValue;
   if (a.num_leaves == 0 || a.p_rows == 0 || a.p_cols == 0) return cudaSuccess;
   const dim3 grid((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / kTR));

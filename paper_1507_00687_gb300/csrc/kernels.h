@@ -124,7 +124,26 @@ struct CombineArgs {
   int blk_t_shift, blk_k_shift;
   void* out;            // 16-bit elements
   int fmt;              // FMM_LEAF_BF16 / FMM_LEAF_F16 / FMM_LEAF_BF16X3
+  // Scaling between recursive steps (null: off): every element of a term of
+  // leaf r is multiplied by 2^(between_sign d[r / leaves_per_node][k1]), k1
+  // its k index inside its level-1 block: (kb mod kb_inner) * bk + k.
+  const int* between_d;
+  int between_sign;
+  int64_t between_k1;       // k extent of a level-1 block (row length of d)
+  int64_t leaves_per_node;  // leaves below one level-1 product
+  int64_t kb_inner;         // leaf k blocks per level-1 k block
+  int64_t bk;               // leaf block k extent
 };
+
+// Node-exponent pass of the scaling between recursive steps: for each
+// level-1 product r (the terms of `a` are the level-1 plan's), the FP32
+// sequential sum S_r over the level-1 blocks (b_rows x b_cols, n_rb x n_cb
+// of them), and out[r * k1 + k] = max over t of the frexp exponent of
+// S_r[t, k] (atomicMax; out pre-filled with kZeroExp).  k runs along the
+// memory columns when a.t_rows, else along the memory rows.
+cudaError_t launch_node_exp(const CombineArgs& a, int* out, int64_t k1, cudaStream_t st);
+// d[i] = floor((rexp[i] - cexp[i]) / 2), 0 where either has no nonzero entry.
+cudaError_t launch_between_finalize(const int* cexp, const int* rexp, int* d, int64_t n, cudaStream_t st);
 
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st);
 

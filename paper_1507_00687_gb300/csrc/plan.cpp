@@ -236,6 +236,7 @@ fmm_status build_plan(const std::vector<CanonRule>& rules_in, int leaf_format, P
 void destroy_plan(Plan* p) {
   if (!p) return;
   if (p->dev) cudaFree(p->dev);
+  destroy_plan(p->level1);
   destroy_plan(p->grad_a);
   destroy_plan(p->grad_b);
   delete p;

@@ -63,6 +63,8 @@ struct Plan {
   // Device copy (on `device`): the LeafDesc array followed by `lists`.
   LeafDesc* dev = nullptr;
   int device = -1;
+  int between = 0;           // scaling between recursive steps (fmm_plan_set_between_scaling)
+  Plan* level1 = nullptr;    // the first level alone (its sums give the between-steps exponents)
   Plan* grad_a = nullptr;  // plan for dA = dC B^T  (lazily built)
   Plan* grad_b = nullptr;  // plan for dB = A^T dC
 };
