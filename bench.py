@@ -122,6 +122,54 @@ def batched_workload(api, inputs, torch, count: int) -> dict:
             "scaling": "OI"}
 
 
+# ---------------------------------------------------------------- fast-matmul linear layer
+
+def linear_layer_workload(api, torch, reps: int = 10) -> dict:
+    """Y = X W with X [8192, 4096] and W [4096, 4096] BF16 (U[-1,1]/sqrt(K),
+    seeded, on the device), Strassen two levels, BF16 leaves with FP32
+    accumulation: the forward product and the backward pair dX = dY W^T,
+    dW = X^T dY through the permuted rules, each timed with CUDA events; the
+    tensor-core kernel's share from the library's per-kernel timing."""
+    M, K, N = 8192, 4096, 4096
+    gen = torch.Generator(device="cuda").manual_seed(1507 + 3000)
+    X = ((torch.rand((M, K), generator=gen, device="cuda") * 2 - 1) / K ** 0.5).to(torch.bfloat16)
+    W = ((torch.rand((K, N), generator=gen, device="cuda") * 2 - 1) / K ** 0.5).to(torch.bfloat16)
+    dY = ((torch.rand((M, N), generator=gen, device="cuda") * 2 - 1)).float()
+    plan = api.Plan(["strassen", "strassen"], "bf16")
+    Y = api.multiply(plan, X, W)
+    api.multiply_backward(plan, dY, X, W)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    api.kernel_timing(True)
+    ev[0].record()
+    for _ in range(reps):
+        api.multiply(plan, X, W, out=Y)
+    ev[1].record()
+    for _ in range(reps):
+        api.multiply_backward(plan, dY, X, W)
+    ev[2].record()
+    torch.cuda.synchronize()
+    api.kernel_timing(False)
+    mult_ms, mult_n = api.kernel_timing_read("multiply")
+    api.sync_status()
+    f_ms = ev[0].elapsed_time(ev[1]) / reps
+    b_ms = ev[1].elapsed_time(ev[2]) / reps
+    flops = 2.0 * M * K * N
+    info = plan.info()
+    leaf_flops = 2.0 * info["leaves"] * (M // info["pm"]) * (K // info["pk"]) * (N // info["pn"])
+    # forward error against an FP64 product of a row sample
+    rows = torch.arange(0, M, 64, device="cuda")
+    ref = X[rows].double() @ W.double()
+    err = float((Y[rows].double() - ref).abs().max())
+    del X, W, dY, Y
+    torch.cuda.empty_cache()
+    return {"shape": [M, K, N], "plan": "strassen L=2, bf16 leaves", "forward_tflops": flops / (f_ms * 1e-3) / 1e12,
+            "backward_tflops": 2 * flops / (b_ms * 1e-3) / 1e12, "forward_ms": f_ms, "backward_ms": b_ms,
+            "multiply_kernel_ms_per_launch": mult_ms / max(1, mult_n),
+            "multiply_kernel_leaf_tflops": leaf_flops / (mult_ms / max(1, mult_n) * 1e-3) / 1e12,
+            "forward_max_abs_err_sampled_rows": err}
+
+
 # ---------------------------------------------------------------- clocks
 
 class Clocks:
@@ -408,6 +456,8 @@ def main():
     del ref, C_fast
     if not args.no_extras and args.batch > 0:
         extras["batched"] = batched_workload(api, inputs, torch, args.batch)
+    if not args.no_extras:
+        extras["autograd_linear"] = linear_layer_workload(api, torch)
 
     # ---------------- roofline of the dominant kernel (the tensor-core multiply)
     import json as _json
