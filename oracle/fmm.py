@@ -255,6 +255,36 @@ def leaf_rounded(fmt: str) -> Callable:
     return leaf
 
 
+def quantize_e4m3_blocks(X: np.ndarray, axis: int, block: int = 128):
+    """E4M3 with power-of-two block scales along ``axis`` (blocks of
+    ``block`` consecutive entries of each row (axis 1) or column (axis 0)):
+    each block is scaled by 2^-s with s = e(max |block|) - 8 (the frexp
+    exponent; s = 0 for an all-zero block), so that its largest magnitude
+    lies in [128, 256), rounded to E4M3 (ties to even), and scaled back.
+    Returns (the represented values, the exponents s per block)."""
+    X = np.asarray(X, dtype=np.float64)
+    Xt = X if axis == 1 else X.T
+    rows, cols = Xt.shape
+    nb = -(-cols // block)
+    out = np.zeros_like(Xt)
+    scales = np.zeros((rows, nb), dtype=np.int64)
+    for b in range(nb):
+        blk = Xt[:, b * block:(b + 1) * block]
+        m = np.abs(blk).max(axis=1)
+        e = np.frexp(m)[1]
+        s_ = np.where(m > 0, e - 8, 0)
+        scales[:, b] = s_
+        f = np.exp2(s_.astype(np.float64))[:, None]
+        out[:, b * block:(b + 1) * block] = precision.round_to(blk / f, "e4m3") * f
+    return (out if axis == 1 else out.T), (scales if axis == 1 else scales.T)
+
+
+def leaf_e4m3_b128(S, T):
+    """Leaf product with S quantized to E4M3 in 128-blocks along K per row
+    and T per column (quantize_e4m3_blocks), the product formed exactly."""
+    return classical(quantize_e4m3_blocks(S, axis=1)[0], quantize_e4m3_blocks(T, axis=0)[0])
+
+
 def leaf_bf16x3(S, T):
     """Leaf product with S = hi + lo, T = hi' + lo' split into bf16 parts and
     the three products hi hi' + hi lo' + lo hi' formed exactly (float64)."""

@@ -45,3 +45,43 @@ def test_split_bf16():
     assert np.array_equal(hi, P.round_to(hi, "bf16")) and np.array_equal(lo, P.round_to(lo, "bf16"))
     assert np.all(np.abs(x - hi - lo) <= 2.0**-16 * np.abs(x))
     assert np.all(np.abs(lo) <= 2.0**-8 * np.abs(x))
+
+
+# ---------------------------------------------------------------- E4M3 with 128-blocks
+
+def test_e4m3_blocks_exact_on_small_integers_and_scale_invariant():
+    from oracle import fmm as F
+    rng = np.random.default_rng(11)
+    X = rng.integers(-15, 16, size=(7, 300)).astype(np.float64)
+    q, s = F.quantize_e4m3_blocks(X, axis=1)
+    assert np.array_equal(q, X)  # every integer of magnitude <= 15 has 4 significant bits
+    # scaling a block by a power of two scales its representation exactly
+    Y = X.copy()
+    Y[:, 128:256] *= 2.0 ** 37
+    qy, sy = F.quantize_e4m3_blocks(Y, axis=1)
+    assert np.array_equal(qy[:, 128:256], q[:, 128:256] * 2.0 ** 37)
+    assert np.array_equal(sy[:, 1] - s[:, 1], np.full(7, 37)) or np.all(X[:, 128:256] == 0)
+    # columns (axis 0) are the transpose
+    qc, sc = F.quantize_e4m3_blocks(X.T, axis=0)
+    assert np.array_equal(qc, X.T) and np.array_equal(sc, s.T)
+
+
+def test_e4m3_blocks_error_bound():
+    # Relative error <= 2^-4 for entries within 2^-6 of... every entry whose
+    # scaled magnitude is a normal E4M3 number (>= 2^-6); smaller entries have
+    # absolute error <= 2^-10 times the block scale (half the subnormal step).
+    from oracle import fmm as F
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((5, 384)) * np.exp2(rng.integers(-30, 30, size=(5, 1)))
+    X[:, 7] *= 2.0 ** -20  # a tiny entry inside a block
+    q, s = F.quantize_e4m3_blocks(X, axis=1)
+    f = np.repeat(np.exp2(s.astype(np.float64)), 128, axis=1)[:, :384]
+    scaled = np.abs(X) / f
+    assert np.all(scaled < 256)
+    normal = scaled >= 2.0 ** -6
+    assert np.all(np.abs(q - X)[normal] <= 2.0 ** -4 * np.abs(X)[normal])
+    assert np.all((np.abs(q - X) / f)[~normal] <= 2.0 ** -10)
+    # each block's largest magnitude scales into [128, 256)
+    for b in range(3):
+        m = (np.abs(X[:, b * 128:(b + 1) * 128]) / f[:, b * 128:b * 128 + 1]).max(axis=1)
+        assert np.all((m >= 128) & (m < 256))
