@@ -271,6 +271,14 @@ static int64_t products_bytes(int64_t Tx, int64_t Ty, int64_t ptx, int64_t pty, 
 // when the plan has more than one leaf).
 static int64_t pass_bytes(const Plan* p, int64_t Tx, int64_t Kd, int64_t Ty, int64_t ptx, int64_t pk,
                           int64_t pty) {
+  if (p->leaf_format == FMM_LEAF_E4M3B128) {
+    // bytes of S_r and T_r, their per-block factors, the stored products
+    const int64_t R = p->leaves;
+    const int64_t ta = round_up(ceil_div(Tx, ptx), 128), tb = round_up(ceil_div(Ty, pty), 128);
+    const int64_t kp = round_up(ceil_div(Kd, pk), 128);
+    return round_up(R * ta * kp, 256) + round_up(R * (kp / 128) * ta * 4, 256) + round_up(R * tb * kp, 256) +
+           round_up(R * (kp / 128) * tb * 4, 256) + round_up(R * ta * tb * 4, 256);
+  }
   const int planes = p->leaf_format == FMM_LEAF_BF16X3 ? 2 : 1;
   int64_t between = 0;
   if (p->between && p->levels >= 2) {
@@ -399,9 +407,84 @@ static OutArgs out_args(const Plan* p, const PassGeom& g, const EpilogueArgs& c,
 // them and either adds W-weighted products into C in its epilogue or stores
 // them for the output pass.  FMM_ERR_WORKSPACE when the workspace is too
 // small.
+// A 2-D byte tensor map (rows x cols, ld), 128 x 128 boxes, 128-byte swizzle.
+static bool make_map_u8(CUtensorMap* m, const void* ptr, int64_t rows, int64_t cols, int64_t ld) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    t_last_error = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld};
+  const cuuint32_t box[2] = {128u, 128u};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    t_last_error = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
+// The pass schedule with E4M3 leaves: the E4M3 combination pass writes
+// S_r, T_r (K-major bytes) and their per-128-block factors; the FP8
+// multiply kernel stores M_r; the output pass forms C.
+static fmm_status run_pass_fp8(const Plan* p, const Source& x, const Source& y, const EpilogueArgs& c,
+                               const LeafDesc* leaves, int* status, void* ws, size_t ws_bytes, cudaStream_t st) {
+  PassGeom g = pass_geom(p, x, y, 128);
+  g.planes = 1;
+  g.tp_a = round_up(g.bt_a, 128);
+  g.tp_b = round_up(g.bt_b, 128);
+  g.kp = round_up(g.bk, 128);
+  const int64_t R = g.R, KB = g.kp / 128;
+  const int64_t ba = round_up(R * g.tp_a * g.kp, 256), fa = round_up(R * KB * g.tp_a * 4, 256);
+  const int64_t bb = round_up(R * g.tp_b * g.kp, 256), fbb = round_up(R * KB * g.tp_b * 4, 256);
+  const int64_t bm = round_up(R * g.tp_a * g.tp_b * 4, 256);
+  if (!ws || (uintptr_t)ws % 256 != 0 || (int64_t)ws_bytes < ba + fa + bb + fbb + bm) return FMM_ERR_WORKSPACE;
+  char* w = static_cast<char*>(ws);
+  char* wa = w;
+  float* sa = reinterpret_cast<float*>(w + ba);
+  char* wb = w + ba + fa;
+  float* sb = reinterpret_cast<float*>(w + ba + fa + bb);
+  float* mbuf = reinterpret_cast<float*>(w + ba + fa + bb + fbb);
+  CombineArgs ca = combine_args(p, g, x, 0, leaves, wa), cb = combine_args(p, g, y, 1, leaves, wb);
+  // both sides K-major: [leaf][t][k]
+  ca.p_rows = g.tp_a;
+  ca.p_cols = g.kp;
+  ca.scale_out = sa;
+  cb.p_rows = g.tp_b;
+  cb.p_cols = g.kp;
+  cb.scale_out = sb;
+  if (!cuda_ok(launch_combine_e4m3(cb, st), "E4M3 combination pass (B)") ||
+      !cuda_ok(launch_combine_e4m3(ca, st), "E4M3 combination pass (A)"))
+    return FMM_ERR_CUDA;
+  Fp8Args f;
+  std::memset(&f, 0, sizeof(f));
+  if (!make_map_u8(&f.map_a, wa, R * g.tp_a, g.kp, g.kp) || !make_map_u8(&f.map_b, wb, R * g.tp_b, g.kp, g.kp))
+    return FMM_ERR_CUDA;
+  f.fa = sa;
+  f.fb = sb;
+  f.mbuf = mbuf;
+  f.tp_a = g.tp_a;
+  f.tp_b = g.tp_b;
+  f.kp = g.kp;
+  f.num_leaves = R;
+  f.status = status;
+  f.timeout_ns = timeout_ns();
+  if (!cuda_ok(launch_fp8_gemm(f, st), "E4M3 multiply launch")) return FMM_ERR_CUDA;
+  return cuda_ok(launch_out_combine(out_args(p, g, c, leaves, mbuf), st), "output combination pass") ? FMM_OK
+                                                                                                     : FMM_ERR_CUDA;
+}
+
 static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, const EpilogueArgs& c,
                            const LeafDesc* leaves, int* status, void* ws, size_t ws_bytes, cudaStream_t st,
                            bool between) {
+  if (p->leaf_format == FMM_LEAF_E4M3B128) {
+    if (between) return FMM_ERR_UNSUPPORTED;
+    return run_pass_fp8(p, x, y, c, leaves, status, ws, ws_bytes, st);
+  }
   const PassGeom g = pass_geom(p, x, y, 0);
   const int64_t R = g.R;
   if (!ws || (uintptr_t)ws % 256 != 0 || (int64_t)ws_bytes < g.bytes_a + g.bytes_b) return FMM_ERR_WORKSPACE;
@@ -504,7 +587,8 @@ static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, floa
                     (p->schedule == FMM_SCHEDULE_AUTO && ws && (uintptr_t)ws % 256 == 0 &&
                      (int64_t)ws_bytes >= pass_bytes(p, M, K, N, p->pm, p->pk, p->pn));
   const bool between = allow_between && p->between && p->levels >= 2 && p->level1;
-  if (between && !pass) return p->schedule == FMM_SCHEDULE_LOAD_STAGE ? FMM_ERR_UNSUPPORTED : FMM_ERR_WORKSPACE;
+  const bool needs_pass = between || p->leaf_format == FMM_LEAF_E4M3B128;
+  if (needs_pass && !pass) return p->schedule == FMM_SCHEDULE_LOAD_STAGE ? FMM_ERR_UNSUPPORTED : FMM_ERR_WORKSPACE;
   if (pass) return run_pass(p, x, y, c, leaves, status, ws, ws_bytes, st, between);
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
@@ -660,7 +744,7 @@ static fmm_status batch_check(const fmm_problem* probs, int count, int dt, const
     if (fmt >= 0 && p->leaf_format != fmt) return FMM_ERR_ARG;
     fmt = p->leaf_format;
     if (dt == FMM_DT_F16 && fmt == FMM_LEAF_BF16X3) return FMM_ERR_DTYPE;
-    if (p->between && p->levels >= 2) return FMM_ERR_UNSUPPORTED;
+    if ((p->between && p->levels >= 2) || p->leaf_format == FMM_LEAF_E4M3B128) return FMM_ERR_UNSUPPORTED;
     if (p->pm * p->pn > kMaxOutBlocks || p->pm * p->pk > 64 || p->pk * p->pn > 64) return FMM_ERR_UNSUPPORTED;
     if (ceil_div(q.M, p->pm) >= (1ll << 30) || ceil_div(q.N, p->pn) >= (1ll << 30) ||
         ceil_div(q.K, p->pk) >= (1ll << 30))

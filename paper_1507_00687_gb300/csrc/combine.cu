@@ -23,6 +23,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include "../../include/fmm.h"
@@ -587,6 +588,114 @@ __global__ void between_finalize_kernel(const int* cexp, const int* rexp, int* d
 }
 
 }  // namespace
+
+// E4M3 combination pass: one CTA covers 16 t x 128 k (one scale block) of
+// every leaf block; the input block tiles are staged as [t][k] (k
+// contiguous, stride kF8Stride) whatever the source's layout; warp w forms
+// row t0 + w of each leaf's sum, 4 consecutive k per lane, reduces the
+// block's max |sum| across the warp, picks s = e(max) - 8 (0 for a zero
+// block), rounds sum 2^-s to E4M3 (ties to even) and writes the 128 bytes
+// of its row plus the factor 2^s.
+constexpr int kF8TT = 16;
+constexpr int kF8Stride = 132;
+
+template <int DT>
+__global__ void __launch_bounds__(512) combine_e4m3_kernel(const CombineArgs a) {
+  extern __shared__ float f8tile[];  // [block][kF8TT][kF8Stride], then the term list
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t t0 = (int64_t)blockIdx.y * kF8TT, k0 = (int64_t)blockIdx.x * 128;
+  const int n_rb = (int)a.n_rb, n_cb = (int)a.n_cb, nb = n_rb * n_cb;
+  const int R = (int)a.num_leaves, nnz = (int)a.t_nnz;
+  int* toff = reinterpret_cast<int*>(f8tile + nb * kF8TT * kF8Stride);
+  float* tcoef = reinterpret_cast<float*>(toff + nnz);
+  int* tstart = reinterpret_cast<int*>(tcoef + nnz);
+  for (int i = tid; i < nnz; i += 512) {
+    const int32_t blk = __ldg(a.t_blk + i);
+    const int bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
+    toff[i] = (a.t_rows ? bt * n_cb + bk : bk * n_cb + bt) * kF8TT * kF8Stride;
+    tcoef[i] = __ldg(a.t_coef + i);
+  }
+  for (int i = tid; i <= R; i += 512) tstart[i] = __ldg(a.t_start + i);
+  // staging: position (t, k) of block (rb, cb) -> memory (t, k) (KC) or (k, t)
+  for (int rb = 0; rb < n_rb; ++rb) {
+    for (int cb = 0; cb < n_cb; ++cb) {
+      float* tile = f8tile + (rb * n_cb + cb) * kF8TT * kF8Stride;
+      const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows), nc = min(a.b_cols, a.cols - cb * a.b_cols);
+      for (int i = tid; i < kF8TT * 128; i += 512) {
+        int t, k;
+        if (a.t_rows) { t = i >> 7; k = i & 127; } else { k = i >> 4; t = i & 15; }
+        const int64_t lt = t0 + t, lk = k0 + k;
+        const int64_t lr = a.t_rows ? lt : lk, lc = a.t_rows ? lk : lt;  // block-local memory row / column
+        float x = 0.f;
+        if (lr < nr && lc < nc) {
+          const int64_t gr = rb * a.b_rows + lr, gc = cb * a.b_cols + lc;
+          const float v = load_elem<DT>(a.src, gr * a.ld + gc);
+          x = scale_pow2(v, (a.re ? a.rs * __ldg(a.re + gr) : 0) + (a.ce ? a.cs * __ldg(a.ce + gc) : 0));
+        }
+        tile[t * kF8Stride + k] = x;
+      }
+    }
+  }
+  __syncthreads();
+  unsigned char* out = static_cast<unsigned char*>(a.out);
+  const int64_t t = t0 + warp;
+  const int64_t kb = k0 / 128, nkb = a.p_cols / 128;
+  int tt = 0;
+  for (int r = 0; r < R; ++r) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int t1 = tstart[r + 1];
+    for (; tt < t1; ++tt) {
+      const float coef = tcoef[tt];
+      const float4 v = *reinterpret_cast<const float4*>(f8tile + toff[tt] + warp * kF8Stride + 4 * lane);
+      acc[0] = fmaf(coef, v.x, acc[0]);
+      acc[1] = fmaf(coef, v.y, acc[1]);
+      acc[2] = fmaf(coef, v.z, acc[2]);
+      acc[3] = fmaf(coef, v.w, acc[3]);
+    }
+    float m = fmaxf(fmaxf(fabsf(acc[0]), fabsf(acc[1])), fmaxf(fabsf(acc[2]), fabsf(acc[3])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bool nf = false;
+    const int e = fexp_f32(__float_as_uint(m), &nf);
+    const int sc = m > 0.f ? e - 8 : 0;
+    uint32_t packed = 0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float2 pr = make_float2(scale_pow2(acc[2 * j], -sc), scale_pow2(acc[2 * j + 1], -sc));
+      const uint32_t q = (uint32_t)__nv_cvt_float2_to_fp8x2(pr, __NV_SATFINITE, __NV_E4M3);
+      packed |= q << (16 * j);
+    }
+    *reinterpret_cast<uint32_t*>(out + ((int64_t)r * a.p_rows + t) * a.p_cols + k0 + 4 * lane) = packed;
+    if (lane == 0) a.scale_out[((int64_t)r * nkb + kb) * a.p_rows + t] = exp2i(sc);
+  }
+}
+
+cudaError_t launch_combine_e4m3(const CombineArgs& a, cudaStream_t st) {
+  if (a.p_rows % kF8TT != 0 || a.p_cols % 128 != 0 || a.p_rows / kF8TT > 65535) return cudaErrorInvalidValue;
+  const int64_t nb = a.n_rb * a.n_cb;
+  const size_t smem = (size_t)nb * kF8TT * kF8Stride * 4 + (size_t)a.t_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
+  if (smem > kStagedSmemMax) return cudaErrorNotSupported;
+  if (a.num_leaves == 0 || a.p_rows == 0 || a.p_cols == 0) return cudaSuccess;
+  static bool attr_done[64][3] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  const dim3 grid((unsigned)(a.p_cols / 128), (unsigned)(a.p_rows / kF8TT));
+  KernelTimer timer("combine", st);
+  auto go = [&](auto kern, int idx) {
+    if (!attr_done[dev][idx]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedSmemMax);
+      attr_done[dev][idx] = true;
+    }
+    kern<<<grid, 512, smem, st>>>(a);
+  };
+  switch (a.dtype) {
+    case kF32: go(combine_e4m3_kernel<kF32>, 0); break;
+    case kBF16: go(combine_e4m3_kernel<kBF16>, 1); break;
+    default: go(combine_e4m3_kernel<kF16>, 2); break;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_node_exp(const CombineArgs& a, int* out, int64_t k1, cudaStream_t st) {
   const int64_t nb = a.n_rb * a.n_cb;

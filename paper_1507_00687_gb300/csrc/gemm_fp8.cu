@@ -1,0 +1,252 @@
+// Leaf products in E4M3 with power-of-two scales per 128-block along K (the
+// leaf format FMM_LEAF_E4M3B128):
+//   M_r[i, j] = sum over k blocks kb of 2^(sa[i, kb] + sb[kb, j]) (S8 T8)_kb[i, j]
+// with S8, T8 the E4M3 operands the combination pass wrote.  A block's
+// scales differ per row and column, so each 128-wide K block is one pipeline
+// stage multiplied into its own TMEM block accumulator; the epilogue warps
+// fold it into FP32 running sums (running = fma(block, 2^sa 2^sb, running),
+// blocks in order) and store the finished tile of M_r for the output pass.
+//
+//   warps 0-7  epilogue: warps w and w + 4 share TMEM lanes 32 (w mod 4) ..
+//              + 31 (one tile row per thread) and take 64 columns each
+//   warp 8     lane 0: TMEM allocator and tcgen05.mma issuer (kind::f8f6f4,
+//              four K = 32 steps per block)
+//   warp 9     lane 0: TMA issuer: per stage the A and B tiles (128 x 128
+//              bytes, K-major, 128-byte swizzle) and the block's 128 column
+//              factors 2^sb (one bulk copy)
+//
+// One CTA per SM, persistent over (leaf, tile) units.  A stage is released
+// when both the MMAs that read its tiles and the epilogue warps that read
+// its column factors are done.  Every wait is bounded; on expiry the kernel
+// sets the timeout bit of the status word, stops, waits for its own copies
+// and MMAs, frees its TMEM and returns.
+#include <algorithm>
+#include <cstring>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/fmm.h"
+#include "device.cuh"
+#include "gemm_common.cuh"
+#include "kernels.h"
+
+namespace fmm {
+namespace fp8 {
+
+using gemm::mbar_arrive_expect_tx;
+using gemm::tma_load_2d;
+
+constexpr int BM = 128, BN = 128, BK = 128;  // BK in bytes = elements
+constexpr int kEpiWarps = 8, kMmaWarp = 8, kTmaWarp = 9, kThreads = 10 * 32;
+constexpr int kTile = 128 * 128;
+constexpr int kScaleBytes = 128 * 4;
+constexpr int kStage = 2 * kTile + 1024;  // tiles + column factors, 1024-aligned
+constexpr int kStages = 6;
+constexpr int kTmemCols = 2 * BN;
+constexpr int kSmem = kStages * kStage + 256 + 1024;
+
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                      uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Instruction descriptor, kind::f8f6f4: fp32 accumulator, A and B E4M3
+// (format code 0), both K-major, M x N.
+constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) fp8_fmm_kernel(const __grid_constant__ Fp8Args args) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStage);
+  uint64_t* empty = full + kStages;
+  uint64_t* tfull = empty + kStages;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1 + kEpiWarps * 32);  // the MMA commit and every epilogue thread
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kEpiWarps * 32);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == kMmaWarp) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int64_t ntn = args.tp_b / BN, ntiles = (args.tp_a / BM) * ntn;
+  const int64_t total = ntiles * args.num_leaves;
+  const int64_t KB = args.kp / BK;
+
+  if (warp == kTmaWarp) {
+    if (lane == 0) {
+      // ------------------------------------------------------ TMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      uint32_t armed = 0, armed_parity = 0;
+      for (int64_t u = blockIdx.x; u < total && ok; u += gridDim.x) {
+        const int64_t leaf = u / ntiles, tile = u % ntiles, tm = tile / ntn, tn = tile % ntn;
+        for (int64_t kb = 0; kb < KB && ok; ++kb) {
+          if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
+          uint8_t* st = smem + stage * kStage;
+          mbar_arrive_expect_tx(&full[stage], (uint32_t)(2 * kTile + kScaleBytes));
+          tma_load_2d(st, &args.map_a, (int32_t)(kb * BK), (int32_t)(leaf * args.tp_a + tm * BM), &full[stage]);
+          tma_load_2d(st + kTile, &args.map_b, (int32_t)(kb * BK), (int32_t)(leaf * args.tp_b + tn * BN), &full[stage]);
+          bulk_load(st + 2 * kTile, args.fb + (leaf * KB + kb) * args.tp_b + tn * BN, kScaleBytes, &full[stage]);
+          armed |= 1u << stage;
+          armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) *abort_flag = 1;
+      for (int s = 0; s < kStages; ++s) {
+        if (armed & (1u << s)) {
+          const uint64_t t0 = globaltimer_ns();
+          while (!mbar_try_wait(&full[s], (armed_parity >> s) & 1u) && globaltimer_ns() - t0 < 1000000000ull) {
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ------------------------------------------------------ MMA issuer
+      constexpr uint32_t idesc = idesc_e4m3(BM, BN);
+      int stage = 0;
+      uint32_t phase = 0, acc_iter = 0;
+      bool ok = true;
+      const uint32_t sbase = smem_u32(smem);
+      for (int64_t u = blockIdx.x; u < total && ok; u += gridDim.x) {
+        for (int64_t kb = 0; kb < KB && ok; ++kb) {
+          const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
+          if (!mbar_wait_bounded(&tempty[buf], aph ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
+          if (!mbar_wait_bounded(&full[stage], phase, abort_flag, args.timeout_ns)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = sbase + stage * kStage, b0 = a0 + kTile;
+#pragma unroll
+          for (int k32 = 0; k32 < BK / 32; ++k32)
+            mma_f8(tmem_base + buf * BN, smem_desc_sw128(a0 + k32 * 32), smem_desc_sw128(b0 + k32 * 32), idesc,
+                   k32 > 0 ? 1u : 0u);
+          mma_commit(&empty[stage]);
+          mma_commit(&tfull[buf]);
+          ++acc_iter;
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) *abort_flag = 1;
+      mma_commit(drain);
+      const uint64_t t0 = globaltimer_ns();
+      while (!mbar_try_wait(drain, 0) && globaltimer_ns() - t0 < 1000000000ull) {
+      }
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------------- epilogue
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
+    int stage = 0;
+    uint32_t phase = 0, acc_iter = 0;
+    bool ok = true;
+    for (int64_t u = blockIdx.x; u < total && ok; u += gridDim.x) {
+      const int64_t leaf = u / ntiles, tile = u % ntiles, tm = tile / ntn, tn = tile % ntn;
+      const int64_t ml = tm * BM + row;
+      float run[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) run[j] = 0.f;
+      for (int64_t kb = 0; kb < KB; ++kb) {
+        const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
+        const float fa = __ldg(args.fa + (leaf * KB + kb) * args.tp_a + ml);
+        // warp-uniform outcome: the TMEM loads below are .sync.aligned
+        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&tfull[buf], aph, abort_flag, args.timeout_ns));
+        if (!ok) break;
+        tc_fence_after();
+        const float* fb = reinterpret_cast<const float*>(smem + stage * kStage + 2 * kTile) + half * 64;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          uint32_t r[32];
+          tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + half * 64 + c * 32, r);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 f = *reinterpret_cast<const float4*>(fb + c * 32 + 4 * q);
+            const int j = c * 32 + 4 * q;
+            run[j] = fmaf(__uint_as_float(r[4 * q]), fa * f.x, run[j]);
+            run[j + 1] = fmaf(__uint_as_float(r[4 * q + 1]), fa * f.y, run[j + 1]);
+            run[j + 2] = fmaf(__uint_as_float(r[4 * q + 2]), fa * f.z, run[j + 2]);
+            run[j + 3] = fmaf(__uint_as_float(r[4 * q + 3]), fa * f.w, run[j + 3]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[buf]);
+        mbar_arrive(&empty[stage]);  // this block's column factors are consumed
+        ++acc_iter;
+        if (++stage == kStages) { stage = 0; phase ^= 1u; }
+      }
+      if (!ok) break;
+      float* dst = args.mbuf + (leaf * args.tp_a + ml) * args.tp_b + tn * BN + half * 64;
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(run[4 * q], run[4 * q + 1], run[4 * q + 2], run[4 * q + 3]);
+    }
+    if (!ok) *abort_flag = 1;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(args.status, kStatusTimeout);
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
+}  // namespace fp8
+
+cudaError_t launch_fp8_gemm(const Fp8Args& a, cudaStream_t st) {
+  if (a.tp_a % fp8::BM != 0 || a.tp_b % fp8::BN != 0 || a.kp % fp8::BK != 0) return cudaErrorInvalidValue;
+  const int64_t units = (a.tp_a / fp8::BM) * (a.tp_b / fp8::BN) * a.num_leaves;
+  if (units == 0 || a.kp == 0) return cudaSuccess;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(fp8::fp8_fmm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fp8::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const int64_t grid = std::min<int64_t>(units, device_sm_count());
+  KernelTimer timer("multiply", st);
+  fp8::fp8_fmm_kernel<<<(unsigned)grid, fp8::kThreads, fp8::kSmem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace fmm

@@ -133,7 +133,32 @@ struct CombineArgs {
   int64_t leaves_per_node;  // leaves below one level-1 product
   int64_t kb_inner;         // leaf k blocks per level-1 k block
   int64_t bk;               // leaf block k extent
+  // E4M3 leaves (fmt FMM_LEAF_E4M3B128): out holds bytes, K-major for both
+  // sides ([leaf][t][k], p_rows = padded t, p_cols = padded k, multiples of
+  // 128), and scale_out[(leaf * p_cols / 128 + kb) * p_rows + t] = 2^s of
+  // each row's 128-block.
+  float* scale_out;
 };
+
+// E4M3 combination pass (see CombineArgs::scale_out); a.p_rows / p_cols are
+// the padded t / k extents whatever the source's layout.
+cudaError_t launch_combine_e4m3(const CombineArgs& a, cudaStream_t st);
+
+// Multiply kernel for E4M3 leaves: stored products only, both operands
+// K-major bytes ([leaf][t][k], tensor maps with 128 x 128 byte boxes), one
+// 128-wide K block per pipeline stage accumulated into a TMEM block
+// accumulator and folded into FP32 running sums with 2^(sa + sb).
+struct Fp8Args {
+  alignas(64) CUtensorMap map_a;
+  alignas(64) CUtensorMap map_b;
+  const float* fa;  // [leaf][kb][tp_a] factors 2^sa
+  const float* fb;  // [leaf][kb][tp_b] factors 2^sb
+  float* mbuf;      // [leaf][tp_a][tp_b] fp32
+  int64_t tp_a, tp_b, kp, num_leaves;
+  int* status;
+  uint64_t timeout_ns;
+};
+cudaError_t launch_fp8_gemm(const Fp8Args& a, cudaStream_t st);
 
 // Node-exponent pass of the scaling between recursive steps: for each
 // level-1 product r (the terms of `a` are the level-1 plan's), the FP32

@@ -143,7 +143,8 @@ void expand(const std::vector<const std::vector<double>*>& X, const std::vector<
 }  // namespace
 
 fmm_status build_plan(const std::vector<CanonRule>& rules_in, int leaf_format, Plan** out) {
-  if (leaf_format != FMM_LEAF_BF16 && leaf_format != FMM_LEAF_F16 && leaf_format != FMM_LEAF_BF16X3)
+  if (leaf_format != FMM_LEAF_BF16 && leaf_format != FMM_LEAF_F16 && leaf_format != FMM_LEAF_BF16X3 &&
+      leaf_format != FMM_LEAF_E4M3B128)
     return FMM_ERR_ARG;
   Plan* p = new Plan();
   p->levels = (int)rules_in.size();

@@ -8,7 +8,7 @@ with G the growth quantity of the proof of Theorem 4.1 evaluated entrywise
 (sum_r |W| |S_r| |T_r| with absolute coefficients, unscaled by 2^(eA+eB)),
 u_leaf the relative error of one leaf product from rounding S and T
 (bf16: 2^-7 + 2^-16, fp16: 2^-10 + 2^-22, bf16 hi+lo with three products:
-3 * 2^-16), K_leaf FP32 accumulations in the tensor core, and at most
+3 * 2^-16, E4M3 with 128-block scales: 2^-3 + 2^-8), K_leaf FP32 accumulations in the tensor core, and at most
 t_max FP32 roundings each for forming S, forming T and adding into C
 (counted with the conservative 2^-23 per operation).
 """
@@ -20,7 +20,8 @@ from oracle import fmm as OF
 from oracle import rules as OR
 from oracle import scaling as OS
 
-U_LEAF = {"bf16": 2.0**-7 + 2.0**-16, "fp16": 2.0**-10 + 2.0**-22, "bf16x3": 3 * 2.0**-16}
+U_LEAF = {"bf16": 2.0**-7 + 2.0**-16, "fp16": 2.0**-10 + 2.0**-22, "bf16x3": 3 * 2.0**-16,
+          "e4m3b128": 2.0**-3 + 2.0**-8}
 
 ORACLE_RULES = {"strassen": OR.strassen, "winograd": OR.winograd, "fast323": OR.fast323,
                 "classical121": lambda: OR.classical(1, 2, 1), "classical211": lambda: OR.classical(2, 1, 1),
