@@ -107,6 +107,30 @@ typedef struct fmm_plan_s* fmm_plan_t;
  */
 fmm_status fmm_plan(fmm_plan_t* out, int levels, const fmm_rule* rules, int leaf_format);
 
+/*
+ * Build a non-uniform plan (Sec. 3.4): every node of the recursion tree
+ * takes its own rule.  rules[0..nrules-1] is a table of distinct rules
+ * (each checked against the Brent equations, FMM_ERR_NOT_MATMUL on
+ * failure); node_rule[0..nnodes-1] gives each internal node's index into
+ * that table, level by level from the root, and within a level in the order
+ * of the parents and then of the parent's product index r = 0..R-1.  So
+ * node_rule[0] is the root, the next R_root entries its children, and so on
+ * down to level `levels`; below that every product is classical.  All nodes
+ * of one level must share (m0, k0, n0), so that every root-to-leaf path
+ * partitions A, B and C alike; their ranks R may differ.  FMM_ERR_ARG when
+ * nnodes does not match the tree the ranks define, an index is out of range
+ * or the dimensions of a level differ.  Leaves are flattened in depth-first
+ * order (product r = 0..R-1 at every node), which for a tree with one rule
+ * per level is the order fmm_plan uses.  fmm_plan_info then reports
+ * max_k delta_k in place of sum Q and max_k xi_k in place of prod E (the
+ * componentwise quantities of Sec. 4.5; they reduce to sum Q and prod E for
+ * uniform plans), so fmm_plan_bound gives the bound of Sec. 4.5.  Scaling
+ * between recursive steps needs every level's ranks equal (else
+ * FMM_ERR_UNSUPPORTED).  The caller keeps ownership of rules and node_rule.
+ */
+fmm_status fmm_plan_tree(fmm_plan_t* out, int nrules, const fmm_rule* rules, int levels, int64_t nnodes,
+                         const int32_t* node_rule, int leaf_format);
+
 fmm_status fmm_plan_destroy(fmm_plan_t plan);
 
 /*

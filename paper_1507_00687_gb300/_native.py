@@ -29,7 +29,7 @@ EXPORTS = [
     "fmm_sync_status", "fmm_status_string", "fmm_version", "fmm_last_error", "fmm_multiply_noalloc",
     "fmm_plan_set_schedule", "fmm_kernel_timing", "fmm_kernel_timing_read",
     "fmm_batch_workspace_size", "fmm_batch_create", "fmm_batch_run", "fmm_batch_destroy",
-    "fmm_plan_set_between_scaling",
+    "fmm_plan_set_between_scaling", "fmm_plan_tree",
 ]
 
 # Bytes of the library's static scratch array (FMM_NOALLOC_SCRATCH_BYTES).
@@ -69,6 +69,8 @@ def lib():
     i64, i32p, vp, st = C.c_int64, C.POINTER(C.c_int32), C.c_void_p, C.c_int
     L.fmm_plan.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(FmmRule), C.c_int]
     L.fmm_plan_destroy.argtypes = [vp]
+    L.fmm_plan_tree.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(FmmRule), C.c_int, i64,
+                                C.POINTER(C.c_int32), C.c_int]
     L.fmm_plan_set_schedule.argtypes = [vp, C.c_int]
     L.fmm_plan_set_between_scaling.argtypes = [vp, C.c_int]
     L.fmm_kernel_timing.argtypes = [C.c_int]

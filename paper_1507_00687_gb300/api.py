@@ -3,6 +3,7 @@ every step of the computation runs in the library's CUDA kernels)."""
 from __future__ import annotations
 
 import ctypes as C
+from dataclasses import dataclass
 from typing import Optional, Sequence, Union
 
 import numpy as np
@@ -36,6 +37,14 @@ def _rowmajor(t: torch.Tensor, name: str) -> int:
     return max(t.stride(0), t.shape[1], 1)
 
 
+@dataclass
+class TreeNode:
+    """One node of a non-uniform plan: ``rule`` (a rule or its name) applied
+    here; ``children[r]`` the node computing product r, None at the leaves."""
+    rule: Union[str, BaseRule]
+    children: list
+
+
 class Plan:
     """A flattened uniform non-stationary plan (fmm_plan): ``rules[l]`` at
     level l+1, classical leaves, leaf products in ``leaf`` format.
@@ -46,12 +55,29 @@ class Plan:
     recursive steps (fmm_plan_set_between_scaling)."""
 
     def __init__(self, rules: Sequence[Union[str, BaseRule]], leaf: str = "bf16x3", schedule: str = "auto",
-                 between: bool = False):
+                 between: bool = False, node_rule: Optional[Sequence[int]] = None, levels: int = 0):
         self.rules = [get_rule(r) if isinstance(r, str) else r for r in rules]
         self.leaf = leaf
         self._keep = []
-        arr = (N.FmmRule * max(1, len(self.rules)))()
-        for i, r in enumerate(self.rules):
+        arr = self._rule_array(self.rules)
+        h = C.c_void_p()
+        if node_rule is None:
+            N.check(N.lib().fmm_plan(C.byref(h), len(self.rules), arr, LEAF[leaf]), "fmm_plan")
+        else:
+            nodes = (C.c_int32 * max(1, len(node_rule)))(*node_rule)
+            N.check(N.lib().fmm_plan_tree(C.byref(h), len(self.rules), arr, levels, len(node_rule), nodes,
+                                          LEAF[leaf]), "fmm_plan_tree")
+        self.node_rule = None if node_rule is None else list(node_rule)
+        self._h = h
+        self.schedule = schedule
+        N.check(N.lib().fmm_plan_set_schedule(h, SCHEDULE[schedule]), "fmm_plan_set_schedule")
+        self.between = between
+        if between:
+            N.check(N.lib().fmm_plan_set_between_scaling(h, 1), "fmm_plan_set_between_scaling")
+
+    def _rule_array(self, rules):
+        arr = (N.FmmRule * max(1, len(rules)))()
+        for i, r in enumerate(rules):
             U = np.ascontiguousarray(r.U, np.float64)
             V = np.ascontiguousarray(r.V, np.float64)
             W = np.ascontiguousarray(r.W, np.float64)
@@ -59,14 +85,29 @@ class Plan:
             dp = C.POINTER(C.c_double)
             arr[i] = N.FmmRule(r.m0, r.k0, r.n0, r.r, U.ctypes.data_as(dp), V.ctypes.data_as(dp),
                                W.ctypes.data_as(dp), r.order_a, r.order_b, r.order_c)
-        h = C.c_void_p()
-        N.check(N.lib().fmm_plan(C.byref(h), len(self.rules), arr, LEAF[leaf]), "fmm_plan")
-        self._h = h
-        self.schedule = schedule
-        N.check(N.lib().fmm_plan_set_schedule(h, SCHEDULE[schedule]), "fmm_plan_set_schedule")
-        self.between = between
-        if between:
-            N.check(N.lib().fmm_plan_set_between_scaling(h, 1), "fmm_plan_set_between_scaling")
+        return arr
+
+    @classmethod
+    def tree(cls, root: "TreeNode", leaf: str = "bf16x3", schedule: str = "auto", between: bool = False):
+        """A non-uniform plan (fmm_plan_tree) from a recursion tree whose
+        nodes are ``TreeNode(rule, children)`` (children[r] computes product
+        r one level down; None below the last level)."""
+        table, index, node_rule = [], {}, []
+        level, levels = [root], 0
+        while level and level[0] is not None:
+            levels += 1
+            nxt = []
+            for node in level:
+                key = id(node.rule)
+                if key not in index:
+                    index[key] = len(table)
+                    table.append(get_rule(node.rule) if isinstance(node.rule, str) else node.rule)
+                node_rule.append(index[key])
+                nxt.extend(node.children)
+            if any(c is None for c in nxt) and not all(c is None for c in nxt):
+                raise ValueError("every leaf of the tree must sit at the same depth")
+            level = nxt
+        return cls(table, leaf=leaf, schedule=schedule, between=between, node_rule=node_rule, levels=levels)
 
     @property
     def handle(self):

@@ -82,9 +82,10 @@ static fmm_status ensure_uploaded(const Plan* cp) {
   return FMM_OK;
 }
 
-static fmm_status make_plan(const std::vector<CanonRule>& rules, int leaf, Plan** out) {
+static fmm_status make_plan(const std::vector<CanonRule>& rules, int leaf, Plan** out,
+                            const std::vector<int>* node_rule = nullptr, int levels = 0) {
   Plan* p = nullptr;
-  fmm_status s = build_plan(rules, leaf, &p);
+  fmm_status s = node_rule ? build_tree_plan(rules, levels, *node_rule, leaf, &p) : build_plan(rules, leaf, &p);
   if (s != FMM_OK) return s;
   if (p->max_terms > kMaxTerms) {
     destroy_plan(p);
@@ -979,6 +980,24 @@ fmm_status fmm_plan(fmm_plan_t* out, int levels, const fmm_rule* rules, int leaf
   return FMM_OK;
 }
 
+fmm_status fmm_plan_tree(fmm_plan_t* out, int nrules, const fmm_rule* rules, int levels, int64_t nnodes,
+                         const int32_t* node_rule, int leaf_format) {
+  if (!out || nrules < 1 || !rules || levels < 1 || levels > 16 || nnodes < 1 || nnodes > (1 << 20) || !node_rule)
+    return FMM_ERR_ARG;
+  *out = nullptr;
+  std::vector<CanonRule> cr((size_t)nrules);
+  for (int i = 0; i < nrules; ++i) {
+    fmm_status s = canonicalize(rules[i], &cr[(size_t)i]);
+    if (s != FMM_OK) return s;
+  }
+  const std::vector<int> nr(node_rule, node_rule + nnodes);
+  Plan* p = nullptr;
+  fmm_status s = make_plan(cr, leaf_format, &p, &nr, levels);
+  if (s != FMM_OK) return s;
+  *out = reinterpret_cast<fmm_plan_t>(p);
+  return FMM_OK;
+}
+
 fmm_status fmm_plan_destroy(fmm_plan_t plan) {
   destroy_plan(reinterpret_cast<Plan*>(plan));
   return FMM_OK;
@@ -996,6 +1015,9 @@ fmm_status fmm_plan_set_schedule(fmm_plan_t plan, int schedule) {
 fmm_status fmm_plan_set_between_scaling(fmm_plan_t plan, int enable) {
   Plan* p = reinterpret_cast<Plan*>(plan);
   if (!p) return FMM_ERR_ARG;
+  // a level-1 product's leaves are contiguous and equally many only when
+  // every level's ranks agree
+  if (enable && !p->level_r_uniform) return FMM_ERR_UNSUPPORTED;
   if (enable && p->levels >= 2 && !p->level1) {
     fmm_status s = make_plan({p->rules[0]}, p->leaf_format, &p->level1);
     if (s != FMM_OK) return s;
@@ -1212,14 +1234,18 @@ fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc,
   {
     std::lock_guard<std::mutex> lock(mu);
     if (!p->grad_a) {
+      // a tree keeps its shape: node r of the gradient tree computes the
+      // same product index as node r of the plan (the symmetry permutes
+      // the operands of each product, not the products)
+      const bool tree = !p->node_rule.empty();
       std::vector<CanonRule> ga, gb;
-      for (const auto& r : p->rules) {
+      for (const auto& r : tree ? p->table : p->rules) {
         ga.push_back(rule_for_grad_a(r));
         gb.push_back(rule_for_grad_b(r));
       }
-      fmm_status s = make_plan(ga, p->leaf_format, &p->grad_a);
+      fmm_status s = make_plan(ga, p->leaf_format, &p->grad_a, tree ? &p->node_rule : nullptr, p->levels);
       if (s != FMM_OK) return s;
-      s = make_plan(gb, p->leaf_format, &p->grad_b);
+      s = make_plan(gb, p->leaf_format, &p->grad_b, tree ? &p->node_rule : nullptr, p->levels);
       if (s != FMM_OK) return s;
       p->grad_a->schedule = p->grad_b->schedule = p->schedule;
     }

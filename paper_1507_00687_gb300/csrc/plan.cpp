@@ -2,6 +2,7 @@
 // quantities (Sec. 4.1), flattening of L levels into R^L leaf descriptors
 // (Eq. 4.4), and the gradient rules obtained by the cyclic symmetry of the
 // matrix-multiplication tensor (Sec. 5.3, App. A-C).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <set>
@@ -95,6 +96,7 @@ void principal_quantities(CanonRule* c) {
     }
   }
   double Q = 0, E = 0;
+  c->gamma.assign(nC, 0.0);
   for (int k = 0; k < nC; ++k) {
     double gamma = 0, mx = 0, e = 0;
     for (int r = 0; r < R; ++r) {
@@ -108,7 +110,12 @@ void principal_quantities(CanonRule* c) {
     }
     Q = std::max(Q, gamma + mx);
     E = std::max(E, e);
+    c->gamma[k] = gamma;
   }
+  c->alpha = alpha;
+  c->beta = beta;
+  c->a = a;
+  c->b = b;
   c->Q = Q;
   c->E = E;
   c->nnz = nnz;
@@ -140,73 +147,31 @@ void expand(const std::vector<const std::vector<double>*>& X, const std::vector<
   }
 }
 
-}  // namespace
 
-fmm_status build_plan(const std::vector<CanonRule>& rules_in, int leaf_format, Plan** out) {
-  if (leaf_format != FMM_LEAF_BF16 && leaf_format != FMM_LEAF_F16 && leaf_format != FMM_LEAF_BF16X3 &&
-      leaf_format != FMM_LEAF_E4M3B128)
-    return FMM_ERR_ARG;
-  Plan* p = new Plan();
-  p->levels = (int)rules_in.size();
-  p->leaf_format = leaf_format;
-  p->rules = rules_in;
-  for (auto& r : p->rules) {
-    if (brent_violations(r) != 0) {
-      delete p;
-      return FMM_ERR_NOT_MATMUL;
-    }
-    principal_quantities(&r);
-    p->pm *= r.m0;
-    p->pk *= r.k0;
-    p->pn *= r.n0;
-    p->leaves *= r.r;
-    p->q_sum += r.Q;
-    p->e_prod *= r.E;
-    if (p->pm > 32768 || p->pk > 32768 || p->pn > 32768 || p->leaves > 1000000) {
-      delete p;
-      return FMM_ERR_UNSUPPORTED;
-    }
+// Append one leaf's flattened terms to p->host; leaves arrive in order.
+// touched: the C blocks some earlier leaf adds into.
+void add_leaf(Plan* p, int64_t leaf, const std::vector<Term>& ta, const std::vector<Term>& tb,
+              const std::vector<Term>& tc, std::set<int32_t>* touched) {
+  p->max_terms = std::max(p->max_terms, (int)std::max(ta.size(), std::max(tb.size(), tc.size())));
+  p->nnz += (int64_t)(ta.size() + tb.size() + tc.size());
+  LeafDesc& d = p->host[(size_t)leaf];
+  std::memset(&d, 0, sizeof(d));
+  if ((int)ta.size() > kMaxTerms || (int)tb.size() > kMaxTerms || (int)tc.size() > kMaxTerms) return;
+  d.na = (int)ta.size();
+  d.nb = (int)tb.size();
+  d.nc = (int)tc.size();
+  for (int t = 0; t < d.na; ++t) { d.a_blk[t] = (ta[t].row << 16) | ta[t].col; d.a_coef[t] = (float)ta[t].coef; }
+  for (int t = 0; t < d.nb; ++t) { d.b_blk[t] = (tb[t].row << 16) | tb[t].col; d.b_coef[t] = (float)tb[t].coef; }
+  for (int t = 0; t < d.nc; ++t) {
+    int32_t blk = (tc[t].row << 16) | tc[t].col;
+    d.c_blk[t] = blk;
+    d.c_coef[t] = (float)tc[t].coef;
+    d.c_first[t] = touched->insert(blk).second ? 1 : 0;
   }
-  const int L = p->levels;
-  std::vector<const std::vector<double>*> Us, Vs, Ws;
-  std::vector<int> m0s, k0s, n0s, Rs;
-  for (auto& r : p->rules) {
-    Us.push_back(&r.U); Vs.push_back(&r.V); Ws.push_back(&r.W);
-    m0s.push_back(r.m0); k0s.push_back(r.k0); n0s.push_back(r.n0); Rs.push_back(r.r);
-  }
-  p->host.resize((size_t)p->leaves);
-  std::set<int32_t> touched;
-  std::vector<int> rl(L, 0);
-  std::vector<Term> ta, tb, tc;
-  for (int64_t leaf = 0; leaf < p->leaves; ++leaf) {
-    // leaf = sum_l r_l prod_{l' > l} R_{l'}  (level 1 slowest)
-    int64_t rem = leaf;
-    for (int l = L - 1; l >= 0; --l) {
-      rl[l] = (int)(rem % Rs[l]);
-      rem /= Rs[l];
-    }
-    ta.clear(); tb.clear(); tc.clear();
-    expand(Us, m0s, k0s, Rs, rl, 0, 0, 0, 1.0, &ta);
-    expand(Vs, k0s, n0s, Rs, rl, 0, 0, 0, 1.0, &tb);
-    expand(Ws, m0s, n0s, Rs, rl, 0, 0, 0, 1.0, &tc);
-    p->max_terms = std::max(p->max_terms, (int)std::max(ta.size(), std::max(tb.size(), tc.size())));
-    p->nnz += (int64_t)(ta.size() + tb.size() + tc.size());
-    LeafDesc& d = p->host[(size_t)leaf];
-    std::memset(&d, 0, sizeof(d));
-    if ((int)ta.size() > kMaxTerms || (int)tb.size() > kMaxTerms || (int)tc.size() > kMaxTerms) continue;
-    d.na = (int)ta.size();
-    d.nb = (int)tb.size();
-    d.nc = (int)tc.size();
-    for (int t = 0; t < d.na; ++t) { d.a_blk[t] = (ta[t].row << 16) | ta[t].col; d.a_coef[t] = (float)ta[t].coef; }
-    for (int t = 0; t < d.nb; ++t) { d.b_blk[t] = (tb[t].row << 16) | tb[t].col; d.b_coef[t] = (float)tb[t].coef; }
-    for (int t = 0; t < d.nc; ++t) {
-      int32_t blk = (tc[t].row << 16) | tc[t].col;
-      d.c_blk[t] = blk;
-      d.c_coef[t] = (float)tc[t].coef;
-      d.c_first[t] = touched.insert(blk).second ? 1 : 0;
-    }
-  }
-  // compact per-side term lists
+}
+
+// The compact per-side term lists from p->host.
+void build_lists(Plan* p) {
   for (int side = 0; side < 3; ++side) {
     int64_t nnz = 0;
     for (const LeafDesc& d : p->host) nnz += side == 0 ? d.na : side == 1 ? d.nb : d.nc;
@@ -230,6 +195,232 @@ fmm_status build_plan(const std::vector<CanonRule>& rules_in, int leaf_format, P
     }
     start[p->leaves] = (int32_t)at;
   }
+}
+
+bool valid_leaf_format(int leaf_format) {
+  return leaf_format == FMM_LEAF_BF16 || leaf_format == FMM_LEAF_F16 || leaf_format == FMM_LEAF_BF16X3 ||
+         leaf_format == FMM_LEAF_E4M3B128;
+}
+
+// The leaves of one root-to-leaf path: X[l] is the path's U (V, W) at
+// level l+1, R[l] that rule's rank, rl[l] the product index taken there.
+struct Path {
+  std::vector<const std::vector<double>*> U, V, W;
+  std::vector<int> m0, k0, n0, R, rl;
+};
+
+void expand_path(const Path& q, std::vector<Term>* ta, std::vector<Term>* tb, std::vector<Term>* tc) {
+  ta->clear(); tb->clear(); tc->clear();
+  expand(q.U, q.m0, q.k0, q.R, q.rl, 0, 0, 0, 1.0, ta);
+  expand(q.V, q.k0, q.n0, q.R, q.rl, 0, 0, 0, 1.0, tb);
+  expand(q.W, q.m0, q.n0, q.R, q.rl, 0, 0, 0, 1.0, tc);
+}
+
+// Node layout of a tree plan: level_start[l] is the index in node_rule of
+// level l's first node, first_child[i] the index of node i's first child.
+struct TreeIndex {
+  std::vector<int64_t> level_start, first_child;
+};
+
+// max_k delta_k over the C blocks below `node` (Sec. 4.5): at a node,
+// delta_k = gamma_{k_l} + max over r with W[k_l, r] != 0 of the child's
+// delta, with chi (the sum of alpha_r + beta_r along the path) at the leaves.
+// The max over k splits into the max over k_l of gamma plus the children's
+// maxima.
+double tree_delta_max(const Plan& p, const TreeIndex& t, int64_t node, int level, double chi) {
+  if (level == p.levels) return chi;
+  const CanonRule& c = p.table[(size_t)p.node_rule[(size_t)node]];
+  std::vector<double> sub((size_t)c.r);
+  for (int r = 0; r < c.r; ++r)
+    sub[(size_t)r] = tree_delta_max(p, t, t.first_child[(size_t)node] + r, level + 1, chi + c.alpha[r] + c.beta[r]);
+  double best = 0;
+  for (int k = 0; k < c.m0 * c.n0; ++k) {
+    double mx = -1;
+    for (int r = 0; r < c.r; ++r)
+      if (c.W[(size_t)k * c.r + r] != 0) mx = std::max(mx, sub[(size_t)r]);
+    if (mx >= 0) best = std::max(best, c.gamma[k] + mx);
+  }
+  return best;
+}
+
+// xi_k over the flattened C blocks below `node` (k_l slowest, Sec. 4.5):
+// xi_k = sum_r |W[k_l, r]| a_r b_r xi^{child r}_{k_{l+1}..}, 1 at the leaves.
+std::vector<double> tree_xi(const Plan& p, const TreeIndex& t, int64_t node, int level) {
+  if (level == p.levels) return {1.0};
+  const CanonRule& c = p.table[(size_t)p.node_rule[(size_t)node]];
+  std::vector<std::vector<double>> sub((size_t)c.r);
+  for (int r = 0; r < c.r; ++r) sub[(size_t)r] = tree_xi(p, t, t.first_child[(size_t)node] + r, level + 1);
+  const size_t n = sub[0].size();
+  std::vector<double> out((size_t)(c.m0 * c.n0) * n, 0.0);
+  for (int k = 0; k < c.m0 * c.n0; ++k)
+    for (int r = 0; r < c.r; ++r) {
+      const double w = std::fabs(c.W[(size_t)k * c.r + r]);
+      if (w == 0) continue;
+      for (size_t j = 0; j < n; ++j) out[(size_t)k * n + j] += w * c.a[r] * c.b[r] * sub[(size_t)r][j];
+    }
+  return out;
+}
+
+// Depth-first walk over the tree's leaves (product r = 0..R-1 at every
+// node, so leaves come in the order the uniform enumeration uses).
+void tree_leaves(Plan* p, const TreeIndex& t, int64_t node, int level, Path* q, int64_t* leaf,
+                 std::vector<Term>* ta, std::vector<Term>* tb, std::vector<Term>* tc, std::set<int32_t>* touched) {
+  if (level == p->levels) {
+    expand_path(*q, ta, tb, tc);
+    add_leaf(p, (*leaf)++, *ta, *tb, *tc, touched);
+    return;
+  }
+  const CanonRule& c = p->table[(size_t)p->node_rule[(size_t)node]];
+  q->U[(size_t)level] = &c.U;
+  q->V[(size_t)level] = &c.V;
+  q->W[(size_t)level] = &c.W;
+  q->R[(size_t)level] = c.r;
+  for (int r = 0; r < c.r; ++r) {
+    q->rl[(size_t)level] = r;
+    tree_leaves(p, t, t.first_child[(size_t)node] + r, level + 1, q, leaf, ta, tb, tc, touched);
+  }
+}
+
+}  // namespace
+
+fmm_status build_plan(const std::vector<CanonRule>& rules_in, int leaf_format, Plan** out) {
+  if (!valid_leaf_format(leaf_format)) return FMM_ERR_ARG;
+  Plan* p = new Plan();
+  p->levels = (int)rules_in.size();
+  p->leaf_format = leaf_format;
+  p->rules = rules_in;
+  for (auto& r : p->rules) {
+    if (brent_violations(r) != 0) {
+      delete p;
+      return FMM_ERR_NOT_MATMUL;
+    }
+    principal_quantities(&r);
+    p->pm *= r.m0;
+    p->pk *= r.k0;
+    p->pn *= r.n0;
+    p->leaves *= r.r;
+    p->q_sum += r.Q;
+    p->e_prod *= r.E;
+    if (p->pm > 32768 || p->pk > 32768 || p->pn > 32768 || p->leaves > 1000000) {
+      delete p;
+      return FMM_ERR_UNSUPPORTED;
+    }
+  }
+  const int L = p->levels;
+  Path q;
+  for (auto& r : p->rules) {
+    q.U.push_back(&r.U); q.V.push_back(&r.V); q.W.push_back(&r.W);
+    q.m0.push_back(r.m0); q.k0.push_back(r.k0); q.n0.push_back(r.n0); q.R.push_back(r.r);
+  }
+  q.rl.assign(L, 0);
+  p->host.resize((size_t)p->leaves);
+  std::set<int32_t> touched;
+  std::vector<Term> ta, tb, tc;
+  for (int64_t leaf = 0; leaf < p->leaves; ++leaf) {
+    // leaf = sum_l r_l prod_{l' > l} R_{l'}  (level 1 slowest)
+    int64_t rem = leaf;
+    for (int l = L - 1; l >= 0; --l) {
+      q.rl[l] = (int)(rem % q.R[l]);
+      rem /= q.R[l];
+    }
+    expand_path(q, &ta, &tb, &tc);
+    add_leaf(p, leaf, ta, tb, tc, &touched);
+  }
+  build_lists(p);
+  *out = p;
+  return FMM_OK;
+}
+
+fmm_status build_tree_plan(const std::vector<CanonRule>& table_in, int levels, const std::vector<int>& node_rule,
+                           int leaf_format, Plan** out) {
+  if (!valid_leaf_format(leaf_format) || levels < 1 || table_in.empty()) return FMM_ERR_ARG;
+  Plan* p = new Plan();
+  p->levels = levels;
+  p->leaf_format = leaf_format;
+  p->table = table_in;
+  p->node_rule = node_rule;
+  for (auto& r : p->table) {
+    if (brent_violations(r) != 0) {
+      delete p;
+      return FMM_ERR_NOT_MATMUL;
+    }
+    principal_quantities(&r);
+  }
+  // Level by level: the nodes of level l+1 are the children of level l's
+  // nodes, R of them per node, in node order.
+  TreeIndex t;
+  t.first_child.assign(node_rule.size(), -1);
+  int64_t at = 0, count = 1;
+  for (int l = 0; l < levels; ++l) {
+    t.level_start.push_back(at);
+    if (at + count > (int64_t)node_rule.size()) {
+      delete p;
+      return FMM_ERR_ARG;
+    }
+    int64_t next = 0;
+    const CanonRule* first = nullptr;
+    for (int64_t i = at; i < at + count; ++i) {
+      const int ri = node_rule[(size_t)i];
+      if (ri < 0 || ri >= (int)p->table.size()) {
+        delete p;
+        return FMM_ERR_ARG;
+      }
+      const CanonRule& c = p->table[(size_t)ri];
+      if (!first) first = &c;
+      // every path partitions A, B and C alike
+      if (c.m0 != first->m0 || c.k0 != first->k0 || c.n0 != first->n0) {
+        delete p;
+        return FMM_ERR_ARG;
+      }
+      if (c.r != first->r) p->level_r_uniform = false;
+      t.first_child[(size_t)i] = at + count + next;
+      next += c.r;
+      if (next > 1000000) {
+        delete p;
+        return FMM_ERR_UNSUPPORTED;
+      }
+    }
+    p->rules.push_back(*first);
+    p->pm *= first->m0;
+    p->pk *= first->k0;
+    p->pn *= first->n0;
+    at += count;
+    count = next;
+    if (p->pm > 32768 || p->pk > 32768 || p->pn > 32768) {
+      delete p;
+      return FMM_ERR_UNSUPPORTED;
+    }
+  }
+  if (at != (int64_t)node_rule.size()) {
+    delete p;
+    return FMM_ERR_ARG;
+  }
+  p->leaves = count;
+  p->q_sum = tree_delta_max(*p, t, 0, 0, 0.0);
+  if (p->pm * p->pn <= (int64_t)1 << 22) {
+    const std::vector<double> xi = tree_xi(*p, t, 0, 0);
+    p->e_prod = *std::max_element(xi.begin(), xi.end());
+  } else {
+    // too many C blocks to list: the product over levels of the largest E
+    // of the level's rules bounds every xi_k
+    p->e_prod = 1;
+    for (int l = 0; l < levels; ++l) {
+      double e = 0;
+      const int64_t end = l + 1 < levels ? t.level_start[(size_t)l + 1] : (int64_t)node_rule.size();
+      for (int64_t i = t.level_start[(size_t)l]; i < end; ++i) e = std::max(e, p->table[(size_t)node_rule[(size_t)i]].E);
+      p->e_prod *= e;
+    }
+  }
+  Path q;
+  q.U.assign(levels, nullptr); q.V.assign(levels, nullptr); q.W.assign(levels, nullptr);
+  q.R.assign(levels, 0); q.rl.assign(levels, 0);
+  for (auto& r : p->rules) { q.m0.push_back(r.m0); q.k0.push_back(r.k0); q.n0.push_back(r.n0); }
+  p->host.resize((size_t)p->leaves);
+  std::set<int32_t> touched;
+  std::vector<Term> ta, tb, tc;
+  int64_t leaf = 0;
+  tree_leaves(p, t, 0, 0, &q, &leaf, &ta, &tb, &tc, &touched);
+  build_lists(p);
   *out = p;
   return FMM_OK;
 }

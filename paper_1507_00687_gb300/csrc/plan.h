@@ -39,6 +39,9 @@ struct CanonRule {
   std::vector<double> U, V, W;  // (m0 k0) x r, (k0 n0) x r, (m0 n0) x r, row-major
   double Q = 0, E = 0;
   int64_t nnz = 0;
+  // per product r: alpha_r, beta_r (nonzeros of column r of U, V) and
+  // a_r, b_r (their 1-norms); per C block k: gamma_k (nonzeros of row k of W)
+  std::vector<double> alpha, beta, a, b, gamma;
 };
 
 struct Plan {
@@ -63,6 +66,15 @@ struct Plan {
   // Device copy (on `device`): the LeafDesc array followed by `lists`.
   LeafDesc* dev = nullptr;
   int device = -1;
+  // Non-uniform plans (Sec. 3.4): one rule per node of the recursion tree.
+  // table holds the distinct rules and node_rule each node's rule index,
+  // level by level, the children of a node in product order (r = 0..R-1).
+  // Both empty for uniform plans, whose levels are `rules`.  For a tree,
+  // rules[l] is the first node's rule of level l+1 (all nodes of a level
+  // partition alike), q_sum is max_k delta_k and e_prod max_k xi_k (Sec. 4.5).
+  std::vector<CanonRule> table;
+  std::vector<int> node_rule;
+  bool level_r_uniform = true;  // all nodes of each level have the same R
   int between = 0;           // scaling between recursive steps (fmm_plan_set_between_scaling)
   Plan* level1 = nullptr;    // the first level alone (its sums give the between-steps exponents)
   Plan* grad_a = nullptr;  // plan for dA = dC B^T  (lazily built)
@@ -74,6 +86,8 @@ fmm_status canonicalize(const fmm_rule& in, CanonRule* out);
 int brent_violations(const CanonRule& r);
 void principal_quantities(CanonRule* r);
 fmm_status build_plan(const std::vector<CanonRule>& rules, int leaf_format, Plan** out);
+fmm_status build_tree_plan(const std::vector<CanonRule>& table, int levels, const std::vector<int>& node_rule,
+                           int leaf_format, Plan** out);
 void destroy_plan(Plan* p);
 CanonRule rule_for_grad_a(const CanonRule& r);  // <m0, n0, k0>: [[W, V^T, U]]
 CanonRule rule_for_grad_b(const CanonRule& r);  // <k0, m0, n0>: [[U^T, W, V]]

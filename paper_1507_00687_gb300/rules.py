@@ -100,6 +100,43 @@ def fast323() -> BaseRule:
     return BaseRule("fast323", 3, 2, 3, U, V, W, COL, COL, ROW)
 
 
+def _index(p: int, q: int, rows: int, cols: int, order: int) -> int:
+    return p * cols + q if order == ROW else q * rows + p
+
+
+def _to_row_major(X: np.ndarray, rows: int, cols: int, order: int) -> np.ndarray:
+    """Rows of X re-indexed so that entry (p, q) of the operand is row p*cols+q."""
+    out = np.zeros_like(X)
+    for p in range(rows):
+        for q in range(cols):
+            out[p * cols + q] = X[_index(p, q, rows, cols, order)]
+    return out
+
+
+def rotate(rule: BaseRule) -> BaseRule:
+    """The cyclic rotation of a <m0,k0,n0> rule into a <n0,m0,k0> rule
+    (Sec. 5.3, App. A-B).  The matrix-multiplication tensor is the sum over
+    (i, k, j) of a_ik (x) b_kj (x) c_ij; cycling the factors to
+    c_ij (x) a_ik (x) b_kj gives the tensor of a <n0, m0, k0> product whose
+    A entry (j, i) is C's entry (i, j), whose B entry (i, k) is A's, and
+    whose C entry (j, k) is B's entry (k, j).  So U' = W, V' = U, W' = V,
+    with the W and V tables read column-major."""
+    U = _to_row_major(rule.U, rule.m0, rule.k0, rule.order_a)
+    V = _to_row_major(rule.V, rule.k0, rule.n0, rule.order_b)
+    W = _to_row_major(rule.W, rule.m0, rule.n0, rule.order_c)
+    return BaseRule(rule.name + "_rot", rule.n0, rule.m0, rule.k0, W, U, V, COL, ROW, COL)
+
+
+def variant(rule: BaseRule, XU: np.ndarray, XV: np.ndarray, XW: np.ndarray, name: str) -> BaseRule:
+    """[[XU U, XV V, XW W]]: the rule with the rows of its tables mixed by XU,
+    XV, XW in the rule's own entry order (Sec. 3.4: permutations of the
+    entries of A, B and C give equivalent rules with other stability
+    vectors).  The library checks the Brent equations of the result."""
+    return BaseRule(name, rule.m0, rule.k0, rule.n0, np.asarray(XU, np.float64) @ rule.U,
+                    np.asarray(XV, np.float64) @ rule.V, np.asarray(XW, np.float64) @ rule.W,
+                    rule.order_a, rule.order_b, rule.order_c)
+
+
 BUILTIN = {"strassen": strassen, "winograd": winograd, "fast323": fast323,
            "classical121": lambda: classical(1, 2, 1), "classical211": lambda: classical(2, 1, 1),
            "classical112": lambda: classical(1, 1, 2), "classical222": lambda: classical(2, 2, 2)}

@@ -116,3 +116,100 @@ def test_package_rules_match_oracle_tables():
         assert np.array_equal(pr.U, orule.U) and np.array_equal(pr.V, orule.V) and np.array_equal(pr.W, orule.W)
         assert (pr.order_a, pr.order_b, pr.order_c) == tuple(0 if o == "row" else 1 for o in
                                                              (orule.order_a, orule.order_b, orule.order_c))
+
+
+# ---------------------------------------------------------------- non-uniform plans (Sec. 3.4)
+
+def _tree_plan(desc, leaf="bf16"):
+    import tree_cases as TC
+    from paper_1507_00687_gb300 import api
+    lib, orc = TC.two_level(*desc)
+    return api.Plan.tree(lib, leaf), orc
+
+
+def test_tree_plan_dalberto_growth_factor(native):
+    # The Sec. 3.4 example: the variant at three level-2 nodes lowers the
+    # largest two-level growth factor of Strassen; the library's max xi_k
+    # must equal the oracle's (pinned to the printed value in the oracle
+    # tests), and max delta_k likewise.
+    import tree_cases as TC
+    plan, orc = _tree_plan(TC.dalberto())
+    info = plan.info()
+    assert info["leaves"] == 49
+    assert info["e_prod"] == float(OF.xi_vector(orc).max())
+    assert info["q_sum"] == float(OF.delta_vector(orc).max())
+    uni = _plan(native, ["strassen", "strassen"]).info()
+    assert info["e_prod"] < uni["e_prod"]
+    assert (info["pm"], info["pk"], info["pn"]) == (4, 4, 4)
+    b = plan.bound(4096, 1.0, 1.0, 2.0**-24)
+    assert b == pytest.approx(OF.bound_tree(orc, 4096, 1.0, 1.0, 2.0**-24))
+
+
+def test_tree_plan_fast323_nonuniform(native):
+    import tree_cases as TC
+    plan, orc = _tree_plan(TC.fast323_nonuniform())
+    info = plan.info()
+    assert info["leaves"] == 225
+    assert info["e_prod"] == float(OF.xi_vector(orc).max())
+    assert info["q_sum"] == float(OF.delta_vector(orc).max())
+    assert (info["pm"], info["pk"], info["pn"]) == (9, 4, 9)
+
+
+def test_tree_plan_with_one_rule_per_level_equals_uniform(native):
+    # A tree whose levels each repeat one rule is the uniform plan: same
+    # leaves, terms, quantities.
+    import tree_cases as TC
+    for desc, names in ((["S", ["S"] * 7], ["strassen", "strassen"]), (["Wg", ["S"] * 7], ["winograd", "strassen"])):
+        t = _tree_plan(desc)[0].info()
+        u = _plan(native, names).info()
+        assert t == u, (desc, t, u)
+
+
+def test_tree_plan_mixed_ranks(native):
+    import tree_cases as TC
+    plan, orc = _tree_plan(TC.mixed_rank())
+    info = plan.info()
+    assert info["leaves"] == 5 * 7 + 2 * 8
+    assert info["e_prod"] == float(OF.xi_vector(orc).max())
+    assert info["q_sum"] == float(OF.delta_vector(orc).max())
+    # the between-steps scaling needs equal ranks on every level
+    assert native.lib().fmm_plan_set_between_scaling(plan.handle, 1) == 10
+    assert native.lib().fmm_plan_set_between_scaling(_tree_plan(TC.dalberto())[0].handle, 1) == 0
+
+
+def test_tree_plan_rejects_bad_trees(native):
+    from paper_1507_00687_gb300 import api
+    L = native.lib()
+    s, f = PR.strassen(), PR.fast323()
+    plan = api.Plan([s])  # keeps the rule arrays alive
+    arr = plan._rule_array([s, f])
+    h = C.c_void_p()
+    nodes = (C.c_int32 * 9)(*([0] * 9))
+    assert L.fmm_plan_tree(C.byref(h), 2, arr, 2, 8, nodes, 0) == 0
+    L.fmm_plan_destroy(h)
+    assert L.fmm_plan_tree(C.byref(h), 2, arr, 2, 7, nodes, 0) == 1   # too few nodes
+    assert L.fmm_plan_tree(C.byref(h), 2, arr, 2, 9, nodes, 0) == 1   # too many
+    bad = (C.c_int32 * 8)(0, 0, 0, 1, 0, 0, 0, 0)                      # <3,2,3> among <2,2,2>
+    assert L.fmm_plan_tree(C.byref(h), 2, arr, 2, 8, bad, 0) == 1
+    oob = (C.c_int32 * 8)(0, 0, 0, 2, 0, 0, 0, 0)
+    assert L.fmm_plan_tree(C.byref(h), 2, arr, 2, 8, oob, 0) == 1
+    assert L.fmm_plan_tree(None, 2, arr, 2, 8, nodes, 0) == 1
+    assert L.fmm_plan_tree(C.byref(h), 2, arr, 0, 8, nodes, 0) == 1
+
+
+def test_rotated_rules_accepted_with_invariant_quantities(native):
+    # App. A-B: the cyclic rotations of a rule are rules of the rotated
+    # shape; Strassen's Q and E are invariant under them.  The library's
+    # Brent check accepts the package's rotations, and its Q, E equal the
+    # oracle's for the oracle's own rotations.
+    import tree_cases as TC
+    from paper_1507_00687_gb300 import api
+    for lab, shape in (("F_r1", (3, 3, 2)), ("F_r2", (2, 3, 3))):
+        pr = TC.package_rule(lab)
+        assert (pr.m0, pr.k0, pr.n0) == shape
+        info = api.Plan([pr]).info()
+        orr = TC.oracle_rule(lab)
+        assert info["q_sum"] == OR.principal(orr).Q and info["e_prod"] == OR.principal(orr).E
+    s = api.Plan(["strassen"]).info()
+    r = api.Plan([PR.rotate(PR.strassen())]).info()
+    assert (r["q_sum"], r["e_prod"]) == (s["q_sum"], s["e_prod"])
