@@ -146,3 +146,62 @@ def pow2_apply(A, B, eA, d, eB):
 def pow2_unscale(Cp, eA, eB):
     """C = 2^{eA_i} C'_ij 2^{eB_j} (exact)."""
     return np.ldexp(np.asarray(Cp, np.float64), np.asarray(eA)[:, None] + np.asarray(eB)[None, :])
+
+
+# ---------------------------------------------------------------------------
+# Adaptive repeated scaling: Alg. 3 with the tau stopping criterion (Sec. 6.3)
+# ---------------------------------------------------------------------------
+#
+# Steps alternate, starting with `first`.  t0 is the index (1-based) of the
+# first O step; every step after it is tested on the factors it computes:
+#   O step: every row factor of A' and column factor of B' >= (1+tau)^(-1/2)
+#   I step: every inside factor in [(1+tau)^(-1/4), (1+tau)^(1/4)]
+# and the iteration stops after the first step that passes (its result is
+# kept: the theorem bounds the distance from the limit after that step), or
+# after max_steps steps.  In power-of-two mode the factors tested are the
+# powers of two the step applies (2^(new - old exponent)).
+
+def _kinds(first: str, max_steps: int) -> str:
+    other = "I" if first == "O" else "O"
+    return "".join(first if t % 2 == 0 else other for t in range(max_steps))
+
+
+def adaptive(A, B, tau: float, max_steps: int, first: str = "O"):
+    """Real-valued adaptive Alg. 3; returns (state, steps taken)."""
+    st = start(A, B)
+    kinds = _kinds(first, max_steps)
+    t0 = kinds.index("O") + 1 if "O" in kinds else max_steps + 1
+    for t, kind in enumerate(kinds, start=1):
+        st = o_step(st) if kind == "O" else i_step(st)
+        if t <= t0:
+            continue
+        if kind == "O":
+            rp, sp = st.history[-1][1]
+            ok = np.all(rp >= (1 + tau) ** -0.5) and np.all(sp >= (1 + tau) ** -0.5)
+        else:
+            (D,) = st.history[-1][1]
+            ok = np.all(D >= (1 + tau) ** -0.25) and np.all(D <= (1 + tau) ** 0.25)
+        if ok:
+            return st, t
+    return st, len(kinds)
+
+
+def pow2_adaptive(A, B, tau: float, max_steps: int, first: str = "O"):
+    """Power-of-two adaptive Alg. 3; returns (state, steps taken)."""
+    st = pow2_start(A, B)
+    kinds = _kinds(first, max_steps)
+    t0 = kinds.index("O") + 1 if "O" in kinds else max_steps + 1
+    for t, kind in enumerate(kinds, start=1):
+        prev = st
+        st = pow2_o_step(st) if kind == "O" else pow2_i_step(st)
+        if t <= t0:
+            continue
+        if kind == "O":
+            f = np.exp2(np.concatenate([st.eA - prev.eA, st.eB - prev.eB]).astype(np.float64))
+            ok = np.all(f >= (1 + tau) ** -0.5)
+        else:
+            f = np.exp2((st.d - prev.d).astype(np.float64))
+            ok = np.all(f >= (1 + tau) ** -0.25) and np.all(f <= (1 + tau) ** 0.25)
+        if ok:
+            return st, t
+    return st, len(kinds)

@@ -144,3 +144,97 @@ def test_lemma_D4_closed_forms():
         assert np.array_equal(st.A, [[1, 0], [1, 2.0 ** -(2 ** (v - h - 1))]])
         assert np.array_equal(st.B, [[1, 0], [0, 2.0 ** -(2 ** (v - h - 1))]])
         st = Sc.o_step(st)
+
+
+# ---------------------------------------------------------------- adaptive Alg. 3 (tau stopping criterion)
+
+def _lemma_d4_stop(v, L):
+    # In the Lemma D.4 example (first O step at t = 1) the I step after h
+    # O-I rounds has factor 2^(2^(v-h-1)) on the second column and the O step
+    # after it the column factor 2^(-2^(v-h-1)) on B; with 1 + tau = 2^L the
+    # I test holds iff 2^(v-h-1) <= L/4 and the O test iff 2^(v-h-1) <= L/2.
+    # The O step at t = 2h+1 (h >= 1) tests the same inequality as the I step
+    # at 2h+2, so the first pass is t = 2 (I test at h = 0) or t = 2h*+3.
+    if 2 ** (v - 1) <= L / 4:
+        return 2
+    h = 0
+    while 2 ** (v - h - 1) > L / 2:
+        h += 1
+    return 2 * h + 3
+
+
+@pytest.mark.parametrize("L", [4, 8, 16, 64])
+def test_adaptive_stop_step_closed_form_lemma_d4(L):
+    v = 6
+    A = np.array([[1.0, 0.0], [1.0, 2.0 ** -(2**v)]])
+    B = np.eye(2)
+    tau = 2.0**L - 1
+    want = _lemma_d4_stop(v, L)
+    assert want <= 2 * (v - 2) + 3  # every exponent along the way is an integer
+    _, t = Sc.adaptive(A, B, tau, 40)
+    assert t == want
+    _, t2 = Sc.pow2_adaptive(A, B, tau, 40)
+    assert t2 == want
+    # a cap below the stopping step returns the cap
+    _, t3 = Sc.adaptive(A, B, tau, want - 1)
+    assert t3 == want - 1
+
+
+def _mu_max(st, lim):
+    # relative distance of r_i s_j ||A'|| ||B'|| from its limit (Sec. 6.3)
+    cur = np.outer(st.r, st.s) * np.abs(st.A).max() * np.abs(st.B).max()
+    ref = np.outer(lim.r, lim.s) * np.abs(lim.A).max() * np.abs(lim.B).max()
+    return float(np.max(np.abs(cur - ref) / np.abs(ref)))
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+@pytest.mark.parametrize("tau", [0.5, 1e-2, 1e-4])
+@pytest.mark.parametrize("first", ["O", "I"])
+def test_adaptive_stopping_theorem(kind, tau, first):
+    # The theorem of Sec. 6.3: once the test passes, the products
+    # r_i s_j ||A'|| ||B'|| are within relative distance tau of their limit.
+    # The limit is approximated by continuing the same alternation until the
+    # scales stop moving.
+    A, B = inputs.paper_distribution(kind, 40, seed=40 + kind)
+    st, t = Sc.adaptive(A, B, tau, 200, first)
+    assert t < 200
+    kinds = Sc._kinds(first, 4000)
+    lim = st
+    for k in kinds[t:t + 3000]:
+        lim = Sc.o_step(lim) if k == "O" else Sc.i_step(lim)
+    assert _mu_max(st, lim) <= tau * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+def test_pow2_adaptive_stops_at_a_fixed_point(kind):
+    # With tau < 3 no power-of-two factor other than 1 passes the I test, and
+    # an O factor passes only if it is >= 1; an I step that passes changes no
+    # exponent, after which further steps change nothing either.
+    A, B = inputs.paper_distribution(kind, 64, seed=60 + kind)
+    st, t = Sc.pow2_adaptive(A, B, 1e-3, 60)
+    assert t < 60
+    nxt = Sc.pow2_o_step(st) if t % 2 == 0 else Sc.pow2_i_step(st)
+    if t % 2 == 0:  # the last step was an I step
+        for s in (Sc.pow2_o_step(st), Sc.pow2_i_step(Sc.pow2_o_step(st))):
+            assert np.array_equal(s.eA, st.eA) and np.array_equal(s.d, st.d) and np.array_equal(s.eB, st.eB)
+    else:  # an O step: no exponent went down
+        prev = Sc.pow2_repeated(A, B, Sc._kinds("O", t - 1))
+        assert np.all(st.eA >= prev.eA) and np.all(st.eB >= prev.eB)
+    assert nxt is not None
+    # the result equals the fixed sequence of the same length
+    ref = Sc.pow2_repeated(A, B, Sc._kinds("O", t))
+    assert np.array_equal(ref.eA, st.eA) and np.array_equal(ref.d, st.d) and np.array_equal(ref.eB, st.eB)
+
+
+def test_adaptive_zero_steps_and_no_o_step():
+    A, B = inputs.paper_distribution(2, 16, seed=1)
+    st, t = Sc.pow2_adaptive(A, B, 0.1, 0)
+    assert t == 0 and not st.eA.any() and not st.d.any() and not st.eB.any()
+    # a single I step is never tested (no O step before it)
+    _, t = Sc.pow2_adaptive(A, B, 1e9, 1, "I")
+    assert t == 1
+    # with a huge tau the first tested step passes: t0 + 1
+    _, t = Sc.pow2_adaptive(A, B, 1e30, 10, "O")
+    assert t == 2
+    _, t = Sc.pow2_adaptive(A, B, 1e30, 10, "I")
+    assert t == 3
