@@ -185,6 +185,30 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
                      int32_t* eB, void* stream);
 
 /*
+ * Adaptive Alg. 3 (Sec. 6.3): O and I steps alternate, starting with an O
+ * step (first_inside = 0) or an I step (first_inside = 1), for at most
+ * max_steps steps.  Each step after the first O step is tested on the
+ * power-of-two factors it applies, 2^(new - old exponent): an O step
+ * passes when every row factor of A and column factor of B is at least
+ * (1 + tau)^(-1/2), an I step when every inside factor lies in
+ * [(1 + tau)^(-1/4), (1 + tau)^(1/4)].  The iteration stops after the first
+ * step that passes, keeping its result; the theorem of Sec. 6.3 puts the
+ * real-valued scales within relative distance tau of their limit there.
+ * With tau < 3 only factors of 1 pass the I test and only factors >= 1 the
+ * O test, so the power-of-two iteration stops at a fixed point.  tau > 0.
+ * eA (M), d (K), eB (N) receive the exponents, as fmm_scale.  steps_taken
+ * (device int32, may be NULL) receives the number of steps applied.  The
+ * stop is decided on the device: all max_steps steps are launched and
+ * those after the stop return at once, so the host does not wait and the
+ * call can be captured in a CUDA graph.  ws: device workspace of at least
+ * 4 (M + K + N + 64) bytes, 16-byte aligned (FMM_ERR_WORKSPACE otherwise).
+ */
+fmm_status fmm_scale_adaptive(const void* A, const void* B, int dtype, int64_t M, int64_t K, int64_t N,
+                              int64_t lda, int64_t ldb, double tau, int max_steps, int first_inside,
+                              int32_t* eA, int32_t* d, int32_t* eB, int32_t* steps_taken, void* ws,
+                              size_t ws_bytes, void* stream);
+
+/*
  * Where a multiply forms the operand combinations S_r = sum u A_i and
  * T_r = sum v B_j of Eq. 4.4 (the products and the output combination are
  * the same in both; so are the sums, in FP32 in index order, and their

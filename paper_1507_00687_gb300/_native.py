@@ -29,7 +29,7 @@ EXPORTS = [
     "fmm_sync_status", "fmm_status_string", "fmm_version", "fmm_last_error", "fmm_multiply_noalloc",
     "fmm_plan_set_schedule", "fmm_kernel_timing", "fmm_kernel_timing_read",
     "fmm_batch_workspace_size", "fmm_batch_create", "fmm_batch_run", "fmm_batch_destroy",
-    "fmm_plan_set_between_scaling", "fmm_plan_tree",
+    "fmm_plan_set_between_scaling", "fmm_plan_tree", "fmm_scale_adaptive",
 ]
 
 # Bytes of the library's static scratch array (FMM_NOALLOC_SCRATCH_BYTES).
@@ -86,6 +86,8 @@ def lib():
     L.fmm_plan_bound.argtypes = [vp, i64, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
     L.fmm_scale_outside.argtypes = [vp, vp, C.c_int, i64, i64, i64, i64, i64, vp, vp, vp, vp]
     L.fmm_scale_inside.argtypes = [vp, vp, C.c_int, i64, i64, i64, i64, i64, vp, vp, vp, vp]
+    L.fmm_scale_adaptive.argtypes = [vp, vp, C.c_int, i64, i64, i64, i64, i64, C.c_double, C.c_int, C.c_int,
+                                     vp, vp, vp, vp, vp, C.c_size_t, vp]
     L.fmm_scale.argtypes = [C.c_char_p, vp, vp, C.c_int, i64, i64, i64, i64, i64, vp, vp, vp, vp]
     L.fmm_workspace_size.argtypes = [vp, i64, i64, i64, C.POINTER(C.c_size_t)]
     L.fmm_multiply.argtypes = [vp, vp, i64, vp, i64, vp, i64, i64, i64, i64, C.c_int, vp, vp, vp, vp,

@@ -152,6 +152,28 @@ def scale(A: torch.Tensor, B: torch.Tensor, steps: str, stream=None):
     return eA, d, eB
 
 
+def scale_adaptive(A: torch.Tensor, B: torch.Tensor, tau: float, max_steps: int, first: str = "O", stream=None):
+    """Adaptive Alg. 3 with the tau stopping test (fmm_scale_adaptive);
+    returns int32 device tensors (eA, d, eB, steps) with steps[0] the number
+    of steps applied (decided on the device, read it when needed)."""
+    M, K = A.shape
+    K2, Nn = B.shape
+    assert K == K2 and A.dtype == B.dtype
+    if first not in ("O", "I"):
+        raise ValueError("first must be 'O' or 'I'")
+    lda, ldb = _rowmajor(A, "A"), _rowmajor(B, "B")
+    dev = A.device
+    eA = torch.empty(M, dtype=torch.int32, device=dev)
+    d = torch.empty(K, dtype=torch.int32, device=dev)
+    eB = torch.empty(Nn, dtype=torch.int32, device=dev)
+    steps = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(M + K + Nn + 64, dtype=torch.int32, device=dev)
+    N.check(N.lib().fmm_scale_adaptive(_ptr(A), _ptr(B), DTYPE[A.dtype], M, K, Nn, lda, ldb, float(tau), max_steps,
+                                       1 if first == "I" else 0, _ptr(eA), _ptr(d), _ptr(eB), _ptr(steps), _ptr(ws),
+                                       ws.numel() * 4, _stream(stream)), "fmm_scale_adaptive")
+    return eA, d, eB, steps
+
+
 def scale_outside(A, B, d=None, eA=None, eB=None, stream=None):
     """One O step (Alg. 1 when d is None); returns (eA, eB)."""
     M, K = A.shape

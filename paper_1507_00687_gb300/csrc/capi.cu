@@ -2,6 +2,7 @@
 // launch sequences of the scaling steps, the forward and the backward
 // multiply.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -1153,6 +1154,71 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
     if (s != FMM_OK) return s;
     if (*c == 'O') e_zero = false;
     else d_zero = false;
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_scale_adaptive(const void* A, const void* B, int dtype, int64_t M, int64_t K, int64_t N,
+                              int64_t lda, int64_t ldb, double tau, int max_steps, int first_inside,
+                              int32_t* eA, int32_t* d, int32_t* eB, int32_t* steps_taken, void* ws,
+                              size_t ws_bytes, void* stream) {
+  if (!valid_dtype(dtype) || M < 0 || K < 0 || N < 0 || max_steps < 0 || max_steps > 100000) return FMM_ERR_ARG;
+  if (!(tau > 0) || !std::isfinite(tau) || (first_inside != 0 && first_inside != 1)) return FMM_ERR_ARG;
+  if ((M > 0 && !eA) || (K > 0 && !d) || (N > 0 && !eB)) return FMM_ERR_ARG;
+  if ((M > 0 && K > 0 && !A) || (K > 0 && N > 0 && !B)) return FMM_ERR_ARG;
+  if ((M > 0 && K > 0 && lda < K) || (K > 0 && N > 0 && ldb < N)) return FMM_ERR_SHAPE;
+  if (!ws || (uintptr_t)ws % 16 != 0 || (int64_t)ws_bytes < 4 * (M + K + N + 64)) return FMM_ERR_WORKSPACE;
+  int* status = status_ptr();
+  if (!status) return FMM_ERR_CUDA;
+  cudaStream_t st = as_stream(stream);
+  // workspace: ctl[64] (stopped, failed, steps applied), then the exponents
+  // a step computes before its test adopts them
+  int* ctl = static_cast<int*>(ws);
+  int* nA = ctl + 64;
+  int* nB = nA + M;
+  int* nD = nB + N;
+  // The tests in exponent form: an O factor 2^g passes when
+  // g >= -log2(1 + tau) / 2, an I factor when |g| <= log2(1 + tau) / 4.
+  const double l2 = std::log2(1.0 + tau);
+  const int o_lo = (int)std::max(-1e9, std::ceil(-l2 / 2)), i_hi = (int)std::min(1e9, std::floor(l2 / 4));
+  if (launch_fill(ctl, 64, 0, st) != cudaSuccess || launch_fill(eA, M, 0, st) != cudaSuccess ||
+      launch_fill(d, K, 0, st) != cudaSuccess || launch_fill(eB, N, 0, st) != cudaSuccess)
+    return FMM_ERR_CUDA;
+  if (steps_taken && launch_fill(steps_taken, 1, 0, st) != cudaSuccess) return FMM_ERR_CUDA;
+  // while a vector is still all zeros its reductions run unshifted
+  bool d_zero = true, e_zero = true, seen_o = false;
+  for (int t = 1; t <= max_steps; ++t) {
+    const bool o = ((t - 1) % 2 == 0) == (first_inside == 0);
+    const bool tested = seen_o;  // every step after the first O step
+    if (o) {
+      // eA_i = e(max_k |A_ik| 2^d_k), eB_j = e(max_k 2^-d_k |B_kj|)
+      if (K == 0) {
+        if (launch_fill(nA, M, 0, st) != cudaSuccess || launch_fill(nB, N, 0, st) != cudaSuccess) return FMM_ERR_CUDA;
+      } else if (!cuda_ok(launch_row_exp(A, dtype, M, K, lda, d_zero ? nullptr : d, +1, nA, kRowOStep, status, st,
+                                         ctl),
+                          "row reduction") ||
+                 !cuda_ok(launch_col_exp(B, dtype, K, N, ldb, d_zero ? nullptr : d, -1, nB, status, st, ctl),
+                          "column reduction") ||
+                 launch_zero_sentinel(nB, N, st) != cudaSuccess) {
+        return FMM_ERR_CUDA;
+      }
+      if (launch_scale_accept(nA, eA, M, o_lo, INT32_MAX, ctl, st) != cudaSuccess ||
+          launch_scale_accept(nB, eB, N, o_lo, INT32_MAX, ctl, st) != cudaSuccess)
+        return FMM_ERR_CUDA;
+      e_zero = false;
+      seen_o = true;
+    } else if (K > 0) {
+      // d_k = floor((e(max_j |B_kj| 2^-eB_j) - e(max_i 2^-eA_i |A_ik|)) / 2)
+      if (!cuda_ok(launch_col_exp(A, dtype, M, K, lda, e_zero ? nullptr : eA, -1, nD, status, st, ctl),
+                   "column reduction") ||
+          !cuda_ok(launch_row_exp(B, dtype, K, N, ldb, e_zero ? nullptr : eB, -1, nD, kRowIStep, status, st, ctl),
+                   "row reduction"))
+        return FMM_ERR_CUDA;
+      if (N == 0 && launch_fill(nD, K, 0, st) != cudaSuccess) return FMM_ERR_CUDA;
+      if (launch_scale_accept(nD, d, K, -i_hi, i_hi, ctl, st) != cudaSuccess) return FMM_ERR_CUDA;
+      d_zero = false;
+    }
+    if (launch_scale_stop(ctl, tested ? 1 : 0, t, steps_taken, st) != cudaSuccess) return FMM_ERR_CUDA;
   }
   return FMM_OK;
 }

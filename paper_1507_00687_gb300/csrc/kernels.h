@@ -12,10 +12,17 @@ namespace fmm {
 constexpr int kRowOStep = 0;
 constexpr int kRowIStep = 1;
 
+// skip (may be NULL): a device flag; when it is set at launch time the
+// reduction does nothing (an adaptive iteration that has stopped).
 cudaError_t launch_row_exp(const void* X, int dt, int64_t R, int64_t C, int64_t ld, const int* ce, int cs,
-                           int* out, int mode, int* status, cudaStream_t st);
+                           int* out, int mode, int* status, cudaStream_t st, const int* skip = nullptr);
 cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t ld, const int* re, int rs,
-                           int* out, int* status, cudaStream_t st);
+                           int* out, int* status, cudaStream_t st, const int* skip = nullptr);
+// Adaptive Alg. 3: test one step's factors 2^(next - cur) against [lo, hi]
+// and adopt next; then record the step and stop when it was tested and
+// passed (ctl: stopped, failed, steps applied).
+cudaError_t launch_scale_accept(const int* next, int* cur, int64_t n, int lo, int hi, int* ctl, cudaStream_t st);
+cudaError_t launch_scale_stop(int* ctl, int tested, int t, int* steps_out, cudaStream_t st);
 cudaError_t launch_zero_sentinel(int* p, int64_t n, cudaStream_t st);
 
 // One problem of a batched reduction (rows: R x C, ld; shift: column

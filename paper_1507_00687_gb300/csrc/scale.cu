@@ -173,7 +173,8 @@ __device__ __forceinline__ void row_exp_one(const void* X, int64_t C, int64_t ld
 template <int DT, bool SHIFT>
 __global__ void __launch_bounds__(kRowWarps * 32) row_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
                                                                  const int* ce, int cs, int* out, int mode,
-                                                                 int vec_ok, int* status) {
+                                                                 int vec_ok, int* status, const int* skip) {
+  if (skip && *skip) return;  // an adaptive iteration that has stopped
   bool nf = false;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (int64_t)blockIdx.x * kRowWarps + (threadIdx.x >> 5);
@@ -300,7 +301,8 @@ __device__ __forceinline__ void col_exp_cta(const void* X, int64_t R, int64_t C,
 template <int DT, bool SHIFT>
 __global__ void __launch_bounds__(kColThreads) col_exp_kernel(const void* X, int64_t R, int64_t C, int64_t ld,
                                                               const int* re, int rs, int* out, int rows_per_cta,
-                                                              int vec_ok, int* status) {
+                                                              int vec_ok, int* status, const int* skip) {
+  if (skip && *skip) return;  // an adaptive iteration that has stopped
   extern __shared__ int red[];  // [kColGroups][kColSpan]
   bool nf = false;
   col_exp_cta<DT, SHIFT>(X, R, C, ld, re, rs, out, rows_per_cta, vec_ok != 0, blockIdx.x, blockIdx.y, red, &nf);
@@ -399,7 +401,7 @@ static int sm_count() {
 }
 
 cudaError_t launch_row_exp(const void* X, int dt, int64_t R, int64_t C, int64_t ld, const int* ce, int cs,
-                           int* out, int mode, int* status, cudaStream_t st) {
+                           int* out, int mode, int* status, cudaStream_t st, const int* skip) {
   if (R == 0) return cudaSuccess;
   const int vec = vec_aligned(X, ld, dt) ? 1 : 0;
   const int64_t grid = std::min<int64_t>((R + kRowWarps - 1) / kRowWarps, (int64_t)sm_count() * 8);
@@ -408,8 +410,8 @@ cudaError_t launch_row_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
   KernelTimer timer("scale", st);
   switch (dt) {
 #define FMM_ROW(DT)                                                                              \
-  (ce ? row_exp_kernel<DT, true><<<g, nt, 0, st>>>(X, R, C, ld, ce, cs, out, mode, vec, status)   \
-      : row_exp_kernel<DT, false><<<g, nt, 0, st>>>(X, R, C, ld, ce, cs, out, mode, vec, status))
+  (ce ? row_exp_kernel<DT, true><<<g, nt, 0, st>>>(X, R, C, ld, ce, cs, out, mode, vec, status, skip)   \
+      : row_exp_kernel<DT, false><<<g, nt, 0, st>>>(X, R, C, ld, ce, cs, out, mode, vec, status, skip))
     case kF32: FMM_ROW(kF32); break;
     case kBF16: FMM_ROW(kBF16); break;
     default: FMM_ROW(kF16); break;
@@ -419,7 +421,7 @@ cudaError_t launch_row_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
 }
 
 cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t ld, const int* re, int rs,
-                           int* out, int* status, cudaStream_t st) {
+                           int* out, int* status, cudaStream_t st, const int* skip) {
   if (C == 0) return cudaSuccess;
   {
     KernelTimer fill_timer("scale", st);
@@ -448,8 +450,9 @@ cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
     cudaFuncSetAttribute(col_exp_kernel<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kColSmem);  \
     attr_done[dev][2 * I] = true;                                                                           \
   }                                                                                                          \
-  if (re) col_exp_kernel<DT, true><<<g, kColThreads, kColSmem, st>>>(X, R, C, ld, re, rs, out, rows, vec, status); \
-  else col_exp_kernel<DT, false><<<g, kColThreads, kColSmem, st>>>(X, R, C, ld, re, rs, out, rows, vec, status);
+  if (re) col_exp_kernel<DT, true><<<g, kColThreads, kColSmem, st>>>(X, R, C, ld, re, rs, out, rows, vec, status,  \
+                                                                     skip);                                    \
+  else col_exp_kernel<DT, false><<<g, kColThreads, kColSmem, st>>>(X, R, C, ld, re, rs, out, rows, vec, status, skip);
     case kF32: { FMM_COL(kF32, 0) break; }
     case kBF16: { FMM_COL(kBF16, 1) break; }
     default: { FMM_COL(kF16, 2) break; }
@@ -533,6 +536,45 @@ cudaError_t launch_prepare(const void* X, int dt, int64_t R, int64_t C, int64_t 
                                                          cs, Y, Rp, Cp, ldy);
       break;
   }
+  return cudaGetLastError();
+}
+
+// Adaptive Alg. 3 (Sec. 6.3).  ctl[0]: stopped; ctl[1]: some factor of the
+// current step failed its test; ctl[2]: steps applied.  One step's accept
+// pass compares the exponents the step computed (next) with the current
+// ones (cur): the step's factor is 2^(next - cur), tested against
+// [lo, hi]; then cur <- next.  Nothing happens once stopped.
+__global__ void scale_accept_kernel(const int* next, int* cur, int64_t n, int lo, int hi, int* ctl) {
+  if (*(volatile int*)ctl) return;
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int g = next[i] - cur[i];
+    bad |= g < lo || g > hi;
+    cur[i] = next[i];
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(ctl + 1, 1);
+}
+
+// After step t: count it, and stop if it was tested and passed.
+__global__ void scale_stop_kernel(int* ctl, int tested, int t, int* steps_out) {
+  if (ctl[0] == 0) {
+    ctl[2] = t;
+    if (tested && ctl[1] == 0) ctl[0] = 1;
+  }
+  ctl[1] = 0;
+  if (steps_out) *steps_out = ctl[2];
+}
+
+cudaError_t launch_scale_accept(const int* next, int* cur, int64_t n, int lo, int hi, int* ctl, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  KernelTimer timer("scale", st);
+  scale_accept_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(next, cur, n, lo, hi, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_stop(int* ctl, int tested, int t, int* steps_out, cudaStream_t st) {
+  KernelTimer timer("scale", st);
+  scale_stop_kernel<<<1, 1, 0, st>>>(ctl, tested, t, steps_out);
   return cudaGetLastError();
 }
 
