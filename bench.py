@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--schedule", default="auto", choices=["auto", "pass", "load_stage"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator / variant timings")
     ap.add_argument("--batch", type=int, default=512, help="products in the batched workload extra (0: skip)")
+    ap.add_argument("--experiment", default="", choices=["", "scaling_accuracy"],
+                    help="scaling_accuracy: relative error of Strassen, L = 1..6, under each scaling (Sec. 6.5)")
+    ap.add_argument("--samples", type=int, default=100, help="samples per distribution (--experiment)")
+    ap.add_argument("--exp-n", type=int, default=2000, help="matrix size (--experiment)")
     return ap.parse_args()
 
 
@@ -289,12 +293,68 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------- accuracy experiment
+
+EXP_SCALINGS = [("none", ""), ("outside", "O"), ("inside", "I"), ("outside-inside", "OI"),
+                ("inside-outside", "IO"), ("2x outside-inside", "OIOI"), ("10x outside-inside", "OI" * 10),
+                ("adaptive tau=1e-3", None)]
+
+
+def scaling_accuracy(args):
+    """The scaling experiment of Sec. 6.5 on the GPU path: for each of the
+    three input distributions, ``samples`` pairs of n x n matrices; for each
+    scaling and L = 1..6 levels of Strassen, the largest componentwise
+    relative error max_ij |C^_ij - C_ij| / |C_ij| over the samples.  C is
+    the float64 classical product of the FP32 inputs (all entries are
+    nonnegative, so its own relative error is below n 2^-53)."""
+    import torch
+    from paper_1507_00687_gb300 import build
+    build.build()
+    from paper_1507_00687_gb300 import api, inputs
+    n, samples, levels = args.exp_n, args.samples, range(1, 7)
+    plans = {L: api.Plan(["strassen"] * L, args.leaf, "pass") for L in levels}
+    worst = {k: {name: [0.0] * len(levels) for name, _ in EXP_SCALINGS} for k in (1, 2, 3)}
+    steps_seen = {k: [] for k in (1, 2, 3)}
+    t0 = time.perf_counter()
+    for kind in (1, 2, 3):
+        for s in range(samples):
+            A64, B64 = inputs.paper_distribution(kind, n, seed=100000 * kind + s)
+            A = torch.from_numpy(A64).float().cuda()
+            B = torch.from_numpy(B64).float().cuda()
+            C = A.double() @ B.double()
+            Cabs = C.abs()
+            for name, steps in EXP_SCALINGS:
+                if steps is None:
+                    eA, d, eB, t = api.scale_adaptive(A, B, 1e-3, 40)
+                    steps_seen[kind].append(int(t.item()))
+                elif steps:
+                    eA, d, eB = api.scale(A, B, steps)
+                else:
+                    eA = d = eB = None
+                for i, L in enumerate(levels):
+                    Ch = api.multiply(plans[L], A, B, eA, d, eB)
+                    err = ((Ch.double() - C).abs() / Cabs).max().item()
+                    worst[kind][name][i] = max(worst[kind][name][i], err)
+        api.sync_status()
+    out = {"experiment": "scaling_accuracy", "rule": "strassen", "levels": list(levels), "n": n,
+           "samples_per_distribution": samples, "leaf": args.leaf, "inputs": "FP32 (rounded from the samples)",
+           "error": "max over samples of max_ij |C^-C|/|C|, C = float64 classical product",
+           "adaptive_steps": {str(k): [min(v), max(v)] for k, v in steps_seen.items()},
+           "seconds": round(time.perf_counter() - t0, 1),
+           "table": {f"distribution {k}": {name: [float(f"{e:.3e}") for e in worst[k][name]]
+                                           for name, _ in EXP_SCALINGS} for k in (1, 2, 3)}}
+    print(json.dumps(out))
+
+
 # ---------------------------------------------------------------- GPU leg
 
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.experiment == "scaling_accuracy":
+        scaling_accuracy(args)
         return
     import torch
     import torch.distributed as dist

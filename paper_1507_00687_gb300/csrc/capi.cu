@@ -401,6 +401,11 @@ static OutArgs out_args(const Plan* p, const PassGeom& g, const EpilogueArgs& c,
   o.c_blk = o.c_start + g.R + 1;
   o.c_coef = reinterpret_cast<const float*>(o.c_blk + p->list_nnz[2]);
   o.c_nnz = p->list_nnz[2];
+  if (p->gather_off >= 0) {
+    o.g_start = lists + p->gather_off;
+    o.g_leaf = o.g_start + o.c_blocks + 1;
+    o.g_coef = reinterpret_cast<const float*>(o.g_leaf + p->list_nnz[2]);
+  }
   return o;
 }
 
@@ -497,7 +502,10 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
   // epilogue leaves SMs idle when tiles per leaf are few, and its C
   // read-modify-writes cost more than one more bandwidth pass).
   const bool want_m = p->schedule != FMM_SCHEDULE_PASS_EPILOGUE;
-  const bool store_m = want_m && g.R > 1 && p->pm * p->pn <= kMaxOutBlocks &&
+  // more C blocks than the stored-products pass keeps on chip: the output
+  // pass gathers per C block instead
+  const bool gather = p->pm * p->pn > kMaxOutBlocks;
+  const bool store_m = want_m && g.R > 1 && (!gather || p->gather_off >= 0) &&
                        (int64_t)ws_bytes >= g.bytes_a + g.bytes_b + g.bytes_m;
   float* mbuf = store_m ? reinterpret_cast<float*>(wb + g.bytes_b) : nullptr;
   CombineArgs ca = combine_args(p, g, x, 0, leaves, wa), cb = combine_args(p, g, y, 1, leaves, wb);
@@ -550,8 +558,10 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
   if (!direct_args(p, g, x, y, c, leaves, wa, wb, mbuf, status, &d)) return FMM_ERR_CUDA;
   if (!cuda_ok(launch_direct_gemm(d, p->leaf_format, g.bn, st), "multiply launch")) return FMM_ERR_CUDA;
   if (!store_m) return FMM_OK;
-  return cuda_ok(launch_out_combine(out_args(p, g, c, leaves, mbuf), st), "output combination pass") ? FMM_OK
-                                                                                                     : FMM_ERR_CUDA;
+  const OutArgs o = out_args(p, g, c, leaves, mbuf);
+  return cuda_ok(gather ? launch_out_gather(o, st) : launch_out_combine(o, st), "output combination pass")
+             ? FMM_OK
+             : FMM_ERR_CUDA;
 }
 
 // Run the flattened plan p: C (M x N) = X (M x K) Y (K x N) with X, Y given

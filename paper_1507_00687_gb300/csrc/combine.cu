@@ -19,6 +19,7 @@
 // them; every output element (padding included) is written.  HBM-bound:
 // each input element is read once from DRAM, each output element written
 // once.
+#include <algorithm>
 #include <type_traits>
 
 #include <cuda_bf16.h>
@@ -99,6 +100,42 @@ __device__ __forceinline__ void store4(unsigned short* hi, unsigned short* lo, c
   }
 }
 
+// The scaled elements (lr, lc .. lc + 3) of one term's block tile (zero
+// outside the source).
+template <int DT>
+__device__ __forceinline__ void load_term4(const CombineArgs& a, int32_t blk, int64_t lr, int64_t lc, bool vec_ok,
+                                           float (&x)[4]) {
+  const int64_t bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
+  const int64_t rb = a.t_rows ? bt : bk, cb = a.t_rows ? bk : bt;
+  // rows / columns of this block that exist in the source
+  const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows), nc = min(a.b_cols, a.cols - cb * a.b_cols);
+  const int64_t gr = rb * a.b_rows + lr, gc = cb * a.b_cols + lc;
+  if (vec_ok && lr < nr && lc + 4 <= nc) {
+    load4<DT>(a.src, gr * a.ld + gc, x);
+    if (a.re || a.ce) {
+      const int er = a.re ? a.rs * __ldg(a.re + gr) : 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = scale_pow2(x[j], er + (a.ce ? a.cs * __ldg(a.ce + gc + j) : 0));
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      x[j] = 0.f;
+      if (lr < nr && lc + j < nc) {
+        const float v = load_elem<DT>(a.src, gr * a.ld + gc + j);
+        const int e = (a.re ? a.rs * __ldg(a.re + gr) : 0) + (a.ce ? a.cs * __ldg(a.ce + gc + j) : 0);
+        x[j] = scale_pow2(v, e);
+      }
+    }
+  }
+}
+
+// Unstaged form (plans with more input blocks than kMaxStaged): a CTA
+// covers one kTR x 64 position tile for a contiguous range of leaves
+// (blockIdx.z) and sums each leaf's terms from the source in term order,
+// issuing the loads of kTermBatch terms together.
+constexpr int kTermBatch = 4;
+
 template <int DT, int FMT>
 __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs a) {
   const int64_t r0 = (int64_t)blockIdx.y * kTR, c0 = (int64_t)blockIdx.x * kTC;
@@ -109,55 +146,42 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs a) 
   const bool vec_ok = ((uintptr_t)a.src % (4 * es) == 0) && (a.ld % 4 == 0) && (a.b_cols % 4 == 0);
   unsigned short* out = static_cast<unsigned short*>(a.out);
   const int64_t plane = R * a.p_rows * a.p_cols;
-  for (int64_t r = 0; r < R; ++r) {
-    const LeafDesc* L = a.leaves + r;
-    const int n = a.side == 0 ? __ldg(&L->na) : __ldg(&L->nb);
+  const int64_t per = (R + gridDim.z - 1) / gridDim.z;
+  const int64_t r_end = min(R, (int64_t)(blockIdx.z + 1) * per);
+  // a tile wholly in the padding of every block only writes zeros
+  const bool pad = r0 >= a.b_rows || c0 >= a.b_cols;
+  for (int64_t r = (int64_t)blockIdx.z * per; r < r_end; ++r) {
+    const int t1 = pad ? 0 : __ldg(a.t_start + r + 1);
     float acc[kRowsPerThread][4];
 #pragma unroll
     for (int i = 0; i < kRowsPerThread; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int t = 0; t < n; ++t) {
-      const int32_t blk = a.side == 0 ? __ldg(&L->a_blk[t]) : __ldg(&L->b_blk[t]);
-      const float coef = a.side == 0 ? __ldg(&L->a_coef[t]) : __ldg(&L->b_coef[t]);
-      const int64_t bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
-      const int64_t rb = a.t_rows ? bt : bk, cb = a.t_rows ? bk : bt;
-      // rows / columns of this block that exist in the source
-      const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows), nc = min(a.b_cols, a.cols - cb * a.b_cols);
-      const int64_t grow0 = rb * a.b_rows, gcol0 = cb * a.b_cols;
-      const bool interior = vec_ok && r0 + kTR <= nr && c0 + kTC <= nc;
+    for (int t = pad ? 0 : __ldg(a.t_start + r); t < t1; t += kTermBatch) {
+      float x[kTermBatch][kRowsPerThread][4];
+      float coef[kTermBatch];
 #pragma unroll
-      for (int i = 0; i < kRowsPerThread; ++i) {
-        const int64_t lr = r0 + tr + 16 * i, lc = c0 + tc;
-        float x[4];
-        if (interior) {
-          const int64_t gr = grow0 + lr, gc = gcol0 + lc;
-          load4<DT>(a.src, gr * a.ld + gc, x);
-          if (a.re || a.ce) {
-            const int er = a.re ? a.rs * __ldg(a.re + gr) : 0;
-            int ec[4] = {0, 0, 0, 0};
-            if (a.ce) {
+      for (int u = 0; u < kTermBatch; ++u) {
+        const bool live = t + u < t1;
+        const int32_t blk = live ? __ldg(a.t_blk + t + u) : 0;
+        coef[u] = live ? __ldg(a.t_coef + t + u) : 0.f;
 #pragma unroll
-              for (int j = 0; j < 4; ++j) ec[j] = a.cs * __ldg(a.ce + gc + j);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = scale_pow2(x[j], er + ec[j]);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            x[j] = 0.f;
-            if (lr < nr && lc + j < nc) {
-              const int64_t gr = grow0 + lr, gc = gcol0 + lc + j;
-              const float v = load_elem<DT>(a.src, gr * a.ld + gc);
-              const int e = (a.re ? a.rs * __ldg(a.re + gr) : 0) + (a.ce ? a.cs * __ldg(a.ce + gc) : 0);
-              x[j] = scale_pow2(v, e);
-            }
+        for (int i = 0; i < kRowsPerThread; ++i) {
+          if (live) {
+            load_term4<DT>(a, blk, r0 + tr + 16 * i, c0 + tc, vec_ok, x[u][i]);
+          } else {
+            x[u][i][0] = x[u][i][1] = x[u][i][2] = x[u][i][3] = 0.f;
           }
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(coef, x[j], acc[i][j]);
       }
+      // in term order
+#pragma unroll
+      for (int u = 0; u < kTermBatch; ++u)
+        if (t + u < t1)
+#pragma unroll
+          for (int i = 0; i < kRowsPerThread; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(coef[u], x[u][i][j], acc[i][j]);
     }
 #pragma unroll
     for (int i = 0; i < kRowsPerThread; ++i) {
@@ -176,7 +200,8 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs a) 
 constexpr int kMaxStaged = 64;
 
 template <int DT, int FMT, int TR, int RPT, bool BETWEEN = false>
-__device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_t bx, int64_t by, float4* tile4) {
+__device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_t bx, int64_t by, float4* tile4,
+                                                    int r_begin, int r_end) {
   // RPT rows per thread: rows tr + (TR / RPT) q, q < RPT; 4 columns each
   constexpr int kT = TR * 16 / RPT;
   const int64_t r0 = by * TR, c0 = bx * kTC;
@@ -209,14 +234,14 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
     for (int rb = 0; rb < n_rb; ++rb) {
       const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows);
       const int64_t gr = rb * a.b_rows + lr;
-      const bool row_in = r0 + TR <= nr;
-      const int er = (a.re && lr < nr) ? a.rs * __ldg(a.re + gr) : 0;
+      const bool row_in = lr < nr;
+      const int er = (a.re && row_in) ? a.rs * __ldg(a.re + gr) : 0;
       const char* src_row = static_cast<const char*>(a.src) + gr * a.ld * es;
       for (int cb = 0; cb < n_cb; ++cb) {
         const int64_t nc = min(a.b_cols, a.cols - cb * a.b_cols);
         const int64_t gc = cb * a.b_cols + lc;
         float x[4];
-        if (vec_ok && row_in && c0 + kTC <= nc) {
+        if (vec_ok && row_in && lc + 4 <= nc) {
           load4<DT>(src_row, gc, x);
           if (a.re || a.ce) {
             int4 ec = make_int4(0, 0, 0, 0);
@@ -245,11 +270,11 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
   const int64_t plane = (int64_t)R * a.p_rows * a.p_cols;
   const int me = tr * 16 + tq;
   constexpr int kRowStep = (TR / RPT) * 16;  // float4 distance between a thread's rows
-  unsigned short* orow = out + (r0 + tr) * a.p_cols + lc;
   const int64_t leaf_stride = a.p_rows * a.p_cols;
+  unsigned short* orow = out + (r0 + tr) * a.p_cols + lc + r_begin * leaf_stride;
   const int64_t qstride = (int64_t)(TR / RPT) * a.p_cols;
-  int t = 0;
-  for (int r = 0; r < R; ++r, orow += leaf_stride) {
+  int t = tstart[r_begin];
+  for (int r = r_begin; r < r_end; ++r, orow += leaf_stride) {
     const int t1 = tstart[r + 1];
     float acc[RPT][4];
 #pragma unroll
@@ -297,7 +322,12 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
 template <int DT, int FMT, int TR, int RPT, bool BETWEEN>
 __global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_kernel(const CombineArgs a) {
   extern __shared__ float4 tile4[];  // [block][TR][16], then the term list
-  combine_staged_body<DT, FMT, TR, RPT, BETWEEN>(a, blockIdx.x, blockIdx.y, tile4);
+  // blockIdx.z takes a contiguous range of the leaves (the input tiles are
+  // staged once per range)
+  const int R = (int)a.num_leaves;
+  const int per = (R + (int)gridDim.z - 1) / (int)gridDim.z;
+  const int r_begin = min(R, (int)blockIdx.z * per), r_end = min(R, r_begin + per);
+  combine_staged_body<DT, FMT, TR, RPT, BETWEEN>(a, blockIdx.x, blockIdx.y, tile4, r_begin, r_end);
 }
 
 // Index of the problem whose [start[p], start[p + 1]) range holds idx.
@@ -320,7 +350,29 @@ __global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_batched_kernel(c
   const int p = find_problem(start, count, blockIdx.x);
   const CombineArgs& a = args[p];
   const int64_t local = blockIdx.x - __ldg(start + p), gx = a.p_cols / kTC;
-  combine_staged_body<DT, FMT, TR, RPT>(a, local % gx, local / gx, tile4);
+  combine_staged_body<DT, FMT, TR, RPT>(a, local % gx, local / gx, tile4, 0, (int)a.num_leaves);
+}
+
+static int device_sms() {
+  static int n[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (n[dev] == 0) {
+    cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (n[dev] <= 0) n[dev] = 132;
+  }
+  return n[dev];
+}
+
+// Leaf ranges per position tile so that the tiles holding data (not only
+// padding) still give about `waves` CTAs per SM when they are few (deep
+// plans have small leaf blocks and many leaves); at most one range per leaf.
+static unsigned leaf_splits(const CombineArgs& a, int tile_rows, int64_t leaves, int waves) {
+  const int64_t tiles = ((std::min(a.b_rows, a.p_rows) + tile_rows - 1) / tile_rows) *
+                        ((std::min(a.b_cols, a.p_cols) + kTC - 1) / kTC);
+  const int64_t want = ((int64_t)device_sms() * waves + tiles - 1) / tiles;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>({want, leaves, 65535}));
 }
 
 // Shared memory of the staged form: block tiles plus the term list (and
@@ -341,8 +393,10 @@ void launch_staged_tr_b(const CombineArgs& a, int nb, cudaStream_t st) {
                          (int)kStagedSmemMax);
     attr_done[dev] = true;
   }
-  combine_staged_kernel<DT, FMT, TR, RPT, BETWEEN><<<dim3((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / TR)),
-                                                     TR * 16 / RPT, staged_smem(nb, TR, a.t_nnz, a.num_leaves), st>>>(a);
+  const dim3 grid((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / TR));
+  combine_staged_kernel<DT, FMT, TR, RPT, BETWEEN>
+      <<<dim3(grid.x, grid.y, leaf_splits(a, TR, a.num_leaves, 4)), TR * 16 / RPT,
+         staged_smem(nb, TR, a.t_nnz, a.num_leaves), st>>>(a);
 }
 
 template <int DT, int FMT, int TR, int RPT = 1>
@@ -367,7 +421,8 @@ void launch_fmt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
   const int tr = nb <= 4 ? 32 : nb <= 8 ? 16 : nb <= 16 ? 8 : nb <= 32 ? 4 : 2;
   if (nb <= kMaxStaged && staged_smem((int)nb, tr, a.t_nnz, a.num_leaves) <= kStagedSmemMax)
     launch_staged<DT, FMT>(a, (int)nb, st);
-  else if (!a.between_d) combine_kernel<DT, FMT><<<grid, kThreads, 0, st>>>(a);
+  else if (!a.between_d)
+    combine_kernel<DT, FMT><<<dim3(grid.x, grid.y, leaf_splits(a, kTR, a.num_leaves, 8)), kThreads, 0, st>>>(a);
 }
 
 template <int DT>
@@ -470,6 +525,81 @@ template <int TR>
 __global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
   extern __shared__ float4 acc4[];  // [c_blocks][TR][16], then the term list
   out_combine_body<TR>(a, blockIdx.x, blockIdx.y, acc4);
+}
+
+// Output pass by C block (Eq. 3.2 read per output block): CTA (x, y)
+// covers position tile x (kOutGatherRows x 64 entries of the leaf block) of
+// C blocks y, y + gridDim.y, ...; each thread forms 4 consecutive entries as
+// the sum over the block's terms, in leaf order, of w * M_r (the first term
+// assigned, as the stored-products pass does), then unscales once and
+// stores.  Every M_r is read once per C block it adds into.
+constexpr int kOutGatherRows = 16;
+
+__global__ void __launch_bounds__(kOutGatherRows * 16) out_gather_kernel(const OutArgs a) {
+  const EpilogueArgs& c = a.c;
+  const int64_t gx = (c.bn + kTC - 1) / kTC;
+  const int64_t bx = blockIdx.x % gx, by = blockIdx.x / gx;
+  const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15;
+  const int64_t lr = by * kOutGatherRows + tr, lc = bx * kTC + tq * 4;
+  if (lr >= c.bm || lc >= c.bn) return;
+  const int64_t leaf_stride = a.tp_a * a.tp_b;
+  const float* mpos = a.mbuf + lr * a.tp_b + lc;
+  const int pn = (int)a.pn;
+  for (int64_t k = blockIdx.y; k < a.c_blocks; k += gridDim.y) {
+    const int t0 = __ldg(a.g_start + k), t1 = __ldg(a.g_start + k + 1);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int t = t0;
+    for (; t + 4 <= t1; t += 4) {
+      float4 m[4];
+      float w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        w[u] = __ldg(a.g_coef + t + u);
+        m[u] = __ldg(reinterpret_cast<const float4*>(mpos + (int64_t)__ldg(a.g_leaf + t + u) * leaf_stride));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 x = make_float4(w[u] * m[u].x, w[u] * m[u].y, w[u] * m[u].z, w[u] * m[u].w);
+        if (t + u == t0) {
+          acc = x;
+        } else {
+          acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
+        }
+      }
+    }
+    for (; t < t1; ++t) {
+      const float w = __ldg(a.g_coef + t);
+      const float4 m = __ldg(reinterpret_cast<const float4*>(mpos + (int64_t)__ldg(a.g_leaf + t) * leaf_stride));
+      const float4 x = make_float4(w * m.x, w * m.y, w * m.z, w * m.w);
+      if (t == t0) {
+        acc = x;
+      } else {
+        acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
+      }
+    }
+    const int bi = (int)(k / pn), bj = (int)(k % pn);
+    const int64_t gi = bi * c.bm + lr, gj = bj * c.bn + lc;
+    if (gi >= c.M) continue;
+    float vv[4] = {acc.x, acc.y, acc.z, acc.w};
+    if (c.eA) {
+      const float fa = exp2i(__ldg(c.eA + gi));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) vv[j] *= fa;
+    }
+    if (c.eB) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (gj + j < c.N) vv[j] *= exp2i(__ldg(c.eB + gj + j));
+    }
+    float* dst = c.C + gi * c.ldc + gj;
+    if (c.vec_ok && lc + 4 <= c.bn && gj + 4 <= c.N) {
+      *reinterpret_cast<float4*>(dst) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (lc + j < c.bn && gj + j < c.N) dst[j] = vv[j];
+    }
+  }
 }
 
 // Batched form: CTA b belongs to problem p with start[p] <= b < start[p + 1]
@@ -728,6 +858,17 @@ cudaError_t launch_between_finalize(const int* cexp, const int* rexp, int* d, in
   if (n == 0) return cudaSuccess;
   KernelTimer timer("scale", st);
   between_finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cexp, rexp, d, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_out_gather(const OutArgs& a, cudaStream_t st) {
+  if (!a.g_start || a.c.bm > a.tp_a || a.c.bn > a.tp_b || a.tp_b % kTC != 0) return cudaErrorInvalidValue;
+  if (a.c.bm == 0 || a.c.bn == 0) return cudaSuccess;
+  KernelTimer timer("combine", st);
+  const int64_t tiles = ((a.c.bn + kTC - 1) / kTC) * ((a.c.bm + kOutGatherRows - 1) / kOutGatherRows);
+  if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  const unsigned gy = (unsigned)std::min<int64_t>(a.c_blocks, 65535);
+  out_gather_kernel<<<dim3((unsigned)tiles, gy), kOutGatherRows * 16, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -214,9 +214,15 @@ struct OutArgs {
   const int32_t* c_blk;
   const float* c_coef;
   int64_t c_nnz;
+  const int32_t* g_start;  // the C terms grouped by C block (Plan::gather_off), or NULL
+  const int32_t* g_leaf;
+  const float* g_coef;
 };
 constexpr int kMaxOutBlocks = 96;
 cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st);
+// The output pass for plans with more than kMaxOutBlocks C blocks: each CTA
+// forms one position tile of one C block from that block's term list.
+cudaError_t launch_out_gather(const OutArgs& a, cudaStream_t st);
 
 // Batched combination / output passes over `count` entries whose arguments
 // live in device memory; start[p] is the first CTA of entry p (combination:

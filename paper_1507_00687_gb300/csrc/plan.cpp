@@ -195,6 +195,29 @@ void build_lists(Plan* p) {
     }
     start[p->leaves] = (int32_t)at;
   }
+  // per-C-block lists, leaves in order
+  const int64_t nblk = p->pm * p->pn;
+  if (nblk > kMaxGatherBlocks) return;
+  std::vector<int32_t> count((size_t)nblk + 1, 0);
+  for (const LeafDesc& d : p->host)
+    for (int t = 0; t < d.nc; ++t) ++count[(size_t)((d.c_blk[t] >> 16) * p->pn + (d.c_blk[t] & 0xFFFF)) + 1];
+  for (int64_t k = 0; k < nblk; ++k) count[(size_t)k + 1] += count[(size_t)k];
+  const int64_t nnz = p->list_nnz[2];
+  p->gather_off = (int64_t)p->lists.size();
+  p->lists.resize(p->lists.size() + (size_t)(nblk + 1 + 2 * nnz));
+  int32_t* gstart = p->lists.data() + p->gather_off;
+  int32_t* gleaf = gstart + nblk + 1;
+  int32_t* gcoef = gleaf + nnz;
+  std::copy(count.begin(), count.end(), gstart);
+  for (int64_t r = 0; r < p->leaves; ++r) {
+    const LeafDesc& d = p->host[(size_t)r];
+    for (int t = 0; t < d.nc; ++t) {
+      const int64_t k = (d.c_blk[t] >> 16) * p->pn + (d.c_blk[t] & 0xFFFF);
+      const int32_t at = count[(size_t)k]++;
+      gleaf[at] = (int32_t)r;
+      std::memcpy(&gcoef[at], &d.c_coef[t], 4);
+    }
+  }
 }
 
 bool valid_leaf_format(int leaf_format) {

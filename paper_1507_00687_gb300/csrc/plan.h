@@ -22,6 +22,9 @@ constexpr int kMaxTerms = 64;
 // epilogue stores instead of accumulating.
 constexpr int32_t kFirstBit = (int32_t)0x80000000u;
 
+// Largest pm x pn for which the plan carries per-C-block term lists.
+constexpr int64_t kMaxGatherBlocks = (int64_t)1 << 20;
+
 struct LeafDesc {
   int32_t na, nb, nc, pad;
   int32_t a_blk[kMaxTerms];
@@ -63,6 +66,11 @@ struct Plan {
   std::vector<int32_t> lists;
   int64_t list_off[3] = {0, 0, 0};
   int64_t list_nnz[3] = {0, 0, 0};
+  // The C terms again, grouped by C block (what the gather output pass
+  // reads): int32 words at gather_off: start[pm pn + 1], then leaf[nnz],
+  // then coef[nnz] (float bits); block k's terms are [start[k], start[k+1])
+  // in leaf order.  gather_off < 0 when pm pn exceeds kMaxGatherBlocks.
+  int64_t gather_off = -1;
   // Device copy (on `device`): the LeafDesc array followed by `lists`.
   LeafDesc* dev = nullptr;
   int device = -1;
