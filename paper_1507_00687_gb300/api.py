@@ -358,12 +358,61 @@ class Autotuner:
         n = min(pts, key=lambda s: abs(np.log(s / g)))
         return self.table[(c, n)] * (M * K * N) / float(n ** 3)
 
-    def choose(self, M, K, N):
-        best = min((c for c in self.candidates if self._fits(c, M, K, N)), key=lambda c: self.predict(c, M, K, N))
+    def choose(self, M, K, N, max_instability: Optional[float] = None):
+        """Fastest predicted candidate; with ``max_instability``, only among
+        candidates whose relative instability (the factor over the classical
+        error bound, :func:`relative_instability`) is at most that value --
+        the accuracy axis of the choice."""
+        ok = [c for c in self.candidates if self._fits(c, M, K, N) and
+              (max_instability is None or not c or relative_instability(self._plans[c]) <= max_instability)]
+        best = min(ok, key=lambda c: self.predict(c, M, K, N))
         return list(best)
 
-    def plan(self, M, K, N) -> "Plan":
-        return self._plans[tuple(self.choose(M, K, N))]
+    def plan(self, M, K, N, max_instability: Optional[float] = None) -> "Plan":
+        return self._plans[tuple(self.choose(M, K, N, max_instability))]
+
+
+def relative_instability(plan: "Plan") -> float:
+    """Factor by which the plan's first-order error bound exceeds the
+    classical one for large K (Sec. 5.3): prod E / (prod k0)^2 for a uniform
+    plan (max_k xi_k / (prod k0)^2 for a tree)."""
+    info = plan.info()
+    return info["e_prod"] / float(info["pk"]) ** 2
+
+
+def algorithm_table(algorithms: dict, levels=(1, 2, 3, 4)) -> list:
+    """Stability and cost figures of Sec. 5.3 for candidate algorithms.
+
+    ``algorithms`` maps a name to a rule sequence; several rules are
+    composed into one base-case rule (e.g. Strassen then a classical <2,1,1>
+    step is a <4,2,2;14> rule).  Per algorithm: the base case <m0,k0,n0>,
+    rank R, nnz, Q and E of that rule from the library's plan compiler; the
+    stability exponent log_{m0 k0 n0} of E E' E'' with E', E'' those of its
+    two cyclic rotations (for a square base case the three are equal, giving
+    log_{n0} E); and per number of recursion steps L the fraction of
+    classical flops (R / (m0 k0 n0))^L and the relative instability
+    (E / k0^2)^L.  Host computation only (no GPU work)."""
+    from .rules import compose, rotate
+    rows = []
+    for name, seq in algorithms.items():
+        rules = [get_rule(r) if isinstance(r, str) else r for r in seq]
+        rule = rules[0]
+        for r in rules[1:]:
+            rule = compose(rule, r)
+        info = Plan([rule], "bf16").info()
+        m0, k0, n0 = info["pm"], info["pk"], info["pn"]
+        e_cyc = info["e_prod"]
+        rot = rule
+        for _ in range(2):
+            rot = rotate(rot)
+            e_cyc *= Plan([rot], "bf16").info()["e_prod"]
+        R = info["leaves"]
+        base = m0 * k0 * n0
+        rows.append({"name": name, "m0": m0, "k0": k0, "n0": n0, "R": R, "nnz": info["nnz"], "Q": info["q_sum"],
+                     "E": info["e_prod"], "stab_exp": float(np.log(e_cyc) / np.log(base)) if base > 1 else 0.0,
+                     "flop_fraction": {L: (R / base) ** L for L in levels},
+                     "relative_instability": {L: (info["e_prod"] / k0**2) ** L for L in levels}})
+    return rows
 
 
 def kernel_timing(enable: bool) -> None:

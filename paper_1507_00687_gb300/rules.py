@@ -127,6 +127,31 @@ def rotate(rule: BaseRule) -> BaseRule:
     return BaseRule(rule.name + "_rot", rule.n0, rule.m0, rule.k0, W, U, V, COL, ROW, COL)
 
 
+def compose(outer: BaseRule, inner: BaseRule) -> BaseRule:
+    """One rule for two recursion steps (Eq. 4.4 with L = 2): block (p1, q1)
+    of the outer split, then (p2, q2) of the inner one, is entry
+    (p1 m2 + p2, q1 k2 + q2) of the <m1 m2, k1 k2, n1 n2> base case, and
+    product (r1, r2) -- numbered r1 R2 + r2 -- has coefficients
+    X1[(p1, q1), r1] X2[(p2, q2), r2].  All tables row-major."""
+    def flat(X1, rows1, cols1, o1, X2, rows2, cols2, o2):
+        A = _to_row_major(X1, rows1, cols1, o1)
+        B = _to_row_major(X2, rows2, cols2, o2)
+        R1, R2 = A.shape[1], B.shape[1]
+        out = np.zeros((rows1 * rows2 * cols1 * cols2, R1 * R2))
+        for p1 in range(rows1):
+            for q1 in range(cols1):
+                for p2 in range(rows2):
+                    for q2 in range(cols2):
+                        row = (p1 * rows2 + p2) * (cols1 * cols2) + q1 * cols2 + q2
+                        out[row] = np.outer(A[p1 * cols1 + q1], B[p2 * cols2 + q2]).reshape(-1)
+        return out
+    o, i = outer, inner
+    return BaseRule(f"{o.name}*{i.name}", o.m0 * i.m0, o.k0 * i.k0, o.n0 * i.n0,
+                    flat(o.U, o.m0, o.k0, o.order_a, i.U, i.m0, i.k0, i.order_a),
+                    flat(o.V, o.k0, o.n0, o.order_b, i.V, i.k0, i.n0, i.order_b),
+                    flat(o.W, o.m0, o.n0, o.order_c, i.W, i.m0, i.n0, i.order_c))
+
+
 def variant(rule: BaseRule, XU: np.ndarray, XV: np.ndarray, XW: np.ndarray, name: str) -> BaseRule:
     """[[XU U, XV V, XW W]]: the rule with the rows of its tables mixed by XU,
     XV, XW in the rule's own entry order (Sec. 3.4: permutations of the

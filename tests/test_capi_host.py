@@ -213,3 +213,53 @@ def test_rotated_rules_accepted_with_invariant_quantities(native):
     s = api.Plan(["strassen"]).info()
     r = api.Plan([PR.rotate(PR.strassen())]).info()
     assert (r["q_sum"], r["e_prod"]) == (s["q_sum"], s["e_prod"])
+
+
+# ---------------------------------------------------------------- algorithm selection figures (Sec. 5.3)
+
+def test_algorithm_table_matches_table_1(native):
+    # Q, E, nnz, R against the Table 1 fixture and the printed stability
+    # exponents (two decimals): <2,2,2> classical 1, Strassen 3.58, the
+    # Strassen-classical <4,2,2> and <2,4,2> compositions 2.94, <3,2,3> 3.21.
+    from paper_1507_00687_gb300 import api
+    rows = api.algorithm_table({"classical222": ["classical222"], "strassen": ["strassen"],
+                                "strassen*classical211": ["strassen", "classical211"],
+                                "strassen*classical121": ["strassen", "classical121"],
+                                "fast323": ["fast323"]})
+    gold = {r[0]: r for r in (line.split() for line in open(os.path.join(ROOT, "tests", "golden", "table1.txt"))
+                              if line.strip() and not line.startswith("#"))}
+    printed = {"classical222": 1.0, "strassen": 3.58, "strassen*classical211": 2.94,
+               "strassen*classical121": 2.94, "fast323": 3.21}
+    for row in rows:
+        g = gold[row["name"]]
+        assert (row["m0"], row["k0"], row["n0"], row["R"], row["nnz"]) == tuple(int(x) for x in g[1:6])
+        assert (row["Q"], row["E"]) == (float(g[6]), float(g[7]))
+        assert round(row["stab_exp"], 2) == printed[row["name"]]
+        for L in (1, 2, 3, 4):
+            base = row["m0"] * row["k0"] * row["n0"]
+            assert row["flop_fraction"][L] == pytest.approx((row["R"] / base) ** L)
+            assert row["relative_instability"][L] == pytest.approx((row["E"] / row["k0"] ** 2) ** L)
+
+
+def test_relative_instability_of_plans(native):
+    from paper_1507_00687_gb300 import api
+    assert api.relative_instability(api.Plan(["strassen", "strassen"])) == 9.0
+    assert api.relative_instability(api.Plan(["winograd"])) == 18.0 / 4
+    import tree_cases as TC
+    lib, orc = TC.two_level(*TC.dalberto())
+    assert api.relative_instability(api.Plan.tree(lib)) == 96.0 / 16
+
+
+def test_package_compose_matches_oracle_compose(native):
+    # Package and oracle compose independently; the composite tables (both
+    # row-major, product r1 R2 + r2) must agree entry for entry, and the
+    # library accepts the composite with the quantities of the two-level plan
+    # (same E, leaves, nnz, base case).
+    from paper_1507_00687_gb300 import api
+    for a, b in (("strassen", "classical211"), ("fast323", "strassen"), ("winograd", "classical121")):
+        pc = PR.compose(PR.get(a), PR.get(b))
+        oc = OR.compose(_oracle_rule(a), _oracle_rule(b))
+        assert np.array_equal(pc.U, oc.U) and np.array_equal(pc.V, oc.V) and np.array_equal(pc.W, oc.W)
+        one, two = api.Plan([pc]).info(), api.Plan([a, b]).info()
+        for k in ("e_prod", "leaves", "nnz", "pm", "pk", "pn"):
+            assert one[k] == two[k], (a, b, k)

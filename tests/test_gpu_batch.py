@@ -126,6 +126,12 @@ def test_autotuner_choices_run_and_respect_cutoff(api):
         got = dev_values(api.multiply(plan, A, B))
         C, G = oracle_reference(dev_values(A), dev_values(B), names)
         assert_within(got, C, G, names, shape[1], "bf16", f"autotuned {names}")
+    # the accuracy axis: a cap on the relative instability keeps only the
+    # candidates whose error bound is within that factor of the classical one
+    for cap in (1.0, 3.0, 4.5, 1e9):
+        names = tuner.choose(2048, 2048, 2048, max_instability=cap)
+        assert not names or api.relative_instability(api.Plan(names, "bf16")) <= cap
+    assert tuner.choose(2048, 2048, 2048, max_instability=1.0) == []
 
 
 def test_batch_many_products_fused_epilogue(api):
