@@ -1103,10 +1103,10 @@ fmm_status fmm_scale_inside(const void* A, const void* B, int dtype, int64_t M, 
   return FMM_OK;
 }
 
-// The step pair O, I of Alg. 3 starting from d = 0 (M, K, N > 0), in the
-// order rows(A) -> eA, columns(A 2^-eA) -> d, columns(B) -> eB,
-// rows(2^-eB B) with d -> d: the same four reductions as fmm_scale_outside
-// then fmm_scale_inside with the same results.
+// The step pair O, I of Alg. 3 starting from d = 0 (M, K, N > 0): the same
+// exponents as fmm_scale_outside then fmm_scale_inside, in two launches
+// (rows of A and column panels of B; then, per k panel, the columns of A
+// and rows of B) that need no initialised outputs.
 static fmm_status scale_oi_from_zero(const void* A, const void* B, int dtype, int64_t M, int64_t K, int64_t N,
                                      int64_t lda, int64_t ldb, int32_t* eA, int32_t* d, int32_t* eB,
                                      cudaStream_t st) {
@@ -1114,16 +1114,9 @@ static fmm_status scale_oi_from_zero(const void* A, const void* B, int dtype, in
   if (lda < K || ldb < N) return FMM_ERR_SHAPE;
   int* status = status_ptr();
   if (!status) return FMM_ERR_CUDA;
-  if (!cuda_ok(launch_row_exp(A, dtype, M, K, lda, nullptr, +1, eA, kRowOStep, status, st), "row reduction"))
-    return FMM_ERR_CUDA;
-  if (!cuda_ok(launch_col_exp(A, dtype, M, K, lda, eA, -1, d, status, st), "column reduction"))
-    return FMM_ERR_CUDA;
-  if (!cuda_ok(launch_col_exp(B, dtype, K, N, ldb, nullptr, -1, eB, status, st), "column reduction"))
-    return FMM_ERR_CUDA;
-  if (launch_zero_sentinel(eB, N, st) != cudaSuccess) return FMM_ERR_CUDA;
-  if (!cuda_ok(launch_row_exp(B, dtype, K, N, ldb, eB, -1, d, kRowIStep, status, st), "row reduction"))
-    return FMM_ERR_CUDA;
-  return FMM_OK;
+  return cuda_ok(launch_oi_from_zero(A, B, dtype, M, K, N, lda, ldb, eA, d, eB, status, st), "O-I reductions")
+             ? FMM_OK
+             : FMM_ERR_CUDA;
 }
 
 fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype, int64_t M, int64_t K, int64_t N,

@@ -24,6 +24,10 @@ cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
 cudaError_t launch_scale_accept(const int* next, int* cur, int64_t n, int lo, int hi, int* ctl, cudaStream_t st);
 cudaError_t launch_scale_stop(int* ctl, int tested, int t, int* steps_out, cudaStream_t st);
 cudaError_t launch_zero_sentinel(int* p, int64_t n, cudaStream_t st);
+// The step pair O, I of Alg. 3 from no scaling (M, K, N > 0) in two
+// launches: eA, eB (O step) then d (I step); no initialisation needed.
+cudaError_t launch_oi_from_zero(const void* A, const void* B, int dt, int64_t M, int64_t K, int64_t N, int64_t lda,
+                                int64_t ldb, int* eA, int* d, int* eB, int* status, cudaStream_t st);
 
 // One problem of a batched reduction (rows: R x C, ld; shift: column
 // exponents for row reductions, row exponents for column reductions, sign

@@ -325,6 +325,130 @@ __global__ void __launch_bounds__(kColThreads) col_exp_batched_kernel(const Redu
   if (nf) atomicOr(status, kStatusNonfinite);
 }
 
+// ---------------------------------------------------------------- fused O-then-I from no scaling
+//
+// The step pair O, I of Alg. 3 on unscaled operands, in two launches with
+// no atomics and no initialisation of the outputs:
+//   oi_outside_kernel: CTAs [0, row_ctas) take rows of A, a warp per row
+//     (eA_i = e(max_k |A_ik|)); the others take 32-column panels of B over
+//     all K rows (eB_j = e(max_k |B_kj|)), the row groups meeting in shared
+//     memory.
+//   oi_inside_kernel: CTA p takes k in [32 p, 32 p + 32): the column maxima
+//     e(max_i 2^-eA_i |A_ik|) over all M rows of A, then the row maxima
+//     e(max_j |B_kj| 2^-eB_j) over all N columns of B, then d_k (Eq. 6.6).
+// The same exponents as the four separate reductions; each operand is read
+// twice, the second time mostly from L2.
+constexpr int kOIThreads = 512;
+constexpr int kOIBatch = 8;  // rows of loads in flight per thread
+
+// Running maxima of columns c0 + 4 tq .. + 3 (tq = thread mod P/4) over the
+// rows tr, tr + G, ... (tr = thread / (P/4), G = 512 / (P/4)) of the R x C
+// matrix X; with SHIFT each row's entries are shifted by -re[row].
+template <int DT, bool SHIFT, int P>
+__device__ __forceinline__ void panel_max(const void* X, int64_t R, int64_t C, int64_t ld, int64_t c0, const int* re,
+                                          bool vec, int (&m)[4], uint32_t (&mb)[4], bool* nf) {
+  constexpr int kTq = P / 4, kG = kOIThreads / kTq;
+  const int tq = threadIdx.x % kTq, tr = threadIdx.x / kTq;
+  const int64_t c = c0 + 4 * tq;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    m[t] = kZeroExp;
+    mb[t] = 0u;
+  }
+  auto take = [&](uint4 v, int sh) {
+    uint32_t b[4];
+    unpack4<DT>(v, b);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if constexpr (SHIFT) m[t] = max(m[t], fexp_fast<DT>(b[t], nf) + sh);
+      else mb[t] = max(mb[t], abs_bits<DT>(b[t]));
+    }
+  };
+  int64_t i = tr;
+  for (; i + (int64_t)kG * (kOIBatch - 1) < R; i += (int64_t)kG * kOIBatch) {
+    uint4 v[kOIBatch];
+    int sh[kOIBatch];
+#pragma unroll
+    for (int u = 0; u < kOIBatch; ++u) v[u] = raw4_guarded<DT>(X, (i + (int64_t)kG * u) * ld, c, C, vec);
+#pragma unroll
+    for (int u = 0; u < kOIBatch; ++u) sh[u] = SHIFT ? -__ldg(re + i + (int64_t)kG * u) : 0;
+#pragma unroll
+    for (int u = 0; u < kOIBatch; ++u) take(v[u], sh[u]);
+  }
+  for (; i < R; i += kG) take(raw4_guarded<DT>(X, i * ld, c, C, vec), SHIFT ? -__ldg(re + i) : 0);
+}
+
+// Combine the per-thread maxima of panel_max over the row groups: returns,
+// for threads 0 .. P-1, the maximum of column c0 + threadIdx.x (as an
+// unshifted |x| key decoded to an exponent, or as a shifted exponent).
+template <int DT, bool SHIFT, int P>
+__device__ __forceinline__ int panel_reduce(const int (&m)[4], const uint32_t (&mb)[4], int* red, bool* nf) {
+  constexpr int kTq = P / 4, kG = kOIThreads / kTq;
+  const int tq = threadIdx.x % kTq, tr = threadIdx.x / kTq;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) red[tr * P + 4 * tq + t] = SHIFT ? m[t] : (int)mb[t];
+  __syncthreads();
+  int e = kZeroExp;
+  if (threadIdx.x < P) {
+    if constexpr (SHIFT) {
+      for (int g = 0; g < kG; ++g) e = max(e, red[g * P + threadIdx.x]);
+    } else {
+      uint32_t k = 0;
+      for (int g = 0; g < kG; ++g) k = max(k, (uint32_t)red[g * P + threadIdx.x]);
+      e = fexp_of_abs_max<DT>(k, nf);
+    }
+  }
+  return e;
+}
+
+constexpr int kOIPanelB = 32;  // columns of B per panel CTA of the O step
+constexpr int kOIPanelK = 32;  // k per CTA of the I step
+
+template <int DT>
+__global__ void __launch_bounds__(kOIThreads) oi_outside_kernel(const void* A, const void* B, int64_t M, int64_t K,
+                                                                int64_t N, int64_t lda, int64_t ldb, int* eA, int* eB,
+                                                                int row_ctas, int vec_a, int vec_b, int* status) {
+  __shared__ int red[(kOIThreads / (kOIPanelB / 4)) * kOIPanelB];
+  bool nf = false;
+  if ((int)blockIdx.x < row_ctas) {
+    constexpr int kWarps = kOIThreads / 32;
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); i < M; i += (int64_t)row_ctas * kWarps)
+      row_exp_one<DT, false>(A, K, lda, nullptr, 0, eA, kRowOStep, vec_a != 0, i, lane, &nf);
+  } else {
+    const int64_t c0 = (int64_t)(blockIdx.x - row_ctas) * kOIPanelB;
+    int m[4];
+    uint32_t mb[4];
+    panel_max<DT, false, kOIPanelB>(B, K, N, ldb, c0, nullptr, vec_b != 0, m, mb, &nf);
+    const int e = panel_reduce<DT, false, kOIPanelB>(m, mb, red, &nf);
+    if (threadIdx.x < kOIPanelB && c0 + threadIdx.x < N) eB[c0 + threadIdx.x] = e <= kZeroThreshold ? 0 : e;
+  }
+  if (nf) atomicOr(status, kStatusNonfinite);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kOIThreads) oi_inside_kernel(const void* A, const void* B, int64_t M, int64_t K,
+                                                               int64_t N, int64_t lda, int64_t ldb, const int* eA,
+                                                               const int* eB, int* d, int vec_a, int vec_b,
+                                                               int* status) {
+  __shared__ int red[(kOIThreads / (kOIPanelK / 4)) * kOIPanelK];
+  bool nf = false;
+  const int64_t k0 = (int64_t)blockIdx.x * kOIPanelK;
+  // e(max_i 2^-eA_i |A_ik|) for the CTA's k, parked in d until the row pass
+  int m[4];
+  uint32_t mb[4];
+  panel_max<DT, true, kOIPanelK>(A, M, K, lda, k0, eA, vec_a != 0, m, mb, &nf);
+  const int ea = panel_reduce<DT, true, kOIPanelK>(m, mb, red, &nf);
+  if (threadIdx.x < kOIPanelK && k0 + threadIdx.x < K) d[k0 + threadIdx.x] = ea;
+  __syncthreads();
+  // d_k = floor((e(max_j |B_kj| 2^-eB_j) - e_A) / 2): a warp per row of B
+  constexpr int kWarps = kOIThreads / 32;
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = k0 + (threadIdx.x >> 5); k < min(K, k0 + kOIPanelK); k += kWarps)
+    row_exp_one<DT, true>(B, N, ldb, eB, -1, d, kRowIStep, vec_b != 0, k, lane, &nf);
+  if (nf) atomicOr(status, kStatusNonfinite);
+}
+
 // Operand preparation (the apply pass of Algs. 1-3, plus blocking): each
 // thread writes 4 consecutive output columns of one output row (row_pad and
 // col_pad are multiples of 4, so a group never straddles two blocks), reading
@@ -505,6 +629,50 @@ cudaError_t launch_col_exp_batched(const ReduceArgs* args, const int64_t* start,
     default: { FMM_COLB(kF16, 2) break; }
   }
 #undef FMM_COLB
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oi_from_zero(const void* A, const void* B, int dt, int64_t M, int64_t K, int64_t N, int64_t lda,
+                                int64_t ldb, int* eA, int* d, int* eB, int* status, cudaStream_t st) {
+  if (M == 0 || K == 0 || N == 0) return cudaErrorInvalidValue;
+  const int vec_a = vec_aligned(A, lda, dt) ? 1 : 0, vec_b = vec_aligned(B, ldb, dt) ? 1 : 0;
+  const int64_t row_ctas = std::min<int64_t>((M + 15) / 16, (int64_t)sm_count() * 4);
+  const int64_t panels = (N + kOIPanelB - 1) / kOIPanelB;
+  const int64_t kctas = (K + kOIPanelK - 1) / kOIPanelK;
+  if (row_ctas + panels > 0x7FFFFFFF || kctas > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  {
+    KernelTimer timer("scale", st);
+    switch (dt) {
+      case kF32:
+        oi_outside_kernel<kF32><<<(unsigned)(row_ctas + panels), kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB,
+                                                                                       (int)row_ctas, vec_a, vec_b, status);
+        break;
+      case kBF16:
+        oi_outside_kernel<kBF16><<<(unsigned)(row_ctas + panels), kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB,
+                                                                                        (int)row_ctas, vec_a, vec_b,
+                                                                                        status);
+        break;
+      default:
+        oi_outside_kernel<kF16><<<(unsigned)(row_ctas + panels), kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB,
+                                                                                       (int)row_ctas, vec_a, vec_b, status);
+        break;
+    }
+  }
+  KernelTimer timer("scale", st);
+  switch (dt) {
+    case kF32:
+      oi_inside_kernel<kF32><<<(unsigned)kctas, kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB, d, vec_a, vec_b,
+                                                                     status);
+      break;
+    case kBF16:
+      oi_inside_kernel<kBF16><<<(unsigned)kctas, kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB, d, vec_a, vec_b,
+                                                                      status);
+      break;
+    default:
+      oi_inside_kernel<kF16><<<(unsigned)kctas, kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB, d, vec_a, vec_b,
+                                                                     status);
+      break;
+  }
   return cudaGetLastError();
 }
 
