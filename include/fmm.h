@@ -394,12 +394,16 @@ fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc,
  * Per-kernel timing, for measurement.  fmm_kernel_timing(1) starts
  * recording (discarding earlier records): every kernel the library launches
  * from then on is bracketed by two CUDA events recorded on its launching
- * stream; fmm_kernel_timing(0) stops recording.  fmm_kernel_timing_read
+ * stream; fmm_kernel_timing(0) stops recording.  Any other value in 2..31
+ * records only the kinds whose bits it sets: 2 "scale" (scaling reductions
+ * and fills), 4 "prepare" (operand copies of the load-stage schedule), 8
+ * "combine" (the combination and output passes), 16 "multiply" (the
+ * tensor-core kernels); FMM_ERR_ARG outside 0..31.  fmm_kernel_timing_read
  * waits for the recorded events and returns the summed device time (ms)
- * and the number of launches of one kind -- "scale" (scaling reductions and
- * fills), "prepare" (operand copies of the load-stage schedule), "combine"
- * (the combination pass), "multiply" (the tensor-core kernels) -- or of all
- * kinds when kind is NULL or "".  The library's own work is unchanged; the
+ * and the number of launches of one kind, or of all kinds when kind is NULL
+ * or "".  The library's own work is unchanged, but an event between two
+ * launches keeps the second from starting before the first ends (the
+ * kernels otherwise overlap one's start with the other's end), and the
  * events add a few microseconds of host time per launch.
  */
 fmm_status fmm_kernel_timing(int enable);

@@ -415,9 +415,14 @@ def algorithm_table(algorithms: dict, levels=(1, 2, 3, 4)) -> list:
     return rows
 
 
-def kernel_timing(enable: bool) -> None:
-    """Start (discarding earlier records) or stop per-kernel event timing."""
-    N.check(N.lib().fmm_kernel_timing(1 if enable else 0), "fmm_kernel_timing")
+TIMING_KINDS = {"scale": 2, "prepare": 4, "combine": 8, "multiply": 16}
+
+
+def kernel_timing(enable: bool, kinds: Sequence[str] = ()) -> None:
+    """Start (discarding earlier records) or stop per-kernel event timing;
+    ``kinds`` restricts the recording to those kinds (default: all)."""
+    mask = (sum(TIMING_KINDS[k] for k in kinds) if kinds else 1) if enable else 0
+    N.check(N.lib().fmm_kernel_timing(mask), "fmm_kernel_timing")
 
 
 def kernel_timing_read(kind: str = "") -> tuple:

@@ -138,6 +138,8 @@ constexpr int kTermBatch = 4;
 
 template <int DT, int FMT>
 __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs a) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t r0 = (int64_t)blockIdx.y * kTR, c0 = (int64_t)blockIdx.x * kTC;
   const int tid = threadIdx.x;
   const int tr = tid >> 4, tc = (tid & 15) * 4;  // rows tr, tr + 16; columns tc .. tc + 3
@@ -322,6 +324,8 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
 template <int DT, int FMT, int TR, int RPT, bool BETWEEN>
 __global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_kernel(const CombineArgs a) {
   extern __shared__ float4 tile4[];  // [block][TR][16], then the term list
+  pdl_wait();
+  pdl_trigger();
   // blockIdx.z takes a contiguous range of the leaves (the input tiles are
   // staged once per range)
   const int R = (int)a.num_leaves;
@@ -394,9 +398,8 @@ void launch_staged_tr_b(const CombineArgs& a, int nb, cudaStream_t st) {
     attr_done[dev] = true;
   }
   const dim3 grid((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / TR));
-  combine_staged_kernel<DT, FMT, TR, RPT, BETWEEN>
-      <<<dim3(grid.x, grid.y, leaf_splits(a, TR, a.num_leaves, 4)), TR * 16 / RPT,
-         staged_smem(nb, TR, a.t_nnz, a.num_leaves), st>>>(a);
+  launch_pdl(combine_staged_kernel<DT, FMT, TR, RPT, BETWEEN>, dim3(grid.x, grid.y, leaf_splits(a, TR, a.num_leaves, 4)),
+             dim3(TR * 16 / RPT), staged_smem(nb, TR, a.t_nnz, a.num_leaves), st, a);
 }
 
 template <int DT, int FMT, int TR, int RPT = 1>
@@ -422,7 +425,8 @@ void launch_fmt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
   if (nb <= kMaxStaged && staged_smem((int)nb, tr, a.t_nnz, a.num_leaves) <= kStagedSmemMax)
     launch_staged<DT, FMT>(a, (int)nb, st);
   else if (!a.between_d)
-    combine_kernel<DT, FMT><<<dim3(grid.x, grid.y, leaf_splits(a, kTR, a.num_leaves, 8)), kThreads, 0, st>>>(a);
+    launch_pdl(combine_kernel<DT, FMT>, dim3(grid.x, grid.y, leaf_splits(a, kTR, a.num_leaves, 8)), dim3(kThreads), 0,
+               st, a);
 }
 
 template <int DT>
@@ -524,6 +528,8 @@ __device__ __forceinline__ void out_combine_body(const OutArgs& a, int64_t bx, i
 template <int TR>
 __global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
   extern __shared__ float4 acc4[];  // [c_blocks][TR][16], then the term list
+  pdl_wait();
+  pdl_trigger();
   out_combine_body<TR>(a, blockIdx.x, blockIdx.y, acc4);
 }
 
@@ -536,6 +542,8 @@ __global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
 constexpr int kOutGatherRows = 16;
 
 __global__ void __launch_bounds__(kOutGatherRows * 16) out_gather_kernel(const OutArgs a) {
+  pdl_wait();
+  pdl_trigger();
   const EpilogueArgs& c = a.c;
   const int64_t gx = (c.bn + kTC - 1) / kTC;
   const int64_t bx = blockIdx.x % gx, by = blockIdx.x / gx;
@@ -868,8 +876,7 @@ cudaError_t launch_out_gather(const OutArgs& a, cudaStream_t st) {
   const int64_t tiles = ((a.c.bn + kTC - 1) / kTC) * ((a.c.bm + kOutGatherRows - 1) / kOutGatherRows);
   if (tiles > 0x7FFFFFFF) return cudaErrorInvalidValue;
   const unsigned gy = (unsigned)std::min<int64_t>(a.c_blocks, 65535);
-  out_gather_kernel<<<dim3((unsigned)tiles, gy), kOutGatherRows * 16, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(out_gather_kernel, dim3((unsigned)tiles, gy), dim3(kOutGatherRows * 16), 0, st, a);
 }
 
 cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st) {
@@ -893,7 +900,7 @@ cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st) {
       attr_done[dev] = true;
     }
     const unsigned gy = (unsigned)((a.c.bm + TR - 1) / TR);
-    out_combine_kernel<TR><<<dim3(gx, gy), TR * 16, (size_t)nb * TR * 256 + list_bytes, st>>>(a);
+    launch_pdl(out_combine_kernel<TR>, dim3(gx, gy), dim3(TR * 16), (size_t)nb * TR * 256 + list_bytes, st, a);
   };
   if (nb <= 6) go(std::integral_constant<int, 32>());
   else if (nb <= 12) go(std::integral_constant<int, 16>());

@@ -3,9 +3,39 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 namespace fmm {
+
+// Programmatic dependent launch (griddepcontrol, sm_90 and later).  A
+// kernel launched with launch_pdl may start while the previous kernel of
+// its stream is finishing; pdl_wait() then blocks until that kernel has
+// completed and its writes are visible, so every such kernel calls it
+// before its first global-memory access that depends on earlier work (it
+// returns at once for a kernel launched the ordinary way).  pdl_trigger()
+// lets the next kernel of the stream begin launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch `kernel` with programmatic stream serialization allowed: its
+// blocks may be scheduled before the previous kernel of the stream has
+// finished (they must call pdl_wait first).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Device status bits (OR-ed into the word fmm_sync_status reads).
 constexpr int kStatusTimeout = 1;

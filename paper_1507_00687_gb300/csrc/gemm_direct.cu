@@ -146,6 +146,10 @@ __global__ void __launch_bounds__(kThreads, 1) direct_fmm_kernel(const __grid_co
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // the set-up above overlaps the previous kernel's tail; its outputs (the
+  // combined operands) are read from here on
+  pdl_wait();
+  pdl_trigger();
 
   // Work units of this CTA: global units u = blockIdx.x, + gridDim.x, ...;
   // a unit is one tile of one leaf product (problems with stored products)
@@ -366,8 +370,7 @@ cudaError_t launch_cfg(const DirectArgs& a, const DirectArgs* tab, const int64_t
   if (units == 0) return cudaSuccess;
   const int64_t grid = std::min<int64_t>(units, device_sm_count());
   KernelTimer timer("multiply", st);
-  kern<<<(unsigned)grid, kThreads, C::kSmem, st>>>(L);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3((unsigned)grid), dim3(kThreads), C::kSmem, st, L);
 }
 
 // Operand layouts used: forward (A K-major, B MN-major), dA = dC B^T (both

@@ -409,6 +409,8 @@ __global__ void __launch_bounds__(kOIThreads) oi_outside_kernel(const void* A, c
                                                                 int64_t N, int64_t lda, int64_t ldb, int* eA, int* eB,
                                                                 int row_ctas, int vec_a, int vec_b, int* status) {
   __shared__ int red[(kOIThreads / (kOIPanelB / 4)) * kOIPanelB];
+  pdl_wait();
+  pdl_trigger();
   bool nf = false;
   if ((int)blockIdx.x < row_ctas) {
     constexpr int kWarps = kOIThreads / 32;
@@ -432,6 +434,8 @@ __global__ void __launch_bounds__(kOIThreads) oi_inside_kernel(const void* A, co
                                                                const int* eB, int* d, int vec_a, int vec_b,
                                                                int* status) {
   __shared__ int red[(kOIThreads / (kOIPanelK / 4)) * kOIPanelK];
+  pdl_wait();
+  pdl_trigger();
   bool nf = false;
   const int64_t k0 = (int64_t)blockIdx.x * kOIPanelK;
   // e(max_i 2^-eA_i |A_ik|) for the CTA's k, parked in d until the row pass
@@ -644,33 +648,26 @@ cudaError_t launch_oi_from_zero(const void* A, const void* B, int dt, int64_t M,
     KernelTimer timer("scale", st);
     switch (dt) {
       case kF32:
-        oi_outside_kernel<kF32><<<(unsigned)(row_ctas + panels), kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB,
-                                                                                       (int)row_ctas, vec_a, vec_b, status);
+        launch_pdl(oi_outside_kernel<kF32>, dim3((unsigned)(row_ctas + panels)), dim3(kOIThreads), 0, st, A, B, M, K, N, lda, ldb, eA, eB, (int)row_ctas, vec_a, vec_b, status);
         break;
       case kBF16:
-        oi_outside_kernel<kBF16><<<(unsigned)(row_ctas + panels), kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB,
-                                                                                        (int)row_ctas, vec_a, vec_b,
-                                                                                        status);
+        launch_pdl(oi_outside_kernel<kBF16>, dim3((unsigned)(row_ctas + panels)), dim3(kOIThreads), 0, st, A, B, M, K, N, lda, ldb, eA, eB, (int)row_ctas, vec_a, vec_b, status);
         break;
       default:
-        oi_outside_kernel<kF16><<<(unsigned)(row_ctas + panels), kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB,
-                                                                                       (int)row_ctas, vec_a, vec_b, status);
+        launch_pdl(oi_outside_kernel<kF16>, dim3((unsigned)(row_ctas + panels)), dim3(kOIThreads), 0, st, A, B, M, K, N, lda, ldb, eA, eB, (int)row_ctas, vec_a, vec_b, status);
         break;
     }
   }
   KernelTimer timer("scale", st);
   switch (dt) {
     case kF32:
-      oi_inside_kernel<kF32><<<(unsigned)kctas, kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB, d, vec_a, vec_b,
-                                                                     status);
+      launch_pdl(oi_inside_kernel<kF32>, dim3((unsigned)kctas), dim3(kOIThreads), 0, st, A, B, M, K, N, lda, ldb, (const int*)eA, (const int*)eB, d, vec_a, vec_b, status);
       break;
     case kBF16:
-      oi_inside_kernel<kBF16><<<(unsigned)kctas, kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB, d, vec_a, vec_b,
-                                                                      status);
+      launch_pdl(oi_inside_kernel<kBF16>, dim3((unsigned)kctas), dim3(kOIThreads), 0, st, A, B, M, K, N, lda, ldb, (const int*)eA, (const int*)eB, d, vec_a, vec_b, status);
       break;
     default:
-      oi_inside_kernel<kF16><<<(unsigned)kctas, kOIThreads, 0, st>>>(A, B, M, K, N, lda, ldb, eA, eB, d, vec_a, vec_b,
-                                                                     status);
+      launch_pdl(oi_inside_kernel<kF16>, dim3((unsigned)kctas), dim3(kOIThreads), 0, st, A, B, M, K, N, lda, ldb, (const int*)eA, (const int*)eB, d, vec_a, vec_b, status);
       break;
   }
   return cudaGetLastError();

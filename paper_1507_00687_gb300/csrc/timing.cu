@@ -1,6 +1,6 @@
 // Per-kernel timing (fmm_kernel_timing / fmm_kernel_timing_read): while
-// enabled, every kernel the library launches is bracketed by a pair of CUDA
-// events recorded on its launching stream, so that a caller can attribute
+// enabled, every kernel of the selected kinds the library launches is
+// bracketed by a pair of CUDA events recorded on its launching stream, so that a caller can attribute
 // the device time of one library call to its kernels (combination pass,
 // multiply, scaling reductions ...).  Measurement only; off by default.
 #include <cstring>
@@ -22,8 +22,16 @@ struct Record {
 };
 
 std::mutex g_mu;
-bool g_on = false;
+int g_mask = 0;  // kinds being recorded (bits of kind_bit)
 std::vector<Record> g_records;
+
+int kind_bit(const char* kind) {
+  if (std::strcmp(kind, "scale") == 0) return 2;
+  if (std::strcmp(kind, "prepare") == 0) return 4;
+  if (std::strcmp(kind, "combine") == 0) return 8;
+  if (std::strcmp(kind, "multiply") == 0) return 16;
+  return 0;
+}
 
 void release_all() {
   for (auto& r : g_records) {
@@ -37,7 +45,7 @@ void release_all() {
 
 KernelTimer::KernelTimer(const char* kind, cudaStream_t st) : kind_(kind), st_(st) {
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_on) return;
+  if (!(g_mask & kind_bit(kind))) return;
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess) return;
   if (cudaEventCreate(&b) != cudaSuccess) {
@@ -63,9 +71,10 @@ using namespace fmm;
 extern "C" {
 
 fmm_status fmm_kernel_timing(int enable) {
+  if (enable < 0 || enable > 31) return FMM_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_mu);
   if (enable) release_all();
-  g_on = enable != 0;
+  g_mask = enable == 1 ? 30 : enable;
   return FMM_OK;
 }
 
