@@ -344,7 +344,7 @@ constexpr int kOIBatch = 8;  // rows of loads in flight per thread
 // Running maxima of columns c0 + 4 tq .. + 3 (tq = thread mod P/4) over the
 // rows tr, tr + G, ... (tr = thread / (P/4), G = 512 / (P/4)) of the R x C
 // matrix X; with SHIFT each row's entries are shifted by -re[row].
-template <int DT, bool SHIFT, int P>
+template <int DT, bool SHIFT, int P, int kOIBatch = kOIBatch>
 __device__ __forceinline__ void panel_max(const void* X, int64_t R, int64_t C, int64_t ld, int64_t c0, const int* re,
                                           bool vec, int (&m)[4], uint32_t (&mb)[4], bool* nf) {
   constexpr int kTq = P / 4, kG = kOIThreads / kTq;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kOIThreads) oi_inside_kernel(const void* A, co
   // e(max_i 2^-eA_i |A_ik|) for the CTA's k, parked in d until the row pass
   int m[4];
   uint32_t mb[4];
-  panel_max<DT, true, kOIPanelK>(A, M, K, lda, k0, eA, vec_a != 0, m, mb, &nf);
+  panel_max<DT, true, kOIPanelK, 2 * kOIBatch>(A, M, K, lda, k0, eA, vec_a != 0, m, mb, &nf);
   const int ea = panel_reduce<DT, true, kOIPanelK>(m, mb, red, &nf);
   if (threadIdx.x < kOIPanelK && k0 + threadIdx.x < K) d[k0 + threadIdx.x] = ea;
   __syncthreads();
