@@ -110,7 +110,7 @@ constexpr int kRowWarps = 8;
 constexpr int kRowBatch = 8;
 
 // Row i, one warp (lane = its lane index).
-template <int DT, bool SHIFT>
+template <int DT, bool SHIFT, int kRowBatch = kRowBatch>
 __device__ __forceinline__ void row_exp_one(const void* X, int64_t C, int64_t ld, const int* ce, int cs, int* out,
                                             int mode, bool vec_ok, int64_t i, int lane, bool* nf) {
   // the vector path also needs the column exponents 16-byte aligned
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kColThreads) col_exp_batched_kernel(const Redu
 //     (eA_i = e(max_k |A_ik|)); the others take 32-column panels of B over
 //     all K rows (eB_j = e(max_k |B_kj|)), the row groups meeting in shared
 //     memory.
-//   oi_inside_kernel: CTA p takes k in [32 p, 32 p + 32): the column maxima
+//   oi_inside_kernel: CTA p takes k in [16 p, 16 p + 16): the column maxima
 //     e(max_i 2^-eA_i |A_ik|) over all M rows of A, then the row maxima
 //     e(max_j |B_kj| 2^-eB_j) over all N columns of B, then d_k (Eq. 6.6).
 // The same exponents as the four separate reductions; each operand is read
@@ -402,7 +402,7 @@ __device__ __forceinline__ int panel_reduce(const int (&m)[4], const uint32_t (&
 }
 
 constexpr int kOIPanelB = 32;  // columns of B per panel CTA of the O step
-constexpr int kOIPanelK = 32;  // k per CTA of the I step
+constexpr int kOIPanelK = 16;  // k per CTA of the I step
 
 template <int DT>
 __global__ void __launch_bounds__(kOIThreads) oi_outside_kernel(const void* A, const void* B, int64_t M, int64_t K,
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kOIThreads) oi_outside_kernel(const void* A, c
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kOIThreads) oi_inside_kernel(const void* A, const void* B, int64_t M, int64_t K,
+__global__ void __launch_bounds__(kOIThreads, 2) oi_inside_kernel(const void* A, const void* B, int64_t M, int64_t K,
                                                                int64_t N, int64_t lda, int64_t ldb, const int* eA,
                                                                const int* eB, int* d, int vec_a, int vec_b,
                                                                int* status) {
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kOIThreads) oi_inside_kernel(const void* A, co
   // e(max_i 2^-eA_i |A_ik|) for the CTA's k, parked in d until the row pass
   int m[4];
   uint32_t mb[4];
-  panel_max<DT, true, kOIPanelK, 2 * kOIBatch>(A, M, K, lda, k0, eA, vec_a != 0, m, mb, &nf);
+  panel_max<DT, true, kOIPanelK>(A, M, K, lda, k0, eA, vec_a != 0, m, mb, &nf);
   const int ea = panel_reduce<DT, true, kOIPanelK>(m, mb, red, &nf);
   if (threadIdx.x < kOIPanelK && k0 + threadIdx.x < K) d[k0 + threadIdx.x] = ea;
   __syncthreads();
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kOIThreads) oi_inside_kernel(const void* A, co
   constexpr int kWarps = kOIThreads / 32;
   const int lane = threadIdx.x & 31;
   for (int64_t k = k0 + (threadIdx.x >> 5); k < min(K, k0 + kOIPanelK); k += kWarps)
-    row_exp_one<DT, true>(B, N, ldb, eB, -1, d, kRowIStep, vec_b != 0, k, lane, &nf);
+    row_exp_one<DT, true, 4>(B, N, ldb, eB, -1, d, kRowIStep, vec_b != 0, k, lane, &nf);
   if (nf) atomicOr(status, kStatusNonfinite);
 }
 
