@@ -243,6 +243,50 @@ def growth(A: np.ndarray, B: np.ndarray, plan: Optional[Node], between: bool = F
     return _recurse(np.abs(Ap), np.abs(Bp), abs_plan(plan), classical, np.float64, dvecs)[:M, :N]
 
 
+def growth_entries(A: np.ndarray, B: np.ndarray, rules: Sequence[Rule], rows, cols) -> np.ndarray:
+    """``growth`` of the uniform plan ``rules`` at the entries (rows[s],
+    cols[s]) only, from the flattened rule of Eq. 4.4 (the levels composed
+    into one <pm, pk, pn; R^L> rule): with A, B zero-padded to the block
+    grid, entry (i, j) of C block (bi, bj) at position (li, lj) is
+        G_ij = sum_r |W_(bi,bj),r| (sum_(p,q) |U_(p,q),r| |A_(p bm + li, q block)|)
+                                   . (sum_(p,q) |V_(p,q),r| |B_(p block, q bn + lj)|)
+    -- the same sums as the recursive evaluation, since every term is
+    nonnegative.  Each sample costs O(R^L K / pk) instead of a full product,
+    so it serves products too large for ``growth``."""
+    from .rules import compose
+    comp = canonical(rules[0])
+    for r in rules[1:]:
+        comp = compose(comp, r)
+    pm, pk, pn = comp.m0, comp.k0, comp.n0
+    M, K = A.shape
+    N = B.shape[1]
+    bm, bk, bn = -(-M // pm), -(-K // pk), -(-N // pn)
+    Ua, Va, Wa = np.abs(comp.U), np.abs(comp.V), np.abs(comp.W)
+    out = np.zeros(len(rows))
+    for s, (i, j) in enumerate(zip(rows, cols)):
+        bi, li = divmod(int(i), bm)
+        bj, lj = divmod(int(j), bn)
+        # |A| row segments of every block: (pm pk) x bk, zero past the edge
+        Aseg = np.zeros((pm, pk * bk))
+        for p in range(pm):
+            r_ = p * bm + li
+            if r_ < M:
+                Aseg[p, :K] = np.abs(A[r_, :])
+        Aseg = Aseg.reshape(pm * pk, bk)
+        Bseg = np.zeros((pn, pk * bk))
+        for q in range(pn):
+            c_ = q * bn + lj
+            if c_ < N:
+                Bseg[q, :K] = np.abs(B[:, c_])
+        # B block (p, q) at flattened index p pn + q holds column lj of block column q
+        Bseg = Bseg.reshape(pn, pk, bk).transpose(1, 0, 2).reshape(pk * pn, bk)
+        S = Ua.T @ Aseg          # R x bk
+        T = Va.T @ Bseg          # R x bk
+        Mr = np.einsum("rk,rk->r", S, T)
+        out[s] = Wa[bi * pn + bj] @ Mr
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Leaf products in reduced precision (emulation of the leaf formats)
 # ---------------------------------------------------------------------------

@@ -215,3 +215,29 @@ def test_between_exponents_balance_each_pair():
             assert et - es in (0, 1), (j, k, et - es)
             checked += 1
     assert checked > 20
+
+
+def _R(name):
+    return {"strassen": R.strassen, "winograd": R.winograd, "fast323": R.fast323,
+            "classical121": lambda: R.classical(1, 2, 1), "classical211": lambda: R.classical(2, 1, 1)}[name]()
+
+
+@pytest.mark.parametrize("names", [["strassen"], ["winograd", "classical121"], ["strassen", "fast323"],
+                                   ["winograd", "classical121", "strassen", "classical211"]])
+def test_growth_entries_equal_full_growth(names):
+    # The sampled-entry growth (flattened rule, Eq. 4.4) against the
+    # recursive evaluation of Eq. 3.2 on |A|, |B|, including padded edges.
+    rules = [_R(n) for n in names]
+    g = np.random.default_rng(7)
+    M, K, N = 37, 53, 41
+    A = g.uniform(-1, 1, size=(M, K))
+    B = g.uniform(-1, 1, size=(K, N))
+    full = F.growth(A, B, F.uniform(rules))
+    rows = g.integers(0, M, size=40)
+    cols = g.integers(0, N, size=40)
+    part = F.growth_entries(A, B, rules, rows, cols)
+    assert np.allclose(part, full[rows, cols], rtol=1e-12, atol=0)
+    # the growth of a product of nonnegative matrices is the product itself
+    # when every coefficient is nonnegative and each entry lies in one term
+    Ac, Bc = np.abs(A), np.abs(B)
+    assert np.allclose(F.growth_entries(Ac, Bc, [R.classical(1, 2, 1)], rows, cols), (Ac @ Bc)[rows, cols])
