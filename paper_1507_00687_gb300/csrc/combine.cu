@@ -533,6 +533,92 @@ __global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
   out_combine_body<TR>(a, blockIdx.x, blockIdx.y, acc4);
 }
 
+// Output pass with the accumulators in registers, for plans with at most
+// NB C blocks: the leaves' W coefficients are laid out densely in shared
+// memory (sW[r][k], zero where leaf r does not add into block k).  A CTA
+// covers TR rows x TC columns of positions (wide rows: long contiguous runs
+// of every M_r and C row); each thread owns 4 consecutive entries of one
+// position row in every C block
+// and walks the leaves in order, adding w * M_r with one fused multiply-add
+// per nonzero coefficient (w * M_r is exact for the power-of-two
+// coefficients of the printed rules, so the sums equal those of the
+// shared-memory pass).  The C sums are unscaled once and stored.
+constexpr int kDenseBatch = 8;  // leaves whose loads are in flight together
+
+template <int NB, int TR, int TC>
+__global__ void __launch_bounds__(TR * TC / 4) out_dense_kernel(const OutArgs a) {
+  extern __shared__ float sW[];  // [num_leaves][NB]
+  pdl_wait();
+  pdl_trigger();
+  const EpilogueArgs& c = a.c;
+  const int R = (int)a.num_leaves;
+  const int pn = (int)a.pn;
+  for (int i = threadIdx.x; i < R * NB; i += TR * TC / 4) sW[i] = 0.f;
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += TR * TC / 4) {
+    for (int t = __ldg(a.c_start + r); t < __ldg(a.c_start + r + 1); ++t) {
+      const int32_t word = __ldg(a.c_blk + t);
+      const int bi = (word >> 16) & 0x7FFF, bj = word & 0xFFFF;
+      sW[r * NB + bi * pn + bj] = __ldg(a.c_coef + t);
+    }
+  }
+  __syncthreads();
+  const int tr = threadIdx.x / (TC / 4), tq = threadIdx.x % (TC / 4);
+  const int64_t lr = (int64_t)blockIdx.y * TR + tr, lc = (int64_t)blockIdx.x * TC + tq * 4;
+  if (lr >= c.bm || lc >= c.bn) return;
+  const float* mpos = a.mbuf + lr * a.tp_b + lc;
+  const int64_t leaf_stride = a.tp_a * a.tp_b;
+  float4 acc[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) acc[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int r0 = 0; r0 < R; r0 += kDenseBatch) {
+    float4 m[kDenseBatch];
+#pragma unroll
+    for (int u = 0; u < kDenseBatch; ++u)
+      if (r0 + u < R) m[u] = __ldg(reinterpret_cast<const float4*>(mpos + (int64_t)(r0 + u) * leaf_stride));
+#pragma unroll
+    for (int u = 0; u < kDenseBatch; ++u) {
+      if (r0 + u >= R) break;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const float w = sW[(r0 + u) * NB + b];
+        if (w != 0.f) {
+          acc[b].x = fmaf(w, m[u].x, acc[b].x);
+          acc[b].y = fmaf(w, m[u].y, acc[b].y);
+          acc[b].z = fmaf(w, m[u].z, acc[b].z);
+          acc[b].w = fmaf(w, m[u].w, acc[b].w);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if (b >= (int)a.c_blocks) break;
+    const int bi = b / pn, bj = b % pn;
+    const int64_t gi = bi * c.bm + lr, gj = bj * c.bn + lc;
+    if (gi >= c.M) continue;
+    float vv[4] = {acc[b].x, acc[b].y, acc[b].z, acc[b].w};
+    if (c.eA) {
+      const float fa = exp2i(__ldg(c.eA + gi));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) vv[j] *= fa;
+    }
+    if (c.eB) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (gj + j < c.N) vv[j] *= exp2i(__ldg(c.eB + gj + j));
+    }
+    float* dst = c.C + gi * c.ldc + gj;
+    if (c.vec_ok && lc + 4 <= c.bn && gj + 4 <= c.N) {
+      *reinterpret_cast<float4*>(dst) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (lc + j < c.bn && gj + j < c.N) dst[j] = vv[j];
+    }
+  }
+}
+
 // Output pass by C block (Eq. 3.2 read per output block): CTA (x, y)
 // covers position tile x (kOutGatherRows x 64 entries of the leaf block) of
 // C blocks y, y + gridDim.y, ...; each thread forms 4 consecutive entries as
@@ -727,8 +813,9 @@ __global__ void between_finalize_kernel(const int* cexp, const int* rexp, int* d
 
 }  // namespace
 
-// E4M3 combination pass: one CTA covers 16 t x 128 k (one scale block) of
-// every leaf block; the input block tiles are staged as [t][k] (k
+// E4M3 combination pass: one CTA covers TT t x 128 k (one scale block) of
+// every leaf block (TT = 16, or 4 when the input blocks are too many to
+// stage sixteen rows of each); the input block tiles are staged as [t][k] (k
 // contiguous, stride kF8Stride) whatever the source's layout; warp w forms
 // row t0 + w of each leaf's sum, 4 consecutive k per lane, reduces the
 // block's max |sum| across the warp, picks s = e(max) - 8 (0 for a zero
@@ -737,31 +824,32 @@ __global__ void between_finalize_kernel(const int* cexp, const int* rexp, int* d
 constexpr int kF8TT = 16;
 constexpr int kF8Stride = 132;
 
-template <int DT>
-__global__ void __launch_bounds__(512) combine_e4m3_kernel(const CombineArgs a) {
-  extern __shared__ float f8tile[];  // [block][kF8TT][kF8Stride], then the term list
+template <int DT, int TT>
+__global__ void __launch_bounds__(TT * 32) combine_e4m3_kernel(const CombineArgs a) {
+  extern __shared__ float f8tile[];  // [block][TT][kF8Stride], then the term list
+  constexpr int kThr = TT * 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t t0 = (int64_t)blockIdx.y * kF8TT, k0 = (int64_t)blockIdx.x * 128;
+  const int64_t t0 = (int64_t)blockIdx.y * TT, k0 = (int64_t)blockIdx.x * 128;
   const int n_rb = (int)a.n_rb, n_cb = (int)a.n_cb, nb = n_rb * n_cb;
   const int R = (int)a.num_leaves, nnz = (int)a.t_nnz;
-  int* toff = reinterpret_cast<int*>(f8tile + nb * kF8TT * kF8Stride);
+  int* toff = reinterpret_cast<int*>(f8tile + nb * TT * kF8Stride);
   float* tcoef = reinterpret_cast<float*>(toff + nnz);
   int* tstart = reinterpret_cast<int*>(tcoef + nnz);
-  for (int i = tid; i < nnz; i += 512) {
+  for (int i = tid; i < nnz; i += kThr) {
     const int32_t blk = __ldg(a.t_blk + i);
     const int bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
-    toff[i] = (a.t_rows ? bt * n_cb + bk : bk * n_cb + bt) * kF8TT * kF8Stride;
+    toff[i] = (a.t_rows ? bt * n_cb + bk : bk * n_cb + bt) * TT * kF8Stride;
     tcoef[i] = __ldg(a.t_coef + i);
   }
-  for (int i = tid; i <= R; i += 512) tstart[i] = __ldg(a.t_start + i);
+  for (int i = tid; i <= R; i += kThr) tstart[i] = __ldg(a.t_start + i);
   // staging: position (t, k) of block (rb, cb) -> memory (t, k) (KC) or (k, t)
   for (int rb = 0; rb < n_rb; ++rb) {
     for (int cb = 0; cb < n_cb; ++cb) {
-      float* tile = f8tile + (rb * n_cb + cb) * kF8TT * kF8Stride;
+      float* tile = f8tile + (rb * n_cb + cb) * TT * kF8Stride;
       const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows), nc = min(a.b_cols, a.cols - cb * a.b_cols);
-      for (int i = tid; i < kF8TT * 128; i += 512) {
+      for (int i = tid; i < TT * 128; i += kThr) {
         int t, k;
-        if (a.t_rows) { t = i >> 7; k = i & 127; } else { k = i >> 4; t = i & 15; }
+        if (a.t_rows) { t = i >> 7; k = i & 127; } else { k = i / TT; t = i % TT; }
         const int64_t lt = t0 + t, lk = k0 + k;
         const int64_t lr = a.t_rows ? lt : lk, lc = a.t_rows ? lk : lt;  // block-local memory row / column
         float x = 0.f;
@@ -809,28 +897,32 @@ __global__ void __launch_bounds__(512) combine_e4m3_kernel(const CombineArgs a) 
 }
 
 cudaError_t launch_combine_e4m3(const CombineArgs& a, cudaStream_t st) {
-  if (a.p_rows % kF8TT != 0 || a.p_cols % 128 != 0 || a.p_rows / kF8TT > 65535) return cudaErrorInvalidValue;
+  if (a.p_rows % kF8TT != 0 || a.p_cols % 128 != 0) return cudaErrorInvalidValue;
   const int64_t nb = a.n_rb * a.n_cb;
-  const size_t smem = (size_t)nb * kF8TT * kF8Stride * 4 + (size_t)a.t_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
-  if (smem > kStagedSmemMax) return cudaErrorNotSupported;
+  const size_t list = (size_t)a.t_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
+  // sixteen rows per CTA when the staged tiles fit, else four
+  const bool wide = (size_t)nb * kF8TT * kF8Stride * 4 + list <= kStagedSmemMax;
+  const int tt = wide ? kF8TT : 4;
+  const size_t smem = (size_t)nb * tt * kF8Stride * 4 + list;
+  if (smem > kStagedSmemMax || a.p_rows / tt > 65535) return cudaErrorNotSupported;
   if (a.num_leaves == 0 || a.p_rows == 0 || a.p_cols == 0) return cudaSuccess;
-  static bool attr_done[64][3] = {};
+  static bool attr_done[64][6] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  const dim3 grid((unsigned)(a.p_cols / 128), (unsigned)(a.p_rows / kF8TT));
+  const dim3 grid((unsigned)(a.p_cols / 128), (unsigned)(a.p_rows / tt));
   KernelTimer timer("combine", st);
   auto go = [&](auto kern, int idx) {
     if (!attr_done[dev][idx]) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedSmemMax);
       attr_done[dev][idx] = true;
     }
-    kern<<<grid, 512, smem, st>>>(a);
+    kern<<<grid, tt * 32, smem, st>>>(a);
   };
   switch (a.dtype) {
-    case kF32: go(combine_e4m3_kernel<kF32>, 0); break;
-    case kBF16: go(combine_e4m3_kernel<kBF16>, 1); break;
-    default: go(combine_e4m3_kernel<kF16>, 2); break;
+    case kF32: wide ? go(combine_e4m3_kernel<kF32, kF8TT>, 0) : go(combine_e4m3_kernel<kF32, 4>, 3); break;
+    case kBF16: wide ? go(combine_e4m3_kernel<kBF16, kF8TT>, 1) : go(combine_e4m3_kernel<kBF16, 4>, 4); break;
+    default: wide ? go(combine_e4m3_kernel<kF16, kF8TT>, 2) : go(combine_e4m3_kernel<kF16, 4>, 5); break;
   }
   return cudaGetLastError();
 }
@@ -883,6 +975,21 @@ cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st) {
   if (a.c_blocks > kMaxOutBlocks || a.c.bm > a.tp_a || a.c.bn > a.tp_b || a.tp_b % kTC != 0)
     return cudaErrorInvalidValue;
   if (a.c.bm == 0 || a.c.bn == 0) return cudaSuccess;
+  if (a.c_blocks <= 16 && a.num_leaves * 16 * 4 <= 48 * 1024) {
+    // register accumulators
+    KernelTimer timer("combine", st);
+    auto go = [&](auto nb_tag, auto tr_tag) {
+      constexpr int NB = decltype(nb_tag)::value, TR = decltype(tr_tag)::value, TC = 1024 / TR;
+      const unsigned gy = (unsigned)((a.c.bm + TR - 1) / TR);
+      launch_pdl(out_dense_kernel<NB, TR, TC>, dim3((unsigned)((a.c.bn + TC - 1) / TC), gy), dim3(TR * TC / 4),
+                 (size_t)a.num_leaves * NB * 4, st, a);
+    };
+    // 256 threads: TR rows of 1024 / TR columns
+    if (a.c_blocks <= 4) go(std::integral_constant<int, 4>(), std::integral_constant<int, 2>());
+    else if (a.c_blocks <= 9) go(std::integral_constant<int, 9>(), std::integral_constant<int, 2>());
+    else go(std::integral_constant<int, 16>(), std::integral_constant<int, 2>());
+    return cudaGetLastError();
+  }
   const size_t list_bytes = (size_t)a.c_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
   if (list_bytes > 150 * 1024) return cudaErrorInvalidValue;
   KernelTimer timer("combine", st);

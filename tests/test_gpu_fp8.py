@@ -32,6 +32,22 @@ def test_e4m3_integers_exact(api, names, M, K, N, dt):
     assert np.array_equal(got, A @ B)
 
 
+@pytest.mark.parametrize("names", [["winograd", "classical121", "winograd", "classical121"],
+                                   ["strassen", "strassen", "strassen"]], ids=lambda n: "-".join(n))
+def test_e4m3_deep_plans_integers_exact(api, names):
+    # Many input blocks per operand (64 for B in the first plan): the
+    # combination pass stages four rows per CTA.  Entries in [-1, 1]: every
+    # S, T entry is an integer of magnitude at most 16, exact in E4M3 after
+    # its power-of-two block scale.
+    M, K, N = 264, 520, 200
+    A = inputs.integers((M, K), -1, 1, seed=3)
+    B = inputs.integers((K, N), -1, 1, seed=4)
+    for dt in ("f32", "bf16"):
+        got = dev_values(api.multiply(api.Plan(names, "e4m3b128"), to_dev(A, dt), to_dev(B, dt)))
+        api.sync_status()
+        assert np.array_equal(got, A @ B), dt
+
+
 @pytest.mark.parametrize("names", [["strassen"], ["winograd"], []], ids=lambda n: "-".join(n) or "classical")
 def test_e4m3_matches_block_quantization(api, names):
     # One level: S_r, T_r are formed in FP32 in index order on both sides and
