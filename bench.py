@@ -458,23 +458,24 @@ def main():
     value = world * flops / (ms * 1e-3) / 1e12
 
     # ---------------- end to end through the public API with host buffers
-    def e2e_step():
-        A.copy_(hA, non_blocking=True)
-        B.copy_(hB, non_blocking=True)
-        step()
-        hC.copy_(C, non_blocking=True)
+    # The public host-memory entry points (fmm_host_*): each step copies A and
+    # B in from pinned host memory, scales, multiplies and copies C out; two
+    # pipeline slots let one step's copies overlap its neighbours' work.
+    pipe = api.HostPipeline(plan, n, n, n, torch.float32, args.scaling, depth=2)
+    hCs = [hC, torch.empty((n, n), dtype=torch.float32).pin_memory()]
 
-    for _ in range(2):
-        e2e_step()
+    def e2e_run(k):
+        for i in range(k):
+            pipe.submit(hA, hB, hCs[i % 2])
+        pipe.wait()
+
+    e2e_run(2)
     torch.cuda.synchronize()
     e_steps = max(3, min(args.steps, 30))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e_steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e_ms = e0.elapsed_time(e1) / e_steps
+    t0 = time.perf_counter()
+    e2e_run(e_steps)
+    e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
+    del pipe
     if world > 1:
         t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -590,7 +591,8 @@ def main():
                         "ms_per_launch": mult_ms_per},
            "e2e": {"value": world * flops / (e_ms * 1e-3) / 1e12, "unit": UNIT,
                    "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
-                   "ms_per_step": e_ms},
+                   "ms_per_step": e_ms, "path": "fmm_host_submit / fmm_host_wait, two pipeline slots, "
+                                                 "pinned host buffers, wall clock over the submissions"},
            "gpu_launches": kern[""][1] // max(1, bd_steps) * args.steps,
            "clocks": ck, "plan": info}
     out.update(extras)

@@ -391,6 +391,35 @@ fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc,
                                  int64_t N, int in_dtype, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * Host-memory pipeline (not from the paper: the paper's products live in
+ * one memory).  For a stream of products of one shape whose operands and
+ * results are in host memory, fmm_host_create sets up `depth` (1..4) slots
+ * of device memory (A, B, C, the exponent vectors) plus one workspace, and
+ * four streams: copy-in of A, copy-in of B, compute, copy-out.  fmm_host_submit enqueues one
+ * product and returns without waiting: the host->device copies of A (M x K,
+ * lda) and B (K x N, ldb) into the next slot, then -- once they are in --
+ * the scaling steps (`steps` as in fmm_scale, "" for none) and
+ * fmm_multiply, then the device->host copy of C (M x N, ldc, float32).  A
+ * slot is reused only after its previous product has been read and
+ * written back, so with depth >= 2 the copies of one product overlap the
+ * computation of its neighbours.  The caller must leave the host buffers of
+ * a submission untouched until fmm_host_wait returns (or until `depth`
+ * further submissions); page-locked host memory lets the copies run
+ * asynchronously, pageable memory works but serialises them.  dtype is
+ * FMM_DT_*.  The pipeline keeps a reference to the plan, which must
+ * outlive it.  Errors: FMM_ERR_ARG (bad sizes, depth, steps), FMM_ERR_CUDA.
+ */
+typedef struct fmm_host_s* fmm_host_t;
+fmm_status fmm_host_create(fmm_host_t* out, fmm_plan_t plan, int64_t M, int64_t K, int64_t N, int dtype,
+                           const char* steps, int depth);
+fmm_status fmm_host_submit(fmm_host_t h, const void* hA, int64_t lda, const void* hB, int64_t ldb, float* hC,
+                           int64_t ldc);
+/* Wait until every submitted product is back in host memory; returns the
+ * first error any of them met (the device status word included). */
+fmm_status fmm_host_wait(fmm_host_t h);
+fmm_status fmm_host_destroy(fmm_host_t h);
+
+/*
  * Per-kernel timing, for measurement.  fmm_kernel_timing(1) starts
  * recording (discarding earlier records): every kernel the library launches
  * from then on is bracketed by two CUDA events recorded on its launching

@@ -30,6 +30,7 @@ EXPORTS = [
     "fmm_plan_set_schedule", "fmm_kernel_timing", "fmm_kernel_timing_read",
     "fmm_batch_workspace_size", "fmm_batch_create", "fmm_batch_run", "fmm_batch_destroy",
     "fmm_plan_set_between_scaling", "fmm_plan_tree", "fmm_scale_adaptive",
+    "fmm_host_create", "fmm_host_submit", "fmm_host_wait", "fmm_host_destroy",
 ]
 
 # Bytes of the library's static scratch array (FMM_NOALLOC_SCRATCH_BYTES).
@@ -69,6 +70,10 @@ def lib():
     i64, i32p, vp, st = C.c_int64, C.POINTER(C.c_int32), C.c_void_p, C.c_int
     L.fmm_plan.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(FmmRule), C.c_int]
     L.fmm_plan_destroy.argtypes = [vp]
+    L.fmm_host_create.argtypes = [C.POINTER(vp), vp, i64, i64, i64, C.c_int, C.c_char_p, C.c_int]
+    L.fmm_host_submit.argtypes = [vp, vp, i64, vp, i64, vp, i64]
+    L.fmm_host_wait.argtypes = [vp]
+    L.fmm_host_destroy.argtypes = [vp]
     L.fmm_plan_tree.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(FmmRule), C.c_int, i64,
                                 C.POINTER(C.c_int32), C.c_int]
     L.fmm_plan_set_schedule.argtypes = [vp, C.c_int]

@@ -256,6 +256,51 @@ def multiply_backward(plan: Plan, dC: torch.Tensor, A: torch.Tensor, B: torch.Te
     return dA, dB
 
 
+class HostPipeline:
+    """Products of one shape whose operands and results live in host memory
+    (fmm_host_*): ``submit`` enqueues the copies in, the scaling steps and
+    the multiply, and the copy out, and returns at once; ``wait`` blocks
+    until every submitted product is back.  Host tensors must stay untouched
+    until then (or until ``depth`` further submissions); pinned tensors let
+    the copies of one product overlap the computation of the next."""
+
+    def __init__(self, plan: "Plan", M: int, K: int, Ncols: int, dtype=torch.float32, steps: str = "OI",
+                 depth: int = 2):
+        self.plan = plan
+        self.shape = (M, K, Ncols)
+        self.dtype = dtype
+        h = C.c_void_p()
+        N.check(N.lib().fmm_host_create(C.byref(h), plan.handle, M, K, Ncols, DTYPE[dtype], steps.encode(), depth),
+                "fmm_host_create")
+        self._h = h
+        self._held = []
+        self.depth = depth
+
+    def submit(self, A: torch.Tensor, B: torch.Tensor, C_out: torch.Tensor) -> None:
+        M, K, Ncols = self.shape
+        for t, shp, dt, name in ((A, (M, K), self.dtype, "A"), (B, (K, Ncols), self.dtype, "B"),
+                                 (C_out, (M, Ncols), torch.float32, "C")):
+            if t.is_cuda or tuple(t.shape) != shp or t.dtype != dt or (t.shape[1] > 1 and t.stride(1) != 1):
+                raise ValueError(f"{name}: host row-major {dt} tensor of shape {shp} required")
+        N.check(N.lib().fmm_host_submit(self._h, C.c_void_p(A.data_ptr()), A.stride(0), C.c_void_p(B.data_ptr()),
+                                        B.stride(0), C.c_void_p(C_out.data_ptr()), C_out.stride(0)),
+                "fmm_host_submit")
+        self._held = (self._held + [(A, B, C_out)])[-(self.depth + 1):]
+
+    def wait(self) -> None:
+        N.check(N.lib().fmm_host_wait(self._h), "fmm_host_wait")
+        self._held = []
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                N.lib().fmm_host_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
 class Batch:
     """Many independent products C_i = A_i B_i, each with its own plan, run
     as one fixed launch sequence (fmm_batch_create / fmm_batch_run): batched
