@@ -418,11 +418,128 @@ void launch_staged(const CombineArgs& a, int nb, cudaStream_t st) {
   else launch_staged_tr<DT, FMT, 2>(a, nb, st);
 }
 
+// x 2^e with the exponent built directly when 2^e is a normal number.
+__device__ __forceinline__ float scale_fast(float x, int e) {
+  return ((unsigned)(e + 126) <= 253u) ? x * __int_as_float((e + 127) << 23) : scale_pow2(x, e);
+}
+
+// The staged combination for operands of at most 2 x 2 blocks (one level of
+// a <2,2,2> rule, or the classical product), with the block loops unrolled
+// and each column's scale exponents loaded once per thread: the same
+// arithmetic as combine_staged_body (each element scaled once, each leaf's
+// terms summed from shared memory in term order, then rounded and split).
+// CTA: 32 rows x 64 columns of every block, 256 threads, rows tr and
+// tr + 16 of 4 columns each.  The term list sits in shared memory as
+// (float4 offset of the term's tile, coefficient) pairs.
+template <int DT, int FMT, int NRB, int NCB>
+__global__ void __launch_bounds__(256) combine_small_kernel(const CombineArgs a) {
+  constexpr int TR = 32, NB = NRB * NCB;
+  __shared__ float4 tile4[NB * TR * 16];
+  extern __shared__ int2 terms[];  // [nnz] (offset, coef bits), then tstart[R + 1]
+  pdl_wait();
+  pdl_trigger();
+  const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * kTC;
+  const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15, tc = tq * 4;
+  const int es = DT == kF32 ? 4 : 2;
+  const bool vec_ok = ((uintptr_t)a.src % (4 * es) == 0) && (a.ld % 4 == 0) && (a.b_cols % 4 == 0) &&
+                      (!a.ce || (uintptr_t)a.ce % 16 == 0);
+  const int R = (int)a.num_leaves, nnz = (int)a.t_nnz;
+  int* tstart = reinterpret_cast<int*>(terms + nnz);
+  for (int i = threadIdx.x; i < nnz; i += 256) {
+    const int32_t blk = __ldg(a.t_blk + i);
+    const int bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
+    terms[i] = make_int2((a.t_rows ? bt * NCB + bk : bk * NCB + bt) * TR * 16, __float_as_int(__ldg(a.t_coef + i)));
+  }
+  for (int i = threadIdx.x; i <= R; i += 256) tstart[i] = __ldg(a.t_start + i);
+  const int64_t lc = c0 + tc;
+  // column exponents of this thread's 4 columns in each block column
+  int ec[NCB][4];
+  int64_t ncols[NCB];
+#pragma unroll
+  for (int cb = 0; cb < NCB; ++cb) {
+    ncols[cb] = min(a.b_cols, a.cols - cb * a.b_cols);
+    const int64_t gc = cb * a.b_cols + lc;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ec[cb][j] = (a.ce && lc + j < ncols[cb]) ? a.cs * __ldg(a.ce + gc + j) : 0;
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int trq = tr + 16 * q;
+    const int64_t lr = r0 + trq;
+#pragma unroll
+    for (int rb = 0; rb < NRB; ++rb) {
+      const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows);
+      const bool row_in = lr < nr;
+      const int64_t gr = rb * a.b_rows + lr;
+      const int er = (a.re && row_in) ? a.rs * __ldg(a.re + gr) : 0;
+      const char* src_row = static_cast<const char*>(a.src) + gr * a.ld * es;
+#pragma unroll
+      for (int cb = 0; cb < NCB; ++cb) {
+        const int64_t gc = cb * a.b_cols + lc;
+        float x[4];
+        if (vec_ok && row_in && lc + 4 <= ncols[cb]) {
+          load4<DT>(src_row, gc, x);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) x[j] = scale_fast(x[j], er + ec[cb][j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            x[j] = (row_in && lc + j < ncols[cb]) ? scale_pow2(load_elem<DT>(src_row, gc + j), er + ec[cb][j]) : 0.f;
+        }
+        tile4[((rb * NCB + cb) * TR + trq) * 16 + tq] = make_float4(x[0], x[1], x[2], x[3]);
+      }
+    }
+  }
+  __syncthreads();
+  unsigned short* out = static_cast<unsigned short*>(a.out);
+  const int64_t leaf_stride = a.p_rows * a.p_cols;
+  const int64_t plane = (int64_t)R * leaf_stride;
+  const int me = tr * 16 + tq;
+  unsigned short* orow = out + (r0 + tr) * a.p_cols + lc;
+  const int64_t qstride = (int64_t)16 * a.p_cols;
+  int t = 0;
+  for (int r = 0; r < R; ++r, orow += leaf_stride) {
+    const int t1 = tstart[r + 1];
+    float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
+    for (; t < t1; ++t) {
+      const int2 term = terms[t];
+      const float coef = __int_as_float(term.y);
+      const float4 v0 = tile4[term.x + me];
+      const float4 v1 = tile4[term.x + me + 256];
+      acc0[0] = fmaf(coef, v0.x, acc0[0]);
+      acc0[1] = fmaf(coef, v0.y, acc0[1]);
+      acc0[2] = fmaf(coef, v0.z, acc0[2]);
+      acc0[3] = fmaf(coef, v0.w, acc0[3]);
+      acc1[0] = fmaf(coef, v1.x, acc1[0]);
+      acc1[1] = fmaf(coef, v1.y, acc1[1]);
+      acc1[2] = fmaf(coef, v1.z, acc1[2]);
+      acc1[3] = fmaf(coef, v1.w, acc1[3]);
+    }
+    store4<FMT>(orow, orow + plane, acc0);
+    store4<FMT>(orow + qstride, orow + qstride + plane, acc1);
+  }
+}
+
+template <int DT, int FMT>
+void launch_small(const CombineArgs& a, cudaStream_t st) {
+  const dim3 grid((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / 32));
+  const size_t smem = (size_t)a.t_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
+  if (a.n_rb == 2 && a.n_cb == 2) launch_pdl(combine_small_kernel<DT, FMT, 2, 2>, grid, dim3(256), smem, st, a);
+  else if (a.n_rb == 2) launch_pdl(combine_small_kernel<DT, FMT, 2, 1>, grid, dim3(256), smem, st, a);
+  else if (a.n_cb == 2) launch_pdl(combine_small_kernel<DT, FMT, 1, 2>, grid, dim3(256), smem, st, a);
+  else launch_pdl(combine_small_kernel<DT, FMT, 1, 1>, grid, dim3(256), smem, st, a);
+}
+
 template <int DT, int FMT>
 void launch_fmt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
   const int64_t nb = a.n_rb * a.n_cb;
   const int tr = nb <= 4 ? 32 : nb <= 8 ? 16 : nb <= 16 ? 8 : nb <= 32 ? 4 : 2;
-  if (nb <= kMaxStaged && staged_smem((int)nb, tr, a.t_nnz, a.num_leaves) <= kStagedSmemMax)
+  // few leaves on a grid that already fills the GPU: the unrolled form
+  const bool small = a.n_rb <= 2 && a.n_cb <= 2 && !a.between_d && a.p_rows % 32 == 0 &&
+                     (int64_t)grid.x * (a.p_rows / 32) >= 2 * device_sms() && a.t_nnz * 8 + (a.num_leaves + 1) * 4 <= 16384;
+  if (small)
+    launch_small<DT, FMT>(a, st);
+  else if (nb <= kMaxStaged && staged_smem((int)nb, tr, a.t_nnz, a.num_leaves) <= kStagedSmemMax)
     launch_staged<DT, FMT>(a, (int)nb, st);
   else if (!a.between_d)
     launch_pdl(combine_kernel<DT, FMT>, dim3(grid.x, grid.y, leaf_splits(a, kTR, a.num_leaves, 8)), dim3(kThreads), 0,
@@ -536,14 +653,13 @@ __global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
 // Output pass with the accumulators in registers, for plans with at most
 // NB C blocks: the leaves' W coefficients are laid out densely in shared
 // memory (sW[r][k], zero where leaf r does not add into block k).  A CTA
-// covers TR rows x TC columns of positions (wide rows: long contiguous runs
-// of every M_r and C row); each thread owns 4 consecutive entries of one
-// position row in every C block
+// covers TR rows x TC columns of positions; each thread owns 4 consecutive
+// entries of one position row in every C block
 // and walks the leaves in order, adding w * M_r with one fused multiply-add
 // per nonzero coefficient (w * M_r is exact for the power-of-two
 // coefficients of the printed rules, so the sums equal those of the
 // shared-memory pass).  The C sums are unscaled once and stored.
-constexpr int kDenseBatch = 8;  // leaves whose loads are in flight together
+constexpr int kDenseBatch = 4;  // leaves whose loads are in flight together
 
 template <int NB, int TR, int TC>
 __global__ void __launch_bounds__(TR * TC / 4) out_dense_kernel(const OutArgs a) {
@@ -979,15 +1095,15 @@ cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st) {
     // register accumulators
     KernelTimer timer("combine", st);
     auto go = [&](auto nb_tag, auto tr_tag) {
-      constexpr int NB = decltype(nb_tag)::value, TR = decltype(tr_tag)::value, TC = 1024 / TR;
+      constexpr int NB = decltype(nb_tag)::value, TR = decltype(tr_tag)::value, TC = kTC;
       const unsigned gy = (unsigned)((a.c.bm + TR - 1) / TR);
       launch_pdl(out_dense_kernel<NB, TR, TC>, dim3((unsigned)((a.c.bn + TC - 1) / TC), gy), dim3(TR * TC / 4),
                  (size_t)a.num_leaves * NB * 4, st, a);
     };
-    // 256 threads: TR rows of 1024 / TR columns
-    if (a.c_blocks <= 4) go(std::integral_constant<int, 4>(), std::integral_constant<int, 2>());
-    else if (a.c_blocks <= 9) go(std::integral_constant<int, 9>(), std::integral_constant<int, 2>());
-    else go(std::integral_constant<int, 16>(), std::integral_constant<int, 2>());
+    // TR rows of 64 columns (measured: wider rows were no faster)
+    if (a.c_blocks <= 4) go(std::integral_constant<int, 4>(), std::integral_constant<int, 32>());
+    else if (a.c_blocks <= 9) go(std::integral_constant<int, 9>(), std::integral_constant<int, 16>());
+    else go(std::integral_constant<int, 16>(), std::integral_constant<int, 16>());
     return cudaGetLastError();
   }
   const size_t list_bytes = (size_t)a.c_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
