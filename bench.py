@@ -174,6 +174,49 @@ def linear_layer_workload(api, torch, reps: int = 10) -> dict:
             "forward_max_abs_err_sampled_rows": err}
 
 
+# ---------------------------------------------------------------- precision sweep
+
+def precision_sweep(api, torch, reps: int = 5) -> dict:
+    """The precision sweep: n = 8192 square and M = 8192, K = 16384,
+    N = 4096; FP32 inputs U[-1, 1] (seeded, on the device); Winograd one
+    level and Strassen then classical <1,2,1>; BF16, FP16 and E4M3 (128-block
+    power-of-two scales) leaves with FP32 accumulation; outside-inside
+    scaling; each configuration timed with CUDA events over `reps` calls
+    (inputs far beyond L2) and its max-norm error against an FP64 product of
+    the same inputs (measurement only), relative to K ||A|| ||B||."""
+    out = {}
+    gen = torch.Generator(device="cuda").manual_seed(1507 + 5000)
+    for M, K, N in ((8192, 8192, 8192), (8192, 16384, 4096)):
+        A = torch.rand((M, K), generator=gen, device="cuda") * 2 - 1
+        B = torch.rand((K, N), generator=gen, device="cuda") * 2 - 1
+        ref = A.double() @ B.double()
+        scale = K * float(A.abs().max()) * float(B.abs().max())
+        flops = 2.0 * M * K * N
+        for names in (["winograd"], ["strassen", "classical121"], []):
+            for leaf in ("bf16", "fp16", "e4m3b128"):
+                plan = api.Plan(names, leaf)
+                C = torch.empty((M, N), device="cuda")
+                eA, d, eB = api.scale(A, B, "OI")
+                api.multiply(plan, A, B, eA, d, eB, out=C)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    eA, d, eB = api.scale(A, B, "OI")
+                    api.multiply(plan, A, B, eA, d, eB, out=C)
+                e1.record()
+                torch.cuda.synchronize()
+                api.sync_status()
+                ms = e0.elapsed_time(e1) / reps
+                key = f"{M}x{K}x{N} {'-'.join(names) or 'classical'} {leaf}"
+                out[key] = {"tflops": flops / (ms * 1e-3) / 1e12, "ms": ms,
+                            "max_err_over_K_normA_normB": float((C.double() - ref).abs().max()) / scale}
+                del C, plan
+        del A, B, ref
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- clocks
 
 class Clocks:
@@ -529,6 +572,7 @@ def main():
         extras["batched"] = batched_workload(api, inputs, torch, args.batch)
     if not args.no_extras:
         extras["autograd_linear"] = linear_layer_workload(api, torch)
+        extras["precision_sweep"] = precision_sweep(api, torch)
 
     # ---------------- roofline of the dominant kernel (the tensor-core multiply)
     import json as _json

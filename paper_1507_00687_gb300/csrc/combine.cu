@@ -958,23 +958,42 @@ __global__ void __launch_bounds__(TT * 32) combine_e4m3_kernel(const CombineArgs
     tcoef[i] = __ldg(a.t_coef + i);
   }
   for (int i = tid; i <= R; i += kThr) tstart[i] = __ldg(a.t_start + i);
-  // staging: position (t, k) of block (rb, cb) -> memory (t, k) (KC) or (k, t)
+  // staging: position (t, k) of block (rb, cb) -> memory (t, k) (k
+  // contiguous) or (k, t) (t contiguous); each thread loads 4 consecutive
+  // memory columns (one vector load where the row allows)
+  const int es = DT == kF32 ? 4 : 2;
+  const bool vec_ok = ((uintptr_t)a.src % (4 * es) == 0) && (a.ld % 4 == 0) && (a.b_cols % 4 == 0);
+  constexpr int kRowThreadsT = 32, kRowThreadsK = TT / 4;  // threads per memory row
   for (int rb = 0; rb < n_rb; ++rb) {
     for (int cb = 0; cb < n_cb; ++cb) {
       float* tile = f8tile + (rb * n_cb + cb) * TT * kF8Stride;
       const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows), nc = min(a.b_cols, a.cols - cb * a.b_cols);
-      for (int i = tid; i < TT * 128; i += kThr) {
-        int t, k;
-        if (a.t_rows) { t = i >> 7; k = i & 127; } else { k = i / TT; t = i % TT; }
-        const int64_t lt = t0 + t, lk = k0 + k;
-        const int64_t lr = a.t_rows ? lt : lk, lc = a.t_rows ? lk : lt;  // block-local memory row / column
-        float x = 0.f;
-        if (lr < nr && lc < nc) {
-          const int64_t gr = rb * a.b_rows + lr, gc = cb * a.b_cols + lc;
-          const float v = load_elem<DT>(a.src, gr * a.ld + gc);
-          x = scale_pow2(v, (a.re ? a.rs * __ldg(a.re + gr) : 0) + (a.ce ? a.cs * __ldg(a.ce + gc) : 0));
+      const int per_row = a.t_rows ? kRowThreadsT : kRowThreadsK;
+      const int n_items = a.t_rows ? TT * kRowThreadsT : 128 * kRowThreadsK;
+      for (int i = tid; i < n_items; i += kThr) {
+        const int mrow = i / per_row, mcol = 4 * (i % per_row);  // within the CTA's window
+        const int64_t lr = (a.t_rows ? t0 : k0) + mrow, lc = (a.t_rows ? k0 : t0) + mcol;
+        const int64_t gr = rb * a.b_rows + lr, gc = cb * a.b_cols + lc;
+        float x[4];
+        const int er = (a.re && lr < nr) ? a.rs * __ldg(a.re + gr) : 0;
+        if (vec_ok && lr < nr && lc + 4 <= nc) {
+          load4<DT>(a.src, gr * a.ld + gc, x);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) x[j] = scale_pow2(x[j], er + (a.ce ? a.cs * __ldg(a.ce + gc + j) : 0));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            x[j] = (lr < nr && lc + j < nc)
+                       ? scale_pow2(load_elem<DT>(a.src, gr * a.ld + gc + j),
+                                    er + (a.ce ? a.cs * __ldg(a.ce + gc + j) : 0))
+                       : 0.f;
         }
-        tile[t * kF8Stride + k] = x;
+        if (a.t_rows) {
+          *reinterpret_cast<float4*>(tile + mrow * kF8Stride + mcol) = make_float4(x[0], x[1], x[2], x[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) tile[(mcol + j) * kF8Stride + mrow] = x[j];
+        }
       }
     }
   }
