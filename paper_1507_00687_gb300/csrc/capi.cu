@@ -678,7 +678,7 @@ static int batch_steps(const char* steps) {
 // by fmm_batch_workspace_size and fmm_batch_create.
 struct BatchLayout {
   size_t off_red[4], off_red_start[4];
-  size_t off_comb, off_comb_start, off_direct, off_unit_start, off_out, off_out_start;
+  size_t off_comb, off_comb_start, off_copy_start, off_direct, off_unit_start, off_out, off_out_start;
   size_t off_exp;                  // eA (sum M) | d (sum K) | eB (sum N), int32
   int64_t sum_m, sum_k, sum_n;
   std::vector<size_t> off_a, off_b, off_m;  // per problem, combined A / B and stored products
@@ -707,6 +707,8 @@ static fmm_status batch_layout(const fmm_problem* probs, int count, int dt, Batc
   L->off_comb = at;
   at = align_up(at + 2 * cnt * sizeof(CombineArgs), 256);
   L->off_comb_start = at;
+  at = align_up(at + (2 * cnt + 1) * 8, 256);
+  L->off_copy_start = at;
   at = align_up(at + (2 * cnt + 1) * 8, 256);
   L->off_direct = at;
   at = align_up(at + cnt * sizeof(DirectArgs), 256);
@@ -771,7 +773,8 @@ struct Batch {
   int* status = nullptr;
   BatchLayout L;
   int64_t red_total[4] = {0, 0, 0, 0};
-  int64_t comb_total = 0, unit_total = 0, out_total = 0;
+  int64_t comb_total = 0, copy_total = 0, unit_total = 0, out_total = 0;
+  int comb_count = 0, copy_count = 0;  // staged entries first in the table, then plain conversions
   int out_count = 0;
   int comb_tr = 32, out_tr = 32;
   size_t comb_smem = 0, out_smem = 0;
@@ -793,7 +796,8 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
     red_start[k].assign((size_t)count + 1, 0);
   }
   std::vector<CombineArgs> comb(2 * (size_t)count);
-  std::vector<int64_t> comb_start(2 * (size_t)count + 1, 0);
+  std::vector<CombineArgs> staged, plain;  // the table is staged entries, then plain conversions
+  std::vector<int64_t> comb_start(1, 0), copy_start(1, 0);
   std::vector<DirectArgs> dir((size_t)count);
   std::vector<int64_t> unit_start((size_t)count + 1, 0);
   std::vector<OutArgs> out;
@@ -802,7 +806,7 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
   int64_t max_nb = 1, max_cb = 1, tiles_all = 0;
   for (int i = 0; i < count; ++i) {
     const Plan* p = reinterpret_cast<const Plan*>(probs[i].plan);
-    max_nb = std::max(max_nb, std::max(p->pm * p->pk, p->pk * p->pn));
+    if (p->leaves > 1) max_nb = std::max(max_nb, std::max(p->pm * p->pk, p->pk * p->pn));
     max_cb = std::max(max_cb, p->pm * p->pn);
     const PassGeom& g = L.geom[(size_t)i];
     tiles_all += (g.tp_a / 128) * (g.tp_b / kBatchTileN);
@@ -848,8 +852,15 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
     comb[2 * u + 1] = combine_args(p, g, y, 1, leaves, wb);
     for (int sd = 0; sd < 2; ++sd) {
       const CombineArgs& ca = comb[2 * u + (size_t)sd];
-      comb_start[2 * u + (size_t)sd + 1] = comb_start[2 * u + (size_t)sd] + (ca.p_rows / b->comb_tr) * (ca.p_cols / 64);
-      b->comb_smem = std::max(b->comb_smem, combine_staged_smem(ca.n_rb * ca.n_cb, b->comb_tr, ca.t_nnz, g.R));
+      if (ca.n_rb == 1 && ca.n_cb == 1 && g.R == 1 && ca.t_nnz == 1) {
+        // one term of one block: a plain scaled conversion
+        plain.push_back(ca);
+        copy_start.push_back(copy_start.back() + convert_batched_ctas(ca));
+      } else {
+        staged.push_back(ca);
+        comb_start.push_back(comb_start.back() + (ca.p_rows / b->comb_tr) * (ca.p_cols / 64));
+        b->comb_smem = std::max(b->comb_smem, combine_staged_smem(ca.n_rb * ca.n_cb, b->comb_tr, ca.t_nnz, g.R));
+      }
     }
     EpilogueArgs c;
     c.C = q.C;
@@ -893,7 +904,12 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
     return FMM_ERR_UNSUPPORTED;
   }
   for (int k = 0; k < 4; ++k) b->red_total[k] = red_start[k][(size_t)count];
-  b->comb_total = comb_start[2 * (size_t)count];
+  b->comb_total = comb_start.back();
+  b->copy_total = copy_start.back();
+  b->comb_count = (int)staged.size();
+  b->copy_count = (int)plain.size();
+  comb = staged;
+  comb.insert(comb.end(), plain.begin(), plain.end());
   b->unit_total = unit_start[(size_t)count];
   b->out_total = out_start.back();
   b->layout = dir[0];
@@ -907,6 +923,7 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
       return FMM_ERR_CUDA;
   if (!put(L.off_comb, comb.data(), comb.size() * sizeof(CombineArgs)) ||
       !put(L.off_comb_start, comb_start.data(), comb_start.size() * 8) ||
+      !put(L.off_copy_start, copy_start.data(), copy_start.size() * 8) ||
       !put(L.off_direct, dir.data(), dir.size() * sizeof(DirectArgs)) ||
       !put(L.off_unit_start, unit_start.data(), unit_start.size() * 8) ||
       (!out.empty() && !put(L.off_out, out.data(), out.size() * sizeof(OutArgs))) ||
@@ -954,10 +971,13 @@ static fmm_status batch_run(const Batch* b, cudaStream_t st) {
                  "batch row reduction"))
       return FMM_ERR_CUDA;
   }
-  if (!cuda_ok(launch_combine_batched(reinterpret_cast<const CombineArgs*>(ws + L.off_comb),
-                                      reinterpret_cast<const int64_t*>(ws + L.off_comb_start), 2 * n, b->comb_total,
-                                      b->dt, b->fmt, b->comb_tr, b->comb_smem, st),
+  const CombineArgs* comb = reinterpret_cast<const CombineArgs*>(ws + L.off_comb);
+  if (!cuda_ok(launch_combine_batched(comb, reinterpret_cast<const int64_t*>(ws + L.off_comb_start), b->comb_count,
+                                      b->comb_total, b->dt, b->fmt, b->comb_tr, b->comb_smem, st),
                "batch combination pass") ||
+      !cuda_ok(launch_convert_batched(comb + b->comb_count, reinterpret_cast<const int64_t*>(ws + L.off_copy_start),
+                                      b->copy_count, b->copy_total, b->dt, b->fmt, st),
+               "batch conversion pass") ||
       !cuda_ok(launch_direct_gemm_batched(b->layout, reinterpret_cast<const DirectArgs*>(ws + L.off_direct),
                                           reinterpret_cast<const int64_t*>(ws + L.off_unit_start), n, b->unit_total,
                                           b->fmt, kBatchTileN, st),

@@ -334,27 +334,83 @@ __global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_kernel(const Com
   combine_staged_body<DT, FMT, TR, RPT, BETWEEN>(a, blockIdx.x, blockIdx.y, tile4, r_begin, r_end);
 }
 
-// Index of the problem whose [start[p], start[p + 1]) range holds idx.
-__device__ __forceinline__ int find_problem(const int64_t* start, int count, int64_t idx) {
-  int lo = 0, hi = count - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(start + mid) <= idx) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Batched form: CTA b belongs to entry p with start[p] <= b < start[p + 1]
-// and covers tile (local mod gx, local / gx), gx = p_cols / 64.
+// Batched form: tile b belongs to entry p with start[p] <= b < start[p + 1]
+// and covers (local mod gx, local / gx), gx = p_cols / 64.  CTAs loop over
+// tiles b = blockIdx.x, + gridDim.x, ... (the launch gives one per tile).
 template <int DT, int FMT, int TR, int RPT>
 __global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_batched_kernel(const CombineArgs* args,
-                                                                              const int64_t* start, int count) {
+                                                                              const int64_t* start, int count,
+                                                                              int64_t total) {
   extern __shared__ float4 tile4[];
-  const int p = find_problem(start, count, blockIdx.x);
+  for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int p = warp_find_problem(start, count, b);
+    const CombineArgs& a = args[p];
+    const int64_t local = b - __ldg(start + p), gx = a.p_cols / kTC;
+    combine_staged_body<DT, FMT, TR, RPT>(a, local % gx, local / gx, tile4, 0, (int)a.num_leaves);
+    __syncthreads();  // the next tile reuses the shared memory
+  }
+}
+
+// Batched conversion for entries whose combination is a single term of a
+// single block with one leaf (the classical product): out = round(c x')
+// with x' the scaled source element, zero in the padding -- the staged
+// pass's arithmetic without its staging.  A CTA covers kConvRows rows x 512
+// columns of one entry: each thread takes 8 consecutive columns of
+// kConvRows / 4 rows, issuing all of its loads before any store, so that
+// small entries still keep many bytes in flight.
+constexpr int kConvRows = 16, kConvCols = 512, kConvIt = kConvRows / 4;
+
+template <int DT, int FMT>
+__global__ void __launch_bounds__(256) convert_batched_kernel(const CombineArgs* args, const int64_t* start, int count) {
+  const int p = warp_find_problem(start, count, blockIdx.x);
   const CombineArgs& a = args[p];
-  const int64_t local = blockIdx.x - __ldg(start + p), gx = a.p_cols / kTC;
-  combine_staged_body<DT, FMT, TR, RPT>(a, local % gx, local / gx, tile4, 0, (int)a.num_leaves);
+  const int64_t local = blockIdx.x - __ldg(start + p);
+  const int64_t gx = (a.p_cols + kConvCols - 1) / kConvCols;
+  const int64_t r0 = (local / gx) * kConvRows + (threadIdx.x >> 6);
+  const int64_t lc = (local % gx) * kConvCols + (threadIdx.x & 63) * 8;
+  if (lc >= a.p_cols) return;
+  const int es = DT == kF32 ? 4 : 2;
+  const bool vec_ok = ((uintptr_t)a.src % (4 * es) == 0) && (a.ld % 4 == 0);
+  const float coef = __ldg(a.t_coef);
+  const int64_t nr = min(a.b_rows, a.rows), nc = min(a.b_cols, a.cols);
+  const bool vec_cols = vec_ok && lc + 8 <= nc;
+  float x[kConvIt][8];
+#pragma unroll
+  for (int it = 0; it < kConvIt; ++it) {
+    const int64_t lr = r0 + 4 * it;
+    const char* src_row = static_cast<const char*>(a.src) + lr * a.ld * es;
+    if (lr < nr && vec_cols) {
+      float v0[4], v1[4];
+      load4<DT>(src_row, lc, v0);
+      load4<DT>(src_row, lc + 4, v1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        x[it][j] = v0[j];
+        x[it][4 + j] = v1[j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[it][j] = (lr < nr && lc + j < nc) ? load_elem<DT>(src_row, lc + j) : 0.f;
+    }
+  }
+  int ec[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) ec[j] = (a.ce && lc + j < nc) ? a.cs * __ldg(a.ce + lc + j) : 0;
+  const int64_t plane = a.p_rows * a.p_cols;
+#pragma unroll
+  for (int it = 0; it < kConvIt; ++it) {
+    const int64_t lr = r0 + 4 * it;
+    if (lr >= a.p_rows) break;
+    const int er = (a.re && lr < nr) ? a.rs * __ldg(a.re + lr) : 0;
+    unsigned short* out = static_cast<unsigned short*>(a.out) + lr * a.p_cols + lc;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float acc[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] = fmaf(coef, scale_pow2(x[it][4 * h + j], er + ec[4 * h + j]), 0.f);
+      store4<FMT>(out + 4 * h, out + 4 * h + plane, acc);
+    }
+  }
 }
 
 static int device_sms() {
@@ -614,8 +670,7 @@ __device__ __forceinline__ void out_combine_body(const OutArgs& a, int64_t bx, i
       }
     }
   }
-  if (lr >= c.bm) return;
-  for (int k = 0; k < (int)a.c_blocks; ++k) {
+  for (int k = 0; k < (int)a.c_blocks && lr < c.bm; ++k) {
     const int bi = k / pn, bj = k % pn;
     const int64_t gi = bi * c.bm + lr, gj = bj * c.bn + lc;
     if (gi >= c.M) continue;
@@ -816,12 +871,15 @@ __global__ void __launch_bounds__(kOutGatherRows * 16) out_gather_kernel(const O
 // and covers position tile (local mod gx, local / gx), gx = ceil(bn / 64).
 template <int TR>
 __global__ void __launch_bounds__(TR * 16) out_combine_batched_kernel(const OutArgs* args, const int64_t* start,
-                                                                      int count) {
+                                                                      int count, int64_t total) {
   extern __shared__ float4 acc4[];
-  const int p = find_problem(start, count, blockIdx.x);
-  const OutArgs& a = args[p];
-  const int64_t local = blockIdx.x - __ldg(start + p), gx = (a.c.bn + kTC - 1) / kTC;
-  out_combine_body<TR>(a, local % gx, local / gx, acc4);
+  for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int p = warp_find_problem(start, count, b);
+    const OutArgs& a = args[p];
+    const int64_t local = b - __ldg(start + p), gx = (a.c.bn + kTC - 1) / kTC;
+    out_combine_body<TR>(a, local % gx, local / gx, acc4);
+    __syncthreads();  // the next tile reuses the shared memory
+  }
 }
 
 // Node-exponent pass (scaling between recursive steps): one CTA covers a
@@ -928,6 +986,32 @@ __global__ void between_finalize_kernel(const int* cexp, const int* rexp, int* d
 }
 
 }  // namespace
+
+// CTAs of one entry of the conversion above.
+int64_t convert_batched_ctas(const CombineArgs& a) {
+  return ((a.p_rows + kConvRows - 1) / kConvRows) * ((a.p_cols + kConvCols - 1) / kConvCols);
+}
+
+cudaError_t launch_convert_batched(const CombineArgs* args, const int64_t* start, int count, int64_t total, int dt,
+                                   int fmt, cudaStream_t st) {
+  if (total == 0 || count == 0) return cudaSuccess;
+  if (total > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  KernelTimer timer("combine", st);
+#define FMM_CV(DT)                                                                                              \
+  switch (fmt) {                                                                                                \
+    case FMM_LEAF_BF16: convert_batched_kernel<DT, FMM_LEAF_BF16><<<(unsigned)total, 256, 0, st>>>(args, start, count); break; \
+    case FMM_LEAF_F16: convert_batched_kernel<DT, FMM_LEAF_F16><<<(unsigned)total, 256, 0, st>>>(args, start, count); break;   \
+    default: convert_batched_kernel<DT, FMM_LEAF_BF16X3><<<(unsigned)total, 256, 0, st>>>(args, start, count); break;         \
+  }
+  switch (dt) {
+    case kF32: FMM_CV(kF32) break;
+    case kBF16: FMM_CV(kBF16) break;
+    default: FMM_CV(kF16) break;
+  }
+#undef FMM_CV
+  return cudaGetLastError();
+}
+
 
 // E4M3 combination pass: one CTA covers TT t x 128 k (one scale block) of
 // every leaf block (TT = 16, or 4 when the input blocks are too many to
@@ -1173,7 +1257,11 @@ static void launch_combine_batched_tr(const CombineArgs* args, const int64_t* st
                          (int)kStagedSmemMax);
     attr_done[dev] = true;
   }
-  combine_staged_batched_kernel<DT, FMT, TR, RPT><<<(unsigned)total, TR * 16 / RPT, smem, st>>>(args, start, count);
+  // one CTA per tile (a grid of a few CTAs per SM looping over the tiles
+  // measured slower: it loses the overlap of one tile's loads with
+  // another's arithmetic that independent CTAs give)
+  combine_staged_batched_kernel<DT, FMT, TR, RPT><<<(unsigned)total, TR * 16 / RPT, smem, st>>>(args, start, count,
+                                                                                                total);
 }
 
 template <int DT, int FMT>
@@ -1223,7 +1311,7 @@ cudaError_t launch_out_combine_batched(const OutArgs* args, const int64_t* start
       cudaFuncSetAttribute(out_combine_batched_kernel<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr_done[dev] = true;
     }
-    out_combine_batched_kernel<TR><<<(unsigned)total, TR * 16, smem, st>>>(args, start, count);
+    out_combine_batched_kernel<TR><<<(unsigned)total, TR * 16, smem, st>>>(args, start, count, total);
   };
   switch (tr) {
     case 32: go(std::integral_constant<int, 32>()); break;

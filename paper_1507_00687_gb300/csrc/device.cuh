@@ -86,6 +86,26 @@ __device__ __forceinline__ float scale_pow2(float x, int e) {
   return (x * exp2i(h)) * exp2i(e - h);
 }
 
+// Index p of the problem whose [start[p], start[p + 1]) holds idx (start
+// ascending, start[0] = 0, count problems; empty problems allowed: the last
+// p with start[p] <= idx).  The 32 lanes of a warp search together: each
+// round loads 32 evenly spaced entries of the remaining range at once, so
+// two or three dependent loads replace the log2(count) of a binary search.
+// Every lane of the warp calls it with the same arguments.
+__device__ __forceinline__ int warp_find_problem(const int64_t* start, int count, int64_t idx) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = count;  // start[lo] <= idx, and idx < start[hi] when hi < count
+  while (hi - lo > 1) {
+    const int step = (hi - lo + 31) >> 5;
+    const int probe = lo + lane * step;
+    const bool le = probe < hi && __ldg(start + probe) <= idx;
+    const unsigned m = __ballot_sync(0xffffffffu, le);
+    lo += (31 - __clz((int)m)) * step;
+    hi = min(hi, lo + step);
+  }
+  return lo;
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -235,6 +235,12 @@ cudaError_t launch_out_gather(const OutArgs& a, cudaStream_t st);
 // (rows per CTA) from combine_batched_rows / out_batched_rows for the largest
 // block count of the batch; smem the largest entry's shared memory.
 int combine_batched_rows(int64_t max_blocks);
+// Batched entries whose combination is one term of one block with one leaf
+// (the classical product): a plain scaled conversion with wide tiles;
+// start[p] is the first CTA of entry p (convert_batched_ctas CTAs each).
+int64_t convert_batched_ctas(const CombineArgs& a);
+cudaError_t launch_convert_batched(const CombineArgs* args, const int64_t* start, int count, int64_t total, int dt,
+                                   int fmt, cudaStream_t st);
 int out_batched_rows(int64_t max_c_blocks);
 size_t combine_staged_smem(int64_t nb, int tr, int64_t nnz, int64_t leaves);
 cudaError_t launch_combine_batched(const CombineArgs* args, const int64_t* start, int count, int64_t total, int dt,

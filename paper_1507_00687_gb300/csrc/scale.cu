@@ -183,18 +183,6 @@ __global__ void __launch_bounds__(kRowWarps * 32) row_exp_kernel(const void* X, 
   if (nf) atomicOr(status, kStatusNonfinite);
 }
 
-// Index of the problem whose [start[p], start[p + 1]) range holds idx
-// (start ascending, start[0] = 0, count problems).
-__device__ __forceinline__ int batch_find(const int64_t* start, int count, int64_t idx) {
-  int lo = 0, hi = count - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(start + mid) <= idx) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 // Batched row reduction: warp w of the launch takes global row w; rows of
 // problem p are [start[p], start[p + 1]).
 template <int DT, bool SHIFT>
@@ -204,7 +192,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) row_exp_batched_kernel(const R
   bool nf = false;
   const int64_t g = (int64_t)blockIdx.x * kRowWarps + (threadIdx.x >> 5);
   if (g >= __ldg(start + count)) return;
-  const int p = batch_find(start, count, g);
+  const int p = warp_find_problem(start, count, g);
   const ReduceArgs a = args[p];
   row_exp_one<DT, SHIFT>(a.X, a.C, a.ld, a.shift, a.sign, a.out, mode, a.vec != 0, g - __ldg(start + p),
                          threadIdx.x & 31, &nf);
@@ -317,7 +305,7 @@ __global__ void __launch_bounds__(kColThreads) col_exp_batched_kernel(const Redu
                                                                       int count, int* status) {
   extern __shared__ int red[];
   bool nf = false;
-  const int p = batch_find(start, count, blockIdx.x);
+  const int p = warp_find_problem(start, count, blockIdx.x);
   const ReduceArgs a = args[p];
   const int64_t local = blockIdx.x - __ldg(start + p);
   col_exp_cta<DT, SHIFT>(a.X, a.R, a.C, a.ld, a.shift, a.sign, a.out, a.rows_per_cta, a.vec != 0, local % a.gx,
