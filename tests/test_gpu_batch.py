@@ -155,3 +155,37 @@ def test_batch_many_products_fused_epilogue(api):
         assert_within(first, Cref, G, nm, Ad.shape[1], "bf16x3", f"fused batch {nm}")
         for copy in range(1, 8):
             assert np.array_equal(dev_values(probs[copy * n + i][3]), first)
+
+
+def test_batch_with_trees_and_rotations(api):
+    # Non-uniform plans and rotated rules in one batch with uniform ones:
+    # each product within tolerance against the oracle's tree.
+    import tree_cases as TC
+    from oracle import fmm as OF
+    from gpu_common import U_LEAF
+    cases = [(TC.dalberto(), 300, 256, 280), (TC.mixed_rank(), 200, 128, 160), (["F_r1", []], 270, 390, 200),
+             (["S", ["S"] * 7], 256, 256, 256)]
+    probs, trees = [], []
+    for i, (desc, M, K, N) in enumerate(cases):
+        if desc[1]:
+            lib, orc = TC.two_level(*desc)
+            plan = api.Plan.tree(lib, "bf16x3")
+        else:
+            plan = api.Plan([TC.package_rule(desc[0])], "bf16x3")
+            orc = OF.uniform([TC.oracle_rule(desc[0])])
+        A, B = inputs.diag_scaled_pair(M, K, N, seed=700 + i, span=6.0)
+        probs.append((plan, to_dev(A, "f32"), to_dev(B, "f32"), torch.full((M, N), float("nan"), device="cuda")))
+        trees.append(orc)
+    batch = api.Batch(probs, "OI")
+    batch.run()
+    api.sync_status()
+    for (plan, Ad, Bd, C), orc in zip(probs, trees):
+        A64, B64 = dev_values(Ad), dev_values(Bd)
+        st = OS.pow2_repeated(A64, B64, "OI")
+        Ap, Bp = OS.pow2_apply(A64, B64, st.eA, st.d, st.eB)
+        Cref = OS.pow2_unscale(OF.fmm(Ap, Bp, orc), st.eA, st.eB)
+        G = OS.pow2_unscale(OF.growth(Ap, Bp, orc), st.eA, st.eB)
+        _, pk, _ = OF.dims(orc)
+        kl = -(-Ad.shape[1] // pk)
+        tol = (U_LEAF["bf16x3"] + (kl + 2 * TC.max_terms(orc) + 8) * 2.0**-23) * G
+        assert np.all(np.abs(dev_values(C) - Cref) <= tol)
