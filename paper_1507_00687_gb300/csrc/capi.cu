@@ -552,8 +552,7 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
     cb.between_sign = -1;
   }
   // B first: a scaling sequence that ends with a pass over B leaves it in L2
-  if (!cuda_ok(launch_combine(cb, st), "combination pass (B)")) return FMM_ERR_CUDA;
-  if (!cuda_ok(launch_combine(ca, st), "combination pass (A)")) return FMM_ERR_CUDA;
+  if (!cuda_ok(launch_combine_pair(cb, ca, st), "combination passes")) return FMM_ERR_CUDA;
   DirectArgs d;
   if (!direct_args(p, g, x, y, c, leaves, wa, wb, mbuf, status, &d)) return FMM_ERR_CUDA;
   if (!cuda_ok(launch_direct_gemm(d, p->leaf_format, g.bn, st), "multiply launch")) return FMM_ERR_CUDA;

@@ -488,13 +488,10 @@ __device__ __forceinline__ float scale_fast(float x, int e) {
 // tr + 16 of 4 columns each.  The term list sits in shared memory as
 // (float4 offset of the term's tile, coefficient) pairs.
 template <int DT, int FMT, int NRB, int NCB>
-__global__ void __launch_bounds__(256) combine_small_kernel(const CombineArgs a) {
-  constexpr int TR = 32, NB = NRB * NCB;
-  __shared__ float4 tile4[NB * TR * 16];
-  extern __shared__ int2 terms[];  // [nnz] (offset, coef bits), then tstart[R + 1]
-  pdl_wait();
-  pdl_trigger();
-  const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * kTC;
+__device__ __forceinline__ void combine_small_body(const CombineArgs& a, int64_t bx, int64_t by, float4* tile4,
+                                                   int2* terms) {
+  constexpr int TR = 32;
+  const int64_t r0 = by * TR, c0 = bx * kTC;
   const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15, tc = tq * 4;
   const int es = DT == kF32 ? 4 : 2;
   const bool vec_ok = ((uintptr_t)a.src % (4 * es) == 0) && (a.ld % 4 == 0) && (a.b_cols % 4 == 0) &&
@@ -576,6 +573,34 @@ __global__ void __launch_bounds__(256) combine_small_kernel(const CombineArgs a)
   }
 }
 
+template <int DT, int FMT, int NRB, int NCB>
+__global__ void __launch_bounds__(256) combine_small_kernel(const CombineArgs a) {
+  __shared__ float4 tile4[NRB * NCB * 32 * 16];
+  extern __shared__ int2 terms[];  // [nnz] (offset, coef bits), then tstart[R + 1]
+  pdl_wait();
+  pdl_trigger();
+  combine_small_body<DT, FMT, NRB, NCB>(a, blockIdx.x, blockIdx.y, tile4, terms);
+}
+
+// Both operands' combination in one launch (the two passes are independent):
+// CTAs [0, split) take a0's tiles, the rest a1's (linear tile indices, gx0 /
+// gx1 tiles per tile row).
+template <int DT, int FMT, int NRB, int NCB>
+__global__ void __launch_bounds__(256) combine_small_pair_kernel(const CombineArgs a0, const CombineArgs a1,
+                                                                 unsigned split) {
+  __shared__ float4 tile4[NRB * NCB * 32 * 16];
+  extern __shared__ int2 terms[];
+  pdl_wait();
+  pdl_trigger();
+  if (blockIdx.x < split) {
+    const int64_t gx = a0.p_cols / kTC;
+    combine_small_body<DT, FMT, NRB, NCB>(a0, blockIdx.x % gx, blockIdx.x / gx, tile4, terms);
+  } else {
+    const int64_t gx = a1.p_cols / kTC, b = blockIdx.x - split;
+    combine_small_body<DT, FMT, NRB, NCB>(a1, b % gx, b / gx, tile4, terms);
+  }
+}
+
 template <int DT, int FMT>
 void launch_small(const CombineArgs& a, cudaStream_t st) {
   const dim3 grid((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / 32));
@@ -586,14 +611,36 @@ void launch_small(const CombineArgs& a, cudaStream_t st) {
   else launch_pdl(combine_small_kernel<DT, FMT, 1, 1>, grid, dim3(256), smem, st, a);
 }
 
+// The operand combination for which the unrolled form applies (see
+// launch_fmt): at most 2 x 2 blocks, no between-steps scale, a grid that
+// fills the GPU, a small term list.
+bool small_ok(const CombineArgs& a, int sms) {
+  return a.n_rb <= 2 && a.n_cb <= 2 && !a.between_d && a.p_rows % 32 == 0 && a.p_cols % kTC == 0 &&
+         (a.p_cols / kTC) * (a.p_rows / 32) >= 2 * (int64_t)sms && a.t_nnz * 8 + (a.num_leaves + 1) * 4 <= 16384;
+}
+
+template <int DT, int FMT>
+void launch_small_pair(const CombineArgs& a0, const CombineArgs& a1, cudaStream_t st) {
+  const int64_t t0 = (a0.p_cols / kTC) * (a0.p_rows / 32), t1 = (a1.p_cols / kTC) * (a1.p_rows / 32);
+  const size_t smem = std::max((size_t)a0.t_nnz * 8 + (size_t)(a0.num_leaves + 1) * 4,
+                               (size_t)a1.t_nnz * 8 + (size_t)(a1.num_leaves + 1) * 4);
+  const dim3 grid((unsigned)(t0 + t1));
+  if (a0.n_rb == 2 && a0.n_cb == 2)
+    launch_pdl(combine_small_pair_kernel<DT, FMT, 2, 2>, grid, dim3(256), smem, st, a0, a1, (unsigned)t0);
+  else if (a0.n_rb == 2)
+    launch_pdl(combine_small_pair_kernel<DT, FMT, 2, 1>, grid, dim3(256), smem, st, a0, a1, (unsigned)t0);
+  else if (a0.n_cb == 2)
+    launch_pdl(combine_small_pair_kernel<DT, FMT, 1, 2>, grid, dim3(256), smem, st, a0, a1, (unsigned)t0);
+  else
+    launch_pdl(combine_small_pair_kernel<DT, FMT, 1, 1>, grid, dim3(256), smem, st, a0, a1, (unsigned)t0);
+}
+
 template <int DT, int FMT>
 void launch_fmt(const CombineArgs& a, dim3 grid, cudaStream_t st) {
   const int64_t nb = a.n_rb * a.n_cb;
   const int tr = nb <= 4 ? 32 : nb <= 8 ? 16 : nb <= 16 ? 8 : nb <= 32 ? 4 : 2;
   // few leaves on a grid that already fills the GPU: the unrolled form
-  const bool small = a.n_rb <= 2 && a.n_cb <= 2 && !a.between_d && a.p_rows % 32 == 0 &&
-                     (int64_t)grid.x * (a.p_rows / 32) >= 2 * device_sms() && a.t_nnz * 8 + (a.num_leaves + 1) * 4 <= 16384;
-  if (small)
+  if (small_ok(a, device_sms()))
     launch_small<DT, FMT>(a, st);
   else if (nb <= kMaxStaged && staged_smem((int)nb, tr, a.t_nnz, a.num_leaves) <= kStagedSmemMax)
     launch_staged<DT, FMT>(a, (int)nb, st);
@@ -1341,6 +1388,33 @@ cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st) {
     case kBF16: return launch_dt<kBF16>(a, grid, st);
     default: return launch_dt<kF16>(a, grid, st);
   }
+}
+
+cudaError_t launch_combine_pair(const CombineArgs& a0, const CombineArgs& a1, cudaStream_t st) {
+  const int sms = device_sms();
+  const bool pair = small_ok(a0, sms) && small_ok(a1, sms) && a0.dtype == a1.dtype && a0.fmt == a1.fmt &&
+                    a0.n_rb == a1.n_rb && a0.n_cb == a1.n_cb && a0.num_leaves > 0 && a1.num_leaves > 0 &&
+                    a0.b_rows <= a0.p_rows && a0.b_cols <= a0.p_cols && a1.b_rows <= a1.p_rows &&
+                    a1.b_cols <= a1.p_cols &&
+                    (a0.p_cols / kTC) * (a0.p_rows / 32) + (a1.p_cols / kTC) * (a1.p_rows / 32) < 0x7FFFFFFF;
+  if (!pair) {
+    const cudaError_t e = launch_combine(a0, st);
+    return e != cudaSuccess ? e : launch_combine(a1, st);
+  }
+  KernelTimer timer("combine", st);
+#define FMM_PAIR(DT)                                                              \
+  switch (a0.fmt) {                                                               \
+    case FMM_LEAF_BF16: launch_small_pair<DT, FMM_LEAF_BF16>(a0, a1, st); break;  \
+    case FMM_LEAF_F16: launch_small_pair<DT, FMM_LEAF_F16>(a0, a1, st); break;    \
+    default: launch_small_pair<DT, FMM_LEAF_BF16X3>(a0, a1, st); break;          \
+  }
+  switch (a0.dtype) {
+    case kF32: FMM_PAIR(kF32) break;
+    case kBF16: FMM_PAIR(kBF16) break;
+    default: FMM_PAIR(kF16) break;
+  }
+#undef FMM_PAIR
+  return cudaGetLastError();
 }
 
 }  // namespace fmm

@@ -182,6 +182,9 @@ cudaError_t launch_node_exp(const CombineArgs& a, int* out, int64_t k1, cudaStre
 cudaError_t launch_between_finalize(const int* cexp, const int* rexp, int* d, int64_t n, cudaStream_t st);
 
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st);
+// Both operands' combination passes, in one launch when both take the
+// unrolled small-block form, else as two launches (a0 first).
+cudaError_t launch_combine_pair(const CombineArgs& a0, const CombineArgs& a1, cudaStream_t st);
 
 // Multiply kernel over combined operands (the pass schedule): each operand
 // is the 16-bit output of the combination pass, K-major ([plane][R][tp][kp],
