@@ -7,11 +7,12 @@
 // fold it into FP32 running sums (running = fma(block, 2^sa 2^sb, running),
 // blocks in order) and store the finished tile of M_r for the output pass.
 //
-//   warps 0-7  epilogue: warps w and w + 4 share TMEM lanes 32 (w mod 4) ..
-//              + 31 (one tile row per thread) and take 64 columns each
-//   warp 8     lane 0: TMEM allocator and tcgen05.mma issuer (kind::f8f6f4,
+//   warps 0-15 epilogue: warps w, w + 4, w + 8, w + 12 share TMEM lanes
+//              32 (w mod 4) .. + 31 (one tile row per thread) and take 32
+//              columns each
+//   warp 16    lane 0: TMEM allocator and tcgen05.mma issuer (kind::f8f6f4,
 //              four K = 32 steps per block)
-//   warp 9     lane 0: TMA issuer: per stage the A and B tiles (128 x 128
+//   warp 17    lane 0: TMA issuer: per stage the A and B tiles (128 x 128
 //              bytes, K-major, 128-byte swizzle) and the block's 128 column
 //              factors 2^sb (one bulk copy)
 //
@@ -38,7 +39,8 @@ using gemm::mbar_arrive_expect_tx;
 using gemm::tma_load_2d;
 
 constexpr int BM = 128, BN = 128, BK = 128;  // BK in bytes = elements
-constexpr int kEpiWarps = 8, kMmaWarp = 8, kTmaWarp = 9, kThreads = 10 * 32;
+constexpr int kEpiWarps = 16, kMmaWarp = 16, kTmaWarp = 17, kThreads = 18 * 32;
+constexpr int kEpiCols = BN / (kEpiWarps / 4);  // tile columns per epilogue thread
 constexpr int kTile = 128 * 128;
 constexpr int kScaleBytes = 128 * 4;
 constexpr int kStage = 2 * kTile + 1024;  // tiles + column factors, 1024-aligned
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp8_fmm_kernel(const __grid_const
     __syncwarp();
   } else {
     // -------------------------------------------------------- epilogue
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, group = warp >> 2;
     const int row = quarter * 32 + lane;
     int stage = 0;
     uint32_t phase = 0, acc_iter = 0;
@@ -179,9 +181,9 @@ __global__ void __launch_bounds__(kThreads, 1) fp8_fmm_kernel(const __grid_const
     for (int64_t u = blockIdx.x; u < total && ok; u += gridDim.x) {
       const int64_t leaf = u / ntiles, tile = u % ntiles, tm = tile / ntn, tn = tile % ntn;
       const int64_t ml = tm * BM + row;
-      float run[64];
+      float run[kEpiCols];
 #pragma unroll
-      for (int j = 0; j < 64; ++j) run[j] = 0.f;
+      for (int j = 0; j < kEpiCols; ++j) run[j] = 0.f;
       for (int64_t kb = 0; kb < KB; ++kb) {
         const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
         const float fa = __ldg(args.fa + (leaf * KB + kb) * args.tp_a + ml);
@@ -189,11 +191,11 @@ __global__ void __launch_bounds__(kThreads, 1) fp8_fmm_kernel(const __grid_const
         ok = __all_sync(0xffffffffu, mbar_wait_bounded(&tfull[buf], aph, abort_flag, args.timeout_ns));
         if (!ok) break;
         tc_fence_after();
-        const float* fb = reinterpret_cast<const float*>(smem + stage * kStage + 2 * kTile) + half * 64;
+        const float* fb = reinterpret_cast<const float*>(smem + stage * kStage + 2 * kTile) + group * kEpiCols;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < kEpiCols / 32; ++c) {
           uint32_t r[32];
-          tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + half * 64 + c * 32, r);
+          tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + group * kEpiCols + c * 32, r);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const float4 f = *reinterpret_cast<const float4*>(fb + c * 32 + 4 * q);
@@ -211,9 +213,9 @@ __global__ void __launch_bounds__(kThreads, 1) fp8_fmm_kernel(const __grid_const
         if (++stage == kStages) { stage = 0; phase ^= 1u; }
       }
       if (!ok) break;
-      float* dst = args.mbuf + (leaf * args.tp_a + ml) * args.tp_b + tn * BN + half * 64;
+      float* dst = args.mbuf + (leaf * args.tp_a + ml) * args.tp_b + tn * BN + group * kEpiCols;
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
+      for (int q = 0; q < kEpiCols / 4; ++q)
         *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(run[4 * q], run[4 * q + 1], run[4 * q + 2], run[4 * q + 3]);
     }
     if (!ok) *abort_flag = 1;
