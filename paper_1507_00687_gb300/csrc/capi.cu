@@ -276,7 +276,7 @@ static int64_t pass_bytes(const Plan* p, int64_t Tx, int64_t Kd, int64_t Ty, int
   if (p->leaf_format == FMM_LEAF_E4M3B128) {
     // bytes of S_r and T_r, their per-block factors, the stored products
     const int64_t R = p->leaves;
-    const int64_t ta = round_up(ceil_div(Tx, ptx), 128), tb = round_up(ceil_div(Ty, pty), 128);
+    const int64_t ta = round_up(ceil_div(Tx, ptx), 128), tb = round_up(ceil_div(Ty, pty), 256);
     const int64_t kp = round_up(ceil_div(Kd, pk), 128);
     return round_up(R * ta * kp, 256) + round_up(R * (kp / 128) * ta * 4, 256) + round_up(R * tb * kp, 256) +
            round_up(R * (kp / 128) * tb * 4, 256) + round_up(R * ta * tb * 4, 256);
@@ -443,7 +443,7 @@ static fmm_status run_pass_fp8(const Plan* p, const Source& x, const Source& y, 
   PassGeom g = pass_geom(p, x, y, 128);
   g.planes = 1;
   g.tp_a = round_up(g.bt_a, 128);
-  g.tp_b = round_up(g.bt_b, 128);
+  g.tp_b = round_up(g.bt_b, 256);  // the E4M3 multiply kernel's 256-wide tiles
   g.kp = round_up(g.bk, 128);
   const int64_t R = g.R, KB = g.kp / 128;
   const int64_t ba = round_up(R * g.tp_a * g.kp, 256), fa = round_up(R * KB * g.tp_a * 4, 256);
@@ -457,6 +457,10 @@ static fmm_status run_pass_fp8(const Plan* p, const Source& x, const Source& y, 
   float* sb = reinterpret_cast<float*>(w + ba + fa + bb);
   float* mbuf = reinterpret_cast<float*>(w + ba + fa + bb + fbb);
   CombineArgs ca = combine_args(p, g, x, 0, leaves, wa), cb = combine_args(p, g, y, 1, leaves, wb);
+  if (!e4m3_combine_fits(ca) || !e4m3_combine_fits(cb)) {
+    t_last_error = "E4M3 leaves: too many input blocks per operand for the combination pass";
+    return FMM_ERR_UNSUPPORTED;
+  }
   // both sides K-major: [leaf][t][k]
   ca.p_rows = g.tp_a;
   ca.p_cols = g.kp;
@@ -481,8 +485,12 @@ static fmm_status run_pass_fp8(const Plan* p, const Source& x, const Source& y, 
   f.status = status;
   f.timeout_ns = timeout_ns();
   if (!cuda_ok(launch_fp8_gemm(f, st), "E4M3 multiply launch")) return FMM_ERR_CUDA;
-  return cuda_ok(launch_out_combine(out_args(p, g, c, leaves, mbuf), st), "output combination pass") ? FMM_OK
-                                                                                                     : FMM_ERR_CUDA;
+  const OutArgs o = out_args(p, g, c, leaves, mbuf);
+  const bool gather = p->pm * p->pn > kMaxOutBlocks;
+  if (gather && p->gather_off < 0) return FMM_ERR_UNSUPPORTED;
+  return cuda_ok(gather ? launch_out_gather(o, st) : launch_out_combine(o, st), "output combination pass")
+             ? FMM_OK
+             : FMM_ERR_CUDA;
 }
 
 static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, const EpilogueArgs& c,

@@ -1162,6 +1162,11 @@ __global__ void __launch_bounds__(TT * 32) combine_e4m3_kernel(const CombineArgs
   }
 }
 
+bool e4m3_combine_fits(const CombineArgs& a) {
+  const size_t list = (size_t)a.t_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
+  return (size_t)(a.n_rb * a.n_cb) * 4 * kF8Stride * 4 + list <= kStagedSmemMax;
+}
+
 cudaError_t launch_combine_e4m3(const CombineArgs& a, cudaStream_t st) {
   if (a.p_rows % kF8TT != 0 || a.p_cols % 128 != 0) return cudaErrorInvalidValue;
   const int64_t nb = a.n_rb * a.n_cb;

@@ -38,13 +38,14 @@ namespace fp8 {
 using gemm::mbar_arrive_expect_tx;
 using gemm::tma_load_2d;
 
-constexpr int BM = 128, BN = 128, BK = 128;  // BK in bytes = elements
+constexpr int BM = 128, BN = 256, BK = 128;  // BK in bytes = elements
 constexpr int kEpiWarps = 16, kMmaWarp = 16, kTmaWarp = 17, kThreads = 18 * 32;
 constexpr int kEpiCols = BN / (kEpiWarps / 4);  // tile columns per epilogue thread
-constexpr int kTile = 128 * 128;
-constexpr int kScaleBytes = 128 * 4;
-constexpr int kStage = 2 * kTile + 1024;  // tiles + column factors, 1024-aligned
-constexpr int kStages = 6;
+constexpr int kTile = BM * BK;                 // A tile
+constexpr int kTileB = BN * BK;                // B tile (two 128-row boxes)
+constexpr int kScaleBytes = BN * 4;
+constexpr int kStage = kTile + kTileB + kScaleBytes;  // tiles + column factors, 1024-aligned
+constexpr int kStages = 4;
 constexpr int kTmemCols = 2 * BN;
 constexpr int kSmem = kStages * kStage + 256 + 1024;
 
@@ -120,10 +121,12 @@ __global__ void __launch_bounds__(kThreads, 1) fp8_fmm_kernel(const __grid_const
         for (int64_t kb = 0; kb < KB && ok; ++kb) {
           if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns)) { ok = false; break; }
           uint8_t* st = smem + stage * kStage;
-          mbar_arrive_expect_tx(&full[stage], (uint32_t)(2 * kTile + kScaleBytes));
+          mbar_arrive_expect_tx(&full[stage], (uint32_t)(kTile + kTileB + kScaleBytes));
           tma_load_2d(st, &args.map_a, (int32_t)(kb * BK), (int32_t)(leaf * args.tp_a + tm * BM), &full[stage]);
-          tma_load_2d(st + kTile, &args.map_b, (int32_t)(kb * BK), (int32_t)(leaf * args.tp_b + tn * BN), &full[stage]);
-          bulk_load(st + 2 * kTile, args.fb + (leaf * KB + kb) * args.tp_b + tn * BN, kScaleBytes, &full[stage]);
+          for (int h = 0; h < BN / 128; ++h)
+            tma_load_2d(st + kTile + h * 128 * BK, &args.map_b, (int32_t)(kb * BK),
+                        (int32_t)(leaf * args.tp_b + tn * BN + h * 128), &full[stage]);
+          bulk_load(st + kTile + kTileB, args.fb + (leaf * KB + kb) * args.tp_b + tn * BN, kScaleBytes, &full[stage]);
           armed |= 1u << stage;
           armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
@@ -191,15 +194,15 @@ __global__ void __launch_bounds__(kThreads, 1) fp8_fmm_kernel(const __grid_const
         ok = __all_sync(0xffffffffu, mbar_wait_bounded(&tfull[buf], aph, abort_flag, args.timeout_ns));
         if (!ok) break;
         tc_fence_after();
-        const float* fb = reinterpret_cast<const float*>(smem + stage * kStage + 2 * kTile) + group * kEpiCols;
+        const float* fb = reinterpret_cast<const float*>(smem + stage * kStage + kTile + kTileB) + group * kEpiCols;
 #pragma unroll
-        for (int c = 0; c < kEpiCols / 32; ++c) {
-          uint32_t r[32];
-          tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + group * kEpiCols + c * 32, r);
+        for (int c = 0; c < kEpiCols / 16; ++c) {
+          uint32_t r[16];
+          tmem_ld_32x32b_x16(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + group * kEpiCols + c * 16, r);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float4 f = *reinterpret_cast<const float4*>(fb + c * 32 + 4 * q);
-            const int j = c * 32 + 4 * q;
+          for (int q = 0; q < 4; ++q) {
+            const float4 f = *reinterpret_cast<const float4*>(fb + c * 16 + 4 * q);
+            const int j = c * 16 + 4 * q;
             run[j] = fmaf(__uint_as_float(r[4 * q]), fa * f.x, run[j]);
             run[j + 1] = fmaf(__uint_as_float(r[4 * q + 1]), fa * f.y, run[j + 1]);
             run[j + 2] = fmaf(__uint_as_float(r[4 * q + 2]), fa * f.z, run[j + 2]);

@@ -33,10 +33,13 @@ def test_e4m3_integers_exact(api, names, M, K, N, dt):
 
 
 @pytest.mark.parametrize("names", [["winograd", "classical121", "winograd", "classical121"],
-                                   ["strassen", "strassen", "strassen"]], ids=lambda n: "-".join(n))
+                                   ["strassen", "strassen", "strassen"],
+                                   ["strassen", "strassen", "classical211", "classical211", "classical112"]],
+                         ids=lambda n: "-".join(n))
 def test_e4m3_deep_plans_integers_exact(api, names):
     # Many input blocks per operand (64 for B in the first plan): the
-    # combination pass stages four rows per CTA.  Entries in [-1, 1]: every
+    # combination pass stages four rows per CTA; 16 x 8 = 128 C blocks in
+    # the last: the output pass gathers per C block.  Entries in [-1, 1]: every
     # S, T entry is an integer of magnitude at most 16, exact in E4M3 after
     # its power-of-two block scale.
     M, K, N = 264, 520, 200
@@ -46,6 +49,16 @@ def test_e4m3_deep_plans_integers_exact(api, names):
         got = dev_values(api.multiply(api.Plan(names, "e4m3b128"), to_dev(A, dt), to_dev(B, dt)))
         api.sync_status()
         assert np.array_equal(got, A @ B), dt
+
+
+def test_e4m3_refuses_too_many_input_blocks(api):
+    # 16 x 16 input blocks per operand (Strassen, four levels) exceed what
+    # the E4M3 combination pass stages: refused before any launch
+    from paper_1507_00687_gb300 import _native as N
+    A = to_dev(inputs.integers((128, 128), -1, 1, seed=1), "f32")
+    with pytest.raises(N.FmmError) as e:
+        api.multiply(api.Plan(["strassen"] * 4, "e4m3b128"), A, A)
+    assert e.value.code == 10
 
 
 @pytest.mark.parametrize("names", [["strassen"], ["winograd"], []], ids=lambda n: "-".join(n) or "classical")
