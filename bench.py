@@ -587,11 +587,12 @@ def main():
     achieved = mma_flops / (mult_ms_per * 1e-3) / 1e12
     sched_used = "pass" if kern["combine"][1] > 0 else "load_stage"
     kname = "direct_fmm_kernel" if sched_used == "pass" else "fused_fmm_kernel"
-    # the bandwidth passes of the pass schedule, per step: two combination
-    # passes (each reads its operand once and writes R^L combined leaf
-    # blocks: two bf16 planes for bf16x3, else one 16-bit plane) and, with
-    # stored leaf products, the output pass (reads the R^L fp32 products,
-    # writes C)
+    # the bandwidth passes of the pass schedule, per step: the combination
+    # of both operands (one launch for small operands, else one per
+    # operand; each operand read once, R^L combined leaf blocks written:
+    # two bf16 planes for bf16x3, else one 16-bit plane) and, with stored
+    # leaf products (every pass-schedule plan with more than one leaf at
+    # these sizes), the output pass (reads the R^L fp32 products, writes C)
     planes = 2 if args.leaf == "bf16x3" else 1
     R = info["leaves"]
     bt = -(-n // info["pm"])
@@ -600,7 +601,7 @@ def main():
     comb_ms, comb_n = kern["combine"]
     per_step = comb_n // max(1, bd_steps)
     pass_bytes = 2 * n * n * 4 + planes * R * (tp_a + tp_b) * kp * 2
-    if per_step >= 3:
+    if sched_used == "pass" and R > 1:
         pass_bytes += R * tp_a * tp_b * 4 + n * n * 4
     kernel_times = {k or "all": {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / max(1, v[1])}
                     for k, v in kern.items()}
