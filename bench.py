@@ -294,6 +294,45 @@ def oracle_step(A, B, args):
     return time.perf_counter() - t0
 
 
+def host_link(h_src, d_buf, h_dst, reps=5):
+    """Copy-engine rates of the host link (GB/s, best of ``reps``): pinned
+    host -> device, device -> pinned host, and both at once on two streams
+    (each way).  ``h_src``, ``d_buf`` and ``h_dst`` have the same size."""
+    import torch
+    nbytes = h_src.numel() * h_src.element_size()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    d2 = torch.empty_like(d_buf)
+
+    def best(fn):
+        t = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t = min(t, e0.elapsed_time(e1))
+        return nbytes / (t * 1e-3) / 1e9
+
+    def both():
+        cur = torch.cuda.current_stream()
+        for s in (s1, s2):
+            s.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            d_buf.copy_(h_src, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_dst.copy_(d2, non_blocking=True)
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+
+    out = {"h2d_GBps": best(lambda: d_buf.copy_(h_src, non_blocking=True)),
+           "d2h_GBps": best(lambda: h_dst.copy_(d_buf, non_blocking=True)),
+           "both_ways_GBps_each": best(both)}
+    del d2
+    return out
+
+
 def cpu_baseline(args) -> dict:
     n_s = min(args.n, 2048)
     oracle_step(*oracle_inputs(256, SEED), args)  # warm numpy / BLAS
@@ -519,6 +558,7 @@ def main():
     e2e_run(e_steps)
     e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
     del pipe
+    link = host_link(hA, A, hCs[1])
     if world > 1:
         t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -580,6 +620,14 @@ def main():
     peaks = _json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     peak_src = "of measured (bf16_tflops_sustained)" if peaks else "of fallback"
+    lin = extras.get("autograd_linear")
+    if lin:
+        # forward and backward against the same tensor-core roofline: the
+        # leaf kernel's executed flops, and the effective 2MNK/t of each call
+        lin["roofline"] = {"bound": "tensor", "peak": peak, "unit": "TFLOP/s", "peak_source": peak_src,
+                           "multiply_kernel_frac": lin["multiply_kernel_leaf_tflops"] / peak,
+                           "forward_effective_frac": lin["forward_tflops"] / peak,
+                           "backward_effective_frac": lin["backward_tflops"] / peak}
     leaf_flops = 2.0 * info["leaves"] * (-(-n // info["pm"])) * (-(-n // info["pk"])) * (-(-n // info["pn"]))
     mma_flops = leaf_flops * (3 if args.leaf == "bf16x3" else 1)
     mult_ms, mult_n = kern_m["multiply"]
@@ -637,7 +685,11 @@ def main():
            "e2e": {"value": world * flops / (e_ms * 1e-3) / 1e12, "unit": UNIT,
                    "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
                    "ms_per_step": e_ms, "path": "fmm_host_submit / fmm_host_wait, two pipeline slots, "
-                                                 "pinned host buffers, wall clock over the submissions"},
+                                                 "pinned host buffers, wall clock over the submissions",
+                   # the host link measured in the same run: a step cannot
+                   # take less than its input bytes over the host->device rate
+                   "host_link": dict(link, bound_ms=2 * n * n * 4 / (link["h2d_GBps"] * 1e9) * 1e3,
+                                     frac=2 * n * n * 4 / (link["h2d_GBps"] * 1e9) * 1e3 / e_ms)},
            "gpu_launches": kern[""][1] // max(1, bd_steps) * args.steps,
            "clocks": ck, "plan": info}
     out.update(extras)

@@ -44,15 +44,22 @@ __device__ __forceinline__ void epi_chunk(const EpilogueArgs& c, const LeafDesc*
     const int64_t gj0 = bj * c.bn + nl0;
     float* crow = c.C + gi * c.ldc;
     if (c.vec_ok && nl0 + 32 <= c.bn && gj0 + 32 <= c.N) {
+      const int* eb = c.eB ? c.eB + gj0 : nullptr;
+      const bool eb_vec = ((uintptr_t)eb & 15) == 0;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         float4 v;
         float* vp = reinterpret_cast<float*>(&v);
+        int4 e4 = make_int4(0, 0, 0, 0);
+        if (eb) {
+          if (eb_vec) e4 = __ldg(reinterpret_cast<const int4*>(eb + 4 * q));
+          else e4 = make_int4(__ldg(eb + 4 * q), __ldg(eb + 4 * q + 1), __ldg(eb + 4 * q + 2), __ldg(eb + 4 * q + 3));
+        }
+        const int ev[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int j = 4 * q + u;
-          float x = s * __uint_as_float(r[j]);
-          if (c.eB) x *= exp2i(__ldg(c.eB + gj0 + j));
+          float x = s * __uint_as_float(r[4 * q + u]);
+          if (eb) x *= exp2i(ev[u]);
           vp[u] = x;
         }
         float4* dst = reinterpret_cast<float4*>(crow + gj0 + 4 * q);
