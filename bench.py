@@ -52,8 +52,9 @@ def parse():
     ap.add_argument("--schedule", default="auto", choices=["auto", "pass", "load_stage"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator / variant timings")
     ap.add_argument("--batch", type=int, default=512, help="products in the batched workload extra (0: skip)")
-    ap.add_argument("--experiment", default="", choices=["", "scaling_accuracy"],
-                    help="scaling_accuracy: relative error of Strassen, L = 1..6, under each scaling (Sec. 6.5)")
+    ap.add_argument("--experiment", default="", choices=["", "scaling_accuracy", "batch"],
+                    help="scaling_accuracy: relative error of Strassen, L = 1..6, under each scaling (Sec. 6.5); "
+                         "batch: the batched workload alone (--batch products)")
     ap.add_argument("--samples", type=int, default=100, help="samples per distribution (--experiment)")
     ap.add_argument("--exp-n", type=int, default=2000, help="matrix size (--experiment)")
     return ap.parse_args()
@@ -108,6 +109,16 @@ def batched_workload(api, inputs, torch, count: int) -> dict:
     torch.cuda.synchronize()
     api.sync_status()
     ms = e0.elapsed_time(e1) / reps
+    # per-kind breakdown from separate runs with events around every launch
+    api.kernel_timing(True)
+    for _ in range(3):
+        batch.run()
+    torch.cuda.synchronize()
+    api.kernel_timing(False)
+    breakdown = {}
+    for kind in ("scale", "combine", "multiply"):
+        k_ms, k_n = api.kernel_timing_read(kind)
+        breakdown[kind] = {"ms_per_run": k_ms / 3, "launches_per_run": k_n // 3}
     flops = float(sum(2 * M * K * N for M, K, N in dims.tolist()))
     # error of a sample of products against an FP64 product of the same inputs
     errs = []
@@ -123,7 +134,8 @@ def batched_workload(api, inputs, torch, count: int) -> dict:
             "plans": choice, "launch": "one CUDA graph replay: 6 scaling + 1 combination + 1 multiply + 1 output launch",
             "workspace_gb": ws_gb, "autotune_s": tune_s,
             "max_err_over_K_normA_normB_sampled": max(errs), "leaf": "bf16", "inputs": "bf16 U[-1,1]",
-            "scaling": "OI"}
+            "scaling": "OI", "operand_gb": sum(M * K + K * N for M, K, N in dims.tolist()) * 2 / 1e9,
+            "breakdown": dict(breakdown, note="separate runs without the graph, events around every launch")}
 
 
 # ---------------------------------------------------------------- fast-matmul linear layer
@@ -437,6 +449,13 @@ def main():
         return
     if args.experiment == "scaling_accuracy":
         scaling_accuracy(args)
+        return
+    if args.experiment == "batch":
+        import torch
+        from paper_1507_00687_gb300 import build
+        build.build()
+        from paper_1507_00687_gb300 import api, inputs
+        print(json.dumps({"experiment": "batch", **batched_workload(api, inputs, torch, max(1, args.batch))}))
         return
     import torch
     import torch.distributed as dist

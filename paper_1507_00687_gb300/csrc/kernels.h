@@ -43,7 +43,7 @@ struct ReduceArgs {
   int rows_per_cta;
   int64_t gx;
 };
-constexpr int kBatchColRows = 64;  // rows per CTA of a batched column reduction
+constexpr int kBatchColRows = 256;  // rows per CTA of a batched column reduction (one atomic per column each)
 constexpr int kBatchColSpan = 2048;  // columns per CTA of a column reduction
 
 // Batched reductions over `count` problems of one element type.  args and

@@ -78,6 +78,32 @@ __device__ __forceinline__ int fexp_fast(uint32_t bits, bool* nf) {
   }
 }
 
+// The biased exponent field of an encoding, minus one (so that a normal
+// number gives a value below kNormalSpan), and the frexp exponent of a
+// normal number from its field.  Shifted maxima over a group of encodings
+// test the whole group once (one branch instead of one per element) and
+// send it through fexp_fast only when some member is zero, subnormal or not
+// finite.
+template <int DT>
+__device__ __forceinline__ uint32_t field_m1(uint32_t bits) {
+  if constexpr (DT == kF32) return ((bits >> 23) & 0xFFu) - 1u;
+  else if constexpr (DT == kBF16) return ((bits >> 7) & 0xFFu) - 1u;
+  else return ((bits >> 10) & 0x1Fu) - 1u;
+}
+template <int DT>
+constexpr uint32_t kNormalSpan = DT == kF16 ? 30u : 254u;
+template <int DT>
+__device__ __forceinline__ int fexp_normal(uint32_t bits) {
+  return (int)field_m1<DT>(bits) + (DT == kF16 ? -13 : -125);
+}
+// The largest field_m1 of the four encodings of a raw4 result.
+template <int DT>
+__device__ __forceinline__ uint32_t worst4(uint4 v) {
+  uint32_t b[4];
+  unpack4<DT>(v, b);
+  return max(max(field_m1<DT>(b[0]), field_m1<DT>(b[1])), max(field_m1<DT>(b[2]), field_m1<DT>(b[3])));
+}
+
 // |x| as an integer: for finite values its order is the order of |x|, so
 // the exponent of a max-abs is the exponent of the max of these keys.
 template <int DT>
@@ -110,7 +136,7 @@ constexpr int kRowWarps = 8;
 constexpr int kRowBatch = 8;
 
 // Row i, one warp (lane = its lane index).
-template <int DT, bool SHIFT, int kRowBatch = kRowBatch>
+template <int DT, bool SHIFT, int kRowBatch = kRowBatch, bool kGroup = false>
 __device__ __forceinline__ void row_exp_one(const void* X, int64_t C, int64_t ld, const int* ce, int cs, int* out,
                                             int mode, bool vec_ok, int64_t i, int lane, bool* nf) {
   // the vector path also needs the column exponents 16-byte aligned
@@ -126,19 +152,49 @@ __device__ __forceinline__ void row_exp_one(const void* X, int64_t C, int64_t ld
   if (vec) {
     const int64_t C4 = C >> 2;
     int64_t j4 = lane;
-    for (; j4 + 32 * (kRowBatch - 1) < C4; j4 += 32 * kRowBatch) {
+    // kGroup: every batch is issued whole, the positions past the row's end
+    // clamped to its last group of four (re-reading an element of the row
+    // never changes a maximum), so a row ends without single-load rounds
+    for (; kGroup ? j4 < C4 : j4 + 32 * (kRowBatch - 1) < C4; j4 += 32 * kRowBatch) {
       uint4 v[kRowBatch];
       int4 c[kRowBatch];
+      int64_t jj[kRowBatch];
 #pragma unroll
-      for (int u = 0; u < kRowBatch; ++u) v[u] = raw4<DT>(X, rowoff + 4 * (j4 + 32 * u));
+      for (int u = 0; u < kRowBatch; ++u) jj[u] = kGroup ? min(j4 + 32 * u, C4 - 1) : j4 + 32 * u;
+#pragma unroll
+      for (int u = 0; u < kRowBatch; ++u) v[u] = raw4<DT>(X, rowoff + 4 * jj[u]);
 #pragma unroll
       for (int u = 0; u < kRowBatch; ++u)
-        c[u] = SHIFT ? __ldg(reinterpret_cast<const int4*>(ce + 4 * (j4 + 32 * u))) : make_int4(0, 0, 0, 0);
+        c[u] = SHIFT ? __ldg(reinterpret_cast<const int4*>(ce + 4 * jj[u])) : make_int4(0, 0, 0, 0);
+      if constexpr (SHIFT && kGroup) {
+        uint32_t worst = 0u;
 #pragma unroll
-      for (int u = 0; u < kRowBatch; ++u) {
-        uint32_t b[4];
-        unpack4<DT>(v[u], b);
-        take(b[0], c[u].x); take(b[1], c[u].y); take(b[2], c[u].z); take(b[3], c[u].w);
+        for (int u = 0; u < kRowBatch; ++u) worst = max(worst, worst4<DT>(v[u]));
+        if (worst < kNormalSpan<DT>) {
+#pragma unroll
+          for (int u = 0; u < kRowBatch; ++u) {
+            uint32_t b[4];
+            unpack4<DT>(v[u], b);
+            m = max(m, fexp_normal<DT>(b[0]) + cs * c[u].x);
+            m = max(m, fexp_normal<DT>(b[1]) + cs * c[u].y);
+            m = max(m, fexp_normal<DT>(b[2]) + cs * c[u].z);
+            m = max(m, fexp_normal<DT>(b[3]) + cs * c[u].w);
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < kRowBatch; ++u) {
+            uint32_t b[4];
+            unpack4<DT>(v[u], b);
+            take(b[0], c[u].x); take(b[1], c[u].y); take(b[2], c[u].z); take(b[3], c[u].w);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) {
+          uint32_t b[4];
+          unpack4<DT>(v[u], b);
+          take(b[0], c[u].x); take(b[1], c[u].y); take(b[2], c[u].z); take(b[3], c[u].w);
+        }
       }
     }
     for (; j4 < C4; j4 += 32) {
@@ -194,7 +250,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) row_exp_batched_kernel(const R
   if (g >= __ldg(start + count)) return;
   const int p = warp_find_problem(start, count, g);
   const ReduceArgs a = args[p];
-  row_exp_one<DT, SHIFT>(a.X, a.C, a.ld, a.shift, a.sign, a.out, mode, a.vec != 0, g - __ldg(start + p),
+  row_exp_one<DT, SHIFT, kRowBatch, true>(a.X, a.C, a.ld, a.shift, a.sign, a.out, mode, a.vec != 0, g - __ldg(start + p),
                          threadIdx.x & 31, &nf);
   if (nf) atomicOr(status, kStatusNonfinite);
 }
@@ -212,7 +268,10 @@ __global__ void __launch_bounds__(kRowWarps * 32) row_exp_batched_kernel(const R
 // false) the maximum is taken over |x| as integers and decoded once.
 constexpr int kColVec = 2;
 constexpr int kColSpan = 256 * 4 * kColVec;  // 2048 columns
-constexpr int kColRows = 2;
+// rows of loads in flight per thread: 4 for 16-bit types (8-byte loads), 2
+// for fp32
+template <int DT>
+constexpr int kColRows = DT == kF32 ? 2 : 4;
 constexpr int kColGroups = 4;
 constexpr int kColThreads = 256 * kColGroups;
 constexpr int kColSmem = kColGroups * kColSpan * 4;
@@ -243,17 +302,17 @@ __device__ __forceinline__ void col_exp_cta(const void* X, int64_t R, int64_t C,
   // column of (q, t): span0 + 1024 q + 4 lt + t
   const int64_t cbase = span0 + 4 * (int64_t)lt;
   int64_t i = r0;
-  for (; i + kColRows <= r1; i += kColRows) {
-    uint4 v[kColRows][kColVec];
-    int sh[kColRows];
+  for (; i + kColRows<DT> <= r1; i += kColRows<DT>) {
+    uint4 v[kColRows<DT>][kColVec];
+    int sh[kColRows<DT>];
 #pragma unroll
-    for (int u = 0; u < kColRows; ++u)
+    for (int u = 0; u < kColRows<DT>; ++u)
 #pragma unroll
       for (int q = 0; q < kColVec; ++q) v[u][q] = raw4_guarded<DT>(X, (i + u) * ld, cbase + 1024 * q, C, vec);
 #pragma unroll
-    for (int u = 0; u < kColRows; ++u) sh[u] = SHIFT ? rs * __ldg(re + i + u) : 0;
+    for (int u = 0; u < kColRows<DT>; ++u) sh[u] = SHIFT ? rs * __ldg(re + i + u) : 0;
 #pragma unroll
-    for (int u = 0; u < kColRows; ++u)
+    for (int u = 0; u < kColRows<DT>; ++u)
 #pragma unroll
       for (int q = 0; q < kColVec; ++q) {
         uint32_t b[4];
@@ -548,7 +607,7 @@ cudaError_t launch_col_exp(const void* X, int dt, int64_t R, int64_t C, int64_t 
   const int64_t gx = (C + kColSpan - 1) / kColSpan;
   // about one CTA per SM in all; each group's rows a multiple of the batch
   const int64_t target = (int64_t)sm_count();
-  const int64_t unit = (int64_t)kColRows * kColGroups;
+  const int64_t unit = (int64_t)kColRows<kBF16> * kColGroups;  // a multiple of every type's batch
   int64_t gy = std::max<int64_t>(1, std::min<int64_t>((target + gx - 1) / gx, (R + unit - 1) / unit));
   gy = std::min<int64_t>(gy, 65535);
   const int rows = (int)(((R + gy - 1) / gy + unit - 1) / unit * unit);
@@ -597,7 +656,7 @@ cudaError_t launch_row_exp_batched(const ReduceArgs* args, const int64_t* start,
 
 cudaError_t launch_col_exp_batched(const ReduceArgs* args, const int64_t* start, int count, int64_t total, int dt,
                                    bool shift, int* status, cudaStream_t st) {
-  static_assert(kBatchColRows % (kColRows * kColGroups) == 0, "row chunk must be whole batches");
+  static_assert(kBatchColRows % (kColRows<kBF16> * kColGroups) == 0, "row chunk must be whole batches");
   static_assert(kBatchColSpan == kColSpan, "column span");
   if (total == 0 || count == 0) return cudaSuccess;
   static bool attr_done[64][6] = {};
