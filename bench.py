@@ -357,6 +357,26 @@ def cpu_baseline(args) -> dict:
                       f"({t:.2f} s each)"}
 
 
+def max_over_ranks(values, device="cuda"):
+    """Each value's maximum over the ranks of the initialised process group
+    (the values themselves on one rank or without a group): step times are
+    taken as the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    vals = [float(v) for v in values]
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return vals
+    t = torch.tensor(vals, device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_tflops(flops_per_rank, world, ms_max):
+    """Whole-job throughput: the flops all ranks processed (each rank its own
+    product, weak scaling) over the slowest rank's time."""
+    return world * flops_per_rank / (ms_max * 1e-3) / 1e12
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -551,12 +571,9 @@ def main():
     bd_steps = min(args.steps, 50)
     kern = {}
     _, kms, _ = timed(bd_steps, kernels=kern)
-    if world > 1:
-        t = torch.tensor([ms, kms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, kms = float(t[0]), float(t[1])
+    ms, kms = max_over_ranks([ms, kms])
     flops = 2.0 * n**3
-    value = world * flops / (ms * 1e-3) / 1e12
+    value = whole_job_tflops(flops, world, ms)
 
     # ---------------- end to end through the public API with host buffers
     # The public host-memory entry points (fmm_host_*): each step copies A and
@@ -578,10 +595,7 @@ def main():
     e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
     del pipe
     link = host_link(hA, A, hCs[1])
-    if world > 1:
-        t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t[0])
+    e_ms = max_over_ranks([e_ms])[0]
     api.sync_status()
 
     # ---------------- accuracy (max-norm vs an FP64 product of the same inputs)
@@ -701,7 +715,7 @@ def main():
                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                         "kernel": kname, "algorithmic_flops_per_launch": mma_flops,
                         "ms_per_launch": mult_ms_per},
-           "e2e": {"value": world * flops / (e_ms * 1e-3) / 1e12, "unit": UNIT,
+           "e2e": {"value": whole_job_tflops(flops, world, e_ms), "unit": UNIT,
                    "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
                    "ms_per_step": e_ms, "path": "fmm_host_submit / fmm_host_wait, two pipeline slots, "
                                                  "pinned host buffers, wall clock over the submissions",
