@@ -250,8 +250,8 @@ __global__ void __launch_bounds__(kRowWarps * 32) row_exp_batched_kernel(const R
   if (g >= __ldg(start + count)) return;
   const int p = warp_find_problem(start, count, g);
   const ReduceArgs a = args[p];
-  row_exp_one<DT, SHIFT, kRowBatch, true>(a.X, a.C, a.ld, a.shift, a.sign, a.out, mode, a.vec != 0, g - __ldg(start + p),
-                         threadIdx.x & 31, &nf);
+  row_exp_one<DT, SHIFT, kRowBatch, true>(a.X, a.C, a.ld, a.shift, a.sign, a.out, mode, a.vec != 0,
+                                          g - __ldg(start + p), threadIdx.x & 31, &nf);
   if (nf) atomicOr(status, kStatusNonfinite);
 }
 
@@ -261,9 +261,10 @@ __global__ void __launch_bounds__(kRowWarps * 32) row_exp_batched_kernel(const R
 // a chunk of rows per CTA (out pre-filled with kZeroExp; nothing is written
 // for a column with no nonzero entry in the chunk).  A CTA covers a span of
 // kColSpan columns with kColGroups groups of 256 threads, each group
-// streaming whole rows of its share of the chunk (16 bytes x kColVec per
-// thread per row, so DRAM sees long contiguous runs) with kColRows rows'
-// loads in flight; the groups' maxima meet in shared memory, so one
+// streaming whole rows of its share of the chunk (4 elements x kColVec per
+// thread per row: 16-byte loads for fp32, 8-byte for 16-bit types, so DRAM
+// sees long contiguous runs) with kColRows rows' loads in flight; the
+// groups' maxima meet in shared memory, so one
 // atomicMax per column covers the CTA's rows.  Without row shifts (SHIFT
 // false) the maximum is taken over |x| as integers and decoded once.
 constexpr int kColVec = 2;
