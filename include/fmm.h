@@ -312,19 +312,26 @@ fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void*
  * memory.  Every GPU that loads the library holds that array until the
  * process exits.
  *
- * Arguments, layouts and results are those of fmm_multiply.  Returns
- * FMM_ERR_WORKSPACE, before touching the device, when the leaf table plus
- * the prepared operands (fp32 upper bound, as fmm_workspace_size counts
- * them for the forward product) would exceed FMM_NOALLOC_SCRATCH_BYTES;
- * fmm_last_error() then says how many bytes the problem needs.
+ * Arguments, layouts and results are those of fmm_multiply (scaling
+ * between recursive steps is not applied).  Returns FMM_ERR_WORKSPACE,
+ * before touching the device, when the leaf table plus the workspace of
+ * the path the call would take exceeds FMM_NOALLOC_SCRATCH_BYTES: the pass
+ * schedule's combined operands and stored products for E4M3 leaves and
+ * the forced pass schedules, the prepared operand copies (fp32 upper
+ * bound) under FMM_SCHEDULE_LOAD_STAGE, the smaller of the two under
+ * FMM_SCHEDULE_AUTO; fmm_last_error() then says how many bytes the problem
+ * needs.  About n <= 2000 for a square fp32 product at one level.
  *
  * The first call on a device looks up the array's device address (once
  * per device); make that first call before any stream capture begins.
- * Nothing in the array needs to start at zero: each call copies the leaf
- * table in and rewrites every prepared element (padding included) before
- * the multiply kernel reads it.  All calls share the one array, so calls
- * whose work overlaps on the GPU (different streams, or threads without
- * ordering) race on it and give wrong results; order them on one stream.
+ * Each call copies the plan's tables into the array with small kernel
+ * launches that carry the data in their arguments (no copy from host
+ * memory, nothing for the host to wait on).  Nothing in the array needs to
+ * start at zero: each call writes the tables and every element of the
+ * operands it forms (padding included) before a kernel reads them.  All
+ * calls share the one array, so calls whose work overlaps on the GPU
+ * (different streams, or threads without ordering) race on it and give
+ * wrong results; order them on one stream.
  */
 fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, const void* B,
                                 int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t K,

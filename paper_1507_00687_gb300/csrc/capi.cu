@@ -651,6 +651,36 @@ static size_t ws_bytes_for(const Plan* p, int64_t M, int64_t K, int64_t N) {
 // array; its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FMM_NOALLOC_SCRATCH_BYTES];
 
+// The plan's tables reach the scratch inside kernel parameters, up to
+// kTableChunkWords 32-bit words per launch: a launch copies its arguments
+// when it is issued, so the host never waits for a copy out of its own
+// (pageable) memory and no staging buffer is needed.
+constexpr int kTableChunkWords = 8000;  // 32000 bytes, under the 32764-byte parameter limit
+struct TableChunk {
+  uint32_t w[kTableChunkWords];
+};
+
+__global__ void __launch_bounds__(256) table_chunk_kernel(const __grid_constant__ TableChunk c, uint32_t* dst,
+                                                          int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = c.w[i];
+}
+
+// Copy `words` 32-bit words from host memory to dst (device) on st, one
+// launch per kTableChunkWords words.
+static bool upload_words(uint32_t* dst, const void* src, size_t words, cudaStream_t st) {
+  static TableChunk chunk;  // staging for the launch arguments (copied by each launch)
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  const char* s = static_cast<const char*>(src);
+  for (size_t off = 0; off < words; off += kTableChunkWords) {
+    const int n = (int)std::min<size_t>(kTableChunkWords, words - off);
+    std::memcpy(chunk.w, s + off * 4, (size_t)n * 4);
+    table_chunk_kernel<<<(n + 255) / 256, 256, 0, st>>>(chunk, dst + off, n);
+    if (!cuda_ok(cudaGetLastError(), "table copy into the no-alloc scratch")) return false;
+  }
+  return true;
+}
+
 // Device address of g_noalloc_scratch on the current device, looked up once
 // per device (the first fmm_multiply_noalloc call there).
 static char* noalloc_scratch() {
@@ -1292,11 +1322,24 @@ fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, con
   if (ceil_div(M, p->pm) >= (1ll << 30) || ceil_div(N, p->pn) >= (1ll << 30) || ceil_div(K, p->pk) >= (1ll << 30))
     return FMM_ERR_SHAPE;
   if (M == 0 || N == 0) return FMM_OK;
-  // The size check comes before any device call.
+  if (K == 0) return run_plan(p, Source{}, Source{}, C, ldc, M, K, N, nullptr, nullptr, nullptr, 0, as_stream(stream));
+  // The size check comes before any device call.  The workspace part is
+  // the one of the path run_plan takes with this much room: the pass
+  // schedule's combined operands and stored products (E4M3 leaves and the
+  // forced pass schedules always take it), or the load-stage schedule's
+  // prepared operand copies (the automatic schedule takes whichever fits,
+  // the pass schedule first).
   const size_t leaf_bytes = p->host.size() * sizeof(LeafDesc);
   const size_t table_bytes = leaf_bytes + p->lists.size() * 4;
   const size_t table = (size_t)round_up((int64_t)table_bytes, 256);
-  const size_t need = table + (size_t)prepared_bytes(M, K, p->pm, p->pk) + (size_t)prepared_bytes(N, K, p->pn, p->pk);
+  const int64_t pass_need = pass_bytes(p, M, K, N, p->pm, p->pk, p->pn);
+  const int64_t stage_need = prepared_bytes(M, K, p->pm, p->pk) + prepared_bytes(N, K, p->pn, p->pk);
+  const bool pass_only = p->leaf_format == FMM_LEAF_E4M3B128 || p->schedule == FMM_SCHEDULE_PASS ||
+                         p->schedule == FMM_SCHEDULE_PASS_EPILOGUE || p->schedule == FMM_SCHEDULE_PASS_PRODUCTS;
+  const int64_t ws_need = pass_only ? pass_need
+                          : p->schedule == FMM_SCHEDULE_LOAD_STAGE ? stage_need
+                                                                   : std::min(pass_need, stage_need);
+  const size_t need = table + (size_t)ws_need;
   if (need > FMM_NOALLOC_SCRATCH_BYTES) {
     t_last_error = "fmm_multiply_noalloc: this problem needs " + std::to_string(need) +
                    " bytes of scratch; the static scratch holds " + std::to_string(FMM_NOALLOC_SCRATCH_BYTES);
@@ -1305,11 +1348,8 @@ fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, con
   char* scratch = noalloc_scratch();
   if (!scratch) return FMM_ERR_CUDA;
   cudaStream_t st = as_stream(stream);
-  if (!cuda_ok(cudaMemcpyAsync(scratch, p->host.data(), leaf_bytes, cudaMemcpyHostToDevice, st),
-               "leaf table copy into the no-alloc scratch") ||
-      !cuda_ok(cudaMemcpyAsync(scratch + leaf_bytes, p->lists.data(), p->lists.size() * 4, cudaMemcpyHostToDevice,
-                               st),
-               "term list copy into the no-alloc scratch"))
+  if (!upload_words(reinterpret_cast<uint32_t*>(scratch), p->host.data(), leaf_bytes / 4, st) ||
+      !upload_words(reinterpret_cast<uint32_t*>(scratch + leaf_bytes), p->lists.data(), p->lists.size(), st))
     return FMM_ERR_CUDA;
   // Operands as in fmm_multiply.
   const Source a{A, lda, in_dtype, true, M, K, p->pm, p->pk, eA, -1, d, +1};

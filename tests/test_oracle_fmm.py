@@ -241,3 +241,26 @@ def test_growth_entries_equal_full_growth(names):
     # when every coefficient is nonnegative and each entry lies in one term
     Ac, Bc = np.abs(A), np.abs(B)
     assert np.allclose(F.growth_entries(Ac, Bc, [R.classical(1, 2, 1)], rows, cols), (Ac @ Bc)[rows, cols])
+
+
+def test_error_norms_on_a_hand_computed_case():
+    # Sec. 6.5 measures the componentwise relative error max |c_hat - c| / |c|
+    # over the entries with c != 0.  Worked by hand on a 2 x 2 case:
+    #   c = 2,  c_hat = 2.2  -> 0.2 / 2 = 0.1
+    #   c = 0,  c_hat = 7    -> skipped (the ratio is undefined there)
+    #   c = -4, c_hat = -3   -> 1 / 4  = 0.25   (dividing by |c_hat| would give 1/3)
+    #   c = 1,  c_hat = 1    -> 0
+    # so the componentwise error is 0.25 and the max-norm error is 7.  A
+    # version that divides by |c_hat| gives 1.0 (the skipped entry's 7/7),
+    # one that keeps zero entries gives inf, one that drops the absolute
+    # value of the denominator gives -0.25 or 0.1.
+    C = np.array([[2.0, 0.0], [-4.0, 1.0]])
+    C_hat = np.array([[2.2, 7.0], [-3.0, 1.0]])
+    assert F.err_componentwise(C_hat, C) == pytest.approx(0.25, rel=1e-15)
+    assert F.err_max(C_hat, C) == 7.0
+    # all-zero reference: no entry defines a ratio
+    assert F.err_componentwise(np.ones((2, 2)), np.zeros((2, 2))) == 0.0
+    # invariant: scaling both by the same nonzero factor leaves the
+    # componentwise error unchanged and scales the max-norm error
+    assert F.err_componentwise(-8.0 * C_hat, -8.0 * C) == pytest.approx(0.25, rel=1e-15)
+    assert F.err_max(-8.0 * C_hat, -8.0 * C) == 56.0
