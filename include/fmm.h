@@ -26,6 +26,11 @@
  *    B' = 2^-d B 2^-eB are exact; fmm_multiply writes them into the
  *    caller's workspace in one bandwidth-bound pass and multiplies its
  *    output by 2^(eA+eB) in the epilogue of the fused kernel.
+ *  - Every wait inside a kernel is bounded: FMM_WAIT_TIMEOUT_NS in the
+ *    environment (read once per process; default 2 s) limits each one;
+ *    past it the kernel stops cleanly and flags FMM_ERR_DEVICE_TIMEOUT.
+ *    FMM_TEST_STALL=1 makes the tensor-core multiply wait once on a barrier
+ *    that nothing arrives at, so that tests can exercise that path.
  *  - Device code needs sm_103a and the CUDA driver's tensor-map encoder.
  *  - Thread safety: plans are immutable after creation and may be used from
  *    several host threads; calls on one stream execute in order.
@@ -132,6 +137,92 @@ fmm_status fmm_plan_tree(fmm_plan_t* out, int nrules, const fmm_rule* rules, int
                          const int32_t* node_rule, int leaf_format);
 
 fmm_status fmm_plan_destroy(fmm_plan_t plan);
+
+/*
+ * Rule algebra.  Each call derives a new base-case rule from given ones,
+ * checks the inputs and the result against the Brent equations
+ * (FMM_ERR_NOT_MATMUL on failure) and writes the result's tables into the
+ * caller's arrays U, V, W (row-major tables, sizes below), with out->U/V/W
+ * pointing at them and all three entry orders FMM_ORDER_ROW.  Host only;
+ * nothing is kept by the library.
+ *
+ * fmm_rule_rotate: the cyclic rotation of a <m0,k0,n0;r> rule into a
+ *   <n0,m0,k0;r> rule (App. A-B: the matrix-multiplication tensor
+ *   sum a_ik b_kj c_ij is invariant when its factors are cycled; the new A
+ *   is C transposed, the new B is A, the new C is B transposed).  U holds
+ *   n0*m0*r, V m0*k0*r, W n0*k0*r doubles.
+ * fmm_rule_compose: two recursion steps as one rule (Eq. 4.4 with L = 2):
+ *   the <m1 m2, k1 k2, n1 n2; r1 r2> rule whose product r1*r2_count + r2
+ *   has coefficients X1[(p1,q1), r1] X2[(p2,q2), r2] at the composite entry
+ *   (p1 m2 + p2, q1 k2 + q2).  FMM_ERR_UNSUPPORTED above 64 per dimension
+ *   or 4096 products.  U holds m1 m2 k1 k2 r1 r2 doubles, and so on.
+ * fmm_rule_transform: [[XU U, XV V, XW W]] (Sec. 3.4), XU (m0 k0 square),
+ *   XV (k0 n0), XW (m0 n0) row-major, applied in the input rule's own
+ *   entry orders; the arrays are the size of the input's.
+ * fmm_rule_permute: the rule applied to A, B blocks whose indices are
+ *   relabelled by the permutations perm_i (m0 entries), perm_k (k0),
+ *   perm_j (n0) -- U'[(i,k)] = U[(perm_i[i], perm_k[k])],
+ *   V'[(k,j)] = V[(perm_k[k], perm_j[j])], W'[(i,j)] = W[(perm_i[i],
+ *   perm_j[j])] -- which computes the same product (the D'Alberto variant
+ *   of Sec. 3.4 exchanges the j blocks); FMM_ERR_ARG when a perm_* is not a
+ *   permutation.  Arrays the size of the input's.
+ */
+fmm_status fmm_rule_rotate(const fmm_rule* in, double* U, double* V, double* W, fmm_rule* out);
+fmm_status fmm_rule_compose(const fmm_rule* outer, const fmm_rule* inner, double* U, double* V, double* W,
+                            fmm_rule* out);
+fmm_status fmm_rule_transform(const fmm_rule* in, const double* XU, const double* XV, const double* XW,
+                              double* U, double* V, double* W, fmm_rule* out);
+fmm_status fmm_rule_permute(const fmm_rule* in, const int32_t* perm_i, const int32_t* perm_k,
+                            const int32_t* perm_j, double* U, double* V, double* W, fmm_rule* out);
+
+/*
+ * The eight Castrapel-Gustafson variants of a <2,2,2> rule (Sec. 3.4):
+ *   [[(P^x (x) P^y) U, (P^z (x) P^x) V, (P^y (x) P^z) W]],  x, y, z in {1, 2},
+ * P the 2 x 2 exchange, read in the paper's entry order (A, B column-major,
+ * C row-major), where the factors exchange the k blocks (P^x), the i
+ * blocks (P^y) and the j blocks (P^z); P^2 = I.  Variant v = 0..7 takes
+ * x = 1 when bit 1 of v is set, y = 1 when bit 0 is set, z = 1 when bit 2
+ * is set (else 2), so v = 0 is the rule itself.
+ *
+ * fmm_plan_variants builds the non-uniform plan of `levels` levels whose
+ * every node runs one variant of `base`, chosen per node (the paper lists
+ * random, round-robin and matrix-dependent selection without fixing them;
+ * these are the library's definitions):
+ *   FMM_SELECT_RANDOM: node n (level order, the node order of
+ *     fmm_plan_tree) takes the top three bits of SplitMix64 output n of
+ *     stream `seed` (z = seed + (n+1) 0x9E3779B97F4A7C15, then the
+ *     generator's two xor-shift-multiply rounds and final xor-shift);
+ *   FMM_SELECT_ROUND_ROBIN: node n takes variant n mod 8;
+ *   FMM_SELECT_MATRIX: from the block max-abs values of A and B on the
+ *     plan's finest grid (block_max_a, block_max_b: 2^levels x 2^levels,
+ *     row-major, as fmm_block_max writes them), level by level: each node
+ *     takes the variant minimising max_k sum_r |W_kr| (sum_i |U_ir| a_i)
+ *     (sum_j |V_jr| b_j), the one-level growth factor of the proof of
+ *     Theorem 4.1 on its own operands, with a_i, b_j bounds on the max-abs
+ *     of its operands' quadrants (ties: the lowest v); the bounds of the
+ *     operands S_r, T_r of its children follow by the triangle inequality
+ *     from the chosen U and V (sums in ascending index order, in double).
+ * block_max_* are host arrays, read only for FMM_SELECT_MATRIX (else
+ * may be NULL).  chosen (nullable, host, 1 + R + ... + R^(levels-1)
+ * entries) receives each node's variant.  FMM_ERR_UNSUPPORTED unless base
+ * is <2,2,2>; otherwise as fmm_plan_tree.
+ */
+enum { FMM_SELECT_RANDOM = 0, FMM_SELECT_ROUND_ROBIN = 1, FMM_SELECT_MATRIX = 2 };
+fmm_status fmm_plan_variants(fmm_plan_t* out, const fmm_rule* base, int levels, int selection, uint64_t seed,
+                             const float* block_max_a, const float* block_max_b, int32_t* chosen,
+                             int leaf_format);
+
+/*
+ * Block max-abs of a row-major matrix X (rows x cols, ld, element type
+ * dtype, device memory) cut into nrb x ncb blocks of ceil(rows/nrb) x
+ * ceil(cols/ncb) elements, as a plan partitions its operands (Sec. 3.2;
+ * missing elements of ragged edge blocks count as zero): out[p*ncb + q] =
+ * max |X| over block (p, q), float32, device memory.  Inf/NaN entries are
+ * skipped and flagged in the status word (FMM_ERR_NONFINITE from
+ * fmm_sync_status).  nrb, ncb in 1..64.  Asynchronous on the stream.
+ */
+fmm_status fmm_block_max(const void* X, int dtype, int64_t rows, int64_t cols, int64_t ld, int nrb, int ncb,
+                         float* out, void* stream);
 
 /*
  * Principal quantities of the plan (Sec. 4.1, Theorem 4.2): sum over levels

@@ -18,6 +18,8 @@ fmm        classical product, recursive stationary / uniform non-stationary
            componentwise quantity bounding the error in the proof of Thm 4.1.
 scaling    outside (Alg. 1), inside (Alg. 2), repeated outside-inside
            (Alg. 3) scaling, real-valued and rounded to powers of two.
+variants   the Castrapel-Gustafson variants of a <2,2,2> rule (Sec. 3.4) and
+           random / round-robin / matrix-dependent selection per tree node.
 precision  round-to-nearest-even emulation of bf16 / fp16 / e4m3 and the
            bf16 hi+lo split, written from the IEEE-754 definitions.
 """

@@ -31,7 +31,10 @@ EXPORTS = [
     "fmm_batch_workspace_size", "fmm_batch_create", "fmm_batch_run", "fmm_batch_destroy",
     "fmm_plan_set_between_scaling", "fmm_plan_tree", "fmm_scale_adaptive",
     "fmm_host_create", "fmm_host_submit", "fmm_host_wait", "fmm_host_destroy",
+    "fmm_rule_rotate", "fmm_rule_compose", "fmm_rule_transform", "fmm_rule_permute", "fmm_plan_variants",
+    "fmm_block_max",
 ]
+SELECT_RANDOM, SELECT_ROUND_ROBIN, SELECT_MATRIX = 0, 1, 2
 
 # Bytes of the library's static scratch array (FMM_NOALLOC_SCRATCH_BYTES).
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -76,6 +79,14 @@ def lib():
     L.fmm_host_destroy.argtypes = [vp]
     L.fmm_plan_tree.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(FmmRule), C.c_int, i64,
                                 C.POINTER(C.c_int32), C.c_int]
+    rp, dp = C.POINTER(FmmRule), C.POINTER(C.c_double)
+    L.fmm_rule_rotate.argtypes = [rp, dp, dp, dp, rp]
+    L.fmm_rule_compose.argtypes = [rp, rp, dp, dp, dp, rp]
+    L.fmm_rule_transform.argtypes = [rp, dp, dp, dp, dp, dp, dp, rp]
+    L.fmm_rule_permute.argtypes = [rp, i32p, i32p, i32p, dp, dp, dp, rp]
+    L.fmm_plan_variants.argtypes = [C.POINTER(vp), rp, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_float),
+                                    C.POINTER(C.c_float), i32p, C.c_int]
+    L.fmm_block_max.argtypes = [vp, C.c_int, i64, i64, i64, C.c_int, C.c_int, vp, vp]
     L.fmm_plan_set_schedule.argtypes = [vp, C.c_int]
     L.fmm_plan_set_between_scaling.argtypes = [vp, C.c_int]
     L.fmm_kernel_timing.argtypes = [C.c_int]

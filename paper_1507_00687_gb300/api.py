@@ -109,6 +109,49 @@ class Plan:
             level = nxt
         return cls(table, leaf=leaf, schedule=schedule, between=between, node_rule=node_rule, levels=levels)
 
+    @classmethod
+    def variants(cls, base: Union[str, BaseRule], levels: int, selection: str = "round_robin", seed: int = 0,
+                 A: Optional[torch.Tensor] = None, B: Optional[torch.Tensor] = None, leaf: str = "bf16x3",
+                 schedule: str = "auto", stream=None) -> "Plan":
+        """A non-uniform plan whose every node runs one of the eight
+        Castrapel-Gustafson variants of a <2,2,2> rule (Sec. 3.4;
+        fmm_plan_variants), chosen per node by ``selection``: "random"
+        (SplitMix64 stream ``seed``), "round_robin", or "matrix" (from the
+        block max-abs of the device operands A and B, found by
+        fmm_block_max).  The chosen variant of each node (level order) is
+        in ``plan.chosen``."""
+        rule = get_rule(base) if isinstance(base, str) else base
+        sel = {"random": N.SELECT_RANDOM, "round_robin": N.SELECT_ROUND_ROBIN, "matrix": N.SELECT_MATRIX}[selection]
+        g = 1 << levels
+        fa = fb = None
+        if sel == N.SELECT_MATRIX:
+            if A is None or B is None:
+                raise ValueError("matrix-dependent selection needs the operands A and B")
+            fa, fb = block_max(A, g, g, stream), block_max(B, g, g, stream)
+            torch.cuda.synchronize(A.device)
+            fa = fa.cpu().contiguous()
+            fb = fb.cpu().contiguous()
+        nodes = sum(rule.r**lvl for lvl in range(levels))
+        chosen = (C.c_int32 * nodes)()
+        self = cls.__new__(cls)
+        self.rules = [rule]
+        self.leaf = leaf
+        self._keep = []
+        arr = self._rule_array([rule])
+        h = C.c_void_p()
+        fp = C.POINTER(C.c_float)
+        N.check(N.lib().fmm_plan_variants(C.byref(h), arr, levels, sel, C.c_uint64(seed & ((1 << 64) - 1)),
+                                          None if fa is None else C.cast(fa.data_ptr(), fp),
+                                          None if fb is None else C.cast(fb.data_ptr(), fp), chosen, LEAF[leaf]),
+                "fmm_plan_variants")
+        self._h = h
+        self.node_rule = list(chosen)
+        self.chosen = list(chosen)
+        self.schedule = schedule
+        N.check(N.lib().fmm_plan_set_schedule(h, SCHEDULE[schedule]), "fmm_plan_set_schedule")
+        self.between = False
+        return self
+
     @property
     def handle(self):
         return self._h
@@ -134,6 +177,17 @@ class Plan:
             except Exception:
                 pass
             self._h = None
+
+
+def block_max(X: torch.Tensor, nrb: int, ncb: int, stream=None) -> torch.Tensor:
+    """Max-abs of each block of the nrb x ncb grid of ceil(rows/nrb) x
+    ceil(cols/ncb) blocks of X (fmm_block_max): a float32 device tensor."""
+    rows, cols = X.shape
+    ld = _rowmajor(X, "X")
+    out = torch.empty((nrb, ncb), dtype=torch.float32, device=X.device)
+    N.check(N.lib().fmm_block_max(_ptr(X), DTYPE[X.dtype], rows, cols, ld, nrb, ncb, _ptr(out), _stream(stream)),
+            "fmm_block_max")
+    return out
 
 
 def scale(A: torch.Tensor, B: torch.Tensor, steps: str, stream=None):

@@ -16,6 +16,7 @@
 #include "device.cuh"
 #include "kernels.h"
 #include "plan.h"
+#include "rules.h"
 
 namespace fmm {
 
@@ -44,6 +45,17 @@ static int* status_ptr() {
     cache[dev] = static_cast<int*>(p);
   }
   return cache[dev];
+}
+
+// FMM_TEST_STALL (environment, read once): the multiply kernel's epilogue
+// waits on a barrier that nothing arrives at, so its bounded wait runs out
+// and the timeout path (status word, clean stop) can be tested.
+static int stall_test() {
+  static int v = [] {
+    const char* s = std::getenv("FMM_TEST_STALL");
+    return s && std::atoi(s) != 0 ? 1 : 0;
+  }();
+  return v;
 }
 
 static uint64_t timeout_ns() {
@@ -380,6 +392,7 @@ static bool direct_args(const Plan* p, const PassGeom& g, const Source& x, const
   d->mbuf = mbuf;
   d->status = status;
   d->timeout_ns = timeout_ns();
+  d->stall_test = stall_test();
   return true;
 }
 
@@ -1064,6 +1077,62 @@ fmm_status fmm_plan_tree(fmm_plan_t* out, int nrules, const fmm_rule* rules, int
   if (s != FMM_OK) return s;
   *out = reinterpret_cast<fmm_plan_t>(p);
   return FMM_OK;
+}
+
+fmm_status fmm_rule_rotate(const fmm_rule* in, double* U, double* V, double* W, fmm_rule* out) {
+  if (!in || !U || !V || !W || !out) return FMM_ERR_ARG;
+  return rule_rotate(*in, U, V, W, out);
+}
+
+fmm_status fmm_rule_compose(const fmm_rule* outer, const fmm_rule* inner, double* U, double* V, double* W,
+                            fmm_rule* out) {
+  if (!outer || !inner || !U || !V || !W || !out) return FMM_ERR_ARG;
+  return rule_compose(*outer, *inner, U, V, W, out);
+}
+
+fmm_status fmm_rule_transform(const fmm_rule* in, const double* XU, const double* XV, const double* XW, double* U,
+                              double* V, double* W, fmm_rule* out) {
+  if (!in || !U || !V || !W || !out) return FMM_ERR_ARG;
+  return rule_transform(*in, XU, XV, XW, U, V, W, out);
+}
+
+fmm_status fmm_rule_permute(const fmm_rule* in, const int32_t* perm_i, const int32_t* perm_k, const int32_t* perm_j,
+                            double* U, double* V, double* W, fmm_rule* out) {
+  if (!in || !U || !V || !W || !out) return FMM_ERR_ARG;
+  return rule_permute(*in, perm_i, perm_k, perm_j, U, V, W, out);
+}
+
+fmm_status fmm_plan_variants(fmm_plan_t* out, const fmm_rule* base, int levels, int selection, uint64_t seed,
+                             const float* block_max_a, const float* block_max_b, int32_t* chosen,
+                             int leaf_format) {
+  if (!out || !base || levels < 1 || levels > 8) return FMM_ERR_ARG;
+  *out = nullptr;
+  CanonRule c;
+  fmm_status s = canonicalize(*base, &c);
+  if (s != FMM_OK) return s;
+  if (brent_violations(c)) return FMM_ERR_NOT_MATMUL;
+  std::vector<int> nr;
+  if ((s = cg_select(c, levels, selection, seed, block_max_a, block_max_b, &nr)) != FMM_OK) return s;
+  std::vector<CanonRule> table(8);
+  for (int v = 0; v < 8; ++v) table[(size_t)v] = cg_variant(c, v);
+  Plan* p = nullptr;
+  if ((s = make_plan(table, leaf_format, &p, &nr, levels)) != FMM_OK) return s;
+  if (chosen)
+    for (size_t i = 0; i < nr.size(); ++i) chosen[i] = nr[i];
+  *out = reinterpret_cast<fmm_plan_t>(p);
+  return FMM_OK;
+}
+
+fmm_status fmm_block_max(const void* X, int dtype, int64_t rows, int64_t cols, int64_t ld, int nrb, int ncb,
+                         float* out, void* stream) {
+  if (!valid_dtype(dtype) || rows < 0 || cols < 0 || nrb < 1 || ncb < 1 || nrb > 64 || ncb > 64 || !out)
+    return FMM_ERR_ARG;
+  if (rows > 0 && cols > 0 && (!X || ld < cols)) return FMM_ERR_ARG;
+  int* status = status_ptr();
+  if (!status) return FMM_ERR_CUDA;
+  return cuda_ok(launch_block_max(X, dtype, rows, cols, ld, nrb, ncb, out, status, as_stream(stream)), "block max")
+             ? FMM_OK
+             : FMM_ERR_CUDA;
 }
 
 fmm_status fmm_plan_destroy(fmm_plan_t plan) {

@@ -127,7 +127,8 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) direct_fmm_kernel(const __g
   uint64_t* tfull = empty + C::kStages;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* never = drain + 1;  // no thread ever arrives here (timeout-path test)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) direct_fmm_kernel(const __g
       mbar_init(&tempty[b], kEpiWarps * 32);
     }
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     mbar_fence_init();
   }
@@ -295,6 +297,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) direct_fmm_kernel(const __g
     // -------------------------------------------------------- epilogue
     uint32_t acc_iter = 0;
     bool ok = true;
+    if (args.stall_test) ok = __all_sync(0xffffffffu, mbar_wait_bounded(never, 0, abort_flag, args.timeout_ns));
     const int quarter = warp & 3, half = EPI == 8 ? warp >> 2 : 0;
     constexpr int kChunks = BN / 32 / (EPI / 4);  // 32-column chunks per warp
     const int row = quarter * 32 + lane;  // TMEM lane = tile row

@@ -55,6 +55,11 @@ cudaError_t launch_row_exp_batched(const ReduceArgs* args, const int64_t* start,
 cudaError_t launch_col_exp_batched(const ReduceArgs* args, const int64_t* start, int count, int64_t total, int dt,
                                    bool shift, int* status, cudaStream_t st);
 cudaError_t launch_fill(int* p, int64_t n, int v, cudaStream_t st);
+// out[p * ncb + q] = max |X| over block (p, q) of the nrb x ncb grid of
+// ceil(R / nrb) x ceil(C / ncb) blocks (ncb <= 64); Inf/NaN skipped and
+// flagged in *status.
+cudaError_t launch_block_max(const void* X, int dt, int64_t R, int64_t C, int64_t ld, int nrb, int ncb, float* out,
+                             int* status, cudaStream_t st);
 
 
 // One operand of the fused multiply as the kernel sees it: a tile has
@@ -205,6 +210,9 @@ struct DirectArgs {
   float* mbuf;         // null: fused epilogue into C; else store M_r, [leaf][tp_a][tp_b] fp32
   int* status;
   uint64_t timeout_ns;
+  // Test of the timeout path (FMM_TEST_STALL set in the environment): the
+  // epilogue first waits, bounded, on a barrier that nothing arrives at.
+  int stall_test;
 };
 
 // Output combination pass (third line of Eq. 4.4) over stored leaf products:

@@ -791,6 +791,59 @@ cudaError_t launch_scale_stop(int* ctl, int tested, int t, int* steps_out, cudaS
   return cudaGetLastError();
 }
 
+// Block max-abs for the matrix-dependent variant selection: CTA (p, c)
+// takes up to kBlockMaxRows rows of block row p; for each column block q its
+// threads stride the block's columns (coalesced), a warp reduction and one
+// shared-memory atomic per warp combine them, and one global atomic per
+// (CTA, q) writes the result.  Non-negative floats order like their bits.
+constexpr int kBlockMaxRows = 32;
+
+__global__ void __launch_bounds__(256) block_max_kernel(const void* X, int dt, int64_t R, int64_t C, int64_t ld,
+                                                        int64_t br, int64_t bc, int ncb, float* out, int* status) {
+  __shared__ unsigned smax[64];
+  if (threadIdx.x < 64) smax[threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t p = blockIdx.x;
+  const int64_t r0 = p * br + (int64_t)blockIdx.y * kBlockMaxRows;
+  const int64_t r1 = min(min(r0 + kBlockMaxRows, (p + 1) * br), R);
+  bool nonfinite = false;
+  const int lane = threadIdx.x & 31;
+  for (int q = 0; q < ncb; ++q) {
+    const int64_t c0 = (int64_t)q * bc, c1 = min(c0 + bc, C);
+    unsigned m = 0u;
+    for (int64_t r = r0; r < r1; ++r)
+      for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        float x;
+        if (dt == kF32) x = static_cast<const float*>(X)[r * ld + c];
+        else {
+          const uint16_t h = static_cast<const uint16_t*>(X)[r * ld + c];
+          x = dt == kBF16 ? __uint_as_float((uint32_t)h << 16) : __half2float(__ushort_as_half(h));
+        }
+        const unsigned b = __float_as_uint(x) & 0x7FFFFFFFu;
+        if (b >= 0x7F800000u) nonfinite = true;
+        else m = max(m, b);
+      }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m) atomicMax(&smax[q], m);
+  }
+  if (nonfinite) atomicOr(status, kStatusNonfinite);
+  __syncthreads();
+  if (threadIdx.x < ncb && smax[threadIdx.x])
+    atomicMax(reinterpret_cast<unsigned*>(out) + p * ncb + threadIdx.x, smax[threadIdx.x]);
+}
+
+cudaError_t launch_block_max(const void* X, int dt, int64_t R, int64_t C, int64_t ld, int nrb, int ncb, float* out,
+                             int* status, cudaStream_t st) {
+  cudaError_t e = launch_fill(reinterpret_cast<int*>(out), (int64_t)nrb * ncb, 0, st);
+  if (e != cudaSuccess || R == 0 || C == 0) return e;
+  const int64_t br = (R + nrb - 1) / nrb, bc = (C + ncb - 1) / ncb;
+  const int64_t chunks = (br + kBlockMaxRows - 1) / kBlockMaxRows;
+  if (chunks > 65535) return cudaErrorInvalidValue;
+  KernelTimer timer("scale", st);
+  block_max_kernel<<<dim3((unsigned)nrb, (unsigned)chunks), 256, 0, st>>>(X, dt, R, C, ld, br, bc, ncb, out, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill(int* p, int64_t n, int v, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   KernelTimer timer("scale", st);

@@ -100,66 +100,97 @@ def fast323() -> BaseRule:
     return BaseRule("fast323", 3, 2, 3, U, V, W, COL, COL, ROW)
 
 
-def _index(p: int, q: int, rows: int, cols: int, order: int) -> int:
-    return p * cols + q if order == ROW else q * rows + p
+# ---------------------------------------------------------------- rule algebra
+# Rotation, composition, transformation and permutation are computed and
+# Brent-checked by the library (fmm_rule_*); these functions marshal the
+# tables in and out.  Results are row-major in A, B and C.
+
+def _c_rule(rule: BaseRule, keep: list):
+    from . import _native as N
+    import ctypes as C
+    arrs = [np.ascontiguousarray(X, np.float64) for X in (rule.U, rule.V, rule.W)]
+    keep.extend(arrs)
+    dp = C.POINTER(C.c_double)
+    return N.FmmRule(rule.m0, rule.k0, rule.n0, rule.r, *(a.ctypes.data_as(dp) for a in arrs),
+                     rule.order_a, rule.order_b, rule.order_c)
 
 
-def _to_row_major(X: np.ndarray, rows: int, cols: int, order: int) -> np.ndarray:
-    """Rows of X re-indexed so that entry (p, q) of the operand is row p*cols+q."""
-    out = np.zeros_like(X)
-    for p in range(rows):
-        for q in range(cols):
-            out[p * cols + q] = X[_index(p, q, rows, cols, order)]
-    return out
+def _c_call(name: str, what: str, shapes, call) -> BaseRule:
+    """Run call(U, V, W, out) with output arrays of the given (rows, R)
+    shapes and wrap the rule the library wrote."""
+    from . import _native as N
+    import ctypes as C
+    U, V, W = (np.zeros(s, np.float64) for s in shapes)
+    dp = C.POINTER(C.c_double)
+    out = N.FmmRule()
+    N.check(call(U.ctypes.data_as(dp), V.ctypes.data_as(dp), W.ctypes.data_as(dp), C.byref(out)), what)
+    assert (out.order_a, out.order_b, out.order_c) == (ROW, ROW, ROW)
+    return BaseRule(name, out.m0, out.k0, out.n0, U, V, W, ROW, ROW, ROW)
 
 
 def rotate(rule: BaseRule) -> BaseRule:
     """The cyclic rotation of a <m0,k0,n0> rule into a <n0,m0,k0> rule
-    (Sec. 5.3, App. A-B).  The matrix-multiplication tensor is the sum over
-    (i, k, j) of a_ik (x) b_kj (x) c_ij; cycling the factors to
-    c_ij (x) a_ik (x) b_kj gives the tensor of a <n0, m0, k0> product whose
-    A entry (j, i) is C's entry (i, j), whose B entry (i, k) is A's, and
-    whose C entry (j, k) is B's entry (k, j).  So U' = W, V' = U, W' = V,
-    with the W and V tables read column-major."""
-    U = _to_row_major(rule.U, rule.m0, rule.k0, rule.order_a)
-    V = _to_row_major(rule.V, rule.k0, rule.n0, rule.order_b)
-    W = _to_row_major(rule.W, rule.m0, rule.n0, rule.order_c)
-    return BaseRule(rule.name + "_rot", rule.n0, rule.m0, rule.k0, W, U, V, COL, ROW, COL)
+    (App. A-B; fmm_rule_rotate)."""
+    from . import _native as N
+    import ctypes as C
+    keep: list = []
+    cr = _c_rule(rule, keep)
+    R = rule.r
+    shapes = ((rule.n0 * rule.m0, R), (rule.m0 * rule.k0, R), (rule.n0 * rule.k0, R))
+    return _c_call(rule.name + "_rot", "fmm_rule_rotate", shapes,
+                   lambda U, V, W, o: N.lib().fmm_rule_rotate(C.byref(cr), U, V, W, o))
 
 
 def compose(outer: BaseRule, inner: BaseRule) -> BaseRule:
-    """One rule for two recursion steps (Eq. 4.4 with L = 2): block (p1, q1)
-    of the outer split, then (p2, q2) of the inner one, is entry
-    (p1 m2 + p2, q1 k2 + q2) of the <m1 m2, k1 k2, n1 n2> base case, and
-    product (r1, r2) -- numbered r1 R2 + r2 -- has coefficients
-    X1[(p1, q1), r1] X2[(p2, q2), r2].  All tables row-major."""
-    def flat(X1, rows1, cols1, o1, X2, rows2, cols2, o2):
-        A = _to_row_major(X1, rows1, cols1, o1)
-        B = _to_row_major(X2, rows2, cols2, o2)
-        R1, R2 = A.shape[1], B.shape[1]
-        out = np.zeros((rows1 * rows2 * cols1 * cols2, R1 * R2))
-        for p1 in range(rows1):
-            for q1 in range(cols1):
-                for p2 in range(rows2):
-                    for q2 in range(cols2):
-                        row = (p1 * rows2 + p2) * (cols1 * cols2) + q1 * cols2 + q2
-                        out[row] = np.outer(A[p1 * cols1 + q1], B[p2 * cols2 + q2]).reshape(-1)
-        return out
+    """One rule for two recursion steps (Eq. 4.4 with L = 2; fmm_rule_compose):
+    product (r1, r2) is numbered r1 R2 + r2."""
+    from . import _native as N
+    import ctypes as C
+    keep: list = []
+    co, ci = _c_rule(outer, keep), _c_rule(inner, keep)
     o, i = outer, inner
-    return BaseRule(f"{o.name}*{i.name}", o.m0 * i.m0, o.k0 * i.k0, o.n0 * i.n0,
-                    flat(o.U, o.m0, o.k0, o.order_a, i.U, i.m0, i.k0, i.order_a),
-                    flat(o.V, o.k0, o.n0, o.order_b, i.V, i.k0, i.n0, i.order_b),
-                    flat(o.W, o.m0, o.n0, o.order_c, i.W, i.m0, i.n0, i.order_c))
+    R = o.r * i.r
+    shapes = ((o.m0 * i.m0 * o.k0 * i.k0, R), (o.k0 * i.k0 * o.n0 * i.n0, R), (o.m0 * i.m0 * o.n0 * i.n0, R))
+    return _c_call(f"{o.name}*{i.name}", "fmm_rule_compose", shapes,
+                   lambda U, V, W, out: N.lib().fmm_rule_compose(C.byref(co), C.byref(ci), U, V, W, out))
 
 
 def variant(rule: BaseRule, XU: np.ndarray, XV: np.ndarray, XW: np.ndarray, name: str) -> BaseRule:
-    """[[XU U, XV V, XW W]]: the rule with the rows of its tables mixed by XU,
-    XV, XW in the rule's own entry order (Sec. 3.4: permutations of the
-    entries of A, B and C give equivalent rules with other stability
-    vectors).  The library checks the Brent equations of the result."""
-    return BaseRule(name, rule.m0, rule.k0, rule.n0, np.asarray(XU, np.float64) @ rule.U,
-                    np.asarray(XV, np.float64) @ rule.V, np.asarray(XW, np.float64) @ rule.W,
-                    rule.order_a, rule.order_b, rule.order_c)
+    """[[XU U, XV V, XW W]] with the mixing matrices in the rule's own entry
+    order (Sec. 3.4; fmm_rule_transform, which rejects a result that is not
+    a matrix-multiplication rule)."""
+    from . import _native as N
+    import ctypes as C
+    keep: list = []
+    cr = _c_rule(rule, keep)
+    xs = [np.ascontiguousarray(X, np.float64) for X in (XU, XV, XW)]
+    dp = C.POINTER(C.c_double)
+    R = rule.r
+    shapes = ((rule.m0 * rule.k0, R), (rule.k0 * rule.n0, R), (rule.m0 * rule.n0, R))
+    return _c_call(name, "fmm_rule_transform", shapes,
+                   lambda U, V, W, o: N.lib().fmm_rule_transform(C.byref(cr), *(x.ctypes.data_as(dp) for x in xs),
+                                                                 U, V, W, o))
+
+
+def permute(rule: BaseRule, perm_i, perm_k, perm_j, name: str) -> BaseRule:
+    """The rule on A, B blocks relabelled by permutations of the block
+    indices i, k, j (fmm_rule_permute); it computes the same product."""
+    from . import _native as N
+    import ctypes as C
+    keep: list = []
+    cr = _c_rule(rule, keep)
+    ps = [(C.c_int32 * len(p))(*p) for p in (perm_i, perm_k, perm_j)]
+    R = rule.r
+    shapes = ((rule.m0 * rule.k0, R), (rule.k0 * rule.n0, R), (rule.m0 * rule.n0, R))
+    return _c_call(name, "fmm_rule_permute", shapes,
+                   lambda U, V, W, o: N.lib().fmm_rule_permute(C.byref(cr), *ps, U, V, W, o))
+
+
+def castrapel_gustafson(rule: BaseRule, v: int) -> BaseRule:
+    """Variant v = 0..7 of a <2,2,2> rule (Sec. 3.4): bit 0 exchanges the i
+    blocks (y = 1), bit 1 the k blocks (x = 1), bit 2 the j blocks (z = 1)."""
+    sw = lambda b: [1, 0] if v & b else [0, 1]  # noqa: E731
+    return permute(rule, sw(1), sw(2), sw(4), f"{rule.name}_cg{v}")
 
 
 BUILTIN = {"strassen": strassen, "winograd": winograd, "fast323": fast323,

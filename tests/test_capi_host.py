@@ -263,3 +263,108 @@ def test_package_compose_matches_oracle_compose(native):
         one, two = api.Plan([pc]).info(), api.Plan([a, b]).info()
         for k in ("e_prod", "leaves", "nnz", "pm", "pk", "pn"):
             assert one[k] == two[k], (a, b, k)
+
+
+# ---------------------------------------------------------------- rule algebra and variants (Sec. 3.4)
+
+def test_rule_algebra_checks_brent(native):
+    # The library's transform rejects the D'Alberto variant as printed (it
+    # fails the Brent equations, pinned in the oracle tests) and accepts the
+    # reading with B's and C's columns exchanged together; permutations
+    # must be permutations.
+    P = np.array([[0, 1], [1, 0]])
+    I2 = np.eye(2)
+    s = PR.strassen()
+    with pytest.raises(native.FmmError) as e:
+        PR.variant(s, np.eye(4), np.kron(P, I2), np.kron(I2, P), "printed")
+    assert e.value.code == 2
+    good = PR.variant(s, np.eye(4), np.kron(I2, P), np.kron(P, I2), "dalberto")
+    # the same rule as exchanging the j blocks
+    perm = PR.permute(s, [0, 1], [0, 1], [1, 0], "j-exchanged")
+    assert np.array_equal(good.U, perm.U) and np.array_equal(good.V, perm.V) and np.array_equal(good.W, perm.W)
+    with pytest.raises(native.FmmError) as e:
+        PR.permute(s, [0, 0], [0, 1], [0, 1], "bad")
+    assert e.value.code == 1
+    with pytest.raises(native.FmmError) as e:
+        PR.rotate(PR.variant.__globals__["BaseRule"]("broken", 2, 2, 2, s.U, s.V, -s.W, s.order_a, s.order_b,
+                                                       s.order_c))
+    assert e.value.code == 2
+
+
+def test_rotation_matches_oracle(native):
+    # the library's rotations are the oracle's (canonical tables equal)
+    for name in ("strassen", "winograd", "fast323"):
+        lib = PR.get(name)
+        orc = _oracle_rule(name)
+        for _ in range(3):
+            lib, orc = PR.rotate(lib), OR.rotate(orc)
+            co = OR.canonical(orc)
+            assert (lib.m0, lib.k0, lib.n0) == (co.m0, co.k0, co.n0)
+            assert np.array_equal(lib.U, co.U) and np.array_equal(lib.V, co.V) and np.array_equal(lib.W, co.W)
+
+
+@pytest.mark.parametrize("name", ["strassen", "winograd"])
+def test_castrapel_gustafson_variants_match_oracle(native, name):
+    from oracle import variants as CG
+    for v in range(8):
+        lib = PR.castrapel_gustafson(PR.get(name), v)
+        orc = OR.canonical(CG.variant(_oracle_rule(name), v))
+        assert np.array_equal(lib.U, orc.U) and np.array_equal(lib.V, orc.V) and np.array_equal(lib.W, orc.W), v
+
+
+@pytest.mark.parametrize("name", ["strassen", "winograd"])
+@pytest.mark.parametrize("selection", ["random", "round_robin"])
+def test_variant_plans_match_oracle_trees(native, name, selection):
+    # fmm_plan_variants picks the same variant per node as the oracle, and
+    # its max xi / max delta (Sec. 4.5) equal the oracle's for that tree
+    from oracle import variants as CG
+    from paper_1507_00687_gb300 import api
+    for levels in (1, 2, 3):
+        plan = api.Plan.variants(name, levels, selection, seed=1234567, leaf="bf16")
+        want = (CG.select_random(7, levels, 1234567) if selection == "random"
+                else CG.select_round_robin(7, levels))
+        assert plan.chosen == want
+        orc = CG.tree(_oracle_rule(name), levels, want)
+        info = plan.info()
+        assert info["leaves"] == 7**levels
+        assert info["e_prod"] == float(OF.xi_vector(orc).max())
+        assert info["q_sum"] == float(OF.delta_vector(orc).max())
+
+
+@pytest.mark.parametrize("name", ["strassen", "winograd"])
+def test_matrix_dependent_selection_matches_oracle(native, name):
+    # From host block maxima (the values fmm_block_max would give), the
+    # library's choice per node equals the oracle's; a dominant block moves
+    # the choice away from the variant the uniform input picks.
+    import ctypes as C
+    from oracle import variants as CG
+    from paper_1507_00687_gb300 import api
+    g = np.random.default_rng(7)
+    rule = PR.get(name)
+    for levels in (1, 2, 3):
+        n = 1 << levels
+        for trial in range(4):
+            Amax = g.uniform(0.01, 4.0, (n, n)).astype(np.float32)
+            Bmax = g.uniform(0.01, 4.0, (n, n)).astype(np.float32)
+            if trial == 1:
+                Amax[n - 1, 0] = 1e4
+            want = CG.select_matrix(_oracle_rule(name), levels, Amax.astype(np.float64), Bmax.astype(np.float64))
+            plan = api.Plan.__new__(api.Plan)
+            plan._keep, plan.rules, plan.leaf = [], [rule], "bf16"
+            arr = plan._rule_array([rule])
+            h = C.c_void_p()
+            nodes = sum(7**lv for lv in range(levels))
+            chosen = (C.c_int32 * nodes)()
+            fp = C.POINTER(C.c_float)
+            assert native.lib().fmm_plan_variants(C.byref(h), arr, levels, native.SELECT_MATRIX, 0,
+                                                  Amax.ctypes.data_as(fp), Bmax.ctypes.data_as(fp), chosen,
+                                                  native.LEAF_BF16) == 0
+            plan._h = h
+            assert list(chosen) == want, (levels, trial)
+    # fmm_plan_variants needs a <2,2,2> base and block maxima for this mode
+    h = C.c_void_p()
+    holder = api.Plan(["strassen"])  # keeps the rule arrays alive
+    arr = holder._rule_array([PR.fast323()])
+    assert native.lib().fmm_plan_variants(C.byref(h), arr, 1, 1, 0, None, None, None, 0) == 10
+    arr = holder._rule_array([rule])
+    assert native.lib().fmm_plan_variants(C.byref(h), arr, 1, native.SELECT_MATRIX, 0, None, None, None, 0) == 1

@@ -368,32 +368,34 @@ def test_full_size_winograd_deep_bf16x3(api, levels, steps):
 # ---------------------------------------------------------------- failure path
 
 def test_device_timeout_reported_without_fault(api):
-    # A tiny wait limit makes the kernel's bounded mbarrier waits run out: the
-    # kernel must stop cleanly, free its TMEM and report the timeout through
-    # the status word; the context stays usable.  Run in a child process so
-    # the limit (read once per process) does not leak into other tests.
+    # FMM_TEST_STALL makes the multiply kernel's epilogue wait on a barrier
+    # that nothing arrives at; its bounded wait (0.1 s here) must run out,
+    # the kernel must stop every role, wait for its own copies and MMAs,
+    # free its TMEM and report FMM_ERR_DEVICE_TIMEOUT through the status
+    # word, and the context must stay usable.  Run in a child process so
+    # the settings (read once per process) do not leak into other tests.
     code = r"""
-import torch, sys
+import torch, sys, time
 sys.path.insert(0, '.')
 from paper_1507_00687_gb300 import api, _native
 A = torch.ones((1024, 1024), device='cuda'); B = torch.ones((1024, 1024), device='cuda')
 p = api.Plan(['strassen'], 'bf16x3')
+t0 = time.time()
 api.multiply(p, A, B)
 try:
     api.sync_status()
     print('NO-TIMEOUT')
 except _native.FmmError as e:
     print('CODE', e.code)
+print('SECONDS', time.time() - t0)
 x = (torch.ones(4, device='cuda') * 2).sum().item()
 print('ALIVE', x)
 """
-    env = dict(os.environ, FMM_WAIT_TIMEOUT_NS="1")
+    env = dict(os.environ, FMM_WAIT_TIMEOUT_NS="100000000", FMM_TEST_STALL="1")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
                        timeout=300)
     assert "ALIVE 8.0" in r.stdout, r.stdout + r.stderr
-    # a 1 ns limit cannot be met by a wait for TMA data or finished MMAs:
-    # the timeout must fire and be reported as FMM_ERR_DEVICE_TIMEOUT
     assert "CODE 8" in r.stdout, r.stdout + r.stderr
 
 

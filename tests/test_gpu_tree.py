@@ -152,3 +152,63 @@ def test_rotated_rules_one_level(api):
             got = dev_values(api.multiply(api.Plan([pr], "bf16x3", schedule), Ad, Bd))
             api.sync_status()
             _check(got, OF.fmm(A64, B64, orc), OF.growth(A64, B64, orc), orc, K, "bf16x3", f"{lab} {schedule}")
+
+
+# ---------------------------------------------------------------- Castrapel-Gustafson variants (Sec. 3.4)
+
+def _cg_max_terms(name, levels):
+    r = OR.principal(OR.winograd() if name == "winograd" else OR.strassen())
+    return int(max(r.alpha.max(), r.beta.max(), r.gamma.max())) ** levels
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+def test_block_max_exact(api, dt):
+    # fmm_block_max against the oracle's block max-abs on ragged grids
+    from oracle import variants as CG
+    for (M, K), (nrb, ncb) in (((300, 260), (4, 4)), ((37, 513), (8, 2)), ((5, 7), (8, 8)), ((1000, 64), (2, 16))):
+        X = inputs.uniform((M, K), -3, 3, seed=M * K)
+        X[M // 3, K // 5] = 40.0
+        Xd = to_dev(X, dt)
+        got = api.block_max(Xd, nrb, ncb).cpu().numpy().astype(np.float64)
+        assert np.array_equal(got, CG.block_max(dev_values(Xd), nrb, ncb)), (M, K, nrb, ncb)
+
+
+@pytest.mark.parametrize("name", ["strassen", "winograd"])
+@pytest.mark.parametrize("selection", ["random", "round_robin", "matrix"])
+@pytest.mark.parametrize("leaf", ["bf16x3", "bf16"])
+def test_variant_plans_against_oracle(api, name, selection, leaf):
+    # Two-level Castrapel-Gustafson plans: the library's choice per node is
+    # the oracle's (for the matrix-dependent one, from the block maxima the
+    # GPU found on the scaled-row/column inputs), and the product is within
+    # tolerance of the oracle's product over the same tree; integer inputs
+    # give the classical product exactly.
+    from oracle import variants as CG
+    levels = 2
+    M, K, N = 610, 530, 470
+    A, B = inputs.diag_scaled_pair(M, K, N, seed=91)
+    Ad, Bd = to_dev(A, "f32"), to_dev(B, "f32")
+    A64, B64 = dev_values(Ad), dev_values(Bd)
+    plan = api.Plan.variants(name, levels, selection, seed=2024, A=Ad, B=Bd, leaf=leaf)
+    base = OR.winograd() if name == "winograd" else OR.strassen()
+    if selection == "random":
+        want = CG.select_random(7, levels, 2024)
+    elif selection == "round_robin":
+        want = CG.select_round_robin(7, levels)
+    else:
+        g = 1 << levels
+        want = CG.select_matrix(base, levels, CG.block_max(A64, g, g), CG.block_max(B64, g, g))
+    assert plan.chosen == want
+    orc = CG.tree(base, levels, want)
+    got = dev_values(api.multiply(plan, Ad, Bd))
+    api.sync_status()
+    _, pk, _ = OF.dims(orc)
+    kl = -(-K // pk)
+    tol = (U_LEAF[leaf] + (kl + 2 * _cg_max_terms(name, levels) + 8) * 2.0**-23) * OF.growth(A64, B64, orc)
+    bad = np.abs(got - OF.fmm(A64, B64, orc)) > tol
+    assert not bad.any(), f"{name} {selection} {leaf}: {bad.sum()} entries outside tolerance"
+    Ai = inputs.integers((M, K), -4, 4, seed=1)
+    Bi = inputs.integers((K, N), -4, 4, seed=2)
+    exact = dev_values(api.multiply(plan, to_dev(Ai, "f32" if leaf == "bf16x3" else "bf16"),
+                                    to_dev(Bi, "f32" if leaf == "bf16x3" else "bf16")))
+    api.sync_status()
+    assert np.array_equal(exact, Ai @ Bi)

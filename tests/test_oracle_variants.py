@@ -1,0 +1,141 @@
+"""Pins for the oracle's Castrapel-Gustafson variants and node selections
+(Sec. 3.4).
+
+Pinned against: the Brent equations of every variant, the identity variant,
+the closed form of a variant's stability vector (a permutation of the
+rule's, since the variant relabels the blocks of C), exactness against the
+classical product on integer inputs for a tree mixing all eight variants,
+the published reference outputs of SplitMix64, brute-force minimality of
+the matrix-dependent choice, and its equivariance: exchanging the block rows
+of A (the block columns of B, both k halves) permutes the node's eight
+costs by v -> v xor 1 (v xor 4, v xor 2).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import fmm as F
+from oracle import rules as R
+from oracle import variants as CG
+from paper_1507_00687_gb300 import inputs
+
+BASES = {"strassen": R.strassen, "winograd": R.winograd}
+
+
+@pytest.mark.parametrize("name", sorted(BASES))
+def test_every_variant_is_a_rule_and_v0_is_the_rule(name):
+    base = BASES[name]()
+    for v in range(8):
+        assert R.brent_violations(CG.variant(base, v)) == 0, v
+    c0, cb = R.canonical(CG.variant(base, 0)), R.canonical(base)
+    assert np.array_equal(c0.U, cb.U) and np.array_equal(c0.V, cb.V) and np.array_equal(c0.W, cb.W)
+    # eight distinct variants
+    tabs = {R.canonical(CG.variant(base, v)).U.tobytes() + R.canonical(CG.variant(base, v)).V.tobytes()
+            + R.canonical(CG.variant(base, v)).W.tobytes() for v in range(8)}
+    assert len(tabs) == 8
+
+
+@pytest.mark.parametrize("name", sorted(BASES))
+def test_variant_stability_vector_is_the_permuted_one(name):
+    # A variant multiplies the blocks of A, B relabelled by the exchanges of
+    # i (y = 1) and j (z = 1) -- and of k, which C does not see -- so its
+    # stability vector e (indexed by C's entries, row-major) is the rule's
+    # with C's block indices relabelled: e_v(i, j) = e(i xor y1, j xor z1).
+    base = BASES[name]()
+    e = R.principal(R.canonical(base)).e.reshape(2, 2)
+    for v in range(8):
+        x, y, z = CG.exponents(v)
+        ev = R.principal(R.canonical(CG.variant(base, v))).e.reshape(2, 2)
+        si, sj = int(y == 1), int(z == 1)
+        for i, j in itertools.product(range(2), range(2)):
+            assert ev[i, j] == e[i ^ si, j ^ sj], (v, i, j)
+        assert R.principal(CG.variant(base, v)).E == R.principal(base).E
+
+
+def test_splitmix64_reference_outputs():
+    # The first outputs of SplitMix64 from state 0, as printed with the
+    # generator's reference implementation.
+    assert [CG.splitmix64(0, n) for n in range(4)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                       0x06C45D188009454F, 0xF88BB8A8724C81EC]
+
+
+def test_random_and_round_robin_selections():
+    assert CG.select_round_robin(7, 2) == [n % 8 for n in range(8)]
+    sel = CG.select_random(7, 3, seed=99)
+    assert len(sel) == 1 + 7 + 49 and all(0 <= v < 8 for v in sel)
+    assert sel == [CG.splitmix64(99, n) >> 61 for n in range(57)]
+    assert CG.select_random(7, 3, seed=99) == sel and CG.select_random(7, 3, seed=100) != sel
+
+
+@pytest.mark.parametrize("name", sorted(BASES))
+def test_variant_trees_exact_on_integers(name):
+    # a two-level tree using all eight variants computes A B exactly on
+    # small integers, like the classical product
+    base = BASES[name]()
+    chosen = CG.select_round_robin(7, 2)
+    assert set(chosen) == set(range(8))
+    tree = CG.tree(base, 2, chosen)
+    A = inputs.integers((36, 44), -4, 4, seed=5)
+    B = inputs.integers((44, 28), -4, 4, seed=6)
+    assert np.array_equal(F.fmm(A, B, tree), F.classical(A, B))
+
+
+def _costs(base, levels, Amax, Bmax):
+    cs = []
+    chosen = CG.select_matrix(base, levels, Amax, Bmax, costs=cs)
+    return chosen, cs
+
+
+@pytest.mark.parametrize("name", sorted(BASES))
+def test_matrix_selection_minimal_at_every_node(name):
+    base = BASES[name]()
+    g = np.random.default_rng(3)
+    for levels in (1, 2):
+        n = 1 << levels
+        Amax = g.integers(1, 50, (n, n)).astype(float)
+        Bmax = g.integers(1, 50, (n, n)).astype(float)
+        chosen, costs = _costs(base, levels, Amax, Bmax)
+        assert len(chosen) == CG.node_count(7, levels) == len(costs)
+        for v, cs in zip(chosen, costs):
+            assert cs[v] == min(cs) and v == cs.index(min(cs))
+        # the root's costs by brute force over the tables: max over C blocks
+        # of sum_r |w| (sum_i |u| a_i)(sum_j |v| b_j)
+        qa = [Amax[p * n // 2:(p + 1) * n // 2, q * n // 2:(q + 1) * n // 2].max() for p in (0, 1) for q in (0, 1)]
+        qb = [Bmax[p * n // 2:(p + 1) * n // 2, q * n // 2:(q + 1) * n // 2].max() for p in (0, 1) for q in (0, 1)]
+        for v in range(8):
+            c = R.canonical(CG.variant(base, v))
+            s = np.abs(c.U).T @ np.array(qa)
+            t = np.abs(c.V).T @ np.array(qb)
+            assert costs[0][v] == float((np.abs(c.W) @ (s * t)).max())
+
+
+@pytest.mark.parametrize("name", sorted(BASES))
+def test_matrix_selection_equivariance(name):
+    # Variant v on relabelled blocks is variant v xor (the relabelling) on
+    # the original ones, so the node costs permute exactly (integer block
+    # maxima keep every cost exact): exchanging A's block rows (i) maps cost
+    # v to v xor 1, A's block columns with B's block rows (k) to v xor 2,
+    # B's block columns (j) to v xor 4.  (Strassen's costs are also
+    # invariant under v -> v xor 7, its own symmetry, so ties are common.)
+    base = BASES[name]()
+    g = np.random.default_rng(11)
+    for _ in range(20):
+        Amax = g.integers(1, 100, (2, 2)).astype(float)
+        Bmax = g.integers(1, 100, (2, 2)).astype(float)
+        _, (cs,) = _costs(base, 1, Amax, Bmax)
+        for (Ap, Bp), flip in (((Amax[::-1, :], Bmax), 1), ((Amax[:, ::-1], Bmax[::-1, :]), 2),
+                               ((Amax, Bmax[:, ::-1]), 4)):
+            _, (cp,) = _costs(base, 1, Ap, Bp)
+            assert [cp[v] for v in range(8)] == [cs[v ^ flip] for v in range(8)], flip
+        # the choice is the lowest index among the minima
+        v = CG.select_matrix(base, 1, Amax, Bmax)[0]
+        assert cs[v] == min(cs) and all(cs[u] > cs[v] for u in range(v))
+
+
+def test_block_max_definition():
+    X = np.arange(35, dtype=float).reshape(5, 7) - 17.0
+    out = CG.block_max(X, 2, 3)   # blocks of 3 x 3, edge blocks 2 rows / 1 column
+    assert out.shape == (2, 3)
+    assert out[0, 0] == 17.0 and out[1, 2] == 17.0 and out[0, 2] == 11.0 and out[1, 0] == 13.0
+    assert CG.block_max(np.zeros((3, 3)), 4, 4)[3, 3] == 0.0
