@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--levels", type=int, default=1)
     ap.add_argument("--leaf", default="bf16x3")
     ap.add_argument("--scaling", default="OI")
-    ap.add_argument("--schedule", default="auto", choices=["auto", "pass", "load_stage"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "pass", "load_stage", "pass_accumulate"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator / variant timings")
     ap.add_argument("--batch", type=int, default=512, help="products in the batched workload extra (0: skip)")
     ap.add_argument("--experiment", default="", choices=["", "scaling_accuracy", "batch"],
@@ -622,6 +622,16 @@ def main():
         torch.cuda.synchronize()
         extras["fast_no_scaling"] = {"tflops": flops / (ns_ms * 1e-3) / 1e12, "ms_per_step": ns_ms,
                                      "max_abs_err": float((C.double() - ref).abs().max())}
+        if args.schedule != "pass_accumulate":
+            plan_acc = api.Plan(rules, args.leaf, "pass_accumulate")
+            a_ms, a_kms, _ = timed(max(10, args.steps // 4), plan_acc, args.scaling)
+            step(plan_acc, args.scaling)
+            torch.cuda.synchronize()
+            extras["fast_accumulate"] = {"tflops": flops / (a_ms * 1e-3) / 1e12, "ms_per_step": a_ms,
+                                         "kernel_ms": a_kms, "max_abs_err": float((C.double() - ref).abs().max()),
+                                         "note": "leaf products added into C by atomic FP32 additions "
+                                                 "(no stored products, no output pass)"}
+            del plan_acc
         rel = lambda X: float(((X - ref).abs() / ref.abs().clamp_min(1e-300)).max())  # noqa: E731
         step(plan, args.scaling)
         torch.cuda.synchronize()
@@ -678,15 +688,16 @@ def main():
     # two bf16 planes for bf16x3, else one 16-bit plane) and, with stored
     # leaf products (every pass-schedule plan with more than one leaf at
     # these sizes), the output pass (reads the R^L fp32 products, writes C)
+    comb_ms, comb_n = kern["combine"]
+    per_step = comb_n // max(1, bd_steps)
     planes = 2 if args.leaf == "bf16x3" else 1
     R = info["leaves"]
     bt = -(-n // info["pm"])
     tp_a, tp_b = -(-bt // 128) * 128, -(-bt // 256) * 256
     kp = -(-(-(-n // info["pk"])) // 64) * 64
-    comb_ms, comb_n = kern["combine"]
-    per_step = comb_n // max(1, bd_steps)
     pass_bytes = 2 * n * n * 4 + planes * R * (tp_a + tp_b) * kp * 2
-    if sched_used == "pass" and R > 1:
+    if sched_used == "pass" and R > 1 and per_step >= 2:
+        # stored leaf products: the output pass reads them and writes C
         pass_bytes += R * tp_a * tp_b * 4 + n * n * 4
     kernel_times = {k or "all": {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / max(1, v[1])}
                     for k, v in kern.items()}

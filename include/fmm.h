@@ -326,12 +326,21 @@ fmm_status fmm_scale_adaptive(const void* A, const void* B, int dtype, int64_t M
  * FMM_SCHEDULE_PASS_EPILOGUE and FMM_SCHEDULE_PASS_PRODUCTS force one form.
  * Stored products need a plan of more than one leaf and at most 96 C
  * blocks; otherwise the epilogue form runs.
+ *   FMM_SCHEDULE_PASS_ACCUMULATE  the pass schedule with every (leaf, tile)
+ *     unit adding its W-weighted, unscaled terms into C (zeroed first) by
+ *     atomic FP32 additions in the multiply kernel's epilogue: no stored
+ *     products, no output pass.  The order in which an element's terms
+ *     arrive varies from run to run, so results may differ in the last
+ *     bits between runs (each is within the same error bound).  Taken by
+ *     the CTA-pair kernel (leaf blocks of at least 256 x 256, 16-bit
+ *     leaves); other products run as FMM_SCHEDULE_PASS.
  */
 #define FMM_SCHEDULE_AUTO 0
 #define FMM_SCHEDULE_LOAD_STAGE 1
 #define FMM_SCHEDULE_PASS 2
 #define FMM_SCHEDULE_PASS_EPILOGUE 3
 #define FMM_SCHEDULE_PASS_PRODUCTS 4
+#define FMM_SCHEDULE_PASS_ACCUMULATE 5
 
 /* Set the plan's schedule (FMM_SCHEDULE_*); FMM_ERR_ARG for other values.
  * The gradient products of fmm_multiply_backward follow it. */

@@ -21,6 +21,7 @@ ORDER_ROW, ORDER_COL = 0, 1
 DT_F32, DT_BF16, DT_F16 = 0, 1, 2
 LEAF_BF16, LEAF_F16, LEAF_BF16X3, LEAF_E4M3B128 = 0, 1, 2, 3
 SCHEDULE_AUTO, SCHEDULE_LOAD_STAGE, SCHEDULE_PASS, SCHEDULE_PASS_EPILOGUE, SCHEDULE_PASS_PRODUCTS = 0, 1, 2, 3, 4
+SCHEDULE_PASS_ACCUMULATE = 5
 
 # Every symbol include/fmm.h declares.
 EXPORTS = [

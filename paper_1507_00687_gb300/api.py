@@ -14,7 +14,8 @@ from .rules import BaseRule, get as get_rule
 
 LEAF = {"bf16": N.LEAF_BF16, "fp16": N.LEAF_F16, "bf16x3": N.LEAF_BF16X3, "e4m3b128": N.LEAF_E4M3B128}
 SCHEDULE = {"auto": N.SCHEDULE_AUTO, "load_stage": N.SCHEDULE_LOAD_STAGE, "pass": N.SCHEDULE_PASS,
-            "pass_epilogue": N.SCHEDULE_PASS_EPILOGUE, "pass_products": N.SCHEDULE_PASS_PRODUCTS}
+            "pass_epilogue": N.SCHEDULE_PASS_EPILOGUE, "pass_products": N.SCHEDULE_PASS_PRODUCTS,
+            "pass_accumulate": N.SCHEDULE_PASS_ACCUMULATE}
 DTYPE = {torch.float32: N.DT_F32, torch.bfloat16: N.DT_BF16, torch.float16: N.DT_F16}
 
 

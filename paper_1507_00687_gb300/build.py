@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libfmm.so")
 BUILD = os.path.join(PKG, "_build")
 SOURCES = ["plan.cpp", "rules.cpp", "scale.cu", "combine.cu", "gemm.cu", "gemm_bf16.cu", "gemm_f16.cu", "gemm_bf16x3.cu",
-           "gemm_direct.cu", "gemm_fp8.cu", "timing.cu", "host.cu", "capi.cu"]
+           "gemm_direct.cu", "gemm_pair.cu", "gemm_fp8.cu", "timing.cu", "host.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

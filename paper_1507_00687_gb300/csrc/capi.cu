@@ -277,7 +277,18 @@ static int64_t combined_bytes(int64_t T, int64_t Kd, int64_t pt, int64_t pk, int
 
 // Bytes of the stored leaf products (fp32, R padded leaf blocks).
 static int64_t products_bytes(int64_t Tx, int64_t Ty, int64_t ptx, int64_t pty, int64_t leaves, int64_t tile_n) {
-  return round_up(leaves * round_up(ceil_div(Tx, ptx), 128) * round_up(ceil_div(Ty, pty), tile_n) * 4, 256);
+  return round_up(leaves * round_up(ceil_div(Tx, ptx), 256) * round_up(ceil_div(Ty, pty), tile_n) * 4, 256);
+}
+
+// Leaf products on CTA pairs (256 x 256 tiles shared by two SMs) for the
+// pass schedule's 16-bit leaves when the leaf blocks are at least 256 x 256;
+// FMM_TILE_PAIRS=0 in the environment (read once) keeps the one-CTA kernel.
+static bool pair_tiles_enabled() {
+  static bool on = [] {
+    const char* s = std::getenv("FMM_TILE_PAIRS");
+    return !(s && std::atoi(s) == 0);
+  }();
+  return on;
 }
 
 // Workspace of the pass schedule for the product X (T_x x Kd) Y (Kd x T_y)
@@ -299,7 +310,9 @@ static int64_t pass_bytes(const Plan* p, int64_t Tx, int64_t Kd, int64_t Ty, int
     const int64_t k1 = ceil_div(Kd, pk) * (pk / p->rules[0].k0);
     between = 3 * round_up(p->rules[0].r * k1 * 4, 256);
   }
-  return combined_bytes(Tx, Kd, ptx, pk, p->leaves, planes, 128) +
+  // A blocks padded to 256 rows when the CTA-pair kernel takes the product
+  const int64_t ta = pair_tiles_enabled() && ceil_div(Tx, ptx) >= 256 ? 256 : 128;
+  return combined_bytes(Tx, Kd, ptx, pk, p->leaves, planes, ta) +
          combined_bytes(Ty, Kd, pty, pk, p->leaves, planes, 256) +
          (p->leaves > 1 ? products_bytes(Tx, Ty, ptx, pty, p->leaves, 256) : 0) + between;
 }
@@ -309,6 +322,7 @@ static int64_t pass_bytes(const Plan* p, int64_t Tx, int64_t Kd, int64_t Ty, int
 // and the workspace bytes of the combined A, B and the stored products.
 struct PassGeom {
   int planes, bn;
+  bool pair;  // the CTA-pair multiply kernel (256 x 256 tiles)
   int64_t R, bt_a, bt_b, bk, tp_a, tp_b, kp, bytes_a, bytes_b, bytes_m;
 };
 
@@ -320,7 +334,8 @@ static PassGeom pass_geom(const Plan* p, const Source& x, const Source& y, int b
   g.bt_b = ceil_div(y.T, y.pt);
   g.bk = ceil_div(x.Kd, x.pk);
   g.bn = bn > 0 ? bn : pass_tile_n(g.bt_b);
-  g.tp_a = round_up(g.bt_a, 128);
+  g.pair = bn <= 0 && g.bn == 256 && g.bt_a >= 256 && p->leaf_format != FMM_LEAF_E4M3B128 && pair_tiles_enabled();
+  g.tp_a = round_up(g.bt_a, g.pair ? 256 : 128);
   g.tp_b = round_up(g.bt_b, g.bn);
   g.kp = round_up(g.bk, 64);
   g.bytes_a = round_up(g.planes * g.R * g.tp_a * g.kp * 2, 256);
@@ -380,7 +395,8 @@ static bool direct_args(const Plan* p, const PassGeom& g, const Source& x, const
     return s.kcontig ? make_map_sw(m, buf, f16, g.planes * g.R * tp, g.kp, g.kp, bk_step, tile)
                      : make_map_sw(m, buf, f16, g.planes * g.R * g.kp, tp, tp, 64, bk_step);
   };
-  if (!map(&d->map_a, x, wa, g.tp_a, 128) || !map(&d->map_b, y, wb, g.tp_b, g.bn)) return false;
+  // K-major B boxes: the tile's width, or half of it per CTA of a pair
+  if (!map(&d->map_a, x, wa, g.tp_a, 128) || !map(&d->map_b, y, wb, g.tp_b, g.pair ? 128 : g.bn)) return false;
   d->a_mn = x.kcontig ? 0 : 1;
   d->b_mn = y.kcontig ? 0 : 1;
   d->c = c;
@@ -522,13 +538,18 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
   // faster at every size (every SM gets (leaf, tile) units; the fused
   // epilogue leaves SMs idle when tiles per leaf are few, and its C
   // read-modify-writes cost more than one more bandwidth pass).
-  const bool want_m = p->schedule != FMM_SCHEDULE_PASS_EPILOGUE;
+  // Accumulating epilogue (CTA pairs only): every (leaf, tile) unit adds
+  // its terms into a zeroed C by atomic FP32 additions, so neither stored
+  // products nor the output pass are needed.
+  const bool accumulate = p->schedule == FMM_SCHEDULE_PASS_ACCUMULATE && g.pair && g.R > 1;
+  const bool want_m = p->schedule != FMM_SCHEDULE_PASS_EPILOGUE && !accumulate;
   // more C blocks than the stored-products pass keeps on chip: the output
   // pass gathers per C block instead
   const bool gather = p->pm * p->pn > kMaxOutBlocks;
   const bool store_m = want_m && g.R > 1 && (!gather || p->gather_off >= 0) &&
                        (int64_t)ws_bytes >= g.bytes_a + g.bytes_b + g.bytes_m;
   float* mbuf = store_m ? reinterpret_cast<float*>(wb + g.bytes_b) : nullptr;
+
   CombineArgs ca = combine_args(p, g, x, 0, leaves, wa), cb = combine_args(p, g, y, 1, leaves, wb);
   if (between) {
     // Scaling between recursive steps: the first level's pairs (S_r, T_r)
@@ -576,7 +597,14 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
   if (!cuda_ok(launch_combine_pair(cb, ca, st), "combination passes")) return FMM_ERR_CUDA;
   DirectArgs d;
   if (!direct_args(p, g, x, y, c, leaves, wa, wb, mbuf, status, &d)) return FMM_ERR_CUDA;
-  if (!cuda_ok(launch_direct_gemm(d, p->leaf_format, g.bn, st), "multiply launch")) return FMM_ERR_CUDA;
+  if (accumulate) {
+    d.accumulate = 1;
+    if (!cuda_ok(cudaMemset2DAsync(c.C, (size_t)c.ldc * 4, 0, (size_t)c.N * 4, (size_t)c.M, st), "C zero fill"))
+      return FMM_ERR_CUDA;
+  }
+  if (!cuda_ok(g.pair ? launch_pair_gemm(d, p->leaf_format, st) : launch_direct_gemm(d, p->leaf_format, g.bn, st),
+               "multiply launch"))
+    return FMM_ERR_CUDA;
   if (!store_m) return FMM_OK;
   const OutArgs o = out_args(p, g, c, leaves, mbuf);
   return cuda_ok(gather ? launch_out_gather(o, st) : launch_out_combine(o, st), "output combination pass")
@@ -615,7 +643,7 @@ static fmm_status run_plan(const Plan* p, const Source& x, const Source& y, floa
   c.eB = eB;
   c.vec_ok = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0) && (c.bn % 4 == 0) ? 1 : 0;
   const bool pass = p->schedule == FMM_SCHEDULE_PASS || p->schedule == FMM_SCHEDULE_PASS_EPILOGUE ||
-                    p->schedule == FMM_SCHEDULE_PASS_PRODUCTS ||
+                    p->schedule == FMM_SCHEDULE_PASS_PRODUCTS || p->schedule == FMM_SCHEDULE_PASS_ACCUMULATE ||
                     (p->schedule == FMM_SCHEDULE_AUTO && ws && (uintptr_t)ws % 256 == 0 &&
                      (int64_t)ws_bytes >= pass_bytes(p, M, K, N, p->pm, p->pk, p->pn));
   const bool between = allow_between && p->between && p->levels >= 2 && p->level1;
@@ -1142,7 +1170,7 @@ fmm_status fmm_plan_destroy(fmm_plan_t plan) {
 
 fmm_status fmm_plan_set_schedule(fmm_plan_t plan, int schedule) {
   Plan* p = reinterpret_cast<Plan*>(plan);
-  if (!p || schedule < FMM_SCHEDULE_AUTO || schedule > FMM_SCHEDULE_PASS_PRODUCTS) return FMM_ERR_ARG;
+  if (!p || schedule < FMM_SCHEDULE_AUTO || schedule > FMM_SCHEDULE_PASS_ACCUMULATE) return FMM_ERR_ARG;
   p->schedule = schedule;
   if (p->grad_a) p->grad_a->schedule = schedule;
   if (p->grad_b) p->grad_b->schedule = schedule;
@@ -1404,7 +1432,8 @@ fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, con
   const int64_t pass_need = pass_bytes(p, M, K, N, p->pm, p->pk, p->pn);
   const int64_t stage_need = prepared_bytes(M, K, p->pm, p->pk) + prepared_bytes(N, K, p->pn, p->pk);
   const bool pass_only = p->leaf_format == FMM_LEAF_E4M3B128 || p->schedule == FMM_SCHEDULE_PASS ||
-                         p->schedule == FMM_SCHEDULE_PASS_EPILOGUE || p->schedule == FMM_SCHEDULE_PASS_PRODUCTS;
+                         p->schedule == FMM_SCHEDULE_PASS_EPILOGUE || p->schedule == FMM_SCHEDULE_PASS_PRODUCTS ||
+                         p->schedule == FMM_SCHEDULE_PASS_ACCUMULATE;
   const int64_t ws_need = pass_only ? pass_need
                           : p->schedule == FMM_SCHEDULE_LOAD_STAGE ? stage_need
                                                                    : std::min(pass_need, stage_need);

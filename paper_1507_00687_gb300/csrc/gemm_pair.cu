@@ -1,0 +1,415 @@
+// Leaf products on CTA pairs (Eq. 4.4, second and third lines): the same
+// work units as the one-CTA multiply kernel (gemm_direct.cu) with 256 x 256
+// tiles shared by two CTAs on neighbouring SMs (a cluster of two):
+// tcgen05.mma.cta_group::2 with M = 256 takes A rows 0..127 from the
+// leader's shared memory and 128..255 from the peer's, B columns 0..127
+// from the leader's and 128..255 from the peer's, and writes each CTA's
+// 128 x 256 FP32 accumulator into its own TMEM.  Per CTA a 64-wide K stage
+// is 16 KB of A and 16 KB of B (32 KB, one plane) for a 128 x 256 x 64
+// share of the products, where the one-CTA 128 x 256 tile needs 48 KB: a
+// third less operand traffic from L2 and through shared memory per flop.
+//
+//   warps 0..E-1  epilogue of this CTA's 128 tile rows (TMEM lane quarters,
+//                 and with E = 8 column halves), as in the one-CTA kernel
+//   warp E        lane 0: TMEM allocation (both CTAs, together); in the
+//                 leader, the single-thread MMA issuer
+//   warp E+1      lane 0: TMA issuer for this CTA's halves of A and B; each
+//                 copy counts its bytes on the leader's stage barrier
+//
+// Protocol (barriers at the same offsets in both CTAs):
+//   full[s]   leader only: the leader's producer expects both CTAs' bytes,
+//             both producers' copies complete on it;
+//   empty[s]  each CTA: the leader's MMA commit arrives on both (multicast);
+//   tfull[b]  each CTA: the leader's commit after a unit's last MMA;
+//   tempty[b] leader only: one arrival per epilogue warp of both CTAs.
+// Every wait is bounded (globaltimer, the status word's timeout bit on
+// expiry); a CTA that stops sets its own and its peer's abort flag.  Both
+// CTAs leave through one path: after their roles end they wait (bounded)
+// for their own outstanding work, meet at a cluster barrier -- reached by
+// every thread of both CTAs, since every loop before it is bounded -- and
+// only then free TMEM and exit, so neither exits while the other may still
+// touch its shared memory or TMEM.
+#include <algorithm>
+#include <cstring>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/fmm.h"
+#include "device.cuh"
+#include "gemm_common.cuh"
+#include "kernels.h"
+
+namespace fmm {
+namespace pair {
+
+using gemm::epi_chunk;
+using gemm::epi_chunk_red;
+using gemm::mbar_arrive_expect_tx;
+using gemm::tma_load_2d_pair;
+
+constexpr int BM = 256, BN = 256;  // tile of the pair
+constexpr int HM = 128, HN = 128;  // this CTA's rows of A, columns of B
+
+template <int FMT>
+struct Cfg {
+  static constexpr int BK = 64;
+  static constexpr int kSplit = FMT == FMM_LEAF_BF16X3 ? 2 : 1;
+  static constexpr int kATile = HM * BK * 2;
+  static constexpr int kBTile = HN * BK * 2;
+  static constexpr int kStage = kSplit * (kATile + kBTile);
+  static constexpr int kStages = (212 * 1024) / kStage > 8 ? 8 : (212 * 1024) / kStage;
+  static constexpr int kTmemCols = 2 * BN;
+  static constexpr int kBarBytes = 256;
+  static constexpr int kSmem = kStages * kStage + kBarBytes + 1024;  // + alignment slack
+};
+
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+
+// This CTA's half of an operand tile: `rows` t x BK k from plane row block
+// `blk` at t offset t0, k offset k0 (MN-major: one 64 t x BK k box per 64 t).
+template <bool MN, int BK>
+__device__ __forceinline__ void load_half(uint8_t* dst, const CUtensorMap* map, int rows, int64_t blk, int64_t tp,
+                                          int64_t kp, int64_t t0, int64_t k0, uint32_t bar) {
+  if constexpr (MN) {
+    for (int c = 0; c < rows / 64; ++c)
+      tma_load_2d_pair(dst + c * (BK * 128), map, (int32_t)(t0 + 64 * c), (int32_t)(blk * kp + k0), bar);
+  } else {
+    tma_load_2d_pair(dst, map, (int32_t)k0, (int32_t)(blk * tp + t0), bar);
+  }
+}
+
+template <bool MN, int BK>
+__device__ __forceinline__ uint64_t tile_desc(uint32_t saddr, int k16) {
+  if constexpr (MN) return smem_desc_mn_sw128(saddr + k16 * 2048, BK * 128);
+  else return smem_desc_sw128(saddr + k16 * 32);
+}
+
+template <int FMT, bool A_MN, bool B_MN, int EPI>
+__global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __grid_constant__ DirectArgs args) {
+  constexpr int kMmaWarp = EPI, kTmaWarp = EPI + 1;
+  using C = Cfg<FMT>;
+  constexpr int BK = C::BK;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStage);
+  uint64_t* empty = full + C::kStages;
+  uint64_t* tfull = empty + C::kStages;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint64_t* never = drain + 1;  // no thread ever arrives here (timeout-path test)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 2 * EPI);
+    }
+    mbar_init(drain, 1);
+    mbar_init(never, 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == kMmaWarp) tmem_alloc_pair(tmem_slot, C::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  // both CTAs' barriers exist before either CTA signals the other's
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t peer_abort = mapa_shared(smem_u32((const void*)abort_flag), rank ^ 1u);
+  auto stop = [&]() {
+    *abort_flag = 1;
+    st_cluster_u32(peer_abort, 1u);
+  };
+  // the combined operands of the previous kernel are read from here on
+  pdl_wait();
+  pdl_trigger();
+
+  // Units of this pair: u = cluster id, + cluster count, ...; one 256 x 256
+  // tile of one leaf (stored products) or one tile position with all its
+  // leaves in leaf order (fused epilogue).
+  const int64_t ntn = args.tp_b / BN, ntiles = (args.tp_a / BM) * ntn;
+  const bool per_leaf = args.mbuf || args.accumulate;  // units are (leaf, tile)
+  const int64_t total_units = per_leaf ? ntiles * args.num_leaves : ntiles;
+  const int64_t u0 = cluster_id_x(), ustep = cluster_count_x();
+  struct Cursor {
+    int64_t u, leaf, leaf_end, tm, tn;
+  };
+  auto decode = [&](Cursor& c) {
+    if (c.u >= total_units) return;
+    int64_t tile;
+    if (per_leaf) {
+      c.leaf = c.u / ntiles;
+      c.leaf_end = c.leaf + 1;
+      tile = c.u % ntiles;
+    } else {
+      c.leaf = 0;
+      c.leaf_end = args.num_leaves;
+      tile = c.u;
+    }
+    c.tm = tile / ntn;
+    c.tn = tile % ntn;
+  };
+  auto first = [&]() {
+    Cursor c;
+    c.u = u0;
+    decode(c);
+    return c;
+  };
+  auto advance = [&](Cursor& c) {
+    if (++c.leaf >= c.leaf_end) {
+      c.u += ustep;
+      decode(c);
+    }
+  };
+  const int64_t KT = args.kp / BK;
+  const int64_t NL = args.num_leaves;
+
+  if (warp == kTmaWarp) {
+    if (lane == 0) {
+      // ------------------------------------------------------ TMA issuer
+      const uint32_t full0 = mapa_shared(smem_u32(&full[0]), 0u);  // the leader's stage barriers
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      uint32_t armed = 0, armed_parity = 0;  // leader: per stage, expecting bytes, parity it completes
+      for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
+        for (int64_t kt = 0; kt < KT && ok; ++kt) {
+          if (!mbar_wait_bounded_cluster(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + stage * C::kStage;
+          const uint32_t fb = full0 + 8u * (uint32_t)stage;
+          if (leader) mbar_arrive_expect_tx(&full[stage], 2u * (uint32_t)C::kStage);
+          const int64_t k0 = kt * BK, ta = w.tm * BM + rank * HM, tb = w.tn * BN + rank * HN;
+          load_half<A_MN, BK>(st, &args.map_a, HM, w.leaf, args.tp_a, args.kp, ta, k0, fb);
+          load_half<B_MN, BK>(st + C::kSplit * C::kATile, &args.map_b, HN, w.leaf, args.tp_b, args.kp, tb, k0, fb);
+          if constexpr (C::kSplit == 2) {
+            load_half<A_MN, BK>(st + C::kATile, &args.map_a, HM, NL + w.leaf, args.tp_a, args.kp, ta, k0, fb);
+            load_half<B_MN, BK>(st + 2 * C::kATile + C::kBTile, &args.map_b, HN, NL + w.leaf, args.tp_b, args.kp,
+                                tb, k0, fb);
+          }
+          if (leader) {
+            armed |= 1u << stage;
+            armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
+          }
+          if (++stage == C::kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) stop();
+      // The leader's stage barriers complete only when both CTAs' copies
+      // have landed: wait (1 s cap each) for every stage it armed.
+      for (int s = 0; s < C::kStages; ++s) {
+        if (armed & (1u << s)) {
+          const uint64_t t0 = globaltimer_ns();
+          while (!mbar_try_wait_cluster(&full[s], (armed_parity >> s) & 1u) &&
+                 globaltimer_ns() - t0 < 1000000000ull) {
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0 && leader) {
+      // ------------------------------------------------------ MMA issuer
+      constexpr uint32_t idesc = idesc_f16(FMT == FMM_LEAF_F16 ? 0u : 1u, BM, BN, A_MN, B_MN);
+      int stage = 0;
+      uint32_t phase = 0, acc_iter = 0;
+      bool ok = true;
+      const uint32_t sbase = smem_u32(smem);
+      for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
+        const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
+        if (!mbar_wait_bounded_cluster(&tempty[buf], aph ^ 1u, abort_flag, args.timeout_ns)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + buf * BN;
+        for (int64_t kt = 0; kt < KT; ++kt) {
+          if (!mbar_wait_bounded_cluster(&full[stage], phase, abort_flag, args.timeout_ns)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_hi = sbase + stage * C::kStage;
+          const uint32_t a_lo = a_hi + C::kATile;
+          const uint32_t b_hi = a_hi + C::kSplit * C::kATile;
+          const uint32_t b_lo = b_hi + C::kBTile;
+#pragma unroll
+          for (int k16 = 0; k16 < BK / 16; ++k16) {
+            const uint32_t acc = (kt > 0 || k16 > 0) ? 1u : 0u;
+            const uint64_t ah = tile_desc<A_MN, BK>(a_hi, k16), bh = tile_desc<B_MN, BK>(b_hi, k16);
+            mma_f16_pair(d_tmem, ah, bh, idesc, acc);
+            if constexpr (C::kSplit == 2) {
+              mma_f16_pair(d_tmem, ah, tile_desc<B_MN, BK>(b_lo, k16), idesc, 1u);
+              mma_f16_pair(d_tmem, tile_desc<A_MN, BK>(a_lo, k16), bh, idesc, 1u);
+            }
+          }
+          mma_commit_pair(&empty[stage]);
+          if (++stage == C::kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit_pair(&tfull[buf]);
+        ++acc_iter;
+      }
+      if (!ok) stop();
+      // every issued MMA completes before either CTA frees its TMEM (own
+      // 1 s cap: MMAs wait on nothing)
+      mma_commit_pair(drain);
+      const uint64_t t0 = globaltimer_ns();
+      while (!mbar_try_wait(drain, 0) && globaltimer_ns() - t0 < 1000000000ull) {
+      }
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------------- epilogue
+    uint32_t acc_iter = 0;
+    bool ok = true;
+    if (args.stall_test) ok = __all_sync(0xffffffffu, mbar_wait_bounded(never, 0, abort_flag, args.timeout_ns));
+    const int quarter = warp & 3, half = EPI == 8 ? warp >> 2 : 0;
+    constexpr int kChunks = BN / 32 / (EPI / 4);  // 32-column chunks per warp
+    const int row = (int)rank * HM + quarter * 32 + lane;  // tile row of this thread (TMEM lane = row mod 128)
+    const uint32_t tempty0 = mapa_shared(smem_u32(&tempty[0]), 0u);
+    for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
+      const int64_t leaf = w.leaf, tn = w.tn;
+      const int64_t ml = w.tm * BM + row;
+      const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded_cluster(&tfull[buf], aph, abort_flag, args.timeout_ns));
+      if (!ok) break;
+      tc_fence_after();
+      const LeafDesc* L = args.leaves + leaf;
+      float* mrow = args.mbuf ? args.mbuf + (leaf * args.tp_a + ml) * args.tp_b + tn * BN : nullptr;
+#pragma unroll 1
+      for (int cc = half * kChunks; cc < (half + 1) * kChunks; ++cc) {
+        uint32_t r[32];
+        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + cc * 32, r);
+        if (mrow) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<uint4*>(mrow + cc * 32 + 4 * q) =
+                make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+        } else if (ml < args.c.bm) {
+          if (args.accumulate) epi_chunk_red(args.c, L, ml, tn * BN + cc * 32, r);
+          else epi_chunk(args.c, L, ml, tn * BN + cc * 32, r);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(tempty0 + 8u * buf);
+      ++acc_iter;
+    }
+    if (!ok && lane == 0) stop();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag) {
+    // copies or arrivals this CTA issued before stopping land within
+    // microseconds; let them before the pair meets for the last time
+    const uint64_t t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < 200000ull) {
+    }
+  }
+  cluster_sync_all();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(args.status, kStatusTimeout);
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, C::kTmemCols);
+  }
+}
+
+template <int FMT, bool A_MN, bool B_MN, int EPI>
+cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
+  using C = Cfg<FMT>;
+  auto kern = pair_fmm_kernel<FMT, A_MN, B_MN, EPI>;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  if (a.tp_a % BM != 0 || a.tp_b % BN != 0 || a.kp % C::BK != 0) return cudaErrorInvalidValue;
+  const int64_t ntiles = (a.tp_a / BM) * (a.tp_b / BN);
+  if (ntiles == 0 || a.num_leaves == 0) return cudaSuccess;
+  const int64_t units = (a.mbuf || a.accumulate) ? ntiles * a.num_leaves : ntiles;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3((EPI + 2) * 32);
+  cfg.dynamicSmemBytes = C::kSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  // as many pairs as can be resident at once (pairs need two SMs of one GPC)
+  static int resident[64] = {0};
+  if (!resident[dev]) {
+    int n = 0;
+    cfg.gridDim = dim3((unsigned)(device_sm_count() & ~1));
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = device_sm_count() / 2;
+    }
+    resident[dev] = n;
+  }
+  const int64_t pairs = std::min<int64_t>(units, resident[dev]);
+  cfg.gridDim = dim3((unsigned)(2 * pairs));
+  KernelTimer timer("multiply", st);
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int FMT>
+cudaError_t launch_layout(const DirectArgs& a, cudaStream_t st) {
+  if (!a.a_mn && a.b_mn) {
+    if (!a.mbuf) return launch_cfg<FMT, false, true, 8>(a, st);
+    return launch_cfg<FMT, false, true, 4>(a, st);
+  }
+  if (!a.a_mn && !a.b_mn) return launch_cfg<FMT, false, false, 4>(a, st);
+  if (a.a_mn && a.b_mn) return launch_cfg<FMT, true, true, 4>(a, st);
+  return cudaErrorNotSupported;
+}
+
+}  // namespace pair
+
+cudaError_t launch_pair_gemm(const DirectArgs& a, int leaf_format, cudaStream_t st) {
+  switch (leaf_format) {
+    case FMM_LEAF_BF16: return pair::launch_layout<FMM_LEAF_BF16>(a, st);
+    case FMM_LEAF_F16: return pair::launch_layout<FMM_LEAF_F16>(a, st);
+    default: return pair::launch_layout<FMM_LEAF_BF16X3>(a, st);
+  }
+}
+
+}  // namespace fmm

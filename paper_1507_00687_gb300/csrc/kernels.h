@@ -208,6 +208,7 @@ struct DirectArgs {
   int64_t kp;          // padded k extent (multiple of 64)
   int a_mn, b_mn;      // operand layouts
   float* mbuf;         // null: fused epilogue into C; else store M_r, [leaf][tp_a][tp_b] fp32
+  int accumulate;      // mbuf null: (leaf, tile) units add into C (zeroed) by atomic FP32 additions
   int* status;
   uint64_t timeout_ns;
   // Test of the timeout path (FMM_TEST_STALL set in the environment): the
@@ -263,6 +264,10 @@ cudaError_t launch_out_combine_batched(const OutArgs* args, const int64_t* start
 
 // bn: tile width along N (128 or 256).
 cudaError_t launch_direct_gemm(const DirectArgs& args, int leaf_format, int bn, cudaStream_t st);
+// The same work on CTA pairs (cluster of two, tcgen05 cta_group::2):
+// 256 x 256 tiles, tp_a and tp_b multiples of 256; a K-major B operand's
+// tensor map has 128-row boxes (each CTA loads half of B's tile).
+cudaError_t launch_pair_gemm(const DirectArgs& args, int leaf_format, cudaStream_t st);
 
 // The same kernel over a batch: tab (device memory) holds `count` problems,
 // each with its tensor maps, leaves and stored-product buffer (mbuf set);

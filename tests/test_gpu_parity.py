@@ -94,7 +94,7 @@ SHAPES = [(256, 256, 256), (300, 200, 250), (16, 16, 16), (1000, 520, 776), (1, 
 # the combination pass into the workspace -- with the output combination in
 # the multiply epilogue or over stored leaf products.  All three are checked
 # everywhere the multiply is.
-SCHEDULES = ["load_stage", "pass_epilogue", "pass_products"]
+SCHEDULES = ["load_stage", "pass_epilogue", "pass_products", "pass_accumulate"]
 
 
 @pytest.mark.parametrize("schedule", SCHEDULES)
@@ -367,7 +367,8 @@ def test_full_size_winograd_deep_bf16x3(api, levels, steps):
 
 # ---------------------------------------------------------------- failure path
 
-def test_device_timeout_reported_without_fault(api):
+@pytest.mark.parametrize("pairs", ["1", "0"], ids=["cta_pairs", "one_cta"])
+def test_device_timeout_reported_without_fault(api, pairs):
     # FMM_TEST_STALL makes the multiply kernel's epilogue wait on a barrier
     # that nothing arrives at; its bounded wait (0.1 s here) must run out,
     # the kernel must stop every role, wait for its own copies and MMAs,
@@ -391,12 +392,99 @@ print('SECONDS', time.time() - t0)
 x = (torch.ones(4, device='cuda') * 2).sum().item()
 print('ALIVE', x)
 """
-    env = dict(os.environ, FMM_WAIT_TIMEOUT_NS="100000000", FMM_TEST_STALL="1")
+    env = dict(os.environ, FMM_WAIT_TIMEOUT_NS="100000000", FMM_TEST_STALL="1", FMM_TILE_PAIRS=pairs)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
                        timeout=300)
     assert "ALIVE 8.0" in r.stdout, r.stdout + r.stderr
     assert "CODE 8" in r.stdout, r.stdout + r.stderr
+
+
+def test_cta_pair_kernel_matches_one_cta_kernel(api, tmp_path):
+    # The CTA-pair multiply (256 x 256 tiles on two SMs) and the one-CTA
+    # multiply (128 x 256 tiles) run the same leaf products with the same
+    # K order per element; both must be within tolerance of the oracle and
+    # of each other, under stored products and the fused epilogue, for the
+    # forward and both gradient layouts.
+    code = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, '.'); sys.path.insert(0, 'tests')
+from paper_1507_00687_gb300 import api, inputs
+M, K, N = 1280, 1024, 1536
+A = torch.from_numpy(inputs.uniform((M, K), -1, 1, seed=71)).float().cuda()
+B = torch.from_numpy(inputs.uniform((K, N), -1, 1, seed=72)).float().cuda()
+G = torch.from_numpy(inputs.uniform((M, N), -1, 1, seed=73)).float().cuda()
+out = {}
+for sched in ("pass_products", "pass_epilogue"):
+    for leaf in ("bf16x3", "bf16"):
+        p = api.Plan(["winograd"], leaf, sched)
+        out[f"{sched}_{leaf}"] = api.multiply(p, A, B).cpu().numpy()
+        dA, dB = api.multiply_backward(p, G, A, B)
+        out[f"{sched}_{leaf}_dA"] = dA.cpu().numpy()
+        out[f"{sched}_{leaf}_dB"] = dB.cpu().numpy()
+api.sync_status()
+np.savez(sys.argv[1], **out)
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for pairs in ("1", "0"):
+        f = str(tmp_path / f"c{pairs}.npz")
+        r = subprocess.run([sys.executable, "-c", code, f], cwd=root, env=dict(os.environ, FMM_TILE_PAIRS=pairs),
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stdout + r.stderr
+        res[pairs] = dict(np.load(f))
+    M, K, N = 1280, 1024, 1536
+    A = inputs.uniform((M, K), -1, 1, seed=71).astype(np.float32).astype(np.float64)
+    B = inputs.uniform((K, N), -1, 1, seed=72).astype(np.float32).astype(np.float64)
+    G = inputs.uniform((M, N), -1, 1, seed=73).astype(np.float32).astype(np.float64)
+    C, Gr = oracle_reference(A, B, ["winograd"])
+    for key in res["1"]:
+        leaf = "bf16x3" if "bf16x3" in key else "bf16"
+        if key.endswith("_dA") or key.endswith("_dB"):
+            continue
+        assert_within(res["1"][key], C, Gr, ["winograd"], K, leaf, "pairs " + key)
+        assert_within(res["0"][key], C, Gr, ["winograd"], K, leaf, "one CTA " + key)
+    # gradients: against the classical FP64 gradients with a norm-wise bound
+    gA, gB = G @ B.T, A.T @ G
+    for key in res["1"]:
+        if key.endswith("_dA") or key.endswith("_dB"):
+            ref = gA if key.endswith("_dA") else gB
+            scale = np.abs(ref).max()
+            tol = (2e-2 if "_bf16_" in key else 1e-3) * scale
+            for pairs in ("1", "0"):
+                assert np.abs(res[pairs][key] - ref).max() <= tol, (pairs, key)
+
+
+@pytest.mark.parametrize("names", [["winograd"], ["strassen", "winograd"], ["winograd", "classical121"]],
+                         ids=lambda n: "-".join(n))
+@pytest.mark.parametrize("leaf", ["bf16x3", "bf16", "fp16"])
+def test_accumulating_epilogue(api, names, leaf):
+    # FMM_SCHEDULE_PASS_ACCUMULATE on CTA pairs: every (leaf, tile) unit adds
+    # its unscaled W-weighted terms into C by atomic FP32 additions.  Scaled
+    # inputs with ragged sizes (leaf blocks of at least 256 rows), two runs:
+    # each within tolerance of the oracle's exact fast product (the
+    # tolerance counts t_max roundings for the C sums in any order), and
+    # integer inputs exact.
+    M, K, N = 1290, 1100, 1170
+    dt = "f16" if leaf == "fp16" else "f32"
+    A, B = inputs.diag_scaled_pair(M, K, N, seed=77, span=4.0 if leaf == "fp16" else 12.0)
+    Ad, Bd = to_dev(A, dt), to_dev(B, dt)
+    A64, B64 = dev_values(Ad), dev_values(Bd)
+    eA, d, eB = api.scale(Ad, Bd, "OI")
+    st = OS.pow2_repeated(A64, B64, "OI")
+    C, G = oracle_reference(A64, B64, names, st.eA, st.d, st.eB)
+    plan = api.Plan(names, leaf, "pass_accumulate")
+    runs = []
+    for _ in range(2):
+        got = dev_values(api.multiply(plan, Ad, Bd, eA, d, eB))
+        api.sync_status()
+        assert_within(got, C, G, names, K, leaf, f"accumulate {names} {leaf}")
+        runs.append(got)
+    Ai = inputs.integers((M, K), -4, 4, seed=5)
+    Bi = inputs.integers((K, N), -4, 4, seed=6)
+    got = dev_values(api.multiply(plan, to_dev(Ai, dt), to_dev(Bi, dt)))
+    api.sync_status()
+    assert np.array_equal(got, Ai @ Bi)
 
 
 # ---------------------------------------------------------------- schedules

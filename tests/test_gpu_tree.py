@@ -14,7 +14,9 @@ pytestmark = pytest.mark.gpu
 
 TREES = {"dalberto": TC.dalberto(), "fast323_nonuniform": TC.fast323_nonuniform(), "mixed_rank": TC.mixed_rank(),
          "fast323_then_rot1": ["F", ["F_r1"] * 15], "rot2_then_S": ["F_r2", ["S"] * 15]}
-SCHEDULES = ["load_stage", "pass_epilogue", "pass_products"]
+SCHEDULES = ["load_stage", "pass_epilogue", "pass_products", "pass_accumulate"]
+# schedules whose results are the same from run to run
+DETERMINISTIC = ["load_stage", "pass_epilogue", "pass_products"]
 
 
 @pytest.fixture(scope="module")
@@ -73,7 +75,7 @@ def test_tree_one_rule_per_level_matches_uniform_plan_bitwise(api):
     lib, _ = TC.two_level("Wg", ["S"] * 7)
     A = to_dev(inputs.uniform((300, 260), -1, 1, seed=3), "f32")
     B = to_dev(inputs.uniform((260, 330), -1, 1, seed=4), "f32")
-    for schedule in SCHEDULES:
+    for schedule in DETERMINISTIC:
         t = api.multiply(api.Plan.tree(lib, "bf16x3", schedule), A, B)
         u = api.multiply(api.Plan(["winograd", "strassen"], "bf16x3", schedule), A, B)
         api.sync_status()
