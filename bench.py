@@ -681,7 +681,10 @@ def main():
     mult_ms_per = mult_ms / max(1, mult_n)
     achieved = mma_flops / (mult_ms_per * 1e-3) / 1e12
     sched_used = "pass" if kern["combine"][1] > 0 else "load_stage"
-    kname = "direct_fmm_kernel" if sched_used == "pass" else "fused_fmm_kernel"
+    # the pass schedule's leaf blocks of at least 256 x 256 run on CTA pairs
+    bt_min = min(-(-n // info["pm"]), -(-n // info["pn"]))
+    pairs = os.environ.get("FMM_TILE_PAIRS", "1") != "0" and bt_min >= 256
+    kname = ("pair_fmm_kernel" if pairs else "direct_fmm_kernel") if sched_used == "pass" else "fused_fmm_kernel"
     # the bandwidth passes of the pass schedule, per step: the combination
     # of both operands (one launch for small operands, else one per
     # operand; each operand read once, R^L combined leaf blocks written:
@@ -693,7 +696,8 @@ def main():
     planes = 2 if args.leaf == "bf16x3" else 1
     R = info["leaves"]
     bt = -(-n // info["pm"])
-    tp_a, tp_b = -(-bt // 128) * 128, -(-bt // 256) * 256
+    tp_a = -(-bt // (256 if bt >= 256 else 128)) * (256 if bt >= 256 else 128)
+    tp_b = -(-bt // 256) * 256
     kp = -(-(-(-n // info["pk"])) // 64) * 64
     pass_bytes = 2 * n * n * 4 + planes * R * (tp_a + tp_b) * kp * 2
     if sched_used == "pass" and R > 1 and per_step >= 2:

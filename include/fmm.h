@@ -23,9 +23,9 @@
  *  - Exponent vectors are int32 device arrays: D_A = diag(2^eA) (length M),
  *    D = diag(2^d) (length K), D_B = diag(2^eB) (length N); any may be NULL
  *    (= all zeros).  The scaled operands A' = 2^-eA A 2^d and
- *    B' = 2^-d B 2^-eB are exact; fmm_multiply writes them into the
- *    caller's workspace in one bandwidth-bound pass and multiplies its
- *    output by 2^(eA+eB) in the epilogue of the fused kernel.
+ *    B' = 2^-d B 2^-eB are exact; fmm_multiply applies them while it
+ *    forms the operand combinations and multiplies C by 2^(eA+eB) when it
+ *    forms the output.
  *  - Every wait inside a kernel is bounded: FMM_WAIT_TIMEOUT_NS in the
  *    environment (read once per process; default 2 s) limits each one;
  *    past it the kernel stops cleanly and flags FMM_ERR_DEVICE_TIMEOUT.
@@ -381,13 +381,24 @@ fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t M, int64_t K, int64_t N, 
  * when exponents are given (Algs. 1-3: C = D_A (A' B') D_B).  A: M x K
  * (lda), B: K x N (ldb), element type in_dtype; C: M x N float32 (ldc),
  * overwritten.  M, K, N are zero-padded internally up to multiples of the
- * plan's granules (Sec. 3.2).  One kernel launch forms S_r and T_r in its
- * load stage, multiplies on the tensor cores and adds W-weighted products
- * into C in its epilogue; each output tile is owned by one CTA, so the
- * result is deterministic.  ws/ws_bytes: device workspace, 256-byte
- * aligned, of fmm_workspace_size bytes, used when an operand needs a
- * prepared copy (see fmm_workspace_size); FMM_ERR_WORKSPACE if one is needed
- * and the workspace is missing or too small.
+ * plan's granules (Sec. 3.2).  What runs depends on the plan's schedule
+ * (fmm_plan_set_schedule) and the workspace given:
+ *  - the pass schedule (the default whenever ws holds fmm_workspace_size
+ *    bytes): one launch forms every S_r and T_r (both operands, scaling
+ *    applied) into the workspace; one tensor-core launch forms the leaf
+ *    products (on CTA pairs with 256 x 256 tiles when the leaf blocks are
+ *    at least 256 x 256, else one CTA per 128 x 256 tile) and stores them;
+ *    one output pass forms C = sum w M_r, unscaled -- three launches (plus
+ *    the between-steps exponent kernels when that scaling is on); a
+ *    single-leaf plan adds its product into C in the multiply epilogue;
+ *  - the load-stage schedule: one launch forms S_r, T_r in the multiply
+ *    kernel's load stage and adds W-weighted products into C in its
+ *    epilogue (operands needing a prepared copy get one bandwidth pass).
+ * Results are deterministic (each C element summed by one thread in leaf
+ * order) except under FMM_SCHEDULE_PASS_ACCUMULATE.  ws/ws_bytes: device
+ * workspace, 256-byte aligned, of fmm_workspace_size bytes (NULL / 0 runs
+ * the load-stage schedule when no operand needs a copy); FMM_ERR_WORKSPACE
+ * if a needed workspace is missing or too small.
  */
 fmm_status fmm_multiply(fmm_plan_t plan, const void* A, int64_t lda, const void* B, int64_t ldb,
                         float* C, int64_t ldc, int64_t M, int64_t K, int64_t N, int in_dtype,
@@ -439,7 +450,10 @@ fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, con
                                 const int32_t* eB, void* stream);
 
 /*
- * Batches: many independent products of uneven shapes, each with its own
+ * Batches (the batched multiply of the call list: fmm_batch_create /
+ * fmm_batch_run / fmm_batch_destroy together are fmm_multiply_batched,
+ * split so that all host work and table uploads happen once and a run only
+ * launches): many independent products of uneven shapes, each with its own
  * plan (rule, recursion depth), run as one fixed sequence of launches over
  * all of them -- the batched scaling reductions, one combination pass, ONE
  * persistent tensor-core launch over every product's (leaf, tile) work

@@ -283,6 +283,17 @@ static int64_t products_bytes(int64_t Tx, int64_t Ty, int64_t ptx, int64_t pty, 
 // Leaf products on CTA pairs (256 x 256 tiles shared by two SMs) for the
 // pass schedule's 16-bit leaves when the leaf blocks are at least 256 x 256;
 // FMM_TILE_PAIRS=0 in the environment (read once) keeps the one-CTA kernel.
+// The streamed combination pass (bulk tensor copies through a ring of
+// stages) for FP32 sources of at most 2 x 2 blocks; FMM_COMBINE_STREAM=0 in
+// the environment (read once) keeps the unrolled one.
+static bool combine_stream_enabled() {
+  static bool on = [] {
+    const char* s = std::getenv("FMM_COMBINE_STREAM");
+    return !(s && std::atoi(s) == 0);
+  }();
+  return on;
+}
+
 static bool pair_tiles_enabled() {
   static bool on = [] {
     const char* s = std::getenv("FMM_TILE_PAIRS");
@@ -594,7 +605,15 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
     cb.between_sign = -1;
   }
   // B first: a scaling sequence that ends with a pass over B leaves it in L2
-  if (!cuda_ok(launch_combine_pair(cb, ca, st), "combination passes")) return FMM_ERR_CUDA;
+  cudaError_t ce = cudaErrorNotSupported;
+  if (combine_stream_enabled() && x.dtype == kF32 && y.dtype == kF32) {
+    CUtensorMap mx, my;
+    if (make_map(&mx, x.ptr, kF32, ca.rows, ca.cols, x.ld, 256, 8) &&
+        make_map(&my, y.ptr, kF32, cb.rows, cb.cols, y.ld, 256, 8))
+      ce = launch_combine_pair_stream(cb, my, ca, mx, timeout_ns(), status, st);
+  }
+  if (ce == cudaErrorNotSupported) ce = launch_combine_pair(cb, ca, st);
+  if (!cuda_ok(ce, "combination passes")) return FMM_ERR_CUDA;
   DirectArgs d;
   if (!direct_args(p, g, x, y, c, leaves, wa, wb, mbuf, status, &d)) return FMM_ERR_CUDA;
   if (accumulate) {

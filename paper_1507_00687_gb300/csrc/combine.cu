@@ -29,6 +29,7 @@
 
 #include "../../include/fmm.h"
 #include "device.cuh"
+#include "gemm_common.cuh"
 #include "kernels.h"
 
 namespace fmm {
@@ -1392,6 +1393,234 @@ cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st) {
     case kF32: return launch_dt<kF32>(a, grid, st);
     case kBF16: return launch_dt<kBF16>(a, grid, st);
     default: return launch_dt<kF16>(a, grid, st);
+  }
+}
+
+// ------------------------------------------------------------ streamed form
+// The unrolled combination (at most 2 x 2 FP32 source blocks) as a
+// persistent kernel that streams the input tiles with bulk tensor copies:
+// each CTA walks position tiles t = blockIdx.x, + gridDim.x, ... of both
+// operands (a0's tiles first), and one thread keeps kStreamStages tiles of
+// every block in flight through an mbarrier ring, so loads no longer wait
+// for the previous tile's stores.  Per tile the threads scale their own
+// elements in place (2^(re + ce), exactly as the unrolled form does), then
+// sum each leaf's terms in term order and store the rounded leaf values:
+// the same arithmetic, so the same results.  Every tile of a block lies
+// inside the block (b_rows, b_cols multiples of 8 and 256 unless the block
+// is the last one along that side, whose rows and columns past the source
+// read as zero from the tensor map).  Tiles are 8 rows x 256 columns, so
+// every source row piece is 1 KB and every output row piece 512 bytes of
+// contiguous memory.
+constexpr int kStreamStages = 3;
+constexpr int kStreamTR = 8, kStreamTC = 256;  // position tile: 8 rows x 256 columns (1 KB source rows)
+constexpr int kStreamBox = kStreamTR * kStreamTC;  // floats per block tile
+
+template <int NB>
+constexpr size_t stream_smem_fixed() {
+  return (size_t)kStreamStages * NB * kStreamBox * 4 + 64;
+}
+
+template <int FMT, int NRB, int NCB>
+__global__ void __launch_bounds__(256, 2) combine_stream_kernel(const __grid_constant__ CUtensorMap m0,
+                                                                const __grid_constant__ CUtensorMap m1,
+                                                                const __grid_constant__ CombineArgs a0,
+                                                                const __grid_constant__ CombineArgs a1, int64_t tiles0,
+                                                                int64_t tiles, int* status, uint64_t timeout_ns) {
+  constexpr int NB = NRB * NCB, TR = kStreamTR, TC = kStreamTC;
+  constexpr int kQ = TC / 4;                 // threads across a tile row (4 columns each)
+  constexpr int kRowsPer = 256 / kQ;         // rows covered by one pass of the CTA
+  constexpr int kPasses = TR / kRowsPer;     // rows per thread
+  extern __shared__ __align__(128) uint8_t sm[];
+  float4* stages = reinterpret_cast<float4*>(sm);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)kStreamStages * NB * kStreamBox * 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(full + kStreamStages);
+  int2* terms = reinterpret_cast<int2*>(sm + stream_smem_fixed<NB>());  // a0's terms, then a1's
+  const int nnz0 = (int)a0.t_nnz, nnz1 = (int)a1.t_nnz;
+  int* tstart = reinterpret_cast<int*>(terms + nnz0 + nnz1);        // a0's R0 + 1 starts, then a1's
+  const int R0 = (int)a0.num_leaves, R1 = (int)a1.num_leaves;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStreamStages; ++s) mbar_init(&full[s], 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  // term lists: (float4 offset of the term's block tile, coefficient bits)
+  auto load_terms = [&](const CombineArgs& a, int2* dst, int* ts, int nnz, int R) {
+    for (int i = threadIdx.x; i < nnz; i += 256) {
+      const int32_t blk = __ldg(a.t_blk + i);
+      const int bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
+      dst[i] = make_int2((a.t_rows ? bt * NCB + bk : bk * NCB + bt) * (kStreamBox / 4),
+                         __float_as_int(__ldg(a.t_coef + i)));
+    }
+    for (int i = threadIdx.x; i <= R; i += 256) ts[i] = __ldg(a.t_start + i);
+  };
+  load_terms(a0, terms, tstart, nnz0, R0);
+  load_terms(a1, terms + nnz0, tstart + R0 + 1, nnz1, R1);
+  __syncthreads();
+  // the sources' exponents (and a source written by the previous kernel)
+  // are read from here on
+  pdl_wait();
+  pdl_trigger();
+
+  auto issue = [&](int64_t t, int s) {
+    const bool second = t >= tiles0;
+    const CombineArgs& a = second ? a1 : a0;
+    const CUtensorMap* m = second ? &m1 : &m0;
+    const int64_t lt = second ? t - tiles0 : t, gx = a.p_cols / TC;
+    const int64_t r0 = (lt / gx) * TR, c0 = (lt % gx) * TC;
+    gemm::mbar_arrive_expect_tx(&full[s], (uint32_t)(NB * kStreamBox * 4));
+#pragma unroll
+    for (int rb = 0; rb < NRB; ++rb)
+#pragma unroll
+      for (int cb = 0; cb < NCB; ++cb)
+        gemm::tma_load_2d(stages + ((size_t)s * NB + rb * NCB + cb) * (kStreamBox / 4), m,
+                          (int32_t)(cb * a.b_cols + c0), (int32_t)(rb * a.b_rows + r0), &full[s]);
+  };
+  const int64_t G = gridDim.x;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kStreamStages - 1; ++i) {
+      const int64_t t = blockIdx.x + i * G;
+      if (t < tiles) issue(t, i);
+    }
+  const int tr = threadIdx.x / kQ, tq = threadIdx.x % kQ, tc = tq * 4;
+  const int me = tr * kQ + tq;  // float4 slot of row tr; row tr + kRowsPer * q at me + 256 q
+  int64_t issued_upto = blockIdx.x + (kStreamStages - 1) * G;  // first tile not yet issued
+  int i = 0;
+  for (int64_t t = blockIdx.x; t < tiles; t += G, ++i) {
+    const int s = i % kStreamStages;
+    const uint32_t ph = (uint32_t)(i / kStreamStages) & 1u;
+    if (threadIdx.x == 0) {
+      // the stage of tile i - 1 was released by the barrier that ended it
+      const int64_t tn = t + (kStreamStages - 1) * G;
+      if (tn < tiles) {
+        fence_proxy_async_smem();
+        issue(tn, (i + kStreamStages - 1) % kStreamStages);
+        issued_upto = tn + G;
+      }
+    }
+    const bool ok = mbar_wait_bounded(&full[s], ph, abort_flag, timeout_ns);
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+      break;
+    }
+    const bool second = t >= tiles0;
+    const CombineArgs& a = second ? a1 : a0;
+    const int2* tm = second ? terms + nnz0 : terms;
+    const int* ts = second ? tstart + R0 + 1 : tstart;
+    const int R = second ? R1 : R0;
+    const int64_t lt = second ? t - tiles0 : t, gx = a.p_cols / TC;
+    const int64_t r0 = (lt / gx) * TR, c0 = (lt % gx) * TC, lc = c0 + tc;
+    float4* tile4 = stages + (size_t)s * NB * (kStreamBox / 4);
+    // scale this thread's elements in place: 2^(rs re[row] + cs ce[col])
+    if (a.re || a.ce) {
+#pragma unroll
+      for (int cb = 0; cb < NCB; ++cb) {
+        const int64_t nc = min(a.b_cols, a.cols - cb * a.b_cols);
+        int ec[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          ec[j] = (a.ce && lc + j < nc) ? a.cs * __ldg(a.ce + cb * a.b_cols + lc + j) : 0;
+#pragma unroll
+        for (int rb = 0; rb < NRB; ++rb) {
+          const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows);
+#pragma unroll
+          for (int q = 0; q < kPasses; ++q) {
+            const int64_t lr = r0 + tr + kRowsPer * q;
+            const int er = (a.re && lr < nr) ? a.rs * __ldg(a.re + rb * a.b_rows + lr) : 0;
+            float4& v = tile4[(rb * NCB + cb) * (kStreamBox / 4) + me + 256 * q];
+            v = make_float4(scale_fast(v.x, er + ec[0]), scale_fast(v.y, er + ec[1]), scale_fast(v.z, er + ec[2]),
+                            scale_fast(v.w, er + ec[3]));
+          }
+        }
+      }
+    }
+    unsigned short* out = static_cast<unsigned short*>(a.out);
+    const int64_t leaf_stride = a.p_rows * a.p_cols;
+    const int64_t plane = (int64_t)R * leaf_stride;
+    unsigned short* orow = out + (r0 + tr) * a.p_cols + lc;
+    const int64_t qstride = (int64_t)kRowsPer * a.p_cols;
+    int k = 0;
+    for (int r = 0; r < R; ++r, orow += leaf_stride) {
+      const int k1 = ts[r + 1];
+      float acc[kPasses][4];
+#pragma unroll
+      for (int q = 0; q < kPasses; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+      for (; k < k1; ++k) {
+        const int2 term = tm[k];
+        const float coef = __int_as_float(term.y);
+#pragma unroll
+        for (int q = 0; q < kPasses; ++q) {
+          const float4 v = tile4[term.x + me + 256 * q];
+          acc[q][0] = fmaf(coef, v.x, acc[q][0]);
+          acc[q][1] = fmaf(coef, v.y, acc[q][1]);
+          acc[q][2] = fmaf(coef, v.z, acc[q][2]);
+          acc[q][3] = fmaf(coef, v.w, acc[q][3]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kPasses; ++q) store4<FMT>(orow + q * qstride, orow + q * qstride + plane, acc[q]);
+    }
+    __syncthreads();  // stage s is free again
+  }
+  // no copy may still be writing shared memory when the CTA exits (only
+  // after a timeout can one be outstanding): wait for each issued stage
+  if (threadIdx.x == 0) {
+    for (int64_t tt = blockIdx.x + (int64_t)i * G, j = i; tt < issued_upto && tt < tiles; tt += G, ++j) {
+      const uint64_t t0 = globaltimer_ns();
+      while (!mbar_try_wait(&full[j % kStreamStages], (uint32_t)(j / kStreamStages) & 1u) &&
+             globaltimer_ns() - t0 < 1000000000ull) {
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Whether the streamed form applies to one operand (see above).
+bool stream_ok(const CombineArgs& a) {
+  const int64_t nb = a.n_rb * a.n_cb;
+  return a.dtype == kF32 && a.n_rb <= 2 && a.n_cb <= 2 && !a.between_d && a.fmt != FMM_LEAF_E4M3B128 &&
+         a.p_rows % kStreamTR == 0 && a.p_cols % kStreamTC == 0 && (a.n_rb == 1 || a.b_rows % kStreamTR == 0) &&
+         (a.n_cb == 1 || a.b_cols % kStreamTC == 0) && a.b_rows <= a.p_rows && a.b_cols <= a.p_cols &&
+         (uintptr_t)a.src % 16 == 0 && (a.ld * 4) % 16 == 0 && (!a.ce || (uintptr_t)a.ce % 16 == 0) && nb >= 1 &&
+         a.num_leaves > 0 && a.rows < 0x7FFFFFFF && a.cols < 0x7FFFFFFF;
+}
+
+cudaError_t launch_combine_pair_stream(const CombineArgs& a0, const CUtensorMap& m0, const CombineArgs& a1,
+                                       const CUtensorMap& m1, uint64_t timeout_ns, int* status, cudaStream_t st) {
+  if (!stream_ok(a0) || !stream_ok(a1) || a0.fmt != a1.fmt || a0.n_rb != a1.n_rb || a0.n_cb != a1.n_cb)
+    return cudaErrorNotSupported;
+  const int64_t tiles0 = (a0.p_cols / kStreamTC) * (a0.p_rows / kStreamTR),
+                tiles = tiles0 + (a1.p_cols / kStreamTC) * (a1.p_rows / kStreamTR);
+  const size_t list = (size_t)(a0.t_nnz + a1.t_nnz) * 8 + (size_t)(a0.num_leaves + a1.num_leaves + 2) * 4;
+  if (tiles == 0 || list > 16384) return cudaErrorNotSupported;
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sms() * 2);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  KernelTimer timer("combine", st);
+  auto go = [&](auto fmt_tag, auto nrb_tag, auto ncb_tag) {
+    constexpr int FMT = decltype(fmt_tag)::value, NRB = decltype(nrb_tag)::value, NCB = decltype(ncb_tag)::value;
+    auto kern = combine_stream_kernel<FMT, NRB, NCB>;
+    const size_t smem = stream_smem_fixed<NRB * NCB>() + list;
+    static bool attr[64] = {};
+    if (!attr[dev]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+      attr[dev] = true;
+    }
+    return launch_pdl(kern, dim3((unsigned)grid), dim3(256), smem, st, m0, m1, a0, a1, tiles0, tiles, status,
+                      timeout_ns);
+  };
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  auto by_blocks = [&](auto fmt_tag) {
+    if (a0.n_rb == 2 && a0.n_cb == 2) return go(fmt_tag, I2(), I2());
+    if (a0.n_rb == 2) return go(fmt_tag, I2(), I1());
+    if (a0.n_cb == 2) return go(fmt_tag, I1(), I2());
+    return go(fmt_tag, I1(), I1());
+  };
+  switch (a0.fmt) {
+    case FMM_LEAF_BF16: return by_blocks(std::integral_constant<int, FMM_LEAF_BF16>());
+    case FMM_LEAF_F16: return by_blocks(std::integral_constant<int, FMM_LEAF_F16>());
+    default: return by_blocks(std::integral_constant<int, FMM_LEAF_BF16X3>());
   }
 }
 

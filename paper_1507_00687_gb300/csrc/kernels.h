@@ -192,6 +192,12 @@ cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st);
 // Both operands' combination passes, in one launch when both take the
 // unrolled small-block form, else as two launches (a0 first).
 cudaError_t launch_combine_pair(const CombineArgs& a0, const CombineArgs& a1, cudaStream_t st);
+// The same pair of passes streamed through bulk tensor copies (FP32 sources
+// of at most 2 x 2 blocks; m0, m1: tensor maps over the sources' memory,
+// 256 x 8 float boxes, no swizzle, zero fill); cudaErrorNotSupported when
+// the operands do not qualify (nothing launched).
+cudaError_t launch_combine_pair_stream(const CombineArgs& a0, const CUtensorMap& m0, const CombineArgs& a1,
+                                       const CUtensorMap& m1, uint64_t timeout_ns, int* status, cudaStream_t st);
 
 // Multiply kernel over combined operands (the pass schedule): each operand
 // is the 16-bit output of the combination pass, K-major ([plane][R][tp][kp],
