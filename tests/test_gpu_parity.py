@@ -427,12 +427,17 @@ np.savez(sys.argv[1], **out)
 """
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     res = {}
-    for pairs in ("1", "0"):
-        f = str(tmp_path / f"c{pairs}.npz")
-        r = subprocess.run([sys.executable, "-c", code, f], cwd=root, env=dict(os.environ, FMM_TILE_PAIRS=pairs),
+    for key, env in (("1", {"FMM_TILE_PAIRS": "1"}), ("0", {"FMM_TILE_PAIRS": "0"}),
+                     ("unstreamed", {"FMM_COMBINE_STREAM": "0"})):
+        f = str(tmp_path / f"c{key}.npz")
+        r = subprocess.run([sys.executable, "-c", code, f], cwd=root, env=dict(os.environ, **env),
                            capture_output=True, text=True, timeout=600)
         assert r.returncode == 0, r.stdout + r.stderr
-        res[pairs] = dict(np.load(f))
+        res[key] = dict(np.load(f))
+    # the streamed combination pass does the arithmetic of the unrolled
+    # one: the same values bit for bit
+    for key in res["1"]:
+        assert np.array_equal(res["1"][key], res["unstreamed"][key]), key
     M, K, N = 1280, 1024, 1536
     A = inputs.uniform((M, K), -1, 1, seed=71).astype(np.float32).astype(np.float64)
     B = inputs.uniform((K, N), -1, 1, seed=72).astype(np.float32).astype(np.float64)
