@@ -294,6 +294,42 @@ static bool combine_stream_enabled() {
   return on;
 }
 
+// Output pass of a first half overlapped with the second half's multiply
+// (CTA-pair products of at least two tile rows); FMM_OVERLAP=0 in the
+// environment (read once) keeps one multiply launch and one output pass.
+static bool overlap_enabled() {
+  static bool on = [] {
+    const char* s = std::getenv("FMM_OVERLAP");
+    return !(s && std::atoi(s) == 0);
+  }();
+  return on;
+}
+
+// A non-blocking stream per device for work that overlaps the caller's
+// stream, with the fork and join events (created on first use; the mutex
+// keeps each fork / join sequence of one call together).
+struct SideStream {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  std::mutex mu;
+};
+
+static SideStream* side_stream() {
+  static SideStream side[64];
+  static std::mutex init_mu;
+  int dev = 0;
+  if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice") || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(init_mu);
+  SideStream& s = side[dev];
+  if (!s.stream) {
+    if (!cuda_ok(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "side stream") ||
+        !cuda_ok(cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming), "side-stream event") ||
+        !cuda_ok(cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming), "side-stream event"))
+      return nullptr;
+  }
+  return &s;
+}
+
 static bool pair_tiles_enabled() {
   static bool on = [] {
     const char* s = std::getenv("FMM_TILE_PAIRS");
@@ -620,6 +656,43 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
     d.accumulate = 1;
     if (!cuda_ok(cudaMemset2DAsync(c.C, (size_t)c.ldc * 4, 0, (size_t)c.N * 4, (size_t)c.M, st), "C zero fill"))
       return FMM_ERR_CUDA;
+  }
+  // Measured on GB300: hiding half of the output pass pays only where the
+  // multiply is compute-bound (leaf K of at least 2048) and each half still
+  // fills the GPU for several waves (n = 8192: +7%); at n = 4096 (three
+  // waves per half) and for short leaf K (stored products compete with the
+  // output pass for DRAM) the single launch is faster.
+  const int64_t ntm = g.tp_a / 256;
+  const int64_t half_waves = ntm >= 2 ? (ntm / 2) * (g.tp_b / 256) * g.R / std::max(1, device_sm_count() / 2) : 0;
+  if (store_m && g.pair && !gather && ntm >= 2 && p->pm * p->pn <= 16 && g.R * 64 <= 48 * 1024 &&
+      half_waves >= 5 && g.kp >= 2048 && overlap_enabled()) {
+    // Two launches over the tile-row halves; the output pass of the first
+    // half runs on a side stream, beside the second half's multiply (one
+    // 256-thread CTA fits on each SM next to a pair CTA), then the second
+    // half's output pass; the caller's stream waits for both.
+    SideStream* side = side_stream();
+    if (!side) return FMM_ERR_CUDA;
+    const int64_t h = ntm / 2;
+    DirectArgs d1 = d, d2 = d;
+    d1.tm_begin = 0;
+    d1.tm_count = h;
+    d2.tm_begin = h;
+    d2.tm_count = ntm - h;
+    OutArgs o1 = out_args(p, g, c, leaves, mbuf), o2 = o1;
+    o1.r_begin = 0;
+    o1.r_end = h * 256;
+    o2.r_begin = h * 256;
+    std::lock_guard<std::mutex> lock(side->mu);
+    if (!cuda_ok(launch_pair_gemm(d1, p->leaf_format, st), "multiply launch (first half)") ||
+        !cuda_ok(cudaEventRecord(side->fork, st), "side-stream fork") ||
+        !cuda_ok(cudaStreamWaitEvent(side->stream, side->fork, 0), "side-stream fork") ||
+        !cuda_ok(launch_out_dense_slim(o1, side->stream), "output combination pass (first half)") ||
+        !cuda_ok(cudaEventRecord(side->join, side->stream), "side-stream join") ||
+        !cuda_ok(launch_pair_gemm(d2, p->leaf_format, st), "multiply launch (second half)") ||
+        !cuda_ok(launch_out_combine(o2, st), "output combination pass (second half)") ||
+        !cuda_ok(cudaStreamWaitEvent(st, side->join, 0), "side-stream join"))
+      return FMM_ERR_CUDA;
+    return FMM_OK;
   }
   if (!cuda_ok(g.pair ? launch_pair_gemm(d, p->leaf_format, st) : launch_direct_gemm(d, p->leaf_format, g.bn, st),
                "multiply launch"))

@@ -764,8 +764,8 @@ __global__ void __launch_bounds__(TR * 16) out_combine_kernel(const OutArgs a) {
 // shared-memory pass).  The C sums are unscaled once and stored.
 constexpr int kDenseBatch = 4;  // leaves whose loads are in flight together
 
-template <int NB, int TR, int TC>
-__global__ void __launch_bounds__(TR * TC / 4) out_dense_kernel(const OutArgs a) {
+template <int NB, int TR, int TC, int MINB = 1>
+__global__ void __launch_bounds__(TR * TC / 4, MINB) out_dense_kernel(const OutArgs a) {
   extern __shared__ float sW[];  // [num_leaves][NB]
   pdl_wait();
   pdl_trigger();
@@ -783,8 +783,8 @@ __global__ void __launch_bounds__(TR * TC / 4) out_dense_kernel(const OutArgs a)
   }
   __syncthreads();
   const int tr = threadIdx.x / (TC / 4), tq = threadIdx.x % (TC / 4);
-  const int64_t lr = (int64_t)blockIdx.y * TR + tr, lc = (int64_t)blockIdx.x * TC + tq * 4;
-  if (lr >= c.bm || lc >= c.bn) return;
+  const int64_t lr = a.r_begin + (int64_t)blockIdx.y * TR + tr, lc = (int64_t)blockIdx.x * TC + tq * 4;
+  if (lr >= (a.r_end ? min(a.r_end, c.bm) : c.bm) || lc >= c.bn) return;
   const float* mpos = a.mbuf + lr * a.tp_b + lc;
   const int64_t leaf_stride = a.tp_a * a.tp_b;
   float4 acc[NB];
@@ -1243,6 +1243,21 @@ cudaError_t launch_out_gather(const OutArgs& a, cudaStream_t st) {
   return launch_pdl(out_gather_kernel, dim3((unsigned)tiles, gy), dim3(kOutGatherRows * 16), 0, st, a);
 }
 
+cudaError_t launch_out_dense_slim(const OutArgs& a, cudaStream_t st) {
+  if (a.c_blocks > 16 || a.num_leaves * 16 * 4 > 48 * 1024 || a.c.bm > a.tp_a || a.c.bn > a.tp_b ||
+      a.tp_b % kTC != 0)
+    return cudaErrorNotSupported;
+  const int64_t rows = (a.r_end ? std::min(a.r_end, a.c.bm) : a.c.bm) - a.r_begin;
+  if (rows <= 0 || a.c.bn == 0) return cudaSuccess;
+  KernelTimer timer("combine", st);
+  constexpr int TR = 16, TC = kTC;  // 256 threads
+  const dim3 grid((unsigned)((a.c.bn + TC - 1) / TC), (unsigned)((rows + TR - 1) / TR));
+  const size_t smem = (size_t)a.num_leaves * 16 * 4;
+  if (a.c_blocks <= 4) return launch_pdl(out_dense_kernel<4, TR, TC, 3>, grid, dim3(TR * TC / 4), smem / 4, st, a);
+  if (a.c_blocks <= 9) return launch_pdl(out_dense_kernel<9, TR, TC, 3>, grid, dim3(TR * TC / 4), smem * 9 / 16, st, a);
+  return launch_pdl(out_dense_kernel<16, TR, TC, 3>, grid, dim3(TR * TC / 4), smem, st, a);
+}
+
 cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st) {
   if (a.c_blocks > kMaxOutBlocks || a.c.bm > a.tp_a || a.c.bn > a.tp_b || a.tp_b % kTC != 0)
     return cudaErrorInvalidValue;
@@ -1252,7 +1267,9 @@ cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st) {
     KernelTimer timer("combine", st);
     auto go = [&](auto nb_tag, auto tr_tag) {
       constexpr int NB = decltype(nb_tag)::value, TR = decltype(tr_tag)::value, TC = kTC;
-      const unsigned gy = (unsigned)((a.c.bm + TR - 1) / TR);
+      const int64_t rows = (a.r_end ? std::min(a.r_end, a.c.bm) : a.c.bm) - a.r_begin;
+      if (rows <= 0) return;
+      const unsigned gy = (unsigned)((rows + TR - 1) / TR);
       launch_pdl(out_dense_kernel<NB, TR, TC>, dim3((unsigned)((a.c.bn + TC - 1) / TC), gy), dim3(TR * TC / 4),
                  (size_t)a.num_leaves * NB * 4, st, a);
     };

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
   // Units of this pair: u = cluster id, + cluster count, ...; one 256 x 256
   // tile of one leaf (stored products) or one tile position with all its
   // leaves in leaf order (fused epilogue).
-  const int64_t ntn = args.tp_b / BN, ntiles = (args.tp_a / BM) * ntn;
+  const int64_t ntn = args.tp_b / BN, ntiles = (args.tm_count ? args.tm_count : args.tp_a / BM) * ntn;
   const bool per_leaf = args.mbuf || args.accumulate;  // units are (leaf, tile)
   const int64_t total_units = per_leaf ? ntiles * args.num_leaves : ntiles;
   const int64_t u0 = cluster_id_x(), ustep = cluster_count_x();
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
       c.leaf_end = args.num_leaves;
       tile = c.u;
     }
-    c.tm = tile / ntn;
+    c.tm = args.tm_begin + tile / ntn;
     c.tn = tile % ntn;
   };
   auto first = [&]() {
@@ -358,7 +358,8 @@ cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
     attr_set[dev] = true;
   }
   if (a.tp_a % BM != 0 || a.tp_b % BN != 0 || a.kp % C::BK != 0) return cudaErrorInvalidValue;
-  const int64_t ntiles = (a.tp_a / BM) * (a.tp_b / BN);
+  if (a.tm_count && a.tm_begin + a.tm_count > a.tp_a / BM) return cudaErrorInvalidValue;
+  const int64_t ntiles = (a.tm_count ? a.tm_count : a.tp_a / BM) * (a.tp_b / BN);
   if (ntiles == 0 || a.num_leaves == 0) return cudaSuccess;
   const int64_t units = (a.mbuf || a.accumulate) ? ntiles * a.num_leaves : ntiles;
   cudaLaunchConfig_t cfg = {};

@@ -220,6 +220,9 @@ struct DirectArgs {
   // Test of the timeout path (FMM_TEST_STALL set in the environment): the
   // epilogue first waits, bounded, on a barrier that nothing arrives at.
   int stall_test;
+  // CTA-pair kernel: only the tile rows tm_begin .. tm_begin + tm_count - 1
+  // (tm_count 0: all), so that a product can run as two launches
+  int64_t tm_begin, tm_count;
 };
 
 // Output combination pass (third line of Eq. 4.4) over stored leaf products:
@@ -241,9 +244,17 @@ struct OutArgs {
   const int32_t* g_start;  // the C terms grouped by C block (Plan::gather_off), or NULL
   const int32_t* g_leaf;
   const float* g_coef;
+  // register-accumulator pass: only leaf-block rows [r_begin, r_end) (r_end
+  // 0: up to c.bm)
+  int64_t r_begin, r_end;
 };
 constexpr int kMaxOutBlocks = 96;
 cudaError_t launch_out_combine(const OutArgs& a, cudaStream_t st);
+// The register-accumulator output pass (at most 16 C blocks) in CTAs of 256
+// threads and at most 85 registers each, so that one fits on an SM beside
+// a CTA of the CTA-pair multiply kernel and the two run together;
+// cudaErrorNotSupported when the plan does not qualify.
+cudaError_t launch_out_dense_slim(const OutArgs& a, cudaStream_t st);
 // The output pass for plans with more than kMaxOutBlocks C blocks: each CTA
 // forms one position tile of one C block from that block's term list.
 cudaError_t launch_out_gather(const OutArgs& a, cudaStream_t st);

@@ -492,6 +492,37 @@ def test_accumulating_epilogue(api, names, leaf):
     assert np.array_equal(got, Ai @ Bi)
 
 
+def test_overlapped_output_pass_bitwise(api, tmp_path):
+    # A product large enough for the overlapped form (two multiply launches
+    # over tile-row halves, the first half's output pass on a side stream)
+    # gives the single launch's values bit for bit, forward and backward.
+    code = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, '.')
+from paper_1507_00687_gb300 import api, inputs
+M, K, N = 8192, 4096, 8192
+A = torch.from_numpy(inputs.uniform((M, K), -1, 1, seed=81)).cuda().to(torch.bfloat16)
+B = torch.from_numpy(inputs.uniform((K, N), -1, 1, seed=82)).cuda().to(torch.bfloat16)
+p = api.Plan(["winograd"], "bf16")
+C = api.multiply(p, A, B)
+eA, d, eB = api.scale(A, B, "OI")
+Cs = api.multiply(p, A, B, eA, d, eB)
+api.sync_status()
+np.savez(sys.argv[1], C=C.cpu().numpy(), Cs=Cs.cpu().numpy())
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for ov in ("1", "0"):
+        f = str(tmp_path / f"o{ov}.npz")
+        r = subprocess.run([sys.executable, "-c", code, f], cwd=root, env=dict(os.environ, FMM_OVERLAP=ov),
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stdout + r.stderr
+        res[ov] = dict(np.load(f))
+    for key in ("C", "Cs"):
+        assert np.isfinite(res["1"][key]).all()
+        assert np.array_equal(res["1"][key], res["0"][key]), key
+
+
 # ---------------------------------------------------------------- schedules
 
 def test_schedule_workspace_rules(api):
