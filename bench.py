@@ -189,6 +189,48 @@ def linear_layer_workload(api, torch, reps: int = 10) -> dict:
             "forward_max_abs_err_sampled_rows": err}
 
 
+# ---------------------------------------------------------------- fast vs classical at n = 8192
+
+def crossover_workload(api, inputs, torch, args, n: int = 8192, reps: int = 10) -> dict:
+    """The benchmark's configuration (Winograd one level, bf16 hi+lo leaves,
+    FP32 inputs D1 X D2 / D3 Y D4, outside-inside scaling) at n = 8192 beside
+    the classical product through the same kernels and scaling: the fast
+    step saves 1/8 of the tensor-core work, whose share grows with n, while
+    its extra bandwidth passes grow with n^2.  Effective TFLOP/s (2n^3/t)
+    and the max-abs error against an FP64 product of a row sample."""
+    A64, B64 = inputs.diag_scaled_pair(n, n, n, seed=SEED + 7)
+    A = torch.from_numpy(A64).float().cuda()
+    B = torch.from_numpy(B64).float().cuda()
+    C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    rows = torch.arange(0, n, 128, device="cuda")
+    ref = A[rows].double() @ B.double()
+    out = {}
+    for name, rules in (("fast", [args.rule]), ("classical", [])):
+        plan = api.Plan(rules, args.leaf, args.schedule)
+
+        def step():
+            eA, d, eB = api.scale(A, B, args.scaling)
+            api.multiply(plan, A, B, eA, d, eB, out=C)
+
+        step()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(reps):
+            step()
+        ev[1].record()
+        torch.cuda.synchronize()
+        api.sync_status()
+        ms = ev[0].elapsed_time(ev[1]) / reps
+        out[name] = {"tflops": 2.0 * n**3 / (ms * 1e-3) / 1e12, "ms_per_step": ms,
+                     "max_abs_err_sampled_rows": float((C[rows].double() - ref).abs().max())}
+        del plan
+    del A, B, C, ref
+    torch.cuda.empty_cache()
+    out["config"] = f"{args.rule} L=1 vs classical, n={n}, FP32 data, {args.leaf} leaves, scaling {args.scaling}"
+    return out
+
+
 # ---------------------------------------------------------------- precision sweep
 
 def precision_sweep(api, torch, reps: int = 5) -> dict:
@@ -654,6 +696,8 @@ def main():
                 extras["fast_L2"] = {"unavailable": str(e)}
         del plan0
     del ref, C_fast
+    if not args.no_extras:
+        extras["headline_n8192"] = crossover_workload(api, inputs, torch, args)
     if not args.no_extras and args.batch > 0:
         extras["batched"] = batched_workload(api, inputs, torch, args.batch)
     if not args.no_extras:
@@ -764,6 +808,19 @@ def main():
     out.update(extras)
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(args)
+    # the comparisons in one short record at the end of the line
+    summ = {"fast_scaled": {"tflops": value, "max_abs_err": err_fast}}
+    for k in ("classical_same_kernel", "fast_no_scaling", "fast_accumulate", "fast_L2"):
+        if k in extras and "tflops" in extras[k]:
+            summ[k] = {"tflops": extras[k]["tflops"], "max_abs_err": extras[k].get("max_abs_err")}
+    if "headline_n8192" in extras:
+        summ["n8192"] = {k: v["tflops"] for k, v in extras["headline_n8192"].items() if isinstance(v, dict)}
+    if "batched" in extras and "tflops" in extras["batched"]:
+        summ["batched_tflops"] = extras["batched"]["tflops"]
+    if "autograd_linear" in extras:
+        summ["linear_fwd_bwd_tflops"] = [extras["autograd_linear"]["forward_tflops"],
+                                         extras["autograd_linear"]["backward_tflops"]]
+    out["summary"] = summ
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
