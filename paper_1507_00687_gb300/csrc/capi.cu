@@ -373,7 +373,7 @@ struct PassGeom {
   int64_t R, bt_a, bt_b, bk, tp_a, tp_b, kp, bytes_a, bytes_b, bytes_m;
 };
 
-static PassGeom pass_geom(const Plan* p, const Source& x, const Source& y, int bn) {
+static PassGeom pass_geom(const Plan* p, const Source& x, const Source& y, int bn, bool force_pair = false) {
   PassGeom g;
   g.planes = p->leaf_format == FMM_LEAF_BF16X3 ? 2 : 1;
   g.R = p->leaves;
@@ -382,6 +382,10 @@ static PassGeom pass_geom(const Plan* p, const Source& x, const Source& y, int b
   g.bk = ceil_div(x.Kd, x.pk);
   g.bn = bn > 0 ? bn : pass_tile_n(g.bt_b);
   g.pair = bn <= 0 && g.bn == 256 && g.bt_a >= 256 && p->leaf_format != FMM_LEAF_E4M3B128 && pair_tiles_enabled();
+  if (force_pair) {  // batches on CTA pairs: 256 x 256 tiles whatever the block size
+    g.bn = 256;
+    g.pair = true;
+  }
   g.tp_a = round_up(g.bt_a, g.pair ? 256 : 128);
   g.tp_b = round_up(g.bt_b, g.bn);
   g.kp = round_up(g.bk, 64);
@@ -865,6 +869,24 @@ static Source batch_source_b(const fmm_problem& q, const Plan* p, int dt, const 
   return Source{q.B, q.ldb, dt, false, q.N, q.K, p->pn, p->pk, d, -1, eB, -1};
 }
 
+// A batch entry whose plan is the classical product (one leaf, one term per
+// side) with bf16 inputs and bf16 leaves: the multiply reads the caller's A
+// and B through tensor maps, with no scaling reductions and no conversion
+// pass.  Power-of-two diagonal scaling cancels exactly for it: the inside
+// factor 2^d_k cancels between A'_ik and B'_kj, and the outside factor
+// 2^-(eA_i + eB_j) is common to every product of C_ij, so the rounded sums
+// scaled and unscaled differ by that exact power of two and the unscaled C
+// is the scaled path's bit for bit whenever no scaled operand or partial
+// sum leaves the normal range.  bf16 has the exponent range of FP32, so
+// that holds but at the extremes; fp16 (normal range down to 2^-14 only)
+// loses or gains bits when small entries are shifted, so fp16 entries keep
+// the scaled path.
+static bool batch_direct(const fmm_problem& q, const Plan* p, int dt) {
+  const bool same = dt == FMM_DT_BF16 && p->leaf_format == FMM_LEAF_BF16;
+  return pair_tiles_enabled() && p->leaves == 1 && p->pm == 1 && p->pk == 1 && p->pn == 1 && same &&
+         (uintptr_t)q.A % 16 == 0 && (uintptr_t)q.B % 16 == 0 && (q.lda * 2) % 16 == 0 && (q.ldb * 2) % 16 == 0;
+}
+
 static fmm_status batch_layout(const fmm_problem* probs, int count, int dt, BatchLayout* L) {
   size_t at = 0;
   const size_t cnt = (size_t)count;
@@ -904,7 +926,9 @@ static fmm_status batch_layout(const fmm_problem* probs, int count, int dt, Batc
     const Plan* p = reinterpret_cast<const Plan*>(probs[i].plan);
     const Source x = batch_source_a(probs[i], p, dt, nullptr, nullptr);
     const Source y = batch_source_b(probs[i], p, dt, nullptr, nullptr);
-    const PassGeom g = pass_geom(p, x, y, kBatchTileN);
+    const bool pairs = pair_tiles_enabled();
+    PassGeom g = pass_geom(p, x, y, kBatchTileN, pairs);
+    if (pairs && batch_direct(probs[i], p, dt)) g.bytes_a = g.bytes_b = g.bytes_m = 0;
     L->geom[(size_t)i] = g;
     L->off_a[(size_t)i] = at;
     at += (size_t)g.bytes_a;
@@ -949,6 +973,8 @@ struct Batch {
   int comb_tr = 32, out_tr = 32;
   size_t comb_smem = 0, out_smem = 0;
   DirectArgs layout;  // status, wait limit, operand layouts
+  bool pairs = false;   // the multiply runs on CTA pairs (256 x 256 tiles)
+  bool any_scaled = true;  // some entry's scaling reductions run
 };
 
 static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
@@ -973,18 +999,22 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
   std::vector<OutArgs> out;
   std::vector<int64_t> out_start(1, 0);
   std::vector<int64_t> unit_cost((size_t)count), units((size_t)count);
+  b->pairs = pair_tiles_enabled();
+  const int64_t tm_rows = b->pairs ? 256 : 128, tn_cols = b->pairs ? 256 : kBatchTileN;
+  const int64_t workers = b->pairs ? device_sm_count() / 2 : device_sm_count();
   int64_t max_nb = 1, max_cb = 1, tiles_all = 0;
   for (int i = 0; i < count; ++i) {
     const Plan* p = reinterpret_cast<const Plan*>(probs[i].plan);
     if (p->leaves > 1) max_nb = std::max(max_nb, std::max(p->pm * p->pk, p->pk * p->pn));
     max_cb = std::max(max_cb, p->pm * p->pn);
     const PassGeom& g = L.geom[(size_t)i];
-    tiles_all += (g.tp_a / 128) * (g.tp_b / kBatchTileN);
+    tiles_all += (g.tp_a / tm_rows) * (g.tp_b / tn_cols);
   }
   // Output combination in the multiply epilogue (each tile of each product
   // a unit covering all its leaves) when the batch has tiles enough to
   // occupy the GPU; else stored leaf products for the many-leaf plans.
-  const bool fused = tiles_all >= 2 * (int64_t)device_sm_count();
+  const bool fused = tiles_all >= 2 * workers;
+  b->any_scaled = false;
   b->comb_tr = combine_batched_rows(max_nb);
   b->out_tr = out_batched_rows(max_cb);
   int64_t om = 0, ok_ = 0, on = 0;
@@ -1000,6 +1030,8 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
     ok_ += q.K;
     on += q.N;
     const size_t u = (size_t)i;
+    const bool direct = b->pairs && batch_direct(q, p, dt);
+    b->any_scaled = b->any_scaled || !direct;
     // scaling reductions: rows(A) -> eA, columns(A) -> d, columns(B) -> eB, rows(B) -> d
     const int vec_a = vec_aligned_host(q.A, q.lda, dt), vec_b = vec_aligned_host(q.B, q.ldb, dt);
     red[0][u] = ReduceArgs{q.A, q.M, q.K, q.lda, nullptr, +1, eA, vec_a, 0, 0};
@@ -1007,10 +1039,11 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
                            ceil_div(q.K, kBatchColSpan)};
     red[2][u] = ReduceArgs{q.B, q.K, q.N, q.ldb, nullptr, -1, eB, vec_b, kBatchColRows, ceil_div(q.N, kBatchColSpan)};
     red[3][u] = ReduceArgs{q.B, q.K, q.N, q.ldb, o_step ? eB : nullptr, -1, d, vec_b, 0, 0};
-    red_start[0][u + 1] = red_start[0][u] + q.M;
-    red_start[1][u + 1] = red_start[1][u] + red[1][u].gx * ceil_div(q.M, kBatchColRows);
-    red_start[2][u + 1] = red_start[2][u] + red[2][u].gx * ceil_div(q.K, kBatchColRows);
-    red_start[3][u + 1] = red_start[3][u] + q.K;
+    // direct entries take no part in the reductions (empty ranges)
+    red_start[0][u + 1] = red_start[0][u] + (direct ? 0 : q.M);
+    red_start[1][u + 1] = red_start[1][u] + (direct ? 0 : red[1][u].gx * ceil_div(q.M, kBatchColRows));
+    red_start[2][u + 1] = red_start[2][u] + (direct ? 0 : red[2][u].gx * ceil_div(q.K, kBatchColRows));
+    red_start[3][u + 1] = red_start[3][u] + (direct ? 0 : q.K);
     // passes and multiply
     const Source x = batch_source_a(q, p, dt, o_step ? eA : nullptr, i_step ? d : nullptr);
     const Source y = batch_source_b(q, p, dt, i_step ? d : nullptr, o_step ? eB : nullptr);
@@ -1020,7 +1053,7 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
     float* mbuf = (fused || g.R == 1) ? nullptr : reinterpret_cast<float*>(ws + L.off_m[u]);
     comb[2 * u] = combine_args(p, g, x, 0, leaves, wa);
     comb[2 * u + 1] = combine_args(p, g, y, 1, leaves, wb);
-    for (int sd = 0; sd < 2; ++sd) {
+    for (int sd = 0; sd < 2 && !direct; ++sd) {
       const CombineArgs& ca = comb[2 * u + (size_t)sd];
       if (ca.n_rb == 1 && ca.n_cb == 1 && g.R == 1 && ca.t_nnz == 1) {
         // one term of one block: a plain scaled conversion
@@ -1039,11 +1072,17 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
     c.N = q.N;
     c.bm = ceil_div(q.M, p->pm);
     c.bn = ceil_div(q.N, p->pn);
-    c.eA = o_step ? eA : nullptr;
-    c.eB = o_step ? eB : nullptr;
+    c.eA = (o_step && !direct) ? eA : nullptr;
+    c.eB = (o_step && !direct) ? eB : nullptr;
     c.vec_ok = ((uintptr_t)q.C % 16 == 0) && (q.ldc % 4 == 0) && (c.bn % 4 == 0) ? 1 : 0;
     if (!direct_args(p, g, x, y, c, leaves, wa, wb, mbuf, b->status, &dir[u])) return FMM_ERR_CUDA;
-    const int64_t tiles = (g.tp_a / 128) * (g.tp_b / kBatchTileN);
+    if (direct) {
+      // the caller's matrices themselves: A K-major (M x K), B MN-major (K x N)
+      if (!make_map_sw(&dir[u].map_a, q.A, false, q.M, q.K, q.lda, 64, 128) ||
+          !make_map_sw(&dir[u].map_b, q.B, false, q.K, q.N, q.ldb, 64, 64))
+        return FMM_ERR_CUDA;
+    }
+    const int64_t tiles = (g.tp_a / tm_rows) * (g.tp_b / tn_cols);
     units[u] = mbuf ? g.R * tiles : tiles;
     unit_cost[u] = (mbuf ? 1 : g.R) * (g.kp / 64);
     if (mbuf) {
@@ -1110,7 +1149,7 @@ static fmm_status batch_run(const Batch* b, cudaStream_t st) {
   int* eB_all = d_all + L.sum_k;
   auto red = [&](int k) { return reinterpret_cast<const ReduceArgs*>(ws + L.off_red[k]); };
   auto red_start = [&](int k) { return reinterpret_cast<const int64_t*>(ws + L.off_red_start[k]); };
-  const bool o_step = b->steps & 1, i_step = b->steps & 2;
+  const bool o_step = (b->steps & 1) && b->any_scaled, i_step = (b->steps & 2) && b->any_scaled;
   const int n = b->count;
   if (o_step && i_step) {
     // rows(A) -> eA; columns(2^-eA A) -> d; columns(B) -> eB; rows(2^-eB B) with d -> d
@@ -1148,9 +1187,12 @@ static fmm_status batch_run(const Batch* b, cudaStream_t st) {
       !cuda_ok(launch_convert_batched(comb + b->comb_count, reinterpret_cast<const int64_t*>(ws + L.off_copy_start),
                                       b->copy_count, b->copy_total, b->dt, b->fmt, st),
                "batch conversion pass") ||
-      !cuda_ok(launch_direct_gemm_batched(b->layout, reinterpret_cast<const DirectArgs*>(ws + L.off_direct),
-                                          reinterpret_cast<const int64_t*>(ws + L.off_unit_start), n, b->unit_total,
-                                          b->fmt, kBatchTileN, st),
+      !cuda_ok(b->pairs ? launch_pair_gemm_batched(b->layout, reinterpret_cast<const DirectArgs*>(ws + L.off_direct),
+                                                   reinterpret_cast<const int64_t*>(ws + L.off_unit_start), n,
+                                                   b->unit_total, b->fmt, st)
+                        : launch_direct_gemm_batched(b->layout, reinterpret_cast<const DirectArgs*>(ws + L.off_direct),
+                                                     reinterpret_cast<const int64_t*>(ws + L.off_unit_start), n,
+                                                     b->unit_total, b->fmt, kBatchTileN, st),
                "batch multiply") ||
       !cuda_ok(launch_out_combine_batched(reinterpret_cast<const OutArgs*>(ws + L.off_out),
                                           reinterpret_cast<const int64_t*>(ws + L.off_out_start), b->out_count,

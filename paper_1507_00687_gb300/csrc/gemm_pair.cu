@@ -61,7 +61,8 @@ struct Cfg {
   static constexpr int kStages = (212 * 1024) / kStage > 8 ? 8 : (212 * 1024) / kStage;
   static constexpr int kTmemCols = 2 * BN;
   static constexpr int kBarBytes = 256;
-  static constexpr int kSmem = kStages * kStage + kBarBytes + 1024;  // + alignment slack
+  static constexpr int kUnitCache = 2048;  // batch unit table entries kept in shared memory
+  static constexpr int kSmem = kStages * kStage + kBarBytes + kUnitCache * 8 + 1024;  // + alignment slack
 };
 
 __device__ __forceinline__ uint32_t cluster_id_x() {
@@ -94,8 +95,32 @@ __device__ __forceinline__ uint64_t tile_desc(uint32_t saddr, int k16) {
   else return smem_desc_sw128(saddr + k16 * 32);
 }
 
+// What one launch covers: one problem (`one`), or, when `tab` is set, the
+// `count` problems of a batch (device table, one DirectArgs each, tensor
+// maps included) whose units are numbered consecutively: units of problem
+// p are [unit_start[p], unit_start[p + 1]).  `one` also gives the status
+// word, the wait limit and the stall test for both forms.
+struct PairLaunch {
+  DirectArgs one;
+  const DirectArgs* tab;
+  const int64_t* unit_start;
+  int count;
+  int64_t total_units;
+};
+
+__device__ __forceinline__ int find_unit_problem(const int64_t* start, int count, int64_t u) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <int FMT, bool A_MN, bool B_MN, int EPI>
-__global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __grid_constant__ DirectArgs args) {
+__global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __grid_constant__ PairLaunch launch) {
+  const DirectArgs& args = launch.one;
   constexpr int kMmaWarp = EPI, kTmaWarp = EPI + 1;
   using C = Cfg<FMT>;
   constexpr int BK = C::BK;
@@ -110,6 +135,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
   uint64_t* never = drain + 1;  // no thread ever arrives here (timeout-path test)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int64_t* ustart = reinterpret_cast<int64_t*>(smem + C::kStages * C::kStage + C::kBarBytes);
 
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
@@ -143,35 +169,63 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
   // the combined operands of the previous kernel are read from here on
   pdl_wait();
   pdl_trigger();
+  // a batch's unit numbering, in shared memory when it fits
+  const bool batched = launch.tab != nullptr;
+  const bool ucached = batched && launch.count + 1 <= C::kUnitCache;
+  if (ucached)
+    for (int i = threadIdx.x; i <= launch.count; i += blockDim.x) ustart[i] = __ldg(launch.unit_start + i);
+  __syncthreads();
 
   // Units of this pair: u = cluster id, + cluster count, ...; one 256 x 256
   // tile of one leaf (stored products) or one tile position with all its
   // leaves in leaf order (fused epilogue).
-  const int64_t ntn = args.tp_b / BN, ntiles = (args.tm_count ? args.tm_count : args.tp_a / BM) * ntn;
-  const bool per_leaf = args.mbuf || args.accumulate;  // units are (leaf, tile)
-  const int64_t total_units = per_leaf ? ntiles * args.num_leaves : ntiles;
+  auto units_of = [&](const DirectArgs& a) {
+    const int64_t nt = (a.tm_count ? a.tm_count : a.tp_a / BM) * (a.tp_b / BN);
+    return (a.mbuf || a.accumulate) ? nt * a.num_leaves : nt;
+  };
+  const int64_t total_units = batched ? launch.total_units : units_of(args);
   const int64_t u0 = cluster_id_x(), ustep = cluster_count_x();
   struct Cursor {
-    int64_t u, leaf, leaf_end, tm, tn;
+    int64_t u, leaf, leaf_end, tm, tn, kt;
+    const DirectArgs* a;
+    int p;  // batch: problem of unit u (each role walks its units in increasing order)
   };
   auto decode = [&](Cursor& c) {
     if (c.u >= total_units) return;
+    int64_t local;
+    if (batched) {
+      if (ucached) {
+        while (c.p + 1 < launch.count && ustart[c.p + 1] <= c.u) ++c.p;
+        local = c.u - ustart[c.p];
+      } else {
+        c.p = find_unit_problem(launch.unit_start, launch.count, c.u);
+        local = c.u - __ldg(launch.unit_start + c.p);
+      }
+      c.a = launch.tab + c.p;
+    } else {
+      c.a = &args;
+      local = c.u;
+    }
+    const DirectArgs& a = *c.a;
+    const int64_t ntn = a.tp_b / BN, ntiles = (a.tm_count ? a.tm_count : a.tp_a / BM) * ntn;
     int64_t tile;
-    if (per_leaf) {
-      c.leaf = c.u / ntiles;
+    if (a.mbuf || a.accumulate) {  // units are (leaf, tile)
+      c.leaf = local / ntiles;
       c.leaf_end = c.leaf + 1;
-      tile = c.u % ntiles;
+      tile = local % ntiles;
     } else {
       c.leaf = 0;
-      c.leaf_end = args.num_leaves;
-      tile = c.u;
+      c.leaf_end = a.num_leaves;
+      tile = local;
     }
-    c.tm = args.tm_begin + tile / ntn;
+    c.tm = a.tm_begin + tile / ntn;
     c.tn = tile % ntn;
+    c.kt = a.kp / BK;
   };
   auto first = [&]() {
     Cursor c;
     c.u = u0;
+    c.p = 0;
     decode(c);
     return c;
   };
@@ -181,8 +235,6 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
       decode(c);
     }
   };
-  const int64_t KT = args.kp / BK;
-  const int64_t NL = args.num_leaves;
 
   if (warp == kTmaWarp) {
     if (lane == 0) {
@@ -193,7 +245,9 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
       bool ok = true;
       uint32_t armed = 0, armed_parity = 0;  // leader: per stage, expecting bytes, parity it completes
       for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
-        for (int64_t kt = 0; kt < KT && ok; ++kt) {
+        const DirectArgs& a = *w.a;
+        const int64_t NL = a.num_leaves;
+        for (int64_t kt = 0; kt < w.kt && ok; ++kt) {
           if (!mbar_wait_bounded_cluster(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns)) {
             ok = false;
             break;
@@ -202,12 +256,12 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
           const uint32_t fb = full0 + 8u * (uint32_t)stage;
           if (leader) mbar_arrive_expect_tx(&full[stage], 2u * (uint32_t)C::kStage);
           const int64_t k0 = kt * BK, ta = w.tm * BM + rank * HM, tb = w.tn * BN + rank * HN;
-          load_half<A_MN, BK>(st, &args.map_a, HM, w.leaf, args.tp_a, args.kp, ta, k0, fb);
-          load_half<B_MN, BK>(st + C::kSplit * C::kATile, &args.map_b, HN, w.leaf, args.tp_b, args.kp, tb, k0, fb);
+          load_half<A_MN, BK>(st, &a.map_a, HM, w.leaf, a.tp_a, a.kp, ta, k0, fb);
+          load_half<B_MN, BK>(st + C::kSplit * C::kATile, &a.map_b, HN, w.leaf, a.tp_b, a.kp, tb, k0, fb);
           if constexpr (C::kSplit == 2) {
-            load_half<A_MN, BK>(st + C::kATile, &args.map_a, HM, NL + w.leaf, args.tp_a, args.kp, ta, k0, fb);
-            load_half<B_MN, BK>(st + 2 * C::kATile + C::kBTile, &args.map_b, HN, NL + w.leaf, args.tp_b, args.kp,
-                                tb, k0, fb);
+            load_half<A_MN, BK>(st + C::kATile, &a.map_a, HM, NL + w.leaf, a.tp_a, a.kp, ta, k0, fb);
+            load_half<B_MN, BK>(st + 2 * C::kATile + C::kBTile, &a.map_b, HN, NL + w.leaf, a.tp_b, a.kp, tb, k0,
+                                fb);
           }
           if (leader) {
             armed |= 1u << stage;
@@ -248,7 +302,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
         }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + buf * BN;
-        for (int64_t kt = 0; kt < KT; ++kt) {
+        for (int64_t kt = 0; kt < w.kt; ++kt) {
           if (!mbar_wait_bounded_cluster(&full[stage], phase, abort_flag, args.timeout_ns)) {
             ok = false;
             break;
@@ -297,14 +351,15 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
     const int row = (int)rank * HM + quarter * 32 + lane;  // tile row of this thread (TMEM lane = row mod 128)
     const uint32_t tempty0 = mapa_shared(smem_u32(&tempty[0]), 0u);
     for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
+      const DirectArgs& a = *w.a;
       const int64_t leaf = w.leaf, tn = w.tn;
       const int64_t ml = w.tm * BM + row;
       const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
       ok = __all_sync(0xffffffffu, mbar_wait_bounded_cluster(&tfull[buf], aph, abort_flag, args.timeout_ns));
       if (!ok) break;
       tc_fence_after();
-      const LeafDesc* L = args.leaves + leaf;
-      float* mrow = args.mbuf ? args.mbuf + (leaf * args.tp_a + ml) * args.tp_b + tn * BN : nullptr;
+      const LeafDesc* L = a.leaves + leaf;
+      float* mrow = a.mbuf ? a.mbuf + (leaf * a.tp_a + ml) * a.tp_b + tn * BN : nullptr;
 #pragma unroll 1
       for (int cc = half * kChunks; cc < (half + 1) * kChunks; ++cc) {
         uint32_t r[32];
@@ -314,9 +369,9 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
           for (int q = 0; q < 8; ++q)
             *reinterpret_cast<uint4*>(mrow + cc * 32 + 4 * q) =
                 make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-        } else if (ml < args.c.bm) {
-          if (args.accumulate) epi_chunk_red(args.c, L, ml, tn * BN + cc * 32, r);
-          else epi_chunk(args.c, L, ml, tn * BN + cc * 32, r);
+        } else if (ml < a.c.bm) {
+          if (a.accumulate) epi_chunk_red(a.c, L, ml, tn * BN + cc * 32, r);
+          else epi_chunk(a.c, L, ml, tn * BN + cc * 32, r);
         }
       }
       tc_fence_before();
@@ -345,7 +400,8 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
 }
 
 template <int FMT, bool A_MN, bool B_MN, int EPI>
-cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
+cudaError_t launch_cfg(const DirectArgs& a, const DirectArgs* tab, const int64_t* unit_start, int count,
+                       int64_t total_units, cudaStream_t st) {
   using C = Cfg<FMT>;
   auto kern = pair_fmm_kernel<FMT, A_MN, B_MN, EPI>;
   static bool attr_set[64] = {false};
@@ -357,11 +413,24 @@ cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  if (a.tp_a % BM != 0 || a.tp_b % BN != 0 || a.kp % C::BK != 0) return cudaErrorInvalidValue;
-  if (a.tm_count && a.tm_begin + a.tm_count > a.tp_a / BM) return cudaErrorInvalidValue;
-  const int64_t ntiles = (a.tm_count ? a.tm_count : a.tp_a / BM) * (a.tp_b / BN);
-  if (ntiles == 0 || a.num_leaves == 0) return cudaSuccess;
-  const int64_t units = (a.mbuf || a.accumulate) ? ntiles * a.num_leaves : ntiles;
+  PairLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.one = a;
+  int64_t units;
+  if (tab) {
+    L.tab = tab;
+    L.unit_start = unit_start;
+    L.count = count;
+    L.total_units = total_units;
+    units = total_units;
+  } else {
+    if (a.tp_a % BM != 0 || a.tp_b % BN != 0 || a.kp % C::BK != 0) return cudaErrorInvalidValue;
+    if (a.tm_count && a.tm_begin + a.tm_count > a.tp_a / BM) return cudaErrorInvalidValue;
+    const int64_t ntiles = (a.tm_count ? a.tm_count : a.tp_a / BM) * (a.tp_b / BN);
+    if (ntiles == 0 || a.num_leaves == 0) return cudaSuccess;
+    units = (a.mbuf || a.accumulate) ? ntiles * a.num_leaves : ntiles;
+  }
+  if (units == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3((EPI + 2) * 32);
   cfg.dynamicSmemBytes = C::kSmem;
@@ -389,17 +458,21 @@ cudaError_t launch_cfg(const DirectArgs& a, cudaStream_t st) {
   const int64_t pairs = std::min<int64_t>(units, resident[dev]);
   cfg.gridDim = dim3((unsigned)(2 * pairs));
   KernelTimer timer("multiply", st);
-  return cudaLaunchKernelEx(&cfg, kern, a);
+  return cudaLaunchKernelEx(&cfg, kern, L);
 }
 
+// Operand layouts: forward (A K-major, B MN-major), dA = dC B^T (both
+// K-major), dB = A^T dC (both MN-major); eight epilogue warps where the
+// epilogue adds into C (fused epilogue, accumulate), four where it stores.
 template <int FMT>
-cudaError_t launch_layout(const DirectArgs& a, cudaStream_t st) {
+cudaError_t launch_fmt(const DirectArgs& a, const DirectArgs* tab, const int64_t* us, int count, int64_t total,
+                       cudaStream_t st) {
   if (!a.a_mn && a.b_mn) {
-    if (!a.mbuf) return launch_cfg<FMT, false, true, 8>(a, st);
-    return launch_cfg<FMT, false, true, 4>(a, st);
+    if (tab || !a.mbuf) return launch_cfg<FMT, false, true, 8>(a, tab, us, count, total, st);
+    return launch_cfg<FMT, false, true, 4>(a, tab, us, count, total, st);
   }
-  if (!a.a_mn && !a.b_mn) return launch_cfg<FMT, false, false, 4>(a, st);
-  if (a.a_mn && a.b_mn) return launch_cfg<FMT, true, true, 4>(a, st);
+  if (!a.a_mn && !a.b_mn) return launch_cfg<FMT, false, false, 4>(a, tab, us, count, total, st);
+  if (a.a_mn && a.b_mn) return launch_cfg<FMT, true, true, 4>(a, tab, us, count, total, st);
   return cudaErrorNotSupported;
 }
 
@@ -407,9 +480,19 @@ cudaError_t launch_layout(const DirectArgs& a, cudaStream_t st) {
 
 cudaError_t launch_pair_gemm(const DirectArgs& a, int leaf_format, cudaStream_t st) {
   switch (leaf_format) {
-    case FMM_LEAF_BF16: return pair::launch_layout<FMM_LEAF_BF16>(a, st);
-    case FMM_LEAF_F16: return pair::launch_layout<FMM_LEAF_F16>(a, st);
-    default: return pair::launch_layout<FMM_LEAF_BF16X3>(a, st);
+    case FMM_LEAF_BF16: return pair::launch_fmt<FMM_LEAF_BF16>(a, nullptr, nullptr, 0, 0, st);
+    case FMM_LEAF_F16: return pair::launch_fmt<FMM_LEAF_F16>(a, nullptr, nullptr, 0, 0, st);
+    default: return pair::launch_fmt<FMM_LEAF_BF16X3>(a, nullptr, nullptr, 0, 0, st);
+  }
+}
+
+cudaError_t launch_pair_gemm_batched(const DirectArgs& layout, const DirectArgs* tab, const int64_t* unit_start,
+                                     int count, int64_t total_units, int leaf_format, cudaStream_t st) {
+  if (count == 0 || total_units == 0) return cudaSuccess;
+  switch (leaf_format) {
+    case FMM_LEAF_BF16: return pair::launch_fmt<FMM_LEAF_BF16>(layout, tab, unit_start, count, total_units, st);
+    case FMM_LEAF_F16: return pair::launch_fmt<FMM_LEAF_F16>(layout, tab, unit_start, count, total_units, st);
+    default: return pair::launch_fmt<FMM_LEAF_BF16X3>(layout, tab, unit_start, count, total_units, st);
   }
 }
 

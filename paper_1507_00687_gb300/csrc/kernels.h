@@ -285,6 +285,11 @@ cudaError_t launch_direct_gemm(const DirectArgs& args, int leaf_format, int bn, 
 // 256 x 256 tiles, tp_a and tp_b multiples of 256; a K-major B operand's
 // tensor map has 128-row boxes (each CTA loads half of B's tile).
 cudaError_t launch_pair_gemm(const DirectArgs& args, int leaf_format, cudaStream_t st);
+// The same over a batch: tab (device memory) holds `count` problems (tp_a,
+// tp_b multiples of 256), unit_start their consecutive unit numbering;
+// `layout` gives the status word, the wait limit and the operand layouts.
+cudaError_t launch_pair_gemm_batched(const DirectArgs& layout, const DirectArgs* tab, const int64_t* unit_start,
+                                     int count, int64_t total_units, int leaf_format, cudaStream_t st);
 
 // The same kernel over a batch: tab (device memory) holds `count` problems,
 // each with its tensor maps, leaves and stored-product buffer (mbuf set);

@@ -189,3 +189,39 @@ def test_batch_with_trees_and_rotations(api):
         kl = -(-Ad.shape[1] // pk)
         tol = (U_LEAF["bf16x3"] + (kl + 2 * TC.max_terms(orc) + 8) * 2.0**-23) * G
         assert np.all(np.abs(dev_values(C) - Cref) <= tol)
+
+
+@pytest.mark.parametrize("dt,leaf", [("bf16", "bf16")])
+def test_batch_classical_entries_read_inputs_directly(api, dt, leaf):
+    # Classical entries with bf16 inputs and leaves are multiplied straight
+    # from the caller's matrices (no scaling reductions, no conversion):
+    # power-of-two scaling cancels exactly for the classical product, so
+    # each result equals, bit for bit, the single-product path with the
+    # batch's scaling applied (conversion, multiply, unscale) and without
+    # it; ragged sizes included, beside a fast entry that is scaled.
+    shapes = [(512, 640, 384), (1000, 520, 776), (129, 65, 257), (768, 1024, 512), (300, 2048, 256)]
+    probs, refs = [], []
+    for i, (M, K, N) in enumerate(shapes):
+        A = inputs.uniform((M, K), -1, 1, seed=700 + i)
+        B = inputs.uniform((K, N), -1, 1, seed=800 + i)
+        Ad, Bd = to_dev(A, dt), to_dev(B, dt)
+        probs.append((api.Plan([], leaf), Ad, Bd, torch.full((M, N), float("nan"), device="cuda")))
+    # a fast entry alongside (scaled through the reductions and combination)
+    A, B = inputs.diag_scaled_pair(640, 512, 768, seed=950, span=4.0)
+    probs.append((api.Plan(["winograd"], leaf), to_dev(A, dt), to_dev(B, dt),
+                  torch.full((640, 768), float("nan"), device="cuda")))
+    batch = api.Batch(probs, "OI")
+    batch.run()
+    api.sync_status()
+    for plan, Ad, Bd, C in probs[:-1]:
+        eA, d, eB = api.scale(Ad, Bd, "OI")
+        scaled = api.multiply(plan, Ad, Bd, eA, d, eB)
+        plain = api.multiply(plan, Ad, Bd)
+        api.sync_status()
+        assert np.array_equal(dev_values(C), dev_values(scaled)), tuple(Ad.shape)
+        assert np.array_equal(dev_values(C), dev_values(plain)), tuple(Ad.shape)
+    plan, Ad, Bd, C = probs[-1]
+    A64, B64 = dev_values(Ad), dev_values(Bd)
+    st = OS.pow2_repeated(A64, B64, "OI")
+    Cref, G = oracle_reference(A64, B64, ["winograd"], st.eA, st.d, st.eB)
+    assert_within(dev_values(C), Cref, G, ["winograd"], 512, leaf, "fast entry beside direct ones")
