@@ -71,14 +71,19 @@ def workload_config(args):
 
 # ---------------------------------------------------------------- batched workload
 
-def batched_workload(api, inputs, torch, count: int) -> dict:
+def batched_workload(api, inputs, torch, count: int, rank: int = 0, world: int = 1) -> dict:
     """``count`` independent products, each dimension log-uniform over the
     multiples of 128 in [512, 4096]; BF16 inputs U[-1, 1] (seeded, made on
     the device), BF16 leaves with FP32 accumulation, outside-inside scaling;
     plans chosen per product by the autotuner; the whole batch one launch
     sequence (one persistent tensor-core launch) replayed from a CUDA graph.
-    Inputs total several GB, far beyond L2, so no flush is needed."""
-    dims = inputs.log_uniform_dims(count, 512, 4096, 128, seed=1507 + 4000)
+    Inputs total several GB, far beyond L2, so no flush is needed.  On
+    several GPUs each rank runs its share of the same batch
+    (fmm_batch_partition: longest-processing-time by flops, no exchange);
+    the batch time is the slowest rank's."""
+    all_dims = inputs.log_uniform_dims(count, 512, 4096, 128, seed=1507 + 4000)
+    mine = api.partition_batch(all_dims.tolist(), world)[rank] if world > 1 else list(range(count))
+    dims = all_dims[mine]
     t0 = time.time()
     tuner = api.Autotuner(leaf="bf16", dtype=torch.bfloat16)
     tune_s = time.time() - t0
@@ -109,6 +114,8 @@ def batched_workload(api, inputs, torch, count: int) -> dict:
     torch.cuda.synchronize()
     api.sync_status()
     ms = e0.elapsed_time(e1) / reps
+    if world > 1:
+        ms = max_over_ranks([ms])[0]
     # per-kind breakdown from separate runs with events around every launch
     api.kernel_timing(True)
     for _ in range(3):
@@ -119,7 +126,7 @@ def batched_workload(api, inputs, torch, count: int) -> dict:
     for kind in ("scale", "combine", "multiply"):
         k_ms, k_n = api.kernel_timing_read(kind)
         breakdown[kind] = {"ms_per_run": k_ms / 3, "launches_per_run": k_n // 3}
-    flops = float(sum(2 * M * K * N for M, K, N in dims.tolist()))
+    flops = float(sum(2 * M * K * N for M, K, N in all_dims.tolist()))
     # error of a sample of products against an FP64 product of the same inputs
     errs = []
     for i in range(0, count, max(1, count // 16)):
@@ -131,6 +138,7 @@ def batched_workload(api, inputs, torch, count: int) -> dict:
     del batch, probs, g
     torch.cuda.empty_cache()
     return {"products": count, "tflops": flops / (ms * 1e-3) / 1e12, "ms_per_batch": ms, "total_gflop": flops / 1e9,
+            "ranks": world, "products_this_rank": len(mine),
             "plans": choice, "launch": "one CUDA graph replay: 6 scaling + 1 combination + 1 multiply + 1 output launch",
             "workspace_gb": ws_gb, "autotune_s": tune_s,
             "max_err_over_K_normA_normB_sampled": max(errs), "leaf": "bf16", "inputs": "bf16 U[-1,1]",
@@ -699,7 +707,7 @@ def main():
     if not args.no_extras:
         extras["headline_n8192"] = crossover_workload(api, inputs, torch, args)
     if not args.no_extras and args.batch > 0:
-        extras["batched"] = batched_workload(api, inputs, torch, args.batch)
+        extras["batched"] = batched_workload(api, inputs, torch, args.batch, rank, world)
     if not args.no_extras:
         extras["autograd_linear"] = linear_layer_workload(api, torch)
         extras["precision_sweep"] = precision_sweep(api, torch)

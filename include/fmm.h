@@ -495,6 +495,19 @@ fmm_status fmm_batch_run(fmm_batch_t batch, void* stream);
 fmm_status fmm_batch_destroy(fmm_batch_t batch);
 
 /*
+ * Split a batch over `parts` GPUs (one process per GPU, each running its
+ * share as a batch of its own: independent products need no exchange):
+ * longest-processing-time order by the classical flop count 2 M K N (ties
+ * by index), each product to the part with the least assigned flops so far
+ * (ties: the lowest part), so the largest share is within 4/3 of the best
+ * possible.  M, K, N: host arrays of `count` sizes; part_of (host, count
+ * entries) receives each product's part.  Host only; the same inputs give
+ * the same assignment on every process.
+ */
+fmm_status fmm_batch_partition(const int64_t* M, const int64_t* K, const int64_t* N, int count, int parts,
+                               int32_t* part_of);
+
+/*
  * Gradients of C = A B for a given dC (M x N, float32, lddc):
  *   dA = dC B^T (M x K, float32, ldda),  dB = A^T dC (K x N, float32, lddb),
  * each by a fast algorithm derived from the plan's rules through the cyclic

@@ -33,7 +33,7 @@ EXPORTS = [
     "fmm_plan_set_between_scaling", "fmm_plan_tree", "fmm_scale_adaptive",
     "fmm_host_create", "fmm_host_submit", "fmm_host_wait", "fmm_host_destroy",
     "fmm_rule_rotate", "fmm_rule_compose", "fmm_rule_transform", "fmm_rule_permute", "fmm_plan_variants",
-    "fmm_block_max",
+    "fmm_block_max", "fmm_batch_partition",
 ]
 SELECT_RANDOM, SELECT_ROUND_ROBIN, SELECT_MATRIX = 0, 1, 2
 
@@ -88,6 +88,8 @@ def lib():
     L.fmm_plan_variants.argtypes = [C.POINTER(vp), rp, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_float),
                                     C.POINTER(C.c_float), i32p, C.c_int]
     L.fmm_block_max.argtypes = [vp, C.c_int, i64, i64, i64, C.c_int, C.c_int, vp, vp]
+    i64p = C.POINTER(i64)
+    L.fmm_batch_partition.argtypes = [i64p, i64p, i64p, C.c_int, C.c_int, i32p]
     L.fmm_plan_set_schedule.argtypes = [vp, C.c_int]
     L.fmm_plan_set_between_scaling.argtypes = [vp, C.c_int]
     L.fmm_kernel_timing.argtypes = [C.c_int]

@@ -356,6 +356,20 @@ class HostPipeline:
             self._h = None
 
 
+def partition_batch(dims, parts: int) -> list:
+    """Indices of the products of each part when a batch of products with
+    sizes ``dims`` ((M, K, N) rows) is split over ``parts`` GPUs
+    (fmm_batch_partition: longest-processing-time by flops)."""
+    d = np.asarray(dims, dtype=np.int64).reshape(-1, 3)
+    n = len(d)
+    M, K, Nn = (np.ascontiguousarray(d[:, j]) for j in range(3))
+    out = np.zeros(n, dtype=np.int32)
+    i64p = C.POINTER(C.c_int64)
+    N.check(N.lib().fmm_batch_partition(M.ctypes.data_as(i64p), K.ctypes.data_as(i64p), Nn.ctypes.data_as(i64p), n,
+                                        parts, out.ctypes.data_as(C.POINTER(C.c_int32))), "fmm_batch_partition")
+    return [np.flatnonzero(out == q).tolist() for q in range(parts)]
+
+
 class Batch:
     """Many independent products C_i = A_i B_i, each with its own plan, run
     as one fixed launch sequence (fmm_batch_create / fmm_batch_run): batched

@@ -1720,6 +1720,28 @@ fmm_status fmm_batch_run(fmm_batch_t batch, void* stream) {
   return batch_run(b, as_stream(stream));
 }
 
+fmm_status fmm_batch_partition(const int64_t* M, const int64_t* K, const int64_t* N, int count, int parts,
+                               int32_t* part_of) {
+  if (count < 0 || parts < 1 || (count > 0 && (!M || !K || !N || !part_of))) return FMM_ERR_ARG;
+  std::vector<int> order((size_t)count);
+  std::vector<double> flops((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    if (M[i] < 0 || K[i] < 0 || N[i] < 0) return FMM_ERR_ARG;
+    order[(size_t)i] = i;
+    flops[(size_t)i] = 2.0 * (double)M[i] * (double)K[i] * (double)N[i];
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return flops[(size_t)a] > flops[(size_t)b]; });
+  std::vector<double> load((size_t)parts, 0.0);
+  for (int i : order) {
+    int best = 0;
+    for (int q = 1; q < parts; ++q)
+      if (load[(size_t)q] < load[(size_t)best]) best = q;
+    part_of[i] = best;
+    load[(size_t)best] += flops[(size_t)i];
+  }
+  return FMM_OK;
+}
+
 fmm_status fmm_batch_destroy(fmm_batch_t batch) {
   delete reinterpret_cast<Batch*>(batch);
   return FMM_OK;
