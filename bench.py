@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--schedule", default="auto", choices=["auto", "pass", "load_stage", "pass_accumulate"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator / variant timings")
     ap.add_argument("--batch", type=int, default=512, help="products in the batched workload extra (0: skip)")
-    ap.add_argument("--experiment", default="", choices=["", "scaling_accuracy", "batch"],
+    ap.add_argument("--experiment", default="", choices=["", "scaling_accuracy", "batch", "oracle_timing"],
                     help="scaling_accuracy: relative error of Strassen, L = 1..6, under each scaling (Sec. 6.5); "
-                         "batch: the batched workload alone (--batch products)")
+                         "batch: the batched workload alone (--batch products); oracle_timing: the float64 "
+                         "oracle on the host cores, single-threaded and on all cores, n = 256, 4096, 8192")
     ap.add_argument("--samples", type=int, default=100, help="samples per distribution (--experiment)")
     ap.add_argument("--exp-n", type=int, default=2000, help="matrix size (--experiment)")
     return ap.parse_args()
@@ -239,6 +240,32 @@ def crossover_workload(api, inputs, torch, args, n: int = 8192, reps: int = 10) 
     return out
 
 
+# ---------------------------------------------------------------- FP8 dense peak probe
+
+def fp8_peak_probe(torch, n: int = 8192, reps: int = 10) -> dict:
+    """The dense E4M3 rate of the library GEMM in torch (a scaled FP8 product
+    at n^3, best of `reps`, CUDA events): the denominator for the E4M3 leaf
+    kernel's fraction of peak (not in the driver's measured peaks).
+    Measurement only."""
+    try:
+        a = torch.randn((n, n), device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn((n, n), device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+        best = float("inf")
+        for i in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= 2:
+                best = min(best, e0.elapsed_time(e1))
+        del a, b
+        return {"fp8_e4m3_tflops": 2.0 * n**3 / (best * 1e-3) / 1e12, "how": f"torch._scaled_mm {n}^3, best of {reps}"}
+    except Exception as e:  # not available in this torch build
+        return {"unavailable": str(e)[:200]}
+
+
 # ---------------------------------------------------------------- precision sweep
 
 def precision_sweep(api, torch, reps: int = 5) -> dict:
@@ -398,13 +425,91 @@ def host_link(h_src, d_buf, h_dst, reps=5):
     return out
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else the kernel's CPU list), or the
+    machine type."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+        with open("/proc/cpuinfo") as f:  # Arm: implementer / part numbers
+            parts = {}
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    parts.setdefault(k.strip(), v.strip())
+        if "CPU part" in parts:
+            return f"Arm implementer {parts.get('CPU implementer')} part {parts.get('CPU part')}"
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_timing_child(n: int, which: str, reps: int, q) -> None:
+    """Median time of `reps` oracle products (a separate process, so that the
+    BLAS thread count set in its environment applies)."""
+    from oracle import fmm as OF
+    from oracle import rules as OR
+    A, B = oracle_inputs(n, SEED)
+    tree = None if which == "classical" else OF.uniform([OR.winograd()])
+    OF.fmm(A[:256, :256], B[:256, :256], tree)  # warm up
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        OF.fmm(A, B, tree)
+        ts.append(time.perf_counter() - t0)
+    q.put(statistics.median(ts))
+
+
+def oracle_timing(args) -> dict:
+    """The float64 oracle on the host cores at n = 256, 4096 and 8192: the
+    classical product and Winograd one level, single-threaded (the paper's
+    Sec. 6.5 setting) and on all cores, median of 5 (3 at n = 8192), as
+    effective GFLOP/s 2 n^3 / t."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = {"cpu_model": cpu_model(), "nproc": os.cpu_count(), "runs": []}
+    for threads in (1, os.cpu_count()):
+        for n in (256, 4096, 8192):
+            for which in ("classical", "winograd"):
+                reps = 3 if n >= 8192 else 5
+                env = {k: str(threads) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                                  "BLIS_NUM_THREADS")}
+                old = {k: os.environ.get(k) for k in env}
+                os.environ.update(env)
+                q = ctx.Queue()
+                p = ctx.Process(target=_oracle_timing_child, args=(n, which, reps, q))
+                p.start()
+                t = q.get()
+                p.join()
+                for k, v in old.items():
+                    if v is None:
+                        os.environ.pop(k, None)
+                    else:
+                        os.environ[k] = v
+                out["runs"].append({"threads": threads, "n": n, "algorithm": which, "median_s": t, "reps": reps,
+                                    "gflops": 2.0 * n**3 / t / 1e9})
+    return out
+
+
 def cpu_baseline(args) -> dict:
     n_s = min(args.n, 2048)
     oracle_step(*oracle_inputs(256, SEED), args)  # warm numpy / BLAS
     A, B = oracle_inputs(n_s, SEED)
     ts = [oracle_step(A, B, args) for _ in range(3)]
     t = statistics.median(ts)
-    return {"value": 2.0 * n_s**3 / t / 1e12, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": 2.0 * n_s**3 / t / 1e12, "unit": UNIT, "cores": os.cpu_count(), "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": f"one n={n_s} product of the same distribution ({(n_s / args.n) ** 3:.3g} of the "
                       f"workload's flops), float64 numpy oracle with BLAS leaf products, median of 3 "
                       f"({t:.2f} s each)"}
@@ -522,6 +627,9 @@ def main():
         return
     if args.experiment == "scaling_accuracy":
         scaling_accuracy(args)
+        return
+    if args.experiment == "oracle_timing":
+        print(json.dumps({"experiment": "oracle_timing", **oracle_timing(args)}))
         return
     if args.experiment == "batch":
         import torch
@@ -711,6 +819,7 @@ def main():
     if not args.no_extras:
         extras["autograd_linear"] = linear_layer_workload(api, torch)
         extras["precision_sweep"] = precision_sweep(api, torch)
+        extras["fp8_peak_probe"] = fp8_peak_probe(torch)
 
     # ---------------- roofline of the dominant kernel (the tensor-core multiply)
     import json as _json
