@@ -62,7 +62,8 @@ struct Cfg {
   static constexpr int kTmemCols = 2 * BN;
   static constexpr int kBarBytes = 256;
   static constexpr int kUnitCache = 2048;  // batch unit table entries kept in shared memory
-  static constexpr int kSmem = kStages * kStage + kBarBytes + kUnitCache * 8 + 1024;  // + alignment slack
+  // + alignment slack; a batched launch also keeps its unit numbering
+  static constexpr int smem(bool batch) { return kStages * kStage + kBarBytes + (batch ? kUnitCache * 8 : 0) + 1024; }
 };
 
 __device__ __forceinline__ uint32_t cluster_id_x() {
@@ -118,7 +119,9 @@ __device__ __forceinline__ int find_unit_problem(const int64_t* start, int count
   return lo;
 }
 
-template <int FMT, bool A_MN, bool B_MN, int EPI>
+// BATCH: the launch covers a batch's problems (`tab`); otherwise one
+// problem, whose arguments every role reads from the launch itself.
+template <int FMT, bool A_MN, bool B_MN, int EPI, bool BATCH>
 __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __grid_constant__ PairLaunch launch) {
   const DirectArgs& args = launch.one;
   constexpr int kMmaWarp = EPI, kTmaWarp = EPI + 1;
@@ -170,8 +173,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
   pdl_wait();
   pdl_trigger();
   // a batch's unit numbering, in shared memory when it fits
-  const bool batched = launch.tab != nullptr;
-  const bool ucached = batched && launch.count + 1 <= C::kUnitCache;
+  const bool ucached = BATCH && launch.count + 1 <= C::kUnitCache;
   if (ucached)
     for (int i = threadIdx.x; i <= launch.count; i += blockDim.x) ustart[i] = __ldg(launch.unit_start + i);
   __syncthreads();
@@ -183,17 +185,22 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
     const int64_t nt = (a.tm_count ? a.tm_count : a.tp_a / BM) * (a.tp_b / BN);
     return (a.mbuf || a.accumulate) ? nt * a.num_leaves : nt;
   };
-  const int64_t total_units = batched ? launch.total_units : units_of(args);
+  const int64_t total_units = BATCH ? launch.total_units : units_of(args);
   const int64_t u0 = cluster_id_x(), ustep = cluster_count_x();
   struct Cursor {
     int64_t u, leaf, leaf_end, tm, tn, kt;
     const DirectArgs* a;
     int p;  // batch: problem of unit u (each role walks its units in increasing order)
   };
+  // the problem a cursor's unit belongs to
+  auto prob = [&](const Cursor& c) -> const DirectArgs& {
+    if constexpr (BATCH) return *c.a;
+    else return args;
+  };
   auto decode = [&](Cursor& c) {
     if (c.u >= total_units) return;
     int64_t local;
-    if (batched) {
+    if constexpr (BATCH) {
       if (ucached) {
         while (c.p + 1 < launch.count && ustart[c.p + 1] <= c.u) ++c.p;
         local = c.u - ustart[c.p];
@@ -206,7 +213,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
       c.a = &args;
       local = c.u;
     }
-    const DirectArgs& a = *c.a;
+    const DirectArgs& a = prob(c);
     const int64_t ntn = a.tp_b / BN, ntiles = (a.tm_count ? a.tm_count : a.tp_a / BM) * ntn;
     int64_t tile;
     if (a.mbuf || a.accumulate) {  // units are (leaf, tile)
@@ -245,7 +252,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
       bool ok = true;
       uint32_t armed = 0, armed_parity = 0;  // leader: per stage, expecting bytes, parity it completes
       for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
-        const DirectArgs& a = *w.a;
+        const DirectArgs& a = prob(w);
         const int64_t NL = a.num_leaves;
         for (int64_t kt = 0; kt < w.kt && ok; ++kt) {
           if (!mbar_wait_bounded_cluster(&empty[stage], phase ^ 1u, abort_flag, args.timeout_ns)) {
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
     const int row = (int)rank * HM + quarter * 32 + lane;  // tile row of this thread (TMEM lane = row mod 128)
     const uint32_t tempty0 = mapa_shared(smem_u32(&tempty[0]), 0u);
     for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
-      const DirectArgs& a = *w.a;
+      const DirectArgs& a = prob(w);
       const int64_t leaf = w.leaf, tn = w.tn;
       const int64_t ml = w.tm * BM + row;
       const uint32_t buf = acc_iter & 1u, aph = (acc_iter >> 1) & 1u;
@@ -399,17 +406,18 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
   }
 }
 
-template <int FMT, bool A_MN, bool B_MN, int EPI>
+template <int FMT, bool A_MN, bool B_MN, int EPI, bool BATCH>
 cudaError_t launch_cfg(const DirectArgs& a, const DirectArgs* tab, const int64_t* unit_start, int count,
                        int64_t total_units, cudaStream_t st) {
   using C = Cfg<FMT>;
-  auto kern = pair_fmm_kernel<FMT, A_MN, B_MN, EPI>;
+  auto kern = pair_fmm_kernel<FMT, A_MN, B_MN, EPI, BATCH>;
+  constexpr int kSmem = C::smem(BATCH);
   static bool attr_set[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   if (!attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
@@ -417,7 +425,8 @@ cudaError_t launch_cfg(const DirectArgs& a, const DirectArgs* tab, const int64_t
   std::memset(&L, 0, sizeof(L));
   L.one = a;
   int64_t units;
-  if (tab) {
+  if (BATCH) {
+    if (!tab) return cudaErrorInvalidValue;
     L.tab = tab;
     L.unit_start = unit_start;
     L.count = count;
@@ -433,7 +442,7 @@ cudaError_t launch_cfg(const DirectArgs& a, const DirectArgs* tab, const int64_t
   if (units == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3((EPI + 2) * 32);
-  cfg.dynamicSmemBytes = C::kSmem;
+  cfg.dynamicSmemBytes = kSmem;
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -467,12 +476,16 @@ cudaError_t launch_cfg(const DirectArgs& a, const DirectArgs* tab, const int64_t
 template <int FMT>
 cudaError_t launch_fmt(const DirectArgs& a, const DirectArgs* tab, const int64_t* us, int count, int64_t total,
                        cudaStream_t st) {
-  if (!a.a_mn && a.b_mn) {
-    if (tab || !a.mbuf) return launch_cfg<FMT, false, true, 8>(a, tab, us, count, total, st);
-    return launch_cfg<FMT, false, true, 4>(a, tab, us, count, total, st);
+  if (tab) {  // batches: forward products, unscaling epilogue
+    if (!a.a_mn && a.b_mn) return launch_cfg<FMT, false, true, 8, true>(a, tab, us, count, total, st);
+    return cudaErrorNotSupported;
   }
-  if (!a.a_mn && !a.b_mn) return launch_cfg<FMT, false, false, 4>(a, tab, us, count, total, st);
-  if (a.a_mn && a.b_mn) return launch_cfg<FMT, true, true, 4>(a, tab, us, count, total, st);
+  if (!a.a_mn && a.b_mn) {
+    if (!a.mbuf) return launch_cfg<FMT, false, true, 8, false>(a, nullptr, nullptr, 0, 0, st);
+    return launch_cfg<FMT, false, true, 4, false>(a, nullptr, nullptr, 0, 0, st);
+  }
+  if (!a.a_mn && !a.b_mn) return launch_cfg<FMT, false, false, 4, false>(a, nullptr, nullptr, 0, 0, st);
+  if (a.a_mn && a.b_mn) return launch_cfg<FMT, true, true, 4, false>(a, nullptr, nullptr, 0, 0, st);
   return cudaErrorNotSupported;
 }
 
