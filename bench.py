@@ -800,16 +800,26 @@ def main():
         step(plan, "")
         torch.cuda.synchronize()
         extras["componentwise_rel_err"]["fast_unscaled"] = rel(C.double())
+        if args.scaling == "OI":
+            o_ms, o_kms, _ = timed(max(10, args.steps // 4), plan, "O")
+            step(plan, "O")
+            torch.cuda.synchronize()
+            extras["fast_O_only"] = {"tflops": flops / (o_ms * 1e-3) / 1e12, "ms_per_step": o_ms,
+                                     "kernel_ms": o_kms, "max_abs_err": float((C.double() - ref).abs().max()),
+                                     "note": "outside scaling only (one O step)"}
         if args.levels == 1:
-            try:
-                plan2 = api.Plan([args.rule] * 2, args.leaf, args.schedule)
-                l2_ms, l2_kms, _ = timed(max(10, args.steps // 4), plan2, args.scaling)
-                step(plan2, args.scaling)
-                torch.cuda.synchronize()
-                extras["fast_L2"] = {"tflops": flops / (l2_ms * 1e-3) / 1e12, "ms_per_step": l2_ms,
-                                     "kernel_ms": l2_kms, "max_abs_err": float((C.double() - ref).abs().max())}
-            except Exception as e:  # plan outside the supported range
-                extras["fast_L2"] = {"unavailable": str(e)}
+            for lv in (2, 3):
+                try:
+                    plan_l = api.Plan([args.rule] * lv, args.leaf, args.schedule)
+                    l_ms, l_kms, _ = timed(max(10, args.steps // 4), plan_l, args.scaling)
+                    step(plan_l, args.scaling)
+                    torch.cuda.synchronize()
+                    extras[f"fast_L{lv}"] = {"tflops": flops / (l_ms * 1e-3) / 1e12, "ms_per_step": l_ms,
+                                             "kernel_ms": l_kms,
+                                             "max_abs_err": float((C.double() - ref).abs().max())}
+                    del plan_l
+                except Exception as e:  # plan outside the supported range
+                    extras[f"fast_L{lv}"] = {"unavailable": str(e)}
         del plan0
     del ref, C_fast
     if not args.no_extras:
@@ -927,7 +937,7 @@ def main():
         out["cpu_baseline"] = cpu_baseline(args)
     # the comparisons in one short record at the end of the line
     summ = {"fast_scaled": {"tflops": value, "max_abs_err": err_fast}}
-    for k in ("classical_same_kernel", "fast_no_scaling", "fast_accumulate", "fast_L2"):
+    for k in ("classical_same_kernel", "fast_no_scaling", "fast_O_only", "fast_accumulate", "fast_L2", "fast_L3"):
         if k in extras and "tflops" in extras[k]:
             summ[k] = {"tflops": extras[k]["tflops"], "max_abs_err": extras[k].get("max_abs_err")}
     if "headline_n8192" in extras:
