@@ -305,6 +305,9 @@ def quantize_e4m3_blocks(X: np.ndarray, axis: int, block: int = 128):
     each block is scaled by 2^-s with s = e(max |block|) - 8 (the frexp
     exponent; s = 0 for an all-zero block), so that its largest magnitude
     lies in [128, 256), rounded to E4M3 (ties to even), and scaled back.
+    The scale is a UE8M0 number (2^-127 .. 2^127), so s is raised to -127
+    for blocks whose largest magnitude is below 2^-120 (which then use the
+    E4M3 subnormals).
     Returns (the represented values, the exponents s per block)."""
     X = np.asarray(X, dtype=np.float64)
     Xt = X if axis == 1 else X.T
@@ -316,7 +319,7 @@ def quantize_e4m3_blocks(X: np.ndarray, axis: int, block: int = 128):
         blk = Xt[:, b * block:(b + 1) * block]
         m = np.abs(blk).max(axis=1)
         e = np.frexp(m)[1]
-        s_ = np.where(m > 0, e - 8, 0)
+        s_ = np.where(m > 0, np.maximum(e - 8, -127), 0)
         scales[:, b] = s_
         f = np.exp2(s_.astype(np.float64))[:, None]
         out[:, b * block:(b + 1) * block] = precision.round_to(blk / f, "e4m3") * f

@@ -515,8 +515,19 @@ static bool make_map_u8(CUtensorMap* m, const void* ptr, int64_t rows, int64_t c
   return true;
 }
 
+// E4M3 leaf products with the tensor core's block scaling (UE8M0 scale
+// atoms); FMM_FP8_FOLD=1 in the environment (read once) keeps the kernel
+// that folds each 128-wide K block's product into FP32 sums itself.
+static bool fp8_block_scaled() {
+  static bool on = [] {
+    const char* s = std::getenv("FMM_FP8_FOLD");
+    return !(s && std::atoi(s) != 0);
+  }();
+  return on;
+}
+
 // The pass schedule with E4M3 leaves: the E4M3 combination pass writes
-// S_r, T_r (K-major bytes) and their per-128-block factors; the FP8
+// S_r, T_r (K-major bytes) and their per-128-block scales; the FP8
 // multiply kernel stores M_r; the output pass forms C.
 static fmm_status run_pass_fp8(const Plan* p, const Source& x, const Source& y, const EpilogueArgs& c,
                                const LeafDesc* leaves, int* status, void* ws, size_t ws_bytes, cudaStream_t st) {
@@ -544,10 +555,13 @@ static fmm_status run_pass_fp8(const Plan* p, const Source& x, const Source& y, 
   // both sides K-major: [leaf][t][k]
   ca.p_rows = g.tp_a;
   ca.p_cols = g.kp;
+  const int bs = fp8_block_scaled() ? 1 : 0;
   ca.scale_out = sa;
+  ca.sf_atoms = bs;
   cb.p_rows = g.tp_b;
   cb.p_cols = g.kp;
   cb.scale_out = sb;
+  cb.sf_atoms = bs;
   if (!cuda_ok(launch_combine_e4m3(cb, st), "E4M3 combination pass (B)") ||
       !cuda_ok(launch_combine_e4m3(ca, st), "E4M3 combination pass (A)"))
     return FMM_ERR_CUDA;
@@ -564,6 +578,7 @@ static fmm_status run_pass_fp8(const Plan* p, const Source& x, const Source& y, 
   f.num_leaves = R;
   f.status = status;
   f.timeout_ns = timeout_ns();
+  f.block_scaled = bs;
   if (!cuda_ok(launch_fp8_gemm(f, st), "E4M3 multiply launch")) return FMM_ERR_CUDA;
   const OutArgs o = out_args(p, g, c, leaves, mbuf);
   const bool gather = p->pm * p->pn > kMaxOutBlocks;

@@ -1150,7 +1150,8 @@ __global__ void __launch_bounds__(TT * 32) combine_e4m3_kernel(const CombineArgs
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     bool nf = false;
     const int e = fexp_f32(__float_as_uint(m), &nf);
-    const int sc = m > 0.f ? e - 8 : 0;
+    // the UE8M0 scale range bounds s below by -127 (blocks whose max is below 2^-120)
+    const int sc = m > 0.f ? max(e - 8, -127) : 0;
     uint32_t packed = 0;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -1159,7 +1160,15 @@ __global__ void __launch_bounds__(TT * 32) combine_e4m3_kernel(const CombineArgs
       packed |= q << (16 * j);
     }
     *reinterpret_cast<uint32_t*>(out + ((int64_t)r * a.p_rows + t) * a.p_cols + k0 + 4 * lane) = packed;
-    if (lane == 0) a.scale_out[((int64_t)r * nkb + kb) * a.p_rows + t] = exp2i(sc);
+    if (lane == 0) {
+      if (a.sf_atoms) {
+        const int64_t atom = ((int64_t)r * nkb + kb) * (a.p_rows / 128) + t / 128;
+        reinterpret_cast<uint32_t*>(a.scale_out)[atom * 128 + (t % 32) * 4 + (t % 128) / 32] =
+            (uint32_t)(sc + 127) * 0x01010101u;
+      } else {
+        a.scale_out[((int64_t)r * nkb + kb) * a.p_rows + t] = exp2i(sc);
+      }
+    }
   }
 }
 
@@ -1169,7 +1178,7 @@ bool e4m3_combine_fits(const CombineArgs& a) {
 }
 
 cudaError_t launch_combine_e4m3(const CombineArgs& a, cudaStream_t st) {
-  if (a.p_rows % kF8TT != 0 || a.p_cols % 128 != 0) return cudaErrorInvalidValue;
+  if (a.p_rows % kF8TT != 0 || a.p_cols % 128 != 0 || (a.sf_atoms && a.p_rows % 128 != 0)) return cudaErrorInvalidValue;
   const int64_t nb = a.n_rb * a.n_cb;
   const size_t list = (size_t)a.t_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
   // sixteen rows per CTA when the staged tiles fit, else four

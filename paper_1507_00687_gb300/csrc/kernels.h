@@ -152,8 +152,13 @@ struct CombineArgs {
   // E4M3 leaves (fmt FMM_LEAF_E4M3B128): out holds bytes, K-major for both
   // sides ([leaf][t][k], p_rows = padded t, p_cols = padded k, multiples of
   // 128), and scale_out[(leaf * p_cols / 128 + kb) * p_rows + t] = 2^s of
-  // each row's 128-block.
+  // each row's 128-block; with sf_atoms, scale_out holds the same blocks'
+  // scales as UE8M0 bytes (s + 127) in the tensor core's block-scale
+  // layout instead: per (leaf, kb, 128-row group g) a 512-byte atom whose
+  // byte (t mod 32) * 16 + ((t mod 128) / 32) * 4 + j is row t's scale for
+  // the 32-wide K sub-block j (the four equal here).
   float* scale_out;
+  int sf_atoms;
 };
 
 // E4M3 combination pass (see CombineArgs::scale_out); a.p_rows / p_cols are
@@ -169,12 +174,13 @@ bool e4m3_combine_fits(const CombineArgs& a);
 struct Fp8Args {
   alignas(64) CUtensorMap map_a;
   alignas(64) CUtensorMap map_b;
-  const float* fa;  // [leaf][kb][tp_a] factors 2^sa
-  const float* fb;  // [leaf][kb][tp_b] factors 2^sb
+  const float* fa;  // [leaf][kb][tp_a] factors 2^sa (block_scaled: UE8M0 atoms, CombineArgs::sf_atoms)
+  const float* fb;  // [leaf][kb][tp_b] factors 2^sb (likewise)
   float* mbuf;      // [leaf][tp_a][tp_b] fp32
   int64_t tp_a, tp_b, kp, num_leaves;
   int* status;
   uint64_t timeout_ns;
+  int block_scaled;  // kind::mxf8f6f4.block_scale (scales applied by the tensor core), else the per-block fold
 };
 cudaError_t launch_fp8_gemm(const Fp8Args& a, cudaStream_t st);
 

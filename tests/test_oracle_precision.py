@@ -85,3 +85,21 @@ def test_e4m3_blocks_error_bound():
     for b in range(3):
         m = (np.abs(X[:, b * 128:(b + 1) * 128]) / f[:, b * 128:b * 128 + 1]).max(axis=1)
         assert np.all((m >= 128) & (m < 256))
+
+
+def test_e4m3_block_scale_floor_is_the_ue8m0_minimum():
+    # Block scales are UE8M0 numbers, 2^-127 at the least: a block whose
+    # largest magnitude is 2^-125 (frexp exponent -124, so s would be -132)
+    # takes s = -127 and is held as 4 = 2^-125 * 2^127; its entry 2^-137
+    # scales to 2^-10, half the smallest E4M3 subnormal (2^-9), and rounds to
+    # zero (ties to even), where s = -132 would have kept it exactly (2^-5).
+    # A block just above the floor (largest magnitude 2^-119, s = -126) is
+    # unaffected.
+    from oracle import fmm as F
+    X = np.zeros((2, 128))
+    X[0, 0], X[0, 1], X[0, 2] = 2.0 ** -125, 2.0 ** -137, 3 * 2.0 ** -131
+    X[1, 0], X[1, 1] = 2.0 ** -119, 2.0 ** -126
+    q, s = F.quantize_e4m3_blocks(X, axis=1)
+    assert s[0, 0] == -127 and s[1, 0] == -126
+    assert q[0, 0] == 2.0 ** -125 and q[0, 1] == 0.0 and q[0, 2] == 3 * 2.0 ** -131
+    assert q[1, 0] == 2.0 ** -119 and q[1, 1] == 2.0 ** -126
