@@ -766,7 +766,7 @@ def main():
     ref = A.double() @ B.double()   # FP64 reference product (measurement only)
     err_fast = float((C_fast - ref).abs().max())
     normA, normB = float(A.abs().max()), float(B.abs().max())
-    eps_leaf = {"bf16x3": 3 * 2.0**-16, "bf16": 2.0**-8, "fp16": 2.0**-11}[args.leaf]
+    eps_leaf = {"bf16x3": 3 * 2.0**-16, "bf16": 2.0**-8, "fp16": 2.0**-11, "e4m3b128": 2.0**-3 + 2.0**-8}[args.leaf]
     bound_unscaled = plan.bound(n, normA, normB, eps_leaf)
     extras = {}
     if not args.no_extras:
@@ -841,6 +841,12 @@ def main():
     peak_sus = peaks.get("bf16_tflops_sustained", 1700.0)
     peak_src = "of measured (bf16_tflops, burst)" if peaks else "of fallback"
     lin = extras.get("autograd_linear")
+    # E4M3 leaves: the dense FP8 rate, the measured bf16 figure times the
+    # nominal FP8 / bf16 ratio of 2
+    fp8 = args.leaf == "e4m3b128"
+    peak_m = peak * (2 if fp8 else 1)
+    peak_sus_m = peak_sus * (2 if fp8 else 1)
+    peak_src_m = peak_src + (" x 2 (nominal FP8 / bf16 ratio)" if fp8 else "")
     if lin:
         # forward and backward against the same tensor-core roofline: the
         # leaf kernel's executed flops, and the effective 2MNK/t of each call
@@ -862,6 +868,8 @@ def main():
     bt_min = min(-(-n // info["pm"]), -(-n // info["pn"]))
     pairs = os.environ.get("FMM_TILE_PAIRS", "1") != "0" and bt_min >= 256
     kname = ("pair_fmm_kernel" if pairs else "direct_fmm_kernel") if sched_used == "pass" else "fused_fmm_kernel"
+    if fp8:
+        kname = "fp8_bs_kernel" if os.environ.get("FMM_FP8_FOLD", "0") == "0" else "fp8_fmm_kernel"
     # the bandwidth passes of the pass schedule, per step: the combination
     # of both operands (one launch for small operands, else one per
     # operand; each operand read once, R^L combined leaf blocks written:
@@ -913,13 +921,13 @@ def main():
                                  "peak_GBps": peaks.get("hbm_gbs"),
                                  "frac": (pass_bytes / (comb_ms / bd_steps * 1e-3) / 1e9 / peaks["hbm_gbs"])
                                  if peaks.get("hbm_gbs") else None} if comb_n else None),
-           "executed_flop_fraction": achieved / peak,
+           "executed_flop_fraction": achieved / peak_m,
            "step_dram_traffic": step_traffic,
            "error": {"max_abs_err_vs_fp64": err_fast, "theorem_4_1_bound_unscaled": bound_unscaled,
                      "eps_leaf": eps_leaf, "normA": normA, "normB": normB},
-           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                        "peak_sustained": peak_sus, "frac_of_sustained": achieved / peak_sus,
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_m, "unit": "TFLOP/s",
+                        "frac": achieved / peak_m, "traffic": traffic, "peak_source": peak_src_m,
+                        "peak_sustained": peak_sus_m, "frac_of_sustained": achieved / peak_sus_m,
                         "kernel": kname, "algorithmic_flops_per_step": mma_flops,
                         "launches_per_step": mult_launches, "ms_per_step": mult_ms_per},
            "e2e": {"value": whole_job_tflops(flops, world, e_ms), "unit": UNIT,
