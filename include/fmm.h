@@ -70,10 +70,12 @@ enum { FMM_DT_F32 = 0, FMM_DT_BF16 = 1, FMM_DT_F16 = 2 };
  * accumulation.  BF16X3 splits x = hi + lo (hi = rn_bf16(x),
  * lo = rn_bf16(x - hi)) and sums hi*hi' + hi*lo' + lo*hi'.  E4M3B128: OCP
  * FP8 E4M3 with a power-of-two scale per 128-block along K (per row of S_r,
- * per column of T_r): s = e(block max) - 8, so the block's largest
- * magnitude scales into [128, 256), then round to nearest even; the leaf
- * product sums 2^(sa + sb) times each block's E4M3 product in FP32 (pass
- * schedule only). */
+ * per column of T_r): s = e(block max) - 8, at least -127 (the scale is a
+ * UE8M0 number), so the block's largest magnitude scales into [128, 256),
+ * then round to nearest even; the leaf product sums 2^(sa + sb) times each
+ * block's E4M3 products in FP32, the tensor core applying the scales
+ * (block-scaled MMA; FMM_FP8_FOLD=1 in the environment, read once, folds
+ * each block's product in the epilogue instead).  Pass schedule only. */
 enum { FMM_LEAF_BF16 = 0, FMM_LEAF_F16 = 1, FMM_LEAF_BF16X3 = 2, FMM_LEAF_E4M3B128 = 3 };
 
 /*

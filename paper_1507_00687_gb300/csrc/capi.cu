@@ -548,10 +548,6 @@ static fmm_status run_pass_fp8(const Plan* p, const Source& x, const Source& y, 
   float* sb = reinterpret_cast<float*>(w + ba + fa + bb);
   float* mbuf = reinterpret_cast<float*>(w + ba + fa + bb + fbb);
   CombineArgs ca = combine_args(p, g, x, 0, leaves, wa), cb = combine_args(p, g, y, 1, leaves, wb);
-  if (!e4m3_combine_fits(ca) || !e4m3_combine_fits(cb)) {
-    t_last_error = "E4M3 leaves: too many input blocks per operand for the combination pass";
-    return FMM_ERR_UNSUPPORTED;
-  }
   // both sides K-major: [leaf][t][k]
   ca.p_rows = g.tp_a;
   ca.p_cols = g.kp;

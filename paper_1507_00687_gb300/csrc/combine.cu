@@ -20,6 +20,7 @@
 // each input element is read once from DRAM, each output element written
 // once.
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 #include <cuda_bf16.h>
@@ -1072,6 +1073,42 @@ cudaError_t launch_convert_batched(const CombineArgs* args, const int64_t* start
 constexpr int kF8TT = 16;
 constexpr int kF8Stride = 132;
 
+// The row's four sums of one leaf (lanes: 4 consecutive k each, 128 k per
+// warp): the block's max |sum| across the warp, s = e(max) - 8 (0 for a
+// zero block; at least -127, the smallest UE8M0 scale, so blocks whose max
+// is below 2^-120 use E4M3 subnormals), sum 2^-s rounded to E4M3 (ties to
+// even), the 4 bytes stored, and the block's scale (lane 0): the factor 2^s
+// or, with sf_atoms, the UE8M0 byte s + 127 at the row's place in the
+// block-scale atom.
+__device__ __forceinline__ void e4m3_store_row(const CombineArgs& a, int r, int64_t t, int64_t k0, int lane,
+                                               const float (&acc)[4]) {
+  float m = fmaxf(fmaxf(fabsf(acc[0]), fabsf(acc[1])), fmaxf(fabsf(acc[2]), fabsf(acc[3])));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  bool nf = false;
+  const int e = fexp_f32(__float_as_uint(m), &nf);
+  const int sc = m > 0.f ? max(e - 8, -127) : 0;
+  uint32_t packed = 0;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float2 pr = make_float2(scale_pow2(acc[2 * j], -sc), scale_pow2(acc[2 * j + 1], -sc));
+    const uint32_t q = (uint32_t)__nv_cvt_float2_to_fp8x2(pr, __NV_SATFINITE, __NV_E4M3);
+    packed |= q << (16 * j);
+  }
+  unsigned char* out = static_cast<unsigned char*>(a.out);
+  *reinterpret_cast<uint32_t*>(out + ((int64_t)r * a.p_rows + t) * a.p_cols + k0 + 4 * lane) = packed;
+  if (lane == 0) {
+    const int64_t kb = k0 / 128, nkb = a.p_cols / 128;
+    if (a.sf_atoms) {
+      const int64_t atom = ((int64_t)r * nkb + kb) * (a.p_rows / 128) + t / 128;
+      reinterpret_cast<uint32_t*>(a.scale_out)[atom * 128 + (t % 32) * 4 + (t % 128) / 32] =
+          (uint32_t)(sc + 127) * 0x01010101u;
+    } else {
+      a.scale_out[((int64_t)r * nkb + kb) * a.p_rows + t] = exp2i(sc);
+    }
+  }
+}
+
 template <int DT, int TT>
 __global__ void __launch_bounds__(TT * 32) combine_e4m3_kernel(const CombineArgs a) {
   extern __shared__ float f8tile[];  // [block][TT][kF8Stride], then the term list
@@ -1130,9 +1167,7 @@ __global__ void __launch_bounds__(TT * 32) combine_e4m3_kernel(const CombineArgs
     }
   }
   __syncthreads();
-  unsigned char* out = static_cast<unsigned char*>(a.out);
   const int64_t t = t0 + warp;
-  const int64_t kb = k0 / 128, nkb = a.p_cols / 128;
   int tt = 0;
   for (int r = 0; r < R; ++r) {
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1145,48 +1180,82 @@ __global__ void __launch_bounds__(TT * 32) combine_e4m3_kernel(const CombineArgs
       acc[2] = fmaf(coef, v.z, acc[2]);
       acc[3] = fmaf(coef, v.w, acc[3]);
     }
-    float m = fmaxf(fmaxf(fabsf(acc[0]), fabsf(acc[1])), fmaxf(fabsf(acc[2]), fabsf(acc[3])));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    bool nf = false;
-    const int e = fexp_f32(__float_as_uint(m), &nf);
-    // the UE8M0 scale range bounds s below by -127 (blocks whose max is below 2^-120)
-    const int sc = m > 0.f ? max(e - 8, -127) : 0;
-    uint32_t packed = 0;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const float2 pr = make_float2(scale_pow2(acc[2 * j], -sc), scale_pow2(acc[2 * j + 1], -sc));
-      const uint32_t q = (uint32_t)__nv_cvt_float2_to_fp8x2(pr, __NV_SATFINITE, __NV_E4M3);
-      packed |= q << (16 * j);
-    }
-    *reinterpret_cast<uint32_t*>(out + ((int64_t)r * a.p_rows + t) * a.p_cols + k0 + 4 * lane) = packed;
-    if (lane == 0) {
-      if (a.sf_atoms) {
-        const int64_t atom = ((int64_t)r * nkb + kb) * (a.p_rows / 128) + t / 128;
-        reinterpret_cast<uint32_t*>(a.scale_out)[atom * 128 + (t % 32) * 4 + (t % 128) / 32] =
-            (uint32_t)(sc + 127) * 0x01010101u;
-      } else {
-        a.scale_out[((int64_t)r * nkb + kb) * a.p_rows + t] = exp2i(sc);
-      }
-    }
+    e4m3_store_row(a, r, t, k0, lane, acc);
   }
 }
 
-bool e4m3_combine_fits(const CombineArgs& a) {
-  const size_t list = (size_t)a.t_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
-  return (size_t)(a.n_rb * a.n_cb) * 4 * kF8Stride * 4 + list <= kStagedSmemMax;
+// Unstaged form for operands with more input blocks than the staged tiles
+// hold: one warp per row t of a 16-row, 128-k window, each term's four
+// elements per lane loaded straight from the source (the window's input
+// tiles are reused from L1 / L2 across terms and warps), scaled and summed
+// in term order as above, so the sums and their rounding are the staged
+// kernel's.
+template <int DT>
+__global__ void __launch_bounds__(kF8TT * 32) combine_e4m3_direct_kernel(const CombineArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t0 = (int64_t)blockIdx.y * kF8TT, k0 = (int64_t)blockIdx.x * 128;
+  const int64_t t = t0 + warp;
+  const int R = (int)a.num_leaves;
+  // this lane's memory positions inside a block: (row, column) offsets of
+  // (t, k0 + 4 lane + j), j = 0..3
+  const int64_t lt = t0 + warp, lk = k0 + 4 * lane;
+  for (int r = 0; r < R; ++r) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int t1 = __ldg(a.t_start + r + 1);
+    for (int tt = __ldg(a.t_start + r); tt < t1; ++tt) {
+      const int32_t blk = __ldg(a.t_blk + tt);
+      const int64_t bt = (blk >> a.blk_t_shift) & 0xFFFF, bk = (blk >> a.blk_k_shift) & 0xFFFF;
+      const float coef = __ldg(a.t_coef + tt);
+      const int64_t rb = a.t_rows ? bt : bk, cb = a.t_rows ? bk : bt;
+      const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows), nc = min(a.b_cols, a.cols - cb * a.b_cols);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t lr = a.t_rows ? lt : lk + j, lc = a.t_rows ? lk + j : lt;
+        float v = 0.f;
+        if (lr < nr && lc < nc) {
+          const int64_t gr = rb * a.b_rows + lr, gc = cb * a.b_cols + lc;
+          const int er = (a.re ? a.rs * __ldg(a.re + gr) : 0) + (a.ce ? a.cs * __ldg(a.ce + gc) : 0);
+          v = scale_pow2(load_elem<DT>(a.src, gr * a.ld + gc), er);
+        }
+        acc[j] = fmaf(coef, v, acc[j]);
+      }
+    }
+    e4m3_store_row(a, r, t, k0, lane, acc);
+  }
+}
+
+// FMM_E4M3_DIRECT=1 in the environment (read once): the unstaged E4M3
+// combination whatever the block count (testing: it must give the staged
+// kernel's bytes and scales exactly).
+static bool e4m3_direct_forced() {
+  static bool on = [] {
+    const char* s = std::getenv("FMM_E4M3_DIRECT");
+    return s && std::atoi(s) != 0;
+  }();
+  return on;
 }
 
 cudaError_t launch_combine_e4m3(const CombineArgs& a, cudaStream_t st) {
   if (a.p_rows % kF8TT != 0 || a.p_cols % 128 != 0 || (a.sf_atoms && a.p_rows % 128 != 0)) return cudaErrorInvalidValue;
   const int64_t nb = a.n_rb * a.n_cb;
   const size_t list = (size_t)a.t_nnz * 8 + (size_t)(a.num_leaves + 1) * 4;
-  // sixteen rows per CTA when the staged tiles fit, else four
+  // sixteen rows per CTA when the staged tiles fit, else four, else the
+  // unstaged kernel (sixteen rows)
   const bool wide = (size_t)nb * kF8TT * kF8Stride * 4 + list <= kStagedSmemMax;
   const int tt = wide ? kF8TT : 4;
   const size_t smem = (size_t)nb * tt * kF8Stride * 4 + list;
-  if (smem > kStagedSmemMax || a.p_rows / tt > 65535) return cudaErrorNotSupported;
+  if (a.p_rows / 4 > 65535) return cudaErrorNotSupported;
   if (a.num_leaves == 0 || a.p_rows == 0 || a.p_cols == 0) return cudaSuccess;
+  if (smem > kStagedSmemMax || e4m3_direct_forced()) {
+    const dim3 grid((unsigned)(a.p_cols / 128), (unsigned)(a.p_rows / kF8TT));
+    KernelTimer timer("combine", st);
+    switch (a.dtype) {
+      case kF32: combine_e4m3_direct_kernel<kF32><<<grid, kF8TT * 32, 0, st>>>(a); break;
+      case kBF16: combine_e4m3_direct_kernel<kBF16><<<grid, kF8TT * 32, 0, st>>>(a); break;
+      default: combine_e4m3_direct_kernel<kF16><<<grid, kF8TT * 32, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
   static bool attr_done[64][6] = {};
   int dev = 0;
   cudaGetDevice(&dev);

@@ -162,10 +162,10 @@ struct CombineArgs {
 };
 
 // E4M3 combination pass (see CombineArgs::scale_out); a.p_rows / p_cols are
-// the padded t / k extents whatever the source's layout.
+// the padded t / k extents whatever the source's layout.  Input tiles are
+// staged in shared memory when they fit, else read per term (any number of
+// input blocks).
 cudaError_t launch_combine_e4m3(const CombineArgs& a, cudaStream_t st);
-// Whether the E4M3 combination pass can stage the operand's input blocks.
-bool e4m3_combine_fits(const CombineArgs& a);
 
 // Multiply kernel for E4M3 leaves: stored products only, both operands
 // K-major bytes ([leaf][t][k], tensor maps with 128 x 128 byte boxes), one

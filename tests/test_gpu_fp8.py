@@ -1,6 +1,10 @@
 """E4M3 leaves with power-of-two scales per 128-block along K against the
 oracle: exact on small integers, the oracle's block quantization to within
 FP32 accumulation, and the parity tolerance on real and scaled inputs."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 import torch
@@ -51,14 +55,56 @@ def test_e4m3_deep_plans_integers_exact(api, names):
         assert np.array_equal(got, A @ B), dt
 
 
-def test_e4m3_refuses_too_many_input_blocks(api):
-    # 16 x 16 input blocks per operand (Strassen, four levels) exceed what
-    # the E4M3 combination pass stages: refused before any launch
-    from paper_1507_00687_gb300 import _native as N
-    A = to_dev(inputs.integers((128, 128), -1, 1, seed=1), "f32")
-    with pytest.raises(N.FmmError) as e:
-        api.multiply(api.Plan(["strassen"] * 4, "e4m3b128"), A, A)
-    assert e.value.code == 10
+def test_e4m3_many_input_blocks_integers_exact(api):
+    # 16 x 16 input blocks per operand (Strassen, four levels) are more than
+    # the E4M3 combination pass stages in shared memory: the unstaged form
+    # reads each term's elements directly.  Entries in [-1, 1]: every S, T
+    # entry is an integer of magnitude at most 16 (exact in E4M3).
+    A = inputs.integers((256, 384), -1, 1, seed=1)
+    B = inputs.integers((384, 320), -1, 1, seed=2)
+    got = dev_values(api.multiply(api.Plan(["strassen"] * 4, "e4m3b128"), to_dev(A, "f32"), to_dev(B, "f32")))
+    api.sync_status()
+    assert np.array_equal(got, A @ B)
+
+
+def test_e4m3_unstaged_combination_and_fold_kernel_match(api, tmp_path):
+    # The unstaged combination (forced for every plan) must give the staged
+    # kernel's E4M3 operands and scales exactly, so the products are equal
+    # bit for bit; the folding multiply kernel (FMM_FP8_FOLD=1) must match
+    # the oracle's block quantization as the block-scaled one does.  Child
+    # processes: both settings are read once per process.
+    code = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, '.'); sys.path.insert(0, 'tests')
+from paper_1507_00687_gb300 import api, inputs
+A = torch.from_numpy(inputs.uniform((384, 640), -1, 1, seed=31)).float().cuda()
+B = torch.from_numpy(inputs.uniform((640, 320), -1, 1, seed=32)).float().cuda()
+A[:, :100] *= 2.0 ** -9
+B[200:, :] *= 2.0 ** 7
+out = {}
+for names in (["strassen"], ["winograd", "classical121"]):
+    out["-".join(names)] = api.multiply(api.Plan(names, "e4m3b128"), A, B).cpu().numpy()
+api.sync_status()
+np.savez(sys.argv[1], **out)
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for tag, extra in (("base", {}), ("direct", {"FMM_E4M3_DIRECT": "1"}), ("fold", {"FMM_FP8_FOLD": "1"})):
+        path = str(tmp_path / f"{tag}.npz")
+        r = subprocess.run([sys.executable, "-c", code, path], cwd=root, env=dict(os.environ, **extra),
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stdout + r.stderr
+        res[tag] = dict(np.load(path))
+    for k in res["base"]:
+        assert np.array_equal(res["base"][k], res["direct"][k]), k
+    A64 = inputs.uniform((384, 640), -1, 1, seed=31).astype(np.float32).astype(np.float64)
+    B64 = inputs.uniform((640, 320), -1, 1, seed=32).astype(np.float32).astype(np.float64)
+    A64[:, :100] *= 2.0 ** -9
+    B64[200:, :] *= 2.0 ** 7
+    emu = OF.fmm(A64, B64, oracle_tree(["strassen"]), leaf=OF.leaf_e4m3_b128, dtype=np.float32).astype(np.float64)
+    _, G = oracle_reference(A64, B64, ["strassen"])
+    for tag in ("base", "fold"):
+        assert np.all(np.abs(res[tag]["strassen"] - emu) <= (320 + 16) * 2.0 ** -23 * G), tag
 
 
 @pytest.mark.parametrize("names", [["strassen"], ["winograd"], []], ids=lambda n: "-".join(n) or "classical")
