@@ -52,10 +52,11 @@ def parse():
     ap.add_argument("--schedule", default="auto", choices=["auto", "pass", "load_stage", "pass_accumulate"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator / variant timings")
     ap.add_argument("--batch", type=int, default=512, help="products in the batched workload extra (0: skip)")
-    ap.add_argument("--experiment", default="", choices=["", "scaling_accuracy", "batch", "oracle_timing"],
+    ap.add_argument("--experiment", default="", choices=["", "scaling_accuracy", "batch", "oracle_timing", "linear"],
                     help="scaling_accuracy: relative error of Strassen, L = 1..6, under each scaling (Sec. 6.5); "
                          "batch: the batched workload alone (--batch products); oracle_timing: the float64 "
-                         "oracle on the host cores, single-threaded and on all cores, n = 256, 4096, 8192")
+                         "oracle on the host cores, single-threaded and on all cores, n = 256, 4096, 8192; linear: the "
+                         "linear layer X[8192,4096] W[4096,4096] forward and backward alone")
     ap.add_argument("--samples", type=int, default=100, help="samples per distribution (--experiment)")
     ap.add_argument("--exp-n", type=int, default=2000, help="matrix size (--experiment)")
     return ap.parse_args()
@@ -637,6 +638,13 @@ def main():
         build.build()
         from paper_1507_00687_gb300 import api, inputs
         print(json.dumps({"experiment": "batch", **batched_workload(api, inputs, torch, max(1, args.batch))}))
+        return
+    if args.experiment == "linear":
+        import torch
+        from paper_1507_00687_gb300 import build
+        build.build()
+        from paper_1507_00687_gb300 import api
+        print(json.dumps({"experiment": "linear", **linear_layer_workload(api, torch)}))
         return
     import torch
     import torch.distributed as dist
