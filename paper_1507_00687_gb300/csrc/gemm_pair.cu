@@ -51,19 +51,37 @@ using gemm::tma_load_2d_pair;
 constexpr int BM = 256, BN = 256;  // tile of the pair
 constexpr int HM = 128, HN = 128;  // this CTA's rows of A, columns of B
 
-template <int FMT>
+// Pipeline depth: the most 64-wide K stages that fit in 212 KB, less
+// FMM_PAIR_SINGLE_STAGE_CUT for one product and FMM_PAIR_BATCH_STAGE_CUT for
+// batches (never below three), which leaves the rest of the SM's 256 KB of
+// shared memory and L1 to L1.  Measured on the 512-product batch (bf16):
+// six stages and a 2048-entry unit cache 706 TFLOP/s, five 737, four with a
+// 1024-entry cache 745; without the cache 696-703.
+#ifndef FMM_PAIR_SINGLE_STAGE_CUT
+#define FMM_PAIR_SINGLE_STAGE_CUT 0
+#endif
+#ifndef FMM_PAIR_BATCH_STAGE_CUT
+#define FMM_PAIR_BATCH_STAGE_CUT 2
+#endif
+#ifndef FMM_PAIR_UNIT_CACHE
+#define FMM_PAIR_UNIT_CACHE 1024
+#endif
+
+template <int FMT, bool BATCH = false>
 struct Cfg {
   static constexpr int BK = 64;
   static constexpr int kSplit = FMT == FMM_LEAF_BF16X3 ? 2 : 1;
   static constexpr int kATile = HM * BK * 2;
   static constexpr int kBTile = HN * BK * 2;
   static constexpr int kStage = kSplit * (kATile + kBTile);
-  static constexpr int kStages = (212 * 1024) / kStage > 8 ? 8 : (212 * 1024) / kStage;
+  static constexpr int kStagesMax = (212 * 1024) / kStage > 8 ? 8 : (212 * 1024) / kStage;
+  static constexpr int kCut = BATCH ? FMM_PAIR_BATCH_STAGE_CUT : FMM_PAIR_SINGLE_STAGE_CUT;
+  static constexpr int kStages = kStagesMax - kCut >= 3 ? kStagesMax - kCut : (kStagesMax < 3 ? kStagesMax : 3);
   static constexpr int kTmemCols = 2 * BN;
   static constexpr int kBarBytes = 256;
-  static constexpr int kUnitCache = 2048;  // batch unit table entries kept in shared memory
-  // + alignment slack; a batched launch also keeps its unit numbering
-  static constexpr int smem(bool batch) { return kStages * kStage + kBarBytes + (batch ? kUnitCache * 8 : 0) + 1024; }
+  static constexpr int kUnitCache = BATCH ? FMM_PAIR_UNIT_CACHE : 0;  // batch unit table entries in shared memory
+  // + alignment slack
+  static constexpr int kSmem = kStages * kStage + kBarBytes + kUnitCache * 8 + 1024;
 };
 
 __device__ __forceinline__ uint32_t cluster_id_x() {
@@ -125,7 +143,7 @@ template <int FMT, bool A_MN, bool B_MN, int EPI, bool BATCH>
 __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __grid_constant__ PairLaunch launch) {
   const DirectArgs& args = launch.one;
   constexpr int kMmaWarp = EPI, kTmaWarp = EPI + 1;
-  using C = Cfg<FMT>;
+  using C = Cfg<FMT, BATCH>;
   constexpr int BK = C::BK;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -409,9 +427,9 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
 template <int FMT, bool A_MN, bool B_MN, int EPI, bool BATCH>
 cudaError_t launch_cfg(const DirectArgs& a, const DirectArgs* tab, const int64_t* unit_start, int count,
                        int64_t total_units, cudaStream_t st) {
-  using C = Cfg<FMT>;
+  using C = Cfg<FMT, BATCH>;
   auto kern = pair_fmm_kernel<FMT, A_MN, B_MN, EPI, BATCH>;
-  constexpr int kSmem = C::smem(BATCH);
+  constexpr int kSmem = C::kSmem;
   static bool attr_set[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
