@@ -178,6 +178,29 @@ static bool make_map_sw(CUtensorMap* m, const void* ptr, bool f16, int64_t rows,
   return true;
 }
 
+// A 2-D tensor map over a row-major fp32 matrix (rows x cols, ld) with
+// 32 x 32 boxes in the 128-byte-swizzle layout (bulk tensor stores of the
+// multiply epilogue's chunks).
+static bool make_map_f32_sw128(CUtensorMap* m, const void* ptr, int64_t rows, int64_t cols, int64_t ld) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    t_last_error = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  const cuuint32_t box[2] = {32u, 32u};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    t_last_error = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
 // Rows of X start on 16-byte boundaries (the reductions' vector path).
 static int vec_aligned_host(const void* X, int64_t ld, int dt) {
   const int es = dt == FMM_DT_F32 ? 4 : 2;
@@ -330,6 +353,17 @@ static SideStream* side_stream() {
   return &s;
 }
 
+// The CTA-pair multiply writes stored products with bulk tensor stores
+// from shared memory (whole 128-byte rows); FMM_TMA_STORE=0 in the
+// environment (read once) keeps per-thread stores.
+static bool tma_store_enabled() {
+  static bool on = [] {
+    const char* s = std::getenv("FMM_TMA_STORE");
+    return !(s && std::atoi(s) == 0);
+  }();
+  return on;
+}
+
 static bool pair_tiles_enabled() {
   static bool on = [] {
     const char* s = std::getenv("FMM_TILE_PAIRS");
@@ -457,6 +491,11 @@ static bool direct_args(const Plan* p, const PassGeom& g, const Source& x, const
   d->tp_b = g.tp_b;
   d->kp = g.kp;
   d->mbuf = mbuf;
+  // CTA pairs store M_r by bulk tensor copies (FMM_TMA_STORE=0: plain stores)
+  if (mbuf && g.pair && tma_store_enabled()) {
+    if (!make_map_f32_sw128(&d->map_m, mbuf, g.R * g.tp_a, g.tp_b, g.tp_b)) return false;
+    d->tma_store = 1;
+  }
   d->status = status;
   d->timeout_ns = timeout_ns();
   d->stall_test = stall_test();

@@ -47,6 +47,11 @@ using gemm::epi_chunk;
 using gemm::epi_chunk_red;
 using gemm::mbar_arrive_expect_tx;
 using gemm::tma_load_2d_pair;
+using gemm::bulk_commit;
+using gemm::bulk_wait;
+using gemm::bulk_wait_read;
+using gemm::fence_proxy_async_shared;
+using gemm::tma_store_2d;
 
 constexpr int BM = 256, BN = 256;  // tile of the pair
 constexpr int HM = 128, HN = 128;  // this CTA's rows of A, columns of B
@@ -67,7 +72,7 @@ constexpr int HM = 128, HN = 128;  // this CTA's rows of A, columns of B
 #define FMM_PAIR_UNIT_CACHE 1024
 #endif
 
-template <int FMT, bool BATCH = false>
+template <int FMT, bool BATCH = false, bool TSTORE = false>
 struct Cfg {
   static constexpr int BK = 64;
   static constexpr int kSplit = FMT == FMM_LEAF_BF16X3 ? 2 : 1;
@@ -80,9 +85,19 @@ struct Cfg {
   static constexpr int kTmemCols = 2 * BN;
   static constexpr int kBarBytes = 256;
   static constexpr int kUnitCache = BATCH ? FMM_PAIR_UNIT_CACHE : 0;  // batch unit table entries in shared memory
+  // TSTORE: two 32 x 32 fp32 staging buffers (4 KB, 128-byte swizzle) per
+  // epilogue warp (four) for the bulk tensor stores of M_r
+  static constexpr int kEpiBuf = TSTORE ? 4 * 2 * 4096 : 0;
   // + alignment slack
-  static constexpr int kSmem = kStages * kStage + kBarBytes + kUnitCache * 8 + 1024;
+  static constexpr int kSmem = kStages * kStage + kEpiBuf + kBarBytes + kUnitCache * 8 + 1024;
 };
+
+// The configuration of one kernel instantiation: single products with four
+// epilogue warps store M_r by bulk tensor stores.  The kernel and its
+// launcher both take it from here, so the shared memory the launch gives is
+// the layout the kernel uses.
+template <int FMT, bool BATCH, int EPI>
+using CfgFor = Cfg<FMT, BATCH, !BATCH && EPI == 4>;
 
 __device__ __forceinline__ uint32_t cluster_id_x() {
   uint32_t r;
@@ -143,12 +158,14 @@ template <int FMT, bool A_MN, bool B_MN, int EPI, bool BATCH>
 __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __grid_constant__ PairLaunch launch) {
   const DirectArgs& args = launch.one;
   constexpr int kMmaWarp = EPI, kTmaWarp = EPI + 1;
-  using C = Cfg<FMT, BATCH>;
+  using C = CfgFor<FMT, BATCH, EPI>;
+  constexpr bool kTStore = C::kEpiBuf > 0;
   constexpr int BK = C::BK;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStage);
+  uint8_t* epibuf = smem + C::kStages * C::kStage;  // 1024-aligned
+  uint64_t* full = reinterpret_cast<uint64_t*>(epibuf + C::kEpiBuf);
   uint64_t* empty = full + C::kStages;
   uint64_t* tfull = empty + C::kStages;
   uint64_t* tempty = tfull + 2;
@@ -156,7 +173,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
   uint64_t* never = drain + 1;  // no thread ever arrives here (timeout-path test)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  int64_t* ustart = reinterpret_cast<int64_t*>(smem + C::kStages * C::kStage + C::kBarBytes);
+  int64_t* ustart = reinterpret_cast<int64_t*>(epibuf + C::kEpiBuf + C::kBarBytes);
 
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
@@ -375,6 +392,11 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
     constexpr int kChunks = BN / 32 / (EPI / 4);  // 32-column chunks per warp
     const int row = (int)rank * HM + quarter * 32 + lane;  // tile row of this thread (TMEM lane = row mod 128)
     const uint32_t tempty0 = mapa_shared(smem_u32(&tempty[0]), 0u);
+    // bulk tensor stores of M_r: this warp's two staging buffers, chunks
+    // stored so far (buffer = count mod 2)
+    const bool tstore = kTStore && args.tma_store && args.mbuf;
+    const uint32_t sbuf0 = smem_u32(epibuf) + (uint32_t)(kTStore ? warp * 8192 : 0);
+    uint32_t nstored = 0;
     for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
       const DirectArgs& a = prob(w);
       const int64_t leaf = w.leaf, tn = w.tn;
@@ -389,7 +411,26 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
       for (int cc = half * kChunks; cc < (half + 1) * kChunks; ++cc) {
         uint32_t r[32];
         tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + cc * 32, r);
-        if (mrow) {
+        if (kTStore && tstore) {
+          // the store that last used this buffer (two chunks ago) has read it
+          if (lane == 0 && nstored >= 2) bulk_wait_read<1>();
+          __syncwarp();
+          // row `lane` of the 32 x 32 chunk, 16-byte piece q at q xor (row mod 8)
+          const uint32_t sb = sbuf0 + (nstored & 1u) * 4096u + (uint32_t)lane * 128u;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sb + (uint32_t)((q ^ (lane & 7)) * 16)),
+                         "r"(r[4 * q]), "r"(r[4 * q + 1]), "r"(r[4 * q + 2]), "r"(r[4 * q + 3])
+                         : "memory");
+          fence_proxy_async_shared();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&args.map_m, sbuf0 + (nstored & 1u) * 4096u, (int32_t)(tn * BN + cc * 32),
+                         (int32_t)(leaf * a.tp_a + w.tm * BM + (int64_t)rank * HM + quarter * 32));
+            bulk_commit();
+          }
+          ++nstored;
+        } else if (mrow) {
 #pragma unroll
           for (int q = 0; q < 8; ++q)
             *reinterpret_cast<uint4*>(mrow + cc * 32 + 4 * q) =
@@ -405,6 +446,10 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
       ++acc_iter;
     }
     if (!ok && lane == 0) stop();
+    // every bulk store of this warp complete before the CTA leaves (its
+    // shared memory stays valid, its writes visible to the next kernel)
+    if (kTStore && lane == 0 && nstored > 0) bulk_wait<0>();
+    __syncwarp();
   }
 
   tc_fence_before();
@@ -427,7 +472,7 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
 template <int FMT, bool A_MN, bool B_MN, int EPI, bool BATCH>
 cudaError_t launch_cfg(const DirectArgs& a, const DirectArgs* tab, const int64_t* unit_start, int count,
                        int64_t total_units, cudaStream_t st) {
-  using C = Cfg<FMT, BATCH>;
+  using C = CfgFor<FMT, BATCH, EPI>;
   auto kern = pair_fmm_kernel<FMT, A_MN, B_MN, EPI, BATCH>;
   constexpr int kSmem = C::kSmem;
   static bool attr_set[64] = {false};

@@ -213,6 +213,11 @@ cudaError_t launch_combine_pair_stream(const CombineArgs& a0, const CUtensorMap&
 struct DirectArgs {
   alignas(64) CUtensorMap map_a;
   alignas(64) CUtensorMap map_b;
+  // CTA-pair kernel, stored products: M_r as a 2-D fp32 tensor (R * tp_a
+  // rows of tp_b), boxes of 32 x 32 with the 128-byte swizzle, for bulk
+  // tensor stores of the epilogue's chunks (tma_store set)
+  alignas(64) CUtensorMap map_m;
+  int tma_store;
   EpilogueArgs c;
   const LeafDesc* leaves;
   int64_t num_leaves;
