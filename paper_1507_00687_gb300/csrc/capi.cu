@@ -1131,6 +1131,13 @@ static fmm_status batch_build(Batch* b, const fmm_problem* probs) {
       if (!make_map_sw(&dir[u].map_a, q.A, false, q.M, q.K, q.lda, 64, 128) ||
           !make_map_sw(&dir[u].map_b, q.B, false, q.K, q.N, q.ldb, 64, 64))
         return FMM_ERR_CUDA;
+      // and C written by bulk tensor stores where its rows allow (the
+      // stores clip the tiles' padding at C's edges)
+      dir[u].tma_store = 0;
+      if (tma_store_enabled() && (uintptr_t)q.C % 16 == 0 && (q.ldc * 4) % 16 == 0 && q.M >= 32 && q.N >= 32) {
+        if (!make_map_f32_sw128(&dir[u].map_m, q.C, q.M, q.N, q.ldc)) return FMM_ERR_CUDA;
+        dir[u].tma_store = 1;
+      }
     }
     const int64_t tiles = (g.tp_a / tm_rows) * (g.tp_b / tn_cols);
     units[u] = mbuf ? g.R * tiles : tiles;

@@ -86,18 +86,21 @@ struct Cfg {
   static constexpr int kBarBytes = 256;
   static constexpr int kUnitCache = BATCH ? FMM_PAIR_UNIT_CACHE : 0;  // batch unit table entries in shared memory
   // TSTORE: two 32 x 32 fp32 staging buffers (4 KB, 128-byte swizzle) per
-  // epilogue warp (four) for the bulk tensor stores of M_r
-  static constexpr int kEpiBuf = TSTORE ? 4 * 2 * 4096 : 0;
+  // epilogue warp (four for one product, eight for batches) for bulk
+  // tensor stores of M_r or C
+  static constexpr int kEpiBuf = TSTORE ? (BATCH ? 8 : 4) * 2 * 4096 : 0;
   // + alignment slack
   static constexpr int kSmem = kStages * kStage + kEpiBuf + kBarBytes + kUnitCache * 8 + 1024;
+  static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
 // The configuration of one kernel instantiation: single products with four
-// epilogue warps store M_r by bulk tensor stores.  The kernel and its
-// launcher both take it from here, so the shared memory the launch gives is
-// the layout the kernel uses.
+// epilogue warps store M_r, and batches (eight epilogue warps, 16-bit
+// leaves: bf16x3 stages leave no room) store the C of their direct entries,
+// by bulk tensor stores.  The kernel and its launcher both take it from
+// here, so the shared memory the launch gives is the layout the kernel uses.
 template <int FMT, bool BATCH, int EPI>
-using CfgFor = Cfg<FMT, BATCH, !BATCH && EPI == 4>;
+using CfgFor = Cfg<FMT, BATCH, BATCH ? (EPI == 8 && FMT != FMM_LEAF_BF16X3) : EPI == 4>;
 
 __device__ __forceinline__ uint32_t cluster_id_x() {
   uint32_t r;
@@ -392,9 +395,9 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
     constexpr int kChunks = BN / 32 / (EPI / 4);  // 32-column chunks per warp
     const int row = (int)rank * HM + quarter * 32 + lane;  // tile row of this thread (TMEM lane = row mod 128)
     const uint32_t tempty0 = mapa_shared(smem_u32(&tempty[0]), 0u);
-    // bulk tensor stores of M_r: this warp's two staging buffers, chunks
-    // stored so far (buffer = count mod 2)
-    const bool tstore = kTStore && args.tma_store && args.mbuf;
+    // bulk tensor stores of M_r (stored products) or of C (batch entries
+    // whose C is the product itself): this warp's two staging buffers,
+    // chunks stored so far (buffer = count mod 2)
     const uint32_t sbuf0 = smem_u32(epibuf) + (uint32_t)(kTStore ? warp * 8192 : 0);
     uint32_t nstored = 0;
     for (Cursor w = first(); w.u < total_units && ok; advance(w)) {
@@ -407,29 +410,41 @@ __global__ void __launch_bounds__((EPI + 2) * 32, 1) pair_fmm_kernel(const __gri
       tc_fence_after();
       const LeafDesc* L = a.leaves + leaf;
       float* mrow = a.mbuf ? a.mbuf + (leaf * a.tp_a + ml) * a.tp_b + tn * BN : nullptr;
+      const bool tstore = kTStore && a.tma_store;
+      // C stores: the leaf's single C term's coefficient, rows of this warp
+      const float ccoef = (tstore && !a.mbuf) ? __ldg(&L->c_coef[0]) : 1.f;
+      const int64_t wrow = w.tm * BM + (int64_t)rank * HM + quarter * 32;
 #pragma unroll 1
       for (int cc = half * kChunks; cc < (half + 1) * kChunks; ++cc) {
         uint32_t r[32];
         tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + cc * 32, r);
         if (kTStore && tstore) {
-          // the store that last used this buffer (two chunks ago) has read it
-          if (lane == 0 && nstored >= 2) bulk_wait_read<1>();
-          __syncwarp();
-          // row `lane` of the 32 x 32 chunk, 16-byte piece q at q xor (row mod 8)
-          const uint32_t sb = sbuf0 + (nstored & 1u) * 4096u + (uint32_t)lane * 128u;
+          const int64_t bx = tn * BN + cc * 32, by = a.mbuf ? leaf * a.tp_a + wrow : wrow;
+          // a C box wholly outside C (tile padding) is not stored
+          if (a.mbuf || (by < a.c.M && bx < a.c.N)) {
+            if (!a.mbuf) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sb + (uint32_t)((q ^ (lane & 7)) * 16)),
-                         "r"(r[4 * q]), "r"(r[4 * q + 1]), "r"(r[4 * q + 2]), "r"(r[4 * q + 3])
-                         : "memory");
-          fence_proxy_async_shared();
-          __syncwarp();
-          if (lane == 0) {
-            tma_store_2d(&args.map_m, sbuf0 + (nstored & 1u) * 4096u, (int32_t)(tn * BN + cc * 32),
-                         (int32_t)(leaf * a.tp_a + w.tm * BM + (int64_t)rank * HM + quarter * 32));
-            bulk_commit();
+              for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(ccoef * __uint_as_float(r[j]));
+            }
+            // the store that last used this buffer (two chunks ago) has read it
+            if (lane == 0 && nstored >= 2) bulk_wait_read<1>();
+            __syncwarp();
+            // row `lane` of the 32 x 32 chunk, 16-byte piece q at q xor (row mod 8)
+            const uint32_t sb = sbuf0 + (nstored & 1u) * 4096u + (uint32_t)lane * 128u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sb + (uint32_t)((q ^ (lane & 7)) * 16)),
+                           "r"(r[4 * q]), "r"(r[4 * q + 1]), "r"(r[4 * q + 2]), "r"(r[4 * q + 3])
+                           : "memory");
+            fence_proxy_async_shared();
+            __syncwarp();
+            if (lane == 0) {
+              // the map of M_r (one product) or of this entry's C (batches)
+              tma_store_2d(&a.map_m, sbuf0 + (nstored & 1u) * 4096u, (int32_t)bx, (int32_t)by);
+              bulk_commit();
+            }
+            ++nstored;
           }
-          ++nstored;
         } else if (mrow) {
 #pragma unroll
           for (int q = 0; q < 8; ++q)
