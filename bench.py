@@ -52,11 +52,12 @@ def parse():
     ap.add_argument("--schedule", default="auto", choices=["auto", "pass", "load_stage", "pass_accumulate"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator / variant timings")
     ap.add_argument("--batch", type=int, default=512, help="products in the batched workload extra (0: skip)")
-    ap.add_argument("--experiment", default="", choices=["", "scaling_accuracy", "batch", "oracle_timing", "linear"],
+    ap.add_argument("--experiment", default="", choices=["", "scaling_accuracy", "batch", "oracle_timing", "linear", "precision"],
                     help="scaling_accuracy: relative error of Strassen, L = 1..6, under each scaling (Sec. 6.5); "
                          "batch: the batched workload alone (--batch products); oracle_timing: the float64 "
                          "oracle on the host cores, single-threaded and on all cores, n = 256, 4096, 8192; linear: the "
-                         "linear layer X[8192,4096] W[4096,4096] forward and backward alone")
+                         "linear layer X[8192,4096] W[4096,4096] forward and backward alone; precision: the precision "
+                         "sweep alone")
     ap.add_argument("--samples", type=int, default=100, help="samples per distribution (--experiment)")
     ap.add_argument("--exp-n", type=int, default=2000, help="matrix size (--experiment)")
     return ap.parse_args()
@@ -271,42 +272,58 @@ def fp8_peak_probe(torch, n: int = 8192, reps: int = 10) -> dict:
 
 def precision_sweep(api, torch, reps: int = 5) -> dict:
     """The precision sweep: n = 8192 square and M = 8192, K = 16384,
-    N = 4096; FP32 inputs U[-1, 1] (seeded, on the device); Winograd one
-    level and Strassen then classical <1,2,1>; BF16, FP16 and E4M3 (128-block
-    power-of-two scales) leaves with FP32 accumulation; outside-inside
-    scaling; each configuration timed with CUDA events over `reps` calls
-    (inputs far beyond L2) and its max-norm error against an FP64 product of
-    the same inputs (measurement only), relative to K ||A|| ||B||."""
+    N = 4096; FP32 inputs U[-1, 1] and the scaled-row/column distribution
+    A = D1 X D2, B = D3 Y D4 (X, Y ~ U[0, 1), D = 2^U(-12, 12)), seeded, on the
+    device; Winograd and Strassen composed with classical <1,2,1> at
+    alternating levels, one to four levels, and the classical product through
+    the same kernels; BF16, FP16 and E4M3 (128-block power-of-two scales)
+    leaves with FP32 accumulation; outside-inside scaling; each configuration
+    timed with CUDA events over `reps` calls (inputs far beyond L2), with its
+    max-norm error against an FP64 product of the same inputs (measurement
+    only), relative to K ||A|| ||B|| and to the plan's Theorem 4.2 bound."""
     out = {}
     gen = torch.Generator(device="cuda").manual_seed(1507 + 5000)
+    plans = (["winograd"], ["strassen", "classical121"], ["winograd", "classical121", "winograd"],
+             ["strassen", "classical121", "strassen", "classical121"], [])
+    eps = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11, "e4m3b128": 2.0 ** -3 + 2.0 ** -8}
     for M, K, N in ((8192, 8192, 8192), (8192, 16384, 4096)):
-        A = torch.rand((M, K), generator=gen, device="cuda") * 2 - 1
-        B = torch.rand((K, N), generator=gen, device="cuda") * 2 - 1
-        ref = A.double() @ B.double()
-        scale = K * float(A.abs().max()) * float(B.abs().max())
-        flops = 2.0 * M * K * N
-        for names in (["winograd"], ["strassen", "classical121"], []):
-            for leaf in ("bf16", "fp16", "e4m3b128"):
-                plan = api.Plan(names, leaf)
-                C = torch.empty((M, N), device="cuda")
-                eA, d, eB = api.scale(A, B, "OI")
-                api.multiply(plan, A, B, eA, d, eB, out=C)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(reps):
+        for dist in ("uniform", "scaled"):
+            if dist == "uniform":
+                A = torch.rand((M, K), generator=gen, device="cuda") * 2 - 1
+                B = torch.rand((K, N), generator=gen, device="cuda") * 2 - 1
+            else:
+                def diag(n):
+                    return torch.exp2(torch.rand(n, generator=gen, device="cuda") * 24 - 12)
+                A = diag(M)[:, None] * torch.rand((M, K), generator=gen, device="cuda") * diag(K)[None, :]
+                B = diag(K)[:, None] * torch.rand((K, N), generator=gen, device="cuda") * diag(N)[None, :]
+            ref = A.double() @ B.double()
+            normA, normB = float(A.abs().max()), float(B.abs().max())
+            scale = K * normA * normB
+            flops = 2.0 * M * K * N
+            for names in plans:
+                for leaf in ("bf16", "fp16", "e4m3b128"):
+                    plan = api.Plan(names, leaf)
+                    C = torch.empty((M, N), device="cuda")
                     eA, d, eB = api.scale(A, B, "OI")
                     api.multiply(plan, A, B, eA, d, eB, out=C)
-                e1.record()
-                torch.cuda.synchronize()
-                api.sync_status()
-                ms = e0.elapsed_time(e1) / reps
-                key = f"{M}x{K}x{N} {'-'.join(names) or 'classical'} {leaf}"
-                out[key] = {"tflops": flops / (ms * 1e-3) / 1e12, "ms": ms,
-                            "max_err_over_K_normA_normB": float((C.double() - ref).abs().max()) / scale}
-                del C, plan
-        del A, B, ref
-        torch.cuda.empty_cache()
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(reps):
+                        eA, d, eB = api.scale(A, B, "OI")
+                        api.multiply(plan, A, B, eA, d, eB, out=C)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    api.sync_status()
+                    ms = e0.elapsed_time(e1) / reps
+                    err = float((C.double() - ref).abs().max())
+                    key = f"{M}x{K}x{N} {dist} {'-'.join(names) or 'classical'} {leaf}"
+                    out[key] = {"tflops": flops / (ms * 1e-3) / 1e12, "ms": ms, "levels": len(names),
+                                "max_err_over_K_normA_normB": err / scale,
+                                "err_over_theorem_4_2_bound": err / plan.bound(K, normA, normB, eps[leaf])}
+                    del C, plan
+            del A, B, ref
+            torch.cuda.empty_cache()
     return out
 
 
@@ -638,6 +655,14 @@ def main():
         build.build()
         from paper_1507_00687_gb300 import api, inputs
         print(json.dumps({"experiment": "batch", **batched_workload(api, inputs, torch, max(1, args.batch))}))
+        return
+    if args.experiment == "precision":
+        import torch
+        from paper_1507_00687_gb300 import build
+        build.build()
+        from paper_1507_00687_gb300 import api
+        print(json.dumps({"experiment": "precision", "precision_sweep": precision_sweep(api, torch),
+                          "fp8_peak_probe": fp8_peak_probe(torch)}))
         return
     if args.experiment == "linear":
         import torch
