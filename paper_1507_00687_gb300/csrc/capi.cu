@@ -318,12 +318,15 @@ static bool combine_stream_enabled() {
 }
 
 // Output pass of a first half overlapped with the second half's multiply
-// (CTA-pair products of at least two tile rows); FMM_OVERLAP=0 in the
-// environment (read once) keeps one multiply launch and one output pass.
+// (CTA-pair products of at least two tile rows), with FMM_OVERLAP=1 in the
+// environment (read once); by default one multiply launch and one output
+// pass.  Measured at 8192^3 Winograd bf16: +7% while the multiply kept M_r
+// with per-thread stores; -1% once its epilogue stages M_r in shared memory
+// for bulk stores (no room is left beside a pair CTA for the output pass).
 static bool overlap_enabled() {
   static bool on = [] {
     const char* s = std::getenv("FMM_OVERLAP");
-    return !(s && std::atoi(s) == 0);
+    return s && std::atoi(s) != 0;
   }();
   return on;
 }
@@ -711,11 +714,11 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
     if (!cuda_ok(cudaMemset2DAsync(c.C, (size_t)c.ldc * 4, 0, (size_t)c.N * 4, (size_t)c.M, st), "C zero fill"))
       return FMM_ERR_CUDA;
   }
-  // Measured on GB300: hiding half of the output pass pays only where the
+  // When enabled: hiding half of the output pass can pay only where the
   // multiply is compute-bound (leaf K of at least 2048) and each half still
-  // fills the GPU for several waves (n = 8192: +7%); at n = 4096 (three
-  // waves per half) and for short leaf K (stored products compete with the
-  // output pass for DRAM) the single launch is faster.
+  // fills the GPU for several waves; at n = 4096 (three waves per half) and
+  // for short leaf K (stored products compete with the output pass for
+  // DRAM) the single launch was faster even with per-thread stores.
   const int64_t ntm = g.tp_a / 256;
   const int64_t half_waves = ntm >= 2 ? (ntm / 2) * (g.tp_b / 256) * g.R / std::max(1, device_sm_count() / 2) : 0;
   if (store_m && g.pair && !gather && ntm >= 2 && p->pm * p->pn <= 16 && g.R * 64 <= 48 * 1024 &&
