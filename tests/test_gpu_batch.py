@@ -225,3 +225,28 @@ def test_batch_classical_entries_read_inputs_directly(api, dt, leaf):
     st = OS.pow2_repeated(A64, B64, "OI")
     Cref, G = oracle_reference(A64, B64, ["winograd"], st.eA, st.d, st.eB)
     assert_within(dev_values(C), Cref, G, ["winograd"], 512, leaf, "fast entry beside direct ones")
+
+
+def test_batch_direct_entries_write_only_their_c(api):
+    # Direct classical entries write C by bulk tensor stores clipped at C's
+    # edges: with C a column slice of a wider row-major buffer (ldc > N) and
+    # ragged M, N, the columns beyond N and the rows beyond M of the buffer
+    # keep their contents, and C equals the single-product result bit for bit.
+    shapes = [(1000, 520, 776), (300, 2048, 264), (777, 384, 520)]
+    probs, bufs = [], []
+    for i, (M, K, N) in enumerate(shapes):
+        A = to_dev(inputs.uniform((M, K), -1, 1, seed=900 + i), "bf16")
+        B = to_dev(inputs.uniform((K, N), -1, 1, seed=910 + i), "bf16")
+        buf = torch.full((M + 40, N + 72), float("nan"), device="cuda")
+        probs.append((api.Plan([], "bf16"), A, B, buf[:M, :N]))
+        bufs.append(buf)
+    batch = api.Batch(probs, "OI")
+    batch.run()
+    api.sync_status()
+    for (plan, A, B, C), buf in zip(probs, bufs):
+        M, N = C.shape
+        want = api.multiply(plan, A, B)
+        api.sync_status()
+        assert np.array_equal(dev_values(C), dev_values(want)), (M, N)
+        rest = dev_values(buf)
+        assert np.isnan(rest[:, N:]).all() and np.isnan(rest[M:, :]).all(), (M, N)
