@@ -714,14 +714,15 @@ static fmm_status run_pass(const Plan* p, const Source& x, const Source& y, cons
     if (!cuda_ok(cudaMemset2DAsync(c.C, (size_t)c.ldc * 4, 0, (size_t)c.N * 4, (size_t)c.M, st), "C zero fill"))
       return FMM_ERR_CUDA;
   }
-  // When enabled: hiding half of the output pass can pay only where the
-  // multiply is compute-bound (leaf K of at least 2048) and each half still
-  // fills the GPU for several waves; at n = 4096 (three waves per half) and
-  // for short leaf K (stored products compete with the output pass for
-  // DRAM) the single launch was faster even with per-thread stores.
+  // Hiding half of the output pass pays only where the multiply is
+  // compute-bound (leaf K of at least 2048), each half still fills the GPU
+  // for several waves, and the output pass is light next to the multiply
+  // (at most 16 leaves): at n = 4096 (three waves per half), for short leaf
+  // K, and for the 49 leaves of two Strassen levels (the linear layer's
+  // weight gradient: 177 vs 150 us) the single launch is faster.
   const int64_t ntm = g.tp_a / 256;
   const int64_t half_waves = ntm >= 2 ? (ntm / 2) * (g.tp_b / 256) * g.R / std::max(1, device_sm_count() / 2) : 0;
-  if (store_m && g.pair && !gather && ntm >= 2 && p->pm * p->pn <= 16 && g.R * 64 <= 48 * 1024 &&
+  if (store_m && g.pair && !gather && ntm >= 2 && p->pm * p->pn <= 16 && g.R <= 16 &&
       half_waves >= 5 && g.kp >= 2048 && overlap_enabled()) {
     // Two launches over the tile-row halves; the output pass of the first
     // half runs on a side stream, beside the second half's multiply (one
