@@ -246,9 +246,9 @@ def crossover_workload(api, inputs, torch, args, n: int = 8192, reps: int = 10) 
 
 def fp8_peak_probe(torch, n: int = 8192, reps: int = 10) -> dict:
     """The dense E4M3 rate of the library GEMM in torch (a scaled FP8 product
-    at n^3, best of `reps`, CUDA events): the denominator for the E4M3 leaf
-    kernel's fraction of peak (not in the driver's measured peaks).
-    Measurement only."""
+    at n^3, best of `reps`, CUDA events): a measured FP8 reference beside the
+    nominal one (the measured bf16 figure x 2) that E4M3 bench lines use; the
+    measured-peaks file has no FP8 figure.  Measurement only."""
     try:
         a = torch.randn((n, n), device="cuda").to(torch.float8_e4m3fn)
         b = torch.randn((n, n), device="cuda").to(torch.float8_e4m3fn).t()
