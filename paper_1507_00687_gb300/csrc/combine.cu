@@ -1089,11 +1089,11 @@ cudaError_t launch_convert_batched(const CombineArgs* args, const int64_t* start
 // E4M3 combination pass: one CTA covers TT t x 128 k (one scale block) of
 // every leaf block (TT = 16, or 4 when the input blocks are too many to
 // stage sixteen rows of each); the input block tiles are staged as [t][k] (k
-// contiguous, stride kF8Stride) whatever the source's layout; warp w forms
-// row t0 + w of each leaf's sum, 4 consecutive k per lane, reduces the
-// block's max |sum| across the warp, picks s = e(max) - 8 (0 for a zero
-// block), rounds sum 2^-s to E4M3 (ties to even) and writes the 128 bytes
-// of its row plus the factor 2^s.
+// contiguous, stride kF8Stride) whatever the source's layout; each half of
+// warp w forms row t0 + 2w (+ 1) of each leaf's sum, 8 consecutive k per
+// lane, reduces the block's max |sum| across its 16 lanes, picks
+// s = e(max) - 8 (0 for a zero block; at least -127), rounds sum 2^-s to
+// E4M3 (ties to even) and writes the 128 bytes of its row plus its scale.
 constexpr int kF8TT = 16;
 constexpr int kF8Stride = 132;
 
@@ -1133,10 +1133,49 @@ __device__ __forceinline__ void e4m3_store_row(const CombineArgs& a, int r, int6
   }
 }
 
+// The same for a row held by a half-warp, 8 consecutive k per lane (sub =
+// lane within the half): the block max reduced over the 16 lanes, 8 bytes
+// stored per lane, the scale by the half's first lane.
+__device__ __forceinline__ void e4m3_store_row8(const CombineArgs& a, int r, int64_t t, int64_t k0, int sub,
+                                                const float (&acc)[8]) {
+  float m = fmaxf(fmaxf(fmaxf(fabsf(acc[0]), fabsf(acc[1])), fmaxf(fabsf(acc[2]), fabsf(acc[3]))),
+                  fmaxf(fmaxf(fabsf(acc[4]), fabsf(acc[5])), fmaxf(fabsf(acc[6]), fabsf(acc[7]))));
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  bool nf = false;
+  const int e = fexp_f32(__float_as_uint(m), &nf);
+  const int sc = m > 0.f ? max(e - 8, -127) : 0;
+  uint32_t packed[2] = {0u, 0u};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float2 pr = make_float2(scale_pow2(acc[2 * j], -sc), scale_pow2(acc[2 * j + 1], -sc));
+    const uint32_t q = (uint32_t)__nv_cvt_float2_to_fp8x2(pr, __NV_SATFINITE, __NV_E4M3);
+    packed[j >> 1] |= q << (16 * (j & 1));
+  }
+  unsigned char* out = static_cast<unsigned char*>(a.out);
+  *reinterpret_cast<uint2*>(out + ((int64_t)r * a.p_rows + t) * a.p_cols + k0 + 8 * sub) =
+      make_uint2(packed[0], packed[1]);
+  if (sub == 0) {
+    const int64_t kb = k0 / 128, nkb = a.p_cols / 128;
+    if (a.sf_atoms) {
+      const int64_t atom = ((int64_t)r * nkb + kb) * (a.p_rows / 128) + t / 128;
+      reinterpret_cast<uint32_t*>(a.scale_out)[atom * 128 + (t % 32) * 4 + (t % 128) / 32] =
+          (uint32_t)(sc + 127) * 0x01010101u;
+    } else {
+      a.scale_out[((int64_t)r * nkb + kb) * a.p_rows + t] = exp2i(sc);
+    }
+  }
+}
+
+// Threads of the E4M3 combination CTA: two rows per warp in the sums, at
+// least four warps for the staging.
+template <int TT>
+constexpr int e4m3_threads() { return TT * 16 > 128 ? TT * 16 : 128; }
+
 template <int DT, int TT>
-__global__ void __launch_bounds__(TT * 32) combine_e4m3_kernel(const CombineArgs a) {
+__global__ void __launch_bounds__(e4m3_threads<TT>()) combine_e4m3_kernel(const CombineArgs a) {
   extern __shared__ float f8tile[];  // [block][TT][kF8Stride], then the term list
-  constexpr int kThr = TT * 32;
+  constexpr int kThr = e4m3_threads<TT>();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t t0 = (int64_t)blockIdx.y * TT, k0 = (int64_t)blockIdx.x * 128;
   const int n_rb = (int)a.n_rb, n_cb = (int)a.n_cb, nb = n_rb * n_cb;
@@ -1191,20 +1230,29 @@ __global__ void __launch_bounds__(TT * 32) combine_e4m3_kernel(const CombineArgs
     }
   }
   __syncthreads();
-  const int64_t t = t0 + warp;
+  // half-warp h of warp w forms row 2w + h, 8 consecutive k per lane
+  const int row = 2 * warp + (lane >> 4), sub = lane & 15;
+  if (row >= TT) return;  // staging-only warps (warp-uniform)
+  const int64_t t = t0 + row;
+  const float* trow = f8tile + row * kF8Stride + 8 * sub;
   int tt = 0;
   for (int r = 0; r < R; ++r) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int t1 = tstart[r + 1];
     for (; tt < t1; ++tt) {
       const float coef = tcoef[tt];
-      const float4 v = *reinterpret_cast<const float4*>(f8tile + toff[tt] + warp * kF8Stride + 4 * lane);
-      acc[0] = fmaf(coef, v.x, acc[0]);
-      acc[1] = fmaf(coef, v.y, acc[1]);
-      acc[2] = fmaf(coef, v.z, acc[2]);
-      acc[3] = fmaf(coef, v.w, acc[3]);
+      const float4 v0 = *reinterpret_cast<const float4*>(trow + toff[tt]);
+      const float4 v1 = *reinterpret_cast<const float4*>(trow + toff[tt] + 4);
+      acc[0] = fmaf(coef, v0.x, acc[0]);
+      acc[1] = fmaf(coef, v0.y, acc[1]);
+      acc[2] = fmaf(coef, v0.z, acc[2]);
+      acc[3] = fmaf(coef, v0.w, acc[3]);
+      acc[4] = fmaf(coef, v1.x, acc[4]);
+      acc[5] = fmaf(coef, v1.y, acc[5]);
+      acc[6] = fmaf(coef, v1.z, acc[6]);
+      acc[7] = fmaf(coef, v1.w, acc[7]);
     }
-    e4m3_store_row(a, r, t, k0, lane, acc);
+    e4m3_store_row8(a, r, t, k0, sub, acc);
   }
 }
 
@@ -1291,7 +1339,7 @@ cudaError_t launch_combine_e4m3(const CombineArgs& a, cudaStream_t st) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedSmemMax);
       attr_done[dev][idx] = true;
     }
-    kern<<<grid, tt * 32, smem, st>>>(a);
+    kern<<<grid, wide ? e4m3_threads<kF8TT>() : e4m3_threads<4>(), smem, st>>>(a);
   };
   switch (a.dtype) {
     case kF32: wide ? go(combine_e4m3_kernel<kF32, kF8TT>, 0) : go(combine_e4m3_kernel<kF32, 4>, 3); break;
