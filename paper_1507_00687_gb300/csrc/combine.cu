@@ -203,13 +203,18 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs a) 
 // use.  TR * 16 threads, one row of 4 columns each.
 constexpr int kMaxStaged = 64;
 
-template <int DT, int FMT, int TR, int RPT, bool BETWEEN = false>
+template <int DT, int FMT, int TR, int RPT, bool BETWEEN = false, int LS = 1>
 __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_t bx, int64_t by, float4* tile4,
                                                     int r_begin, int r_end) {
-  // RPT rows per thread: rows tr + (TR / RPT) q, q < RPT; 4 columns each
-  constexpr int kT = TR * 16 / RPT;
+  // RPT rows per thread: rows tr + (TR / RPT) q, q < RPT; 4 columns each.
+  // LS groups of threads share the staged tiles: group ls stages blocks
+  // ls, ls + LS, ... and forms leaves r_begin + ls, + LS, ... (LS > 1 gives
+  // the small CTAs of plans with many blocks enough warps).
+  constexpr int kP = TR * 16 / RPT;  // threads per group (one per position)
+  constexpr int kT = kP * LS;
   const int64_t r0 = by * TR, c0 = bx * kTC;
-  const int tr = threadIdx.x >> 4, tq = threadIdx.x & 15, tc = tq * 4;
+  const int ls = (int)threadIdx.x / kP, pt = (int)threadIdx.x % kP;
+  const int tr = pt >> 4, tq = pt & 15, tc = tq * 4;
   const int es = DT == kF32 ? 4 : 2;
   const bool vec_ok = ((uintptr_t)a.src % (4 * es) == 0) && (a.ld % 4 == 0) && (a.b_cols % 4 == 0) &&
                       (!a.ce || (uintptr_t)a.ce % 16 == 0);
@@ -243,12 +248,12 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
   for (int q = 0; q < RPT; ++q) {
     const int trq = tr + (TR / RPT) * q;
     const int64_t lr = r0 + trq;
-    for (int b0 = 0; b0 < nb; b0 += kStageGroup) {
+    for (int b0 = ls; b0 < nb; b0 += kStageGroup * LS) {
       float x[kStageGroup][4];
       int ex[kStageGroup][4];
 #pragma unroll
       for (int u = 0; u < kStageGroup; ++u) {
-        const int b = b0 + u;
+        const int b = b0 + u * LS;
         if (b >= nb) break;
         const int rb = b / n_cb, cb = b - (b / n_cb) * n_cb;
         const int64_t nr = min(a.b_rows, a.rows - rb * a.b_rows);
@@ -280,7 +285,7 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
       }
 #pragma unroll
       for (int u = 0; u < kStageGroup; ++u) {
-        const int b = b0 + u;
+        const int b = b0 + u * LS;
         if (b >= nb) break;
         float y[4];
 #pragma unroll
@@ -295,10 +300,10 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
   const int me = tr * 16 + tq;
   constexpr int kRowStep = (TR / RPT) * 16;  // float4 distance between a thread's rows
   const int64_t leaf_stride = a.p_rows * a.p_cols;
-  unsigned short* orow = out + (r0 + tr) * a.p_cols + lc + r_begin * leaf_stride;
+  unsigned short* orow = out + (r0 + tr) * a.p_cols + lc + (int64_t)(r_begin + ls) * leaf_stride;
   const int64_t qstride = (int64_t)(TR / RPT) * a.p_cols;
-  int t = tstart[r_begin];
-  for (int r = r_begin; r < r_end; ++r, orow += leaf_stride) {
+  for (int r = r_begin + ls; r < r_end; r += LS, orow += LS * leaf_stride) {
+    int t = tstart[r];
     const int t1 = tstart[r + 1];
     float acc[RPT][4];
 #pragma unroll
@@ -343,8 +348,13 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
   }
 }
 
+// Groups of threads sharing a CTA's staged tiles (see combine_staged_body):
+// more for the small tiles of plans with many blocks.
+template <int TR>
+constexpr int staged_groups() { return TR <= 2 ? 8 : (TR <= 4 ? 4 : 1); }
+
 template <int DT, int FMT, int TR, int RPT, bool BETWEEN>
-__global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_kernel(const CombineArgs a) {
+__global__ void __launch_bounds__(TR * 16 / RPT * staged_groups<TR>()) combine_staged_kernel(const CombineArgs a) {
   extern __shared__ float4 tile4[];  // [block][TR][16], then the term list
   pdl_wait();
   pdl_trigger();
@@ -353,7 +363,8 @@ __global__ void __launch_bounds__(TR * 16 / RPT) combine_staged_kernel(const Com
   const int R = (int)a.num_leaves;
   const int per = (R + (int)gridDim.z - 1) / (int)gridDim.z;
   const int r_begin = min(R, (int)blockIdx.z * per), r_end = min(R, r_begin + per);
-  combine_staged_body<DT, FMT, TR, RPT, BETWEEN>(a, blockIdx.x, blockIdx.y, tile4, r_begin, r_end);
+  combine_staged_body<DT, FMT, TR, RPT, BETWEEN, staged_groups<TR>()>(a, blockIdx.x, blockIdx.y, tile4, r_begin,
+                                                                      r_end);
 }
 
 // Batched form: tile b belongs to entry p with start[p] <= b < start[p + 1]
@@ -477,7 +488,7 @@ void launch_staged_tr_b(const CombineArgs& a, int nb, cudaStream_t st) {
   }
   const dim3 grid((unsigned)(a.p_cols / kTC), (unsigned)(a.p_rows / TR));
   launch_pdl(combine_staged_kernel<DT, FMT, TR, RPT, BETWEEN>, dim3(grid.x, grid.y, leaf_splits(a, TR, a.num_leaves, 4)),
-             dim3(TR * 16 / RPT), staged_smem(nb, TR, a.t_nnz, a.num_leaves), st, a);
+             dim3(TR * 16 / RPT * staged_groups<TR>()), staged_smem(nb, TR, a.t_nnz, a.num_leaves), st, a);
 }
 
 template <int DT, int FMT, int TR, int RPT = 1>
