@@ -350,15 +350,17 @@ __device__ __forceinline__ void combine_staged_body(const CombineArgs& a, int64_
 
 // Groups of threads sharing a CTA's staged tiles (see combine_staged_body):
 // more for the small tiles of plans with many blocks.
-// For 5 to 16 blocks (8 or 16 rows per CTA) the groups raise the warps per
-// SM that the shared-memory tiles allow; measured with one, two and four
+// For 9 to 16 blocks (8 rows per CTA) the groups raise the warps per SM
+// that the shared-memory tiles allow; measured with one, two and four
 // groups: Winograd two levels at n = 4096 266 / 293 / 298 TFLOP/s, the
-// linear layer X[8192,4096] W[4096,4096] forward 524 / 579 / 594.
+// linear layer X[8192,4096] W[4096,4096] forward 524 / 579 / 594.  With 16
+// rows per CTA (5 to 8 blocks) four groups made Strassen with classical
+// <1,2,1> at 8192^3 slower (852 -> 727), so those CTAs keep one.
 #ifndef FMM_STAGED_MID_GROUPS
 #define FMM_STAGED_MID_GROUPS 4
 #endif
 template <int TR>
-constexpr int staged_groups() { return TR <= 2 ? 8 : (TR <= 4 ? 4 : (TR <= 16 ? FMM_STAGED_MID_GROUPS : 1)); }
+constexpr int staged_groups() { return TR <= 2 ? 8 : (TR <= 4 ? 4 : (TR <= 8 ? FMM_STAGED_MID_GROUPS : 1)); }
 
 template <int DT, int FMT, int TR, int RPT, bool BETWEEN>
 __global__ void __launch_bounds__(TR * 16 / RPT * staged_groups<TR>()) combine_staged_kernel(const CombineArgs a) {
