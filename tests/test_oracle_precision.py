@@ -1,5 +1,7 @@
 """Pins for the oracle's rounding emulation against IEEE / OCP definitions
-(hand-computed ties) and independent library conversions."""
+(hand-computed ties) and independent library conversions, and for the
+E4M3 leaf with 128-block power-of-two scales (exactness on small integers,
+the per-entry error bound, the UE8M0 scale floor, the quantization axes)."""
 import numpy as np
 import pytest
 import torch
@@ -103,3 +105,24 @@ def test_e4m3_block_scale_floor_is_the_ue8m0_minimum():
     assert s[0, 0] == -127 and s[1, 0] == -126
     assert q[0, 0] == 2.0 ** -125 and q[0, 1] == 0.0 and q[0, 2] == 3 * 2.0 ** -131
     assert q[1, 0] == 2.0 ** -119 and q[1, 1] == 2.0 ** -126
+
+
+def test_e4m3_leaf_scales_rows_of_s_and_columns_of_t():
+    # The E4M3 leaf quantizes S (rows x K) in 128-blocks along K per row and
+    # T (K x cols) per column.  Rows and columns at very different scales
+    # then keep their relative accuracy: each scaled entry is a normal E4M3
+    # number, so |fl(s) fl(t) - s t| <= (2 * 2^-4 + 2^-8) |s t| entrywise.
+    # Had S been quantized along its columns (T along its rows), the rows at
+    # 2^-30 and 2^-50 would share a scale with the row at 2^10 and vanish.
+    from oracle import fmm as F
+    g = np.random.default_rng(13)
+    S = g.uniform(1, 2, (4, 256)) * np.exp2(np.array([0.0, -30.0, 10.0, -50.0]))[:, None]
+    T = g.uniform(1, 2, (256, 3)) * np.exp2(np.array([0.0, -40.0, 20.0]))[None, :]
+    C = F.leaf_e4m3_b128(S, T)
+    exact = S @ T
+    assert np.all(np.abs(C - exact) <= (2 * 2.0 ** -4 + 2.0 ** -8) * exact)
+    # the same leaf inside one Strassen level on small integers is exact
+    A = g.integers(-3, 4, (256, 512)).astype(np.float64)
+    B = g.integers(-3, 4, (512, 128)).astype(np.float64)
+    from oracle import rules as R
+    assert np.array_equal(F.fmm(A, B, F.uniform([R.strassen()]), leaf=F.leaf_e4m3_b128), A @ B)

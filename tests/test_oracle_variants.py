@@ -8,7 +8,9 @@ classical product on integer inputs for a tree mixing all eight variants,
 the published reference outputs of SplitMix64, brute-force minimality of
 the matrix-dependent choice, and its equivariance: exchanging the block rows
 of A (the block columns of B, both k halves) permutes the node's eight
-costs by v -> v xor 1 (v xor 4, v xor 2).
+costs by v -> v xor 1 (v xor 4, v xor 2); the bounds passed to a node's
+children hold on real matrices and are attained by sign-matched constant
+blocks.
 """
 import itertools
 
@@ -139,3 +141,34 @@ def test_block_max_definition():
     assert out.shape == (2, 3)
     assert out[0, 0] == 17.0 and out[1, 2] == 17.0 and out[0, 2] == 11.0 and out[1, 0] == 13.0
     assert CG.block_max(np.zeros((3, 3)), 4, 4)[3, 3] == 0.0
+
+
+@pytest.mark.parametrize("name", sorted(BASES))
+def test_child_bounds_hold_and_are_attained(name):
+    # The matrix-dependent selection passes bounds on the finest blocks of
+    # each product's operands, S_r = sum_i U_ir A_i and T_r = sum_j V_jr B_j
+    # (quadrants row-major, canonical tables), down the tree.  By the
+    # triangle inequality max|block of S_r| <= sum_i |U_ir| max|block of
+    # A_i|: checked on real matrices with random signs, and attained when
+    # every quadrant is a sign-matched constant-block matrix.
+    base = BASES[name]()
+    g = np.random.default_rng(21)
+    n, b = 4, 3                                   # a 4 x 4 grid of 3 x 3 blocks
+    h = n * b // 2
+    quad = lambda X, i: X[(i // 2) * h:(i // 2 + 1) * h, (i % 2) * h:(i % 2 + 1) * h]  # noqa: E731
+    for v in range(8):
+        c = R.canonical(CG.variant(base, v))
+        for T in (c.U, c.V):
+            for _ in range(5):
+                X = g.standard_normal((n * b, n * b)) * np.exp2(g.integers(-3, 4, (n * b, n * b)))
+                Xmax = CG.block_max(X, n, n)
+                for r in range(c.R):
+                    S = sum(float(T[i, r]) * quad(X, i) for i in range(4))
+                    assert np.all(CG.block_max(S, 2, 2) <= CG.child_bounds(T, Xmax, r) * (1 + 1e-15))
+            Xmax = g.integers(1, 50, (n, n)).astype(float)
+            for r in range(c.R):
+                X = np.kron(Xmax, np.ones((b, b)))
+                for i in range(4):
+                    quad(X, i)[...] *= np.sign(T[i, r]) if T[i, r] != 0 else 1.0
+                S = sum(float(T[i, r]) * quad(X, i) for i in range(4))
+                assert np.array_equal(CG.block_max(S, 2, 2), CG.child_bounds(T, Xmax, r))
