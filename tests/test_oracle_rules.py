@@ -178,3 +178,22 @@ def test_composition_matches_two_levels():
     assert np.array_equal(one, A @ B) and np.array_equal(two, A @ B)
     pc = R.principal(comp)
     assert pc.E == R.principal(s).E * R.principal(c).E
+
+
+def test_stated_order_reindexing():
+    # Sec. 3.1 states A and B column-major and C row-major.  App. B's table
+    # is read in that order, so re-indexing it changes nothing; Strassen's
+    # second product (a21 + a22) b11 puts a21 at index 2 row-major and at
+    # index 1 column-major.  Every rule keeps its canonical form and Brent.
+    f = R.fast323()
+    s = R.to_stated_order(f)
+    assert np.array_equal(s.U, f.U) and np.array_equal(s.V, f.V) and np.array_equal(s.W, f.W)
+    st = R.to_stated_order(R.strassen())
+    assert list(R.canonical(R.strassen()).U[:, 1]) == [0, 0, 1, 1]
+    assert list(st.U[:, 1]) == [0, 1, 0, 1] and list(st.V[:, 1]) == [1, 0, 0, 0]
+    for r in (R.strassen(), R.winograd(), R.classical(2, 3, 4), R.fast323(), R.rotate(R.fast323())):
+        s = R.to_stated_order(r)
+        assert (s.order_a, s.order_b, s.order_c) == ("col", "col", "row")
+        assert R.brent_violations(s) == 0
+        c0, c1 = R.canonical(r), R.canonical(s)
+        assert np.array_equal(c0.U, c1.U) and np.array_equal(c0.V, c1.V) and np.array_equal(c0.W, c1.W)
