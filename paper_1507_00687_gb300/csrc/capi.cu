@@ -1470,7 +1470,7 @@ static fmm_status scale_oi_from_zero(const void* A, const void* B, int dtype, in
 
 fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype, int64_t M, int64_t K, int64_t N,
                      int64_t lda, int64_t ldb, int32_t* eA, int32_t* d, int32_t* eB, void* stream) {
-  if (!steps) return FMM_ERR_ARG;
+  if (!steps || !valid_dtype(dtype) || M < 0 || K < 0 || N < 0) return FMM_ERR_ARG;
   bool has_o = false, has_i = false;
   for (const char* c = steps; *c; ++c) {
     if (*c != 'O' && *c != 'I') return FMM_ERR_ARG;
@@ -1478,6 +1478,9 @@ fmm_status fmm_scale(const char* steps, const void* A, const void* B, int dtype,
     has_i |= *c == 'I';
   }
   if ((M > 0 && !eA) || (K > 0 && !d) || (N > 0 && !eB)) return FMM_ERR_ARG;
+  // The steps' own checks, made before the fills below launch anything.
+  if (steps[0] && ((M > 0 && K > 0 && !A) || (K > 0 && N > 0 && !B))) return FMM_ERR_ARG;
+  if (steps[0] && ((M > 0 && K > 0 && lda < K) || (K > 0 && N > 0 && ldb < N))) return FMM_ERR_SHAPE;
   cudaStream_t st = as_stream(stream);
   // Every vector starts at zero (no scaling).  A vector that some step
   // overwrites completely needs no fill; and while a vector is still all
