@@ -235,6 +235,34 @@ fmm_status fmm_block_max(const void* X, int dtype, int64_t rows, int64_t cols, i
 fmm_status fmm_plan_info(fmm_plan_t plan, double* q_sum, double* e_prod, int64_t* leaves,
                          int64_t* nnz, int64_t* pm, int64_t* pk, int64_t* pn);
 
+/* Tables fmm_plan_flatten reads back. */
+enum { FMM_TABLE_LEAVES = 0, FMM_TABLE_LISTS = 1, FMM_TABLE_GATHER = 2 };
+
+/*
+ * The plan's flattened rule [[U^(L), V^(L), W^(L)]] (Eq. 4.4; for a tree,
+ * Sec. 3.4, each leaf flattened along its own root-to-leaf path), read back
+ * from one of the tables the kernels execute, so that a caller can check
+ * them against its own derivation or export the algorithm.  Dense,
+ * row-major, in host memory the caller provides (sizes from fmm_plan_info):
+ * U is (pm pk) x leaves, V (pk pn) x leaves, W (pm pn) x leaves, entry
+ * (i, r) at [i * leaves + r], with i = p pk + q for block (p, q) of A's
+ * pm x pk block grid (B's and C's grids likewise).  first (optional, int32,
+ * W's shape) is 1 where leaf r is the first in leaf order to add into C
+ * block k (there the fused epilogue stores instead of adding), else 0.
+ * table: FMM_TABLE_LEAVES = the per-leaf descriptors the tensor-core kernels
+ * read; FMM_TABLE_LISTS = the per-side term lists of the combination and
+ * output passes; FMM_TABLE_GATHER = the per-C-block lists of the gather
+ * output pass (W and first only, U and V are not written;
+ * FMM_ERR_UNSUPPORTED when pm pn > 2^20, where the plan carries none).  Any
+ * of U, V, W, first may be NULL.  Coefficients are the float values the
+ * kernels multiply by.  Host only (no device access, no allocation); the
+ * dense tables grow as blocks x leaves, so this is meant for plans of up
+ * to some thousands of leaves.  FMM_ERR_ARG for a NULL plan or an unknown
+ * table.
+ */
+fmm_status fmm_plan_flatten(fmm_plan_t plan, int table, double* U, double* V, double* W,
+                            int32_t* first);
+
 /*
  * First-order bound of Theorem 4.2 for this plan and a K-dimension:
  *   (Kl + sum Q)(Kl) (prod E) normA normB eps,  Kl = ceil(K / prod k0).

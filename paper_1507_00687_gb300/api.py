@@ -165,6 +165,25 @@ class Plan:
         return {"q_sum": q.value, "e_prod": e.value, "leaves": leaves.value, "nnz": nnz.value,
                 "pm": pm.value, "pk": pk.value, "pn": pn.value}
 
+    def flatten(self, table: str = "leaves"):
+        """The flattened rule (Eq. 4.4) read back from one of the plan's
+        kernel tables (fmm_plan_flatten): "leaves" (the tensor-core kernels'
+        leaf descriptors), "lists" (the combination and output passes' term
+        lists) or "gather" (the gather output pass's per-C-block lists: U and
+        V come back as None).  Returns numpy arrays U (pm pk x leaves),
+        V (pk pn x leaves), W (pm pn x leaves) and first (int32, W's shape:
+        1 where the leaf is the first to add into the C block)."""
+        t = {"leaves": N.TABLE_LEAVES, "lists": N.TABLE_LISTS, "gather": N.TABLE_GATHER}[table]
+        inf = self.info()
+        R = inf["leaves"]
+        U = None if t == N.TABLE_GATHER else np.zeros((inf["pm"] * inf["pk"], R))
+        V = None if t == N.TABLE_GATHER else np.zeros((inf["pk"] * inf["pn"], R))
+        W = np.zeros((inf["pm"] * inf["pn"], R))
+        first = np.zeros(W.shape, np.int32)
+        ptr = lambda a: None if a is None else C.c_void_p(a.ctypes.data)  # noqa: E731
+        N.check(N.lib().fmm_plan_flatten(self._h, t, ptr(U), ptr(V), ptr(W), ptr(first)), "fmm_plan_flatten")
+        return U, V, W, first
+
     def bound(self, K: int, normA: float, normB: float, eps: float) -> float:
         b = C.c_double()
         N.check(N.lib().fmm_plan_bound(self._h, K, normA, normB, eps, C.byref(b)), "fmm_plan_bound")

@@ -1400,6 +1400,59 @@ fmm_status fmm_plan_info(fmm_plan_t plan, double* q_sum, double* e_prod, int64_t
   return FMM_OK;
 }
 
+fmm_status fmm_plan_flatten(fmm_plan_t plan, int table, double* U, double* V, double* W, int32_t* first) {
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  if (!p || table < FMM_TABLE_LEAVES || table > FMM_TABLE_GATHER) return FMM_ERR_ARG;
+  if (table == FMM_TABLE_GATHER && p->gather_off < 0) return FMM_ERR_UNSUPPORTED;
+  const int64_t R = p->leaves;
+  const int64_t rows[3] = {p->pm * p->pk, p->pk * p->pn, p->pm * p->pn};
+  const int64_t grid_cols[3] = {p->pk, p->pn, p->pn};
+  double* out[3] = {U, V, W};
+  if (table == FMM_TABLE_GATHER) out[0] = out[1] = nullptr;
+  for (int s = 0; s < 3; ++s)
+    if (out[s]) std::fill(out[s], out[s] + rows[s] * R, 0.0);
+  if (first) std::fill(first, first + rows[2] * R, 0);
+  // one term: coefficient c of block blk ((row << 16) | col) in leaf r
+  auto put = [&](int s, int32_t blk, int64_t r, float c, bool is_first) {
+    const int64_t i = (int64_t)((blk & 0x7FFFFFFF) >> 16) * grid_cols[s] + (blk & 0xFFFF);
+    if (out[s]) out[s][i * R + r] += (double)c;
+    if (s == 2 && first && is_first) first[i * R + r] = 1;
+  };
+  if (table == FMM_TABLE_LEAVES) {
+    for (int64_t r = 0; r < R; ++r) {
+      const LeafDesc& d = p->host[(size_t)r];
+      for (int t = 0; t < d.na; ++t) put(0, d.a_blk[t], r, d.a_coef[t], false);
+      for (int t = 0; t < d.nb; ++t) put(1, d.b_blk[t], r, d.b_coef[t], false);
+      for (int t = 0; t < d.nc; ++t) put(2, d.c_blk[t], r, d.c_coef[t], d.c_first[t] != 0);
+    }
+  } else if (table == FMM_TABLE_LISTS) {
+    for (int s = 0; s < 3; ++s) {
+      const int32_t* start = p->lists.data() + p->list_off[s];
+      const int32_t* blk = start + R + 1;
+      const int32_t* coef = blk + p->list_nnz[s];
+      for (int64_t r = 0; r < R; ++r)
+        for (int32_t t = start[r]; t < start[r + 1]; ++t) {
+          float c;
+          std::memcpy(&c, &coef[t], 4);
+          put(s, blk[t], r, c, (blk[t] & kFirstBit) != 0);
+        }
+    }
+  } else {
+    const int64_t nblk = rows[2];
+    const int32_t* gstart = p->lists.data() + p->gather_off;
+    const int32_t* gleaf = gstart + nblk + 1;
+    const int32_t* gcoef = gleaf + p->list_nnz[2];
+    for (int64_t k = 0; k < nblk; ++k)
+      for (int32_t t = gstart[k]; t < gstart[k + 1]; ++t) {
+        float c;
+        std::memcpy(&c, &gcoef[t], 4);
+        if (W) W[k * R + gleaf[t]] += (double)c;
+        if (first && t == gstart[k]) first[k * R + gleaf[t]] = 1;
+      }
+  }
+  return FMM_OK;
+}
+
 fmm_status fmm_plan_bound(fmm_plan_t plan, int64_t K, double normA, double normB, double eps, double* bound) {
   const Plan* p = reinterpret_cast<const Plan*>(plan);
   if (!p || !bound || K < 0) return FMM_ERR_ARG;

@@ -368,3 +368,112 @@ def test_matrix_dependent_selection_matches_oracle(native, name):
     assert native.lib().fmm_plan_variants(C.byref(h), arr, 1, 1, 0, None, None, None, 0) == 10
     arr = holder._rule_array([rule])
     assert native.lib().fmm_plan_variants(C.byref(h), arr, 1, native.SELECT_MATRIX, 0, None, None, None, 0) == 1
+
+
+# ---------------------------------------------------------------- the tables the kernels execute (Eq. 4.4)
+
+def _oracle_flattened(node):
+    """[[U, V, W]] of the flattened plan, read off the oracle's recursion
+    (Eq. 3.2) itself: one product on operands whose finest blocks are unit
+    vectors.  A is pm x (pk P) with block (p, q) = e_(p pk + q)^T (1 x P),
+    B is (pk P) x (pn R) with block (p, q) holding e_(p pn + q) in its first
+    column, and leaf r records S_r (1 x P: column r of U) and T_r (its first
+    column: column r of V) and returns e_r^T (1 x R), so that C block k is
+    row k of W.  Every sum is exact (small dyadic coefficients)."""
+    pm, pk, pn = OF.dims(node)
+    R = _count_leaves(node)
+    P = max(pm * pk, pk * pn)
+    A = np.zeros((pm, pk * P))
+    for p in range(pm):
+        for q in range(pk):
+            A[p, q * P + p * pk + q] = 1.0
+    B = np.zeros((pk * P, pn * R))
+    for p in range(pk):
+        for q in range(pn):
+            B[p * P + p * pn + q, q * R] = 1.0
+    Us, Vs = [], []
+
+    def leaf(S, T):
+        r = len(Us)
+        Us.append(S[0, :pm * pk].copy())
+        Vs.append(T[:pk * pn, 0].copy())
+        out = np.zeros((1, R))
+        out[0, r] = 1.0
+        return out
+    C = OF.fmm(A, B, node, leaf=leaf)
+    assert len(Us) == R
+    W = np.stack([C[p, q * R:(q + 1) * R] for p in range(pm) for q in range(pn)])
+    return np.stack(Us, axis=1), np.stack(Vs, axis=1), W
+
+
+def _count_leaves(node):
+    if node is None:
+        return 1
+    return sum(_count_leaves(c) for c in node.children)
+
+
+def _first_touch(W):
+    first = np.zeros(W.shape, np.int32)
+    for k in range(W.shape[0]):
+        nz = np.nonzero(W[k])[0]
+        if nz.size:
+            first[k, nz[0]] = 1
+    return first
+
+
+def _plan_cases():
+    from paper_1507_00687_gb300 import api
+    import tree_cases as TC
+    cases = []
+    for names in (["strassen"], ["winograd"], ["strassen", "strassen"], ["winograd"] * 3,
+                  ["strassen", "classical121", "strassen"], ["fast323"], ["fast323", "strassen"],
+                  ["classical121", "winograd"]):
+        cases.append((api.Plan(names, "bf16"), OF.uniform([_oracle_rule(n) for n in names])))
+    # a rotation (<3,3,2>, A and B grids of different sizes) over Strassen
+    cases.append((api.Plan([PR.rotate(PR.get("fast323")), "strassen"], "bf16"),
+                  OF.uniform([OR.rotate(OR.fast323()), OR.strassen()])))
+    for root, children in (TC.dalberto(), TC.fast323_nonuniform(), TC.mixed_rank()):
+        lib, orc = TC.two_level(root, children)
+        cases.append((api.Plan.tree(lib, "bf16"), orc))
+    from oracle import variants as CG
+    for name, levels in (("strassen", 2), ("winograd", 3)):
+        plan = api.Plan.variants(name, levels, "random", seed=99, leaf="bf16")
+        cases.append((plan, CG.tree(_oracle_rule(name), levels, plan.chosen)))
+    return cases
+
+
+def test_kernel_tables_are_the_flattened_rule(native):
+    # Every table the kernels read -- the per-leaf descriptors, the per-side
+    # term lists and the per-C-block gather lists -- holds exactly the
+    # flattened rule of Eq. 4.4 (uniform and non-stationary plans) or of
+    # each root-to-leaf path (trees, Castrapel-Gustafson variant trees), in
+    # depth-first leaf order, with the first-touch flags the fused epilogue
+    # uses; uniform plans also equal the oracle's repeated composition.
+    for plan, orc in _plan_cases():
+        U0, V0, W0 = _oracle_flattened(orc)
+        want_first = _first_touch(W0)
+        for table in ("leaves", "lists", "gather"):
+            U, V, W, first = plan.flatten(table)
+            if table != "gather":
+                assert np.array_equal(U, U0) and np.array_equal(V, V0), (plan.rules, table)
+            assert np.array_equal(W, W0) and np.array_equal(first, want_first), (plan.rules, table)
+        info = plan.info()
+        assert info["nnz"] == np.count_nonzero(U0) + np.count_nonzero(V0) + np.count_nonzero(W0)
+    # repeated composition (Eq. 4.4) of the oracle's rules for uniform plans
+    from paper_1507_00687_gb300 import api
+    for names in (["strassen", "strassen"], ["winograd", "classical121", "winograd"]):
+        comp = _oracle_rule(names[0])
+        for n in names[1:]:
+            comp = OR.compose(comp, _oracle_rule(n))
+        U, V, W, _ = api.Plan(names, "bf16").flatten()
+        assert np.array_equal(U, comp.U) and np.array_equal(V, comp.V) and np.array_equal(W, comp.W)
+
+
+def test_plan_flatten_rejections(native):
+    from paper_1507_00687_gb300 import api
+    L = native.lib()
+    plan = api.Plan(["strassen"], "bf16")
+    assert L.fmm_plan_flatten(None, 0, None, None, None, None) == 1
+    assert L.fmm_plan_flatten(plan._h, 3, None, None, None, None) == 1
+    assert L.fmm_plan_flatten(plan._h, -1, None, None, None, None) == 1
+    assert L.fmm_plan_flatten(plan._h, 2, None, None, None, None) == 0
