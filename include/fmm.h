@@ -421,6 +421,15 @@ fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t M, int64_t K, int64_t N, 
  *    one output pass forms C = sum w M_r, unscaled -- three launches (plus
  *    the between-steps exponent kernels when that scaling is on); a
  *    single-leaf plan adds its product into C in the multiply epilogue;
+ *    with 16-bit leaves on CTA pairs, where the multiply is compute-bound
+ *    (leaf K >= 2048, at most 16 leaves and 16 C blocks, each half of the
+ *    tile rows filling the GPU for 5 waves or more), it runs as two
+ *    launches over the tile-row halves, and the first half's output pass
+ *    runs on a library-owned side stream beside the second half's
+ *    multiply, joined back to the caller's stream by events (FMM_OVERLAP=0
+ *    in the environment, read once, keeps one launch); E4M3 leaves always
+ *    take the pass schedule, with their own combination pass (the E4M3
+ *    bytes and the per-block scales) and the block-scaled multiply;
  *  - the load-stage schedule: one launch forms S_r, T_r in the multiply
  *    kernel's load stage and adds W-weighted products into C in its
  *    epilogue (operands needing a prepared copy get one bandwidth pass).
