@@ -38,6 +38,28 @@ def _rowmajor(t: torch.Tensor, name: str) -> int:
     return max(t.stride(0), t.shape[1], 1)
 
 
+def _check_exponents(vectors, lengths, device) -> None:
+    """Exponent vectors are read as int32 arrays of a fixed length: anything
+    else would have the kernels read past them or misread them."""
+    for name, v in vectors.items():
+        if v is None:
+            continue
+        n = lengths[name]
+        if (not isinstance(v, torch.Tensor) or v.dtype != torch.int32 or v.dim() != 1 or v.numel() != n
+                or not v.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous 1-D int32 tensor of length {n}")
+        if v.device != device:
+            raise ValueError(f"{name} must be on {device}, like the operands")
+
+
+def _check_out(out: torch.Tensor, M: int, Ncols: int, device) -> None:
+    """The kernels write M x Ncols float32 values through ``out``."""
+    if out.dtype != torch.float32 or tuple(out.shape) != (M, Ncols):
+        raise ValueError(f"out must be a float32 tensor of shape ({M}, {Ncols})")
+    if out.device != device:
+        raise ValueError(f"out must be on {device}, like the operands")
+
+
 @dataclass
 class TreeNode:
     """One node of a non-uniform plan: ``rule`` (a rule or its name) applied
@@ -252,6 +274,7 @@ def scale_outside(A, B, d=None, eA=None, eB=None, stream=None):
     """One O step (Alg. 1 when d is None); returns (eA, eB)."""
     M, K = A.shape
     Nn = B.shape[1]
+    _check_exponents({"d": d, "eA": eA, "eB": eB}, {"d": K, "eA": M, "eB": Nn}, A.device)
     eA = eA if eA is not None else torch.empty(M, dtype=torch.int32, device=A.device)
     eB = eB if eB is not None else torch.empty(Nn, dtype=torch.int32, device=A.device)
     N.check(N.lib().fmm_scale_outside(_ptr(A), _ptr(B), DTYPE[A.dtype], M, K, Nn, _rowmajor(A, "A"),
@@ -264,6 +287,7 @@ def scale_inside(A, B, eA=None, eB=None, d=None, stream=None):
     """One I step (Alg. 2 when eA, eB are None); returns d."""
     M, K = A.shape
     Nn = B.shape[1]
+    _check_exponents({"eA": eA, "eB": eB, "d": d}, {"eA": M, "eB": Nn, "d": K}, A.device)
     d = d if d is not None else torch.empty(K, dtype=torch.int32, device=A.device)
     N.check(N.lib().fmm_scale_inside(_ptr(A), _ptr(B), DTYPE[A.dtype], M, K, Nn, _rowmajor(A, "A"),
                                      _rowmajor(B, "B"), _ptr(eA), _ptr(eB), _ptr(d), _stream(stream)),
@@ -300,10 +324,12 @@ def multiply(plan: Plan, A: torch.Tensor, B: torch.Tensor, eA=None, d=None, eB=N
     realigned); a cached one is used when not given."""
     M, K = A.shape
     K2, Nn = B.shape
-    if K != K2 or A.dtype != B.dtype:
-        raise ValueError("shape / dtype mismatch")
+    if K != K2 or A.dtype != B.dtype or B.device != A.device:
+        raise ValueError("shape / dtype / device mismatch")
+    _check_exponents({"eA": eA, "d": d, "eB": eB}, {"eA": M, "d": K, "eB": Nn}, A.device)
     if out is None:
         out = torch.empty((M, Nn), dtype=torch.float32, device=A.device)
+    _check_out(out, M, Nn, A.device)
     if ws is None:
         ws = _workspace(plan, M, K, Nn, A.device)
     N.check(N.lib().fmm_multiply(plan.handle, _ptr(A), _rowmajor(A, "A"), _ptr(B), _rowmajor(B, "B"),
@@ -317,6 +343,10 @@ def multiply_backward(plan: Plan, dC: torch.Tensor, A: torch.Tensor, B: torch.Te
     """(dA, dB) = (dC B^T, A^T dC) by the permuted fast rules."""
     M, K = A.shape
     Nn = B.shape[1]
+    if B.shape[0] != K or tuple(dC.shape) != (M, Nn) or A.dtype != B.dtype:
+        raise ValueError("dC must be M x N for A (M x K) and B (K x N) of one dtype")
+    if B.device != A.device or dC.device != A.device:
+        raise ValueError("dC, A and B must be on one device")
     dC = dC.contiguous().float()
     if ws is None:
         ws = _workspace(plan, M, K, Nn, A.device)

@@ -190,3 +190,35 @@ def test_host_pipeline_rejections(L, plans):
     assert L.fmm_host_submit(None, FAKE, 64, FAKE, 64, FAKE, 64) == ARG
     assert L.fmm_host_wait(None) == ARG
     assert L.fmm_host_destroy(None) == 0
+
+
+def test_python_wrappers_check_their_tensors(L):
+    # The wrappers reject output and exponent tensors the kernels would
+    # write past or misread, before anything reaches the library.
+    from paper_1507_00687_gb300 import api
+    plan = api.Plan(["strassen"], "bf16x3")
+    A, B = torch.zeros((64, 48)), torch.zeros((48, 32))
+    i32 = lambda n: torch.zeros(n, dtype=torch.int32)  # noqa: E731
+    bad = [
+        dict(out=torch.zeros((64, 32), dtype=torch.bfloat16)),      # 2-byte elements
+        dict(out=torch.zeros((64, 16))),                             # too few columns
+        dict(eA=torch.zeros(64, dtype=torch.int64)),                 # 8-byte exponents
+        dict(eA=i32(63)),                                            # one short
+        dict(d=i32(64)),                                             # d has length K = 48
+        dict(eB=i32(64)[::2]),                                       # strided
+        dict(eB=torch.zeros((32, 1), dtype=torch.int32)),            # not 1-D
+    ]
+    for kw in bad:
+        with pytest.raises(ValueError):
+            api.multiply(plan, A, B, **kw)
+    with pytest.raises(ValueError):
+        api.multiply(plan, A, torch.zeros((48, 32), dtype=torch.bfloat16))
+    with pytest.raises(ValueError):
+        api.multiply_backward(plan, torch.zeros((64, 31)), A, B)
+    with pytest.raises(ValueError):
+        api.scale_outside(A, B, d=i32(47))
+    with pytest.raises(ValueError):
+        api.scale_inside(A, B, eA=i32(64), eB=torch.zeros(32, dtype=torch.int16))
+    # well-formed tensors get past these checks and stop at the device check
+    with pytest.raises(ValueError, match="CUDA"):
+        api.multiply(plan, A, B, i32(64), i32(48), i32(32), out=torch.zeros((64, 40))[:, :32])
