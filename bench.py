@@ -490,7 +490,8 @@ def _oracle_timing_child(n: int, which: str, reps: int, q) -> None:
 
 
 def oracle_timing(args) -> dict:
-    """The float64 oracle on the host cores at n = 256, 4096 and 8192: the
+    """The CPU-baseline leg at more sizes and thread counts: the float64
+    oracle as it stands on the host cores at n = 256, 4096 and 8192, the
     classical product and Winograd one level, single-threaded (the paper's
     Sec. 6.5 setting) and on all cores, median of 5 (3 at n = 8192), as
     effective GFLOP/s 2 n^3 / t."""
