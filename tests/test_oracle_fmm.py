@@ -264,3 +264,48 @@ def test_error_norms_on_a_hand_computed_case():
     # componentwise error unchanged and scales the max-norm error
     assert F.err_componentwise(-8.0 * C_hat, -8.0 * C) == pytest.approx(0.25, rel=1e-15)
     assert F.err_max(-8.0 * C_hat, -8.0 * C) == 56.0
+
+
+def test_sums_follow_index_order_in_the_working_precision():
+    # Eq. 4.3's model: S_r, T_r and C_k are sequential sums in index order,
+    # each step rounded to the working precision.  In FP32, 1 + 2^-24 is a
+    # tie that rounds to 1 (even), so 1 + 2^-24 + 2^-24 stays 1 in index
+    # order but is 1 + 2^-23 if the two small terms meet first.  Winograd
+    # (flattened, row-major): S_2 = a11 + a12 - a21 - a22,
+    # T_5 = b11 - b12 + b22, c12 = m1 + m3 + m5 + m6.
+    u = 2.0 ** -24
+    A = np.array([[1.0, u], [-u, 0.0]])
+    B = np.array([[1.0, -u], [0.0, u]])
+    M = {0: 1.0, 2: u, 4: u, 5: 0.0}
+    rec = []
+
+    def leaf(S, T):
+        rec.append((float(S[0, 0]), float(T[0, 0])))
+        return np.array([[M.get(len(rec) - 1, 0.0)]])
+    C = F.fmm(A, B, F.uniform([Wg]), leaf=leaf, dtype=np.float32)
+    assert rec[2][0] == 1.0 and rec[5][1] == 1.0 and C[0, 1] == 1.0
+    rec.clear()
+    C = F.fmm(A, B, F.uniform([Wg]), leaf=leaf, dtype=np.float64)
+    assert rec[2][0] == 1 + 2 * u and rec[5][1] == 1 + 2 * u and C[0, 1] == 1 + 2 * u
+
+
+def test_between_exponents_come_from_fp32_sums():
+    # The between-steps exponents are taken from the root's sums formed in
+    # FP32, the precision the operand sums are formed in: T_1 of Strassen's
+    # first product is b11 + b22 = 0.75 + (0.25 - 2^-26), which is 1 - 2^-26
+    # exactly (frexp exponent 0) but 1 in FP32 (exponent 1); with
+    # S_1 = a11 + a22 = 1, d = floor((e(T) - e(S)) / 2) is 0, not -1.
+    A = np.array([[1.0, 0.0], [0.0, 0.0]])
+    B = np.array([[0.75, 0.0], [0.0, 0.25 - 2.0 ** -26]])
+    d = F.between_exponents(A, B, F.uniform([S, S]))
+    assert list(d[0]) == [0]
+
+
+def test_flop_count_on_a_rectangular_plan():
+    # <2,1,1> over the rotated <3,3,2>: pm = 6, pk = 3, pn = 2, 2 x 15
+    # leaves; leaf flops 2 R^L (Mp/pm)(Kp/pk)(Np/pn) on the padded shape.
+    plan = F.uniform([R.classical(2, 1, 1), R.rotate(R.fast323())])
+    assert F.dims(plan) == (6, 3, 2)
+    f = F.flop_count(plan, 12, 9, 4)
+    assert f["leaves"] == 30 and f["leaf"] == 2.0 * 30 * 2 * 3 * 2 and f["classical"] == 2.0 * 12 * 9 * 4
+    assert F.flop_count(plan, 13, 9, 5)["leaf"] == 2.0 * 30 * 3 * 3 * 3

@@ -126,3 +126,20 @@ def test_e4m3_leaf_scales_rows_of_s_and_columns_of_t():
     B = g.integers(-3, 4, (512, 128)).astype(np.float64)
     from oracle import rules as R
     assert np.array_equal(F.fmm(A, B, F.uniform([R.strassen()]), leaf=F.leaf_e4m3_b128), A @ B)
+
+
+def test_e4m3_block_quantization_by_hand():
+    # One block [200, 1.25 * 2^-9]: its max 200 has frexp exponent 8, so
+    # s = 0 and the entries are rounded on the E4M3 grid itself: 200 lies
+    # midway between 192 and 208 and goes to the even significand (192);
+    # 1.25 * 2^-9 is a subnormal multiple of 2^-9 and goes to 2^-9.
+    from oracle import fmm as F
+    q, s = F.quantize_e4m3_blocks(np.array([[200.0, 1.25 * 2.0 ** -9]]), axis=1)
+    assert s.tolist() == [[0]] and q.tolist() == [[192.0, 2.0 ** -9]]
+
+
+def test_non_finite_values_pass_through():
+    x = np.array([np.inf, -np.inf, np.nan, 1.0])
+    for fmt in ("bf16", "fp16", "fp32"):
+        r = P.round_to(x, fmt)
+        assert r[0] == np.inf and r[1] == -np.inf and np.isnan(r[2]) and r[3] == 1.0

@@ -197,3 +197,76 @@ def test_stated_order_reindexing():
         assert R.brent_violations(s) == 0
         c0, c1 = R.canonical(r), R.canonical(s)
         assert np.array_equal(c0.U, c1.U) and np.array_equal(c0.V, c1.V) and np.array_equal(c0.W, c1.W)
+
+
+def _flattened_by_recursion(rules):
+    """[[U, V, W]] of L levels read off the recursion of Eq. 3.2 itself:
+    one product whose finest blocks are unit vectors, with a leaf that
+    records S_r and T_r and returns e_r (so C block k holds row k of W)."""
+    node = F.uniform(rules)
+    pm, pk, pn = F.dims(node)
+    R_ = int(np.prod([r.R for r in rules]))
+    P = max(pm * pk, pk * pn)
+    A = np.zeros((pm, pk * P))
+    for p in range(pm):
+        for q in range(pk):
+            A[p, q * P + p * pk + q] = 1.0
+    B = np.zeros((pk * P, pn * R_))
+    for p in range(pk):
+        for q in range(pn):
+            B[p * P + p * pn + q, q * R_] = 1.0
+    Us, Vs = [], []
+
+    def leaf(S, T):
+        out = np.zeros((1, R_))
+        out[0, len(Us)] = 1.0
+        Us.append(S[0, :pm * pk].copy())
+        Vs.append(T[:pk * pn, 0].copy())
+        return out
+    C = F.fmm(A, B, node, leaf=leaf)
+    W = np.stack([C[p, q * R_:(q + 1) * R_] for p in range(pm) for q in range(pn)])
+    return np.stack(Us, axis=1), np.stack(Vs, axis=1), W
+
+
+@pytest.mark.parametrize("pair", [("strassen", "classical121"), ("winograd", "strassen"),
+                                  ("fast323", "classical211"), ("classical121", "fast323")])
+def test_composition_is_the_recursions_flattening(pair):
+    # Eq. 4.4: leaf (r1, r2) of two levels multiplies S = sum U[i1,r1]
+    # U[i2,r2] A_(i1,i2) by T likewise and adds W[k1,r1] W[k2,r2] times the
+    # product into C block (k1,k2); the recursion visits r2 fastest, so the
+    # composite's product r1 R2 + r2 must be the recursion's leaf number
+    # r1 R2 + r2, entry for entry.
+    mk = {"strassen": R.strassen, "winograd": R.winograd, "fast323": R.fast323,
+          "classical121": lambda: R.classical(1, 2, 1), "classical211": lambda: R.classical(2, 1, 1)}
+    outer, inner = mk[pair[0]](), mk[pair[1]]()
+    comp = R.compose(outer, inner)
+    U, V, W = _flattened_by_recursion([outer, inner])
+    assert np.array_equal(comp.U, U) and np.array_equal(comp.V, V) and np.array_equal(comp.W, W)
+
+
+def test_principal_quantities_under_product_rescaling():
+    # Scaling product r's A-combination by c_r and its output row by 1/c_r
+    # (U_r -> c_r U_r, W_r -> W_r / c_r) or its B-combination likewise gives
+    # another rule for the same product: the nonzero counts (alpha, beta,
+    # gamma, Q, nnz) stay, a_r (b_r) = ||u_r||_1 (||v_r||_1) scales by
+    # |c_r|, and every e_k = sum_r a_r b_r |w_kr| is unchanged (Defs.
+    # 4.1-4.2).  Powers of two keep every product exact.
+    s = R.canonical(R.strassen())
+    p0 = R.principal(s)
+    c = np.array([2.0, 0.5, 4.0, 1.0, 0.25, 2.0, 8.0])
+    for which in ("U", "V"):
+        U, V = s.U.copy(), s.V.copy()
+        if which == "U":
+            U = U * c[None, :]
+        else:
+            V = V * c[None, :]
+        r = R.Rule("rescaled", 2, 2, 2, U, V, s.W / c[None, :], "row", "row", "row", "test")
+        assert R.brent_violations(r) == 0
+        p = R.principal(r)
+        assert np.array_equal(p.alpha, p0.alpha) and np.array_equal(p.beta, p0.beta)
+        assert p.Q == p0.Q and p.nnz == p0.nnz
+        scaled = p.a if which == "U" else p.b
+        same = p.b if which == "U" else p.a
+        base = p0.a if which == "U" else p0.b
+        assert np.array_equal(scaled, base * c) and np.array_equal(same, p0.b if which == "U" else p0.a)
+        assert np.allclose(p.e, p0.e) and p.E == p0.E

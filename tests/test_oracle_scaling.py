@@ -110,6 +110,14 @@ def test_pow2_zero_rows_and_cols():
     st = Sc.pow2_repeated(A, B, "OIOI")
     assert st.eA[0] == 0 and st.eB[0] == 0
     assert np.all(np.isfinite(st.A)) and np.all(np.isfinite(st.B))
+    # an I step with one side zero leaves d_k = 0, whatever the other side
+    # holds: column 0 of A is zero while row 0 of B is large, row 1 of B is
+    # zero while column 1 of A is large; k = 2 has both sides, max 2 in A
+    # (frexp exponent 2) and 1 in B (exponent 1): floor((1 - 2) / 2) = -1
+    A = np.array([[0.0, 64.0, 1.0], [0.0, 32.0, 2.0]])
+    B = np.array([[64.0, 128.0], [0.0, 0.0], [1.0, 0.5]])
+    st = Sc.pow2_repeated(A, B, "I")
+    assert list(st.d) == [0, 0, -1]
 
 
 @pytest.mark.parametrize("kind", [1, 2, 3])

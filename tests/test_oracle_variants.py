@@ -110,6 +110,24 @@ def test_matrix_selection_minimal_at_every_node(name):
             s = np.abs(c.U).T @ np.array(qa)
             t = np.abs(c.V).T @ np.array(qb)
             assert costs[0][v] == float((np.abs(c.W) @ (s * t)).max())
+        if levels == 2:
+            # the children's costs by brute force too: child r of the
+            # chosen root variant multiplies sum_i U_ir A_i by sum_j V_jr
+            # B_j, whose 2 x 2 block bounds are sum_i |U_ir| (quadrant i of
+            # Amax) and sum_j |V_jr| (quadrant j of Bmax)
+            root = R.canonical(CG.variant(base, chosen[0]))
+            for r in range(root.R):
+                Ab = sum(abs(root.U[i, r]) * Amax[(i // 2) * 2:(i // 2) * 2 + 2, (i % 2) * 2:(i % 2) * 2 + 2]
+                         for i in range(4))
+                Bb = sum(abs(root.V[j, r]) * Bmax[(j // 2) * 2:(j // 2) * 2 + 2, (j % 2) * 2:(j % 2) * 2 + 2]
+                         for j in range(4))
+                qa2 = [Ab[p, q] for p in (0, 1) for q in (0, 1)]
+                qb2 = [Bb[p, q] for p in (0, 1) for q in (0, 1)]
+                for v in range(8):
+                    c = R.canonical(CG.variant(base, v))
+                    s2 = np.abs(c.U).T @ np.array(qa2)
+                    t2 = np.abs(c.V).T @ np.array(qb2)
+                    assert costs[1 + r][v] == float((np.abs(c.W) @ (s2 * t2)).max()), (r, v)
 
 
 @pytest.mark.parametrize("name", sorted(BASES))
@@ -172,3 +190,21 @@ def test_child_bounds_hold_and_are_attained(name):
                     quad(X, i)[...] *= np.sign(T[i, r]) if T[i, r] != 0 else 1.0
                 S = sum(float(T[i, r]) * quad(X, i) for i in range(4))
                 assert np.array_equal(CG.block_max(S, 2, 2), CG.child_bounds(T, Xmax, r))
+
+
+def test_tree_nodes_in_level_order():
+    # node n of the level-order list runs variant chosen[n]; a node's
+    # children follow in product order, level by level: at three levels,
+    # the child r2 of the root's child r1 is node 1 + R + R r1 + r2
+    base = R.strassen()
+    chosen = CG.select_random(7, 3, seed=5)
+    t = CG.tree(base, 3, chosen)
+    same = lambda a, b: (np.array_equal(a.U, b.U) and np.array_equal(a.V, b.V)  # noqa: E731
+                         and np.array_equal(a.W, b.W))
+    v = [CG.variant(base, k) for k in range(8)]
+    assert same(t.rule, v[chosen[0]])
+    for r1 in range(7):
+        assert same(t.children[r1].rule, v[chosen[1 + r1]])
+        for r2 in range(7):
+            node = t.children[r1].children[r2]
+            assert same(node.rule, v[chosen[8 + 7 * r1 + r2]]) and node.children == [None] * 7
