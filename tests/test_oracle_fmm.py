@@ -309,3 +309,51 @@ def test_flop_count_on_a_rectangular_plan():
     f = F.flop_count(plan, 12, 9, 4)
     assert f["leaves"] == 30 and f["leaf"] == 2.0 * 30 * 2 * 3 * 2 and f["classical"] == 2.0 * 12 * 9 * 4
     assert F.flop_count(plan, 13, 9, 5)["leaf"] == 2.0 * 30 * 3 * 3 * 3
+
+
+def test_delta_vector_entries_of_one_level():
+    # Sec. 4.5 / Def. 4.1 for one Strassen level: delta_k = gamma_k + max
+    # over the products feeding C block k of alpha_r + beta_r (canonical
+    # order c11, c12, c21, c22): c11 = m1 + m4 - m5 + m7 -> 4 + 4,
+    # c12 = m3 + m5 -> 2 + 3, c21 = m2 + m4 -> 2 + 3, c22 = m1 - m2 + m3 + m6
+    # -> 4 + 4.  Two levels add each path's counts: max is 8 + 8.
+    assert list(F.delta_vector(F.uniform([S]))) == [8.0, 5.0, 5.0, 8.0]
+    assert F.delta_vector(F.uniform([S, S])).max() == 16.0
+
+
+def test_rounded_leaves_round_both_operands():
+    # 1 + 2^-8 is a bf16 tie (and 1 + 2^-11 an fp16 one) that rounds to 1:
+    # the leaf multiplies the rounded S and T, so the product is exactly 1.
+    for fmt, u in (("bf16", 2.0 ** -8), ("fp16", 2.0 ** -11)):
+        x = np.array([[1.0 + u]])
+        assert F.leaf_rounded(fmt)(x, x)[0, 0] == 1.0
+
+
+def test_growth_with_between_scaling_assembled_by_hand():
+    # With scaling between recursive steps, root product r's absolute sums
+    # |S_r| = sum_i |U_ir| |A_i| and |T_r| = sum_j |V_jr| |B_j| are scaled by
+    # 2^d (columns of S_r) and 2^-d (rows of T_r), d from the root's signed
+    # sums; the lower levels' growth of that scaled pair, weighted by |W|,
+    # gives G.  Assembled here block by block from the growth of the lower
+    # plan, with inputs whose exponents are not all zero.
+    g = np.random.default_rng(8)
+    n = 16
+    A = g.uniform(-1, 1, (n, n)) * np.exp2(g.integers(-6, 7, (1, n)))
+    B = g.uniform(-1, 1, (n, n)) * np.exp2(g.integers(-6, 7, (n, 1)))
+    plan = F.uniform([S, Wg])
+    d = F.between_exponents(A, B, plan)
+    assert any(np.any(v != 0) for v in d)
+    c = R.canonical(S)
+    h = n // 2
+    Ab = [np.abs(A[p * h:(p + 1) * h, q * h:(q + 1) * h]) for p in (0, 1) for q in (0, 1)]
+    Bb = [np.abs(B[p * h:(p + 1) * h, q * h:(q + 1) * h]) for p in (0, 1) for q in (0, 1)]
+    G = np.zeros((n, n))
+    for r in range(7):
+        Sr = sum(abs(c.U[i, r]) * Ab[i] for i in range(4)) * np.exp2(d[r].astype(float))[None, :]
+        Tr = sum(abs(c.V[j, r]) * Bb[j] for j in range(4)) * np.exp2(-d[r].astype(float))[:, None]
+        Gr = F.growth(Sr, Tr, F.uniform([Wg]))
+        for k in range(4):
+            p, q = divmod(k, 2)
+            G[p * h:(p + 1) * h, q * h:(q + 1) * h] += abs(c.W[k, r]) * Gr
+    assert np.allclose(F.growth(A, B, plan, between=True), G, rtol=1e-14, atol=0)
+    assert not np.allclose(F.growth(A, B, plan), G, rtol=1e-6, atol=0)

@@ -143,3 +143,16 @@ def test_non_finite_values_pass_through():
     for fmt in ("bf16", "fp16", "fp32"):
         r = P.round_to(x, fmt)
         assert r[0] == np.inf and r[1] == -np.inf and np.isnan(r[2]) and r[3] == 1.0
+
+
+def test_e4m3_block_max_is_by_magnitude_and_saturation():
+    # The block scale follows the largest magnitude, here a negative entry:
+    # -200 gives s = 0 and rounds to -192 (a tie, even significand).
+    from oracle import fmm as F
+    q, s = F.quantize_e4m3_blocks(np.array([[-200.0, 1.0]]), axis=1)
+    assert s.tolist() == [[0]] and q.tolist() == [[-192.0, 1.0]]
+    # overflow: infinity by default, the largest finite value when saturating
+    big = float.fromhex("0x1.fep127")
+    assert P.round_to(np.array([1e39]), "bf16")[0] == np.inf
+    assert P.round_to(np.array([1e39, -1e39]), "bf16", saturate=True).tolist() == [big, -big]
+    assert P.round_to(np.array([7e4]), "fp16", saturate=True)[0] == 65504.0

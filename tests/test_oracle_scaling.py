@@ -118,6 +118,11 @@ def test_pow2_zero_rows_and_cols():
     B = np.array([[64.0, 128.0], [0.0, 0.0], [1.0, 0.5]])
     st = Sc.pow2_repeated(A, B, "I")
     assert list(st.d) == [0, 0, -1]
+    # the real-valued steps give zero rows / columns the scale 1 as well
+    A = np.array([[0.0, 0.0], [3.0, 1.0]])
+    B = np.array([[0.0, 2.0], [0.0, 5.0]])
+    st = Sc.repeated(A, B, "OI")
+    assert st.r[0] == 1.0 and st.s[0] == 1.0 and st.r[1] == 3.0 and st.s[1] == 5.0
 
 
 @pytest.mark.parametrize("kind", [1, 2, 3])
