@@ -563,6 +563,22 @@ fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc,
                                  int64_t ldda, float* dB, int64_t lddb, int64_t M, int64_t K,
                                  int64_t N, int in_dtype, void* ws, size_t ws_bytes, void* stream);
 
+/* Gradients fmm_plan_gradient returns the plan of. */
+enum { FMM_GRAD_A = 0, FMM_GRAD_B = 1 };
+
+/*
+ * The plan fmm_multiply_backward runs for one gradient, as a plan of its
+ * own (for inspection with fmm_plan_info / fmm_plan_flatten, or to run a
+ * gradient product through fmm_multiply): FMM_GRAD_A gives the
+ * <pm, pn, pk> plan of dA = dC B^T whose levels (or tree nodes) use
+ * [[W, V^T, U]], FMM_GRAD_B the <pk, pm, pn> plan of dB = A^T dC with
+ * [[U^T, W, V]]; a tree keeps its shape, every node's rule transformed;
+ * the leaf format and schedule are the plan's.  *out is a new plan owned
+ * by the caller (fmm_plan_destroy).  Host only.  FMM_ERR_ARG for a NULL
+ * plan or out, or an unknown `which`.
+ */
+fmm_status fmm_plan_gradient(fmm_plan_t plan, int which, fmm_plan_t* out);
+
 /*
  * Host-memory pipeline (not from the paper: the paper's products live in
  * one memory).  For a stream of products of one shape whose operands and

@@ -33,10 +33,11 @@ EXPORTS = [
     "fmm_plan_set_between_scaling", "fmm_plan_tree", "fmm_scale_adaptive",
     "fmm_host_create", "fmm_host_submit", "fmm_host_wait", "fmm_host_destroy",
     "fmm_rule_rotate", "fmm_rule_compose", "fmm_rule_transform", "fmm_rule_permute", "fmm_plan_variants",
-    "fmm_block_max", "fmm_batch_partition", "fmm_plan_flatten",
+    "fmm_block_max", "fmm_batch_partition", "fmm_plan_flatten", "fmm_plan_gradient",
 ]
 SELECT_RANDOM, SELECT_ROUND_ROBIN, SELECT_MATRIX = 0, 1, 2
 TABLE_LEAVES, TABLE_LISTS, TABLE_GATHER = 0, 1, 2
+GRAD_A, GRAD_B = 0, 1
 
 # Bytes of the library's static scratch array (FMM_NOALLOC_SCRATCH_BYTES).
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -105,6 +106,7 @@ def lib():
                                 C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     L.fmm_plan_bound.argtypes = [vp, i64, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
     L.fmm_plan_flatten.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+    L.fmm_plan_gradient.argtypes = [vp, C.c_int, C.POINTER(vp)]
     L.fmm_scale_outside.argtypes = [vp, vp, C.c_int, i64, i64, i64, i64, i64, vp, vp, vp, vp]
     L.fmm_scale_inside.argtypes = [vp, vp, C.c_int, i64, i64, i64, i64, i64, vp, vp, vp, vp]
     L.fmm_scale_adaptive.argtypes = [vp, vp, C.c_int, i64, i64, i64, i64, i64, C.c_double, C.c_int, C.c_int,

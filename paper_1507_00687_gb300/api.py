@@ -206,6 +206,18 @@ class Plan:
         N.check(N.lib().fmm_plan_flatten(self._h, t, ptr(U), ptr(V), ptr(W), ptr(first)), "fmm_plan_flatten")
         return U, V, W, first
 
+    def gradient(self, which: str) -> "Plan":
+        """The plan fmm_multiply_backward runs for "dA" (dC B^T, [[W, V^T, U]]
+        per level or node) or "dB" (A^T dC, [[U^T, W, V]]), as a plan of its
+        own (fmm_plan_gradient)."""
+        w = {"dA": N.GRAD_A, "dB": N.GRAD_B}[which]
+        h = C.c_void_p()
+        N.check(N.lib().fmm_plan_gradient(self._h, w, C.byref(h)), "fmm_plan_gradient")
+        g = Plan.__new__(Plan)
+        g._keep, g.rules, g.leaf, g.node_rule = [], [], self.leaf, self.node_rule
+        g.schedule, g.between, g._h = self.schedule, False, h
+        return g
+
     def bound(self, K: int, normA: float, normB: float, eps: float) -> float:
         b = C.c_double()
         N.check(N.lib().fmm_plan_bound(self._h, K, normA, normB, eps, C.byref(b)), "fmm_plan_bound")

@@ -1707,6 +1707,23 @@ fmm_status fmm_multiply_noalloc(fmm_plan_t plan, const void* A, int64_t lda, con
                   reinterpret_cast<const LeafDesc*>(scratch), /*allow_between=*/false);
 }
 
+fmm_status fmm_plan_gradient(fmm_plan_t plan, int which, fmm_plan_t* out) {
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  if (!p || !out || (which != FMM_GRAD_A && which != FMM_GRAD_B)) return FMM_ERR_ARG;
+  *out = nullptr;
+  // the same rule transforms and plan compiler calls as the backward pass
+  const bool tree = !p->node_rule.empty();
+  std::vector<CanonRule> g;
+  for (const auto& r : tree ? p->table : p->rules)
+    g.push_back(which == FMM_GRAD_A ? rule_for_grad_a(r) : rule_for_grad_b(r));
+  Plan* q = nullptr;
+  fmm_status s = make_plan(g, p->leaf_format, &q, tree ? &p->node_rule : nullptr, p->levels);
+  if (s != FMM_OK) return s;
+  q->schedule = p->schedule;
+  *out = reinterpret_cast<fmm_plan_t>(q);
+  return FMM_OK;
+}
+
 fmm_status fmm_multiply_backward(fmm_plan_t plan, const float* dC, int64_t lddc, const void* A, int64_t lda,
                                  const void* B, int64_t ldb, float* dA, int64_t ldda, float* dB, int64_t lddb,
                                  int64_t M, int64_t K, int64_t N, int in_dtype, void* ws, size_t ws_bytes,

@@ -477,3 +477,39 @@ def test_plan_flatten_rejections(native):
     assert L.fmm_plan_flatten(plan._h, 3, None, None, None, None) == 1
     assert L.fmm_plan_flatten(plan._h, -1, None, None, None, None) == 1
     assert L.fmm_plan_flatten(plan._h, 2, None, None, None, None) == 0
+
+
+def _oracle_gradient_tree(node, which):
+    """The oracle's tree with every node's rule replaced by its gradient
+    rule (rule_for_dA / rule_for_dB), the shape kept."""
+    if node is None:
+        return None
+    f = OR.rule_for_dA if which == "dA" else OR.rule_for_dB
+    return OF.Node(f(node.rule), [_oracle_gradient_tree(c, which) for c in node.children])
+
+
+def test_gradient_plans_are_the_transformed_rules(native):
+    # The plan the backward pass runs for dA (dB) is the flattening of the
+    # plan's rules transformed to [[W, V^T, U]] ([[U^T, W, V]]) at every
+    # level or tree node (Sec. 5.3, App. A-C): Brent-valid, with the grid
+    # <pm, pn, pk> (<pk, pm, pn>), and equal, table for table, to the
+    # oracle's gradient rules flattened by its own recursion.
+    for plan, orc in _plan_cases():
+        info = plan.info()
+        for which, dims in (("dA", (info["pm"], info["pn"], info["pk"])),
+                            ("dB", (info["pk"], info["pm"], info["pn"]))):
+            g = plan.gradient(which)
+            gi = g.info()
+            assert (gi["pm"], gi["pk"], gi["pn"]) == dims and gi["leaves"] == info["leaves"]
+            U0, V0, W0 = _oracle_flattened(_oracle_gradient_tree(orc, which))
+            for table in ("leaves", "lists"):
+                U, V, W, first = g.flatten(table)
+                assert np.array_equal(U, U0) and np.array_equal(V, V0) and np.array_equal(W, W0), (which, table)
+                assert np.array_equal(first, _first_touch(W0))
+    L = native.lib()
+    h = C.c_void_p()
+    from paper_1507_00687_gb300 import api
+    p = api.Plan(["strassen"], "bf16")
+    assert L.fmm_plan_gradient(None, 0, C.byref(h)) == 1
+    assert L.fmm_plan_gradient(p._h, 2, C.byref(h)) == 1
+    assert L.fmm_plan_gradient(p._h, 0, None) == 1
