@@ -177,6 +177,17 @@ def test_tree_plan_mixed_ranks(native):
     assert native.lib().fmm_plan_set_between_scaling(_tree_plan(TC.dalberto())[0].handle, 1) == 0
 
 
+def test_tree_plan_delta_follows_the_feeding_products(native):
+    # max_k delta_k (Sec. 4.5) takes, for each C block, only the products
+    # that add into it: here the deep child sits under Winograd's m2, which
+    # adds into c11 alone (2 terms), so the maximum is 2 + 12 = 4 + 10 = 14,
+    # not the largest gamma plus the largest child (4 + 12 = 16).
+    import tree_cases as TC
+    plan, orc = _tree_plan(TC.uneven_delta())
+    assert float(OF.delta_vector(orc).max()) == 14.0
+    assert plan.info()["q_sum"] == 14.0
+
+
 def test_tree_plan_rejects_bad_trees(native):
     from paper_1507_00687_gb300 import api
     L = native.lib()
@@ -432,7 +443,7 @@ def _plan_cases():
     # a rotation (<3,3,2>, A and B grids of different sizes) over Strassen
     cases.append((api.Plan([PR.rotate(PR.get("fast323")), "strassen"], "bf16"),
                   OF.uniform([OR.rotate(OR.fast323()), OR.strassen()])))
-    for root, children in (TC.dalberto(), TC.fast323_nonuniform(), TC.mixed_rank()):
+    for root, children in (TC.dalberto(), TC.fast323_nonuniform(), TC.mixed_rank(), TC.uneven_delta()):
         lib, orc = TC.two_level(root, children)
         cases.append((api.Plan.tree(lib, "bf16"), orc))
     from oracle import variants as CG

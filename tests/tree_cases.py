@@ -119,3 +119,11 @@ def max_terms(orc):
     p = OR.principal(r)
     here = int(max(p.alpha.max(), p.beta.max(), (r.W != 0).sum(axis=0).max()))
     return here * max(max_terms(c) for c in orc.children)
+
+
+def uneven_delta():
+    """Winograd at the root, Winograd under its second product (which adds
+    into C block c11 alone, the block with the fewest terms) and classical
+    <2,2,2;8> under the others: the largest delta_k of Sec. 4.5 is not the
+    largest gamma_k plus the largest child delta."""
+    return ["Wg", ["Wg" if r == 1 else "C222" for r in range(7)]]
