@@ -58,6 +58,17 @@ def test_partition_within_lpt_bound_of_optimum(api):
             assert lpt <= (4.0 / 3.0 - 1.0 / (3 * parts)) * best + 1e-6, (dims, parts)
 
 
+def test_partition_order_and_ties(api):
+    # Longest processing time first, equal flop counts in index order, each
+    # product to the least-loaded part with ties to the lowest part: four
+    # equal products alternate 0, 1, 0, 1; a large product goes first and
+    # alone, the small ones then fill the other part before sharing.
+    assert api.partition_batch([(256, 256, 256)] * 4, 2) == [[0, 2], [1, 3]]
+    assert api.partition_batch([(256, 256, 256)] * 3, 3) == [[0], [1], [2]]
+    dims = [(128, 128, 128), (512, 512, 512), (128, 128, 128), (128, 128, 128)]
+    assert api.partition_batch(dims, 2) == [[1], [0, 2, 3]]
+
+
 def test_partition_rejects_bad_arguments(api):
     from paper_1507_00687_gb300 import _native as N
     import ctypes as C

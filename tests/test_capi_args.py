@@ -154,6 +154,13 @@ def test_batch_rejections(L, plans):
     assert ws(probs((b16, 256, 256, 256)), 1, 9, b"OI", C.byref(n)) == ARG
     assert ws(probs((None, 256, 256, 256)), 1, 1, b"OI", C.byref(n)) == ARG
     assert ws(probs((b16, 0, 256, 256)), 1, 1, b"OI", C.byref(n)) == SHAPE
+    bad_ld = probs((b16, 256, 256, 256), (b16, 256, 256, 256))
+    bad_ld[1].lda, bad_ld[1].ldb, bad_ld[1].ldc = 256, 256, 255
+    assert ws(bad_ld, 2, 1, b"OI", C.byref(n)) == SHAPE                  # ldc < N
+    bad_ld[1].ldc, bad_ld[1].ldb = 256, 255
+    assert ws(bad_ld, 2, 1, b"OI", C.byref(n)) == SHAPE                  # ldb < N
+    bad_ld[1].ldb, bad_ld[1].lda = 256, 255
+    assert ws(bad_ld, 2, 1, b"OI", C.byref(n)) == SHAPE                  # lda < K
     assert ws(probs((b16, 256, 256, 256), (x3, 256, 256, 256)), 2, 1, b"OI", C.byref(n)) == ARG  # mixed leaves
     assert ws(probs((x3, 256, 256, 256)), 1, 2, b"OI", C.byref(n)) == DTYPE
     assert ws(probs((e4, 256, 256, 256)), 1, 1, b"OI", C.byref(n)) == UNSUPPORTED
