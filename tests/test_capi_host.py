@@ -524,3 +524,30 @@ def test_gradient_plans_are_the_transformed_rules(native):
     assert L.fmm_plan_gradient(None, 0, C.byref(h)) == 1
     assert L.fmm_plan_gradient(p._h, 2, C.byref(h)) == 1
     assert L.fmm_plan_gradient(p._h, 0, None) == 1
+
+
+def test_binding_matches_header_signatures(native):
+    # Every declaration in include/fmm.h has a ctypes signature with the
+    # same number of parameters, each of the same kind and width (the
+    # binding is argument marshalling only, so a mismatch would pass wrong
+    # values across the C ABI without any error).
+    src = open(os.path.join(ROOT, "include", "fmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    decls = re.findall(r"(?:const\s+char\s*\*|fmm_status)\s*(fmm_\w+)\s*\(([^)]*)\)\s*;", src)
+    assert len(decls) == len(header_symbols())
+    scalar = {"int": C.c_int, "int64_t": C.c_int64, "size_t": C.c_size_t, "double": C.c_double,
+              "uint64_t": C.c_uint64, "fmm_status": C.c_int}
+    handles = ("fmm_plan_t", "fmm_batch_t", "fmm_host_t")
+    L = native.lib()
+    for name, params in decls:
+        params = params.strip()
+        plist = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+        argtypes = getattr(L, name).argtypes
+        assert argtypes is not None and len(argtypes) == len(plist), name
+        for p, at in zip(plist, argtypes):
+            ptype = re.sub(r"\s*\b\w+$", "", p).replace("const ", "").strip()   # drop the parameter name
+            if "*" in ptype or ptype in handles:
+                ok = at in (C.c_void_p, C.c_char_p) or hasattr(at, "_type_") and issubclass(at, C._Pointer)
+            else:
+                ok = at is scalar[ptype]
+            assert ok, (name, p, at)
