@@ -962,6 +962,8 @@ def main():
                                  "frac": (pass_bytes / (comb_ms / bd_steps * 1e-3) / 1e9 / peaks["hbm_gbs"])
                                  if peaks.get("hbm_gbs") else None} if comb_n else None),
            "executed_flop_fraction": achieved / peak_m,
+           # a fraction of the measured library GEMM rate, not of a clock-derived tensor-pipe peak
+           "executed_flop_fraction_of": peak_src_m,
            "step_dram_traffic": step_traffic,
            "error": {"max_abs_err_vs_fp64": err_fast, "theorem_4_1_bound_unscaled": bound_unscaled,
                      "eps_leaf": eps_leaf, "normA": normA, "normB": normB},
