@@ -551,3 +551,35 @@ def test_binding_matches_header_signatures(native):
             else:
                 ok = at is scalar[ptype]
             assert ok, (name, p, at)
+
+
+def test_workspace_covers_what_the_pass_schedule_writes(native):
+    # fmm_workspace_size must hold, for the forward product and both
+    # gradient products, at least what the pass schedule writes: every
+    # leaf's combined A and B blocks (16-bit, two planes for bf16 hi+lo; for
+    # E4M3 one byte plus one scale byte per 128-block of each row) and, with
+    # more than one leaf, the FP32 stored products -- an unpadded lower
+    # bound computed here from the plan's grid alone.
+    from paper_1507_00687_gb300 import api
+    g = np.random.default_rng(17)
+    cdiv = lambda a, b: -(-a // b)  # noqa: E731
+
+    def lower(leaf, R, pm, pk, pn, M, K, N):
+        bm, bk, bn = cdiv(M, pm), cdiv(K, pk), cdiv(N, pn)
+        prods = R * bm * bn * 4 if R > 1 else 0
+        if leaf == "e4m3b128":
+            return R * (bm + bn) * bk + R * (bm + bn) * cdiv(bk, 128) + prods
+        planes = 2 if leaf == "bf16x3" else 1
+        return planes * R * (bm + bn) * bk * 2 + prods
+
+    for names in (["winograd"], ["strassen", "classical121"], ["winograd"] * 2, ["fast323"], []):
+        for leaf in ("bf16", "bf16x3", "e4m3b128"):
+            plan = api.Plan(names, leaf)
+            info = plan.info()
+            R, pm, pk, pn = info["leaves"], info["pm"], info["pk"], info["pn"]
+            for _ in range(6):
+                M, K, N = (int(x) for x in g.integers(1, 5000, size=3))
+                need = max(lower(leaf, R, pm, pk, pn, M, K, N),     # C = A B
+                           lower(leaf, R, pm, pn, pk, M, N, K),     # dA = dC B^T
+                           lower(leaf, R, pk, pm, pn, K, M, N))     # dB = A^T dC
+                assert api.workspace_bytes(plan, M, K, N) >= need, (names, leaf, M, K, N)
