@@ -229,3 +229,36 @@ def test_python_wrappers_check_their_tensors(L):
     # well-formed tensors get past these checks and stop at the device check
     with pytest.raises(ValueError, match="CUDA"):
         api.multiply(plan, A, B, i32(64), i32(48), i32(32), out=torch.zeros((64, 40))[:, :32])
+
+
+def test_batch_workspace_covers_every_entry():
+    # fmm_batch_workspace_size holds at least every entry's exponent vectors
+    # and what its passes write: the combined (or, for a classical entry
+    # whose data needs converting, the converted) operands and, with more
+    # than one leaf, the FP32 stored products; classical entries with bf16
+    # data and bf16 leaves read the caller's matrices and need none.
+    import numpy as np
+    from paper_1507_00687_gb300 import _native as N
+    from paper_1507_00687_gb300 import api
+    cdiv = lambda a, b: -(-a // b)  # noqa: E731
+    g = np.random.default_rng(23)
+    for dt in (N.DT_F32, N.DT_BF16):
+        for leaf in ("bf16", "bf16x3"):
+            plans = [api.Plan(r, leaf) for r in ([], ["winograd"], ["strassen", "strassen"])]
+            specs, need = [], 0
+            for i in range(12):
+                p = plans[i % 3]
+                M, K, N_ = (int(x) for x in g.integers(1, 40, size=3) * 64)
+                specs.append((p, M, K, N_))
+                inf = p.info()
+                R, bm, bk, bn = inf["leaves"], cdiv(M, inf["pm"]), cdiv(K, inf["pk"]), cdiv(N_, inf["pn"])
+                need += 4 * (M + K + N_)
+                direct = R == 1 and dt == N.DT_BF16 and leaf == "bf16"
+                if not direct:
+                    need += (2 if leaf == "bf16x3" else 1) * R * (bm + bn) * bk * 2 + (R * bm * bn * 4 if R > 1 else 0)
+            arr = (N.FmmProblem * len(specs))()
+            for i, (p, M, K, N_) in enumerate(specs):
+                arr[i] = N.FmmProblem(p._h.value, FAKE.value, K, FAKE.value, N_, FAKE.value, N_, M, K, N_)
+            n = C.c_size_t()
+            assert N.lib().fmm_batch_workspace_size(arr, len(specs), dt, b"OI", C.byref(n)) == 0
+            assert n.value >= need, (dt, leaf, n.value, need)
